@@ -1,0 +1,409 @@
+"""Pins for the CPU oracle: facts fixed by the ParAC paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a library
+routine (numpy's Philox), exact arithmetic, closed forms (degree <= 2 pivots
+are exact eliminations), invariants (zero row sums, spanning trees,
+dependency counters), the paper's worked example (Fig. 1, Sec. III), a
+statistical identity (E[G G^T] = L, Sec. II-B) and a dense direct solve.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_02977_gb300 import workloads as W
+from tests.helpers import reconstruct, same_factor
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- Philox
+def test_philox_matches_numpy_bitgenerator():
+    """Philox4x64-10 equals numpy's Philox (which advances the counter by one
+    before producing its first block)."""
+    rng = np.random.default_rng(1234)
+    for _ in range(50):
+        key = rng.integers(0, 2 ** 63, 2, dtype=np.uint64)
+        ctr = rng.integers(0, 2 ** 63, 4, dtype=np.uint64)
+        ref = np.random.Philox(key=key, counter=ctr).random_raw(4)
+        ctr1 = ctr.copy(); ctr1[0] += np.uint64(1)
+        assert np.array_equal(oracle.philox4x64_10(ctr1, key), ref)
+
+
+def test_slot_uniform_definition_and_range():
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        seed, k, p, s = (int(x) for x in rng.integers(0, 2 ** 40, 4))
+        raw = np.random.Philox(key=np.array([seed, 0], np.uint64),
+                               counter=np.array([k - 1 if k else 0, p, s, 0], np.uint64)).random_raw(1)[0] \
+            if k else None
+        v = oracle.slot_uniform(seed, k, p, s)
+        assert 0.0 < v <= 1.0
+        if raw is not None:
+            assert v == ((int(raw) >> 11) + 1) * 2.0 ** -53
+
+
+# ----------------------------------------------------------------- suffix sums
+def test_suffix_scan_exact_on_integers():
+    """Integer weights make every partial sum exact: any misplaced index shows."""
+    rng = np.random.default_rng(3)
+    for d in list(range(1, 70)) + [95, 96, 97, 128, 129, 300, 1025]:
+        w = rng.integers(1, 1000, d).astype(float)
+        S = oracle.suffix_scan(w)
+        assert np.array_equal(S, np.cumsum(w[::-1])[::-1])
+
+
+def test_suffix_scan_error_bound():
+    rng = np.random.default_rng(4)
+    for d in (1, 5, 31, 32, 33, 200, 5000):
+        w = np.sort(rng.lognormal(0, 2, d))
+        S = oracle.suffix_scan(w)
+        ref = np.array([math.fsum(w[i:]) for i in range(d)])
+        # every sum has at most ~(5 + d/32) rounded additions of positive terms
+        bound = (6 + d / 32 + 1) * 2.0 ** -53 * ref
+        assert np.all(np.abs(S - ref) <= bound)
+
+
+# ----------------------------------------------------------------- sampling search
+def test_pick_search_equals_literal_rule():
+    rng = np.random.default_rng(5)
+    for _ in range(3000):
+        d = int(rng.integers(1, 40))
+        S = np.cumsum(rng.random(d)[::-1])[::-1]
+        if rng.random() < 0.5:          # break monotonicity on purpose
+            S = S * (1 + 1e-15 * rng.standard_normal(d))
+            S[rng.integers(0, d)] *= 1.0 + rng.random() * 0.3
+        lo = int(rng.integers(0, d))
+        R = S[lo] * (rng.random() if rng.random() < 0.9 else 1.0)
+        assert oracle.pick_search(S, lo, R) == oracle.pick_bruteforce(S, lo, R)
+
+
+# ----------------------------------------------------------------- one pivot
+def _union_find_tree(nodes, edges):
+    parent = {v: v for v in nodes}
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+    for a, b in edges:
+        ra, rb = find(a), find(b)
+        if ra == rb:
+            return False
+        parent[ra] = rb
+    return len({find(v) for v in nodes}) == 1
+
+
+def test_eliminate_merge_factor_column_and_spanning_tree():
+    rng = np.random.default_rng(6)
+    for trial in range(300):
+        d0 = int(rng.integers(1, 30))
+        base = np.sort(rng.choice(np.arange(10, 10000), d0, replace=False)).astype(np.int32)
+        mult = rng.integers(1, 4, d0)
+        rows = np.repeat(base, mult)
+        w = rng.lognormal(0, 1, len(rows))
+        perm = rng.permutation(len(rows))
+        out = oracle.eliminate_one(rows[perm], w[perm], seed=trial, k=5)
+        assert out["d"] == d0
+        assert np.array_equal(out["rows"], base)
+        assert np.array_equal(out["mult"], mult)
+        for u, wu in zip(base, out["w"]):
+            assert wu == pytest.approx(w[rows == u].sum(), rel=1e-14)
+        assert out["D"] == pytest.approx(w.sum(), rel=1e-13)
+        assert np.all(out["fval"] == -out["w"] / out["D"])
+        # Alg. 2: d-1 sampled edges forming a spanning tree of N_k, each slot
+        # linked to a later slot of the weight order (Sec. II-B)
+        assert len(out["lo"]) == d0 - 1
+        assert np.all(out["lo"] < out["hi"])
+        assert np.all(out["pick"] >= np.arange(1, d0))
+        assert _union_find_tree(list(base), list(zip(out["lo"], out["hi"]))) if d0 > 1 else True
+
+
+def _expected_update(out):
+    """E[sampled clique] from the oracle's slot weights and Alg. 2's probabilities."""
+    rows = out["rows"]; w = out["w"]; D = out["D"]
+    order = np.lexsort((rows, w))          # weight order
+    ws = w[order]; rs = rows[order]
+    idx = {r: i for i, r in enumerate(rows)}
+    d = len(rows)
+    E = np.zeros((d, d))
+    S = np.cumsum(ws[::-1])[::-1]
+    for p in range(1, d):
+        c = out["c"][p - 1]                  # the oracle's weight for slot p
+        u = rs[p - 1]
+        for j in range(p, d):
+            prob = ws[j] / S[p]
+            a, b = idx[u], idx[rs[j]]
+            E[a, a] += prob * c; E[b, b] += prob * c; E[a, b] -= prob * c; E[b, a] -= prob * c
+    return E
+
+
+def test_unbiased_update_by_enumeration():
+    """Sum over all sampling outcomes of P(outcome) * C = C_exact (Sec. II-B)."""
+    rng = np.random.default_rng(8)
+    for trial in range(200):
+        d = int(rng.integers(1, 7))
+        rows = np.arange(100, 100 + d, dtype=np.int32)
+        w = rng.lognormal(0, 1, d)
+        out = oracle.eliminate_one(rows, w, seed=trial, k=1)
+        E = _expected_update(out)
+        wm = out["w"]; D = out["D"]
+        Cex = np.diag(wm) - np.outer(wm, wm) / D       # L^(k) - l_k l_k^T / l_kk on N_k
+        assert np.allclose(E, Cex, rtol=0, atol=1e-14 * max(1.0, np.abs(Cex).max()))
+
+
+def test_sampler_frequencies_chi_square():
+    """Slot p picks later entry j with probability w_j / S[p] (Alg. 2/3)."""
+    from scipy.stats import chi2
+    w = np.array([0.3, 0.5, 1.0, 1.7, 2.9, 4.1])
+    rows = np.arange(50, 56, dtype=np.int32)
+    d = len(w)
+    N = 20000
+    counts = np.zeros((d, d))
+    for k in range(N):
+        out = oracle.eliminate_one(rows, w, seed=99, k=k)
+        for p in range(1, d):
+            counts[p, out["pick"][p - 1]] += 1
+    S = np.cumsum(w[::-1])[::-1]
+    for p in range(1, d - 1):
+        exp = N * w[p:] / S[p]
+        stat = ((counts[p, p:] - exp) ** 2 / exp).sum()
+        assert chi2.sf(stat, d - p - 1) > 1e-4, (p, counts[p], exp)
+    assert counts[d - 1, d - 1] == N
+
+
+# ----------------------------------------------------------------- whole factors
+def _mat(n, a, b, w, excess=None):
+    return W.laplacian_from_edges(n, a, b, w, excess)
+
+
+@pytest.mark.parametrize("n", [2, 3, 10, 57])
+def test_path_and_cycle_exact_under_any_order(n):
+    """Pivots of degree <= 2 sample their only pair with weight w_i w_j/(w_i+w_j):
+    an exact series reduction, so F D F^T = L under every ordering."""
+    rng = np.random.default_rng(n)
+    for edges in (W.path_edges(n), W.cycle_edges(n) if n > 2 else W.path_edges(n)):
+        a, b = edges
+        A = _mat(n, a, b, rng.uniform(0.5, 5, len(a)))
+        Ad = A.dense()
+        for s in range(3):
+            perm = W.random_ordering(n, 10 * n + s)
+            F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=s)
+            assert np.allclose(reconstruct(F, perm), Ad, rtol=0, atol=1e-13 * np.abs(Ad).max())
+            assert np.sum(F["D"] == 0) == 1
+
+
+def test_tree_exact_with_leaf_first_order():
+    for s in range(5):
+        n = 40 + 13 * s
+        a, b = W.random_tree_edges(n, s)
+        A = _mat(n, a, b, np.random.default_rng(s).uniform(0.1, 9, len(a)))
+        perm = W.leaf_first_ordering(n, a, b, s)
+        F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=s)
+        Ad = A.dense()
+        assert np.allclose(reconstruct(F, perm), Ad, rtol=0, atol=1e-13 * np.abs(Ad).max())
+
+
+def test_tree_random_order_is_not_exact():
+    """Sanity check of the above: with degree-3 pivots the sample is a proper approximation."""
+    n = 60
+    a, b = W.random_tree_edges(n, 3)
+    A = _mat(n, a, b, np.ones(len(a)))
+    perm = W.random_ordering(n, 5)
+    F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=1)
+    assert F["max_gather"] >= 3
+    assert not np.allclose(reconstruct(F, perm), A.dense(), atol=1e-8)
+
+
+def test_sddm_with_ground_node_exact_on_a_path():
+    """SDDM -> Laplacian through a ground node (Sec. V); a path whose end has the
+    only excess stays a path after augmentation, so the factor is exact."""
+    n = 30
+    a, b = W.path_edges(n)
+    rng = np.random.default_rng(2)
+    exc = np.zeros(n); exc[n - 1] = 0.75
+    A = _mat(n, a, b, rng.uniform(1, 2, n - 1), exc)
+    for s in range(3):
+        perm = W.random_ordering(n, s)
+        F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=s, kind=oracle.KIND_SDDM)
+        Ad = A.dense()
+        assert np.allclose(reconstruct(F, perm), Ad, rtol=0, atol=1e-13 * np.abs(Ad).max())
+        assert np.all(F["D"] > 0)
+
+
+def test_zero_row_sums_of_reconstruction():
+    """Each sampled update is a Laplacian (Sec. II-B), so F D F^T 1 = 0."""
+    for s in range(6):
+        n = 300
+        a, b = W.sparse_random_edges(n, 900, s)
+        A = _mat(n, a, b, np.random.default_rng(s).lognormal(0, 1.5, len(a)))
+        perm = W.random_ordering(n, s + 100)
+        F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=s)
+        G = reconstruct(F, perm)
+        assert np.abs(G.sum(axis=1)).max() <= 1e-13 * np.abs(np.diag(G)).max()
+        assert np.allclose(G, G.T, atol=1e-13 * np.abs(np.diag(G)).max())
+
+
+def test_sample_mean_matches_L():
+    """E[G G^T] = L (Sec. II-B): the mean of F D F^T over 1e5 seeds on small
+    graphs lies within 4 standard errors of L, entry by entry."""
+    rng = np.random.default_rng(11)
+    graphs = []
+    n = 6
+    ia, ib = np.triu_indices(n, 1)
+    graphs.append((n, ia, ib, rng.uniform(0.2, 3, len(ia))))             # K6
+    n2 = 8
+    a, b = W.sparse_random_edges(n2, 14, 4)
+    graphs.append((n2, a, b, rng.lognormal(0, 1, len(a))))
+    nseeds = 100_000
+    for n, a, b, w in graphs:
+        A = _mat(n, a, b, w)
+        perm = W.random_ordering(n, 77)
+        L = oracle.lib()
+        acc = np.zeros((n, n)); acc2 = np.zeros((n, n))
+        for s in range(nseeds):
+            F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=s, L=L)
+            G = reconstruct(F, perm)
+            acc += G; acc2 += G * G
+        mean = acc / nseeds
+        var = acc2 / nseeds - mean ** 2
+        se = np.sqrt(np.maximum(var, 0) / nseeds)
+        Ad = A.dense()
+        dev = np.abs(mean - Ad)
+        # entries that are deterministic (zero variance) only carry summation rounding
+        assert np.all(dev <= 4 * se + 1e-10 * np.abs(Ad).max()), (dev / (se + 1e-300)).max()
+        assert var.max() > 0          # genuinely random
+
+
+# ----------------------------------------------------------------- dependency counters
+def _golden_fig1():
+    vals = {}
+    with open(os.path.join(GOLDEN, "fig1_dependency_counters.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.split()
+    return vals
+
+
+def test_fig1_worked_example():
+    g = _golden_fig1()
+    edges = [tuple(int(x) for x in e.split("-")) for e in g["edges"]]
+    n = 6
+    a = np.array([e[0] for e in edges]); b = np.array([e[1] for e in edges])
+    A = _mat(n, a, b, np.ones(len(edges)))
+    low = oracle.ingest(A.colptr, A.rowind, A.val, None, oracle.KIND_LAPLACIAN)
+    dp0 = np.bincount(low["row"], minlength=n)          # counters start (R8)
+    assert list(dp0) == [int(x) for x in g["initial_counts"]]
+    samples = [tuple(int(x) for x in e.split("-")) for e in g["sampled_edges"]]
+    nbrs = [int(x) for x in g["pivot_neighbours"]]
+    dp_ins, _ = oracle.dp_update(dp0, samples, [], [])
+    assert dp_ins[5] == int(g["counts_after_inserts_d5"][0])
+    dp1, enq = oracle.dp_update(dp0, samples, nbrs, [1] * len(nbrs))
+    assert list(dp1[1:]) == [int(x) for x in g["counts_after_d1_to_d5"]]
+    assert sorted(enq) == [int(x) for x in g["enqueued"]]
+
+
+def test_insert_before_delete_hazard():
+    """Sec. III: deleting before inserting can enqueue a vertex whose incoming
+    sampled edge is not yet recorded."""
+    dp = np.array([0, 1, 1])
+    dp_ok, enq_ok = oracle.dp_update(dp, [(1, 2)], [1, 2], [1, 1])
+    assert list(enq_ok) == [1] and dp_ok[2] == 1
+    _, enq_bad = oracle.dp_update(dp, [(1, 2)], [1, 2], [1, 1], deletes_first=True)
+    assert sorted(enq_bad) == [1, 2]
+
+
+@pytest.mark.parametrize("s", range(6))
+def test_tracked_schedule_invariants_and_bit_identity(s):
+    """Counters equal recomputed d_t(i) after every pivot, ready pivots are
+    pairwise non-adjacent, and every counter-respecting schedule gives the
+    label-order factor bit for bit (Sec. III 'Distribution Preservation')."""
+    rng = np.random.default_rng(s)
+    n = int(rng.integers(20, 120))
+    a, b = W.sparse_random_edges(n, 3 * n, s, connected=(s % 3 != 0))
+    w = rng.lognormal(0, 1, len(a))
+    exc = rng.uniform(0, 0.5, n) if s % 2 else None
+    A = _mat(n, a, b, w, exc)
+    perm = W.random_ordering(n, s + 1)
+    ref = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=1000 + s)
+    for sched in range(3):
+        T = oracle.factor_tracked(A.colptr, A.rowind, A.val, perm, seed=1000 + s, sched_seed=sched, check=True)
+        assert T["violations"] == 0
+        assert same_factor(T, ref)
+
+
+# ----------------------------------------------------------------- ingest
+def test_ingest_conventions_and_errors():
+    n = 5
+    a, b = W.path_edges(n)
+    A = _mat(n, a, b, np.ones(n - 1))
+    lo = oracle.ingest(A.colptr, A.rowind, A.val, None)
+    assert lo["n"] == n and not lo["ground"] and len(lo["row"]) == n - 1
+    assert np.all(lo["w"] == 1.0)
+    # SDDM: ground node labelled last with edges of the row excess
+    S = _mat(n, a, b, np.ones(n - 1), np.array([0.5, 0, 0, 0, 0.25]))
+    lo = oracle.ingest(S.colptr, S.rowind, S.val, None)
+    assert lo["ground"] and lo["n"] == n + 1
+    gw = sorted(lo["w"][lo["row"] == n])
+    assert gw == [0.25, 0.5]
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.ingest(S.colptr, S.rowind, S.val, None, oracle.KIND_LAPLACIAN)
+    assert e.value.code == 1
+    bad = S.val.copy(); bad[np.where((S.rowind != np.repeat(np.arange(n), np.diff(S.colptr))))[0][0]] = 0.3
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.ingest(S.colptr, S.rowind, bad, None)
+    assert e.value.code == 2
+    neg = A.val.copy(); neg[0] = 0.5           # diagonal below the off-diagonal sum
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.ingest(A.colptr, A.rowind, neg, None)
+    assert e.value.code == 2
+    with pytest.raises(oracle.OracleError):
+        oracle.ingest(A.colptr, A.rowind, A.val, np.array([0, 1, 1, 2, 3]))
+
+
+# ----------------------------------------------------------------- preconditioner / PCG
+def test_precond_inverts_exact_factor():
+    """For an exact factor (a path) and r orthogonal to 1, L M^{-1} r = r."""
+    n = 80
+    a, b = W.path_edges(n)
+    A = _mat(n, a, b, np.random.default_rng(1).uniform(1, 3, n - 1))
+    perm = W.random_ordering(n, 2)
+    F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=3)
+    r = np.random.default_rng(4).standard_normal(n); r -= r.mean()
+    z = oracle.precond_apply(F, perm, r)
+    assert np.allclose(A.dense() @ z, r, atol=1e-11 * np.abs(r).max())
+
+
+def test_pcg_matches_dense_solve():
+    for s in range(4):
+        n = 200 + 100 * s
+        a, b = W.sparse_random_edges(n, 4 * n, s)
+        rng = np.random.default_rng(s)
+        exc = rng.uniform(0, 1, n) if s % 2 else None
+        A = _mat(n, a, b, rng.lognormal(0, 1, len(a)), exc)
+        perm = W.random_ordering(n, s)
+        F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=s)
+        bvec = W.gaussian_rhs(n, 1, s, center=exc is None)
+        x, it, rr = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, bvec, 1e-13, 2000)
+        Ad = A.dense()
+        xs = np.linalg.lstsq(Ad, bvec, rcond=None)[0]
+        if exc is None:
+            x = x - x.mean(); xs = xs - xs.mean()
+        assert rr <= 1e-13
+        assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+
+
+def test_pcg_path_converges_at_once():
+    n = 500
+    a, b = W.path_edges(n)
+    A = _mat(n, a, b, np.random.default_rng(0).uniform(1, 2, n - 1))
+    perm = W.random_ordering(n, 1)
+    F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=2)
+    bvec = W.gaussian_rhs(n, 1, 3)
+    _, it, rr = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, bvec, 1e-8, 50)
+    assert it <= 2 and rr <= 1e-8
