@@ -1,0 +1,207 @@
+/*
+ * parac.h -- C ABI of libparac: randomized approximate Cholesky (rchol's
+ * elimination, scheduled by ParAC's dynamic dependency tracking) and PCG,
+ * on one GB300 GPU (sm_103a).
+ *
+ * Problem statement (ParAC paper, Sec. I, Eq. 1-2): solve L x = b for a graph
+ * Laplacian or SDDM matrix L, using a randomized factor L ~ G G^T as the PCG
+ * preconditioner.  The factor is kept in the scaled form of Sec. IV:
+ * L ~ F D F^T with F unit lower triangular and D diagonal (G = F D^{1/2}).
+ *
+ * Conventions shared by every entry point
+ *   Matrices    Full symmetric CSC: colptr int64[n+1] (colptr[0] = 0,
+ *               non-decreasing), rowind int32[nnz] in [0, n), val double[nnz].
+ *               Sign convention of Sec. V: positive diagonal, off-diagonal
+ *               entries <= 0 (explicit zeros are ignored).  Both triangles
+ *               must be stored; the library reads the strict lower triangle
+ *               in elimination-label order and the column sums.
+ *   Pointers    Every array argument may be host or device memory; the
+ *               library checks which with cudaPointerGetAttributes and copies
+ *               host data itself.  Inputs are read during the call only; the
+ *               caller keeps ownership.  Output arrays are written only on
+ *               PARAC_OK.
+ *   Handles     parac_factor_t is owned by the library; release it with
+ *               parac_factor_free.  A handle is bound to the device that was
+ *               current when it was created.
+ *   Streams     All device work of a call is ordered on opts->stream (the
+ *               legacy default stream if NULL); calls return after that work
+ *               has completed.
+ *   Errors      Every call returns a parac_status; no exception crosses the
+ *               ABI.  parac_last_error() gives a thread-local message.
+ *   Determinism The factor (F, D) is a deterministic function of (L,
+ *               ordering, seed, kind) whatever the GPU schedule: it is
+ *               bit-identical to a sequential elimination in label order.
+ */
+#ifndef PARAC_H
+#define PARAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct parac_factor_s *parac_factor_t;
+
+typedef enum {
+    PARAC_OK = 0,
+    PARAC_EINVAL = 1,    /* malformed arguments, ordering not a permutation, kind mismatch */
+    PARAC_ENOT_SDD = 2,  /* positive off-diagonal entry or negative row excess */
+    PARAC_ENOMEM = 3,    /* device or host allocation failed */
+    PARAC_EPOOL = 4,     /* fill workspace still overflowed after the allowed regrowths */
+    PARAC_ETIMEOUT = 5,  /* a device wait exceeded opts->spin_limit polls (watchdog) */
+    PARAC_ECUDA = 6,     /* a CUDA runtime call failed */
+    PARAC_ENOCONV = 7    /* PCG reached maxit before the tolerance (outputs still written) */
+} parac_status;
+
+enum { PARAC_KIND_AUTO = 0, PARAC_KIND_LAPLACIAN = 1, PARAC_KIND_SDDM = 2 };
+enum { PARAC_SPTRSV_AUTO = 0, PARAC_SPTRSV_SYNCFREE = 1, PARAC_SPTRSV_LEVELSET = 2 };
+
+/*
+ * Options.  parac_opts_default() fills the defaults; a NULL opts pointer
+ * means the defaults.
+ *   kind            AUTO: SDDM when some row excess exceeds 1e-12 of its
+ *                   diagonal, else Laplacian.  SDDM rows with positive excess
+ *                   get an edge to a ground node labelled last (Sec. V); the
+ *                   ground row and column are removed from the factor.
+ *   g_precision     64: PCG applies F in FP64.  32: F values are stored as
+ *                   FP32 and the triangular solves run in FP32, while PCG's
+ *                   SpMV, residual update and dot products stay FP64.
+ *   pool_mult       Initial fill-workspace capacity, in units of the strict
+ *                   lower input entries (Sec. IV-A uses 4-6).
+ *   max_pool_regrow Reruns with a 2x larger workspace after an overflow (the
+ *                   rerun gives the same factor).
+ *   spin_limit      Polls any device wait may take before PARAC_ETIMEOUT
+ *                   (0: library default, 2^24).  Waits on the ready queue
+                   count only polls during which no vertex was published.
+ *   warps_per_block, blocks, queue_chunk, big_threshold
+ *                   Elimination schedule (0 = autotuned/default): worker warps
+ *                   per CTA, CTAs (0 = all co-resident), ready-queue slots a
+ *                   worker claims at once, gathered-entry count above which a
+ *                   vertex leaves the per-warp shared-memory path.
+ *   sptrsv          Triangular-solve strategy (PARAC_SPTRSV_*).
+ *   check_every     PCG iterations between host convergence checks (0 = 8).
+ *   stream          cudaStream_t to order all work on.
+ *   timing          Nonzero: record per-phase device times in the stats.
+ */
+typedef struct {
+    int32_t kind;
+    int32_t g_precision;
+    double pool_mult;
+    int32_t max_pool_regrow;
+    int32_t warps_per_block;
+    int64_t spin_limit;
+    int32_t blocks;
+    int32_t queue_chunk;
+    int32_t big_threshold;
+    int32_t sptrsv;
+    int32_t check_every;
+    int32_t timing;
+    void *stream;
+} parac_opts;
+
+void parac_opts_default(parac_opts *opts);
+
+/*
+ * parac_factor -- randomized approximate Cholesky of one matrix
+ * (Alg. 1 with Alg. 2 per pivot, run by the dependency-counter schedule of
+ * Sec. III on the GPU, Alg. 4's structure re-derived for sm_103a).
+ *   n         order of L (0 <= n < 2^31 - 1)
+ *   colptr, rowind, val   L in the convention above
+ *   ordering  ordering[k] = original vertex eliminated k-th (a permutation of
+ *             0..n-1); NULL means the identity.  Labels are positions in
+ *             this ordering.
+ *   seed      keys the Philox4x64-10 stream: slot p of pivot k draws counter
+ *             (k, p, 0, 0) under key (seed, 0).
+ *   opts      NULL for defaults.
+ *   out       receives a new handle on PARAC_OK (NULL otherwise).
+ * Errors: EINVAL, ENOT_SDD, ENOMEM, EPOOL, ETIMEOUT, ECUDA.
+ */
+parac_status parac_factor(int64_t n, const int64_t *colptr, const int32_t *rowind, const double *val,
+                          const int32_t *ordering, uint64_t seed, const parac_opts *opts,
+                          parac_factor_t *out);
+
+/*
+ * parac_pcg -- preconditioned conjugate gradients for L X = B (Sec. V),
+ * preconditioner M^{-1} = P^T F^{-T} D^+ F^{-1} P (D^+ skips zero pivots).
+ *   G         handle from parac_factor / parac_factor_many
+ *   n, colptr, rowind, val   the matrix to solve with (normally the one that
+ *             was factored); colptr == NULL uses the device copy kept in G.
+ *   B         n x nrhs right-hand sides, column-major, leading dimension ldb
+ *   nrhs      1..32
+ *   tol       stop when ||r_j|| <= tol ||b_j|| for the recurrence residual
+ *             and then for the recomputed true residual b_j - L x_j
+ *   maxit     iteration cap (per right-hand side)
+ *   X         n x nrhs output, column-major, leading dimension ldx (x0 = 0)
+ *   iters     [nrhs] iterations taken (may be NULL)
+ *   true_relres [nrhs] ||b_j - L x_j|| / ||b_j|| at exit (may be NULL)
+ * For singular Laplacians each b_j must be orthogonal to the constant vector.
+ * Returns PARAC_ENOCONV (with X, iters, true_relres written) when some
+ * right-hand side has not converged within maxit.
+ */
+parac_status parac_pcg(parac_factor_t G, int64_t n, const int64_t *colptr, const int32_t *rowind,
+                       const double *val, const double *B, int32_t nrhs, int64_t ldb, double tol,
+                       int32_t maxit, double *X, int64_t ldx, int32_t *iters, double *true_relres);
+
+/* One system of a batch. */
+typedef struct {
+    int64_t n;
+    const int64_t *colptr;
+    const int32_t *rowind;
+    const double *val;
+    const int32_t *ordering;   /* NULL = identity */
+} parac_system;
+
+/*
+ * parac_factor_many -- factor `count` independent systems in ONE persistent
+ * elimination launch sharing one ready queue (batched form of Alg. 4).
+ * System s draws its randomness from counter (k, p, s, 0) under key
+ * (seed, 0), so its factor equals the one a sequential elimination of that
+ * system alone with system index s gives.  out[s] receives the handles
+ * (all NULL on error).  Errors as parac_factor.
+ */
+parac_status parac_factor_many(int32_t count, const parac_system *systems, uint64_t seed,
+                               const parac_opts *opts, parac_factor_t *out);
+
+/*
+ * parac_precond_apply -- z = M^{-1} r = P^T F^{-T} D^+ F^{-1} P r with the
+ * factor in G (the preconditioner PCG applies; Sec. IV scaled form, D^+ = 0
+ * on zero pivots).  r and z are n-vectors in the original numbering, host or
+ * device memory.  Errors: EINVAL, ETIMEOUT, ECUDA.
+ */
+parac_status parac_precond_apply(parac_factor_t G, const double *r, double *z);
+
+/*
+ * parac_factor_export -- copy the factor out (label space, ground removed).
+ *   nnz       receives the strict-lower entry count of F
+ *   colptr    int64[n+1], rowind int32[nnz], Fval double[nnz] (rows ascending
+ *             within each column), D double[n]
+ * Pass colptr == NULL to query nnz (and n via parac_factor_stats) first.
+ * Arrays may be host or device memory.
+ */
+parac_status parac_factor_export(parac_factor_t G, int64_t *nnz, int64_t *colptr, int32_t *rowind,
+                                 double *Fval, double *D);
+
+/*
+ * parac_factor_stats -- JSON object with sizes and timings of the factor
+ * (n, nnz_F, nnz_G = nnz_F + n, fill entries, pool use, per-phase times in
+ * ms when opts->timing was set).  Writes at most cap bytes including the
+ * terminating NUL; returns PARAC_EINVAL if cap is too small.
+ */
+parac_status parac_factor_stats(parac_factor_t G, char *json, size_t cap);
+
+/* Release a handle (NULL is ignored). */
+void parac_factor_free(parac_factor_t G);
+
+/* Static description of a status code. */
+const char *parac_status_string(parac_status s);
+
+/* Message describing the last failing call on this thread ("" if none). */
+const char *parac_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PARAC_H */

@@ -1,0 +1,903 @@
+// api.cu -- the C ABI of libparac (declared in include/parac.h): argument
+// checks, host/device marshalling, workspace sizing and regrowth, and the
+// orchestration of ingest -> persistent elimination -> compaction -> solve.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/parac.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace parac;
+
+namespace {
+
+thread_local std::string g_err;
+
+void set_err(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+struct CudaFail {
+    cudaError_t e;
+    const char *where;
+};
+
+#define CK(call)                                                                \
+    do {                                                                        \
+        cudaError_t e_ = (call);                                                \
+        if (e_ != cudaSuccess) throw CudaFail{e_, #call};                       \
+    } while (0)
+
+struct StatusFail {
+    parac_status s;
+};
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Stream-ordered device buffer.
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t st = nullptr;
+    DBuf() = default;
+    DBuf(size_t b, cudaStream_t s) { alloc(b, s); }
+    void alloc(size_t b, cudaStream_t s)
+    {
+        release();
+        st = s;
+        bytes = b;
+        if (b) {
+            cudaError_t e = cudaMallocAsync(&p, b, s);
+            if (e != cudaSuccess) { p = nullptr; cudaGetLastError(); throw StatusFail{PARAC_ENOMEM}; }
+        }
+    }
+    void release()
+    {
+        if (p) cudaFreeAsync(p, st);
+        p = nullptr;
+        bytes = 0;
+    }
+    ~DBuf() { release(); }
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept : p(o.p), bytes(o.bytes), st(o.st) { o.p = nullptr; o.bytes = 0; }
+    DBuf &operator=(DBuf &&o) noexcept
+    {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; st = o.st; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    template <typename T> T *as() const { return (T *)p; }
+};
+
+template <typename T>
+DBuf dalloc(size_t count, cudaStream_t s) { return DBuf(count * sizeof(T), s); }
+
+// A device view of a caller array: the caller's pointer if it is device memory,
+// else a stream-ordered copy.
+template <typename T>
+struct DView {
+    const T *p = nullptr;
+    DBuf own;
+    void set(const T *src, size_t count, cudaStream_t s)
+    {
+        if (!src || count == 0) { p = src; return; }
+        if (is_device_ptr(src)) { p = src; return; }
+        own.alloc(count * sizeof(T), s);
+        CK(cudaMemcpyAsync(own.p, src, count * sizeof(T), cudaMemcpyHostToDevice, s));
+        p = own.as<T>();
+    }
+};
+
+void copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    if (!bytes) return;
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+}
+
+int num_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+void set_mempool_keep()
+{
+    static bool done = false;
+    if (done) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done = true;
+}
+
+int lanes_for(double avg)
+{
+    if (avg <= 6.0) return 4;
+    if (avg <= 12.0) return 8;
+    if (avg <= 24.0) return 16;
+    return 32;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+struct SolveCache {
+    int32_t n = -1;
+    DBuf x, r, z, p, q, b, y64, zl64, y32, zl32, partials, state;
+    PcgBuffers B{};
+};
+
+struct parac_factor_s {
+    int device = 0;
+    int64_t n = 0;
+    int64_t nnzF = 0;
+    int32_t prec = 64;
+    long long spin_limit = 0;
+    int32_t sptrsv = 0;
+    int32_t check_every = 8;
+    cudaStream_t stream = nullptr;
+    DBuf perm, Fcp, Frow, Fval, Fval32, Frp, Fcol, Fvalr, Fvalr32, D, Dinv, Lp, Li, Lv;
+    int64_t nnzL = 0;
+    std::string stats;
+    SolveCache cache;
+    DBuf status;
+};
+
+namespace {
+
+struct Opts {
+    parac_opts o;
+    cudaStream_t st;
+};
+
+Opts read_opts(const parac_opts *in)
+{
+    Opts r;
+    parac_opts_default(&r.o);
+    if (in) r.o = *in;
+    if (r.o.pool_mult <= 0) r.o.pool_mult = 4.0;
+    if (r.o.max_pool_regrow < 0) r.o.max_pool_regrow = 0;
+    if (r.o.spin_limit <= 0) r.o.spin_limit = 1ll << 24;
+    if (r.o.warps_per_block <= 0) r.o.warps_per_block = 8;
+    if (r.o.warps_per_block > 16) r.o.warps_per_block = 16;
+    if (r.o.queue_chunk <= 0) r.o.queue_chunk = 1;
+    if (r.o.check_every <= 0) r.o.check_every = 8;
+    if (r.o.g_precision != 32) r.o.g_precision = 64;
+    r.st = (cudaStream_t)r.o.stream;
+    return r;
+}
+
+// ---------------------------------------------------------------- factor job
+struct SysDesc {
+    int64_t n;
+    int64_t obase, lbase;
+    int32_t ground;   // label or -1
+};
+
+struct FactorOut {
+    // output-space (N) arrays
+    DBuf Fcp, Frow, Fval, D;
+    int64_t nnzF = 0;
+    int64_t nl = 0, nnz_low = 0;
+    unsigned long long stats[8] = {0};
+    unsigned long long pool_used = 0, f_used = 0, scratch_used = 0;
+    int regrows = 0;
+    double t_ingest = 0, t_elim = 0, t_compact = 0;
+    int blocks = 0, warps = 0;
+};
+
+parac_status map_status(int32_t s)
+{
+    switch (s) {
+    case ST_OK: return PARAC_OK;
+    case ST_POOL: return PARAC_EPOOL;
+    case ST_TIMEOUT: return PARAC_ETIMEOUT;
+    case ST_NOT_SDD: return PARAC_ENOT_SDD;
+    default: return PARAC_EINVAL;
+    }
+}
+
+struct EvTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool on;
+    cudaStream_t st;
+    EvTimer(bool on_, cudaStream_t s) : on(on_), st(s)
+    {
+        if (on) { cudaEventCreate(&a); cudaEventCreate(&b); cudaEventRecord(a, st); }
+    }
+    double stop()
+    {
+        if (!on) return 0.0;
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms;
+    }
+    ~EvTimer() { if (a) cudaEventDestroy(a); if (b) cudaEventDestroy(b); }
+};
+
+// Factor a (possibly block-diagonal) system already on the device.
+//   N, colptr/rowind/val: concatenated input (global row indices)
+//   ord_global / label_of_k: position q -> original vertex / label (nullptr: identity)
+//   systems: per-system ranges (size 1 for a single matrix)
+void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const double *val,
+                const int32_t *ord_global, const int32_t *label_of_k, const std::vector<SysDesc> &systems,
+                int32_t kind, uint64_t seed, const Opts &O, FactorOut &out)
+{
+    cudaStream_t st = O.st;
+    const int S = (int)systems.size();
+    const bool batch = S > 1;
+    int64_t nl = 0;
+    for (auto &s : systems) nl = std::max<int64_t>(nl, s.lbase + s.n + (s.ground >= 0 ? 1 : 0));
+    out.nl = nl;
+    if (nl >= 0x7fffffffLL) throw StatusFail{PARAC_EINVAL};
+
+    EvTimer t_in(O.o.timing != 0, st);
+    // per-system device descriptors (batch only)
+    DBuf d_sys_of_orig, d_sys_obase, d_sys_n, d_sys_ground, d_sys_lbase, d_sys_of_label;
+    if (batch) {
+        std::vector<int32_t> obase(S), nn(S), gr(S), lb(S);
+        for (int s = 0; s < S; ++s) {
+            obase[s] = (int32_t)systems[s].obase; nn[s] = (int32_t)systems[s].n;
+            gr[s] = systems[s].ground; lb[s] = (int32_t)systems[s].lbase;
+        }
+        d_sys_obase = dalloc<int32_t>(S, st); d_sys_n = dalloc<int32_t>(S, st);
+        d_sys_ground = dalloc<int32_t>(S, st); d_sys_lbase = dalloc<int32_t>(S, st);
+        CK(cudaMemcpyAsync(d_sys_obase.p, obase.data(), 4 * S, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_sys_n.p, nn.data(), 4 * S, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_sys_ground.p, gr.data(), 4 * S, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_sys_lbase.p, lb.data(), 4 * S, cudaMemcpyHostToDevice, st));
+        d_sys_of_orig = dalloc<int32_t>(N, st);
+        d_sys_of_label = dalloc<int32_t>(nl, st);
+        for (int s = 0; s < S; ++s)
+            CK(launch_fill_i32(d_sys_of_orig.as<int32_t>() + systems[s].obase, systems[s].n, s, st));
+        CK(launch_sys_of_label(S, d_sys_lbase.as<int32_t>(), (int32_t)nl, d_sys_of_label.as<int32_t>(), st));
+    }
+
+    DBuf flags = dalloc<int32_t>(1, st);
+    CK(cudaMemsetAsync(flags.p, 0, 4, st));
+    DBuf iperm = dalloc<int32_t>(N, st);
+    if (ord_global) {
+        CK(cudaMemsetAsync(iperm.p, 0xff, 4 * N, st));
+        CK(launch_iperm(N, ord_global, label_of_k, iperm.as<int32_t>(), flags.as<int32_t>(), st));
+    } else {
+        CK(launch_identity_iperm(N, iperm.as<int32_t>(), st));
+    }
+    DBuf lcnt = dalloc<int32_t>(nl, st), dp0 = dalloc<int32_t>(nl, st), gw = dalloc<double>(N, st);
+    CK(cudaMemsetAsync(lcnt.p, 0, 4 * nl, st));
+    CK(cudaMemsetAsync(dp0.p, 0, 4 * nl, st));
+    IngestArgs ia{};
+    ia.n = N; ia.colptr = colptr; ia.rowind = rowind; ia.val = val;
+    ia.sys_of_orig = batch ? d_sys_of_orig.as<int32_t>() : nullptr;
+    ia.sys_obase = batch ? d_sys_obase.as<int32_t>() : nullptr;
+    ia.sys_n = batch ? d_sys_n.as<int32_t>() : nullptr;
+    ia.sys_ground = batch ? d_sys_ground.as<int32_t>() : nullptr;
+    ia.single_ground = systems[0].ground;
+    ia.kind = kind;
+    ia.iperm = iperm.as<int32_t>(); ia.lcnt = lcnt.as<int32_t>(); ia.dp = dp0.as<int32_t>(); ia.gw = gw.as<double>();
+    ia.status = flags.as<int32_t>();
+    // the count kernel reads iperm; a bad ordering must be reported before
+    int32_t hflags = 0;
+    CK(cudaMemcpyAsync(&hflags, flags.p, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hflags & INGEST_BAD_INDEX) { set_err("ordering is not a permutation"); throw StatusFail{PARAC_EINVAL}; }
+    CK(launch_ingest_count(ia, st));
+    DBuf lcp = dalloc<int64_t>(nl + 1, st);
+    DBuf scan_tmp(scan_tmp_bytes(std::max<int64_t>(nl, N) + 1), st);
+    CK(scan_i32_to_i64(lcnt.as<int32_t>(), lcp.as<int64_t>(), nl, scan_tmp.p, st));
+    int64_t nnz_low = 0;
+    CK(cudaMemcpyAsync(&hflags, flags.p, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&nnz_low, lcp.as<int64_t>() + nl, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hflags & INGEST_BAD_INDEX) { set_err("row index out of range"); throw StatusFail{PARAC_EINVAL}; }
+    if (hflags & INGEST_NOT_SDD) { set_err("positive off-diagonal entry or negative row excess"); throw StatusFail{PARAC_ENOT_SDD}; }
+    if (hflags & INGEST_KIND) { set_err("matrix has row excess but kind is LAPLACIAN"); throw StatusFail{PARAC_EINVAL}; }
+    out.nnz_low = nnz_low;
+    DBuf lrow = dalloc<int32_t>(std::max<int64_t>(nnz_low, 1), st), lw = dalloc<double>(std::max<int64_t>(nnz_low, 1), st);
+    CK(launch_ingest_scatter(ia, lcp.as<int64_t>(), lrow.as<int32_t>(), lw.as<double>(), st));
+    out.t_ingest = t_in.stop();
+
+    // ---------------------------------------------------------------- elimination
+    EvTimer t_el(O.o.timing != 0, st);
+    const int warps = O.o.warps_per_block;
+    int warp_cap = 128, block_cap = 1024;
+    if (O.o.big_threshold > 0) {
+        int b = 32;
+        while (b < O.o.big_threshold && b < 4096) b <<= 1;
+        warp_cap = b;
+        if (block_cap < 2 * warp_cap) block_cap = 2 * warp_cap;
+    }
+    int bps = 0;
+    CK(elim_configure(warps, warp_cap, block_cap, &bps));
+    if (bps < 1) { block_cap = 0; CK(elim_configure(warps, warp_cap, block_cap, &bps)); }
+    if (bps < 1) { set_err("elimination kernel does not fit on an SM"); throw StatusFail{PARAC_EINVAL}; }
+    int blocks = num_sms() * bps;
+    if (O.o.blocks > 0) blocks = std::min(blocks, O.o.blocks);
+    out.blocks = blocks; out.warps = warps;
+    const int total_warps = blocks * warps;
+    const int fchunk = 256;
+
+    DBuf dp = dalloc<int32_t>(nl, st), queue = dalloc<int32_t>(nl, st), ctrs = dalloc<uint32_t>(2, st);
+    DBuf fcnt = dalloc<uint32_t>(nl, st), in_row = dalloc<int32_t>((size_t)nl * FILL_C0, st),
+         in_w = dalloc<double>((size_t)nl * FILL_C0, st), dir = dalloc<uint32_t>((size_t)nl * FILL_LEVELS, st);
+    DBuf f_start = dalloc<int64_t>(nl, st), f_len = dalloc<int32_t>(nl, st), Dl = dalloc<double>(nl, st);
+    DBuf tops = dalloc<unsigned long long>(3, st), status = dalloc<int32_t>(1, st), stats = dalloc<unsigned long long>(8, st);
+
+    double mult = O.o.pool_mult;
+    unsigned long long scratch_cap = 64ull << 20;
+    DBuf pool_row, pool_w, f_row, f_val, scratch;
+    for (int attempt = 0;; ++attempt) {
+        const unsigned long long pool_cap = (unsigned long long)std::ceil(mult * (double)nnz_low) + 4096ull;
+        const unsigned long long f_cap = (unsigned long long)std::ceil(std::max(mult, 4.0) * (double)nnz_low) +
+                                         (unsigned long long)nl + (unsigned long long)total_warps * fchunk + 4096ull;
+        pool_row = dalloc<int32_t>(pool_cap, st); pool_w = dalloc<double>(pool_cap, st);
+        f_row = dalloc<int32_t>(f_cap, st); f_val = dalloc<double>(f_cap, st);
+        scratch.alloc(scratch_cap, st);
+        CK(cudaMemcpyAsync(dp.p, dp0.p, 4 * nl, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemsetAsync(queue.p, 0xff, 4 * nl, st));
+        CK(cudaMemsetAsync(ctrs.p, 0, 8, st));
+        CK(cudaMemsetAsync(fcnt.p, 0, 4 * nl, st));
+        CK(cudaMemsetAsync(dir.p, 0, 4 * (size_t)nl * FILL_LEVELS, st));
+        CK(cudaMemsetAsync(tops.p, 0, 24, st));
+        CK(cudaMemsetAsync(status.p, 0, 4, st));
+        CK(cudaMemsetAsync(stats.p, 0, 64, st));
+        CK(launch_queue_init((int32_t)nl, dp.as<int32_t>(), queue.as<int32_t>(), ctrs.as<uint32_t>() + 1, st));
+
+        ElimArgs a{};
+        a.nl = (int32_t)nl; a.lcp = lcp.as<int64_t>(); a.lrow = lrow.as<int32_t>(); a.lw = lw.as<double>();
+        a.sys_of = batch ? d_sys_of_label.as<int32_t>() : nullptr;
+        a.sys_base = batch ? d_sys_lbase.as<int32_t>() : nullptr;
+        a.seed = seed;
+        a.dp = dp.as<int32_t>(); a.queue = queue.as<int32_t>();
+        a.q_head = ctrs.as<uint32_t>(); a.q_tail = ctrs.as<uint32_t>() + 1;
+        a.fcnt = fcnt.as<uint32_t>(); a.in_row = in_row.as<int32_t>(); a.in_w = in_w.as<double>();
+        a.dir = dir.as<uint32_t>(); a.pool_row = pool_row.as<int32_t>(); a.pool_w = pool_w.as<double>();
+        a.pool_top = tops.as<unsigned long long>(); a.pool_cap = pool_cap;
+        a.f_row = f_row.as<int32_t>(); a.f_val = f_val.as<double>();
+        a.f_top = tops.as<unsigned long long>() + 1; a.f_cap = f_cap;
+        a.f_start = f_start.as<int64_t>(); a.f_len = f_len.as<int32_t>(); a.D = Dl.as<double>();
+        a.scratch = scratch.as<unsigned char>(); a.scratch_top = tops.as<unsigned long long>() + 2;
+        a.scratch_cap = scratch_cap;
+        a.status = status.as<int32_t>(); a.spin_limit = O.o.spin_limit;
+        a.stats = stats.as<unsigned long long>();
+        a.warp_cap = warp_cap; a.block_cap = block_cap; a.queue_chunk = O.o.queue_chunk;
+        if (nl > 0) CK(elim_launch(a, blocks, warps, fchunk, st));
+        int32_t hst = 0;
+        unsigned long long htops[3];
+        CK(cudaMemcpyAsync(&hst, status.p, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(htops, tops.p, 24, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(out.stats, stats.p, 64, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        out.pool_used = htops[0]; out.f_used = htops[1]; out.scratch_used = htops[2];
+        if (hst == ST_OK) break;
+        if (hst == ST_POOL && attempt < O.o.max_pool_regrow) {
+            mult *= 2.0;
+            scratch_cap *= 2;
+            out.regrows++;
+            continue;
+        }
+        set_err(hst == ST_POOL ? "fill workspace overflow (raise pool_mult or max_pool_regrow)"
+                               : "device wait exceeded spin_limit");
+        throw StatusFail{map_status(hst)};
+    }
+    scratch.release(); pool_row.release(); pool_w.release();
+    out.t_elim = t_el.stop();
+
+    // ---------------------------------------------------------------- compaction
+    EvTimer t_cp(O.o.timing != 0, st);
+    DBuf out_of_label = dalloc<int32_t>(nl, st);
+    if (batch)
+        CK(launch_out_of_label_batch((int32_t)nl, d_sys_of_label.as<int32_t>(), d_sys_lbase.as<int32_t>(),
+                                     d_sys_obase.as<int32_t>(), d_sys_n.as<int32_t>(), out_of_label.as<int32_t>(), st));
+    else
+        CK(launch_out_of_label_single((int32_t)nl, (int32_t)N, out_of_label.as<int32_t>(), st));
+    DBuf olen = dalloc<int32_t>(std::max<int64_t>(N, 1), st);
+    CK(launch_out_len((int32_t)nl, out_of_label.as<int32_t>(), f_start.as<int64_t>(), f_len.as<int32_t>(),
+                      f_row.as<int32_t>(), olen.as<int32_t>(), st));
+    out.Fcp = dalloc<int64_t>(N + 1, st);
+    CK(scan_i32_to_i64(olen.as<int32_t>(), out.Fcp.as<int64_t>(), N, scan_tmp.p, st));
+    int64_t nnzF = 0;
+    CK(cudaMemcpyAsync(&nnzF, out.Fcp.as<int64_t>() + N, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out.nnzF = nnzF;
+    out.Frow = dalloc<int32_t>(std::max<int64_t>(nnzF, 1), st);
+    out.Fval = dalloc<double>(std::max<int64_t>(nnzF, 1), st);
+    out.D = dalloc<double>(std::max<int64_t>(N, 1), st);
+    CK(launch_gather_factor((int32_t)nl, out_of_label.as<int32_t>(), f_start.as<int64_t>(), f_row.as<int32_t>(),
+                            f_val.as<double>(), Dl.as<double>(), out.Fcp.as<int64_t>(), out.Frow.as<int32_t>(),
+                            out.Fval.as<double>(), out.D.as<double>(), st));
+    out.t_compact = t_cp.stop();
+}
+
+// Build the solve-side arrays of a handle from CSC(F) of n columns.
+void finish_handle(parac_factor_s *h, int64_t n, int64_t nnzF, const Opts &O)
+{
+    cudaStream_t st = O.st;
+    h->Frp = dalloc<int64_t>(n + 1, st);
+    h->Fcol = dalloc<int32_t>(std::max<int64_t>(nnzF, 1), st);
+    h->Fvalr = dalloc<double>(std::max<int64_t>(nnzF, 1), st);
+    DBuf cnt = dalloc<int32_t>(std::max<int64_t>(n, 1), st);
+    CK(cudaMemsetAsync(cnt.p, 0, 4 * std::max<int64_t>(n, 1), st));
+    CK(launch_row_count(nnzF, h->Frow.as<int32_t>(), cnt.as<int32_t>(), st));
+    DBuf tmp(scan_tmp_bytes(n + 1), st);
+    CK(scan_i32_to_i64(cnt.as<int32_t>(), h->Frp.as<int64_t>(), n, tmp.p, st));
+    CK(cudaMemsetAsync(cnt.p, 0, 4 * std::max<int64_t>(n, 1), st));
+    CK(launch_transpose_scatter((int32_t)n, h->Fcp.as<int64_t>(), h->Frow.as<int32_t>(), h->Fval.as<double>(),
+                                h->Frp.as<int64_t>(), cnt.as<int32_t>(), h->Fcol.as<int32_t>(), h->Fvalr.as<double>(), st));
+    CK(launch_sort_rows((int32_t)n, h->Frp.as<int64_t>(), h->Fcol.as<int32_t>(), h->Fvalr.as<double>(), st));
+    h->Dinv = dalloc<double>(std::max<int64_t>(n, 1), st);
+    CK(launch_dinv((int32_t)n, h->D.as<double>(), h->Dinv.as<double>(), st));
+    if (h->prec == 32) {
+        h->Fval32 = dalloc<float>(std::max<int64_t>(nnzF, 1), st);
+        h->Fvalr32 = dalloc<float>(std::max<int64_t>(nnzF, 1), st);
+        CK(launch_to_f32(h->Fval.as<double>(), h->Fval32.as<float>(), nnzF, st));
+        CK(launch_to_f32(h->Fvalr.as<double>(), h->Fvalr32.as<float>(), nnzF, st));
+    }
+    h->status = dalloc<int32_t>(1, st);
+}
+
+std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_index)
+{
+    char buf[1024];
+    snprintf(buf, sizeof buf,
+             "{\"n\": %lld, \"nnz_F\": %lld, \"nnz_G\": %lld, \"labels\": %lld, \"nnz_lower_input\": %lld, "
+             "\"fill_entries\": %llu, \"pool_entries_used\": %llu, \"factor_entries_used\": %llu, "
+             "\"scratch_bytes_used\": %llu, \"vertices_warp_path\": %llu, \"vertices_block_path\": %llu, "
+             "\"vertices_global_path\": %llu, \"queue_spins\": %llu, \"regrows\": %d, \"blocks\": %d, "
+             "\"warps_per_block\": %d, \"precision\": %d, \"system\": %d, \"t_ingest_ms\": %.4f, "
+             "\"t_elim_ms\": %.4f, \"t_compact_ms\": %.4f}",
+             (long long)h->n, (long long)h->nnzF, (long long)(h->nnzF + h->n), (long long)fo.nl,
+             (long long)fo.nnz_low, fo.stats[3], fo.pool_used, fo.f_used, fo.scratch_used, fo.stats[0], fo.stats[1],
+             fo.stats[2], fo.stats[4], fo.regrows, fo.blocks, fo.warps, h->prec, sys_index, fo.t_ingest, fo.t_elim,
+             fo.t_compact);
+    return buf;
+}
+
+template <typename F>
+parac_status guarded(F &&f)
+{
+    try {
+        g_err.clear();
+        return f();
+    } catch (const StatusFail &e) {
+        if (g_err.empty()) g_err = parac_status_string(e.s);
+        cudaGetLastError();
+        return e.s;
+    } catch (const CudaFail &e) {
+        set_err("%s failed: %s", e.where, cudaGetErrorString(e.e));
+        cudaGetLastError();
+        return PARAC_ECUDA;
+    } catch (const std::bad_alloc &) {
+        set_err("host allocation failed");
+        return PARAC_ENOMEM;
+    }
+}
+
+bool check_csc_host(int64_t n, const int64_t *colptr)
+{
+    if (!colptr) return n == 0;
+    if (is_device_ptr(colptr)) return true;   // checked by kernels
+    if (colptr[0] != 0) return false;
+    for (int64_t j = 0; j < n; ++j)
+        if (colptr[j + 1] < colptr[j]) return false;
+    return true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+extern "C" {
+
+void parac_opts_default(parac_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->kind = PARAC_KIND_AUTO;
+    o->g_precision = 64;
+    o->pool_mult = 4.0;
+    o->max_pool_regrow = 2;
+    o->spin_limit = 1ll << 24;
+    o->warps_per_block = 8;
+    o->queue_chunk = 1;
+    o->check_every = 8;
+}
+
+const char *parac_status_string(parac_status s)
+{
+    switch (s) {
+    case PARAC_OK: return "PARAC_OK";
+    case PARAC_EINVAL: return "PARAC_EINVAL: invalid argument";
+    case PARAC_ENOT_SDD: return "PARAC_ENOT_SDD: matrix is not a Laplacian/SDDM (sign or dominance)";
+    case PARAC_ENOMEM: return "PARAC_ENOMEM: allocation failed";
+    case PARAC_EPOOL: return "PARAC_EPOOL: fill workspace overflow";
+    case PARAC_ETIMEOUT: return "PARAC_ETIMEOUT: device wait exceeded the spin limit";
+    case PARAC_ECUDA: return "PARAC_ECUDA: CUDA runtime error";
+    case PARAC_ENOCONV: return "PARAC_ENOCONV: PCG did not reach the tolerance";
+    }
+    return "unknown parac_status";
+}
+
+const char *parac_last_error(void) { return g_err.c_str(); }
+
+parac_status parac_factor(int64_t n, const int64_t *colptr, const int32_t *rowind, const double *val,
+                          const int32_t *ordering, uint64_t seed, const parac_opts *opts, parac_factor_t *out)
+{
+    if (out) *out = nullptr;
+    return guarded([&]() -> parac_status {
+        if (!out || n < 0 || n >= 0x7ffffffeLL) { set_err("bad n or out"); return PARAC_EINVAL; }
+        if (n > 0 && (!colptr || !rowind || !val)) { set_err("null matrix array"); return PARAC_EINVAL; }
+        if (!check_csc_host(n, colptr)) { set_err("colptr must start at 0 and be non-decreasing"); return PARAC_EINVAL; }
+        Opts O = read_opts(opts);
+        if (O.o.kind < 0 || O.o.kind > 2) { set_err("bad kind"); return PARAC_EINVAL; }
+        set_mempool_keep();
+        cudaStream_t st = O.st;
+        std::unique_ptr<parac_factor_s> h(new parac_factor_s());
+        cudaGetDevice(&h->device);
+        h->n = n; h->prec = O.o.g_precision; h->spin_limit = O.o.spin_limit; h->sptrsv = O.o.sptrsv;
+        h->check_every = O.o.check_every; h->stream = st;
+        DView<int64_t> cp; cp.set(colptr, (size_t)n + 1, st);
+        int64_t nnz = 0;
+        if (n > 0) {
+            if (is_device_ptr(colptr)) {
+                CK(cudaMemcpyAsync(&nnz, colptr + n, 8, cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+            } else {
+                nnz = colptr[n];
+            }
+        }
+        h->nnzL = nnz;
+        DView<int32_t> ri; ri.set(rowind, (size_t)nnz, st);
+        DView<double> va; va.set(val, (size_t)nnz, st);
+        DView<int32_t> od; od.set(ordering, (size_t)n, st);
+        std::vector<SysDesc> sys(1);
+        sys[0].n = n; sys[0].obase = 0; sys[0].lbase = 0;
+        sys[0].ground = O.o.kind == PARAC_KIND_LAPLACIAN ? -1 : (int32_t)n;
+        FactorOut fo;
+        if (n > 0) {
+            run_factor(n, cp.p, ri.p, va.p, od.p, nullptr, sys, O.o.kind, seed, O, fo);
+        } else {
+            fo.Fcp = dalloc<int64_t>(1, st);
+            CK(cudaMemsetAsync(fo.Fcp.p, 0, 8, st));
+            fo.Frow = dalloc<int32_t>(1, st); fo.Fval = dalloc<double>(1, st); fo.D = dalloc<double>(1, st);
+        }
+        h->nnzF = fo.nnzF;
+        h->Fcp = std::move(fo.Fcp); h->Frow = std::move(fo.Frow); h->Fval = std::move(fo.Fval); h->D = std::move(fo.D);
+        h->perm = dalloc<int32_t>(std::max<int64_t>(n, 1), st);
+        if (ordering) copy_out(h->perm.p, od.p, 4 * (size_t)n, st);
+        else CK(launch_iota_i32(h->perm.as<int32_t>(), n, 0, st));
+        h->Lp = dalloc<int64_t>(n + 1, st); h->Li = dalloc<int32_t>(std::max<int64_t>(nnz, 1), st);
+        h->Lv = dalloc<double>(std::max<int64_t>(nnz, 1), st);
+        copy_out(h->Lp.p, cp.p, 8 * ((size_t)n + 1), st);
+        copy_out(h->Li.p, ri.p, 4 * (size_t)nnz, st);
+        copy_out(h->Lv.p, va.p, 8 * (size_t)nnz, st);
+        finish_handle(h.get(), n, fo.nnzF, O);
+        CK(cudaStreamSynchronize(st));
+        h->stats = stats_json(h.get(), fo, 0);
+        *out = h.release();
+        return PARAC_OK;
+    });
+}
+
+parac_status parac_factor_many(int32_t count, const parac_system *systems, uint64_t seed, const parac_opts *opts,
+                               parac_factor_t *out)
+{
+    if (out && count > 0) for (int32_t s = 0; s < count; ++s) out[s] = nullptr;
+    return guarded([&]() -> parac_status {
+        if (count < 0 || (count > 0 && (!systems || !out))) { set_err("bad count/systems/out"); return PARAC_EINVAL; }
+        if (count == 0) return PARAC_OK;
+        Opts O = read_opts(opts);
+        if (O.o.kind < 0 || O.o.kind > 2) { set_err("bad kind"); return PARAC_EINVAL; }
+        set_mempool_keep();
+        cudaStream_t st = O.st;
+        std::vector<SysDesc> sys(count);
+        std::vector<int64_t> nnz(count);
+        int64_t N = 0, NNZ = 0, NL = 0;
+        for (int s = 0; s < count; ++s) {
+            const parac_system &y = systems[s];
+            if (y.n < 0 || (y.n > 0 && (!y.colptr || !y.rowind || !y.val))) { set_err("system %d: bad arrays", s); return PARAC_EINVAL; }
+            if (!check_csc_host(y.n, y.colptr)) { set_err("system %d: bad colptr", s); return PARAC_EINVAL; }
+            int64_t z = 0;
+            if (y.n > 0) {
+                if (is_device_ptr(y.colptr)) {
+                    CK(cudaMemcpyAsync(&z, y.colptr + y.n, 8, cudaMemcpyDeviceToHost, st));
+                    CK(cudaStreamSynchronize(st));
+                } else z = y.colptr[y.n];
+            }
+            nnz[s] = z;
+            sys[s].n = y.n; sys[s].obase = N; sys[s].lbase = NL;
+            sys[s].ground = O.o.kind == PARAC_KIND_LAPLACIAN ? -1 : (int32_t)(NL + y.n);
+            N += y.n; NNZ += z; NL += y.n + (sys[s].ground >= 0 ? 1 : 0);
+        }
+        if (NL >= 0x7fffffffLL) { set_err("batch too large for 32-bit labels"); return PARAC_EINVAL; }
+        // concatenated device input with global indices
+        DBuf cp = dalloc<int64_t>(N + 1, st), ri = dalloc<int32_t>(std::max<int64_t>(NNZ, 1), st),
+             va = dalloc<double>(std::max<int64_t>(NNZ, 1), st), ord = dalloc<int32_t>(std::max<int64_t>(N, 1), st),
+             lab = dalloc<int32_t>(std::max<int64_t>(N, 1), st);
+        int64_t zb = 0;
+        for (int s = 0; s < count; ++s) {
+            const parac_system &y = systems[s];
+            const int64_t n = y.n;
+            if (n == 0) continue;
+            DView<int64_t> c; c.set(y.colptr, (size_t)n + 1, st);
+            DView<int32_t> r; r.set(y.rowind, (size_t)nnz[s], st);
+            DView<double> v; v.set(y.val, (size_t)nnz[s], st);
+            CK(launch_add_offset_i64(c.p, cp.as<int64_t>() + sys[s].obase, n, zb, st));
+            CK(launch_add_offset_i32(r.p, ri.as<int32_t>() + zb, nnz[s], (int32_t)sys[s].obase, st));
+            copy_out(va.as<double>() + zb, v.p, 8 * (size_t)nnz[s], st);
+            if (y.ordering) {
+                DView<int32_t> o; o.set(y.ordering, (size_t)n, st);
+                CK(launch_add_offset_i32(o.p, ord.as<int32_t>() + sys[s].obase, n, (int32_t)sys[s].obase, st));
+                CK(cudaStreamSynchronize(st));
+            } else {
+                CK(launch_iota_i32(ord.as<int32_t>() + sys[s].obase, n, (int32_t)sys[s].obase, st));
+            }
+            CK(launch_iota_i32(lab.as<int32_t>() + sys[s].obase, n, (int32_t)sys[s].lbase, st));
+            zb += nnz[s];
+            CK(cudaStreamSynchronize(st));   // host views of this system can go
+        }
+        const int64_t total = zb;
+        CK(cudaMemcpyAsync(cp.as<int64_t>() + N, &total, 8, cudaMemcpyHostToDevice, st));
+        FactorOut fo;
+        run_factor(N, cp.as<int64_t>(), ri.as<int32_t>(), va.as<double>(), ord.as<int32_t>(), lab.as<int32_t>(), sys,
+                   O.o.kind, seed, O, fo);
+        std::vector<int64_t> fcp_h(N + 1);
+        CK(cudaMemcpyAsync(fcp_h.data(), fo.Fcp.p, 8 * (N + 1), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<std::unique_ptr<parac_factor_s>> hs(count);
+        int64_t zoff = 0;
+        for (int s = 0; s < count; ++s) {
+            const int64_t n = sys[s].n, ob = sys[s].obase;
+            std::unique_ptr<parac_factor_s> h(new parac_factor_s());
+            cudaGetDevice(&h->device);
+            h->n = n; h->prec = O.o.g_precision; h->spin_limit = O.o.spin_limit; h->sptrsv = O.o.sptrsv;
+            h->check_every = O.o.check_every; h->stream = st;
+            const int64_t f0 = fcp_h[ob], f1 = fcp_h[ob + n];
+            h->nnzF = f1 - f0;
+            h->Fcp = dalloc<int64_t>(n + 1, st);
+            CK(launch_add_offset_i64(fo.Fcp.as<int64_t>() + ob, h->Fcp.as<int64_t>(), n + 1, -f0, st));
+            h->Frow = dalloc<int32_t>(std::max<int64_t>(h->nnzF, 1), st);
+            CK(launch_add_offset_i32(fo.Frow.as<int32_t>() + f0, h->Frow.as<int32_t>(), h->nnzF, -(int32_t)ob, st));
+            h->Fval = dalloc<double>(std::max<int64_t>(h->nnzF, 1), st);
+            copy_out(h->Fval.p, fo.Fval.as<double>() + f0, 8 * (size_t)h->nnzF, st);
+            h->D = dalloc<double>(std::max<int64_t>(n, 1), st);
+            copy_out(h->D.p, fo.D.as<double>() + ob, 8 * (size_t)n, st);
+            h->perm = dalloc<int32_t>(std::max<int64_t>(n, 1), st);
+            CK(launch_add_offset_i32(ord.as<int32_t>() + ob, h->perm.as<int32_t>(), n, -(int32_t)ob, st));
+            h->nnzL = nnz[s];
+            h->Lp = dalloc<int64_t>(n + 1, st); h->Li = dalloc<int32_t>(std::max<int64_t>(nnz[s], 1), st);
+            h->Lv = dalloc<double>(std::max<int64_t>(nnz[s], 1), st);
+            CK(launch_add_offset_i64(cp.as<int64_t>() + ob, h->Lp.as<int64_t>(), n + 1, -zoff, st));
+            CK(launch_add_offset_i32(ri.as<int32_t>() + zoff, h->Li.as<int32_t>(), nnz[s], -(int32_t)ob, st));
+            copy_out(h->Lv.p, va.as<double>() + zoff, 8 * (size_t)nnz[s], st);
+            zoff += nnz[s];
+            finish_handle(h.get(), n, h->nnzF, O);
+            h->stats = stats_json(h.get(), fo, s);
+            hs[s] = std::move(h);
+        }
+        CK(cudaStreamSynchronize(st));
+        for (int s = 0; s < count; ++s) out[s] = hs[s].release();
+        return PARAC_OK;
+    });
+}
+
+parac_status parac_factor_export(parac_factor_t G, int64_t *nnz, int64_t *colptr, int32_t *rowind, double *Fval,
+                                 double *D)
+{
+    return guarded([&]() -> parac_status {
+        if (!G || !nnz) { set_err("null handle or nnz"); return PARAC_EINVAL; }
+        *nnz = G->nnzF;
+        if (!colptr) return PARAC_OK;
+        if (!rowind || !Fval || !D) { set_err("null output array"); return PARAC_EINVAL; }
+        cudaStream_t st = G->stream;
+        copy_out(colptr, G->Fcp.p, 8 * ((size_t)G->n + 1), st);
+        copy_out(rowind, G->Frow.p, 4 * (size_t)G->nnzF, st);
+        copy_out(Fval, G->Fval.p, 8 * (size_t)G->nnzF, st);
+        copy_out(D, G->D.p, 8 * (size_t)G->n, st);
+        CK(cudaStreamSynchronize(st));
+        return PARAC_OK;
+    });
+}
+
+parac_status parac_factor_stats(parac_factor_t G, char *json, size_t cap)
+{
+    if (!G || !json) { g_err = "null handle or buffer"; return PARAC_EINVAL; }
+    if (G->stats.size() + 1 > cap) { g_err = "buffer too small"; return PARAC_EINVAL; }
+    std::memcpy(json, G->stats.c_str(), G->stats.size() + 1);
+    return PARAC_OK;
+}
+
+void parac_factor_free(parac_factor_t G)
+{
+    if (!G) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    const int dev = G->device;
+    cudaStream_t st = G->stream;
+    if (cur != dev) cudaSetDevice(dev);
+    delete G;
+    cudaStreamSynchronize(st);
+    if (cur != dev) cudaSetDevice(cur);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ solve
+namespace {
+
+SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, const double *Lv, int64_t nnzL)
+{
+    SolveArgs A{};
+    A.n = (int32_t)G->n;
+    A.Lp = Lp; A.Li = Li; A.Lv = Lv;
+    A.Fcp = G->Fcp.as<int64_t>(); A.Frow = G->Frow.as<int32_t>(); A.Fval64 = G->Fval.as<double>();
+    A.Fval32 = G->Fval32.as<float>();
+    A.Frp = G->Frp.as<int64_t>(); A.Fcol = G->Fcol.as<int32_t>(); A.Fvalr64 = G->Fvalr.as<double>();
+    A.Fvalr32 = G->Fvalr32.as<float>();
+    A.Dinv = G->Dinv.as<double>(); A.perm = G->perm.as<int32_t>();
+    A.prec = G->prec;
+    const double n = G->n > 0 ? (double)G->n : 1.0;
+    A.lanes_spmv = lanes_for((double)nnzL / n);
+    A.lanes_trsv = lanes_for((double)G->nnzF / n);
+    A.trsv_warps = 8;
+    int bps = 0;
+    trsv_configure(A.lanes_trsv, A.trsv_warps, &bps, A.prec);
+    if (bps < 1) bps = 1;
+    A.trsv_blocks = num_sms() * bps;
+    const int64_t rows_per_group = (int64_t)A.trsv_warps * (32 / A.lanes_trsv);
+    const int64_t groups = (G->n + rows_per_group - 1) / rows_per_group;
+    if (groups < A.trsv_blocks) A.trsv_blocks = (int)std::max<int64_t>(groups, 1);
+    A.spin_limit = G->spin_limit;
+    A.status = G->status.as<int32_t>();
+    return A;
+}
+
+void ensure_cache(parac_factor_s *G, const SolveArgs &A, cudaStream_t st)
+{
+    SolveCache &c = G->cache;
+    if (c.n == (int32_t)G->n && c.B.vec_blocks > 0) return;
+    const size_t n = (size_t)std::max<int64_t>(G->n, 1);
+    c.x = dalloc<double>(n, st); c.r = dalloc<double>(n, st); c.z = dalloc<double>(n, st);
+    c.p = dalloc<double>(n, st); c.q = dalloc<double>(n, st); c.b = dalloc<double>(n, st);
+    if (G->prec == 32) { c.y32 = dalloc<float>(n, st); c.zl32 = dalloc<float>(n, st); }
+    else { c.y64 = dalloc<double>(n, st); c.zl64 = dalloc<double>(n, st); }
+    int vb = (int)std::min<int64_t>((G->n + 255) / 256, (int64_t)num_sms() * 8);
+    if (vb < 1) vb = 1;
+    const int pstride = std::max(vb, A.trsv_blocks);
+    c.partials = dalloc<double>((size_t)3 * pstride, st);
+    c.state = DBuf(pcg_state_bytes(), st);
+    c.B.x = c.x.as<double>(); c.B.r = c.r.as<double>(); c.B.z = c.z.as<double>(); c.B.p = c.p.as<double>();
+    c.B.q = c.q.as<double>(); c.B.b = c.b.as<double>();
+    c.B.yl64 = c.y64.as<double>(); c.B.zl64 = c.zl64.as<double>(); c.B.yl32 = c.y32.as<float>(); c.B.zl32 = c.zl32.as<float>();
+    c.B.partials = c.partials.as<double>(); c.B.state = c.state.as<PcgState>();
+    c.B.vec_blocks = vb; c.B.pstride = pstride;
+    c.n = (int32_t)G->n;
+}
+
+int32_t read_dev_status(parac_factor_s *G, cudaStream_t st)
+{
+    int32_t s = 0;
+    CK(cudaMemcpyAsync(&s, G->status.p, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return s;
+}
+
+}  // namespace
+
+extern "C" parac_status parac_pcg(parac_factor_t G, int64_t n, const int64_t *colptr, const int32_t *rowind,
+                                  const double *val, const double *B, int32_t nrhs, int64_t ldb, double tol,
+                                  int32_t maxit, double *X, int64_t ldx, int32_t *iters, double *true_relres)
+{
+    return guarded([&]() -> parac_status {
+        if (!G || n != G->n || nrhs < 1 || nrhs > 32 || (n > 0 && (!B || !X)) || ldb < n || ldx < n || maxit < 0) {
+            set_err("bad arguments to parac_pcg");
+            return PARAC_EINVAL;
+        }
+        cudaStream_t st = G->stream;
+        DView<int64_t> cp; DView<int32_t> ri; DView<double> va;
+        const int64_t *Lp = G->Lp.as<int64_t>();
+        const int32_t *Li = G->Li.as<int32_t>();
+        const double *Lv = G->Lv.as<double>();
+        int64_t nnzL = G->nnzL;
+        if (colptr) {
+            if (!rowind || !val) { set_err("null matrix array"); return PARAC_EINVAL; }
+            if (!check_csc_host(n, colptr)) { set_err("bad colptr"); return PARAC_EINVAL; }
+            cp.set(colptr, (size_t)n + 1, st);
+            if (is_device_ptr(colptr)) {
+                CK(cudaMemcpyAsync(&nnzL, colptr + n, 8, cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+            } else nnzL = colptr[n];
+            ri.set(rowind, (size_t)nnzL, st);
+            va.set(val, (size_t)nnzL, st);
+            Lp = cp.p; Li = ri.p; Lv = va.p;
+        }
+        if (n == 0) {
+            for (int j = 0; j < nrhs; ++j) { if (iters) iters[j] = 0; if (true_relres) true_relres[j] = 0.0; }
+            return PARAC_OK;
+        }
+        SolveArgs A = solve_args(G, Lp, Li, Lv, nnzL);
+        ensure_cache(G, A, st);
+        PcgBuffers &Bf = G->cache.B;
+        CK(cudaMemsetAsync(G->status.p, 0, 4, st));
+        const bool bdev = is_device_ptr(B), xdev = is_device_ptr(X);
+        bool all_conv = true;
+        for (int j = 0; j < nrhs; ++j) {
+            CK(cudaMemcpyAsync(Bf.b, B + (size_t)j * ldb, 8 * (size_t)n,
+                               bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+            CK(pcg_init(A, Bf, tol, maxit, st));
+            PcgHostState hs{};
+            for (;;) {
+                for (int c = 0; c < G->check_every; ++c) CK(pcg_iteration(A, Bf, st));
+                CK(pcg_read_state(Bf, &hs, st));
+                if (read_dev_status(G, st) != ST_OK) { set_err("triangular solve wait exceeded the spin limit"); return PARAC_ETIMEOUT; }
+                if (!hs.done) continue;
+                CK(pcg_true_residual(A, Bf, st));
+                CK(pcg_read_state(Bf, &hs, st));
+                const bool ok = hs.true_rr <= tol * tol * hs.bb;
+                if (ok || hs.iters >= maxit || hs.bb == 0.0) break;
+                CK(pcg_clear_done(Bf, st));
+                CK(pcg_resume(A, Bf, st));
+            }
+            if (read_dev_status(G, st) != ST_OK) { set_err("triangular solve wait exceeded the spin limit"); return PARAC_ETIMEOUT; }
+            CK(cudaMemcpyAsync(X + (size_t)j * ldx, Bf.x, 8 * (size_t)n,
+                               xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+            const double rel = hs.bb > 0.0 ? std::sqrt(hs.true_rr / hs.bb) : 0.0;
+            if (iters) iters[j] = hs.iters;
+            if (true_relres) true_relres[j] = rel;
+            if (!(hs.true_rr <= tol * tol * hs.bb) && hs.bb > 0.0) all_conv = false;
+        }
+        CK(cudaStreamSynchronize(st));
+        if (!all_conv) { set_err("PCG reached maxit"); return PARAC_ENOCONV; }
+        return PARAC_OK;
+    });
+}
+
+extern "C" parac_status parac_precond_apply(parac_factor_t G, const double *r, double *z)
+{
+    return guarded([&]() -> parac_status {
+        if (!G || (G->n > 0 && (!r || !z))) { set_err("bad arguments"); return PARAC_EINVAL; }
+        if (G->n == 0) return PARAC_OK;
+        cudaStream_t st = G->stream;
+        SolveArgs A = solve_args(G, G->Lp.as<int64_t>(), G->Li.as<int32_t>(), G->Lv.as<double>(), G->nnzL);
+        ensure_cache(G, A, st);
+        PcgBuffers &Bf = G->cache.B;
+        CK(cudaMemsetAsync(G->status.p, 0, 4, st));
+        const size_t bytes = 8 * (size_t)G->n;
+        CK(cudaMemcpyAsync(Bf.r, r, bytes, cudaMemcpyDefault, st));
+        CK(precond_apply(A, Bf, Bf.r, Bf.z, st));
+        CK(cudaMemcpyAsync(z, Bf.z, bytes, cudaMemcpyDefault, st));
+        CK(cudaStreamSynchronize(st));
+        if (read_dev_status(G, st) != ST_OK) { set_err("triangular solve wait exceeded the spin limit"); return PARAC_ETIMEOUT; }
+        return PARAC_OK;
+    });
+}

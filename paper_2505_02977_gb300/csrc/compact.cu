@@ -1,0 +1,228 @@
+// compact.cu -- factor compaction (the step between the elimination and the
+// solve; the paper's GPU "Total" counts the solver's analysis here, Sec. V-B):
+// per-pivot columns written anywhere in the factor workspace become CSC(F)
+// with F(u,k) = -w_u / D_k (Sec. IV scaled form), ground rows/columns
+// removed (Sec. V SDDM handling), plus CSR(F) by transposition for the
+// forward triangular solve and optional FP32 copies.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace parac {
+
+namespace {
+
+inline int grid_for(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 65535LL * 16) b = 65535LL * 16;
+    return (int)b;
+}
+
+__global__ void k_out_of_label_single(int32_t nl, int32_t n, int32_t *o)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nl; l += (int64_t)gridDim.x * blockDim.x)
+        o[l] = l < n ? (int32_t)l : -1;
+}
+
+__global__ void k_out_of_label_batch(int32_t nl, const int32_t *sys_of_label, const int32_t *sys_lbase,
+                                     const int32_t *sys_obase, const int32_t *sys_n, int32_t *o)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nl; l += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = sys_of_label[l];
+        const int32_t loc = (int32_t)l - sys_lbase[s];
+        o[l] = loc < sys_n[s] ? sys_obase[s] + loc : -1;
+    }
+}
+
+__global__ void k_sys_of_label(int32_t S, const int32_t *sys_lbase, int32_t nl, int32_t *sys_of_label)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t b = sys_lbase[s], e = (s + 1 < S) ? sys_lbase[s + 1] : nl;
+        for (int32_t l = b; l < e; ++l) sys_of_label[l] = (int32_t)s;
+    }
+}
+
+// output column length: the pivot's merged count, minus its ground row (the
+// largest label of its system, hence last in row order) when present
+__global__ void k_out_len(int32_t nl, const int32_t *out_of_label, const int64_t *f_start, const int32_t *f_len,
+                          const int32_t *f_row, int32_t *olen)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nl; l += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = out_of_label[l];
+        if (o < 0) continue;
+        int32_t len = f_len[l];
+        if (len > 0 && out_of_label[f_row[f_start[l] + len - 1]] < 0) --len;
+        olen[o] = len;
+    }
+}
+
+// one warp per label column
+__global__ void k_gather_factor(int32_t nl, const int32_t *out_of_label, const int64_t *f_start,
+                                const int32_t *f_row, const double *f_val, const double *D, const int64_t *fcp,
+                                int32_t *Frow, double *Fval, double *Dout)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t l = w0; l < nl; l += nw) {
+        const int32_t o = out_of_label[l];
+        if (o < 0) continue;
+        const int64_t dst = fcp[o];
+        const int64_t len = fcp[o + 1] - dst;
+        const int64_t src = f_start[l];
+        const double Dk = D[l];
+        for (int64_t i = lane; i < len; i += 32) {
+            Frow[dst + i] = out_of_label[f_row[src + i]];
+            Fval[dst + i] = __ddiv_rn(-f_val[src + i], Dk);
+        }
+        if (lane == 0) Dout[o] = Dk;
+    }
+}
+
+__global__ void k_row_count(int64_t nnz, const int32_t *rows, int32_t *cnt)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz; t += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt + rows[t], 1);
+}
+
+// one warp per column of CSC: entries go to their rows in CSR
+__global__ void k_transpose_scatter(int32_t n, const int64_t *cp, const int32_t *rows, const double *vals,
+                                    const int64_t *rp, int32_t *cursor, int32_t *cols_out, double *vals_out)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = w0; c < n; c += nw) {
+        for (int64_t t = cp[c] + lane; t < cp[c + 1]; t += 32) {
+            const int32_t r = rows[t];
+            const int64_t at = rp[r] + atomicAdd(cursor + r, 1);
+            cols_out[at] = (int32_t)c;
+            vals_out[at] = vals[t];
+        }
+    }
+}
+
+// Sort each CSR row by column (one warp per row, rows of up to SORT_STAGE
+// entries staged in shared memory; an entry's slot is the number of entries
+// with a smaller column).  Longer rows keep the scatter order, which only
+// changes the summation order of the forward solve.
+constexpr int SORT_STAGE = 256;
+
+__global__ void k_sort_rows(int32_t n, const int64_t *rp, int32_t *cols, double *vals)
+{
+    __shared__ int32_t sc[8][SORT_STAGE];
+    __shared__ double sv[8][SORT_STAGE];
+    const unsigned lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w0; r < n; r += nw) {
+        const int64_t b = rp[r], len = rp[r + 1] - b;
+        if (len <= 1 || len > SORT_STAGE) continue;
+        for (int64_t i = lane; i < len; i += 32) { sc[wib][i] = cols[b + i]; sv[wib][i] = vals[b + i]; }
+        __syncwarp();
+        for (int64_t i = lane; i < len; i += 32) {
+            const int32_t c = sc[wib][i];
+            int64_t rank = 0;
+            for (int64_t q = 0; q < len; ++q) rank += sc[wib][q] < c;
+            cols[b + rank] = c;
+            vals[b + rank] = sv[wib][i];
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_to_f32(const double *in, float *out, int64_t n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = __double2float_rn(in[t]);
+}
+
+__global__ void k_dinv(int32_t n, const double *D, double *Dinv)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        Dinv[t] = D[t] > 0.0 ? 1.0 / D[t] : 0.0;
+}
+
+}  // namespace
+
+cudaError_t launch_out_of_label_single(int32_t nl, int32_t n, int32_t *o, cudaStream_t st)
+{
+    if (nl == 0) return cudaSuccess;
+    k_out_of_label_single<<<grid_for(nl, 256), 256, 0, st>>>(nl, n, o);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_out_of_label_batch(int32_t nl, const int32_t *sys_of_label, const int32_t *sys_lbase,
+                                      const int32_t *sys_obase, const int32_t *sys_n, int32_t *o, cudaStream_t st)
+{
+    if (nl == 0) return cudaSuccess;
+    k_out_of_label_batch<<<grid_for(nl, 256), 256, 0, st>>>(nl, sys_of_label, sys_lbase, sys_obase, sys_n, o);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sys_of_label(int32_t S, const int32_t *sys_lbase, int32_t nl, int32_t *sys_of_label, cudaStream_t st)
+{
+    if (S == 0) return cudaSuccess;
+    k_sys_of_label<<<grid_for(S, 64), 64, 0, st>>>(S, sys_lbase, nl, sys_of_label);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_out_len(int32_t nl, const int32_t *out_of_label, const int64_t *f_start, const int32_t *f_len,
+                           const int32_t *f_row, int32_t *olen, cudaStream_t st)
+{
+    if (nl == 0) return cudaSuccess;
+    k_out_len<<<grid_for(nl, 256), 256, 0, st>>>(nl, out_of_label, f_start, f_len, f_row, olen);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_factor(int32_t nl, const int32_t *out_of_label, const int64_t *f_start,
+                                 const int32_t *f_row, const double *f_val, const double *D, const int64_t *fcp,
+                                 int32_t *Frow, double *Fval, double *Dout, cudaStream_t st)
+{
+    if (nl == 0) return cudaSuccess;
+    k_gather_factor<<<grid_for((int64_t)nl * 32, 256), 256, 0, st>>>(nl, out_of_label, f_start, f_row, f_val, D,
+                                                                     fcp, Frow, Fval, Dout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_count(int64_t nnz, const int32_t *rows, int32_t *cnt, cudaStream_t st)
+{
+    if (nnz == 0) return cudaSuccess;
+    k_row_count<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, rows, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_scatter(int32_t n, const int64_t *cp, const int32_t *rows, const double *vals,
+                                     const int64_t *rp, int32_t *cursor, int32_t *cols_out, double *vals_out,
+                                     cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_transpose_scatter<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, cp, rows, vals, rp, cursor, cols_out,
+                                                                         vals_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_rows(int32_t n, const int64_t *rp, int32_t *cols, double *vals, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_sort_rows<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, rp, cols, vals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double *in, float *out, int64_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_to_f32<<<grid_for(n, 256), 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dinv(int32_t n, const double *D, double *Dinv, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_dinv<<<grid_for(n, 256), 256, 0, st>>>(n, D, Dinv);
+    return cudaGetLastError();
+}
+
+}  // namespace parac

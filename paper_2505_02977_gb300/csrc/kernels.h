@@ -1,0 +1,125 @@
+// kernels.h -- host-side launchers of libparac's device kernels (internal).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace parac {
+
+struct ElimArgs;
+
+// ---------------------------------------------------------------- scan.cu
+// out[0] = 0, out[i+1] = out[i] + in[i] for i < n (n+1 outputs).  tmp must
+// hold scan_tmp_bytes(n) bytes.
+size_t scan_tmp_bytes(int64_t n);
+cudaError_t scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t st);
+
+// ---------------------------------------------------------------- ingest.cu
+// Ingest flags (OR-ed into the ingest status word; priority in this order).
+enum : int32_t { INGEST_BAD_INDEX = 1, INGEST_NOT_SDD = 2, INGEST_KIND = 4 };
+// Single input system or a block-diagonal concatenation of systems
+// (sys_of_orig / sys_ground_label describe the batch; nullptr = one system).
+struct IngestArgs {
+    int64_t n;                  // original vertices (all systems)
+    const int64_t *colptr;      // [n+1]
+    const int32_t *rowind;      // global row indices
+    const double *val;
+    const int32_t *sys_of_orig; // [n] system of each vertex (nullptr: system 0)
+    const int32_t *sys_obase;   // [S] first original vertex of each system
+    const int32_t *sys_n;       // [S] vertices per system
+    const int32_t *sys_ground;  // [S] ground label of each system (-1: none)
+    int32_t single_ground;      // ground label when sys_of_orig == nullptr (-1: none)
+    int32_t kind;               // 0 auto, 1 laplacian, 2 sddm
+    int32_t *iperm;             // [n] original vertex -> label
+    int32_t *lcnt;              // [nl] strict-lower entries per label column
+    int32_t *dp;                // [nl] dependency counters (zeroed by caller)
+    double *gw;                 // [n] ground-edge weight per original vertex (0 = none)
+    int32_t *status;
+};
+
+// ordering (global: label k <- original vertex ord[k]); iperm must be filled
+// with -1 first.  label_of_k maps position k of the concatenated ordering to
+// its label (nullptr: identity).
+cudaError_t launch_iperm(int64_t n, const int32_t *ord, const int32_t *label_of_k, int32_t *iperm,
+                         int32_t *status, cudaStream_t st);
+cudaError_t launch_identity_iperm(int64_t n, int32_t *iperm, cudaStream_t st);
+cudaError_t launch_ingest_count(const IngestArgs &a, cudaStream_t st);
+cudaError_t launch_ingest_scatter(const IngestArgs &a, const int64_t *lcp, int32_t *lrow, double *lw,
+                                  cudaStream_t st);
+cudaError_t launch_queue_init(int32_t nl, const int32_t *dp, int32_t *queue, uint32_t *q_tail, cudaStream_t st);
+cudaError_t launch_add_offset_i32(const int32_t *in, int32_t *out, int64_t n, int32_t off, cudaStream_t st);
+cudaError_t launch_add_offset_i64(const int64_t *in, int64_t *out, int64_t n, int64_t off, cudaStream_t st);
+cudaError_t launch_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t st);
+cudaError_t launch_iota_i32(int32_t *p, int64_t n, int32_t base, cudaStream_t st);
+
+// ---------------------------------------------------------------- elim.cu
+size_t elim_smem_bytes(int warps_per_block, int warp_cap, int block_cap);
+cudaError_t elim_configure(int warps_per_block, int warp_cap, int block_cap, int *blocks_per_sm);
+cudaError_t elim_launch(const ElimArgs &a, int blocks, int warps_per_block, int fchunk, cudaStream_t st);
+
+// ---------------------------------------------------------------- compact.cu
+// out_of_label: label -> output column (-1 for ground labels).
+cudaError_t launch_out_len(int32_t nl, const int32_t *out_of_label, const int64_t *f_start, const int32_t *f_len,
+                           const int32_t *f_row, int32_t *olen, cudaStream_t st);
+cudaError_t launch_gather_factor(int32_t nl, const int32_t *out_of_label, const int64_t *f_start,
+                                 const int32_t *f_row, const double *f_val, const double *D, const int64_t *fcp,
+                                 int32_t *Frow, double *Fval, double *Dout, cudaStream_t st);
+cudaError_t launch_out_of_label_single(int32_t nl, int32_t n, int32_t *out_of_label, cudaStream_t st);
+cudaError_t launch_out_of_label_batch(int32_t nl, const int32_t *sys_of_label, const int32_t *sys_lbase,
+                                      const int32_t *sys_obase, const int32_t *sys_n, int32_t *out_of_label,
+                                      cudaStream_t st);
+cudaError_t launch_row_count(int64_t nnz, const int32_t *rows, int32_t *cnt, cudaStream_t st);
+cudaError_t launch_transpose_scatter(int32_t n, const int64_t *cp, const int32_t *rows, const double *vals,
+                                     const int64_t *rp, int32_t *cursor, int32_t *cols_out, double *vals_out,
+                                     cudaStream_t st);
+cudaError_t launch_sort_rows(int32_t n, const int64_t *rp, int32_t *cols, double *vals, cudaStream_t st);
+cudaError_t launch_to_f32(const double *in, float *out, int64_t n, cudaStream_t st);
+cudaError_t launch_dinv(int32_t n, const double *D, double *Dinv, cudaStream_t st);
+cudaError_t launch_sys_of_label(int32_t S, const int32_t *sys_lbase, int32_t nl, int32_t *sys_of_label,
+                                cudaStream_t st);
+
+// ---------------------------------------------------------------- solve.cu
+struct PcgState;   // device-resident scalars of one PCG run (solve.cu)
+
+struct SolveArgs {
+    int32_t n;                    // rows (original numbering)
+    // the matrix (symmetric CSC = CSR)
+    const int64_t *Lp; const int32_t *Li; const double *Lv;
+    // factor (label space)
+    const int64_t *Fcp; const int32_t *Frow; const double *Fval64; const float *Fval32;   // CSC (backward)
+    const int64_t *Frp; const int32_t *Fcol; const double *Fvalr64; const float *Fvalr32; // CSR (forward)
+    const double *Dinv;           // [n] 1/D or 0
+    const int32_t *perm;          // [n] label k <- original perm[k]
+    int32_t prec;                 // 64 or 32
+    int32_t lanes_spmv;           // lanes per row for SpMV (4, 8, 16, 32)
+    int32_t lanes_trsv;           // lanes per row for the triangular solves
+    int32_t trsv_blocks;          // persistent grid of the triangular solves
+    int32_t trsv_warps;           // warps per block of the triangular solves
+    long long spin_limit;
+    int32_t *status;
+};
+
+struct PcgBuffers {
+    double *x, *r, *z, *p, *q, *b;  // [n]
+    double *yl64, *zl64;            // label-space work (FP64 apply)
+    float *yl32, *zl32;             // label-space work (FP32 apply)
+    double *partials;               // [3 * pstride]
+    PcgState *state;
+    int32_t vec_blocks;             // grid of the vector kernels
+    int32_t pstride;                // >= max(vec_blocks, trsv_blocks)
+};
+
+size_t pcg_state_bytes();
+cudaError_t pcg_init(const SolveArgs &A, const PcgBuffers &B, double tol, int32_t maxit, cudaStream_t st);
+cudaError_t pcg_iteration(const SolveArgs &A, const PcgBuffers &B, cudaStream_t st);
+cudaError_t pcg_true_residual(const SolveArgs &A, const PcgBuffers &B, cudaStream_t st);
+// host view of the scalars after a sync
+struct PcgHostState { int32_t done; int32_t iters; double rr; double bb; double true_rr; int32_t maxit; };
+cudaError_t pcg_read_state(const PcgBuffers &B, PcgHostState *h, cudaStream_t st);
+cudaError_t pcg_clear_done(const PcgBuffers &B, cudaStream_t st);
+cudaError_t pcg_resume(const SolveArgs &A, const PcgBuffers &B, cudaStream_t st);
+cudaError_t precond_apply(const SolveArgs &A, const PcgBuffers &B, const double *r, double *z, cudaStream_t st);
+int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec);
+
+}  // namespace parac

@@ -1,0 +1,489 @@
+// solve.cu -- PCG with the randomized factor as preconditioner (Sec. V):
+// SpMV on L, sync-free triangular solves with F (forward, pull over CSR rows)
+// and F^T (backward, pull over CSC columns) around the D^+ scaling, and the
+// PCG vector/scalar steps, all on device-resident scalars so that one
+// iteration can be captured in a CUDA graph.
+//
+// Sync-free solves: every unknown starts as a signalling-NaN sentinel (never
+// produced by arithmetic); a row's lanes poll the unknowns they need until the
+// sentinel is gone, so the value itself is the ready flag.  Rows are handed to
+// a persistent, fully co-resident grid in a static round-robin of row groups
+// (increasing order for the forward solve, decreasing for the backward one):
+// the smallest unfinished group never waits on an unfinished group, so the
+// solve always progresses; every wait is bounded by the spin limit.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace parac {
+
+struct PcgState {
+    double rz, alpha, beta, bb, rr, tol2bb, true_rr, pad0;
+    int32_t done, iters, maxit, converged;
+};
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int VEC_THREADS = 256;
+
+__device__ __forceinline__ double sentinel64() { return __longlong_as_double((long long)0xfff7ffffffffffffull); }
+__device__ __forceinline__ float sentinel32() { return __int_as_float((int)0xffbfffffu); }
+__device__ __forceinline__ bool is_sentinel(double x) { return __double_as_longlong(x) == (long long)0xfff7ffffffffffffull; }
+__device__ __forceinline__ bool is_sentinel(float x) { return __float_as_int(x) == (int)0xffbfffffu; }
+
+template <typename T> __device__ __forceinline__ T sentinel();
+template <> __device__ __forceinline__ double sentinel<double>() { return sentinel64(); }
+template <> __device__ __forceinline__ float sentinel<float>() { return sentinel32(); }
+
+__device__ __forceinline__ double ld_poll(const double *p) { return ld_relaxed_f64(p); }
+__device__ __forceinline__ float ld_poll(const float *p) { return ld_relaxed_f32(p); }
+__device__ __forceinline__ void st_pub(double *p, double v) { st_relaxed_f64(p, v); }
+__device__ __forceinline__ void st_pub(float *p, float v) { st_relaxed_f32(p, v); }
+
+// block-wide sum; result valid in thread 0
+__device__ double block_sum(double v)
+{
+    __shared__ double ws[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) ws[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += ws[i];
+    __syncthreads();
+    return s;
+}
+
+// ---------------------------------------------------------------- SpMV: y = L x (+ partial x.y)
+template <int S>
+__global__ void k_spmv(int32_t n, const int64_t *Lp, const int32_t *Li, const double *Lv, const double *x, double *y,
+                       double *partial, const PcgState *st)
+{
+    if (st && st->done) return;
+    const unsigned lane = threadIdx.x & 31;
+    const int sub = lane / S, sl = lane % S;
+    const unsigned smask = (S == 32) ? FULL : (((1u << S) - 1u) << (sub * S));
+    const int64_t rows_per_iter = ((int64_t)gridDim.x * blockDim.x) / S;
+    double dotacc = 0.0;
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / S; i < n; i += rows_per_iter) {
+        double acc = 0.0;
+        for (int64_t t = Lp[i] + sl; t < Lp[i + 1]; t += S) acc += Lv[t] * __ldg(x + Li[t]);
+#pragma unroll
+        for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
+        if (sl == 0) {
+            y[i] = acc;
+            dotacc += acc * x[i];
+        }
+    }
+    if (partial) {
+        const double s = block_sum(dotacc);
+        if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------- scalar kernels (one block)
+__device__ double reduce_partials(const double *partial, int nb)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
+    return block_sum(s);
+}
+
+__global__ void k_alpha(PcgState *st, const double *partial_pq, int nb)
+{
+    if (st->done) return;
+    const double pq = reduce_partials(partial_pq, nb);
+    if (threadIdx.x == 0) st->alpha = st->rz / pq;
+}
+
+__global__ void k_check(PcgState *st, const double *partial_rr, int nb)
+{
+    if (st->done) return;
+    const double rr = reduce_partials(partial_rr, nb);
+    if (threadIdx.x == 0) {
+        st->rr = rr;
+        st->iters += 1;
+        if (rr <= st->tol2bb) { st->done = 1; st->converged = 1; }
+        else if (st->iters >= st->maxit) st->done = 1;
+    }
+}
+
+__global__ void k_beta(PcgState *st, const double *partial_rz, int nb)
+{
+    if (st->done) return;
+    const double rz = reduce_partials(partial_rz, nb);
+    if (threadIdx.x == 0) {
+        st->beta = rz / st->rz;
+        st->rz = rz;
+    }
+}
+
+__global__ void k_init_scalars(PcgState *st, const double *partial_bb, int nb, const double *partial_rz, int nbz,
+                               double tol, int32_t maxit)
+{
+    const double bb = reduce_partials(partial_bb, nb);
+    const double rz = reduce_partials(partial_rz, nbz);
+    if (threadIdx.x == 0) {
+        st->bb = bb; st->rz = rz; st->rr = bb;
+        st->tol2bb = tol * tol * bb;
+        st->iters = 0; st->maxit = maxit; st->converged = 0;
+        st->done = (bb == 0.0 || maxit <= 0) ? 1 : 0;
+        if (bb == 0.0) st->converged = 1;
+        st->alpha = st->beta = 0.0;
+        st->true_rr = 0.0;
+    }
+}
+
+__global__ void k_true_rr(PcgState *st, const double *partial, int nb)
+{
+    const double s = reduce_partials(partial, nb);
+    if (threadIdx.x == 0) st->true_rr = s;
+}
+
+// ---------------------------------------------------------------- vector kernels
+__global__ void k_update_xr(int32_t n, double *x, double *r, const double *p, const double *q, double *partial_rr,
+                            const PcgState *st)
+{
+    if (st->done) return;
+    const double a = st->alpha;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] += a * p[i];
+        const double ri = r[i] - a * q[i];
+        r[i] = ri;
+        acc += ri * ri;
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partial_rr[blockIdx.x] = s;
+}
+
+__global__ void k_update_p(int32_t n, double *p, const double *z, const PcgState *st)
+{
+    if (st->done) return;
+    const double b = st->beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = z[i] + b * p[i];
+}
+
+__global__ void k_init_vectors(int32_t n, const double *b, double *x, double *r, double *partial_bb)
+{
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double bi = b[i];
+        x[i] = 0.0; r[i] = bi;
+        acc += bi * bi;
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partial_bb[blockIdx.x] = s;
+}
+
+__global__ void k_copy(int32_t n, const double *a, double *b)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = a[i];
+}
+
+template <typename T>
+__global__ void k_fill_sentinel(int32_t n, T *a, T *b)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        a[i] = sentinel<T>();
+        b[i] = sentinel<T>();
+    }
+}
+
+__global__ void k_resid_sq(int32_t n, const double *b, const double *Lx, double *partial)
+{
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = b[i] - Lx[i];
+        acc += d * d;
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// ---------------------------------------------------------------- triangular solves
+template <typename XT> __device__ __forceinline__ XT to_x(double v);
+template <> __device__ __forceinline__ double to_x<double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_x<float>(double v) { return __double2float_rn(v); }
+
+// Forward: y[i] = rhs[perm[i]] - sum_{k<i} F(i,k) y[k] over the CSR row i.
+// Also resets the backward unknowns z[i] to the sentinel.
+template <int S, typename VT, typename XT>
+__global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, const VT *v, const int32_t *perm,
+                           const double *rhs, XT *y, XT *zreset, const PcgState *st, long long spin_limit,
+                           int32_t *status)
+{
+    if (st && st->done) return;
+    const unsigned lane = threadIdx.x & 31;
+    const int sub = lane / S, sl = lane % S;
+    const unsigned smask = (S == 32) ? FULL : (((1u << S) - 1u) << (sub * S));
+    const int rows_per_group = (blockDim.x / 32) * (32 / S);
+    const int my = (threadIdx.x >> 5) * (32 / S) + sub;
+    const int64_t ngroups = ((int64_t)n + rows_per_group - 1) / rows_per_group;
+    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const int64_t i = g * rows_per_group + my;
+        if (i >= n) continue;
+        XT acc = 0;
+        bool ok = true;
+        for (int64_t t = rp[i] + sl; t < rp[i + 1]; t += S) {
+            const int32_t k = ci[t];
+            const XT f = (XT)v[t];
+            XT yk = ld_poll(y + k);
+            long long spins = 0;
+            while (is_sentinel(yk)) {
+                if (++spins > spin_limit || read_status(status) != ST_OK) { ok = false; break; }
+                yk = ld_poll(y + k);
+            }
+            if (!ok) break;
+            acc += f * yk;
+        }
+        if (!ok) set_status(status, ST_TIMEOUT);
+#pragma unroll
+        for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
+        if (sl == 0) {
+            zreset[i] = sentinel<XT>();
+            st_pub(y + i, to_x<XT>(rhs[perm[i]]) - acc);
+        }
+    }
+}
+
+// Backward: z[k] = y[k] Dinv[k] - sum_{i>k} F(i,k) z[i] over the CSC column k;
+// writes z_orig[perm[k]], resets y[k] to the sentinel, and accumulates
+// r_orig . z_orig into the block partial.
+template <int S, typename VT, typename XT>
+__global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, const VT *v, const double *Dinv,
+                           const int32_t *perm, XT *y, XT *z, double *zout, const double *r_orig, double *partial,
+                           const PcgState *st, long long spin_limit, int32_t *status)
+{
+    if (st && st->done) return;
+    const unsigned lane = threadIdx.x & 31;
+    const int sub = lane / S, sl = lane % S;
+    const unsigned smask = (S == 32) ? FULL : (((1u << S) - 1u) << (sub * S));
+    const int rows_per_group = (blockDim.x / 32) * (32 / S);
+    const int my = (threadIdx.x >> 5) * (32 / S) + sub;
+    const int64_t ngroups = ((int64_t)n + rows_per_group - 1) / rows_per_group;
+    double dotacc = 0.0;
+    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const int64_t kk = g * rows_per_group + my;
+        if (kk >= n) continue;
+        const int64_t k = n - 1 - kk;
+        XT acc = 0;
+        bool ok = true;
+        for (int64_t t = cp[k] + sl; t < cp[k + 1]; t += S) {
+            const int32_t i = ri[t];
+            const XT f = (XT)v[t];
+            XT zi = ld_poll(z + i);
+            long long spins = 0;
+            while (is_sentinel(zi)) {
+                if (++spins > spin_limit || read_status(status) != ST_OK) { ok = false; break; }
+                zi = ld_poll(z + i);
+            }
+            if (!ok) break;
+            acc += f * zi;
+        }
+        if (!ok) set_status(status, ST_TIMEOUT);
+#pragma unroll
+        for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
+        if (sl == 0) {
+            const XT yk = y[k];
+            const XT scaled = to_x<XT>((double)yk * Dinv[k]);
+            const XT zk = scaled - acc;
+            y[k] = sentinel<XT>();
+            st_pub(z + k, zk);
+            const int32_t o = perm[k];
+            zout[o] = (double)zk;
+            if (r_orig) dotacc += r_orig[o] * (double)zk;
+        }
+    }
+    if (partial) {
+        const double s = block_sum(dotacc);
+        if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    }
+}
+
+inline int vec_grid(int32_t n, int maxb)
+{
+    int b = (int)(((int64_t)n + VEC_THREADS - 1) / VEC_THREADS);
+    if (b < 1) b = 1;
+    return b < maxb ? b : maxb;
+}
+
+template <int S>
+cudaError_t spmv_t(const SolveArgs &A, const double *x, double *y, double *partial, const PcgState *st, int blocks,
+                   cudaStream_t s)
+{
+    k_spmv<S><<<blocks, VEC_THREADS, 0, s>>>(A.n, A.Lp, A.Li, A.Lv, x, y, partial, st);
+    return cudaGetLastError();
+}
+
+cudaError_t spmv(const SolveArgs &A, const double *x, double *y, double *partial, const PcgState *st, int blocks,
+                 cudaStream_t s)
+{
+    switch (A.lanes_spmv) {
+    case 4: return spmv_t<4>(A, x, y, partial, st, blocks, s);
+    case 8: return spmv_t<8>(A, x, y, partial, st, blocks, s);
+    case 16: return spmv_t<16>(A, x, y, partial, st, blocks, s);
+    default: return spmv_t<32>(A, x, y, partial, st, blocks, s);
+    }
+}
+
+template <int S, typename VT, typename XT>
+cudaError_t apply_t(const SolveArgs &A, const VT *vr, const VT *vc, XT *y, XT *z, const double *r, double *zout,
+                    double *partial, const PcgState *st, cudaStream_t s)
+{
+    const int threads = A.trsv_warps * 32;
+    k_trsv_fwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Frp, A.Fcol, vr, A.perm, r, y, z, st,
+                                                             A.spin_limit, A.status);
+    k_trsv_bwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Fcp, A.Frow, vc, A.Dinv, A.perm, y, z, zout, r,
+                                                             partial, st, A.spin_limit, A.status);
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t apply_s(const SolveArgs &A, const PcgBuffers &B, const double *r, double *zout, double *partial,
+                    const PcgState *st, cudaStream_t s)
+{
+    if (A.prec == 32) return apply_t<S, float, float>(A, A.Fvalr32, A.Fval32, B.yl32, B.zl32, r, zout, partial, st, s);
+    return apply_t<S, double, double>(A, A.Fvalr64, A.Fval64, B.yl64, B.zl64, r, zout, partial, st, s);
+}
+
+cudaError_t apply(const SolveArgs &A, const PcgBuffers &B, const double *r, double *zout, double *partial,
+                  const PcgState *st, cudaStream_t s)
+{
+    switch (A.lanes_trsv) {
+    case 4: return apply_s<4>(A, B, r, zout, partial, st, s);
+    case 8: return apply_s<8>(A, B, r, zout, partial, st, s);
+    case 16: return apply_s<16>(A, B, r, zout, partial, st, s);
+    default: return apply_s<32>(A, B, r, zout, partial, st, s);
+    }
+}
+
+cudaError_t fill_sentinels(const SolveArgs &A, const PcgBuffers &B, cudaStream_t s)
+{
+    const int g = vec_grid(A.n, 4096);
+    if (A.prec == 32) k_fill_sentinel<float><<<g, VEC_THREADS, 0, s>>>(A.n, B.yl32, B.zl32);
+    else k_fill_sentinel<double><<<g, VEC_THREADS, 0, s>>>(A.n, B.yl64, B.zl64);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t pcg_state_bytes() { return sizeof(PcgState); }
+
+int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec)
+{
+    cudaError_t e;
+    const int threads = warps * 32;
+    switch (lanes) {
+    case 4:
+        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<4, float, float>, threads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<4, double, double>, threads, 0);
+        break;
+    case 8:
+        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<8, float, float>, threads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<8, double, double>, threads, 0);
+        break;
+    case 16:
+        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<16, float, float>, threads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<16, double, double>, threads, 0);
+        break;
+    default:
+        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<32, float, float>, threads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<32, double, double>, threads, 0);
+    }
+    int b2 = 0;
+    // the backward kernel must fit the same grid
+    switch (lanes) {
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<4, float, float> : (const void *)k_trsv_bwd<4, double, double>, threads, 0); break;
+    case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<8, float, float> : (const void *)k_trsv_bwd<8, double, double>, threads, 0); break;
+    case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<16, float, float> : (const void *)k_trsv_bwd<16, double, double>, threads, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<32, float, float> : (const void *)k_trsv_bwd<32, double, double>, threads, 0);
+    }
+    if (b2 < *blocks_per_sm) *blocks_per_sm = b2;
+    return e == cudaSuccess ? 0 : -1;
+}
+
+cudaError_t precond_apply(const SolveArgs &A, const PcgBuffers &B, const double *r, double *z, cudaStream_t st)
+{
+    cudaError_t e = fill_sentinels(A, B, st);
+    if (e != cudaSuccess) return e;
+    return apply(A, B, r, z, nullptr, nullptr, st);
+}
+
+cudaError_t pcg_init(const SolveArgs &A, const PcgBuffers &B, double tol, int32_t maxit, cudaStream_t s)
+{
+    const int nb = B.vec_blocks;
+    double *p_bb = B.partials, *p_rz = B.partials + B.pstride;
+    k_init_vectors<<<nb, VEC_THREADS, 0, s>>>(A.n, B.b, B.x, B.r, p_bb);
+    cudaError_t e = fill_sentinels(A, B, s);
+    if (e != cudaSuccess) return e;
+    e = apply(A, B, B.r, B.z, p_rz, nullptr, s);
+    if (e != cudaSuccess) return e;
+    k_init_scalars<<<1, 256, 0, s>>>(B.state, p_bb, nb, p_rz, A.trsv_blocks, tol, maxit);
+    k_copy<<<nb, VEC_THREADS, 0, s>>>(A.n, B.z, B.p);
+    return cudaGetLastError();
+}
+
+cudaError_t pcg_iteration(const SolveArgs &A, const PcgBuffers &B, cudaStream_t s)
+{
+    const int nb = B.vec_blocks;
+    double *p_pq = B.partials, *p_rr = B.partials + B.pstride, *p_rz = B.partials + 2 * B.pstride;
+    cudaError_t e = spmv(A, B.p, B.q, p_pq, B.state, nb, s);
+    if (e != cudaSuccess) return e;
+    k_alpha<<<1, 256, 0, s>>>(B.state, p_pq, nb);
+    k_update_xr<<<nb, VEC_THREADS, 0, s>>>(A.n, B.x, B.r, B.p, B.q, p_rr, B.state);
+    k_check<<<1, 256, 0, s>>>(B.state, p_rr, nb);
+    e = apply(A, B, B.r, B.z, p_rz, B.state, s);
+    if (e != cudaSuccess) return e;
+    k_beta<<<1, 256, 0, s>>>(B.state, p_rz, A.trsv_blocks);
+    k_update_p<<<nb, VEC_THREADS, 0, s>>>(A.n, B.p, B.z, B.state);
+    return cudaGetLastError();
+}
+
+// resume after a recurrence convergence that the true residual rejected:
+// precondition the current residual and update p, then clear `done`.
+__global__ void k_clear_done(PcgState *st) { st->done = 0; st->converged = 0; }
+
+cudaError_t pcg_clear_done(const PcgBuffers &B, cudaStream_t s)
+{
+    k_clear_done<<<1, 1, 0, s>>>(B.state);
+    return cudaGetLastError();
+}
+
+cudaError_t pcg_resume(const SolveArgs &A, const PcgBuffers &B, cudaStream_t s)
+{
+    const int nb = B.vec_blocks;
+    double *p_rz = B.partials + 2 * B.pstride;
+    cudaError_t e = apply(A, B, B.r, B.z, p_rz, B.state, s);
+    if (e != cudaSuccess) return e;
+    k_beta<<<1, 256, 0, s>>>(B.state, p_rz, A.trsv_blocks);
+    k_update_p<<<nb, VEC_THREADS, 0, s>>>(A.n, B.p, B.z, B.state);
+    return cudaGetLastError();
+}
+
+cudaError_t pcg_true_residual(const SolveArgs &A, const PcgBuffers &B, cudaStream_t s)
+{
+    const int nb = B.vec_blocks;
+    cudaError_t e = spmv(A, B.x, B.q, nullptr, nullptr, nb, s);
+    if (e != cudaSuccess) return e;
+    k_resid_sq<<<nb, VEC_THREADS, 0, s>>>(A.n, B.b, B.q, B.partials);
+    k_true_rr<<<1, 256, 0, s>>>(B.state, B.partials, nb);
+    return cudaGetLastError();
+}
+
+cudaError_t pcg_read_state(const PcgBuffers &B, PcgHostState *h, cudaStream_t s)
+{
+    PcgState hs;
+    cudaError_t e = cudaMemcpyAsync(&hs, B.state, sizeof(PcgState), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    h->done = hs.done; h->iters = hs.iters; h->rr = hs.rr; h->bb = hs.bb; h->true_rr = hs.true_rr; h->maxit = hs.maxit;
+    return cudaSuccess;
+}
+
+}  // namespace parac

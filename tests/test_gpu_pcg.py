@@ -1,0 +1,125 @@
+"""GPU solve parity: preconditioner apply and PCG against the oracle (FP64),
+and the FP32-stored factor inside FP64 PCG."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_02977_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2505_02977_gb300 import parac
+    return parac
+
+
+def _factor(P, A, perm, seed, **opts):
+    return P.parac_factor(A.n, A.colptr, A.rowind, A.val, perm, seed, P.parac_opts_default(**opts) if opts else None)
+
+
+def _cases():
+    out = [W.config("grid2d-64")]
+    rng = np.random.default_rng(2)
+    for s in range(3):
+        n = int(rng.integers(300, 4000))
+        a, b = W.sparse_random_edges(n, 3 * n, s)
+        A = W.laplacian_from_edges(n, a, b, rng.lognormal(0, 1, len(a)))
+        out.append((A, W.random_ordering(n, s), s, W.gaussian_rhs(n, 1, s)))
+    return out
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_precond_apply_matches_oracle(P, case):
+    A, perm, seed, b = _cases()[case]
+    G = _factor(P, A, perm, seed)
+    F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)
+    r = np.random.default_rng(case).standard_normal(A.n)
+    z = P.parac_precond_apply(G, r)
+    zr = oracle.precond_apply(F, perm, r)
+    assert np.linalg.norm(z - zr) <= 1e-12 * np.linalg.norm(zr)
+    G.free()
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_pcg_matches_oracle(P, case):
+    A, perm, seed, b = _cases()[case]
+    G = _factor(P, A, perm, seed)
+    F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)
+    xo, ito, rro = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, b, 1e-8, 1000)
+    x, it, rr, status = P.parac_pcg(G, A.n, None, None, None, b, tol=1e-8, maxit=1000)
+    assert status == "PARAC_OK" and rr[0] <= 1e-8
+    assert abs(int(it[0]) - ito) <= 1
+    # same number of iterations on both sides -> same iterate up to rounding
+    x2, it2, _, _ = P.parac_pcg(G, A.n, None, None, None, b, tol=0.0, maxit=ito)
+    assert it2[0] == ito
+    xa, xb = x2 - x2.mean(), xo - xo.mean()
+    assert np.linalg.norm(xa - xb) <= 1e-10 * np.linalg.norm(xb)
+    G.free()
+
+
+def test_pcg_with_caller_matrix_and_device_arrays(P):
+    import torch
+    A, perm, seed, b = W.config("grid2d-64")
+    G = _factor(P, A, perm, seed)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    x, it, rr, status = P.parac_pcg(G, A.n, dev(A.colptr), dev(A.rowind), dev(A.val), dev(b), tol=1e-8)
+    assert status == "PARAC_OK" and rr[0] <= 1e-8
+    xh, ith, rrh, _ = P.parac_pcg(G, A.n, A.colptr, A.rowind, A.val, b, tol=1e-8)
+    assert it[0] == ith[0]
+    assert np.allclose(x.cpu().numpy(), xh, rtol=0, atol=1e-12 * np.abs(xh).max())
+    G.free()
+
+
+def test_pcg_sddm_matches_dense_solve(P):
+    rng = np.random.default_rng(4)
+    n = 600
+    a, b = W.sparse_random_edges(n, 4 * n, 4)
+    w = rng.uniform(0.1, 10, len(a))
+    deg = np.bincount(a, weights=w, minlength=n) + np.bincount(b, weights=w, minlength=n)
+    A = W.laplacian_from_edges(n, a, b, w, rng.uniform(0, 0.1, n) * deg)
+    perm = W.random_ordering(n, 1)
+    bvec = rng.standard_normal(n)
+    G = _factor(P, A, perm, 3)
+    x, it, rr, status = P.parac_pcg(G, n, None, None, None, bvec, tol=1e-12, maxit=500)
+    xs = np.linalg.solve(A.dense(), bvec)
+    assert status == "PARAC_OK"
+    assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+    G.free()
+
+
+def test_fp32_factor_converges(P):
+    """FP32-stored G applied in FP32 inside FP64 PCG reaches the same 1e-8 true
+    residual, within a few iterations of the FP64 solve."""
+    A, perm, seed, b = W.config("grid3d-32")
+    G64 = _factor(P, A, perm, seed)
+    G32 = _factor(P, A, perm, seed, g_precision=32)
+    _, it64, rr64, s64 = P.parac_pcg(G64, A.n, None, None, None, b, tol=1e-8, maxit=500)
+    _, it32, rr32, s32 = P.parac_pcg(G32, A.n, None, None, None, b, tol=1e-8, maxit=500)
+    assert s64 == s32 == "PARAC_OK" and rr32[0] <= 1e-8 and rr64[0] <= 1e-8
+    assert it32[0] <= it64[0] + 3
+    G64.free(); G32.free()
+
+
+def test_pcg_multiple_rhs(P):
+    A, perm, seed, _ = W.config("grid2d-64")
+    B = W.gaussian_rhs(A.n, 4, 9)
+    G = _factor(P, A, perm, seed)
+    X, it, rr, status = P.parac_pcg(G, A.n, None, None, None, B, tol=1e-8, maxit=500)
+    assert status == "PARAC_OK" and np.all(rr <= 1e-8)
+    for j in range(4):
+        xj, itj, _, _ = P.parac_pcg(G, A.n, None, None, None, B[:, j], tol=1e-8, maxit=500)
+        assert itj[0] == it[j]
+        assert np.allclose(X[:, j], xj, rtol=0, atol=1e-12 * np.abs(xj).max())
+    G.free()
+
+
+def test_pcg_noconv_status(P):
+    A, perm, seed, b = W.config("grid2d-64")
+    G = _factor(P, A, perm, seed)
+    x, it, rr, status = P.parac_pcg(G, A.n, None, None, None, b, tol=1e-14, maxit=3)
+    assert status == "PARAC_ENOCONV" and it[0] == 3 and rr[0] > 1e-14
+    G.free()
