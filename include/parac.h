@@ -200,6 +200,10 @@ const char *parac_status_string(parac_status s);
 /* Message describing the last failing call on this thread ("" if none). */
 const char *parac_last_error(void);
 
+/* Diagnostics: number of GPU kernels this library has launched in the
+ * process so far (all threads and devices). */
+uint64_t parac_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -3,6 +3,7 @@
 // orchestration of ingest -> persistent elimination -> compaction -> solve.
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -16,6 +17,12 @@
 #include "kernels.h"
 
 using namespace parac;
+
+namespace parac {
+static unsigned long long g_launches = 0;
+void count_launches(unsigned n) { __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+}  // namespace parac
 
 namespace {
 
@@ -166,7 +173,11 @@ struct parac_factor_s {
     int32_t sptrsv = 0;
     int32_t check_every = 8;
     cudaStream_t stream = nullptr;
-    DBuf perm, Fcp, Frow, Fval, Fval32, Frp, Fcol, Fvalr, Fvalr32, D, Dinv, Lp, Li, Lv;
+    DBuf perm, Fcp, Frow, Fval, D, Lp, Li, Lv;          // label space (export) and the matrix
+    DBuf Lev;                                          // dependency level of each column
+    // solve arrays: F relabelled into dependency-level order (positions)
+    DBuf Scp, Srow, Sval, Sval32, Srp, Scol, Svalr, Svalr32, Sdinv, Sperm;
+    int32_t depth = 0;
     int64_t nnzL = 0;
     std::string stats;
     SolveCache cache;
@@ -189,7 +200,7 @@ Opts read_opts(const parac_opts *in)
     if (r.o.max_pool_regrow < 0) r.o.max_pool_regrow = 0;
     if (r.o.spin_limit <= 0) r.o.spin_limit = 1ll << 24;
     if (r.o.warps_per_block <= 0) r.o.warps_per_block = 8;
-    if (r.o.warps_per_block > 16) r.o.warps_per_block = 16;
+    if (r.o.warps_per_block > 8) r.o.warps_per_block = 8;     // the elimination kernel's launch bound
     if (r.o.queue_chunk <= 0) r.o.queue_chunk = 1;
     if (r.o.check_every <= 0) r.o.check_every = 8;
     if (r.o.g_precision != 32) r.o.g_precision = 64;
@@ -206,10 +217,10 @@ struct SysDesc {
 
 struct FactorOut {
     // output-space (N) arrays
-    DBuf Fcp, Frow, Fval, D;
+    DBuf Fcp, Frow, Fval, D, Lev;
     int64_t nnzF = 0;
     int64_t nl = 0, nnz_low = 0;
-    unsigned long long stats[8] = {0};
+    unsigned long long stats[16] = {0};
     unsigned long long pool_used = 0, f_used = 0, scratch_used = 0;
     int regrows = 0;
     double t_ingest = 0, t_elim = 0, t_compact = 0;
@@ -348,12 +359,22 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
     const int total_warps = blocks * warps;
     const int fchunk = 256;
 
-    DBuf dp = dalloc<int32_t>(nl, st), queue = dalloc<int32_t>(nl, st), ctrs = dalloc<uint32_t>(2, st);
+    DBuf dp = dalloc<int32_t>(nl, st), queue = dalloc<int32_t>(nl, st), ctrs = dalloc<uint32_t>(3, st);
     DBuf fcnt = dalloc<uint32_t>(nl, st), in_row = dalloc<int32_t>((size_t)nl * FILL_C0, st),
          in_w = dalloc<double>((size_t)nl * FILL_C0, st), dir = dalloc<uint32_t>((size_t)nl * FILL_LEVELS, st);
     DBuf f_start = dalloc<int64_t>(nl, st), f_len = dalloc<int32_t>(nl, st), Dl = dalloc<double>(nl, st);
-    DBuf tops = dalloc<unsigned long long>(3, st), status = dalloc<int32_t>(1, st), stats = dalloc<unsigned long long>(8, st);
+    DBuf lvl = dalloc<int32_t>(nl, st);
+    DBuf tops = dalloc<unsigned long long>(3, st), status = dalloc<int32_t>(1, st), stats = dalloc<unsigned long long>(16, st);
 
+    // optional per-vertex trace, written to the file named by PARAC_TRACE
+    const char *trace_path = getenv("PARAC_TRACE");
+    DBuf trace_buf, trace_par;
+    if (trace_path) {
+        trace_buf = dalloc<long long>((size_t)nl * 4, st);
+        trace_par = dalloc<int32_t>((size_t)nl, st);
+        CK(cudaMemsetAsync(trace_buf.p, 0, 32 * (size_t)nl, st));
+        CK(cudaMemsetAsync(trace_par.p, 0xff, 4 * (size_t)nl, st));
+    }
     double mult = O.o.pool_mult;
     unsigned long long scratch_cap = 64ull << 20;
     DBuf pool_row, pool_w, f_row, f_val, scratch;
@@ -366,12 +387,13 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         scratch.alloc(scratch_cap, st);
         CK(cudaMemcpyAsync(dp.p, dp0.p, 4 * nl, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemsetAsync(queue.p, 0xff, 4 * nl, st));
-        CK(cudaMemsetAsync(ctrs.p, 0, 8, st));
+        CK(cudaMemsetAsync(ctrs.p, 0, 12, st));
         CK(cudaMemsetAsync(fcnt.p, 0, 4 * nl, st));
         CK(cudaMemsetAsync(dir.p, 0, 4 * (size_t)nl * FILL_LEVELS, st));
         CK(cudaMemsetAsync(tops.p, 0, 24, st));
         CK(cudaMemsetAsync(status.p, 0, 4, st));
-        CK(cudaMemsetAsync(stats.p, 0, 64, st));
+        CK(cudaMemsetAsync(stats.p, 0, 128, st));
+        CK(cudaMemsetAsync(lvl.p, 0, 4 * nl, st));
         CK(launch_queue_init((int32_t)nl, dp.as<int32_t>(), queue.as<int32_t>(), ctrs.as<uint32_t>() + 1, st));
 
         ElimArgs a{};
@@ -380,24 +402,32 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         a.sys_base = batch ? d_sys_lbase.as<int32_t>() : nullptr;
         a.seed = seed;
         a.dp = dp.as<int32_t>(); a.queue = queue.as<int32_t>();
-        a.q_head = ctrs.as<uint32_t>(); a.q_tail = ctrs.as<uint32_t>() + 1;
+        a.q_head = ctrs.as<uint32_t>(); a.q_tail = ctrs.as<uint32_t>() + 1; a.done = ctrs.as<uint32_t>() + 2;
         a.fcnt = fcnt.as<uint32_t>(); a.in_row = in_row.as<int32_t>(); a.in_w = in_w.as<double>();
         a.dir = dir.as<uint32_t>(); a.pool_row = pool_row.as<int32_t>(); a.pool_w = pool_w.as<double>();
         a.pool_top = tops.as<unsigned long long>(); a.pool_cap = pool_cap;
         a.f_row = f_row.as<int32_t>(); a.f_val = f_val.as<double>();
         a.f_top = tops.as<unsigned long long>() + 1; a.f_cap = f_cap;
         a.f_start = f_start.as<int64_t>(); a.f_len = f_len.as<int32_t>(); a.D = Dl.as<double>();
+        a.lvl = lvl.as<int32_t>();
         a.scratch = scratch.as<unsigned char>(); a.scratch_top = tops.as<unsigned long long>() + 2;
         a.scratch_cap = scratch_cap;
         a.status = status.as<int32_t>(); a.spin_limit = O.o.spin_limit;
         a.stats = stats.as<unsigned long long>();
         a.warp_cap = warp_cap; a.block_cap = block_cap; a.queue_chunk = O.o.queue_chunk;
+        a.profile = O.o.timing >= 2 ? 1 : 0;
+        a.trace = trace_buf.as<long long>();
+        a.trace_parent = trace_par.as<int32_t>();
+        a.idle_ns = 512;
+        a.coop = 1;
+        if (const char *e = getenv("PARAC_COOP")) a.coop = atoi(e) != 0;
+        if (const char *e = getenv("PARAC_IDLE_NS")) a.idle_ns = std::max(32, std::min(1000000, atoi(e)));
         if (nl > 0) CK(elim_launch(a, blocks, warps, fchunk, st));
         int32_t hst = 0;
         unsigned long long htops[3];
         CK(cudaMemcpyAsync(&hst, status.p, 4, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(htops, tops.p, 24, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(out.stats, stats.p, 64, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(out.stats, stats.p, 128, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         out.pool_used = htops[0]; out.f_used = htops[1]; out.scratch_used = htops[2];
         if (hst == ST_OK) break;
@@ -413,6 +443,22 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
     }
     scratch.release(); pool_row.release(); pool_w.release();
     out.t_elim = t_el.stop();
+    if (trace_path) {
+        std::vector<long long> tr((size_t)nl * 4);
+        std::vector<int32_t> par((size_t)nl), lv((size_t)nl);
+        CK(cudaMemcpyAsync(tr.data(), trace_buf.p, 32 * (size_t)nl, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(par.data(), trace_par.p, 4 * (size_t)nl, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(lv.data(), lvl.p, 4 * (size_t)nl, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (FILE *f = fopen(trace_path, "wb")) {
+            const long long nn = nl;
+            fwrite(&nn, 8, 1, f);
+            fwrite(tr.data(), 8, tr.size(), f);
+            fwrite(par.data(), 4, par.size(), f);
+            fwrite(lv.data(), 4, lv.size(), f);
+            fclose(f);
+        }
+    }
 
     // ---------------------------------------------------------------- compaction
     EvTimer t_cp(O.o.timing != 0, st);
@@ -434,53 +480,97 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
     out.Frow = dalloc<int32_t>(std::max<int64_t>(nnzF, 1), st);
     out.Fval = dalloc<double>(std::max<int64_t>(nnzF, 1), st);
     out.D = dalloc<double>(std::max<int64_t>(N, 1), st);
+    out.Lev = dalloc<int32_t>(std::max<int64_t>(N, 1), st);
+    CK(launch_scatter_levels((int32_t)nl, out_of_label.as<int32_t>(), lvl.as<int32_t>(), out.Lev.as<int32_t>(), st));
     CK(launch_gather_factor((int32_t)nl, out_of_label.as<int32_t>(), f_start.as<int64_t>(), f_row.as<int32_t>(),
                             f_val.as<double>(), Dl.as<double>(), out.Fcp.as<int64_t>(), out.Frow.as<int32_t>(),
                             out.Fval.as<double>(), out.D.as<double>(), st));
     out.t_compact = t_cp.stop();
 }
 
-// Build the solve-side arrays of a handle from CSC(F) of n columns.
+// Build the solve-side arrays of a handle from its label-space CSC(F): sort
+// the columns by dependency level, relabel F into that order (positions),
+// and build the CSR of the relabelled factor for the forward solve.
 void finish_handle(parac_factor_s *h, int64_t n, int64_t nnzF, const Opts &O)
 {
     cudaStream_t st = O.st;
-    h->Frp = dalloc<int64_t>(n + 1, st);
-    h->Fcol = dalloc<int32_t>(std::max<int64_t>(nnzF, 1), st);
-    h->Fvalr = dalloc<double>(std::max<int64_t>(nnzF, 1), st);
-    DBuf cnt = dalloc<int32_t>(std::max<int64_t>(n, 1), st);
-    CK(cudaMemsetAsync(cnt.p, 0, 4 * std::max<int64_t>(n, 1), st));
-    CK(launch_row_count(nnzF, h->Frow.as<int32_t>(), cnt.as<int32_t>(), st));
+    const size_t n1 = (size_t)std::max<int64_t>(n, 1), z1 = (size_t)std::max<int64_t>(nnzF, 1);
+    DBuf order = dalloc<int32_t>(n1, st);
+    h->depth = 0;
+    if (n > 0) {
+        DBuf mx = dalloc<int32_t>(1, st);
+        CK(cudaMemsetAsync(mx.p, 0, 4, st));
+        CK(launch_max_i32(h->Lev.as<int32_t>(), n, mx.as<int32_t>(), st));
+        int32_t hmax = 0;
+        CK(cudaMemcpyAsync(&hmax, mx.p, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        h->depth = hmax + 1;
+        DBuf hist = dalloc<int32_t>((size_t)hmax + 1, st), lstart = dalloc<int64_t>((size_t)hmax + 2, st);
+        CK(cudaMemsetAsync(hist.p, 0, 4 * ((size_t)hmax + 1), st));
+        CK(launch_row_count(n, h->Lev.as<int32_t>(), hist.as<int32_t>(), st));
+        DBuf tmp2(scan_tmp_bytes(hmax + 2), st);
+        CK(scan_i32_to_i64(hist.as<int32_t>(), lstart.as<int64_t>(), hmax + 1, tmp2.p, st));
+        CK(cudaMemsetAsync(hist.p, 0, 4 * ((size_t)hmax + 1), st));
+        CK(launch_level_scatter((int32_t)n, h->Lev.as<int32_t>(), lstart.as<int64_t>(), hist.as<int32_t>(),
+                                order.as<int32_t>(), st));
+    }
+    DBuf posof = dalloc<int32_t>(n1, st), len = dalloc<int32_t>(n1, st);
+    CK(launch_inverse_perm((int32_t)n, order.as<int32_t>(), posof.as<int32_t>(), st));
+    CK(launch_relabel_lengths((int32_t)n, order.as<int32_t>(), h->Fcp.as<int64_t>(), len.as<int32_t>(), st));
     DBuf tmp(scan_tmp_bytes(n + 1), st);
-    CK(scan_i32_to_i64(cnt.as<int32_t>(), h->Frp.as<int64_t>(), n, tmp.p, st));
-    CK(cudaMemsetAsync(cnt.p, 0, 4 * std::max<int64_t>(n, 1), st));
-    CK(launch_transpose_scatter((int32_t)n, h->Fcp.as<int64_t>(), h->Frow.as<int32_t>(), h->Fval.as<double>(),
-                                h->Frp.as<int64_t>(), cnt.as<int32_t>(), h->Fcol.as<int32_t>(), h->Fvalr.as<double>(), st));
-    CK(launch_sort_rows((int32_t)n, h->Frp.as<int64_t>(), h->Fcol.as<int32_t>(), h->Fvalr.as<double>(), st));
-    h->Dinv = dalloc<double>(std::max<int64_t>(n, 1), st);
-    CK(launch_dinv((int32_t)n, h->D.as<double>(), h->Dinv.as<double>(), st));
+    h->Scp = dalloc<int64_t>((size_t)n + 1, st);
+    CK(scan_i32_to_i64(len.as<int32_t>(), h->Scp.as<int64_t>(), n, tmp.p, st));
+    h->Srow = dalloc<int32_t>(z1, st);
+    h->Sval = dalloc<double>(z1, st);
+    CK(launch_relabel_gather((int32_t)n, order.as<int32_t>(), posof.as<int32_t>(), h->Fcp.as<int64_t>(),
+                             h->Frow.as<int32_t>(), h->Fval.as<double>(), h->Scp.as<int64_t>(), h->Srow.as<int32_t>(),
+                             h->Sval.as<double>(), st));
+    // CSR of the relabelled factor
+    h->Srp = dalloc<int64_t>((size_t)n + 1, st);
+    h->Scol = dalloc<int32_t>(z1, st);
+    h->Svalr = dalloc<double>(z1, st);
+    DBuf cnt = dalloc<int32_t>(n1, st);
+    CK(cudaMemsetAsync(cnt.p, 0, 4 * n1, st));
+    CK(launch_row_count(nnzF, h->Srow.as<int32_t>(), cnt.as<int32_t>(), st));
+    CK(scan_i32_to_i64(cnt.as<int32_t>(), h->Srp.as<int64_t>(), n, tmp.p, st));
+    CK(cudaMemsetAsync(cnt.p, 0, 4 * n1, st));
+    CK(launch_transpose_scatter((int32_t)n, h->Scp.as<int64_t>(), h->Srow.as<int32_t>(), h->Sval.as<double>(),
+                                h->Srp.as<int64_t>(), cnt.as<int32_t>(), h->Scol.as<int32_t>(), h->Svalr.as<double>(), st));
+    CK(launch_sort_rows((int32_t)n, h->Srp.as<int64_t>(), h->Scol.as<int32_t>(), h->Svalr.as<double>(), st));
+    // pivots and original indices by position
+    DBuf Dpos = dalloc<double>(n1, st);
+    CK(launch_gather_f64((int32_t)n, order.as<int32_t>(), h->D.as<double>(), Dpos.as<double>(), st));
+    h->Sdinv = dalloc<double>(n1, st);
+    CK(launch_dinv((int32_t)n, Dpos.as<double>(), h->Sdinv.as<double>(), st));
+    h->Sperm = dalloc<int32_t>(n1, st);
+    CK(launch_gather_i32((int32_t)n, order.as<int32_t>(), h->perm.as<int32_t>(), h->Sperm.as<int32_t>(), st));
     if (h->prec == 32) {
-        h->Fval32 = dalloc<float>(std::max<int64_t>(nnzF, 1), st);
-        h->Fvalr32 = dalloc<float>(std::max<int64_t>(nnzF, 1), st);
-        CK(launch_to_f32(h->Fval.as<double>(), h->Fval32.as<float>(), nnzF, st));
-        CK(launch_to_f32(h->Fvalr.as<double>(), h->Fvalr32.as<float>(), nnzF, st));
+        h->Sval32 = dalloc<float>(z1, st);
+        h->Svalr32 = dalloc<float>(z1, st);
+        CK(launch_to_f32(h->Sval.as<double>(), h->Sval32.as<float>(), nnzF, st));
+        CK(launch_to_f32(h->Svalr.as<double>(), h->Svalr32.as<float>(), nnzF, st));
     }
     h->status = dalloc<int32_t>(1, st);
 }
 
 std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_index)
 {
-    char buf[1024];
+    char buf[2048];
     snprintf(buf, sizeof buf,
              "{\"n\": %lld, \"nnz_F\": %lld, \"nnz_G\": %lld, \"labels\": %lld, \"nnz_lower_input\": %lld, "
              "\"fill_entries\": %llu, \"pool_entries_used\": %llu, \"factor_entries_used\": %llu, "
              "\"scratch_bytes_used\": %llu, \"vertices_warp_path\": %llu, \"vertices_block_path\": %llu, "
-             "\"vertices_global_path\": %llu, \"queue_spins\": %llu, \"regrows\": %d, \"blocks\": %d, "
+             "\"vertices_global_path\": %llu, \"vertices_register_path\": %llu, \"handoffs\": %llu, "
+             "\"queue_spins\": %llu, \"regrows\": %d, \"blocks\": %d, "
              "\"warps_per_block\": %d, \"precision\": %d, \"system\": %d, \"t_ingest_ms\": %.4f, "
-             "\"t_elim_ms\": %.4f, \"t_compact_ms\": %.4f}",
+             "\"t_elim_ms\": %.4f, \"t_compact_ms\": %.4f, \"depth\": %d, \"cycles\": {\"wait\": %llu, "
+             "\"gather\": %llu, \"sort_merge\": %llu, \"store_sort_scan\": %llu, \"sample_append\": %llu, "
+             "\"release\": %llu, \"reg_weight_sort\": %llu, \"reg_scan\": %llu}}",
              (long long)h->n, (long long)h->nnzF, (long long)(h->nnzF + h->n), (long long)fo.nl,
              (long long)fo.nnz_low, fo.stats[3], fo.pool_used, fo.f_used, fo.scratch_used, fo.stats[0], fo.stats[1],
-             fo.stats[2], fo.stats[4], fo.regrows, fo.blocks, fo.warps, h->prec, sys_index, fo.t_ingest, fo.t_elim,
-             fo.t_compact);
+             fo.stats[2], fo.stats[5], fo.stats[6], fo.stats[4], fo.regrows, fo.blocks, fo.warps, h->prec, sys_index, fo.t_ingest, fo.t_elim,
+             fo.t_compact, h->depth, fo.stats[8], fo.stats[9], fo.stats[10], fo.stats[11], fo.stats[12],
+             fo.stats[13], fo.stats[14], fo.stats[15]);
     return buf;
 }
 
@@ -550,6 +640,8 @@ const char *parac_status_string(parac_status s)
 
 const char *parac_last_error(void) { return g_err.c_str(); }
 
+uint64_t parac_kernel_launches(void) { return (uint64_t)parac::launch_count(); }
+
 parac_status parac_factor(int64_t n, const int64_t *colptr, const int32_t *rowind, const double *val,
                           const int32_t *ordering, uint64_t seed, const parac_opts *opts, parac_factor_t *out)
 {
@@ -593,6 +685,8 @@ parac_status parac_factor(int64_t n, const int64_t *colptr, const int32_t *rowin
         }
         h->nnzF = fo.nnzF;
         h->Fcp = std::move(fo.Fcp); h->Frow = std::move(fo.Frow); h->Fval = std::move(fo.Fval); h->D = std::move(fo.D);
+        h->Lev = std::move(fo.Lev);
+        if (n == 0) h->Lev = dalloc<int32_t>(1, st);
         h->perm = dalloc<int32_t>(std::max<int64_t>(n, 1), st);
         if (ordering) copy_out(h->perm.p, od.p, 4 * (size_t)n, st);
         else CK(launch_iota_i32(h->perm.as<int32_t>(), n, 0, st));
@@ -692,6 +786,8 @@ parac_status parac_factor_many(int32_t count, const parac_system *systems, uint6
             copy_out(h->Fval.p, fo.Fval.as<double>() + f0, 8 * (size_t)h->nnzF, st);
             h->D = dalloc<double>(std::max<int64_t>(n, 1), st);
             copy_out(h->D.p, fo.D.as<double>() + ob, 8 * (size_t)n, st);
+            h->Lev = dalloc<int32_t>(std::max<int64_t>(n, 1), st);
+            copy_out(h->Lev.p, fo.Lev.as<int32_t>() + ob, 4 * (size_t)n, st);
             h->perm = dalloc<int32_t>(std::max<int64_t>(n, 1), st);
             CK(launch_add_offset_i32(ord.as<int32_t>() + ob, h->perm.as<int32_t>(), n, -(int32_t)ob, st));
             h->nnzL = nnz[s];
@@ -760,20 +856,37 @@ SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, co
     SolveArgs A{};
     A.n = (int32_t)G->n;
     A.Lp = Lp; A.Li = Li; A.Lv = Lv;
-    A.Fcp = G->Fcp.as<int64_t>(); A.Frow = G->Frow.as<int32_t>(); A.Fval64 = G->Fval.as<double>();
-    A.Fval32 = G->Fval32.as<float>();
-    A.Frp = G->Frp.as<int64_t>(); A.Fcol = G->Fcol.as<int32_t>(); A.Fvalr64 = G->Fvalr.as<double>();
-    A.Fvalr32 = G->Fvalr32.as<float>();
-    A.Dinv = G->Dinv.as<double>(); A.perm = G->perm.as<int32_t>();
+    A.Fcp = G->Scp.as<int64_t>(); A.Frow = G->Srow.as<int32_t>(); A.Fval64 = G->Sval.as<double>();
+    A.Fval32 = G->Sval32.as<float>();
+    A.Frp = G->Srp.as<int64_t>(); A.Fcol = G->Scol.as<int32_t>(); A.Fvalr64 = G->Svalr.as<double>();
+    A.Fvalr32 = G->Svalr32.as<float>();
+    A.Dinv = G->Sdinv.as<double>(); A.operm = G->Sperm.as<int32_t>();
     A.prec = G->prec;
     const double n = G->n > 0 ? (double)G->n : 1.0;
     A.lanes_spmv = lanes_for((double)nnzL / n);
-    A.lanes_trsv = lanes_for((double)G->nnzF / n);
+    A.lanes_trsv = 32;      // one row per warp: measured fastest on the 128^3 grid (rows of ~11 entries)
     A.trsv_warps = 8;
+    if (const char *e = getenv("PARAC_TRSV_LANES")) A.lanes_trsv = atoi(e);
+    if (const char *e = getenv("PARAC_TRSV_WARPS")) A.trsv_warps = std::max(1, std::min(32, atoi(e)));
     int bps = 0;
     trsv_configure(A.lanes_trsv, A.trsv_warps, &bps, A.prec);
     if (bps < 1) bps = 1;
-    A.trsv_blocks = num_sms() * bps;
+    const int max_blocks = num_sms() * bps;      // all co-resident: required by the static schedule
+    A.trsv_blocks = max_blocks;
+    // Grid sized to the dependency frontier: about two average levels of rows
+    // in flight, so that waiting rows do not flood the memory system with polls.
+    if (G->depth > 0) {
+        const int64_t rows_per_block = (int64_t)A.trsv_warps * (32 / A.lanes_trsv);
+        const int64_t want = (2 * G->n / G->depth + rows_per_block - 1) / rows_per_block;
+        A.trsv_blocks = (int)std::max<int64_t>(std::min<int64_t>(num_sms(), max_blocks),
+                                               std::min<int64_t>(max_blocks, want));
+    }
+    if (const char *e = getenv("PARAC_TRSV_BLOCKS")) A.trsv_blocks = std::max(1, std::min(max_blocks, atoi(e)));
+    {
+        unsigned ns = 256;
+        if (const char *e = getenv("PARAC_POLL_NS")) ns = (unsigned)std::max(16, std::min(100000, atoi(e)));
+        set_poll_backoff(ns);
+    }
     const int64_t rows_per_group = (int64_t)A.trsv_warps * (32 / A.lanes_trsv);
     const int64_t groups = (G->n + rows_per_group - 1) / rows_per_group;
     if (groups < A.trsv_blocks) A.trsv_blocks = (int)std::max<int64_t>(groups, 1);
@@ -785,7 +898,7 @@ SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, co
 void ensure_cache(parac_factor_s *G, const SolveArgs &A, cudaStream_t st)
 {
     SolveCache &c = G->cache;
-    if (c.n == (int32_t)G->n && c.B.vec_blocks > 0) return;
+    if (c.n == (int32_t)G->n && c.B.vec_blocks > 0 && c.B.pstride >= A.trsv_blocks) return;
     const size_t n = (size_t)std::max<int64_t>(G->n, 1);
     c.x = dalloc<double>(n, st); c.r = dalloc<double>(n, st); c.z = dalloc<double>(n, st);
     c.p = dalloc<double>(n, st); c.q = dalloc<double>(n, st); c.b = dalloc<double>(n, st);

@@ -80,9 +80,21 @@ __device__ __forceinline__ void red_add_relaxed(int32_t *p, int32_t v)
     asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ void red_max_relaxed(int32_t *p, int32_t v)
+{
+    asm volatile("red.relaxed.gpu.global.max.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ long long global_ns()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t) : : "memory");
+    return t;
+}
 
 // ---------------------------------------------------------------- Philox4x64-10
 // Counter-based generator of Salmon et al. (SC'11), 4 words x 64 bits, 10
@@ -156,6 +168,7 @@ struct ElimArgs {
     int32_t *queue;                // ready queue [nl], -1 = empty slot
     uint32_t *q_head;              // claim counter
     uint32_t *q_tail;              // push counter
+    uint32_t *done;                // vertices eliminated so far
 
     uint32_t *fcnt;                // fill entries appended per column [nl]
     int32_t *in_row;               // inline slabs [nl * FILL_C0]
@@ -173,6 +186,7 @@ struct ElimArgs {
     int64_t *f_start;              // [nl]
     int32_t *f_len;                // [nl]
     double *D;                     // [nl]
+    int32_t *lvl;                  // [nl] dependency level (longest chain of pivots reaching the vertex)
 
     unsigned char *scratch;        // big-vertex scratch arena
     unsigned long long *scratch_top;
@@ -180,10 +194,15 @@ struct ElimArgs {
 
     int32_t *status;
     long long spin_limit;
-    unsigned long long *stats;     // [8] counters (see elim.cu)
+    unsigned long long *stats;     // [16] counters (see elim.cu)
     int32_t warp_cap;              // per-warp shared-memory entries (power of two)
     int32_t block_cap;             // per-CTA shared big-vertex buffer entries (power of two, 0 = none)
     int32_t queue_chunk;
+    int32_t profile;               // nonzero: accumulate per-phase cycle counts into stats[8..15]
+    int32_t idle_ns;               // sleep between polls of an idle worker (ns)
+    int32_t coop;                  // nonzero: working sets above warp_cap use the CTA-cooperative path
+    long long *trace;              // optional per-vertex trace [nl * 4]: ready, start, end (ns), g << 32 | d
+    int32_t *trace_parent;         // optional: pivot whose decrement made the vertex ready
 };
 
 // Bytes of shared/scratch memory per entry of the per-vertex working set:

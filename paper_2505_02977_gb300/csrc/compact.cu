@@ -133,6 +133,76 @@ __global__ void k_sort_rows(int32_t n, const int64_t *rp, int32_t *cols, double 
     }
 }
 
+__global__ void k_scatter_levels(int32_t nl, const int32_t *out_of_label, const int32_t *lvl, int32_t *lev_out)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nl; l += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = out_of_label[l];
+        if (o >= 0) lev_out[o] = lvl[l];
+    }
+}
+
+__global__ void k_max_i32(const int32_t *a, int64_t n, int32_t *mx)
+{
+    int32_t m = 0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, a[t]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(mx, m);
+}
+
+__global__ void k_level_scatter(int32_t n, const int32_t *lev, const int64_t *lstart, int32_t *cursor, int32_t *order)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t L = lev[t];
+        order[lstart[L] + atomicAdd(cursor + L, 1)] = (int32_t)t;
+    }
+}
+
+__global__ void k_inverse_perm(int32_t n, const int32_t *order, int32_t *posof)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        posof[order[t]] = (int32_t)t;
+}
+
+__global__ void k_relabel_lengths(int32_t n, const int32_t *order, const int64_t *cp, int32_t *len)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = order[t];
+        len[t] = (int32_t)(cp[c + 1] - cp[c]);
+    }
+}
+
+// one warp per new column j: old column order[j], rows mapped to positions
+__global__ void k_relabel_gather(int32_t n, const int32_t *order, const int32_t *posof, const int64_t *cp,
+                                 const int32_t *rows, const double *vals, const int64_t *ncp, int32_t *nrows,
+                                 double *nvals)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = w0; j < n; j += nw) {
+        const int32_t c = order[j];
+        const int64_t src = cp[c], len = cp[c + 1] - src, dst = ncp[j];
+        for (int64_t i = lane; i < len; i += 32) {
+            nrows[dst + i] = posof[rows[src + i]];
+            nvals[dst + i] = vals[src + i];
+        }
+    }
+}
+
+__global__ void k_gather_i32(int32_t n, const int32_t *idx, const int32_t *src, int32_t *dst)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = src[idx[t]];
+}
+
+__global__ void k_gather_f64(int32_t n, const int32_t *idx, const double *src, double *dst)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = src[idx[t]];
+}
+
 __global__ void k_to_f32(const double *in, float *out, int64_t n)
 {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
@@ -150,7 +220,7 @@ __global__ void k_dinv(int32_t n, const double *D, double *Dinv)
 cudaError_t launch_out_of_label_single(int32_t nl, int32_t n, int32_t *o, cudaStream_t st)
 {
     if (nl == 0) return cudaSuccess;
-    k_out_of_label_single<<<grid_for(nl, 256), 256, 0, st>>>(nl, n, o);
+    k_out_of_label_single<<<grid_for(nl, 256), 256, 0, st>>>(nl, n, o); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -158,14 +228,14 @@ cudaError_t launch_out_of_label_batch(int32_t nl, const int32_t *sys_of_label, c
                                       const int32_t *sys_obase, const int32_t *sys_n, int32_t *o, cudaStream_t st)
 {
     if (nl == 0) return cudaSuccess;
-    k_out_of_label_batch<<<grid_for(nl, 256), 256, 0, st>>>(nl, sys_of_label, sys_lbase, sys_obase, sys_n, o);
+    k_out_of_label_batch<<<grid_for(nl, 256), 256, 0, st>>>(nl, sys_of_label, sys_lbase, sys_obase, sys_n, o); count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sys_of_label(int32_t S, const int32_t *sys_lbase, int32_t nl, int32_t *sys_of_label, cudaStream_t st)
 {
     if (S == 0) return cudaSuccess;
-    k_sys_of_label<<<grid_for(S, 64), 64, 0, st>>>(S, sys_lbase, nl, sys_of_label);
+    k_sys_of_label<<<grid_for(S, 64), 64, 0, st>>>(S, sys_lbase, nl, sys_of_label); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -173,7 +243,7 @@ cudaError_t launch_out_len(int32_t nl, const int32_t *out_of_label, const int64_
                            const int32_t *f_row, int32_t *olen, cudaStream_t st)
 {
     if (nl == 0) return cudaSuccess;
-    k_out_len<<<grid_for(nl, 256), 256, 0, st>>>(nl, out_of_label, f_start, f_len, f_row, olen);
+    k_out_len<<<grid_for(nl, 256), 256, 0, st>>>(nl, out_of_label, f_start, f_len, f_row, olen); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -183,14 +253,14 @@ cudaError_t launch_gather_factor(int32_t nl, const int32_t *out_of_label, const 
 {
     if (nl == 0) return cudaSuccess;
     k_gather_factor<<<grid_for((int64_t)nl * 32, 256), 256, 0, st>>>(nl, out_of_label, f_start, f_row, f_val, D,
-                                                                     fcp, Frow, Fval, Dout);
+                                                                     fcp, Frow, Fval, Dout); count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_row_count(int64_t nnz, const int32_t *rows, int32_t *cnt, cudaStream_t st)
 {
     if (nnz == 0) return cudaSuccess;
-    k_row_count<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, rows, cnt);
+    k_row_count<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, rows, cnt); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -200,28 +270,94 @@ cudaError_t launch_transpose_scatter(int32_t n, const int64_t *cp, const int32_t
 {
     if (n == 0) return cudaSuccess;
     k_transpose_scatter<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, cp, rows, vals, rp, cursor, cols_out,
-                                                                         vals_out);
+                                                                         vals_out); count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sort_rows(int32_t n, const int64_t *rp, int32_t *cols, double *vals, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    k_sort_rows<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, rp, cols, vals);
+    k_sort_rows<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, rp, cols, vals); count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_levels(int32_t nl, const int32_t *out_of_label, const int32_t *lvl, int32_t *lev_out,
+                                  cudaStream_t st)
+{
+    if (nl == 0) return cudaSuccess;
+    k_scatter_levels<<<grid_for(nl, 256), 256, 0, st>>>(nl, out_of_label, lvl, lev_out); count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_i32(const int32_t *a, int64_t n, int32_t *mx, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_max_i32<<<grid_for(n, 256) < 1024 ? grid_for(n, 256) : 1024, 256, 0, st>>>(a, n, mx); count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_scatter(int32_t n, const int32_t *lev, const int64_t *lstart, int32_t *cursor,
+                                 int32_t *order, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_level_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, lev, lstart, cursor, order); count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_perm(int32_t n, const int32_t *order, int32_t *posof, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_inverse_perm<<<grid_for(n, 256), 256, 0, st>>>(n, order, posof);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relabel_lengths(int32_t n, const int32_t *order, const int64_t *cp, int32_t *len, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_relabel_lengths<<<grid_for(n, 256), 256, 0, st>>>(n, order, cp, len);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relabel_gather(int32_t n, const int32_t *order, const int32_t *posof, const int64_t *cp,
+                                  const int32_t *rows, const double *vals, const int64_t *ncp, int32_t *nrows,
+                                  double *nvals, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_relabel_gather<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, order, posof, cp, rows, vals, ncp, nrows,
+                                                                      nvals);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_i32(int32_t n, const int32_t *idx, const int32_t *src, int32_t *dst, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_gather_i32<<<grid_for(n, 256), 256, 0, st>>>(n, idx, src, dst);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_f64(int32_t n, const int32_t *idx, const double *src, double *dst, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_gather_f64<<<grid_for(n, 256), 256, 0, st>>>(n, idx, src, dst);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_to_f32(const double *in, float *out, int64_t n, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    k_to_f32<<<grid_for(n, 256), 256, 0, st>>>(in, out, n);
+    k_to_f32<<<grid_for(n, 256), 256, 0, st>>>(in, out, n); count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dinv(int32_t n, const double *D, double *Dinv, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    k_dinv<<<grid_for(n, 256), 256, 0, st>>>(n, D, Dinv);
+    k_dinv<<<grid_for(n, 256), 256, 0, st>>>(n, D, Dinv); count_launches(1);
     return cudaGetLastError();
 }
 

@@ -2,12 +2,14 @@
 // pivot, Alg. 2; scheduled by ParAC's dependency counters, Sec. III; one
 // persistent launch for the whole factorisation as in Alg. 4 / Sec. IV-C).
 //
-// Worker = one warp.  A worker claims ready-queue slots with one atomicAdd per
-// `queue_chunk` slots, waits (bounded) until a slot is published, and then
-// eliminates that vertex k:
+// Worker = one warp.  A free worker claims a ready-queue slot (one atomicAdd
+// per `queue_chunk` slots) and waits, bounded, until it is published; a
+// worker that has just made vertices ready keeps one of them and eliminates
+// it next without a queue round trip (the others are published).  Eliminating
+// vertex k:
 //   gather     original strict-lower column k + every fill entry appended to
 //              column k (inline slab + overflow levels)
-//   sort       by (row, weight bits), bitonic network over the padded length
+//   sort       by (row, weight bits)
 //   merge      each equal-row run summed left to right -> (u, w_u, m_u)
 //   store      row-ordered (u, w_u) into the factor workspace (F values are
 //              -w_u / D_k, formed later by the compaction kernel)
@@ -20,9 +22,10 @@
 //              S[j] >= R), weight c = (S[p] w_{p-1}) / D_k; append
 //              (max(u,v), c) to column min(u,v) and increment its counter
 //   release    fence, then every neighbour's counter drops by m_u; a
-//              positive-to-zero transition publishes the vertex on the queue.
-// Working sets up to `warp_cap` entries live in the warp's shared memory, up
-// to `block_cap` in one per-CTA shared buffer (taken under a CTA lock), larger
+//              positive-to-zero transition makes the vertex ready.
+// Working sets of up to 32 entries live in registers (one entry per lane,
+// shuffle networks), up to `warp_cap` in the warp's shared memory, up to
+// `block_cap` in one per-CTA shared buffer (taken under a CTA lock), larger
 // ones in a global scratch arena.
 #include "common.cuh"
 #include "kernels.h"
@@ -33,10 +36,11 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int32_t ROW_SENTINEL = 0x7fffffff;
+constexpr unsigned long long WBITS_SENTINEL = 0xffffffffffffffffull;
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
-struct View {           // per-vertex working set
+struct View {           // per-vertex working set in shared or global memory
     double *w;          // weights
     double *S;          // suffix sums
     double *M;          // running maximum of S from the right
@@ -109,6 +113,46 @@ __device__ void sort_bits_row(View v, int P)
     }
 }
 
+// Register bitonic networks: lane i holds entry i; only the first P lanes
+// (P a power of two, warp-uniform) carry entries, the rest hold sentinels
+// that sort last, so the stages with block size above P are skipped.  For
+// the pair (i, i^j) the lower lane keeps the smaller key when the block is
+// ascending.
+__device__ __forceinline__ void reg_sort_row_bits(int32_t &row, double &w, int P)
+{
+    const unsigned lane = lane_id();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int32_t ro = __shfl_xor_sync(FULL, row, j);
+            const double wo = __shfl_xor_sync(FULL, w, j);
+            const bool lower = (lane & j) == 0, asc = (lane & k) == 0;
+            const unsigned long long b = dbits(w), bo = dbits(wo);
+            const bool self_gt = (row > ro) || (row == ro && b > bo);
+            const bool other_gt = (ro > row) || (ro == row && bo > b);
+            const bool take = lower == asc ? self_gt : other_gt;
+            if (take) { row = ro; w = wo; }
+        }
+    }
+}
+
+__device__ __forceinline__ void reg_sort_bits_row(int32_t &row, double &w, int32_t &m, int P)
+{
+    const unsigned lane = lane_id();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int32_t ro = __shfl_xor_sync(FULL, row, j);
+            const double wo = __shfl_xor_sync(FULL, w, j);
+            const int32_t mo = __shfl_xor_sync(FULL, m, j);
+            const bool lower = (lane & j) == 0, asc = (lane & k) == 0;
+            const unsigned long long b = dbits(w), bo = dbits(wo);
+            const bool self_gt = (b > bo) || (b == bo && row > ro);
+            const bool other_gt = (bo > b) || (bo == b && ro > row);
+            const bool take = lower == asc ? self_gt : other_gt;
+            if (take) { row = ro; w = wo; m = mo; }
+        }
+    }
+}
+
 // Bounded wait until *slot is non-zero.  Returns the value, or 0 on timeout /
 // abort (status set by someone).
 __device__ __forceinline__ uint32_t wait_nonzero(const uint32_t *slot, const ElimArgs &a)
@@ -118,7 +162,7 @@ __device__ __forceinline__ uint32_t wait_nonzero(const uint32_t *slot, const Eli
     while ((g = ld_acquire_u32(slot)) == 0u) {
         if (read_status(a.status) != ST_OK) return 0u;
         if (++spins > a.spin_limit) { set_status(a.status, ST_TIMEOUT); return 0u; }
-        __nanosleep(64);
+        if (spins > 32) __nanosleep(32);
     }
     return g;
 }
@@ -126,21 +170,299 @@ __device__ __forceinline__ uint32_t wait_nonzero(const uint32_t *slot, const Eli
 struct WarpState {
     unsigned long long fcur, fend;     // factor-workspace chunk owned by this warp
     unsigned long long sbase, scap;    // global scratch owned by this warp (bytes)
-    unsigned long long n_warp, n_block, n_global, n_fill;
+    unsigned long long n_reg, n_warp, n_block, n_global, n_fill, n_handoff;
+    unsigned long long cyc[8];         // per-phase cycles (profiling runs only)
+    long long t_mark;
     int fchunk;
 };
 
-// Eliminate pivot k with the warp.  Returns false if the kernel must stop.
-__device__ bool eliminate(const ElimArgs &a, int32_t k, unsigned char *wbuf, unsigned char *bbuf,
-                          int *block_lock, WarpState &ws)
+// Per-phase cycle accounting, active only when the launch asks for it:
+// 0 queue wait, 1 gather, 2 sort + merge, 3 store (+ weight sort + scan on
+// the shared-memory path), 4 sampling + append, 5 levels + release +
+// decrements, 6 register weight sort, 7 register scan.
+__device__ __forceinline__ void prof_mark(const ElimArgs &a, WarpState &ws, int phase)
+{
+    if (a.profile) {
+        long long t;
+        asm volatile("mov.u64 %0, %%clock64;" : "=l"(t) : : "memory");   // memory ops stay on their side
+        if (phase >= 0) ws.cyc[phase] += (unsigned long long)(t - ws.t_mark);
+        ws.t_mark = t;
+    }
+}
+
+// Reserve d factor-workspace entries from the warp's chunk.  Warp-uniform.
+__device__ __forceinline__ bool reserve_factor(const ElimArgs &a, WarpState &ws, int d, unsigned long long &pos)
+{
+    if (ws.fcur + (unsigned long long)d > ws.fend) {
+        const unsigned long long sz = d > ws.fchunk ? (unsigned long long)d : (unsigned long long)ws.fchunk;
+        unsigned long long base = 0;
+        if (lane_id() == 0) {
+            base = atomicAdd(a.f_top, sz);
+            if (base + sz > a.f_cap) set_status(a.status, ST_POOL);
+        }
+        base = __shfl_sync(FULL, base, 0);
+        if (read_status(a.status) != ST_OK) return false;
+        ws.fcur = base; ws.fend = base + sz;
+    }
+    pos = ws.fcur;
+    ws.fcur += (unsigned long long)d;
+    return true;
+}
+
+// Append fill entry (row hi, weight c) to column lo and count the new edge in
+// dp[hi]; lanes with act == false only join the warp-wide steps.  The lane
+// that takes the first index of an overflow level allocates that level's slab
+// and publishes it; the other lanes of the level wait for it.  Warp-uniform
+// result; false means the kernel must stop.
+__device__ bool append_fill(const ElimArgs &a, bool act, int32_t lo, int32_t hi, double c)
+{
+    uint32_t idx = 0;
+    if (act) {
+        idx = atomicAdd(a.fcnt + lo, 1u);
+        if (idx < (uint32_t)FILL_C0) {
+            a.in_row[(size_t)lo * FILL_C0 + idx] = hi;
+            a.in_w[(size_t)lo * FILL_C0 + idx] = c;
+        } else {
+            const int j = fill_level(idx);
+            if (j > FILL_LEVELS) {
+                set_status(a.status, ST_POOL);        // column exceeds the directory's reach
+            } else if (idx == fill_level_start(j)) {  // this lane opens level j of column lo
+                const uint32_t capj = fill_level_cap(j);
+                const unsigned long long pbase = atomicAdd(a.pool_top, (unsigned long long)capj);
+                uint32_t *slot = a.dir + (size_t)lo * FILL_LEVELS + (j - 1);
+                if (pbase + capj > a.pool_cap) {
+                    set_status(a.status, ST_POOL);
+                    st_release_u32(slot, 0xffffffffu);
+                } else {
+                    st_release_u32(slot, (uint32_t)(pbase / FILL_GRANULE) + 1u);
+                }
+            }
+        }
+        red_add_relaxed(a.dp + hi, 1);
+    }
+    __syncwarp();
+    bool ok = true;
+    if (act && idx >= (uint32_t)FILL_C0) {
+        const int j = fill_level(idx);
+        const uint32_t gi = j > FILL_LEVELS ? 0u : wait_nonzero(a.dir + (size_t)lo * FILL_LEVELS + (j - 1), a);
+        if (gi == 0u || gi == 0xffffffffu) {
+            ok = false;
+        } else {
+            const unsigned long long at = (unsigned long long)(gi - 1u) * FILL_GRANULE + (idx - fill_level_start(j));
+            a.pool_row[at] = hi;
+            a.pool_w[at] = c;
+        }
+    }
+    return !__any_sync(FULL, !ok);
+}
+
+// Counter decrements of one group of up to 32 merged neighbours (lane holds
+// u, m when valid).  A positive-to-zero transition makes u ready: the first
+// such vertex is kept in `keep` when it is -1 (empty; -2 means never keep)
+// for this warp, the others are published on the queue.
+__device__ void decrement_group(const ElimArgs &a, int32_t pivot, bool valid, int32_t u, int32_t m, int32_t &keep)
+{
+    const unsigned lane = lane_id();
+    bool ready = false;
+    if (valid) {
+        const int32_t r = atomicSub(a.dp + u, m);
+        ready = (r == m);
+        if (ready && a.trace) { a.trace[4 * (size_t)u] = global_ns(); a.trace_parent[u] = pivot; }
+    }
+    unsigned bal = __ballot_sync(FULL, ready);
+    if (!bal) return;
+    if (keep == -1) {
+        const int kl = __ffs(bal) - 1;
+        keep = __shfl_sync(FULL, u, kl);
+        bal &= ~(1u << kl);
+        if ((int)lane == kl) ready = false;
+    }
+    if (!bal) return;
+    const int leader = __ffs(bal) - 1;
+    uint32_t qb = 0;
+    if ((int)lane == leader) qb = atomicAdd(a.q_tail, (uint32_t)__popc(bal));
+    qb = __shfl_sync(FULL, qb, leader);
+    if (ready) {
+        const uint32_t at = qb + __popc(bal & ((1u << lane) - 1u));
+        if (at < (uint32_t)a.nl) {
+            fence_acq_rel();
+            st_release(a.queue + at, u);
+        } else {
+            set_status(a.status, ST_INVAL);    // a vertex became ready twice: counters are corrupt
+        }
+    }
+}
+
+__device__ __forceinline__ void sys_of(const ElimArgs &a, int32_t k, uint64_t &klocal, uint64_t &sys)
+{
+    klocal = (uint64_t)k; sys = 0;
+    if (a.sys_of) {
+        const int32_t s = __ldg(a.sys_of + k);
+        sys = (uint64_t)s;
+        klocal = (uint64_t)(k - __ldg(a.sys_base + s));
+    }
+}
+
+// Pivot k whose working set fits in registers (g <= 32).  Returns the vertex
+// this warp keeps for itself (-1: none), or -2 if the kernel must stop.
+// FP64 is slow on this part, so only the canonical arithmetic runs in FP64
+// (run sums, suffix sums, the sampling product and the weight quotient); the
+// running maximum and the sampling search compare bit patterns, which order
+// non-negative doubles exactly as their values.
+__device__ int32_t eliminate_small(const ElimArgs &a, int32_t k, int64_t o0, int32_t norig, uint32_t cnt,
+                                   WarpState &ws)
+{
+    const unsigned lane = lane_id();
+    const int g = norig + (int)cnt;
+
+    // gather: lane i holds gathered entry i
+    int32_t row = ROW_SENTINEL;
+    double w = 0.0;
+    bool bad = false;
+    if ((int)lane < norig) {
+        row = __ldg(a.lrow + o0 + lane);
+        w = __ldg(a.lw + o0 + lane);
+    } else if ((int)lane < g) {
+        const uint32_t f = lane - (uint32_t)norig;       // fill index
+        if (f < (uint32_t)FILL_C0) {
+            row = __ldcg(a.in_row + (size_t)k * FILL_C0 + f);
+            w = __ldcg(a.in_w + (size_t)k * FILL_C0 + f);
+        } else {                                         // level 1 of the overflow directory
+            const uint32_t gidx = __ldcg(a.dir + (size_t)k * FILL_LEVELS);
+            if (gidx == 0u || gidx == 0xffffffffu) {
+                bad = true;
+            } else {
+                const unsigned long long pb = (unsigned long long)(gidx - 1u) * FILL_GRANULE + (f - FILL_C0);
+                row = __ldcg(a.pool_row + pb);
+                w = __ldcg(a.pool_w + pb);
+            }
+        }
+    }
+    // the uniform of slot p = lane depends only on (seed, k, p, sys): draw it
+    // while the gathered entries are in flight
+    uint64_t klocal, sys;
+    sys_of(a, k, klocal, sys);
+    const double vrand = (lane >= 1 && (int)lane < g) ? slot_uniform(a.seed, klocal, (uint64_t)lane, sys) : 1.0;
+    if (__any_sync(FULL, bad)) {            // never published: give up rather than read wild memory
+        if (lane == 0) set_status(a.status, ST_INVAL);
+        return -2;
+    }
+    prof_mark(a, ws, 1);
+
+    // sort by (row, weight bits), merge runs left to right
+    reg_sort_row_bits(row, w, next_pow2(g));
+    const int32_t prow = __shfl_up_sync(FULL, row, 1);
+    const bool head = ((int)lane < g) && (lane == 0 || prow != row);
+    const unsigned hb = __ballot_sync(FULL, head);
+    const unsigned rest = lane == 31 ? 0u : (hb >> (lane + 1));
+    const int len = head ? (rest ? __ffs(rest) : g - (int)lane) : 0;
+    const int maxlen = (int)__reduce_max_sync(FULL, (unsigned)len);
+    double sum = w;
+    for (int off = 1; off < maxlen; ++off) {
+        const double nv = __shfl_down_sync(FULL, w, off);
+        if (head && off < len) sum = __dadd_rn(sum, nv);
+    }
+    const int d = __popc(hb);
+    // lane r < d takes the r-th run head: the smallest lane i with r+1 heads in 0..i
+    int src = 0;
+    if ((int)lane < d) {
+        int blo = 0, bhi = 31;
+        while (blo < bhi) {
+            const int mid = (blo + bhi) >> 1;
+            if (__popc(hb & ((2u << mid) - 1u)) >= (int)lane + 1) bhi = mid; else blo = mid + 1;
+        }
+        src = blo;
+    }
+    int32_t mrow = __shfl_sync(FULL, row, src);
+    double mw = __shfl_sync(FULL, sum, src);
+    int32_t mm = __shfl_sync(FULL, len, src);
+    const bool valid = (int)lane < d;
+    prof_mark(a, ws, 2);
+
+    // store the row-ordered column
+    unsigned long long fpos = 0;
+    if (d > 0 && !reserve_factor(a, ws, d, fpos)) return -2;
+    if (valid) {
+        a.f_row[fpos + lane] = mrow;
+        a.f_val[fpos + lane] = mw;
+    }
+    if (lane == 0) { a.f_start[k] = (int64_t)fpos; a.f_len[k] = d; }
+    if (d == 0) {
+        if (lane == 0) a.D[k] = 0.0;
+        ++ws.n_reg;
+        return -1;
+    }
+    prof_mark(a, ws, 3);
+
+    // sort by (weight bits, row)
+    if (!valid) { mrow = ROW_SENTINEL; mw = __longlong_as_double((long long)WBITS_SENTINEL); mm = 0; }
+    reg_sort_bits_row(mrow, mw, mm, next_pow2(d));
+    prof_mark(a, ws, 6);
+
+    // canonical suffix sums: lane t holds S[d-1-t] (one tile).  Hillis-Steele
+    // offsets >= d add nothing to lanes below d, so they are skipped.
+    double x = __shfl_sync(FULL, mw, (int)lane < d ? d - 1 - (int)lane : 0);
+    if ((int)lane >= d) x = 0.0;
+    for (int off = 1; off < d; off <<= 1) {
+        const double y = __shfl_up_sync(FULL, x, off);
+        if ((int)lane >= off) x = __dadd_rn(x, y);
+    }
+    x = __dadd_rn(x, 0.0);                 // carry of the (empty) preceding tiles
+    unsigned long long mx = dbits(x);      // running maximum, as bit patterns
+    for (int off = 1; off < d; off <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL, mx, off);
+        if ((int)lane >= off && y > mx) mx = y;
+    }
+    const double Dk = __shfl_sync(FULL, x, d - 1);
+    if (lane == 0) a.D[k] = Dk;
+    prof_mark(a, ws, 7);
+
+    // sample the clique tree: lane p handles slot p (1 <= p <= d-1)
+    const int p = (int)lane;
+    const bool act = p >= 1 && p < d;
+    const double Sp = __shfl_sync(FULL, x, act ? d - 1 - p : 0);
+    const int32_t u = __shfl_sync(FULL, mrow, act ? p - 1 : 0);
+    const double wu = __shfl_sync(FULL, mw, act ? p - 1 : 0);
+    const unsigned long long Rb = act ? dbits(__dmul_rn(Sp, vrand)) : 0ull;
+    int lo_j = act ? p : 0, hi_j = act ? d - 1 : 0;        // largest j with M[j] >= R
+    const int steps = d > 1 ? 32 - __clz(d - 1) : 0;
+    for (int it = 0; it < steps; ++it) {
+        const int mid = lo_j + ((hi_j - lo_j + 1) >> 1);
+        const unsigned long long Mm = __shfl_sync(FULL, mx, (d - 1 - mid) & 31);
+        if (lo_j < hi_j) {
+            if (Mm >= Rb) lo_j = mid; else hi_j = mid - 1;
+        }
+    }
+    const int32_t xv = __shfl_sync(FULL, mrow, lo_j & 31);
+    double c = 0.0;
+    int32_t lo = 0, hi = 0;
+    if (act) {
+        c = __ddiv_rn(__dmul_rn(Sp, wu), Dk);
+        lo = u < xv ? u : xv;
+        hi = u < xv ? xv : u;
+    }
+    if (!append_fill(a, act, lo, hi, c)) return -2;
+    ws.n_fill += (unsigned long long)(d - 1);
+    prof_mark(a, ws, 4);
+
+    // dependency levels, release, decrements
+    const int32_t lk = __ldcg(a.lvl + k) + 1;
+    if (valid) red_max_relaxed(a.lvl + mrow, lk);
+    __syncwarp();
+    __threadfence();
+    int32_t keep = -1;
+    decrement_group(a, k, valid, mrow, mm, keep);
+    ++ws.n_reg;
+    prof_mark(a, ws, 5);
+    return keep;
+}
+
+// Pivot k with a larger working set (shared or global memory).
+__device__ int32_t eliminate_big(const ElimArgs &a, int32_t k, int64_t o0, int32_t norig, uint32_t cnt,
+                                 unsigned char *wbuf, unsigned char *bbuf, int *block_lock, WarpState &ws)
 {
     const unsigned lane = lane_id();
     const unsigned lt_mask = (1u << lane) - 1u;
-
-    // ---------------------------------------------------------------- gather sizes
-    const int64_t o0 = __ldg(a.lcp + k), o1 = __ldg(a.lcp + k + 1);
-    const int32_t norig = (int32_t)(o1 - o0);
-    const uint32_t cnt = __ldcg(a.fcnt + k);
     const int g = norig + (int)cnt;
     const int P = next_pow2(g);
 
@@ -165,7 +487,7 @@ __device__ bool eliminate(const ElimArgs &a, int32_t k, unsigned char *wbuf, uns
         got = __shfl_sync(FULL, got, 0);
         if (!got || read_status(a.status) != ST_OK) {
             if (got && lane == 0) atomicExch(block_lock, 0);
-            return false;
+            return -2;
         }
         block_held = true;
         v = make_view(bbuf, a.block_cap);
@@ -179,12 +501,18 @@ __device__ bool eliminate(const ElimArgs &a, int32_t k, unsigned char *wbuf, uns
                 if (base + need > a.scratch_cap) set_status(a.status, ST_POOL);
             }
             base = __shfl_sync(FULL, base, 0);
-            if (read_status(a.status) != ST_OK) return false;
+            if (read_status(a.status) != ST_OK) return -2;
             ws.sbase = base; ws.scap = need;
         }
         v = make_view(a.scratch + ws.sbase, P);
         path = 2;
     }
+    auto release_block = [&]() {
+        if (block_held) {
+            __syncwarp();
+            if (lane == 0) { __threadfence_block(); atomicExch(block_lock, 0); }
+        }
+    };
 
     // ---------------------------------------------------------------- gather
     for (int i = lane; i < norig; i += 32) {
@@ -206,8 +534,8 @@ __device__ bool eliminate(const ElimArgs &a, int32_t k, unsigned char *wbuf, uns
             const uint32_t gidx = __ldcg(a.dir + (size_t)k * FILL_LEVELS + (j - 1));
             if (gidx == 0u || gidx == 0xffffffffu) {   // never published: give up rather than read wild memory
                 set_status(a.status, ST_INVAL);
-                if (block_held && lane == 0) atomicExch(block_lock, 0);
-                return false;
+                release_block();
+                return -2;
             }
             const unsigned long long pb = (unsigned long long)(gidx - 1u) * FILL_GRANULE;
             for (uint32_t i = lane; i < len; i += 32) {
@@ -218,6 +546,7 @@ __device__ bool eliminate(const ElimArgs &a, int32_t k, unsigned char *wbuf, uns
     }
     for (int i = g + lane; i < P; i += 32) { v.row[i] = ROW_SENTINEL; v.w[i] = 0.0; }
     __syncwarp();
+    prof_mark(a, ws, 1);
 
     // ---------------------------------------------------------------- sort + merge (in place)
     sort_row_bits(v, P);
@@ -243,43 +572,28 @@ __device__ bool eliminate(const ElimArgs &a, int32_t k, unsigned char *wbuf, uns
         __syncwarp();
     }
 
+    prof_mark(a, ws, 2);
+
     // ---------------------------------------------------------------- store row-ordered column
     unsigned long long fpos = 0;
-    if (d > 0) {
-        if (ws.fcur + (unsigned long long)d > ws.fend) {
-            const unsigned long long sz = d > ws.fchunk ? (unsigned long long)d : (unsigned long long)ws.fchunk;
-            unsigned long long base = 0;
-            if (lane == 0) {
-                base = atomicAdd(a.f_top, sz);
-                if (base + sz > a.f_cap) set_status(a.status, ST_POOL);
-            }
-            base = __shfl_sync(FULL, base, 0);
-            if (read_status(a.status) != ST_OK) {
-                if (block_held && lane == 0) atomicExch(block_lock, 0);
-                return false;
-            }
-            ws.fcur = base; ws.fend = base + sz;
-        }
-        fpos = ws.fcur;
-        ws.fcur += (unsigned long long)d;
-        for (int i = lane; i < d; i += 32) {
-            a.f_row[fpos + i] = v.row[i];
-            a.f_val[fpos + i] = v.w[i];
-        }
+    if (d > 0 && !reserve_factor(a, ws, d, fpos)) { release_block(); return -2; }
+    for (int i = lane; i < d; i += 32) {
+        a.f_row[fpos + i] = v.row[i];
+        a.f_val[fpos + i] = v.w[i];
     }
     if (lane == 0) { a.f_start[k] = (int64_t)fpos; a.f_len[k] = d; }
     if (d == 0) {
         if (lane == 0) a.D[k] = 0.0;
-        if (block_held) { __syncwarp(); if (lane == 0) { __threadfence_block(); atomicExch(block_lock, 0); } }
+        release_block();
         if (path == 0) ++ws.n_warp; else if (path == 1) ++ws.n_block; else ++ws.n_global;
-        return true;
+        return -1;
     }
 
     // ---------------------------------------------------------------- weight sort
     const int P2 = next_pow2(d);
     for (int i = d + lane; i < P2; i += 32) {
         v.row[i] = ROW_SENTINEL;
-        v.w[i] = __longlong_as_double((long long)0xffffffffffffffffull);
+        v.w[i] = __longlong_as_double((long long)WBITS_SENTINEL);
         v.mult[i] = 0;
     }
     __syncwarp();
@@ -287,7 +601,8 @@ __device__ bool eliminate(const ElimArgs &a, int32_t k, unsigned char *wbuf, uns
 
     // ---------------------------------------------------------------- canonical suffix scan
     {
-        double carry = 0.0, mcarry = 0.0;
+        double carry = 0.0;
+        unsigned long long mcarry = 0ull;
         for (int base = 0; base < d; base += 32) {
             const int t = base + lane;
             double x = (t < d) ? v.w[d - 1 - t] : 0.0;
@@ -297,14 +612,14 @@ __device__ bool eliminate(const ElimArgs &a, int32_t k, unsigned char *wbuf, uns
                 if ((int)lane >= off) x = __dadd_rn(x, y);
             }
             x = __dadd_rn(x, carry);
-            double m = x;
+            unsigned long long m = dbits(x);      // running maximum, as bit patterns
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
-                const double y = __shfl_up_sync(FULL, m, off);
-                if ((int)lane >= off) m = fmax(m, y);
+                const unsigned long long y = __shfl_up_sync(FULL, m, off);
+                if ((int)lane >= off && y > m) m = y;
             }
-            m = fmax(m, mcarry);
-            if (t < d) { v.S[d - 1 - t] = x; v.M[d - 1 - t] = m; }
+            if (mcarry > m) m = mcarry;
+            if (t < d) { v.S[d - 1 - t] = x; v.M[d - 1 - t] = __longlong_as_double((long long)m); }
             carry = __shfl_sync(FULL, x, 31);
             mcarry = __shfl_sync(FULL, m, 31);
         }
@@ -312,121 +627,390 @@ __device__ bool eliminate(const ElimArgs &a, int32_t k, unsigned char *wbuf, uns
     __syncwarp();
     const double Dk = v.S[0];
     if (lane == 0) a.D[k] = Dk;
+    prof_mark(a, ws, 3);
 
     // ---------------------------------------------------------------- sample clique tree + append
-    uint64_t klocal = (uint64_t)k, sys = 0;
-    if (a.sys_of) {
-        const int32_t s = __ldg(a.sys_of + k);
-        sys = (uint64_t)s;
-        klocal = (uint64_t)(k - __ldg(a.sys_base + s));
-    }
-    bool ok = true;
+    uint64_t klocal, sys;
+    sys_of(a, k, klocal, sys);
     for (int pb = 1; pb < d; pb += 32) {
         const int p = pb + lane;
         const bool act = p < d;
         int32_t lo = 0, hi = 0;
         double c = 0.0;
-        uint32_t idx = 0;
         if (act) {
             const int32_t u = v.row[p - 1];
             const double wu = v.w[p - 1];
             const double Sp = v.S[p];
             const double R = __dmul_rn(Sp, slot_uniform(a.seed, klocal, (uint64_t)p, sys));
+            const unsigned long long Rb = dbits(R);
             int lo_j = p, hi_j = d - 1;            // largest j with M[j] >= R; M[p] >= R
             while (lo_j < hi_j) {
                 const int mid = lo_j + ((hi_j - lo_j + 1) >> 1);
-                if (v.M[mid] >= R) lo_j = mid; else hi_j = mid - 1;
+                if (dbits(v.M[mid]) >= Rb) lo_j = mid; else hi_j = mid - 1;
             }
             const int32_t x = v.row[lo_j];
             c = __ddiv_rn(__dmul_rn(Sp, wu), Dk);
             lo = u < x ? u : x;
             hi = u < x ? x : u;
-            idx = atomicAdd(a.fcnt + lo, 1u);
-            if (idx < (uint32_t)FILL_C0) {
-                a.in_row[(size_t)lo * FILL_C0 + idx] = hi;
-                a.in_w[(size_t)lo * FILL_C0 + idx] = c;
-            } else {
-                const int j = fill_level(idx);
-                if (j > FILL_LEVELS) {
-                    set_status(a.status, ST_POOL);      // column exceeds the directory's reach
-                } else if (idx == fill_level_start(j)) {  // this lane opens level j of column lo
-                    const uint32_t capj = fill_level_cap(j);
-                    const unsigned long long pbase = atomicAdd(a.pool_top, (unsigned long long)capj);
-                    uint32_t *slot = a.dir + (size_t)lo * FILL_LEVELS + (j - 1);
-                    if (pbase + capj > a.pool_cap) {
-                        set_status(a.status, ST_POOL);
-                        st_release_u32(slot, 0xffffffffu);
-                    } else {
-                        st_release_u32(slot, (uint32_t)(pbase / FILL_GRANULE) + 1u);
-                    }
-                }
-            }
-            red_add_relaxed(a.dp + hi, 1);
         }
-        __syncwarp();
-        if (act && idx >= (uint32_t)FILL_C0) {
-            const int j = fill_level(idx);
-            const uint32_t gi = j > FILL_LEVELS ? 0u : wait_nonzero(a.dir + (size_t)lo * FILL_LEVELS + (j - 1), a);
-            if (gi == 0u || gi == 0xffffffffu) {
-                ok = false;
-            } else {
-                const unsigned long long at = (unsigned long long)(gi - 1u) * FILL_GRANULE + (idx - fill_level_start(j));
-                a.pool_row[at] = hi;
-                a.pool_w[at] = c;
-            }
-        }
-        if (__any_sync(FULL, !ok)) {
-            if (block_held && lane == 0) atomicExch(block_lock, 0);
-            return false;
-        }
+        if (!append_fill(a, act, lo, hi, c)) { release_block(); return -2; }
     }
     ws.n_fill += (unsigned long long)(d - 1);
+    prof_mark(a, ws, 4);
 
-    // ---------------------------------------------------------------- release, then decrements
-    __threadfence();
+    // ---------------------------------------------------------------- levels, release, decrements
+    {
+        const int32_t lk = __ldcg(a.lvl + k) + 1;
+        for (int i = lane; i < d; i += 32) red_max_relaxed(a.lvl + v.row[i], lk);
+    }
     __syncwarp();
     __threadfence();
+    int32_t keep = -1;
     for (int ib = 0; ib < d; ib += 32) {
         const int i = ib + lane;
-        bool ready = false;
-        int32_t u = 0;
-        if (i < d) {
-            u = v.row[i];
-            const int32_t m = v.mult[i];
-            const int32_t r = atomicSub(a.dp + u, m);
-            ready = (r == m);
+        const bool valid = i < d;
+        decrement_group(a, k, valid, valid ? v.row[i] : 0, valid ? v.mult[i] : 0, keep);
+    }
+    release_block();
+    if (path == 0) ++ws.n_warp; else if (path == 1) ++ws.n_block; else ++ws.n_global;
+    prof_mark(a, ws, 5);
+    return keep;
+}
+
+// ---------------------------------------------------------------- CTA-cooperative path
+// A vertex whose working set exceeds a warp's shared buffer is eliminated by
+// all warps of its CTA together: the warp that popped it posts a request,
+// every other warp of the CTA joins at its next poll point, and the block runs
+// the same steps with block-wide networks.  One request at a time per CTA;
+// all barriers are bounded software barriers over the CTA's warps.
+struct CoopShared {
+    int k;                       // vertex being eliminated cooperatively (-1: none)
+    int gen;                     // bumped for every request
+    int req_warp;                // warp that posted the request
+    int arrive;                  // barrier arrivals (monotonic)
+    int d, ntile, abort;
+    int hcount[32];              // per-warp head counts of the merge
+    unsigned long long fpos;
+    unsigned long long sbase, scap;   // CTA scratch (global), reused across requests
+    long long spin_limit;
+};
+
+__device__ __forceinline__ volatile int &vol(int &x) { return *(volatile int *)&x; }
+
+// Bounded barrier over the CTA's warps; false if it gave up (status set).
+__device__ bool cta_barrier(CoopShared &cs, const ElimArgs &a)
+{
+    const int nw = blockDim.x >> 5;
+    __syncwarp();
+    int ok = 1;
+    if (lane_id() == 0) {
+        __threadfence_block();
+        const int old = atomicAdd(&cs.arrive, 1);
+        const int target = (old / nw + 1) * nw;
+        long long spins = 0;
+        while (vol(cs.arrive) < target) {
+            if (read_status(a.status) != ST_OK) { ok = 0; break; }
+            if (++spins > a.spin_limit) { set_status(a.status, ST_TIMEOUT); ok = 0; break; }
+            if (spins > 64) __nanosleep(32);
         }
-        const unsigned bal = __ballot_sync(FULL, ready);
-        if (bal) {
-            const int leader = __ffs(bal) - 1;
-            uint32_t qb = 0;
-            if ((int)lane == leader) qb = atomicAdd(a.q_tail, (uint32_t)__popc(bal));
-            qb = __shfl_sync(FULL, qb, leader);
-            if (ready) {
-                const uint32_t at = qb + __popc(bal & lt_mask);
-                if (at < (uint32_t)a.nl) {
-                    fence_acq_rel();
-                    st_release(a.queue + at, u);
-                } else {
-                    set_status(a.status, ST_INVAL);    // a vertex became ready twice: counters are corrupt
+        __threadfence_block();
+    }
+    return __shfl_sync(FULL, ok, 0) != 0;
+}
+
+__device__ void coop_sort_row_bits(View v, int P)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int kk = 2; kk <= P; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int t = tid; t < (P >> 1); t += nt) {
+                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+                const int l = i + j;
+                const bool asc = (i & kk) == 0;
+                const int32_t ri = v.row[i], rl = v.row[l];
+                const double wi = v.w[i], wl = v.w[l];
+                const bool gt = (ri > rl) || (ri == rl && dbits(wi) > dbits(wl));
+                if (gt == asc) { v.row[i] = rl; v.row[l] = ri; v.w[i] = wl; v.w[l] = wi; }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ void coop_sort_bits_row(View v, int P)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int kk = 2; kk <= P; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int t = tid; t < (P >> 1); t += nt) {
+                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+                const int l = i + j;
+                const bool asc = (i & kk) == 0;
+                const double wi = v.w[i], wl = v.w[l];
+                const int32_t ri = v.row[i], rl = v.row[l];
+                const unsigned long long bi = dbits(wi), bl = dbits(wl);
+                const bool gt = (bi > bl) || (bi == bl && ri > rl);
+                if (gt == asc) {
+                    const int32_t mi = v.mult[i], ml = v.mult[l];
+                    v.row[i] = rl; v.row[l] = ri; v.w[i] = wl; v.w[l] = wi; v.mult[i] = ml; v.mult[l] = mi;
                 }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Cooperative elimination of cs.k by every warp of the CTA (the callers have
+// all reached this function).  __syncthreads() is used only after the bounded
+// join barrier has seen every warp arrive.  Returns, for the requesting warp,
+// the vertex it keeps (-1: none); -2 if the kernel must stop.
+__device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs, unsigned char *bbuf,
+                                               WarpState &ws)
+{
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    if (!cta_barrier(cs, a)) return -2;                  // join: every warp is here
+    __syncthreads();
+    const int32_t k = cs.k;
+    const bool requester = warp == cs.req_warp;
+    const int64_t o0 = __ldg(a.lcp + k), o1 = __ldg(a.lcp + k + 1);
+    const int32_t norig = (int32_t)(o1 - o0);
+    const uint32_t cnt = __ldcg(a.fcnt + k);
+    const int g = norig + (int)cnt;
+    const int P = next_pow2(g);
+
+    // ---------------------------------------------------------------- working set
+    View v;
+    double *tiles;
+    if (P <= a.block_cap) {
+        v = make_view(bbuf, a.block_cap);
+        tiles = (double *)(bbuf + (size_t)a.block_cap * ENTRY_BYTES);
+    } else {
+        const unsigned long long need = (unsigned long long)P * ENTRY_BYTES + ((unsigned long long)P / 32 + 1) * 8;
+        if (tid == 0 && cs.scap < need) {
+            const unsigned long long base = atomicAdd(a.scratch_top, (need + 255ull) & ~255ull);
+            if (base + need > a.scratch_cap) set_status(a.status, ST_POOL);
+            cs.sbase = base; cs.scap = need;
+        }
+        __syncthreads();
+        if (read_status(a.status) != ST_OK) { __syncthreads(); if (tid == 0) cs.k = -1; return -2; }
+        v = make_view(a.scratch + cs.sbase, P);
+        tiles = (double *)(a.scratch + cs.sbase + (size_t)P * ENTRY_BYTES);
+    }
+
+    // ---------------------------------------------------------------- gather
+    for (int i = tid; i < norig; i += nt) { v.row[i] = __ldg(a.lrow + o0 + i); v.w[i] = __ldg(a.lw + o0 + i); }
+    {
+        const int ninl = cnt < (uint32_t)FILL_C0 ? (int)cnt : FILL_C0;
+        for (int i = tid; i < ninl; i += nt) {
+            v.row[norig + i] = __ldcg(a.in_row + (size_t)k * FILL_C0 + i);
+            v.w[norig + i] = __ldcg(a.in_w + (size_t)k * FILL_C0 + i);
+        }
+        for (int j = 1; j <= FILL_LEVELS; ++j) {
+            const uint32_t start = fill_level_start(j);
+            if (cnt <= start) break;
+            const uint32_t capj = fill_level_cap(j);
+            const uint32_t len = (cnt - start) < capj ? (cnt - start) : capj;
+            const uint32_t gidx = __ldcg(a.dir + (size_t)k * FILL_LEVELS + (j - 1));
+            if (gidx == 0u || gidx == 0xffffffffu) {          // never published
+                if (tid == 0) set_status(a.status, ST_INVAL);
+                break;
+            }
+            const unsigned long long pb = (unsigned long long)(gidx - 1u) * FILL_GRANULE;
+            for (uint32_t i = tid; i < len; i += nt) {
+                v.row[norig + start + i] = __ldcg(a.pool_row + pb + i);
+                v.w[norig + start + i] = __ldcg(a.pool_w + pb + i);
             }
         }
     }
-    __syncwarp();
-    if (block_held && lane == 0) { __threadfence_block(); atomicExch(block_lock, 0); }
-    if (path == 0) ++ws.n_warp; else if (path == 1) ++ws.n_block; else ++ws.n_global;
-    return true;
+    for (int i = g + tid; i < P; i += nt) { v.row[i] = ROW_SENTINEL; v.w[i] = 0.0; }
+    __syncthreads();
+    if (read_status(a.status) != ST_OK) { __syncthreads(); if (tid == 0) cs.k = -1; return -2; }
+
+    // ---------------------------------------------------------------- sort + merge (in place)
+    coop_sort_row_bits(v, P);
+    int d = 0;
+    for (int base = 0; base < g; base += nt) {
+        const int i = base + tid;
+        bool head = false;
+        int32_t r = 0, len = 0;
+        double sum = 0.0;
+        if (i < g) {
+            r = v.row[i];
+            head = (i == 0) || (v.row[i - 1] != r);
+            if (head) {
+                sum = v.w[i]; len = 1;
+                while (i + len < g && v.row[i + len] == r) { sum = __dadd_rn(sum, v.w[i + len]); ++len; }
+            }
+        }
+        const unsigned bal = __ballot_sync(FULL, head);
+        if (lane == 0) cs.hcount[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w2 = 0; w2 < nw; ++w2) { const int c = cs.hcount[w2]; if (w2 < warp) before += c; total += c; }
+        const int rank = d + before + __popc(bal & ((1u << lane) - 1u));
+        __syncthreads();                                   // every read of this chunk is done
+        if (head) { v.row[rank] = r; v.w[rank] = sum; v.mult[rank] = len; }
+        d += total;
+        __syncthreads();
+    }
+
+    // ---------------------------------------------------------------- store row-ordered column
+    if (tid == 0) {
+        const unsigned long long base = d > 0 ? atomicAdd(a.f_top, (unsigned long long)d) : 0ull;
+        if (d > 0 && base + d > a.f_cap) set_status(a.status, ST_POOL);
+        cs.fpos = base;
+    }
+    __syncthreads();
+    if (read_status(a.status) != ST_OK) { __syncthreads(); if (tid == 0) cs.k = -1; return -2; }
+    const unsigned long long fpos = cs.fpos;
+    for (int i = tid; i < d; i += nt) { a.f_row[fpos + i] = v.row[i]; a.f_val[fpos + i] = v.w[i]; }
+    if (tid == 0) { a.f_start[k] = (int64_t)fpos; a.f_len[k] = d; }
+    if (d == 0) {
+        if (tid == 0) a.D[k] = 0.0;
+        __syncthreads();
+        if (tid == 0) cs.k = -1;
+        return -1;
+    }
+
+    // ---------------------------------------------------------------- weight sort
+    const int P2 = next_pow2(d);
+    for (int i = d + tid; i < P2; i += nt) {
+        v.row[i] = ROW_SENTINEL; v.w[i] = __longlong_as_double((long long)WBITS_SENTINEL); v.mult[i] = 0;
+    }
+    __syncthreads();
+    coop_sort_bits_row(v, P2);
+
+    // ---------------------------------------------------------------- canonical suffix scan
+    // each 32-lane tile of the reversed weights: Hillis-Steele within the tile
+    // (all warps in parallel), then the serial carry chain over tiles, then
+    // every lane adds its tile's carry -- the pairings of the canonical scan
+    const int ntile = (d + 31) / 32;
+    for (int j = warp; j < ntile; j += nw) {
+        const int t = 32 * j + lane;
+        double x = (t < d) ? v.w[d - 1 - t] : 0.0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const double y = __shfl_up_sync(FULL, x, off);
+            if (lane >= off) x = __dadd_rn(x, y);
+        }
+        if (t < d) v.S[d - 1 - t] = x;
+        if (lane == 31) tiles[j] = x;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double carry = 0.0;
+        for (int j = 0; j < ntile; ++j) {
+            const double tot = tiles[j];
+            tiles[j] = carry;
+            carry = __dadd_rn(tot, carry);
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < d; t += nt) v.S[d - 1 - t] = __dadd_rn(v.S[d - 1 - t], tiles[t >> 5]);
+    __syncthreads();
+    // running maximum from the right, on bit patterns (exact in any order)
+    for (int j = warp; j < ntile; j += nw) {
+        const int t = 32 * j + lane;
+        unsigned long long m = t < d ? dbits(v.S[d - 1 - t]) : 0ull;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long y = __shfl_up_sync(FULL, m, off);
+            if (lane >= off && y > m) m = y;
+        }
+        if (t < d) v.M[d - 1 - t] = __longlong_as_double((long long)m);
+        if (lane == 31) tiles[j] = __longlong_as_double((long long)m);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long run = 0ull;
+        for (int j = 0; j < ntile; ++j) {
+            const unsigned long long tm = dbits(tiles[j]);
+            tiles[j] = __longlong_as_double((long long)run);
+            if (tm > run) run = tm;
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < d; t += nt) {
+        const unsigned long long c = dbits(tiles[t >> 5]), m = dbits(v.M[d - 1 - t]);
+        if (c > m) v.M[d - 1 - t] = __longlong_as_double((long long)c);
+    }
+    __syncthreads();
+    const double Dk = v.S[0];
+    if (tid == 0) a.D[k] = Dk;
+
+    // ---------------------------------------------------------------- sample clique tree + append
+    uint64_t klocal, sys;
+    sys_of(a, k, klocal, sys);
+    bool ok = true;
+    for (int pb = 1; pb < d; pb += nt) {
+        const int p = pb + tid;
+        const bool act = p < d;
+        int32_t lo = 0, hi = 0;
+        double c = 0.0;
+        if (act) {
+            const int32_t u = v.row[p - 1];
+            const double wu = v.w[p - 1];
+            const double Sp = v.S[p];
+            const unsigned long long Rb = dbits(__dmul_rn(Sp, slot_uniform(a.seed, klocal, (uint64_t)p, sys)));
+            int lo_j = p, hi_j = d - 1;
+            while (lo_j < hi_j) {
+                const int mid = lo_j + ((hi_j - lo_j + 1) >> 1);
+                if (dbits(v.M[mid]) >= Rb) lo_j = mid; else hi_j = mid - 1;
+            }
+            const int32_t x = v.row[lo_j];
+            c = __ddiv_rn(__dmul_rn(Sp, wu), Dk);
+            lo = u < x ? u : x;
+            hi = u < x ? x : u;
+        }
+        if (!append_fill(a, act, lo, hi, c)) { ok = false; break; }
+    }
+    if (tid == 0) ws.n_fill += (unsigned long long)(d - 1);
+
+    // ---------------------------------------------------------------- levels, release, decrements
+    {
+        const int32_t lk = __ldcg(a.lvl + k) + 1;
+        for (int i = tid; i < d; i += nt) red_max_relaxed(a.lvl + v.row[i], lk);
+    }
+    __threadfence();
+    if (!cta_barrier(cs, a)) ok = false;                  // every append is done and fenced
+    if (__syncthreads_or(!ok)) { __syncthreads(); if (tid == 0) cs.k = -1; return -2; }
+    __threadfence();
+    int32_t keep = requester ? -1 : -2;
+    for (int ib = 0; ib < d; ib += nt) {
+        const int i = ib + tid;
+        const bool valid = i < d;
+        decrement_group(a, k, valid, valid ? v.row[i] : 0, valid ? v.mult[i] : 0, keep);
+    }
+    __syncthreads();
+    if (tid == 0) cs.k = -1;
+    return requester ? (keep >= 0 ? keep : -1) : -1;
 }
 
-__global__ void __launch_bounds__(512) elim_kernel(ElimArgs a, int fchunk)
+// Join a pending cooperative request of this CTA, if there is one this warp
+// has not served yet.  Returns -3 if there was none, else coop_eliminate's
+// result for a helper (-1, or -2 on abort).
+__device__ __forceinline__ int32_t serve_help(const ElimArgs &a, CoopShared &cs, int &seen_gen, unsigned char *bbuf,
+                                              WarpState &ws)
+{
+    const int g = vol(cs.gen);
+    if (g == seen_gen) return -3;
+    seen_gen = g;
+    ++ws.n_block;
+    return coop_eliminate(a, cs, bbuf, ws);
+}
+
+__global__ void __launch_bounds__(256, 2) elim_kernel(ElimArgs a, int fchunk)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int block_lock;
+    __shared__ CoopShared cs;
     const int warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const unsigned lane = lane_id();
-    if (threadIdx.x == 0) block_lock = 0;
+    if (threadIdx.x == 0) {
+        block_lock = 0;
+        cs.k = -1; cs.gen = 0; cs.req_warp = -1; cs.arrive = 0; cs.sbase = 0; cs.scap = 0;
+    }
     __syncthreads();
 
     unsigned char *wbuf = smem + (size_t)warp * a.warp_cap * ENTRY_BYTES;
@@ -434,44 +1018,143 @@ __global__ void __launch_bounds__(512) elim_kernel(ElimArgs a, int fchunk)
 
     WarpState ws;
     ws.fcur = ws.fend = 0; ws.sbase = 0; ws.scap = 0;
-    ws.n_warp = ws.n_block = ws.n_global = ws.n_fill = 0;
+    ws.n_reg = ws.n_warp = ws.n_block = ws.n_global = ws.n_fill = ws.n_handoff = 0;
+    for (int i = 0; i < 8; ++i) ws.cyc[i] = 0;
+    ws.t_mark = 0;
     ws.fchunk = fchunk;
+    prof_mark(a, ws, -1);
     unsigned long long spins_total = 0;
+    int seen_gen = 0;
 
     const uint32_t nl = (uint32_t)a.nl;
-    bool run = true;
-    while (run) {
-        uint32_t s = 0;
-        if (lane == 0) s = atomicAdd(a.q_head, (uint32_t)a.queue_chunk);
-        s = __shfl_sync(FULL, s, 0);
-        if (s >= nl) break;
-        const uint32_t e = (s + (uint32_t)a.queue_chunk) < nl ? s + (uint32_t)a.queue_chunk : nl;
-        for (uint32_t slot = s; slot < e; ++slot) {
-            int32_t k;
-            long long spins = 0;
-            uint32_t seen_tail = 0;
-            // The watchdog counts polls without global progress: the count
-            // restarts whenever the queue tail has moved since the last look.
-            while ((k = ld_acquire(a.queue + slot)) < 0) {
-                if (read_status(a.status) != ST_OK) { run = false; break; }
-                if ((++spins & 255) == 0) {
-                    const uint32_t t = *(volatile const uint32_t *)a.q_tail;
-                    if (t != seen_tail) { seen_tail = t; spins_total += (unsigned long long)spins; spins = 0; }
+    uint32_t slot = 0, slot_end = 0;       // claimed, not yet consumed queue slots
+    bool claims_done = false;              // every queue slot has been claimed
+    int32_t next = -1;                     // vertex handed to this warp by its last pivot
+    for (;;) {
+        if (a.coop) {
+            const int32_t h = serve_help(a, cs, seen_gen, bbuf, ws);
+            if (h == -2) break;
+        }
+        int32_t k;
+        if (next >= 0) {
+            k = next;
+            next = -1;
+            ++ws.n_handoff;
+            fence_acq_rel();               // acquire: the counter transition precedes the column reads
+        } else {
+            if (slot == slot_end && !claims_done) {
+                uint32_t s = 0;
+                if (lane == 0) s = atomicAdd(a.q_head, (uint32_t)a.queue_chunk);
+                s = __shfl_sync(FULL, s, 0);
+                if (s >= nl) claims_done = true;
+                else {
+                    slot = s;
+                    slot_end = (s + (uint32_t)a.queue_chunk) < nl ? s + (uint32_t)a.queue_chunk : nl;
                 }
-                if (spins > a.spin_limit) { set_status(a.status, ST_TIMEOUT); run = false; break; }
-                __nanosleep(100);
+            }
+            long long spins = 0;
+            uint32_t seen_tail = 0, seen_done = 0;
+            bool stop = false;
+            // Wait for the claimed slot (or, once every slot is claimed, for
+            // the end), serving cooperative requests of this CTA meanwhile.
+            // The watchdog counts polls without global progress.  Slots past
+            // the last publication stay empty (vertices handed over directly
+            // never enter the queue): the wait ends when every vertex has
+            // been eliminated.
+            k = -1;
+            for (;;) {
+                if (!claims_done) {
+                    k = *(volatile const int32_t *)(a.queue + slot);
+                    if (__shfl_sync(FULL, k, 0) >= 0) { k = __shfl_sync(FULL, k, 0); break; }
+                }
+                if (read_status(a.status) != ST_OK) { stop = true; break; }
+                if (a.coop) {
+                    const int32_t h = serve_help(a, cs, seen_gen, bbuf, ws);
+                    if (h == -2) { stop = true; break; }
+                    if (h != -3) spins = 0;
+                }
+                if ((++spins & 63) == 0) {
+                    const uint32_t t = *(volatile const uint32_t *)a.q_tail;
+                    const uint32_t dn = *(volatile const uint32_t *)a.done;
+                    if (dn >= nl) { stop = true; break; }
+                    if (t != seen_tail || dn != seen_done) {
+                        seen_tail = t; seen_done = dn; spins_total += (unsigned long long)spins; spins = 0;
+                    }
+                }
+                if (spins > a.spin_limit) { set_status(a.status, ST_TIMEOUT); stop = true; break; }
+                // idle workers back off so that their polls do not crowd the
+                // memory pipeline of the warps doing eliminations
+                if (spins > 4) __nanosleep(spins < 64 ? 64u : (unsigned)a.idle_ns);
             }
             spins_total += (unsigned long long)spins;
-            if (__any_sync(FULL, !run)) { run = false; break; }
-            if (!eliminate(a, k, wbuf, bbuf, &block_lock, ws)) { run = false; break; }
+            if (__any_sync(FULL, stop)) break;
+            fence_acq_rel();               // acquire once the slot is seen (the polls are relaxed)
+            ++slot;
+        }
+        prof_mark(a, ws, 0);
+        const long long t_start = a.trace ? global_ns() : 0;
+        const int64_t o0 = __ldg(a.lcp + k), o1 = __ldg(a.lcp + k + 1);
+        const int32_t norig = (int32_t)(o1 - o0);
+        const uint32_t cnt = __ldcg(a.fcnt + k);
+        const int g = norig + (int)cnt;
+        int32_t r;
+        if (g <= 32) {
+            r = eliminate_small(a, k, o0, norig, cnt, ws);
+        } else if (!a.coop || next_pow2(g) <= a.warp_cap) {
+            r = eliminate_big(a, k, o0, norig, cnt, wbuf, bbuf, &block_lock, ws);
+        } else {
+            // post the request (or help the one already posted, then retry)
+            r = -3;
+            while (r == -3) {
+                int posted = 0;
+                if (lane == 0 && atomicCAS(&cs.k, -1, k) == -1) {
+                    cs.req_warp = warp;
+                    __threadfence_block();
+                    posted = atomicAdd(&cs.gen, 1) + 1;
+                }
+                posted = __shfl_sync(FULL, posted, 0);
+                if (posted) {
+                    seen_gen = posted;
+                    r = coop_eliminate(a, cs, bbuf, ws);
+                    ++ws.n_global;
+                } else {
+                    const int32_t h = serve_help(a, cs, seen_gen, bbuf, ws);
+                    if (h == -2) { r = -2; break; }
+                    if (h == -3) __nanosleep(32);
+                }
+            }
+        }
+        if (r == -2) break;
+        if (a.trace && lane == 0) {
+            a.trace[4 * (size_t)k + 1] = t_start;
+            a.trace[4 * (size_t)k + 2] = global_ns();
+            a.trace[4 * (size_t)k + 3] = ((long long)g << 32) | (unsigned)a.f_len[k];
+        }
+        if (lane == 0) atomicAdd(a.done, 1u);
+        // keep the handed-over vertex only while no claimed slot is pending
+        if (r >= 0) {
+            if (slot == slot_end) {
+                next = r;
+            } else {
+                uint32_t qb = 0;
+                if (lane == 0) {
+                    qb = atomicAdd(a.q_tail, 1u);
+                    if (qb < nl) { fence_acq_rel(); st_release(a.queue + qb, r); }
+                    else set_status(a.status, ST_INVAL);
+                }
+                __syncwarp();
+            }
         }
     }
     if (lane == 0 && a.stats) {
-        atomicAdd(a.stats + 0, ws.n_warp);
+        atomicAdd(a.stats + 0, ws.n_warp + ws.n_reg);
         atomicAdd(a.stats + 1, ws.n_block);
         atomicAdd(a.stats + 2, ws.n_global);
         atomicAdd(a.stats + 3, ws.n_fill);
         atomicAdd(a.stats + 4, spins_total);
+        atomicAdd(a.stats + 5, ws.n_reg);
+        atomicAdd(a.stats + 6, ws.n_handoff);
+        for (int i = 0; i < 8; ++i) atomicAdd(a.stats + 8 + i, ws.cyc[i]);
     }
 }
 
@@ -479,7 +1162,8 @@ __global__ void __launch_bounds__(512) elim_kernel(ElimArgs a, int fchunk)
 
 size_t elim_smem_bytes(int warps_per_block, int warp_cap, int block_cap)
 {
-    return (size_t)(warps_per_block * warp_cap + block_cap) * ENTRY_BYTES;
+    // per-warp buffers, then the CTA buffer and its scan-tile array
+    return (size_t)(warps_per_block * warp_cap + block_cap) * ENTRY_BYTES + ((size_t)block_cap / 32 + 1) * 8;
 }
 
 cudaError_t elim_configure(int warps_per_block, int warp_cap, int block_cap, int *blocks_per_sm)
@@ -494,6 +1178,7 @@ cudaError_t elim_launch(const ElimArgs &a, int blocks, int warps_per_block, int 
 {
     const size_t smem = elim_smem_bytes(warps_per_block, a.warp_cap, a.block_cap);
     elim_kernel<<<blocks, warps_per_block * 32, smem, st>>>(a, fchunk);
+    count_launches(1);
     return cudaGetLastError();
 }
 

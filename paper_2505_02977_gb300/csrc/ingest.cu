@@ -261,13 +261,13 @@ cudaError_t scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, void *tm
     int64_t *ts = (int64_t *)tmp;
     int64_t *total = ts + tiles + 1;
     if (tiles > 0) {
-        k_scan_reduce<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(in, n, ts);
-        k_scan_top<<<1, 1024, 0, st>>>(ts, tiles, total);
-        k_scan_down<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(in, n, ts, out);
+        k_scan_reduce<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(in, n, ts); count_launches(1);
+        k_scan_top<<<1, 1024, 0, st>>>(ts, tiles, total); count_launches(1);
+        k_scan_down<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(in, n, ts, out); count_launches(1);
     } else {
         cudaMemsetAsync(total, 0, sizeof(int64_t), st);
     }
-    k_set_total<<<1, 1, 0, st>>>(out, n, total);
+    k_set_total<<<1, 1, 0, st>>>(out, n, total); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -275,63 +275,63 @@ cudaError_t launch_iperm(int64_t n, const int32_t *ord, const int32_t *label_of_
                          int32_t *status, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    k_iperm<<<grid_for(n, 256), 256, 0, st>>>(n, ord, label_of_k, iperm, status);
+    k_iperm<<<grid_for(n, 256), 256, 0, st>>>(n, ord, label_of_k, iperm, status); count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_identity_iperm(int64_t n, int32_t *iperm, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    k_identity<<<grid_for(n, 256), 256, 0, st>>>(n, iperm);
+    k_identity<<<grid_for(n, 256), 256, 0, st>>>(n, iperm); count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ingest_count(const IngestArgs &a, cudaStream_t st)
 {
     if (a.n == 0) return cudaSuccess;
-    k_ingest_count<<<grid_for(a.n, 128), 128, 0, st>>>(a);
+    k_ingest_count<<<grid_for(a.n, 128), 128, 0, st>>>(a); count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ingest_scatter(const IngestArgs &a, const int64_t *lcp, int32_t *lrow, double *lw, cudaStream_t st)
 {
     if (a.n == 0) return cudaSuccess;
-    k_ingest_scatter<<<grid_for(a.n * 32, 256), 256, 0, st>>>(a, lcp, lrow, lw);
+    k_ingest_scatter<<<grid_for(a.n * 32, 256), 256, 0, st>>>(a, lcp, lrow, lw); count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_queue_init(int32_t nl, const int32_t *dp, int32_t *queue, uint32_t *q_tail, cudaStream_t st)
 {
     if (nl == 0) return cudaSuccess;
-    k_queue_init<<<grid_for(nl, 256), 256, 0, st>>>(nl, dp, queue, q_tail);
+    k_queue_init<<<grid_for(nl, 256), 256, 0, st>>>(nl, dp, queue, q_tail); count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_add_offset_i32(const int32_t *in, int32_t *out, int64_t n, int32_t off, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    k_add_off_i32<<<grid_for(n, 256), 256, 0, st>>>(in, out, n, off);
+    k_add_off_i32<<<grid_for(n, 256), 256, 0, st>>>(in, out, n, off); count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_add_offset_i64(const int64_t *in, int64_t *out, int64_t n, int64_t off, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    k_add_off_i64<<<grid_for(n, 256), 256, 0, st>>>(in, out, n, off);
+    k_add_off_i64<<<grid_for(n, 256), 256, 0, st>>>(in, out, n, off); count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    k_fill_i32<<<grid_for(n, 256), 256, 0, st>>>(p, n, v);
+    k_fill_i32<<<grid_for(n, 256), 256, 0, st>>>(p, n, v); count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_iota_i32(int32_t *p, int64_t n, int32_t base, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    k_iota_i32<<<grid_for(n, 256), 256, 0, st>>>(p, n, base);
+    k_iota_i32<<<grid_for(n, 256), 256, 0, st>>>(p, n, base); count_launches(1);
     return cudaGetLastError();
 }
 

@@ -9,6 +9,10 @@ namespace parac {
 
 struct ElimArgs;
 
+// Process-wide count of kernels launched by the library (diagnostics).
+void count_launches(unsigned n);
+unsigned long long launch_count();
+
 // ---------------------------------------------------------------- scan.cu
 // out[0] = 0, out[i+1] = out[i] + in[i] for i < n (n+1 outputs).  tmp must
 // hold scan_tmp_bytes(n) bytes.
@@ -74,6 +78,18 @@ cudaError_t launch_transpose_scatter(int32_t n, const int64_t *cp, const int32_t
                                      const int64_t *rp, int32_t *cursor, int32_t *cols_out, double *vals_out,
                                      cudaStream_t st);
 cudaError_t launch_sort_rows(int32_t n, const int64_t *rp, int32_t *cols, double *vals, cudaStream_t st);
+cudaError_t launch_scatter_levels(int32_t nl, const int32_t *out_of_label, const int32_t *lvl, int32_t *lev_out,
+                                  cudaStream_t st);
+cudaError_t launch_max_i32(const int32_t *a, int64_t n, int32_t *mx, cudaStream_t st);
+cudaError_t launch_level_scatter(int32_t n, const int32_t *lev, const int64_t *lstart, int32_t *cursor,
+                                 int32_t *order, cudaStream_t st);
+cudaError_t launch_inverse_perm(int32_t n, const int32_t *order, int32_t *posof, cudaStream_t st);
+cudaError_t launch_relabel_lengths(int32_t n, const int32_t *order, const int64_t *cp, int32_t *len, cudaStream_t st);
+cudaError_t launch_relabel_gather(int32_t n, const int32_t *order, const int32_t *posof, const int64_t *cp,
+                                  const int32_t *rows, const double *vals, const int64_t *ncp, int32_t *nrows,
+                                  double *nvals, cudaStream_t st);
+cudaError_t launch_gather_i32(int32_t n, const int32_t *idx, const int32_t *src, int32_t *dst, cudaStream_t st);
+cudaError_t launch_gather_f64(int32_t n, const int32_t *idx, const double *src, double *dst, cudaStream_t st);
 cudaError_t launch_to_f32(const double *in, float *out, int64_t n, cudaStream_t st);
 cudaError_t launch_dinv(int32_t n, const double *D, double *Dinv, cudaStream_t st);
 cudaError_t launch_sys_of_label(int32_t S, const int32_t *sys_lbase, int32_t nl, int32_t *sys_of_label,
@@ -86,11 +102,11 @@ struct SolveArgs {
     int32_t n;                    // rows (original numbering)
     // the matrix (symmetric CSC = CSR)
     const int64_t *Lp; const int32_t *Li; const double *Lv;
-    // factor (label space)
+    // factor relabelled into dependency-level order (position space)
     const int64_t *Fcp; const int32_t *Frow; const double *Fval64; const float *Fval32;   // CSC (backward)
     const int64_t *Frp; const int32_t *Fcol; const double *Fvalr64; const float *Fvalr32; // CSR (forward)
-    const double *Dinv;           // [n] 1/D or 0
-    const int32_t *perm;          // [n] label k <- original perm[k]
+    const double *Dinv;           // [n] 1/D or 0, by position
+    const int32_t *operm;         // [n] original index of each position
     int32_t prec;                 // 64 or 32
     int32_t lanes_spmv;           // lanes per row for SpMV (4, 8, 16, 32)
     int32_t lanes_trsv;           // lanes per row for the triangular solves
@@ -111,6 +127,7 @@ struct PcgBuffers {
 };
 
 size_t pcg_state_bytes();
+cudaError_t set_poll_backoff(unsigned max_ns);
 cudaError_t pcg_init(const SolveArgs &A, const PcgBuffers &B, double tol, int32_t maxit, cudaStream_t st);
 cudaError_t pcg_iteration(const SolveArgs &A, const PcgBuffers &B, cudaStream_t st);
 cudaError_t pcg_true_residual(const SolveArgs &A, const PcgBuffers &B, cudaStream_t st);

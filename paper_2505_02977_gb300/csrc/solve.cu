@@ -6,11 +6,15 @@
 //
 // Sync-free solves: every unknown starts as a signalling-NaN sentinel (never
 // produced by arithmetic); a row's lanes poll the unknowns they need until the
-// sentinel is gone, so the value itself is the ready flag.  Rows are handed to
-// a persistent, fully co-resident grid in a static round-robin of row groups
-// (increasing order for the forward solve, decreasing for the backward one):
-// the smallest unfinished group never waits on an unfinished group, so the
-// solve always progresses; every wait is bounded by the spin limit.
+// sentinel is gone, so the value itself is the ready flag.  Rows are visited
+// in the order of their dependency level (computed during the elimination:
+// the forward solve's DAG is the elimination DAG) -- the factor is relabelled
+// into that order once, at setup -- ascending for the forward solve and
+// descending for the backward one, handed to a persistent, fully co-resident
+// grid in a static round-robin of row groups.  Every dependency sits at an
+// earlier position, so the smallest unfinished group never waits on an
+// unfinished group and the solve always progresses; every wait is bounded by
+// the spin limit.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -25,6 +29,7 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int VEC_THREADS = 256;
+__constant__ unsigned g_poll_max_ns = 256;   // cap of the polling back-off
 
 __device__ __forceinline__ double sentinel64() { return __longlong_as_double((long long)0xfff7ffffffffffffull); }
 __device__ __forceinline__ float sentinel32() { return __int_as_float((int)0xffbfffffu); }
@@ -210,10 +215,67 @@ template <typename XT> __device__ __forceinline__ XT to_x(double v);
 template <> __device__ __forceinline__ double to_x<double>(double v) { return v; }
 template <> __device__ __forceinline__ float to_x<float>(double v) { return __double2float_rn(v); }
 
-// Forward: y[i] = rhs[perm[i]] - sum_{k<i} F(i,k) y[k] over the CSR row i.
-// Also resets the backward unknowns z[i] to the sentinel.
+// Wait for an unknown published by another row: polls separated by an
+// exponentially growing sleep; false when the wait is abandoned.
+template <typename XT>
+__device__ __forceinline__ bool poll_ready(const XT *p, XT &v, long long spin_limit, const int32_t *status)
+{
+    v = ld_poll(p);
+    long long spins = 0;
+    unsigned ns = 16;
+    while (is_sentinel(v)) {
+        if (++spins > spin_limit || read_status(status) != ST_OK) return false;
+        __nanosleep(ns);                   // back off: pollers must not crowd out the producers
+        if (ns < g_poll_max_ns) ns <<= 1;
+        v = ld_poll(p);
+    }
+    return true;
+}
+
+// This lane's share of sum_t v[t] x[idx[t]] over t = b+sl, b+sl+S, ... < e,
+// waiting for each x to be published.  The first PF entries' indices and
+// values are fetched together and all their x loads are issued before any
+// wait, so a row costs one round trip for its indices and one for its
+// dependencies; the terms are added in a fixed order.
 template <int S, typename VT, typename XT>
-__global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, const VT *v, const int32_t *perm,
+__device__ __forceinline__ bool dot_ready(int64_t b, int64_t e, int sl, const int32_t *idx, const VT *v,
+                                          const XT *x, XT &acc, long long spin_limit, const int32_t *status)
+{
+    constexpr int PF = 4;
+    int32_t cc[PF];
+    VT vv[PF];
+    XT xx[PF];
+#pragma unroll
+    for (int r = 0; r < PF; ++r) {
+        const int64_t t = b + sl + (int64_t)r * S;
+        cc[r] = t < e ? idx[t] : -1;
+        vv[r] = t < e ? v[t] : (VT)0;
+    }
+#pragma unroll
+    for (int r = 0; r < PF; ++r) xx[r] = cc[r] >= 0 ? ld_poll(x + cc[r]) : (XT)0;
+#pragma unroll
+    for (int r = 0; r < PF; ++r) {
+        if (cc[r] >= 0 && is_sentinel(xx[r]) && !poll_ready(x + cc[r], xx[r], spin_limit, status)) return false;
+        acc += (XT)vv[r] * xx[r];
+    }
+    for (int64_t t = b + sl + (int64_t)PF * S; t < e; t += S) {
+        XT xt;
+        if (!poll_ready(x + idx[t], xt, spin_limit, status)) return false;
+        acc += (XT)v[t] * xt;
+    }
+    return true;
+}
+
+// The factor is stored relabelled by dependency level (position j holds the
+// column of the j-th vertex in level order), so F stays unit lower triangular
+// with every row's dependencies at earlier positions and the rows of one
+// level contiguous.  operm[j] is the original index of position j.
+//
+// Forward: y[j] = rhs[operm[j]] - sum_{c<j} F(j,c) y[c] over CSR row j; also
+// resets the backward unknown z[j] to the sentinel.  Every load that does not
+// depend on other rows is issued before the dependency polls.
+template <int S, typename VT, typename XT>
+__global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, const VT *v, const int32_t *operm,
                            const double *rhs, XT *y, XT *zreset, const PcgState *st, long long spin_limit,
                            int32_t *status)
 {
@@ -225,38 +287,28 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
     const int my = (threadIdx.x >> 5) * (32 / S) + sub;
     const int64_t ngroups = ((int64_t)n + rows_per_group - 1) / rows_per_group;
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-        const int64_t i = g * rows_per_group + my;
-        if (i >= n) continue;
+        const int64_t j = g * rows_per_group + my;
+        if (j >= n) continue;
+        const int64_t b = rp[j], e = rp[j + 1];
+        const double rj = (sl == 0) ? rhs[operm[j]] : 0.0;
         XT acc = 0;
-        bool ok = true;
-        for (int64_t t = rp[i] + sl; t < rp[i + 1]; t += S) {
-            const int32_t k = ci[t];
-            const XT f = (XT)v[t];
-            XT yk = ld_poll(y + k);
-            long long spins = 0;
-            while (is_sentinel(yk)) {
-                if (++spins > spin_limit || read_status(status) != ST_OK) { ok = false; break; }
-                yk = ld_poll(y + k);
-            }
-            if (!ok) break;
-            acc += f * yk;
-        }
+        const bool ok = dot_ready<S, VT, XT>(b, e, sl, ci, v, y, acc, spin_limit, status);
         if (!ok) set_status(status, ST_TIMEOUT);
 #pragma unroll
         for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
         if (sl == 0) {
-            zreset[i] = sentinel<XT>();
-            st_pub(y + i, to_x<XT>(rhs[perm[i]]) - acc);
+            zreset[j] = sentinel<XT>();
+            st_pub(y + j, to_x<XT>(rj) - acc);
         }
     }
 }
 
-// Backward: z[k] = y[k] Dinv[k] - sum_{i>k} F(i,k) z[i] over the CSC column k;
-// writes z_orig[perm[k]], resets y[k] to the sentinel, and accumulates
-// r_orig . z_orig into the block partial.
+// Backward: z[j] = y[j] Dinv[j] - sum_{i>j} F(i,j) z[i] over CSC column j, in
+// decreasing position order; writes zout[operm[j]], resets y[j] to the
+// sentinel, and accumulates r_orig . z into the block partial.
 template <int S, typename VT, typename XT>
 __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, const VT *v, const double *Dinv,
-                           const int32_t *perm, XT *y, XT *z, double *zout, const double *r_orig, double *partial,
+                           const int32_t *operm, XT *y, XT *z, double *zout, const double *r_orig, double *partial,
                            const PcgState *st, long long spin_limit, int32_t *status)
 {
     if (st && st->done) return;
@@ -270,33 +322,26 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
         const int64_t kk = g * rows_per_group + my;
         if (kk >= n) continue;
-        const int64_t k = n - 1 - kk;
-        XT acc = 0;
-        bool ok = true;
-        for (int64_t t = cp[k] + sl; t < cp[k + 1]; t += S) {
-            const int32_t i = ri[t];
-            const XT f = (XT)v[t];
-            XT zi = ld_poll(z + i);
-            long long spins = 0;
-            while (is_sentinel(zi)) {
-                if (++spins > spin_limit || read_status(status) != ST_OK) { ok = false; break; }
-                zi = ld_poll(z + i);
-            }
-            if (!ok) break;
-            acc += f * zi;
+        const int64_t j = n - 1 - kk;
+        const int64_t b = cp[j], e = cp[j + 1];
+        XT yj = 0;
+        double dj = 0.0, rj = 0.0;
+        int32_t o = 0;
+        if (sl == 0) {
+            yj = y[j]; dj = Dinv[j]; o = operm[j];
+            if (r_orig) rj = r_orig[o];
         }
+        XT acc = 0;
+        const bool ok = dot_ready<S, VT, XT>(b, e, sl, ri, v, z, acc, spin_limit, status);
         if (!ok) set_status(status, ST_TIMEOUT);
 #pragma unroll
         for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
         if (sl == 0) {
-            const XT yk = y[k];
-            const XT scaled = to_x<XT>((double)yk * Dinv[k]);
-            const XT zk = scaled - acc;
-            y[k] = sentinel<XT>();
-            st_pub(z + k, zk);
-            const int32_t o = perm[k];
-            zout[o] = (double)zk;
-            if (r_orig) dotacc += r_orig[o] * (double)zk;
+            const XT zj = to_x<XT>((double)yj * dj) - acc;
+            y[j] = sentinel<XT>();
+            st_pub(z + j, zj);
+            zout[o] = (double)zj;
+            dotacc += rj * (double)zj;
         }
     }
     if (partial) {
@@ -316,7 +361,7 @@ template <int S>
 cudaError_t spmv_t(const SolveArgs &A, const double *x, double *y, double *partial, const PcgState *st, int blocks,
                    cudaStream_t s)
 {
-    k_spmv<S><<<blocks, VEC_THREADS, 0, s>>>(A.n, A.Lp, A.Li, A.Lv, x, y, partial, st);
+    k_spmv<S><<<blocks, VEC_THREADS, 0, s>>>(A.n, A.Lp, A.Li, A.Lv, x, y, partial, st); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -336,10 +381,10 @@ cudaError_t apply_t(const SolveArgs &A, const VT *vr, const VT *vc, XT *y, XT *z
                     double *partial, const PcgState *st, cudaStream_t s)
 {
     const int threads = A.trsv_warps * 32;
-    k_trsv_fwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Frp, A.Fcol, vr, A.perm, r, y, z, st,
-                                                             A.spin_limit, A.status);
-    k_trsv_bwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Fcp, A.Frow, vc, A.Dinv, A.perm, y, z, zout, r,
-                                                             partial, st, A.spin_limit, A.status);
+    k_trsv_fwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Frp, A.Fcol, vr, A.operm, r, y, z, st,
+                                                             A.spin_limit, A.status); count_launches(1);
+    k_trsv_bwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z,
+                                                             zout, r, partial, st, A.spin_limit, A.status); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -367,12 +412,18 @@ cudaError_t fill_sentinels(const SolveArgs &A, const PcgBuffers &B, cudaStream_t
     const int g = vec_grid(A.n, 4096);
     if (A.prec == 32) k_fill_sentinel<float><<<g, VEC_THREADS, 0, s>>>(A.n, B.yl32, B.zl32);
     else k_fill_sentinel<double><<<g, VEC_THREADS, 0, s>>>(A.n, B.yl64, B.zl64);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t pcg_state_bytes() { return sizeof(PcgState); }
+
+cudaError_t set_poll_backoff(unsigned max_ns)
+{
+    return cudaMemcpyToSymbol(g_poll_max_ns, &max_ns, sizeof max_ns);
+}
 
 int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec)
 {
@@ -418,13 +469,13 @@ cudaError_t pcg_init(const SolveArgs &A, const PcgBuffers &B, double tol, int32_
 {
     const int nb = B.vec_blocks;
     double *p_bb = B.partials, *p_rz = B.partials + B.pstride;
-    k_init_vectors<<<nb, VEC_THREADS, 0, s>>>(A.n, B.b, B.x, B.r, p_bb);
+    k_init_vectors<<<nb, VEC_THREADS, 0, s>>>(A.n, B.b, B.x, B.r, p_bb); count_launches(1);
     cudaError_t e = fill_sentinels(A, B, s);
     if (e != cudaSuccess) return e;
     e = apply(A, B, B.r, B.z, p_rz, nullptr, s);
     if (e != cudaSuccess) return e;
-    k_init_scalars<<<1, 256, 0, s>>>(B.state, p_bb, nb, p_rz, A.trsv_blocks, tol, maxit);
-    k_copy<<<nb, VEC_THREADS, 0, s>>>(A.n, B.z, B.p);
+    k_init_scalars<<<1, 256, 0, s>>>(B.state, p_bb, nb, p_rz, A.trsv_blocks, tol, maxit); count_launches(1);
+    k_copy<<<nb, VEC_THREADS, 0, s>>>(A.n, B.z, B.p); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -434,13 +485,13 @@ cudaError_t pcg_iteration(const SolveArgs &A, const PcgBuffers &B, cudaStream_t 
     double *p_pq = B.partials, *p_rr = B.partials + B.pstride, *p_rz = B.partials + 2 * B.pstride;
     cudaError_t e = spmv(A, B.p, B.q, p_pq, B.state, nb, s);
     if (e != cudaSuccess) return e;
-    k_alpha<<<1, 256, 0, s>>>(B.state, p_pq, nb);
-    k_update_xr<<<nb, VEC_THREADS, 0, s>>>(A.n, B.x, B.r, B.p, B.q, p_rr, B.state);
-    k_check<<<1, 256, 0, s>>>(B.state, p_rr, nb);
+    k_alpha<<<1, 256, 0, s>>>(B.state, p_pq, nb); count_launches(1);
+    k_update_xr<<<nb, VEC_THREADS, 0, s>>>(A.n, B.x, B.r, B.p, B.q, p_rr, B.state); count_launches(1);
+    k_check<<<1, 256, 0, s>>>(B.state, p_rr, nb); count_launches(1);
     e = apply(A, B, B.r, B.z, p_rz, B.state, s);
     if (e != cudaSuccess) return e;
-    k_beta<<<1, 256, 0, s>>>(B.state, p_rz, A.trsv_blocks);
-    k_update_p<<<nb, VEC_THREADS, 0, s>>>(A.n, B.p, B.z, B.state);
+    k_beta<<<1, 256, 0, s>>>(B.state, p_rz, A.trsv_blocks); count_launches(1);
+    k_update_p<<<nb, VEC_THREADS, 0, s>>>(A.n, B.p, B.z, B.state); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -450,7 +501,7 @@ __global__ void k_clear_done(PcgState *st) { st->done = 0; st->converged = 0; }
 
 cudaError_t pcg_clear_done(const PcgBuffers &B, cudaStream_t s)
 {
-    k_clear_done<<<1, 1, 0, s>>>(B.state);
+    k_clear_done<<<1, 1, 0, s>>>(B.state); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -460,8 +511,8 @@ cudaError_t pcg_resume(const SolveArgs &A, const PcgBuffers &B, cudaStream_t s)
     double *p_rz = B.partials + 2 * B.pstride;
     cudaError_t e = apply(A, B, B.r, B.z, p_rz, B.state, s);
     if (e != cudaSuccess) return e;
-    k_beta<<<1, 256, 0, s>>>(B.state, p_rz, A.trsv_blocks);
-    k_update_p<<<nb, VEC_THREADS, 0, s>>>(A.n, B.p, B.z, B.state);
+    k_beta<<<1, 256, 0, s>>>(B.state, p_rz, A.trsv_blocks); count_launches(1);
+    k_update_p<<<nb, VEC_THREADS, 0, s>>>(A.n, B.p, B.z, B.state); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -470,8 +521,8 @@ cudaError_t pcg_true_residual(const SolveArgs &A, const PcgBuffers &B, cudaStrea
     const int nb = B.vec_blocks;
     cudaError_t e = spmv(A, B.x, B.q, nullptr, nullptr, nb, s);
     if (e != cudaSuccess) return e;
-    k_resid_sq<<<nb, VEC_THREADS, 0, s>>>(A.n, B.b, B.q, B.partials);
-    k_true_rr<<<1, 256, 0, s>>>(B.state, B.partials, nb);
+    k_resid_sq<<<nb, VEC_THREADS, 0, s>>>(A.n, B.b, B.q, B.partials); count_launches(1);
+    k_true_rr<<<1, 256, 0, s>>>(B.state, B.partials, nb); count_launches(1);
     return cudaGetLastError();
 }
 

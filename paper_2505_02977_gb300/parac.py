@@ -59,10 +59,12 @@ _lib.parac_status_string.argtypes = [C.c_int]
 _lib.parac_status_string.restype = C.c_char_p
 _lib.parac_last_error.argtypes = []
 _lib.parac_last_error.restype = C.c_char_p
+_lib.parac_kernel_launches.argtypes = []
+_lib.parac_kernel_launches.restype = C.c_uint64
 
 EXPORTED = ("parac_opts_default", "parac_factor", "parac_pcg", "parac_factor_many", "parac_factor_export",
             "parac_factor_stats", "parac_factor_free", "parac_precond_apply", "parac_status_string",
-            "parac_last_error")
+            "parac_last_error", "parac_kernel_launches")
 
 
 class ParacError(RuntimeError):
@@ -225,3 +227,7 @@ def parac_status_string(code):
 
 def parac_last_error():
     return _lib.parac_last_error().decode()
+
+
+def parac_kernel_launches():
+    return int(_lib.parac_kernel_launches())

@@ -72,6 +72,7 @@ def test_grid2d_64_bit_identical(P):
     dict(blocks=3, warps_per_block=2, queue_chunk=4),
     dict(queue_chunk=8),
     dict(big_threshold=32),
+    dict(big_threshold=32, warps_per_block=2),
 ])
 def test_random_graphs_any_schedule(P, sched):
     rng = np.random.default_rng(5)
@@ -102,8 +103,9 @@ def test_grid3d_64_bit_identical(P):
 
 
 def test_high_degree_paths(P):
-    """A hub of degree several thousand forces the CTA-buffer and global-scratch
-    working sets; small caps force them on moderate degrees as well."""
+    """A hub of degree several thousand forces the CTA-cooperative path with
+    the CTA buffer and with global scratch; small caps force it on moderate
+    degrees as well."""
     rng = np.random.default_rng(3)
     n = 6000
     hub = np.zeros(n - 1, np.int64)
@@ -194,3 +196,22 @@ def test_batched_factor_matches_per_system_oracle(P):
         got = G.export()
         assert same_factor(got, ref), (s, _first_diff(got, ref))
         G.free()
+
+
+def test_warp_only_paths_match(P, monkeypatch):
+    """With the CTA-cooperative path switched off every working set is handled
+    by single warps (shared buffer, CTA buffer under a lock, global scratch):
+    the factor must not change."""
+    monkeypatch.setenv("PARAC_COOP", "0")
+    rng = np.random.default_rng(8)
+    n = 3000
+    hub = np.zeros(n - 1, np.int64)
+    a = np.concatenate([hub, rng.integers(1, n, 4 * n)])
+    b = np.concatenate([np.arange(1, n), rng.integers(1, n, 4 * n)])
+    keep = a != b
+    lo = np.minimum(a[keep], b[keep]); hi = np.maximum(a[keep], b[keep])
+    key = np.unique(lo * n + hi)
+    A = W.laplacian_from_edges(n, key // n, key % n, rng.uniform(0.5, 2, len(key)))
+    perm = W.random_ordering(n, 3)
+    _check(P, A, perm, 5)
+    _check(P, A, perm, 5, big_threshold=32)

@@ -46,6 +46,11 @@ def test_precond_apply_matches_oracle(P, case):
 
 @pytest.mark.parametrize("case", range(4))
 def test_pcg_matches_oracle(P, case):
+    """Same stopping rule as the oracle: converged to 1e-8 within one iteration
+    of the oracle's count; solutions converged to 1e-12 agree to 1e-10
+    relative; after the same iteration count the iterates agree to 1e-8 (the
+    dot products and sparse sums are reduced in different orders, and CG
+    amplifies that rounding from one iteration to the next)."""
     A, perm, seed, b = _cases()[case]
     G = _factor(P, A, perm, seed)
     F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)
@@ -53,11 +58,14 @@ def test_pcg_matches_oracle(P, case):
     x, it, rr, status = P.parac_pcg(G, A.n, None, None, None, b, tol=1e-8, maxit=1000)
     assert status == "PARAC_OK" and rr[0] <= 1e-8
     assert abs(int(it[0]) - ito) <= 1
-    # same number of iterations on both sides -> same iterate up to rounding
+    xo12, _, _ = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, b, 1e-12, 2000)
+    x12, _, rr12, _ = P.parac_pcg(G, A.n, None, None, None, b, tol=1e-12, maxit=2000)
+    xa, xb = x12 - x12.mean(), xo12 - xo12.mean()
+    assert np.linalg.norm(xa - xb) <= 1e-10 * np.linalg.norm(xb)
     x2, it2, _, _ = P.parac_pcg(G, A.n, None, None, None, b, tol=0.0, maxit=ito)
     assert it2[0] == ito
     xa, xb = x2 - x2.mean(), xo - xo.mean()
-    assert np.linalg.norm(xa - xb) <= 1e-10 * np.linalg.norm(xb)
+    assert np.linalg.norm(xa - xb) <= 1e-8 * np.linalg.norm(xb)
     G.free()
 
 
@@ -122,4 +130,21 @@ def test_pcg_noconv_status(P):
     G = _factor(P, A, perm, seed)
     x, it, rr, status = P.parac_pcg(G, A.n, None, None, None, b, tol=1e-14, maxit=3)
     assert status == "PARAC_ENOCONV" and it[0] == 3 and rr[0] > 1e-14
+    G.free()
+
+
+def test_grid3d_128_full_size(P):
+    """The 128^3 workload at full size: the factor is bit-identical to the
+    oracle's, and PCG reaches 1e-8 within two iterations of the oracle."""
+    import torch
+    from tests.helpers import same_factor
+    A, perm, seed, b = W.config("grid3d-128")
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    G = P.parac_factor(A.n, dev(A.colptr), dev(A.rowind), dev(A.val), dev(perm), seed)
+    F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)
+    assert same_factor(G.export(), F)
+    x, it, rr, status = P.parac_pcg(G, A.n, None, None, None, dev(b), tol=1e-8, maxit=1000)
+    xo, ito, rro = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, b, 1e-8, 1000)
+    assert status == "PARAC_OK" and rr[0] <= 1e-8 and rro <= 1e-8
+    assert abs(int(it[0]) - ito) <= 2
     G.free()
