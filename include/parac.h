@@ -173,6 +173,32 @@ parac_status parac_factor_many(int32_t count, const parac_system *systems, uint6
 parac_status parac_precond_apply(parac_factor_t G, const double *r, double *z);
 
 /*
+ * parac_precond_apply_noalloc -- the same z = M^{-1} r as parac_precond_apply
+ * (same kernels, same result), for callers that cannot allocate device memory
+ * when they need the preconditioner: code that must not enter a memory
+ * allocator once its solve loop is running (fixed memory budgets, latency-
+ * critical inner loops, host code driving its own Krylov method around an
+ * allocator it does not control).  The ParAC paper has no counterpart; this
+ * entry point is an interface convenience of this library.
+ *   Allocation  none: the two work vectors of the triangular solves live in a
+ *               fixed device array of 4 MiB inside the library (every GPU
+ *               that loads the library holds it until the process exits).
+ *   Limit       the factor's order n must be at most 262,144 (2^18);
+ *               larger factors return PARAC_EINVAL.
+ *   Pointers    r and z are n-vectors of DEVICE memory in the original
+ *               numbering; host pointers return PARAC_EINVAL.
+ *   Set-up      the first call on a device looks up the array's device
+ *               address (cudaGetSymbolAddress) with that device current;
+ *               make that first call before any stream capture.
+ *   Sharing     every call uses the same array and leaves the last call's
+ *               values in it (each call resets what it reads); calls whose
+ *               work overlaps on the GPU (other streams, other threads) race
+ *               on it and must be serialised by the caller.
+ * Errors: EINVAL, ETIMEOUT, ECUDA.
+ */
+parac_status parac_precond_apply_noalloc(parac_factor_t G, const double *r, double *z);
+
+/*
  * parac_factor_export -- copy the factor out (label space, ground removed).
  *   nnz       receives the strict-lower entry count of F
  *   colptr    int64[n+1], rowind int32[nnz], Fval double[nnz] (rows ascending

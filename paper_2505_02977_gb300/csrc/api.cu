@@ -1014,3 +1014,31 @@ extern "C" parac_status parac_precond_apply(parac_factor_t G, const double *r, d
         return PARAC_OK;
     });
 }
+
+// Allocation-free preconditioner apply (see include/parac.h).  Uses only the
+// handle's arrays and the library's fixed work array: no device allocation
+// and no allocating library call happens here.
+extern "C" parac_status parac_precond_apply_noalloc(parac_factor_t G, const double *r, double *z)
+{
+    return guarded([&]() -> parac_status {
+        if (!G || (G->n > 0 && (!r || !z))) { set_err("bad arguments"); return PARAC_EINVAL; }
+        if (G->n > NOALLOC_MAX_N) {
+            set_err("parac_precond_apply_noalloc handles at most %d unknowns (factor has %lld)", NOALLOC_MAX_N,
+                    (long long)G->n);
+            return PARAC_EINVAL;
+        }
+        if (G->n == 0) return PARAC_OK;
+        if (!is_device_ptr(r) || !is_device_ptr(z)) { set_err("r and z must be device memory"); return PARAC_EINVAL; }
+        int cur = 0;
+        CK(cudaGetDevice(&cur));
+        if (cur != G->device) CK(cudaSetDevice(G->device));
+        cudaStream_t st = G->stream;
+        SolveArgs A = solve_args(G, G->Lp.as<int64_t>(), G->Li.as<int32_t>(), G->Lv.as<double>(), G->nnzL);
+        CK(cudaMemsetAsync(G->status.p, 0, 4, st));
+        CK(precond_apply_noalloc(A, r, z, st));
+        const int32_t dst = read_dev_status(G, st);
+        if (cur != G->device) CK(cudaSetDevice(cur));
+        if (dst != ST_OK) { set_err("triangular solve wait exceeded the spin limit"); return PARAC_ETIMEOUT; }
+        return PARAC_OK;
+    });
+}

@@ -137,6 +137,10 @@ cudaError_t pcg_read_state(const PcgBuffers &B, PcgHostState *h, cudaStream_t st
 cudaError_t pcg_clear_done(const PcgBuffers &B, cudaStream_t st);
 cudaError_t pcg_resume(const SolveArgs &A, const PcgBuffers &B, cudaStream_t st);
 cudaError_t precond_apply(const SolveArgs &A, const PcgBuffers &B, const double *r, double *z, cudaStream_t st);
+// Allocation-free variant: work vectors in a fixed device array (n <= NOALLOC_MAX_N).
+constexpr int NOALLOC_MAX_N = 1 << 18;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+cudaError_t precond_apply_noalloc(const SolveArgs &A, const double *r, double *z, cudaStream_t st);
 int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec);
 
 }  // namespace parac

@@ -15,6 +15,8 @@
 // earlier position, so the smallest unfinished group never waits on an
 // unfinished group and the solve always progresses; every wait is bounded by
 // the spin limit.
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -461,6 +463,55 @@ int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec)
 cudaError_t precond_apply(const SolveArgs &A, const PcgBuffers &B, const double *r, double *z, cudaStream_t st)
 {
     cudaError_t e = fill_sentinels(A, B, st);
+    if (e != cudaSuccess) return e;
+    return apply(A, B, r, z, nullptr, nullptr, st);
+}
+
+// ---------------------------------------------------------------- allocation-free apply
+// Work space of parac_precond_apply_noalloc: the forward and backward
+// unknowns of the two triangular solves (two n-vectors, FP64 or FP32), held
+// in a fixed array that every device loading the library keeps until exit.
+// All calls share it; its contents are the last call's, and every call
+// resets the part it uses before reading it.
+static __device__ __align__(256) double g_noalloc_work[2 * (size_t)NOALLOC_MAX_N];
+
+// Device address of g_noalloc_work on the current device.  The name is only a
+// host-side stand-in in host code, so the address is looked up once per
+// device (with that device current) and cached.
+static cudaError_t noalloc_work_ptr(double **out)
+{
+    static std::mutex mu;
+    static double *ptrs[NOALLOC_MAX_DEVICES] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_work);
+        if (e != cudaSuccess) return e;
+        ptrs[dev] = (double *)p;
+    }
+    *out = ptrs[dev];
+    return cudaSuccess;
+}
+
+cudaError_t precond_apply_noalloc(const SolveArgs &A, const double *r, double *z, cudaStream_t st)
+{
+    if (A.n > NOALLOC_MAX_N) return cudaErrorInvalidValue;
+    double *work = nullptr;
+    cudaError_t e = noalloc_work_ptr(&work);
+    if (e != cudaSuccess) return e;
+    PcgBuffers B{};
+    if (A.prec == 32) {
+        B.yl32 = (float *)work;
+        B.zl32 = (float *)work + A.n;
+    } else {
+        B.yl64 = work;
+        B.zl64 = work + A.n;
+    }
+    e = fill_sentinels(A, B, st);     // the unknowns must start as "not yet published"
     if (e != cudaSuccess) return e;
     return apply(A, B, r, z, nullptr, nullptr, st);
 }

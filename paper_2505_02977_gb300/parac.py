@@ -55,6 +55,8 @@ _lib.parac_factor_free.argtypes = [C.c_void_p]
 _lib.parac_factor_free.restype = None
 _lib.parac_precond_apply.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
 _lib.parac_precond_apply.restype = C.c_int
+_lib.parac_precond_apply_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.parac_precond_apply_noalloc.restype = C.c_int
 _lib.parac_status_string.argtypes = [C.c_int]
 _lib.parac_status_string.restype = C.c_char_p
 _lib.parac_last_error.argtypes = []
@@ -64,7 +66,7 @@ _lib.parac_kernel_launches.restype = C.c_uint64
 
 EXPORTED = ("parac_opts_default", "parac_factor", "parac_pcg", "parac_factor_many", "parac_factor_export",
             "parac_factor_stats", "parac_factor_free", "parac_precond_apply", "parac_status_string",
-            "parac_last_error", "parac_kernel_launches")
+            "parac_last_error", "parac_kernel_launches", "parac_precond_apply_noalloc")
 
 
 class ParacError(RuntimeError):
@@ -196,6 +198,12 @@ def parac_precond_apply(G, r, z=None):
     r = np.ascontiguousarray(r, np.float64)
     z = np.zeros_like(r) if z is None else z
     _check(_lib.parac_precond_apply(G.handle, r.ctypes.data, z.ctypes.data), "parac_precond_apply")
+    return z
+
+
+def parac_precond_apply_noalloc(G, r, z):
+    """Allocation-free z = M^{-1} r; r and z are torch CUDA tensors (device memory)."""
+    _check(_lib.parac_precond_apply_noalloc(G.handle, r.data_ptr(), z.data_ptr()), "parac_precond_apply_noalloc")
     return z
 
 
