@@ -47,6 +47,31 @@ def measured_peak_hbm():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+def csrc_sha():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2505_02977_gb300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, alg_bytes):
+    """DRAM bytes per launch from the last ncu capture of this kernel, scaled from the
+    captured workload to this one by the ratio traffic / algorithmic bytes; None when
+    the kernel sources changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    if rec.get("csrc_sha") != csrc_sha() or kernel not in rec.get("kernels", {}):
+        return None
+    return rec["kernels"][kernel]["ratio"] * alg_bytes
+
+
 def algorithmic_bytes_elim(st):
     """Bytes the elimination must move once (per launch): read the original
     strict-lower entries (12 B each), write and read back every fill entry
@@ -311,7 +336,7 @@ def run_ours(args, world, rank, local, pg):
         "vertices_per_s": A.n / (statistics.median(setup_ms) * 1e-3),
         "elim_ms": elim_ms, "depth": st_el.get("depth"),
         "roofline": {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": recorded_traffic(name, alg),
                      "algorithmic_bytes": alg, "kernel_ms": t_ms},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
         "wall_s": t_wall,
