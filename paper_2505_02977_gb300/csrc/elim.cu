@@ -160,8 +160,11 @@ __device__ __forceinline__ uint32_t wait_nonzero(const uint32_t *slot, const Eli
     long long spins = 0;
     uint32_t g;
     while ((g = ld_acquire_u32(slot)) == 0u) {
-        if (read_status(a.status) != ST_OK) return 0u;
-        if (++spins > a.spin_limit) { set_status(a.status, ST_TIMEOUT); return 0u; }
+        ++spins;
+        if ((spins & 63) == 0) {           // the shared status word is read only now and then
+            if (read_status(a.status) != ST_OK) return 0u;
+            if (spins > a.spin_limit) { set_status(a.status, ST_TIMEOUT); return 0u; }
+        }
         if (spins > 32) __nanosleep(32);
     }
     return g;
@@ -478,8 +481,10 @@ __device__ int32_t eliminate_big(const ElimArgs &a, int32_t k, int64_t o0, int32
         if (lane == 0) {
             long long spins = 0;
             while (!(got = (atomicCAS(block_lock, 0, 1) == 0))) {
-                if (read_status(a.status) != ST_OK) break;
-                if (++spins > a.spin_limit) { set_status(a.status, ST_TIMEOUT); break; }
+                if ((++spins & 63) == 0) {
+                    if (read_status(a.status) != ST_OK) break;
+                    if (spins > a.spin_limit) { set_status(a.status, ST_TIMEOUT); break; }
+                }
                 __nanosleep(64);
             }
             __threadfence_block();
@@ -709,8 +714,11 @@ __device__ bool cta_barrier(CoopShared &cs, const ElimArgs &a)
         const int target = (old / nw + 1) * nw;
         long long spins = 0;
         while (vol(cs.arrive) < target) {
-            if (read_status(a.status) != ST_OK) { ok = 0; break; }
-            if (++spins > a.spin_limit) { set_status(a.status, ST_TIMEOUT); ok = 0; break; }
+            ++spins;
+            if ((spins & 63) == 0) {
+                if (read_status(a.status) != ST_OK) { ok = 0; break; }
+                if (spins > a.spin_limit) { set_status(a.status, ST_TIMEOUT); ok = 0; break; }
+            }
             if (spins > 64) __nanosleep(32);
         }
         __threadfence_block();
@@ -1067,13 +1075,13 @@ __global__ void __launch_bounds__(256, 2) elim_kernel(ElimArgs a, int fchunk)
                     k = *(volatile const int32_t *)(a.queue + slot);
                     if (__shfl_sync(FULL, k, 0) >= 0) { k = __shfl_sync(FULL, k, 0); break; }
                 }
-                if (read_status(a.status) != ST_OK) { stop = true; break; }
                 if (a.coop) {
                     const int32_t h = serve_help(a, cs, seen_gen, bbuf, ws);
                     if (h == -2) { stop = true; break; }
                     if (h != -3) spins = 0;
                 }
                 if ((++spins & 63) == 0) {
+                    if (read_status(a.status) != ST_OK) { stop = true; break; }
                     const uint32_t t = *(volatile const uint32_t *)a.q_tail;
                     const uint32_t dn = *(volatile const uint32_t *)a.done;
                     if (dn >= nl) { stop = true; break; }

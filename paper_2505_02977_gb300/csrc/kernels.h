@@ -114,6 +114,7 @@ struct SolveArgs {
     int32_t trsv_warps;           // warps per block of the triangular solves
     long long spin_limit;
     int32_t *status;
+    long long *trace;             // optional per-row trace of the forward solve [n * 8]
 };
 
 struct PcgBuffers {

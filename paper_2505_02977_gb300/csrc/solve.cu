@@ -226,7 +226,10 @@ __device__ __forceinline__ bool poll_ready(const XT *p, XT &v, long long spin_li
     long long spins = 0;
     unsigned ns = 16;
     while (is_sentinel(v)) {
-        if (++spins > spin_limit || read_status(status) != ST_OK) return false;
+        ++spins;
+        // the shared status word is read only now and then: every poller
+        // reading it on every spin would turn its cache line into a hot spot
+        if ((spins & 127) == 0 && (spins > spin_limit || read_status(status) != ST_OK)) return false;
         __nanosleep(ns);                   // back off: pollers must not crowd out the producers
         if (ns < g_poll_max_ns) ns <<= 1;
         v = ld_poll(p);
@@ -235,35 +238,55 @@ __device__ __forceinline__ bool poll_ready(const XT *p, XT &v, long long spin_li
 }
 
 // This lane's share of sum_t v[t] x[idx[t]] over t = b+sl, b+sl+S, ... < e,
-// waiting for each x to be published.  The first PF entries' indices and
-// values are fetched together and all their x loads are issued before any
-// wait, so a row costs one round trip for its indices and one for its
-// dependencies; the terms are added in a fixed order.
+// waiting for each x to be published.  Entries are taken in chunks of PF per
+// lane: a chunk's indices and values are fetched together, then the chunk's
+// x loads are issued in rounds -- every entry still unpublished is re-loaded
+// in the same round -- so a chunk costs one round trip for its indices and
+// one per round of waiting, whatever the row length; the terms are added in
+// a fixed order once all are known.
 template <int S, typename VT, typename XT>
 __device__ __forceinline__ bool dot_ready(int64_t b, int64_t e, int sl, const int32_t *idx, const VT *v,
-                                          const XT *x, XT &acc, long long spin_limit, const int32_t *status)
+                                          const XT *x, XT &acc, long long spin_limit, const int32_t *status,
+                                          long long *t_seen = nullptr, int32_t *seen_idx = nullptr)
 {
-    constexpr int PF = 4;
-    int32_t cc[PF];
-    VT vv[PF];
-    XT xx[PF];
+    constexpr int PF = 8;
+    for (int64_t base = b + sl; base < e; base += (int64_t)PF * S) {
+        int32_t cc[PF];
+        VT vv[PF];
+        XT xx[PF];
 #pragma unroll
-    for (int r = 0; r < PF; ++r) {
-        const int64_t t = b + sl + (int64_t)r * S;
-        cc[r] = t < e ? idx[t] : -1;
-        vv[r] = t < e ? v[t] : (VT)0;
-    }
+        for (int r = 0; r < PF; ++r) {
+            const int64_t t = base + (int64_t)r * S;
+            cc[r] = t < e ? idx[t] : -1;
+            vv[r] = t < e ? v[t] : (VT)0;
+        }
 #pragma unroll
-    for (int r = 0; r < PF; ++r) xx[r] = cc[r] >= 0 ? ld_poll(x + cc[r]) : (XT)0;
+        for (int r = 0; r < PF; ++r) xx[r] = cc[r] >= 0 ? ld_poll(x + cc[r]) : (XT)0;
+        long long spins = 0;
+        unsigned ns = 16;
+        for (;;) {
+            int last = -1;
 #pragma unroll
-    for (int r = 0; r < PF; ++r) {
-        if (cc[r] >= 0 && is_sentinel(xx[r]) && !poll_ready(x + cc[r], xx[r], spin_limit, status)) return false;
-        acc += (XT)vv[r] * xx[r];
-    }
-    for (int64_t t = b + sl + (int64_t)PF * S; t < e; t += S) {
-        XT xt;
-        if (!poll_ready(x + idx[t], xt, spin_limit, status)) return false;
-        acc += (XT)v[t] * xt;
+            for (int r = 0; r < PF; ++r)
+                if (cc[r] >= 0 && is_sentinel(xx[r])) last = r;
+            if (last < 0) break;
+            ++spins;
+            if ((spins & 127) == 0 && (spins > spin_limit || read_status(status) != ST_OK)) return false;
+            __nanosleep(ns);               // back off: pollers must not crowd out the producers
+            if (ns < g_poll_max_ns) ns <<= 1;
+            bool seen = false;
+            int32_t seen_c = -1;
+#pragma unroll
+            for (int r = 0; r < PF; ++r) {
+                if (cc[r] >= 0 && is_sentinel(xx[r])) {
+                    xx[r] = ld_poll(x + cc[r]);
+                    if (!is_sentinel(xx[r])) { seen = true; seen_c = cc[r]; }
+                }
+            }
+            if (t_seen && seen) { *t_seen = global_ns(); *seen_idx = seen_c; }
+        }
+#pragma unroll
+        for (int r = 0; r < PF; ++r) acc += (XT)vv[r] * xx[r];
     }
     return true;
 }
@@ -279,7 +302,7 @@ __device__ __forceinline__ bool dot_ready(int64_t b, int64_t e, int sl, const in
 template <int S, typename VT, typename XT>
 __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, const VT *v, const int32_t *operm,
                            const double *rhs, XT *y, XT *zreset, const PcgState *st, long long spin_limit,
-                           int32_t *status)
+                           int32_t *status, long long *trace)
 {
     if (st && st->done) return;
     const unsigned lane = threadIdx.x & 31;
@@ -291,16 +314,44 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
         const int64_t j = g * rows_per_group + my;
         if (j >= n) continue;
+        const long long t_arrive = trace ? global_ns() : 0;
         const int64_t b = rp[j], e = rp[j + 1];
         const double rj = (sl == 0) ? rhs[operm[j]] : 0.0;
         XT acc = 0;
-        const bool ok = dot_ready<S, VT, XT>(b, e, sl, ci, v, y, acc, spin_limit, status);
+        long long t_seen = 0;
+        int32_t seen_idx = -1;
+        const bool ok = trace ? dot_ready<S, VT, XT>(b, e, sl, ci, v, y, acc, spin_limit, status, &t_seen, &seen_idx)
+                              : dot_ready<S, VT, XT>(b, e, sl, ci, v, y, acc, spin_limit, status);
         if (!ok) set_status(status, ST_TIMEOUT);
+        long long t_acc = 0;
+        if (trace) {                                   // latest dependency seen by any lane of the row
+            t_acc = global_ns();
+#pragma unroll
+            for (int off = S / 2; off > 0; off >>= 1) {
+                const long long to = __shfl_xor_sync(smask, t_seen, off);
+                const int32_t io = __shfl_xor_sync(smask, seen_idx, off);
+                const long long ta = __shfl_xor_sync(smask, t_acc, off);
+                if (to > t_seen) { t_seen = to; seen_idx = io; }
+                if (ta > t_acc) t_acc = ta;
+            }
+        }
+        const long long t_red0 = trace ? global_ns() : 0;
 #pragma unroll
         for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
+        const long long t_red = trace ? global_ns() : 0;
         if (sl == 0) {
             zreset[j] = sentinel<XT>();
             st_pub(y + j, to_x<XT>(rj) - acc);
+            if (trace) {
+                trace[8 * j] = t_arrive;
+                trace[8 * j + 1] = t_seen;
+                trace[8 * j + 2] = global_ns();
+                trace[8 * j + 3] = seen_idx;
+                trace[8 * j + 4] = t_acc;
+                trace[8 * j + 5] = t_red0;
+                trace[8 * j + 6] = t_red;
+                trace[8 * j + 7] = e - b;
+            }
         }
     }
 }
@@ -384,7 +435,7 @@ cudaError_t apply_t(const SolveArgs &A, const VT *vr, const VT *vc, XT *y, XT *z
 {
     const int threads = A.trsv_warps * 32;
     k_trsv_fwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Frp, A.Fcol, vr, A.operm, r, y, z, st,
-                                                             A.spin_limit, A.status); count_launches(1);
+                                                             A.spin_limit, A.status, A.trace); count_launches(1);
     k_trsv_bwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z,
                                                              zout, r, partial, st, A.spin_limit, A.status); count_launches(1);
     return cudaGetLastError();
