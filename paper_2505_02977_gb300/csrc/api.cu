@@ -220,7 +220,7 @@ struct FactorOut {
     DBuf Fcp, Frow, Fval, D, Lev;
     int64_t nnzF = 0;
     int64_t nl = 0, nnz_low = 0;
-    unsigned long long stats[16] = {0};
+    unsigned long long stats[32] = {0};
     unsigned long long pool_used = 0, f_used = 0, scratch_used = 0;
     int regrows = 0;
     double t_ingest = 0, t_elim = 0, t_compact = 0;
@@ -364,7 +364,7 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
          in_w = dalloc<double>((size_t)nl * FILL_C0, st), dir = dalloc<uint32_t>((size_t)nl * FILL_LEVELS, st);
     DBuf f_start = dalloc<int64_t>(nl, st), f_len = dalloc<int32_t>(nl, st), Dl = dalloc<double>(nl, st);
     DBuf lvl = dalloc<int32_t>(nl, st);
-    DBuf tops = dalloc<unsigned long long>(3, st), status = dalloc<int32_t>(1, st), stats = dalloc<unsigned long long>(16, st);
+    DBuf tops = dalloc<unsigned long long>(3, st), status = dalloc<int32_t>(1, st), stats = dalloc<unsigned long long>(32, st);
 
     // optional per-vertex trace, written to the file named by PARAC_TRACE
     const char *trace_path = getenv("PARAC_TRACE");
@@ -392,7 +392,7 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         CK(cudaMemsetAsync(dir.p, 0, 4 * (size_t)nl * FILL_LEVELS, st));
         CK(cudaMemsetAsync(tops.p, 0, 24, st));
         CK(cudaMemsetAsync(status.p, 0, 4, st));
-        CK(cudaMemsetAsync(stats.p, 0, 128, st));
+        CK(cudaMemsetAsync(stats.p, 0, 256, st));
         CK(cudaMemsetAsync(lvl.p, 0, 4 * nl, st));
         CK(launch_queue_init((int32_t)nl, dp.as<int32_t>(), queue.as<int32_t>(), ctrs.as<uint32_t>() + 1, st));
 
@@ -427,7 +427,7 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         unsigned long long htops[3];
         CK(cudaMemcpyAsync(&hst, status.p, 4, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(htops, tops.p, 24, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(out.stats, stats.p, 128, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(out.stats, stats.p, 256, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         out.pool_used = htops[0]; out.f_used = htops[1]; out.scratch_used = htops[2];
         if (hst == ST_OK) break;
@@ -555,7 +555,7 @@ void finish_handle(parac_factor_s *h, int64_t n, int64_t nnzF, const Opts &O)
 
 std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_index)
 {
-    char buf[2048];
+    char buf[3072];
     snprintf(buf, sizeof buf,
              "{\"n\": %lld, \"nnz_F\": %lld, \"nnz_G\": %lld, \"labels\": %lld, \"nnz_lower_input\": %lld, "
              "\"fill_entries\": %llu, \"pool_entries_used\": %llu, \"factor_entries_used\": %llu, "
@@ -565,12 +565,16 @@ std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_ind
              "\"warps_per_block\": %d, \"precision\": %d, \"system\": %d, \"t_ingest_ms\": %.4f, "
              "\"t_elim_ms\": %.4f, \"t_compact_ms\": %.4f, \"depth\": %d, \"cycles\": {\"wait\": %llu, "
              "\"gather\": %llu, \"sort_merge\": %llu, \"store_sort_scan\": %llu, \"sample_append\": %llu, "
-             "\"release\": %llu, \"reg_weight_sort\": %llu, \"reg_scan\": %llu}}",
+             "\"release\": %llu, \"reg_weight_sort\": %llu, \"reg_scan\": %llu, \"coop_join\": %llu, "
+             "\"coop_gather\": %llu, \"coop_row_sort\": %llu, \"coop_merge_store\": %llu, "
+             "\"coop_weight_sort\": %llu, \"coop_scan\": %llu, \"coop_sample_append\": %llu, "
+             "\"coop_release\": %llu}}",
              (long long)h->n, (long long)h->nnzF, (long long)(h->nnzF + h->n), (long long)fo.nl,
              (long long)fo.nnz_low, fo.stats[3], fo.pool_used, fo.f_used, fo.scratch_used, fo.stats[0], fo.stats[1],
              fo.stats[2], fo.stats[5], fo.stats[6], fo.stats[4], fo.regrows, fo.blocks, fo.warps, h->prec, sys_index, fo.t_ingest, fo.t_elim,
              fo.t_compact, h->depth, fo.stats[8], fo.stats[9], fo.stats[10], fo.stats[11], fo.stats[12],
-             fo.stats[13], fo.stats[14], fo.stats[15]);
+             fo.stats[13], fo.stats[14], fo.stats[15], fo.stats[16], fo.stats[17], fo.stats[18], fo.stats[19],
+             fo.stats[20], fo.stats[21], fo.stats[22], fo.stats[23]);
     return buf;
 }
 

@@ -174,7 +174,7 @@ struct WarpState {
     unsigned long long fcur, fend;     // factor-workspace chunk owned by this warp
     unsigned long long sbase, scap;    // global scratch owned by this warp (bytes)
     unsigned long long n_reg, n_warp, n_block, n_global, n_fill, n_handoff;
-    unsigned long long cyc[8];         // per-phase cycles (profiling runs only)
+    unsigned long long cyc[16];        // per-phase cycles (profiling runs only)
     long long t_mark;
     int fchunk;
 };
@@ -182,7 +182,9 @@ struct WarpState {
 // Per-phase cycle accounting, active only when the launch asks for it:
 // 0 queue wait, 1 gather, 2 sort + merge, 3 store (+ weight sort + scan on
 // the shared-memory path), 4 sampling + append, 5 levels + release +
-// decrements, 6 register weight sort, 7 register scan.
+// decrements, 6 register weight sort, 7 register scan; cooperative path (as
+// seen by the requesting warp): 8 join, 9 gather, 10 row sort, 11 merge +
+// store, 12 weight sort, 13 scan, 14 sampling + append, 15 release.
 __device__ __forceinline__ void prof_mark(const ElimArgs &a, WarpState &ws, int phase)
 {
     if (a.profile) {
@@ -726,45 +728,81 @@ __device__ bool cta_barrier(CoopShared &cs, const ElimArgs &a)
     return __shfl_sync(FULL, ok, 0) != 0;
 }
 
-__device__ void coop_sort_row_bits(View v, int P)
+// One compare-exchange of the bitonic network: entries i < l = i + j of
+// direction asc (ascending when (i & block) == 0).  KEY 0 orders by (row,
+// weight bits), KEY 1 by (weight bits, row) and carries the multiplicity.
+template <int KEY>
+__device__ __forceinline__ void cex(View v, int i, int l, bool asc)
 {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int kk = 2; kk <= P; kk <<= 1) {
-        for (int j = kk >> 1; j > 0; j >>= 1) {
-            for (int t = tid; t < (P >> 1); t += nt) {
-                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
-                const int l = i + j;
-                const bool asc = (i & kk) == 0;
-                const int32_t ri = v.row[i], rl = v.row[l];
-                const double wi = v.w[i], wl = v.w[l];
-                const bool gt = (ri > rl) || (ri == rl && dbits(wi) > dbits(wl));
-                if (gt == asc) { v.row[i] = rl; v.row[l] = ri; v.w[i] = wl; v.w[l] = wi; }
-            }
-            __syncthreads();
-        }
+    const int32_t ri = v.row[i], rl = v.row[l];
+    const double wi = v.w[i], wl = v.w[l];
+    const unsigned long long bi = dbits(wi), bl = dbits(wl);
+    const bool gt = KEY == 0 ? ((ri > rl) || (ri == rl && bi > bl)) : ((bi > bl) || (bi == bl && ri > rl));
+    if (gt == asc) {
+        v.row[i] = rl; v.row[l] = ri; v.w[i] = wl; v.w[l] = wi;
+        if (KEY == 1) { const int32_t mi = v.mult[i], ml = v.mult[l]; v.mult[i] = ml; v.mult[l] = mi; }
     }
 }
 
-__device__ void coop_sort_bits_row(View v, int P)
+// Block-wide bitonic sort of P entries of v (a power of two).  When v lives
+// in global memory and P exceeds the shared tile (T entries, a power of two),
+// the stages with stride below T run on T-entry tiles staged in shared
+// memory: tiles are sorted first, then every merge block of size kk > T runs
+// its strides >= T on global memory and its strides < T tile by tile.  This
+// is the same network (the direction of an exchange depends on the global
+// index), so the result is identical; it only moves fewer bytes.
+template <int KEY>
+__device__ void coop_sort(View v, int P, View tile, int T)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int kk = 2; kk <= P; kk <<= 1) {
-        for (int j = kk >> 1; j > 0; j >>= 1) {
-            for (int t = tid; t < (P >> 1); t += nt) {
-                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
-                const int l = i + j;
-                const bool asc = (i & kk) == 0;
-                const double wi = v.w[i], wl = v.w[l];
-                const int32_t ri = v.row[i], rl = v.row[l];
-                const unsigned long long bi = dbits(wi), bl = dbits(wl);
-                const bool gt = (bi > bl) || (bi == bl && ri > rl);
-                if (gt == asc) {
-                    const int32_t mi = v.mult[i], ml = v.mult[l];
-                    v.row[i] = rl; v.row[l] = ri; v.w[i] = wl; v.w[l] = wi; v.mult[i] = ml; v.mult[l] = mi;
+    if (T <= 0 || P <= T) {
+        for (int kk = 2; kk <= P; kk <<= 1) {
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int t = tid; t < (P >> 1); t += nt) {
+                    const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+                    cex<KEY>(v, i, i + j, (i & kk) == 0);
                 }
+                __syncthreads();
+            }
+        }
+        return;
+    }
+    // strides below T of merge blocks up to kk_hi, on shared tiles
+    auto tile_pass = [&](int kk_lo, int kk_hi) {
+        for (int base = 0; base < P; base += T) {
+            for (int i = tid; i < T; i += nt) {
+                tile.row[i] = v.row[base + i];
+                tile.w[i] = v.w[base + i];
+                if (KEY == 1) tile.mult[i] = v.mult[base + i];
+            }
+            __syncthreads();
+            for (int kk = kk_lo; kk <= kk_hi; kk <<= 1) {
+                for (int j = (kk >> 1) < T ? (kk >> 1) : (T >> 1); j > 0; j >>= 1) {
+                    for (int t = tid; t < (T >> 1); t += nt) {
+                        const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+                        cex<KEY>(tile, i, i + j, ((base + i) & kk) == 0);
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int i = tid; i < T; i += nt) {
+                v.row[base + i] = tile.row[i];
+                v.w[base + i] = tile.w[i];
+                if (KEY == 1) v.mult[base + i] = tile.mult[i];
             }
             __syncthreads();
         }
+    };
+    tile_pass(2, T);                                  // every tile sorted (direction by global index)
+    for (int kk = 2 * T; kk <= P; kk <<= 1) {
+        for (int j = kk >> 1; j >= T; j >>= 1) {      // large strides on global memory
+            for (int t = tid; t < (P >> 1); t += nt) {
+                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+                cex<KEY>(v, i, i + j, (i & kk) == 0);
+            }
+            __syncthreads();
+        }
+        tile_pass(kk, kk);                            // strides below T of this merge block
     }
 }
 
@@ -780,6 +818,7 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     __syncthreads();
     const int32_t k = cs.k;
     const bool requester = warp == cs.req_warp;
+    if (requester) prof_mark(a, ws, 8);
     const int64_t o0 = __ldg(a.lcp + k), o1 = __ldg(a.lcp + k + 1);
     const int32_t norig = (int32_t)(o1 - o0);
     const uint32_t cnt = __ldcg(a.fcnt + k);
@@ -833,9 +872,13 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     for (int i = g + tid; i < P; i += nt) { v.row[i] = ROW_SENTINEL; v.w[i] = 0.0; }
     __syncthreads();
     if (read_status(a.status) != ST_OK) { __syncthreads(); if (tid == 0) cs.k = -1; return -2; }
+    if (requester) prof_mark(a, ws, 9);
 
     // ---------------------------------------------------------------- sort + merge (in place)
-    coop_sort_row_bits(v, P);
+    const bool global_ws = P > a.block_cap;
+    const View tile = make_view(bbuf, a.block_cap);
+    coop_sort<0>(v, P, tile, global_ws ? a.block_cap : 0);
+    if (requester) prof_mark(a, ws, 10);
     int d = 0;
     for (int base = 0; base < g; base += nt) {
         const int i = base + tid;
@@ -886,7 +929,9 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
         v.row[i] = ROW_SENTINEL; v.w[i] = __longlong_as_double((long long)WBITS_SENTINEL); v.mult[i] = 0;
     }
     __syncthreads();
-    coop_sort_bits_row(v, P2);
+    if (requester) prof_mark(a, ws, 11);
+    coop_sort<1>(v, P2, tile, global_ws ? a.block_cap : 0);
+    if (requester) prof_mark(a, ws, 12);
 
     // ---------------------------------------------------------------- canonical suffix scan
     // each 32-lane tile of the reversed weights: Hillis-Steele within the tile
@@ -945,8 +990,21 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     __syncthreads();
     const double Dk = v.S[0];
     if (tid == 0) a.D[k] = Dk;
+    if (requester) prof_mark(a, ws, 13);
 
     // ---------------------------------------------------------------- sample clique tree + append
+    // For a working set in global memory, a coarse copy of M (every
+    // stride-th value) in shared memory narrows each search to one stride of
+    // global values.  M is non-increasing and M[p] >= R, so the largest j
+    // with M[j] >= R over the whole list is the one searched for in [p, d).
+    int stride = 1, ncoarse = 0;
+    unsigned long long *coarse = (unsigned long long *)tile.w;
+    if (global_ws) {
+        stride = (d + a.block_cap - 1) / a.block_cap;
+        ncoarse = (d + stride - 1) / stride;
+        for (int c = tid; c < ncoarse; c += nt) coarse[c] = dbits(v.M[c * stride]);
+        __syncthreads();
+    }
     uint64_t klocal, sys;
     sys_of(a, k, klocal, sys);
     bool ok = true;
@@ -961,6 +1019,16 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
             const double Sp = v.S[p];
             const unsigned long long Rb = dbits(__dmul_rn(Sp, slot_uniform(a.seed, klocal, (uint64_t)p, sys)));
             int lo_j = p, hi_j = d - 1;
+            if (global_ws) {                       // largest coarse index c with M[c * stride] >= R
+                int clo = 0, chi = ncoarse - 1;
+                while (clo < chi) {
+                    const int mid = clo + ((chi - clo + 1) >> 1);
+                    if (coarse[mid] >= Rb) clo = mid; else chi = mid - 1;
+                }
+                const int jl = clo * stride, jh = (clo + 1) * stride - 1 < d - 1 ? (clo + 1) * stride - 1 : d - 1;
+                lo_j = jl > p ? jl : p;
+                hi_j = jh;
+            }
             while (lo_j < hi_j) {
                 const int mid = lo_j + ((hi_j - lo_j + 1) >> 1);
                 if (dbits(v.M[mid]) >= Rb) lo_j = mid; else hi_j = mid - 1;
@@ -973,6 +1041,7 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
         if (!append_fill(a, act, lo, hi, c)) { ok = false; break; }
     }
     if (tid == 0) ws.n_fill += (unsigned long long)(d - 1);
+    if (requester) prof_mark(a, ws, 14);
 
     // ---------------------------------------------------------------- levels, release, decrements
     {
@@ -991,6 +1060,7 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     }
     __syncthreads();
     if (tid == 0) cs.k = -1;
+    if (requester) prof_mark(a, ws, 15);
     return requester ? (keep >= 0 ? keep : -1) : -1;
 }
 
@@ -1027,7 +1097,7 @@ __global__ void __launch_bounds__(256, 2) elim_kernel(ElimArgs a, int fchunk)
     WarpState ws;
     ws.fcur = ws.fend = 0; ws.sbase = 0; ws.scap = 0;
     ws.n_reg = ws.n_warp = ws.n_block = ws.n_global = ws.n_fill = ws.n_handoff = 0;
-    for (int i = 0; i < 8; ++i) ws.cyc[i] = 0;
+    for (int i = 0; i < 16; ++i) ws.cyc[i] = 0;
     ws.t_mark = 0;
     ws.fchunk = fchunk;
     prof_mark(a, ws, -1);
@@ -1113,6 +1183,7 @@ __global__ void __launch_bounds__(256, 2) elim_kernel(ElimArgs a, int fchunk)
         } else {
             // post the request (or help the one already posted, then retry)
             r = -3;
+            prof_mark(a, ws, 1);
             while (r == -3) {
                 int posted = 0;
                 if (lane == 0 && atomicCAS(&cs.k, -1, k) == -1) {
@@ -1162,7 +1233,7 @@ __global__ void __launch_bounds__(256, 2) elim_kernel(ElimArgs a, int fchunk)
         atomicAdd(a.stats + 4, spins_total);
         atomicAdd(a.stats + 5, ws.n_reg);
         atomicAdd(a.stats + 6, ws.n_handoff);
-        for (int i = 0; i < 8; ++i) atomicAdd(a.stats + 8 + i, ws.cyc[i]);
+        for (int i = 0; i < 16; ++i) atomicAdd(a.stats + 8 + i, ws.cyc[i]);
     }
 }
 

@@ -220,8 +220,8 @@ def parac_factor_export(G):
 
 
 def parac_factor_stats(G):
-    buf = C.create_string_buffer(4096)
-    _check(_lib.parac_factor_stats(G.handle, buf, 4096), "parac_factor_stats")
+    buf = C.create_string_buffer(8192)
+    _check(_lib.parac_factor_stats(G.handle, buf, 8192), "parac_factor_stats")
     return json.loads(buf.value.decode())
 
 
