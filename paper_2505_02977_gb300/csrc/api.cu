@@ -20,7 +20,16 @@ using namespace parac;
 
 namespace parac {
 static unsigned long long g_launches = 0;
-void count_launches(unsigned n) { __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+// launches recorded into a graph being captured by this thread are counted
+// here instead, and added to the total at each replay
+static thread_local unsigned long long *t_capture_count = nullptr;
+void count_launches(unsigned n)
+{
+    if (t_capture_count) *t_capture_count += n;
+    else __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED);
+}
+void count_graph_launches(unsigned long long n) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
+void capture_launch_counts(unsigned long long *acc) { t_capture_count = acc; }
 unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 }  // namespace parac
 
@@ -164,6 +173,52 @@ struct SolveCache {
     PcgBuffers B{};
 };
 
+// Buffers of the block (several right-hand sides) PCG: row-major n x nrhs.
+struct BlockCache {
+    int32_t n = -1, nrhs = 0, prec = 0, pstride = 0;
+    DBuf x, r, z, p, q, b, y, zl, partials, state;
+    DBuf gs_f, gs_b;                 // SpTRSM row groups (depend on the factor and the warps per block)
+    int32_t ng_f = 0, ng_b = 0, g_warps = 0;
+    BlockBuffers B{};
+};
+
+// A captured CUDA graph of `check_every` PCG iterations, replayed until the
+// run stops.  The key holds every pointer and scalar baked into the captured
+// launches; any change re-captures.
+struct GraphCache {
+    static constexpr int KEY = 24;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches = 0;     // kernel launches in one replay
+    uint64_t key[KEY] = {0};
+    GraphCache() = default;
+    GraphCache(const GraphCache &) = delete;
+    GraphCache &operator=(const GraphCache &) = delete;
+    void reset()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        launches = 0;
+    }
+    ~GraphCache() { reset(); }
+};
+
+// The solves run on a stream of the library's own (joined to the handle's
+// stream by events), so that graph capture never touches a caller's or the
+// legacy default stream.
+struct SolveStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t in = nullptr, out = nullptr;
+    SolveStream() = default;
+    SolveStream(const SolveStream &) = delete;
+    SolveStream &operator=(const SolveStream &) = delete;
+    ~SolveStream()
+    {
+        if (s) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+        if (in) cudaEventDestroy(in);
+        if (out) cudaEventDestroy(out);
+    }
+};
+
 struct parac_factor_s {
     int device = 0;
     int64_t n = 0;
@@ -181,7 +236,10 @@ struct parac_factor_s {
     int64_t nnzL = 0;
     std::string stats;
     SolveCache cache;
+    BlockCache bcache;
     DBuf status;
+    SolveStream sstream;
+    GraphCache graph;
 };
 
 namespace {
@@ -929,6 +987,224 @@ int32_t read_dev_status(parac_factor_s *G, cudaStream_t st)
     return s;
 }
 
+void ensure_block_cache(parac_factor_s *G, const SolveArgs &A, int nrhs, cudaStream_t st)
+{
+    BlockCache &c = G->bcache;
+    int vb = (int)std::min<int64_t>((G->n * 32 + 255) / 256, (int64_t)num_sms() * 8);
+    if (vb < 1) vb = 1;
+    const int pstride = std::max(vb, A.trsv_blocks);
+    if (c.n == (int32_t)G->n && c.nrhs == nrhs && c.prec == G->prec && c.pstride >= pstride) return;
+    const size_t m = (size_t)std::max<int64_t>(G->n, 1) * nrhs;
+    c.x = dalloc<double>(m, st); c.r = dalloc<double>(m, st); c.z = dalloc<double>(m, st);
+    c.p = dalloc<double>(m, st); c.q = dalloc<double>(m, st); c.b = dalloc<double>(m, st);
+    if (G->prec == 32) { c.y = dalloc<float>(m, st); c.zl = dalloc<float>(m, st); }
+    else { c.y = dalloc<double>(m, st); c.zl = dalloc<double>(m, st); }
+    c.partials = dalloc<double>((size_t)3 * 32 * pstride, st);
+    c.state = DBuf(block_state_bytes(), st);
+    BlockBuffers &B = c.B;
+    B = BlockBuffers{};
+    B.x = c.x.as<double>(); B.r = c.r.as<double>(); B.z = c.z.as<double>(); B.p = c.p.as<double>();
+    B.q = c.q.as<double>(); B.b = c.b.as<double>();
+    if (G->prec == 32) { B.yl32 = c.y.as<float>(); B.zl32 = c.zl.as<float>(); }
+    else { B.yl64 = c.y.as<double>(); B.zl64 = c.zl.as<double>(); }
+    B.partials = c.partials.as<double>();
+    B.state = (BlockState *)c.state.p;
+    B.nrhs = nrhs; B.vec_blocks = vb; B.pstride = pstride;
+    c.n = (int32_t)G->n; c.nrhs = nrhs; c.prec = G->prec; c.pstride = pstride;
+}
+
+// Row groups of the block triangular solves, built once per handle (and
+// warps per block) from the relabelled factor's row and column pointers.
+void ensure_block_groups(parac_factor_s *G, int warps, cudaStream_t st)
+{
+    BlockCache &c = G->bcache;
+    if (c.g_warps != warps) {
+        const size_t n = (size_t)G->n;
+        std::vector<int64_t> rp(n + 1), cp(n + 1);
+        CK(cudaMemcpyAsync(rp.data(), G->Srp.p, 8 * (n + 1), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(cp.data(), G->Scp.p, 8 * (n + 1), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const std::vector<int32_t> gf = row_groups(rp, false, warps), gb = row_groups(cp, true, warps);
+        c.gs_f = dalloc<int32_t>(gf.size(), st);
+        c.gs_b = dalloc<int32_t>(gb.size(), st);
+        CK(cudaMemcpyAsync(c.gs_f.p, gf.data(), 4 * gf.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c.gs_b.p, gb.data(), 4 * gb.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));       // the host vectors go out of scope
+        c.ng_f = (int32_t)gf.size() - 1;
+        c.ng_b = (int32_t)gb.size() - 1;
+        c.g_warps = warps;
+    }
+    c.B.gs_f = c.gs_f.as<int32_t>(); c.B.gs_b = c.gs_b.as<int32_t>();
+    c.B.ng_f = c.ng_f; c.B.ng_b = c.ng_b;
+}
+
+// The library's own solve stream for this handle, made to wait for the work
+// already queued on the handle's stream.
+cudaStream_t enter_solve_stream(parac_factor_s *G)
+{
+    SolveStream &ss = G->sstream;
+    if (!ss.s) {
+        CK(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ss.in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ss.out, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(ss.in, G->stream));
+    CK(cudaStreamWaitEvent(ss.s, ss.in, 0));
+    return ss.s;
+}
+
+// ... and the handle's stream made to wait for the solve stream's work.
+void leave_solve_stream(parac_factor_s *G)
+{
+    SolveStream &ss = G->sstream;
+    CK(cudaEventRecord(ss.out, ss.s));
+    CK(cudaStreamWaitEvent(G->stream, ss.out, 0));
+}
+
+bool graphs_enabled()
+{
+    const char *e = getenv("PARAC_GRAPH");
+    return !(e && e[0] == '0');
+}
+
+// Run `iters` iterations given by `launch(stream)`: replay the cached graph
+// if its key matches, else capture a new one (or launch directly when graphs
+// are switched off).
+template <class Launch>
+cudaError_t run_iterations(parac_factor_s *G, const uint64_t (&key)[GraphCache::KEY], Launch &&launch,
+                           cudaStream_t ps)
+{
+    if (!graphs_enabled()) return launch(ps);
+    GraphCache &gc = G->graph;
+    if (!gc.exec || memcmp(gc.key, key, sizeof key) != 0) {
+        gc.reset();
+        cudaGraph_t g = nullptr;
+        unsigned long long nk = 0;
+        cudaError_t e = cudaStreamBeginCapture(ps, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        capture_launch_counts(&nk);
+        const cudaError_t le = launch(ps);
+        capture_launch_counts(nullptr);
+        e = cudaStreamEndCapture(ps, &g);
+        if (le != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return le != cudaSuccess ? le : e;
+        }
+        e = cudaGraphInstantiate(&gc.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { gc.exec = nullptr; return e; }
+        memcpy(gc.key, key, sizeof key);
+        gc.launches = nk;
+    }
+    cudaError_t e = cudaGraphLaunch(gc.exec, ps);
+    if (e == cudaSuccess) count_graph_launches(gc.launches);
+    return e;
+}
+
+void graph_key(uint64_t (&k)[GraphCache::KEY], const SolveArgs &A, int form, int nrhs, int iters, const void *x,
+               const void *y, const void *partials, const void *state, int vec_blocks, int pstride)
+{
+    memset(k, 0, sizeof k);
+    int i = 0;
+    k[i++] = (uint64_t)form; k[i++] = (uint64_t)nrhs; k[i++] = (uint64_t)iters;
+    k[i++] = (uint64_t)(uintptr_t)A.Lp; k[i++] = (uint64_t)(uintptr_t)A.Li; k[i++] = (uint64_t)(uintptr_t)A.Lv;
+    k[i++] = (uint64_t)(uintptr_t)A.Fcp; k[i++] = (uint64_t)(uintptr_t)A.Frp;
+    k[i++] = (uint64_t)A.n; k[i++] = (uint64_t)A.prec; k[i++] = (uint64_t)A.lanes_spmv; k[i++] = (uint64_t)A.lanes_trsv;
+    k[i++] = (uint64_t)A.trsv_blocks; k[i++] = (uint64_t)A.trsv_warps; k[i++] = (uint64_t)A.spin_limit;
+    k[i++] = (uint64_t)(uintptr_t)A.status; k[i++] = (uint64_t)(uintptr_t)A.trace;
+    k[i++] = (uint64_t)(uintptr_t)x; k[i++] = (uint64_t)(uintptr_t)y; k[i++] = (uint64_t)(uintptr_t)partials;
+    k[i++] = (uint64_t)(uintptr_t)state; k[i++] = (uint64_t)vec_blocks; k[i++] = (uint64_t)pstride;
+}
+
+// One right-hand side: B, X are n-vectors on the device.
+parac_status pcg_single(parac_factor_s *G, const SolveArgs &A, const double *b, double *x, double tol, int32_t maxit,
+                        cudaStream_t ps, int32_t *iters, double *relres, bool *converged)
+{
+    PcgBuffers &Bf = G->cache.B;
+    CK(cudaMemcpyAsync(Bf.b, b, 8 * (size_t)A.n, cudaMemcpyDeviceToDevice, ps));
+    CK(pcg_init(A, Bf, tol, maxit, ps));
+    uint64_t key[GraphCache::KEY];
+    graph_key(key, A, 1, 1, G->check_every, Bf.x, Bf.yl64 ? (const void *)Bf.yl64 : (const void *)Bf.yl32,
+              Bf.partials, Bf.state, Bf.vec_blocks, Bf.pstride);
+    const int every = G->check_every;
+    auto step = [&](cudaStream_t s) -> cudaError_t {
+        for (int c = 0; c < every; ++c) {
+            cudaError_t e = pcg_iteration(A, Bf, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    PcgHostState hs{};
+    for (;;) {
+        CK(run_iterations(G, key, step, ps));
+        CK(pcg_read_state(Bf, &hs, ps));
+        if (read_dev_status(G, ps) != ST_OK) return PARAC_ETIMEOUT;
+        if (!hs.done) continue;
+        CK(pcg_true_residual(A, Bf, ps));
+        CK(pcg_read_state(Bf, &hs, ps));
+        const bool ok = hs.true_rr <= tol * tol * hs.bb;
+        if (ok || hs.iters >= maxit || hs.bb == 0.0) break;
+        CK(pcg_clear_done(Bf, ps));
+        CK(pcg_resume(A, Bf, ps));
+    }
+    if (read_dev_status(G, ps) != ST_OK) return PARAC_ETIMEOUT;
+    CK(cudaMemcpyAsync(x, Bf.x, 8 * (size_t)A.n, cudaMemcpyDeviceToDevice, ps));
+    *iters = hs.iters;
+    *relres = hs.bb > 0.0 ? std::sqrt(hs.true_rr / hs.bb) : 0.0;
+    *converged = hs.true_rr <= tol * tol * hs.bb || hs.bb == 0.0;
+    return PARAC_OK;
+}
+
+// Several right-hand sides: Bcm / Xcm are device n x nrhs column-major with
+// leading dimensions ldb / ldx.
+parac_status pcg_block(parac_factor_s *G, SolveArgs A, int nrhs, const double *Bcm, int64_t ldb, double *Xcm,
+                       int64_t ldx, double tol, int32_t maxit, cudaStream_t st, cudaStream_t ps, int32_t *iters,
+                       double *relres, bool *all_conv)
+{
+    // the SpTRSM kernels' own co-residency bound
+    const int bps = std::max(1, btrsm_blocks_per_sm(A.trsv_warps, A.prec));
+    A.trsv_blocks = std::min(A.trsv_blocks, num_sms() * bps);
+    ensure_block_cache(G, A, nrhs, st);
+    ensure_block_groups(G, A.trsv_warps, st);
+    const BlockBuffers &B = G->bcache.B;
+    CK(bpack((int32_t)A.n, nrhs, Bcm, ldb, B.b, ps));
+    CK(bpcg_init(A, B, tol, maxit, ps));
+    uint64_t key[GraphCache::KEY];
+    graph_key(key, A, 2, nrhs, G->check_every, B.x, B.yl64 ? (const void *)B.yl64 : (const void *)B.yl32,
+              B.partials, B.state, B.vec_blocks, B.pstride);
+    const int every = G->check_every;
+    auto step = [&](cudaStream_t s) -> cudaError_t {
+        for (int c = 0; c < every; ++c) {
+            cudaError_t e = bpcg_iteration(A, B, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    BlockHostState hs{};
+    for (;;) {
+        CK(run_iterations(G, key, step, ps));
+        CK(bpcg_read_state(B, &hs, ps));
+        if (read_dev_status(G, ps) != ST_OK) return PARAC_ETIMEOUT;
+        if (!hs.all_done) continue;
+        CK(bpcg_true_residual(A, B, ps));
+        CK(bpcg_read_state(B, &hs, ps));
+        bool reopen = false;
+        for (int j = 0; j < nrhs; ++j)
+            if (hs.converged[j] && !(hs.true_rr[j] <= tol * tol * hs.bb[j]) && hs.iters[j] < maxit) reopen = true;
+        if (!reopen) break;
+        CK(bpcg_reopen(A, B, ps));
+    }
+    if (read_dev_status(G, ps) != ST_OK) return PARAC_ETIMEOUT;
+    CK(bunpack((int32_t)A.n, nrhs, B.x, Xcm, ldx, ps));
+    *all_conv = true;
+    for (int j = 0; j < nrhs; ++j) {
+        iters[j] = hs.iters[j];
+        relres[j] = hs.bb[j] > 0.0 ? std::sqrt(hs.true_rr[j] / hs.bb[j]) : 0.0;
+        if (!(hs.true_rr[j] <= tol * tol * hs.bb[j]) && hs.bb[j] > 0.0) *all_conv = false;
+    }
+    return PARAC_OK;
+}
+
 }  // namespace
 
 extern "C" parac_status parac_pcg(parac_factor_t G, int64_t n, const int64_t *colptr, const int32_t *rowind,
@@ -963,37 +1239,58 @@ extern "C" parac_status parac_pcg(parac_factor_t G, int64_t n, const int64_t *co
             return PARAC_OK;
         }
         SolveArgs A = solve_args(G, Lp, Li, Lv, nnzL);
-        ensure_cache(G, A, st);
-        PcgBuffers &Bf = G->cache.B;
-        CK(cudaMemsetAsync(G->status.p, 0, 4, st));
         const bool bdev = is_device_ptr(B), xdev = is_device_ptr(X);
-        bool all_conv = true;
-        for (int j = 0; j < nrhs; ++j) {
-            CK(cudaMemcpyAsync(Bf.b, B + (size_t)j * ldb, 8 * (size_t)n,
-                               bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-            CK(pcg_init(A, Bf, tol, maxit, st));
-            PcgHostState hs{};
-            for (;;) {
-                for (int c = 0; c < G->check_every; ++c) CK(pcg_iteration(A, Bf, st));
-                CK(pcg_read_state(Bf, &hs, st));
-                if (read_dev_status(G, st) != ST_OK) { set_err("triangular solve wait exceeded the spin limit"); return PARAC_ETIMEOUT; }
-                if (!hs.done) continue;
-                CK(pcg_true_residual(A, Bf, st));
-                CK(pcg_read_state(Bf, &hs, st));
-                const bool ok = hs.true_rr <= tol * tol * hs.bb;
-                if (ok || hs.iters >= maxit || hs.bb == 0.0) break;
-                CK(pcg_clear_done(Bf, st));
-                CK(pcg_resume(A, Bf, st));
-            }
-            if (read_dev_status(G, st) != ST_OK) { set_err("triangular solve wait exceeded the spin limit"); return PARAC_ETIMEOUT; }
-            CK(cudaMemcpyAsync(X + (size_t)j * ldx, Bf.x, 8 * (size_t)n,
-                               xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-            const double rel = hs.bb > 0.0 ? std::sqrt(hs.true_rr / hs.bb) : 0.0;
-            if (iters) iters[j] = hs.iters;
-            if (true_relres) true_relres[j] = rel;
-            if (!(hs.true_rr <= tol * tol * hs.bb) && hs.bb > 0.0) all_conv = false;
+        // right-hand sides and solutions on the device, column-major
+        DBuf Bstage, Xstage;
+        const double *Bd = B;
+        double *Xd = X;
+        int64_t ldbd = ldb, ldxd = ldx;
+        if (!bdev) {
+            Bstage = dalloc<double>((size_t)n * nrhs, st);
+            CK(cudaMemcpy2DAsync(Bstage.p, 8 * (size_t)n, B, 8 * (size_t)ldb, 8 * (size_t)n, (size_t)nrhs,
+                                 cudaMemcpyHostToDevice, st));
+            Bd = Bstage.as<double>(); ldbd = n;
         }
+        if (!xdev) { Xstage = dalloc<double>((size_t)n * nrhs, st); Xd = Xstage.as<double>(); ldxd = n; }
+        CK(cudaMemsetAsync(G->status.p, 0, 4, st));
+        std::vector<int32_t> it(nrhs, 0);
+        std::vector<double> rel(nrhs, 0.0);
+        bool all_conv = true;
+        parac_status rs = PARAC_OK;
+        if (nrhs == 1) {
+            ensure_cache(G, A, st);
+            cudaStream_t ps = enter_solve_stream(G);
+            bool conv = true;
+            rs = pcg_single(G, A, Bd, Xd, tol, maxit, ps, &it[0], &rel[0], &conv);
+            all_conv = conv;
+            leave_solve_stream(G);
+        } else {
+            cudaStream_t ps = nullptr;
+            {
+                // buffers are allocated on the handle's stream before the join
+                const int bps = std::max(1, btrsm_blocks_per_sm(A.trsv_warps, A.prec));
+                SolveArgs Ab = A;
+                Ab.trsv_blocks = std::min(A.trsv_blocks, num_sms() * bps);
+                ensure_block_cache(G, Ab, nrhs, st);
+                ensure_block_groups(G, A.trsv_warps, st);
+            }
+            ps = enter_solve_stream(G);
+            rs = pcg_block(G, A, nrhs, Bd, ldbd, Xd, ldxd, tol, maxit, st, ps, it.data(), rel.data(), &all_conv);
+            leave_solve_stream(G);
+        }
+        if (rs == PARAC_ETIMEOUT) {
+            CK(cudaStreamSynchronize(st));
+            set_err("triangular solve wait exceeded the spin limit");
+            return PARAC_ETIMEOUT;
+        }
+        if (!xdev)
+            CK(cudaMemcpy2DAsync(X, 8 * (size_t)ldx, Xd, 8 * (size_t)n, 8 * (size_t)n, (size_t)nrhs,
+                                 cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        for (int j = 0; j < nrhs; ++j) {
+            if (iters) iters[j] = it[j];
+            if (true_relres) true_relres[j] = rel[j];
+        }
         if (!all_conv) { set_err("PCG reached maxit"); return PARAC_ENOCONV; }
         return PARAC_OK;
     });

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <vector>
 
 namespace parac {
 
@@ -11,6 +12,8 @@ struct ElimArgs;
 
 // Process-wide count of kernels launched by the library (diagnostics).
 void count_launches(unsigned n);
+void count_graph_launches(unsigned long long n);
+void capture_launch_counts(unsigned long long *acc);   // nullptr: count globally again
 unsigned long long launch_count();
 
 // ---------------------------------------------------------------- scan.cu
@@ -138,6 +141,41 @@ cudaError_t pcg_read_state(const PcgBuffers &B, PcgHostState *h, cudaStream_t st
 cudaError_t pcg_clear_done(const PcgBuffers &B, cudaStream_t st);
 cudaError_t pcg_resume(const SolveArgs &A, const PcgBuffers &B, cudaStream_t st);
 cudaError_t precond_apply(const SolveArgs &A, const PcgBuffers &B, const double *r, double *z, cudaStream_t st);
+// ---------------------------------------------------------------- block.cu
+// PCG on nrhs <= 32 right-hand sides at once: row-major n x nrhs blocks, one
+// lane per column, per-column scalars and stopping.
+struct BlockState;
+struct BlockBuffers {
+    double *x, *r, *z, *p, *q, *b;  // [n * nrhs] row-major
+    double *yl64, *zl64;            // [n * nrhs] position-space unknowns (FP64 apply)
+    float *yl32, *zl32;             // [n * nrhs] (FP32 apply)
+    double *partials;               // [3 * 32 * pstride]
+    BlockState *state;
+    const int32_t *gs_f, *gs_b;     // row groups of the forward / backward SpTRSM
+    int32_t ng_f, ng_b;
+    int32_t nrhs;
+    int32_t vec_blocks;             // grid of the vector kernels
+    int32_t pstride;                // >= max(vec_blocks, trsv grid)
+};
+struct BlockHostState {
+    int32_t all_done;
+    int32_t iters[32], converged[32], done[32];
+    double bb[32], true_rr[32];
+};
+size_t block_state_bytes();
+// Row groups of the SpTRSM schedule over positions in ascending (forward) or
+// descending (backward) order: gs[g]..gs[g+1] is either up to `warps` rows of
+// at most LONG_ROW entries or a single longer row.  ptr = row pointers [n+1].
+std::vector<int32_t> row_groups(const std::vector<int64_t> &ptr, bool descending, int warps);
+int btrsm_blocks_per_sm(int warps, int prec);
+cudaError_t bpack(int32_t n, int nrhs, const double *B, int64_t ldb, double *Bt, cudaStream_t st);
+cudaError_t bunpack(int32_t n, int nrhs, const double *Xt, double *X, int64_t ldx, cudaStream_t st);
+cudaError_t bpcg_init(const SolveArgs &A, const BlockBuffers &B, double tol, int32_t maxit, cudaStream_t st);
+cudaError_t bpcg_iteration(const SolveArgs &A, const BlockBuffers &B, cudaStream_t st);
+cudaError_t bpcg_true_residual(const SolveArgs &A, const BlockBuffers &B, cudaStream_t st);
+cudaError_t bpcg_reopen(const SolveArgs &A, const BlockBuffers &B, cudaStream_t st);
+cudaError_t bpcg_read_state(const BlockBuffers &B, BlockHostState *h, cudaStream_t st);
+
 // Allocation-free variant: work vectors in a fixed device array (n <= NOALLOC_MAX_N).
 constexpr int NOALLOC_MAX_N = 1 << 18;
 constexpr int NOALLOC_MAX_DEVICES = 64;

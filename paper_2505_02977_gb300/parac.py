@@ -157,23 +157,44 @@ def parac_factor_many(systems, seed=0, opts=None):
 
 
 def parac_pcg(G, n, colptr, rowind, val, B, tol=1e-8, maxit=1000, X=None, nrhs=None, allow_noconv=True):
-    """Solve L X = B; B and X column-major n x nrhs (numpy or torch).  Returns (X, iters, relres, status)."""
-    Bh = B
+    """Solve L X = B for nrhs <= 32 right-hand sides (PCG, Sec. V).
+
+    B is an n-vector or an (m, nrhs) array with m >= n (numpy, or a torch CUDA
+    tensor); column j is B[:n, j] and m is passed as the leading dimension.
+    X, if given, is an (mx, nrhs) Fortran-ordered numpy array or a torch
+    tensor of the same layout.  Returns (X, iters, relres, status); X has B's
+    kind and shape (n,) or (n, nrhs)."""
     if nrhs is None:
         nrhs = 1 if len(getattr(B, "shape", (n,))) == 1 else B.shape[1]
     if hasattr(B, "data_ptr"):
         import torch
-        Bd = B if nrhs == 1 else B.t().contiguous()       # column-major storage
+        Bd = B.reshape(-1, 1) if B.dim() == 1 else B
+        ldb = Bd.shape[0]
+        Bd = Bd.t().contiguous()                     # column-major storage
         if X is None:
-            X = torch.empty(nrhs * n, dtype=torch.float64, device=B.device)
+            X = torch.empty((nrhs, n), dtype=torch.float64, device=B.device)
+            ldx = n
+            Xv = X.t()
+        else:
+            ldx = X.shape[0] if X.dim() > 1 else n
+            Xv = X
+            X = X.t() if X.dim() > 1 else X
+            assert X.is_contiguous()
         pb, kb = Bd.data_ptr(), Bd
         px, kx = X.data_ptr(), X
+        Xout = Xv[:n] if nrhs > 1 else Xv.reshape(-1)[:n]
     else:
-        Bc = np.asfortranarray(np.asarray(Bh, np.float64).reshape(n, nrhs))
+        Ba = np.asarray(B, np.float64)
+        Ba = Ba.reshape(-1, 1) if Ba.ndim == 1 else Ba
+        ldb = Ba.shape[0]
+        Bc = np.asfortranarray(Ba)
         if X is None:
             X = np.zeros((n, nrhs), np.float64, order="F")
+        assert X.flags.f_contiguous and X.dtype == np.float64
+        ldx = X.shape[0]
         pb, kb = Bc.ctypes.data, Bc
         px, kx = X.ctypes.data, X
+        Xout = X[:n, 0] if nrhs == 1 else X[:n]
     keep = [kb, kx]
     ps = []
     for a, dt in ((colptr, np.int64), (rowind, np.int32), (val, np.float64)):
@@ -181,11 +202,9 @@ def parac_pcg(G, n, colptr, rowind, val, B, tol=1e-8, maxit=1000, X=None, nrhs=N
         ps.append(p); keep.append(k)
     iters = np.zeros(nrhs, np.int32)
     rel = np.zeros(nrhs, np.float64)
-    code = _lib.parac_pcg(G.handle, n, *ps, pb, nrhs, n, tol, maxit, px, n, iters.ctypes.data, rel.ctypes.data)
+    code = _lib.parac_pcg(G.handle, n, *ps, pb, nrhs, ldb, tol, maxit, px, ldx, iters.ctypes.data, rel.ctypes.data)
     _check(code, "parac_pcg", allow=(7,) if allow_noconv else ())
-    if not hasattr(X, "data_ptr") and nrhs == 1:
-        X = X[:, 0]
-    return X, iters, rel, STATUS[code]
+    return Xout, iters, rel, STATUS[code]
 
 
 def parac_precond_apply(G, r, z=None):

@@ -113,15 +113,85 @@ def test_fp32_factor_converges(P):
 
 
 def test_pcg_multiple_rhs(P):
+    """Block PCG on 5 right-hand sides: every column converges to 1e-8 within
+    one iteration of the oracle's single-vector PCG on that column, and after
+    the oracle's iteration count its iterate agrees with the oracle's to 1e-8
+    (reduction orders differ; see test_pcg_matches_oracle)."""
     A, perm, seed, _ = W.config("grid2d-64")
-    B = W.gaussian_rhs(A.n, 4, 9)
+    B = W.gaussian_rhs(A.n, 5, 9)
     G = _factor(P, A, perm, seed)
+    F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)
     X, it, rr, status = P.parac_pcg(G, A.n, None, None, None, B, tol=1e-8, maxit=500)
+    assert status == "PARAC_OK" and X.shape == (A.n, 5) and np.all(rr <= 1e-8)
+    kmin = None
+    for j in range(5):
+        xo, ito, rro = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, B[:, j], 1e-8, 500)
+        assert abs(int(it[j]) - ito) <= 1
+        kmin = ito if kmin is None else min(kmin, ito)
+    X2, it2, _, _ = P.parac_pcg(G, A.n, None, None, None, B, tol=0.0, maxit=kmin)
+    assert np.all(it2 == kmin)
+    for j in range(5):
+        xo, _, _ = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, B[:, j], 0.0, kmin)
+        xa, xb = X2[:, j] - X2[:, j].mean(), xo - xo.mean()
+        assert np.linalg.norm(xa - xb) <= 1e-8 * np.linalg.norm(xb)
+    G.free()
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_block_pcg_columns_independent(P, prec):
+    """32 right-hand sides (the maximum) with leading dimensions above n:
+    a column scaled by 2^20 gives exactly 2^20 times the other's iterate
+    (power-of-two scaling is exact in every step, so any mixing between the
+    lanes of different columns shows), a zero column stops at once with x = 0,
+    columns stop on their own counts, and the padding rows of X are left
+    untouched."""
+    A, perm, seed, _ = W.config("grid2d-64")
+    n, k = A.n, 32
+    B = np.zeros((n + 7, k), order="F")
+    B[:n] = W.gaussian_rhs(n, k, 17)
+    B[:n, 1] = B[:n, 0] * 2.0 ** 20
+    B[:n, 2] = 0.0
+    B[:n, 3] = B[:n, 4] * 1e-3 + B[:n, 5] * 1e-6
+    B[n:] = 123.0                                                       # padding: must not be read
+    X = np.full((n + 3, k), -7.0, order="F")
+    G = _factor(P, A, perm, seed, g_precision=prec)
+    Xo, it, rr, status = P.parac_pcg(G, n, None, None, None, B, tol=1e-8, maxit=500, X=X)
     assert status == "PARAC_OK" and np.all(rr <= 1e-8)
-    for j in range(4):
-        xj, itj, _, _ = P.parac_pcg(G, A.n, None, None, None, B[:, j], tol=1e-8, maxit=500)
-        assert itj[0] == it[j]
-        assert np.allclose(X[:, j], xj, rtol=0, atol=1e-12 * np.abs(xj).max())
+    assert np.all(X[n:] == -7.0)
+    assert np.array_equal(X[:n, 1], X[:n, 0] * 2.0 ** 20) and it[1] == it[0]
+    assert np.all(X[:n, 2] == 0.0) and it[2] == 0 and rr[2] == 0.0
+    for j in (0, 5, 31):
+        xj, itj, rrj, _ = P.parac_pcg(G, n, None, None, None, np.ascontiguousarray(B[:n, j]), tol=1e-8, maxit=500)
+        assert abs(int(itj[0]) - int(it[j])) <= 1
+        assert np.linalg.norm((xj - xj.mean()) - (X[:n, j] - X[:n, j].mean())) <= 1e-6 * np.linalg.norm(xj)
+    G.free()
+
+
+def test_block_pcg_device_arrays(P):
+    import torch
+    A, perm, seed, _ = W.config("grid2d-64")
+    B = W.gaussian_rhs(A.n, 8, 21)
+    G = _factor(P, A, perm, seed)
+    Xh, ith, rrh, _ = P.parac_pcg(G, A.n, None, None, None, B, tol=1e-8)
+    Xd, itd, rrd, status = P.parac_pcg(G, A.n, None, None, None, torch.from_numpy(B).cuda(), tol=1e-8)
+    assert status == "PARAC_OK" and tuple(Xd.shape) == (A.n, 8)
+    assert np.array_equal(ith, itd) and np.array_equal(Xd.cpu().numpy(), Xh)
+    G.free()
+
+
+@pytest.mark.parametrize("nrhs", [1, 6])
+def test_graph_replay_matches_direct_launches(P, monkeypatch, nrhs):
+    """The captured-graph replay of the PCG iterations runs the same kernels
+    in the same order as direct launches: identical bits."""
+    A, perm, seed, _ = W.config("grid2d-64")
+    B = W.gaussian_rhs(A.n, nrhs, 23)
+    G = _factor(P, A, perm, seed)
+    Xg, itg, rrg, _ = P.parac_pcg(G, A.n, None, None, None, B, tol=1e-10, maxit=500)
+    Xg2, itg2, _, _ = P.parac_pcg(G, A.n, None, None, None, B, tol=1e-10, maxit=500)    # replay of a cached graph
+    monkeypatch.setenv("PARAC_GRAPH", "0")
+    Xd, itd, rrd, _ = P.parac_pcg(G, A.n, None, None, None, B, tol=1e-10, maxit=500)
+    assert np.array_equal(itg, itd) and np.array_equal(Xg, Xd) and np.array_equal(rrg, rrd)
+    assert np.array_equal(itg2, itd) and np.array_equal(Xg2, Xd)
     G.free()
 
 
