@@ -236,6 +236,9 @@ struct parac_factor_s {
     int64_t nnzL = 0;
     std::string stats;
     SolveCache cache;
+    int32_t max_row = 0;                               // longest row / column of F
+    DBuf sgs_f, sgs_b;                                 // row groups of the one-row-per-warp solves
+    int32_t sng_f = 0, sng_b = 0;
     BlockCache bcache;
     DBuf status;
     SolveStream sstream;
@@ -280,6 +283,7 @@ struct FactorOut {
     int64_t nl = 0, nnz_low = 0;
     unsigned long long stats[32] = {0};
     unsigned long long pool_used = 0, f_used = 0, scratch_used = 0;
+    int32_t max_lower_column = 0;
     int regrows = 0;
     double t_ingest = 0, t_elim = 0, t_compact = 0;
     int blocks = 0, warps = 0;
@@ -434,7 +438,27 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         CK(cudaMemsetAsync(trace_par.p, 0xff, 4 * (size_t)nl, st));
     }
     double mult = O.o.pool_mult;
-    unsigned long long scratch_cap = 64ull << 20;
+    // Global scratch of the cooperative (CTA-per-vertex) path: every CTA may
+    // hold a working set of next_pow2(gather) entries, and a vertex's gather
+    // is its original lower column plus the fill it receives.  Sized from the
+    // longest lower column (x4 for fill, x2 for the arena's growth by
+    // doubling), at most a quarter of the free device memory.
+    unsigned long long scratch_cap = 256ull << 20;
+    {
+        DBuf mx = dalloc<int32_t>(1, st);
+        CK(cudaMemsetAsync(mx.p, 0, 4, st));
+        if (nl > 0) CK(launch_max_i32(lcnt.as<int32_t>(), nl, mx.as<int32_t>(), st));
+        int32_t maxlow = 0;
+        CK(cudaMemcpyAsync(&maxlow, mx.p, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        unsigned long long p2 = 1;
+        while (p2 < 4ull * (unsigned long long)maxlow + 64ull) p2 <<= 1;
+        const unsigned long long want = (unsigned long long)blocks * 2ull * (ENTRY_BYTES + 1) * p2 + (256ull << 20);
+        size_t freeb = 0, totalb = 0;
+        if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) { cudaGetLastError(); freeb = 0; }
+        scratch_cap = std::max(scratch_cap, std::min<unsigned long long>(want, freeb / 4));
+        out.max_lower_column = maxlow;
+    }
     DBuf pool_row, pool_w, f_row, f_val, scratch;
     for (int attempt = 0;; ++attempt) {
         const unsigned long long pool_cap = (unsigned long long)std::ceil(mult * (double)nnz_low) + 4096ull;
@@ -489,14 +513,19 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         CK(cudaStreamSynchronize(st));
         out.pool_used = htops[0]; out.f_used = htops[1]; out.scratch_used = htops[2];
         if (hst == ST_OK) break;
+        // which workspace ran out: every reservation bumps its top, also past the end
+        const bool over_pool = htops[0] > pool_cap || htops[1] > f_cap, over_scratch = htops[2] > scratch_cap;
         if (hst == ST_POOL && attempt < O.o.max_pool_regrow) {
-            mult *= 2.0;
-            scratch_cap *= 2;
+            if (over_pool || !over_scratch) mult *= 2.0;
+            if (over_scratch) scratch_cap *= 4;
             out.regrows++;
             continue;
         }
-        set_err(hst == ST_POOL ? "fill workspace overflow (raise pool_mult or max_pool_regrow)"
-                               : "device wait exceeded spin_limit");
+        if (hst == ST_POOL)
+            set_err("%s workspace overflow (raise pool_mult or max_pool_regrow)",
+                    over_scratch ? "cooperative-path scratch" : "fill");
+        else
+            set_err("device wait exceeded spin_limit");
         throw StatusFail{map_status(hst)};
     }
     scratch.release(); pool_row.release(); pool_w.release();
@@ -591,6 +620,13 @@ void finish_handle(parac_factor_s *h, int64_t n, int64_t nnzF, const Opts &O)
     CK(cudaMemsetAsync(cnt.p, 0, 4 * n1, st));
     CK(launch_row_count(nnzF, h->Srow.as<int32_t>(), cnt.as<int32_t>(), st));
     CK(scan_i32_to_i64(cnt.as<int32_t>(), h->Srp.as<int64_t>(), n, tmp.p, st));
+    // longest row (forward) or column (backward) of the solves
+    DBuf mxlen = dalloc<int32_t>(1, st);
+    CK(cudaMemsetAsync(mxlen.p, 0, 4, st));
+    CK(launch_max_i32(cnt.as<int32_t>(), n, mxlen.as<int32_t>(), st));
+    CK(launch_max_i32(len.as<int32_t>(), n, mxlen.as<int32_t>(), st));
+    int32_t maxlen = 0;
+    CK(cudaMemcpyAsync(&maxlen, mxlen.p, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaMemsetAsync(cnt.p, 0, 4 * n1, st));
     CK(launch_transpose_scatter((int32_t)n, h->Scp.as<int64_t>(), h->Srow.as<int32_t>(), h->Sval.as<double>(),
                                 h->Srp.as<int64_t>(), cnt.as<int32_t>(), h->Scol.as<int32_t>(), h->Svalr.as<double>(), st));
@@ -609,6 +645,25 @@ void finish_handle(parac_factor_s *h, int64_t n, int64_t nnzF, const Opts &O)
         CK(launch_to_f32(h->Svalr.as<double>(), h->Svalr32.as<float>(), nnzF, st));
     }
     h->status = dalloc<int32_t>(1, st);
+    // Row groups of the one-row-per-warp solves, only when some row is long
+    // enough to be shared by a block (else the fixed groups are the same).
+    CK(cudaStreamSynchronize(st));
+    h->max_row = maxlen;
+    if (maxlen > LONG_ROW_SINGLE) {
+        std::vector<int64_t> rp((size_t)n + 1), cp((size_t)n + 1);
+        CK(cudaMemcpyAsync(rp.data(), h->Srp.p, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(cp.data(), h->Scp.p, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const std::vector<int32_t> gf = row_groups(rp, false, SOLVE_WARPS, LONG_ROW_SINGLE),
+                                   gb = row_groups(cp, true, SOLVE_WARPS, LONG_ROW_SINGLE);
+        h->sgs_f = dalloc<int32_t>(gf.size(), st);
+        h->sgs_b = dalloc<int32_t>(gb.size(), st);
+        CK(cudaMemcpyAsync(h->sgs_f.p, gf.data(), 4 * gf.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(h->sgs_b.p, gb.data(), 4 * gb.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        h->sng_f = (int32_t)gf.size() - 1;
+        h->sng_b = (int32_t)gb.size() - 1;
+    }
 }
 
 std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_index)
@@ -619,7 +674,7 @@ std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_ind
              "\"fill_entries\": %llu, \"pool_entries_used\": %llu, \"factor_entries_used\": %llu, "
              "\"scratch_bytes_used\": %llu, \"vertices_warp_path\": %llu, \"vertices_block_path\": %llu, "
              "\"vertices_global_path\": %llu, \"vertices_register_path\": %llu, \"handoffs\": %llu, "
-             "\"queue_spins\": %llu, \"regrows\": %d, \"blocks\": %d, "
+             "\"queue_spins\": %llu, \"regrows\": %d, \"max_lower_column\": %d, \"blocks\": %d, "
              "\"warps_per_block\": %d, \"precision\": %d, \"system\": %d, \"t_ingest_ms\": %.4f, "
              "\"t_elim_ms\": %.4f, \"t_compact_ms\": %.4f, \"depth\": %d, \"cycles\": {\"wait\": %llu, "
              "\"gather\": %llu, \"sort_merge\": %llu, \"store_sort_scan\": %llu, \"sample_append\": %llu, "
@@ -629,7 +684,7 @@ std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_ind
              "\"coop_release\": %llu}}",
              (long long)h->n, (long long)h->nnzF, (long long)(h->nnzF + h->n), (long long)fo.nl,
              (long long)fo.nnz_low, fo.stats[3], fo.pool_used, fo.f_used, fo.scratch_used, fo.stats[0], fo.stats[1],
-             fo.stats[2], fo.stats[5], fo.stats[6], fo.stats[4], fo.regrows, fo.blocks, fo.warps, h->prec, sys_index, fo.t_ingest, fo.t_elim,
+             fo.stats[2], fo.stats[5], fo.stats[6], fo.stats[4], fo.regrows, fo.max_lower_column, fo.blocks, fo.warps, h->prec, sys_index, fo.t_ingest, fo.t_elim,
              fo.t_compact, h->depth, fo.stats[8], fo.stats[9], fo.stats[10], fo.stats[11], fo.stats[12],
              fo.stats[13], fo.stats[14], fo.stats[15], fo.stats[16], fo.stats[17], fo.stats[18], fo.stats[19],
              fo.stats[20], fo.stats[21], fo.stats[22], fo.stats[23]);
@@ -927,7 +982,7 @@ SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, co
     const double n = G->n > 0 ? (double)G->n : 1.0;
     A.lanes_spmv = lanes_for((double)nnzL / n);
     A.lanes_trsv = 32;      // one row per warp: measured fastest on the 128^3 grid (rows of ~11 entries)
-    A.trsv_warps = 8;
+    A.trsv_warps = SOLVE_WARPS;
     if (const char *e = getenv("PARAC_TRSV_LANES")) A.lanes_trsv = atoi(e);
     if (const char *e = getenv("PARAC_TRSV_WARPS")) A.trsv_warps = std::max(1, std::min(32, atoi(e)));
     int bps = 0;
@@ -954,6 +1009,10 @@ SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, co
     if (groups < A.trsv_blocks) A.trsv_blocks = (int)std::max<int64_t>(groups, 1);
     A.spin_limit = G->spin_limit;
     A.status = G->status.as<int32_t>();
+    if (G->sng_f > 0 && A.lanes_trsv == 32 && A.trsv_warps == SOLVE_WARPS) {
+        A.gs_f = G->sgs_f.as<int32_t>(); A.ng_f = G->sng_f;
+        A.gs_b = G->sgs_b.as<int32_t>(); A.ng_b = G->sng_b;
+    }
     return A;
 }
 
@@ -1024,7 +1083,8 @@ void ensure_block_groups(parac_factor_s *G, int warps, cudaStream_t st)
         CK(cudaMemcpyAsync(rp.data(), G->Srp.p, 8 * (n + 1), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(cp.data(), G->Scp.p, 8 * (n + 1), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        const std::vector<int32_t> gf = row_groups(rp, false, warps), gb = row_groups(cp, true, warps);
+        const std::vector<int32_t> gf = row_groups(rp, false, warps, LONG_ROW_BLOCK),
+                                   gb = row_groups(cp, true, warps, LONG_ROW_BLOCK);
         c.gs_f = dalloc<int32_t>(gf.size(), st);
         c.gs_b = dalloc<int32_t>(gb.size(), st);
         CK(cudaMemcpyAsync(c.gs_f.p, gf.data(), 4 * gf.size(), cudaMemcpyHostToDevice, st));

@@ -314,7 +314,7 @@ __global__ void k_breopen(BlockState *st)
 // late ones are awaited.  Two accumulators (even / odd entries of a stage) and
 // a fixed cross-warp order for shared rows keep the result deterministic.
 constexpr int MAXW = 32;         // warps per block, at most
-constexpr int LONG_ROW = 64;     // entries above which a row gets the whole block
+constexpr int LONG_ROW = LONG_ROW_BLOCK;     // entries above which a row gets the whole block
 
 // Entries u = u0, u0+1, ..., in stages of 32 starting every `stride`, of the
 // row [b, b+len): entry u is b+u, or b+len-1-u when REV (the backward solve
@@ -498,7 +498,7 @@ inline int grid_for(int64_t m, int maxb)
 
 size_t block_state_bytes() { return sizeof(BlockState); }
 
-std::vector<int32_t> row_groups(const std::vector<int64_t> &ptr, bool descending, int warps)
+std::vector<int32_t> row_groups(const std::vector<int64_t> &ptr, bool descending, int warps, int long_row)
 {
     const int64_t n = (int64_t)ptr.size() - 1;
     std::vector<int32_t> gs;
@@ -507,7 +507,7 @@ std::vector<int32_t> row_groups(const std::vector<int64_t> &ptr, bool descending
     int cur = 0;
     for (int64_t kk = 0; kk < n; ++kk) {
         const int64_t j = descending ? n - 1 - kk : kk;
-        if (ptr[j + 1] - ptr[j] > LONG_ROW) {
+        if (ptr[j + 1] - ptr[j] > long_row) {
             if (cur > 0) gs.push_back((int32_t)kk);
             gs.push_back((int32_t)(kk + 1));
             cur = 0;

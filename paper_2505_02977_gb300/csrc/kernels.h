@@ -118,7 +118,16 @@ struct SolveArgs {
     long long spin_limit;
     int32_t *status;
     long long *trace;             // optional per-row trace of the forward solve [n * 8]
+    // optional row groups of the one-row-per-warp solves (row_groups with
+    // LONG_ROW_SINGLE and trsv_warps warps); nullptr: fixed groups
+    const int32_t *gs_f, *gs_b;
+    int32_t ng_f, ng_b;
 };
+// rows above this many entries are shared by a whole block in the
+// one-right-hand-side solves (LONG_ROW in the block solves)
+constexpr int LONG_ROW_SINGLE = 512;
+constexpr int SOLVE_WARPS = 8;        // warps per block of the solves (default)
+constexpr int LONG_ROW_BLOCK = 64;
 
 struct PcgBuffers {
     double *x, *r, *z, *p, *q, *b;  // [n]
@@ -165,8 +174,8 @@ struct BlockHostState {
 size_t block_state_bytes();
 // Row groups of the SpTRSM schedule over positions in ascending (forward) or
 // descending (backward) order: gs[g]..gs[g+1] is either up to `warps` rows of
-// at most LONG_ROW entries or a single longer row.  ptr = row pointers [n+1].
-std::vector<int32_t> row_groups(const std::vector<int64_t> &ptr, bool descending, int warps);
+// at most long_row entries or a single longer row.  ptr = row pointers [n+1].
+std::vector<int32_t> row_groups(const std::vector<int64_t> &ptr, bool descending, int warps, int long_row);
 int btrsm_blocks_per_sm(int warps, int prec);
 cudaError_t bpack(int32_t n, int nrhs, const double *B, int64_t ldb, double *Bt, cudaStream_t st);
 cudaError_t bunpack(int32_t n, int nrhs, const double *Xt, double *X, int64_t ldx, cudaStream_t st);

@@ -237,28 +237,33 @@ __device__ __forceinline__ bool poll_ready(const XT *p, XT &v, long long spin_li
     return true;
 }
 
-// This lane's share of sum_t v[t] x[idx[t]] over t = b+sl, b+sl+S, ... < e,
-// waiting for each x to be published.  Entries are taken in chunks of PF per
-// lane: a chunk's indices and values are fetched together, then the chunk's
-// x loads are issued in rounds -- every entry still unpublished is re-loaded
-// in the same round -- so a chunk costs one round trip for its indices and
-// one per round of waiting, whatever the row length; the terms are added in
-// a fixed order once all are known.
-template <int S, typename VT, typename XT>
-__device__ __forceinline__ bool dot_ready(int64_t b, int64_t e, int sl, const int32_t *idx, const VT *v,
-                                          const XT *x, XT &acc, long long spin_limit, const int32_t *status,
-                                          long long *t_seen = nullptr, int32_t *seen_idx = nullptr)
+// This lane's share of sum_u v[t(u)] x[idx[t(u)]] over u = sl, sl+stride, ...
+// < e-b, where t(u) = b+u, or e-1-u when REV (the backward solve walks a
+// column from its last entry, whose unknown was published first), waiting
+// for each x to be published.  Entries are taken in chunks of PF per lane: a
+// chunk's indices and values are fetched together, then the chunk's x loads
+// are issued in rounds -- every entry still unpublished is re-loaded in the
+// same round -- so a chunk costs one round trip for its indices and one per
+// round of waiting, whatever the row length; the terms are added in a fixed
+// order once all are known.
+template <bool REV, typename VT, typename XT>
+__device__ __forceinline__ bool dot_ready(int64_t b, int64_t e, int sl, int stride, const int32_t *idx,
+                                          const VT *v, const XT *x, XT &acc, long long spin_limit,
+                                          const int32_t *status, long long *t_seen = nullptr,
+                                          int32_t *seen_idx = nullptr)
 {
     constexpr int PF = 8;
-    for (int64_t base = b + sl; base < e; base += (int64_t)PF * S) {
+    const int64_t len = e - b;
+    for (int64_t base = sl; base < len; base += (int64_t)PF * stride) {
         int32_t cc[PF];
         VT vv[PF];
         XT xx[PF];
 #pragma unroll
         for (int r = 0; r < PF; ++r) {
-            const int64_t t = base + (int64_t)r * S;
-            cc[r] = t < e ? idx[t] : -1;
-            vv[r] = t < e ? v[t] : (VT)0;
+            const int64_t u = base + (int64_t)r * stride;
+            const int64_t t = REV ? e - 1 - u : b + u;
+            cc[r] = u < len ? idx[t] : -1;
+            vv[r] = u < len ? v[t] : (VT)0;
         }
 #pragma unroll
         for (int r = 0; r < PF; ++r) xx[r] = cc[r] >= 0 ? ld_poll(x + cc[r]) : (XT)0;
@@ -291,6 +296,21 @@ __device__ __forceinline__ bool dot_ready(int64_t b, int64_t e, int sl, const in
     return true;
 }
 
+// Sum over the block of one value per warp (lane 0's), in warp order, for a
+// row shared by the whole block; the result is valid in thread 0.
+template <typename XT>
+__device__ __forceinline__ XT block_row_sum(XT acc, XT *red)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    XT s = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    return s;
+}
+
 // The factor is stored relabelled by dependency level (position j holds the
 // column of the j-th vertex in level order), so F stays unit lower triangular
 // with every row's dependencies at earlier positions and the rows of one
@@ -299,29 +319,58 @@ __device__ __forceinline__ bool dot_ready(int64_t b, int64_t e, int sl, const in
 // Forward: y[j] = rhs[operm[j]] - sum_{c<j} F(j,c) y[c] over CSR row j; also
 // resets the backward unknown z[j] to the sentinel.  Every load that does not
 // depend on other rows is issued before the dependency polls.
+//
+// With a group table gs (one row per warp, S == 32), rows are handed out in
+// groups gs[g]..gs[g+1]: up to one row per warp, or one row longer than
+// LONG_ROW_SINGLE entries shared by every warp of the block (the rows that
+// collect the most fill, e.g. of hub vertices, would otherwise leave one warp
+// to walk them alone on the critical path).
 template <int S, typename VT, typename XT>
 __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, const VT *v, const int32_t *operm,
-                           const double *rhs, XT *y, XT *zreset, const PcgState *st, long long spin_limit,
-                           int32_t *status, long long *trace)
+                           const double *rhs, XT *y, XT *zreset, const int32_t *gs, int32_t ngs,
+                           const PcgState *st, long long spin_limit, int32_t *status, long long *trace)
 {
+    __shared__ XT red[32];
     if (st && st->done) return;
     const unsigned lane = threadIdx.x & 31;
     const int sub = lane / S, sl = lane % S;
     const unsigned smask = (S == 32) ? FULL : (((1u << S) - 1u) << (sub * S));
     const int rows_per_group = (blockDim.x / 32) * (32 / S);
     const int my = (threadIdx.x >> 5) * (32 / S) + sub;
-    const int64_t ngroups = ((int64_t)n + rows_per_group - 1) / rows_per_group;
+    const int64_t ngroups = gs ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-        const int64_t j = g * rows_per_group + my;
-        if (j >= n) continue;
+        int64_t j;
+        if (gs) {
+            const int32_t p0 = gs[g], p1 = gs[g + 1];
+            if (p1 - p0 == 1 && rp[p0 + 1] - rp[p0] > LONG_ROW_SINGLE) {      // shared row (block-uniform)
+                const int64_t b = rp[p0], e = rp[p0 + 1];
+                const double rj = threadIdx.x == 0 ? rhs[operm[p0]] : 0.0;
+                XT acc = 0;
+                if (!dot_ready<false, VT, XT>(b, e, threadIdx.x, blockDim.x, ci, v, y, acc, spin_limit, status))
+                    set_status(status, ST_TIMEOUT);
+                const XT sum = block_row_sum(acc, red);
+                if (threadIdx.x == 0) {
+                    zreset[p0] = sentinel<XT>();
+                    st_pub(y + p0, to_x<XT>(rj) - sum);
+                }
+                __syncthreads();
+                continue;
+            }
+            j = p0 + my;
+            if (j >= p1) continue;
+        } else {
+            j = g * rows_per_group + my;
+            if (j >= n) continue;
+        }
         const long long t_arrive = trace ? global_ns() : 0;
         const int64_t b = rp[j], e = rp[j + 1];
         const double rj = (sl == 0) ? rhs[operm[j]] : 0.0;
         XT acc = 0;
         long long t_seen = 0;
         int32_t seen_idx = -1;
-        const bool ok = trace ? dot_ready<S, VT, XT>(b, e, sl, ci, v, y, acc, spin_limit, status, &t_seen, &seen_idx)
-                              : dot_ready<S, VT, XT>(b, e, sl, ci, v, y, acc, spin_limit, status);
+        const bool ok = trace ? dot_ready<false, VT, XT>(b, e, sl, S, ci, v, y, acc, spin_limit, status, &t_seen,
+                                                         &seen_idx)
+                              : dot_ready<false, VT, XT>(b, e, sl, S, ci, v, y, acc, spin_limit, status);
         if (!ok) set_status(status, ST_TIMEOUT);
         long long t_acc = 0;
         if (trace) {                                   // latest dependency seen by any lane of the row
@@ -362,19 +411,52 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
 template <int S, typename VT, typename XT>
 __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, const VT *v, const double *Dinv,
                            const int32_t *operm, XT *y, XT *z, double *zout, const double *r_orig, double *partial,
-                           const PcgState *st, long long spin_limit, int32_t *status)
+                           const int32_t *gs, int32_t ngs, const PcgState *st, long long spin_limit,
+                           int32_t *status)
 {
+    __shared__ XT red[32];
     if (st && st->done) return;
     const unsigned lane = threadIdx.x & 31;
     const int sub = lane / S, sl = lane % S;
     const unsigned smask = (S == 32) ? FULL : (((1u << S) - 1u) << (sub * S));
     const int rows_per_group = (blockDim.x / 32) * (32 / S);
     const int my = (threadIdx.x >> 5) * (32 / S) + sub;
-    const int64_t ngroups = ((int64_t)n + rows_per_group - 1) / rows_per_group;
+    const int64_t ngroups = gs ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
     double dotacc = 0.0;
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-        const int64_t kk = g * rows_per_group + my;
-        if (kk >= n) continue;
+        int64_t kk;
+        if (gs) {
+            const int32_t k0 = gs[g], k1 = gs[g + 1];
+            const int64_t j0 = (int64_t)n - 1 - k0;
+            if (k1 - k0 == 1 && cp[j0 + 1] - cp[j0] > LONG_ROW_SINGLE) {      // shared column (block-uniform)
+                const int64_t b = cp[j0], e = cp[j0 + 1];
+                XT yj = 0;
+                double dj = 0.0, rj = 0.0;
+                int32_t o = 0;
+                if (threadIdx.x == 0) {
+                    yj = y[j0]; dj = Dinv[j0]; o = operm[j0];
+                    if (r_orig) rj = r_orig[o];
+                }
+                XT acc = 0;
+                if (!dot_ready<true, VT, XT>(b, e, threadIdx.x, blockDim.x, ri, v, z, acc, spin_limit, status))
+                    set_status(status, ST_TIMEOUT);
+                const XT sum = block_row_sum(acc, red);
+                if (threadIdx.x == 0) {
+                    const XT zj = to_x<XT>((double)yj * dj) - sum;
+                    y[j0] = sentinel<XT>();
+                    st_pub(z + j0, zj);
+                    zout[o] = (double)zj;
+                    dotacc += rj * (double)zj;
+                }
+                __syncthreads();
+                continue;
+            }
+            kk = k0 + my;
+            if (kk >= k1) continue;
+        } else {
+            kk = g * rows_per_group + my;
+            if (kk >= n) continue;
+        }
         const int64_t j = n - 1 - kk;
         const int64_t b = cp[j], e = cp[j + 1];
         XT yj = 0;
@@ -385,7 +467,7 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
             if (r_orig) rj = r_orig[o];
         }
         XT acc = 0;
-        const bool ok = dot_ready<S, VT, XT>(b, e, sl, ri, v, z, acc, spin_limit, status);
+        const bool ok = dot_ready<true, VT, XT>(b, e, sl, S, ri, v, z, acc, spin_limit, status);
         if (!ok) set_status(status, ST_TIMEOUT);
 #pragma unroll
         for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
@@ -434,10 +516,13 @@ cudaError_t apply_t(const SolveArgs &A, const VT *vr, const VT *vc, XT *y, XT *z
                     double *partial, const PcgState *st, cudaStream_t s)
 {
     const int threads = A.trsv_warps * 32;
-    k_trsv_fwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Frp, A.Fcol, vr, A.operm, r, y, z, st,
-                                                             A.spin_limit, A.status, A.trace); count_launches(1);
+    // group tables apply to one row per warp only
+    const int32_t *gf = S == 32 ? A.gs_f : nullptr, *gb = S == 32 ? A.gs_b : nullptr;
+    k_trsv_fwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Frp, A.Fcol, vr, A.operm, r, y, z, gf, A.ng_f,
+                                                             st, A.spin_limit, A.status, A.trace); count_launches(1);
     k_trsv_bwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z,
-                                                             zout, r, partial, st, A.spin_limit, A.status); count_launches(1);
+                                                             zout, r, partial, gb, A.ng_b, st, A.spin_limit,
+                                                             A.status); count_launches(1);
     return cudaGetLastError();
 }
 
