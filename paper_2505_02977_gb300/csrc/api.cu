@@ -404,15 +404,27 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
     // ---------------------------------------------------------------- elimination
     EvTimer t_el(O.o.timing != 0, st);
     const int warps = O.o.warps_per_block;
-    int warp_cap = 128, block_cap = 1024;
+    // CTA buffer of the cooperative path: 2048 entries while two CTAs still
+    // fit an SM, else 1024
+    int warp_cap = 128, block_cap = 2048;
     if (O.o.big_threshold > 0) {
         int b = 32;
         while (b < O.o.big_threshold && b < 4096) b <<= 1;
         warp_cap = b;
+        block_cap = 1024;
         if (block_cap < 2 * warp_cap) block_cap = 2 * warp_cap;
+    }
+    if (const char *e = getenv("PARAC_BLOCK_CAP")) {
+        int b = 256;
+        while (b < atoi(e) && b < 8192) b <<= 1;
+        block_cap = std::max(b, 2 * warp_cap);
     }
     int bps = 0;
     CK(elim_configure(warps, warp_cap, block_cap, &bps));
+    if (bps < 2 && block_cap > 1024 && block_cap > 2 * warp_cap) {
+        block_cap = std::max(1024, 2 * warp_cap);
+        CK(elim_configure(warps, warp_cap, block_cap, &bps));
+    }
     if (bps < 1) { block_cap = 0; CK(elim_configure(warps, warp_cap, block_cap, &bps)); }
     if (bps < 1) { set_err("elimination kernel does not fit on an SM"); throw StatusFail{PARAC_EINVAL}; }
     int blocks = num_sms() * bps;
@@ -430,12 +442,14 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
 
     // optional per-vertex trace, written to the file named by PARAC_TRACE
     const char *trace_path = getenv("PARAC_TRACE");
-    DBuf trace_buf, trace_par;
+    DBuf trace_buf, trace_par, trace_ph;
     if (trace_path) {
         trace_buf = dalloc<long long>((size_t)nl * 4, st);
         trace_par = dalloc<int32_t>((size_t)nl, st);
         CK(cudaMemsetAsync(trace_buf.p, 0, 32 * (size_t)nl, st));
         CK(cudaMemsetAsync(trace_par.p, 0xff, 4 * (size_t)nl, st));
+        trace_ph = dalloc<int32_t>((size_t)nl * 8, st);
+        CK(cudaMemsetAsync(trace_ph.p, 0, 32 * (size_t)nl, st));
     }
     double mult = O.o.pool_mult;
     // Global scratch of the cooperative (CTA-per-vertex) path: every CTA may
@@ -500,9 +514,12 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         a.profile = O.o.timing >= 2 ? 1 : 0;
         a.trace = trace_buf.as<long long>();
         a.trace_parent = trace_par.as<int32_t>();
+        a.trace_phase = trace_ph.as<int32_t>();
         a.idle_ns = 512;
         a.coop = 1;
         if (const char *e = getenv("PARAC_COOP")) a.coop = atoi(e) != 0;
+        a.sample_sort = 1;
+        if (const char *e = getenv("PARAC_SAMPLE_SORT")) a.sample_sort = atoi(e) != 0;
         if (const char *e = getenv("PARAC_IDLE_NS")) a.idle_ns = std::max(32, std::min(1000000, atoi(e)));
         if (nl > 0) CK(elim_launch(a, blocks, warps, fchunk, st));
         int32_t hst = 0;
@@ -535,6 +552,8 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         std::vector<int32_t> par((size_t)nl), lv((size_t)nl);
         CK(cudaMemcpyAsync(tr.data(), trace_buf.p, 32 * (size_t)nl, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(par.data(), trace_par.p, 4 * (size_t)nl, cudaMemcpyDeviceToHost, st));
+        std::vector<int32_t> ph((size_t)nl * 8);
+        CK(cudaMemcpyAsync(ph.data(), trace_ph.p, 32 * (size_t)nl, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(lv.data(), lvl.p, 4 * (size_t)nl, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (FILE *f = fopen(trace_path, "wb")) {
@@ -543,6 +562,7 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
             fwrite(tr.data(), 8, tr.size(), f);
             fwrite(par.data(), 4, par.size(), f);
             fwrite(lv.data(), 4, lv.size(), f);
+            fwrite(ph.data(), 4, ph.size(), f);
             fclose(f);
         }
     }

@@ -203,6 +203,8 @@ struct ElimArgs {
     int32_t coop;                  // nonzero: working sets above warp_cap use the CTA-cooperative path
     long long *trace;              // optional per-vertex trace [nl * 4]: ready, start, end (ns), g << 32 | d
     int32_t *trace_parent;         // optional: pivot whose decrement made the vertex ready
+    int32_t *trace_phase;          // optional: cycles of the cooperative path's 8 phases [nl * 8]
+    int32_t sample_sort;           // cooperative path: sample sort for working sets in global memory
 };
 
 // Bytes of shared/scratch memory per entry of the per-vertex working set:

@@ -690,6 +690,8 @@ __device__ int32_t eliminate_big(const ElimArgs &a, int32_t k, int64_t o0, int32
 // every other warp of the CTA joins at its next poll point, and the block runs
 // the same steps with block-wide networks.  One request at a time per CTA;
 // all barriers are bounded software barriers over the CTA's warps.
+constexpr int MAX_BIG_BUCKETS = 64;    // buckets above a warp's slice, sorted by the whole CTA
+
 struct CoopShared {
     int k;                       // vertex being eliminated cooperatively (-1: none)
     int gen;                     // bumped for every request
@@ -697,6 +699,8 @@ struct CoopShared {
     int arrive;                  // barrier arrivals (monotonic)
     int d, ntile, abort;
     int hcount[32];              // per-warp head counts of the merge
+    int nbig, maxcnt;            // sample sort: oversized buckets, largest bucket
+    int big[MAX_BIG_BUCKETS];
     unsigned long long fpos;
     unsigned long long sbase, scap;   // CTA scratch (global), reused across requests
     long long spin_limit;
@@ -806,6 +810,304 @@ __device__ void coop_sort(View v, int P, View tile, int T)
     }
 }
 
+// ---------------------------------------------------------------- sample sort
+// Sorting a working set that lives in global memory (more entries than the
+// CTA's shared buffer): a sorted sample of cap entries in shared memory gives
+// B-1 splitters, every entry is counted into its bucket and scattered to the
+// temporary arrays (weights in v.S, row | mult << 32 in v.M), and each bucket
+// is sorted in shared memory -- by one warp when it fits the warp's slice of
+// the buffer, else by the whole CTA.  Bucket boundaries are a deterministic
+// function of the keys and every bucket is fully sorted, so the result is the
+// sorted sequence itself, as from any other exact sort.  The bucket offsets
+// and merged counts live in global scratch (gbo[B+1], gbd[B]).
+
+// Exclusive scan of n ints by the CTA (a and out may be the same array).
+__device__ int block_excl_scan(const int *a, int n, int *out, CoopShared &cs)
+{
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int c = (n + nt - 1) / nt;
+    const int lo = tid * c < n ? tid * c : n, hi = lo + c < n ? lo + c : n;
+    int sum = 0;
+    for (int i = lo; i < hi; ++i) sum += a[i];
+    int x = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) cs.hcount[warp] = x;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < nw; ++w) { const int h = cs.hcount[w]; if (w < warp) before += h; total += h; }
+    int run = before + x - sum;
+    for (int i = lo; i < hi; ++i) { const int ai = a[i]; out[i] = run; run += ai; }
+    __syncthreads();
+    return total;
+}
+
+// Bucket of a key: the number of splitters strictly below it, splitter b
+// (b = 1..B-1) being sample entry b*stride (stride = SS/B, both powers of two).  KEY 0 compares rows only (every
+// entry of a row falls in one bucket), KEY 1 the full (weight bits, row) key.
+template <int KEY>
+__device__ __forceinline__ int bucket_of(const View &smp, int stride, int B, int32_t r, unsigned long long wb)
+{
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int si = mid * stride;
+        const int32_t sr = smp.row[si];
+        bool below;
+        if (KEY == 0) {
+            below = sr < r;
+        } else {
+            const unsigned long long sw = dbits(smp.w[si]);
+            below = sw < wb || (sw == wb && sr < r);
+        }
+        if (below) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Shared part of both sorts: sample, count, bucket offsets, scatter.  n >
+// cap entries (row, w, mult) of v; returns B, or 0 when a bucket exceeds the
+// CTA's buffer or more than MAX_BIG_BUCKETS exceed a warp's slice (nothing
+// has been moved then).
+template <int KEY>
+__device__ int sample_partition(View v, int n, View tile, int cap, int wcap, CoopShared &cs, int *gbo)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int SS = cap, lg = __ffs(SS) - 1;              // cap: a power of two
+    for (int s2 = tid; s2 < SS; s2 += nt) {
+        const int i = (int)(((long long)s2 * n) >> lg);
+        tile.row[s2] = v.row[i];
+        tile.w[s2] = v.w[i];
+        if (KEY == 1) tile.mult[s2] = v.mult[i];
+    }
+    __syncthreads();
+    coop_sort<KEY>(tile, SS, tile, 0);
+    // B a power of two, at least 4 samples per bucket, buckets half a warp's slice on average
+    int B = next_pow2((2 * n + wcap - 1) / wcap);
+    if (B > SS / 4) B = SS / 4;
+    if (B < 1) B = 1;
+    const int stride = SS / B;
+    int *cnt = (int *)tile.S, *cur = (int *)tile.S + cap, *off = (int *)tile.M;
+    for (int b = tid; b < B; b += nt) { cnt[b] = 0; cur[b] = 0; }
+    if (tid == 0) { cs.nbig = 0; cs.maxcnt = 0; }
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) {
+        const int32_t r = v.row[i];
+        const unsigned long long wb = KEY == 1 ? dbits(v.w[i]) : 0ull;
+        atomicAdd(cnt + bucket_of<KEY>(tile, stride, B, r, wb), 1);
+    }
+    __syncthreads();
+    for (int b = tid; b < B; b += nt) {
+        const int c = cnt[b];
+        atomicMax(&cs.maxcnt, c);
+        if (c > wcap) atomicAdd(&cs.nbig, 1);
+    }
+    block_excl_scan(cnt, B, off, cs);
+    const bool fits = cs.maxcnt <= cap && cs.nbig <= MAX_BIG_BUCKETS;
+    __syncthreads();
+    if (!fits) return 0;
+    if (tid == 0) { off[B] = n; cs.nbig = 0; }
+    __syncthreads();
+    unsigned long long *tM = (unsigned long long *)v.M;
+    for (int i = tid; i < n; i += nt) {
+        const int32_t r = v.row[i];
+        const double w = v.w[i];
+        const int32_t m = KEY == 1 ? v.mult[i] : 0;
+        const int b = bucket_of<KEY>(tile, stride, B, r, KEY == 1 ? dbits(w) : 0ull);
+        const int pos = off[b] + atomicAdd(cur + b, 1);
+        v.S[pos] = w;
+        tM[pos] = (unsigned long long)(uint32_t)r | ((unsigned long long)(uint32_t)m << 32);
+    }
+    for (int b = tid; b <= B; b += nt) gbo[b] = off[b];
+    __syncthreads();
+    return B;
+}
+
+// Merge the sorted runs of a bucket held in a shared view (rows, weights in
+// [0, cb)), writing (sum, row | len << 32) to [o, o + d_b) of the temporaries
+// by one warp; returns d_b.  Runs are summed left to right.
+__device__ __forceinline__ int warp_merge_bucket(View sv, int cb, double *tS, unsigned long long *tM, int o)
+{
+    const unsigned lane = lane_id();
+    int db = 0;
+    for (int base = 0; base < cb; base += 32) {
+        const int i = base + (int)lane;
+        bool head = false;
+        int32_t r = 0;
+        int len = 0;
+        double sum = 0.0;
+        if (i < cb) {
+            r = sv.row[i];
+            head = (i == 0) || (sv.row[i - 1] != r);
+            if (head) {
+                sum = sv.w[i]; len = 1;
+                while (i + len < cb && sv.row[i + len] == r) { sum = __dadd_rn(sum, sv.w[i + len]); ++len; }
+            }
+        }
+        const unsigned bal = __ballot_sync(FULL, head);
+        if (head) {
+            const int rank = db + __popc(bal & ((1u << lane) - 1u));
+            tS[o + rank] = sum;
+            tM[o + rank] = (unsigned long long)(uint32_t)r | ((unsigned long long)(uint32_t)len << 32);
+        }
+        db += __popc(bal);
+    }
+    return db;
+}
+
+// Row phase on a global working set: sort (row, weight bits), merge runs,
+// compact in bucket order into v[0, d) (row, w, mult) and store the F column
+// rows / merged weights.  Returns d, or -1 when the sample sort does not
+// apply (the caller takes the bitonic path; v is untouched).
+__device__ int coop_row_phase(const ElimArgs &a, CoopShared &cs, View v, int g, unsigned char *bbuf, int cap,
+                              int *gbo, int *gbd, int32_t k)
+{
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int wcap = cap / nw;
+    const View tile = make_view(bbuf, cap);
+    const int B = sample_partition<0>(v, g, tile, cap, wcap, cs, gbo);
+    if (B == 0) return -1;
+    double *tS = v.S;
+    unsigned long long *tM = (unsigned long long *)v.M;
+    // buckets that fit a warp's slice: one warp each
+    const View sv = make_view(bbuf + (size_t)warp * wcap * ENTRY_BYTES, wcap);
+    for (int b = warp; b < B; b += nw) {
+        const int o = gbo[b], cb = gbo[b + 1] - o;
+        if (cb > wcap) {
+            if (lane == 0) cs.big[atomicAdd(&cs.nbig, 1)] = b;
+            continue;
+        }
+        int db = 0;
+        if (cb > 0) {
+            const int Pb = next_pow2(cb);
+            for (int i = lane; i < Pb; i += 32) {
+                if (i < cb) { sv.row[i] = (int32_t)(uint32_t)tM[o + i]; sv.w[i] = tS[o + i]; }
+                else { sv.row[i] = ROW_SENTINEL; sv.w[i] = 0.0; }
+            }
+            __syncwarp();
+            sort_row_bits(sv, Pb);
+            db = warp_merge_bucket(sv, cb, tS, tM, o);
+            __syncwarp();
+        }
+        if (lane == 0) gbd[b] = db;
+    }
+    __syncthreads();
+    // oversized buckets: the whole CTA, one after another
+    const int nbig = cs.nbig;
+    for (int q = 0; q < nbig; ++q) {
+        const int b = cs.big[q];
+        const int o = gbo[b], cb = gbo[b + 1] - o;
+        const int Pb = next_pow2(cb);
+        for (int i = tid; i < Pb; i += nt) {
+            if (i < cb) { tile.row[i] = (int32_t)(uint32_t)tM[o + i]; tile.w[i] = tS[o + i]; }
+            else { tile.row[i] = ROW_SENTINEL; tile.w[i] = 0.0; }
+        }
+        __syncthreads();
+        coop_sort<0>(tile, Pb, tile, 0);
+        if (warp == 0) {
+            const int db = warp_merge_bucket(tile, cb, tS, tM, o);
+            if (lane == 0) gbd[b] = db;
+        }
+        __syncthreads();
+    }
+    // compaction in bucket order, with the F column store
+    int *pd = (int *)bbuf;
+    for (int b = tid; b < B; b += nt) pd[b] = gbd[b];
+    __syncthreads();
+    const int d = block_excl_scan(pd, B, pd, cs);
+    if (tid == 0) {
+        const unsigned long long base = d > 0 ? atomicAdd(a.f_top, (unsigned long long)d) : 0ull;
+        if (d > 0 && base + d > a.f_cap) set_status(a.status, ST_POOL);
+        cs.fpos = base;
+    }
+    if (__syncthreads_or(read_status(a.status) != ST_OK)) return -2;
+    const unsigned long long fpos = cs.fpos;
+    for (int b = warp; b < B; b += nw) {
+        const int o = gbo[b], db = gbd[b], p0 = pd[b];
+        for (int i = lane; i < db; i += 32) {
+            const unsigned long long rm = tM[o + i];
+            const int32_t r = (int32_t)(uint32_t)rm;
+            const double w = tS[o + i];
+            v.row[p0 + i] = r; v.w[p0 + i] = w; v.mult[p0 + i] = (int32_t)(rm >> 32);
+            a.f_row[fpos + p0 + i] = r; a.f_val[fpos + p0 + i] = w;
+        }
+    }
+    if (tid == 0) { a.f_start[k] = (int64_t)fpos; a.f_len[k] = d; }
+    __syncthreads();
+    return d;
+}
+
+// Weight phase on a global working set: sort v[0, d) by (weight bits, row)
+// carrying the multiplicity.  Returns false when the sample sort does not
+// apply (v untouched).
+__device__ bool coop_weight_phase(View v, int d, unsigned char *bbuf, int cap, CoopShared &cs, int *gbo)
+{
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int wcap = cap / nw;
+    const View tile = make_view(bbuf, cap);
+    if (d <= cap) {                                   // one tile
+        const int Pd = next_pow2(d);
+        for (int i = tid; i < Pd; i += nt) {
+            if (i < d) { tile.row[i] = v.row[i]; tile.w[i] = v.w[i]; tile.mult[i] = v.mult[i]; }
+            else { tile.row[i] = ROW_SENTINEL; tile.w[i] = __longlong_as_double((long long)WBITS_SENTINEL); tile.mult[i] = 0; }
+        }
+        __syncthreads();
+        coop_sort<1>(tile, Pd, tile, 0);
+        for (int i = tid; i < d; i += nt) { v.row[i] = tile.row[i]; v.w[i] = tile.w[i]; v.mult[i] = tile.mult[i]; }
+        __syncthreads();
+        return true;
+    }
+    const int B = sample_partition<1>(v, d, tile, cap, wcap, cs, gbo);
+    if (B == 0) return false;
+    const double *tS = v.S;
+    const unsigned long long *tM = (const unsigned long long *)v.M;
+    const View sv = make_view(bbuf + (size_t)warp * wcap * ENTRY_BYTES, wcap);
+    for (int b = warp; b < B; b += nw) {
+        const int o = gbo[b], cb = gbo[b + 1] - o;
+        if (cb > wcap) {
+            if (lane == 0) cs.big[atomicAdd(&cs.nbig, 1)] = b;
+            continue;
+        }
+        if (cb == 0) continue;
+        const int Pb = next_pow2(cb);
+        for (int i = lane; i < Pb; i += 32) {
+            if (i < cb) {
+                const unsigned long long rm = tM[o + i];
+                sv.row[i] = (int32_t)(uint32_t)rm; sv.mult[i] = (int32_t)(rm >> 32); sv.w[i] = tS[o + i];
+            } else {
+                sv.row[i] = ROW_SENTINEL; sv.mult[i] = 0; sv.w[i] = __longlong_as_double((long long)WBITS_SENTINEL);
+            }
+        }
+        __syncwarp();
+        sort_bits_row(sv, Pb);
+        for (int i = lane; i < cb; i += 32) { v.row[o + i] = sv.row[i]; v.w[o + i] = sv.w[i]; v.mult[o + i] = sv.mult[i]; }
+        __syncwarp();
+    }
+    __syncthreads();
+    const int nbig = cs.nbig;
+    for (int q = 0; q < nbig; ++q) {
+        const int b = cs.big[q];
+        const int o = gbo[b], cb = gbo[b + 1] - o;
+        const int Pb = next_pow2(cb);
+        for (int i = tid; i < Pb; i += nt) {
+            if (i < cb) {
+                const unsigned long long rm = tM[o + i];
+                tile.row[i] = (int32_t)(uint32_t)rm; tile.mult[i] = (int32_t)(rm >> 32); tile.w[i] = tS[o + i];
+            } else {
+                tile.row[i] = ROW_SENTINEL; tile.mult[i] = 0; tile.w[i] = __longlong_as_double((long long)WBITS_SENTINEL);
+            }
+        }
+        __syncthreads();
+        coop_sort<1>(tile, Pb, tile, 0);
+        for (int i = tid; i < cb; i += nt) { v.row[o + i] = tile.row[i]; v.w[o + i] = tile.w[i]; v.mult[o + i] = tile.mult[i]; }
+        __syncthreads();
+    }
+    return true;
+}
+
 // Cooperative elimination of cs.k by every warp of the CTA (the callers have
 // all reached this function).  __syncthreads() is used only after the bounded
 // join barrier has seen every warp arrive.  Returns, for the requesting warp,
@@ -814,11 +1116,23 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
                                                WarpState &ws)
 {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    long long tp = 0;
+    if (a.trace_phase) tp = clock64();
     if (!cta_barrier(cs, a)) return -2;                  // join: every warp is here
     __syncthreads();
     const int32_t k = cs.k;
     const bool requester = warp == cs.req_warp;
-    if (requester) prof_mark(a, ws, 8);
+    // phase accounting of the requesting warp (profile counters, per-vertex trace)
+    auto mark = [&](int phase) {
+        if (!requester) return;
+        prof_mark(a, ws, phase);
+        if (a.trace_phase && lane == 0) {
+            const long long t = clock64();
+            a.trace_phase[8 * (size_t)k + (phase - 8)] = (int32_t)(t - tp);
+            tp = t;
+        }
+    };
+    mark(8);
     const int64_t o0 = __ldg(a.lcp + k), o1 = __ldg(a.lcp + k + 1);
     const int32_t norig = (int32_t)(o1 - o0);
     const uint32_t cnt = __ldcg(a.fcnt + k);
@@ -832,17 +1146,20 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
         v = make_view(bbuf, a.block_cap);
         tiles = (double *)(bbuf + (size_t)a.block_cap * ENTRY_BYTES);
     } else {
-        const unsigned long long need = (unsigned long long)P * ENTRY_BYTES + ((unsigned long long)P / 32 + 1) * 8;
+        const unsigned long long need = (unsigned long long)P * ENTRY_BYTES + ((unsigned long long)P / 32 + 1) * 8 +
+                                        16ull + 4ull * (2ull * (unsigned long long)a.block_cap + 2ull);
         if (tid == 0 && cs.scap < need) {
             const unsigned long long base = atomicAdd(a.scratch_top, (need + 255ull) & ~255ull);
             if (base + need > a.scratch_cap) set_status(a.status, ST_POOL);
             cs.sbase = base; cs.scap = need;
         }
-        __syncthreads();
-        if (read_status(a.status) != ST_OK) { __syncthreads(); if (tid == 0) cs.k = -1; return -2; }
+        if (__syncthreads_or(read_status(a.status) != ST_OK)) { __syncthreads(); if (tid == 0) cs.k = -1; return -2; }
         v = make_view(a.scratch + cs.sbase, P);
         tiles = (double *)(a.scratch + cs.sbase + (size_t)P * ENTRY_BYTES);
     }
+    // bucket offsets and merged counts of the sample sort (global working sets)
+    int *gbo = (int *)(((uintptr_t)(tiles + (P / 32 + 1)) + 15) & ~(uintptr_t)15);
+    int *gbd = gbo + a.block_cap + 1;
 
     // ---------------------------------------------------------------- gather
     for (int i = tid; i < norig; i += nt) { v.row[i] = __ldg(a.lrow + o0 + i); v.w[i] = __ldg(a.lw + o0 + i); }
@@ -870,52 +1187,59 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
         }
     }
     for (int i = g + tid; i < P; i += nt) { v.row[i] = ROW_SENTINEL; v.w[i] = 0.0; }
-    __syncthreads();
-    if (read_status(a.status) != ST_OK) { __syncthreads(); if (tid == 0) cs.k = -1; return -2; }
-    if (requester) prof_mark(a, ws, 9);
+    if (__syncthreads_or(read_status(a.status) != ST_OK)) { __syncthreads(); if (tid == 0) cs.k = -1; return -2; }
+    mark(9);
 
-    // ---------------------------------------------------------------- sort + merge (in place)
+    // ---------------------------------------------------------------- sort + merge
     const bool global_ws = P > a.block_cap;
     const View tile = make_view(bbuf, a.block_cap);
-    coop_sort<0>(v, P, tile, global_ws ? a.block_cap : 0);
-    if (requester) prof_mark(a, ws, 10);
-    int d = 0;
-    for (int base = 0; base < g; base += nt) {
-        const int i = base + tid;
-        bool head = false;
-        int32_t r = 0, len = 0;
-        double sum = 0.0;
-        if (i < g) {
-            r = v.row[i];
-            head = (i == 0) || (v.row[i - 1] != r);
-            if (head) {
-                sum = v.w[i]; len = 1;
-                while (i + len < g && v.row[i + len] == r) { sum = __dadd_rn(sum, v.w[i + len]); ++len; }
+    int d = -1;
+    const bool sample = global_ws && a.sample_sort && a.block_cap >= 256;
+    if (sample) {
+        d = coop_row_phase(a, cs, v, g, bbuf, a.block_cap, gbo, gbd, k);
+        if (d == -2) { __syncthreads(); if (tid == 0) cs.k = -1; return -2; }
+        if (d >= 0) { mark(10); mark(11); }
+    }
+    if (d < 0) {                                   // bitonic network, merge in place, store
+        coop_sort<0>(v, P, tile, global_ws ? a.block_cap : 0);
+        mark(10);
+        d = 0;
+        for (int base = 0; base < g; base += nt) {
+            const int i = base + tid;
+            bool head = false;
+            int32_t r = 0, len = 0;
+            double sum = 0.0;
+            if (i < g) {
+                r = v.row[i];
+                head = (i == 0) || (v.row[i - 1] != r);
+                if (head) {
+                    sum = v.w[i]; len = 1;
+                    while (i + len < g && v.row[i + len] == r) { sum = __dadd_rn(sum, v.w[i + len]); ++len; }
+                }
             }
+            const unsigned bal = __ballot_sync(FULL, head);
+            if (lane == 0) cs.hcount[warp] = __popc(bal);
+            __syncthreads();
+            int before = 0, total = 0;
+            for (int w2 = 0; w2 < nw; ++w2) { const int c = cs.hcount[w2]; if (w2 < warp) before += c; total += c; }
+            const int rank = d + before + __popc(bal & ((1u << lane) - 1u));
+            __syncthreads();                                   // every read of this chunk is done
+            if (head) { v.row[rank] = r; v.w[rank] = sum; v.mult[rank] = len; }
+            d += total;
+            __syncthreads();
         }
-        const unsigned bal = __ballot_sync(FULL, head);
-        if (lane == 0) cs.hcount[warp] = __popc(bal);
-        __syncthreads();
-        int before = 0, total = 0;
-        for (int w2 = 0; w2 < nw; ++w2) { const int c = cs.hcount[w2]; if (w2 < warp) before += c; total += c; }
-        const int rank = d + before + __popc(bal & ((1u << lane) - 1u));
-        __syncthreads();                                   // every read of this chunk is done
-        if (head) { v.row[rank] = r; v.w[rank] = sum; v.mult[rank] = len; }
-        d += total;
-        __syncthreads();
+        // store the row-ordered column
+        if (tid == 0) {
+            const unsigned long long base = d > 0 ? atomicAdd(a.f_top, (unsigned long long)d) : 0ull;
+            if (d > 0 && base + d > a.f_cap) set_status(a.status, ST_POOL);
+            cs.fpos = base;
+        }
+        if (__syncthreads_or(read_status(a.status) != ST_OK)) { __syncthreads(); if (tid == 0) cs.k = -1; return -2; }
+        const unsigned long long fpos = cs.fpos;
+        for (int i = tid; i < d; i += nt) { a.f_row[fpos + i] = v.row[i]; a.f_val[fpos + i] = v.w[i]; }
+        if (tid == 0) { a.f_start[k] = (int64_t)fpos; a.f_len[k] = d; }
+        mark(11);
     }
-
-    // ---------------------------------------------------------------- store row-ordered column
-    if (tid == 0) {
-        const unsigned long long base = d > 0 ? atomicAdd(a.f_top, (unsigned long long)d) : 0ull;
-        if (d > 0 && base + d > a.f_cap) set_status(a.status, ST_POOL);
-        cs.fpos = base;
-    }
-    __syncthreads();
-    if (read_status(a.status) != ST_OK) { __syncthreads(); if (tid == 0) cs.k = -1; return -2; }
-    const unsigned long long fpos = cs.fpos;
-    for (int i = tid; i < d; i += nt) { a.f_row[fpos + i] = v.row[i]; a.f_val[fpos + i] = v.w[i]; }
-    if (tid == 0) { a.f_start[k] = (int64_t)fpos; a.f_len[k] = d; }
     if (d == 0) {
         if (tid == 0) a.D[k] = 0.0;
         __syncthreads();
@@ -924,14 +1248,16 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     }
 
     // ---------------------------------------------------------------- weight sort
-    const int P2 = next_pow2(d);
-    for (int i = d + tid; i < P2; i += nt) {
-        v.row[i] = ROW_SENTINEL; v.w[i] = __longlong_as_double((long long)WBITS_SENTINEL); v.mult[i] = 0;
-    }
     __syncthreads();
-    if (requester) prof_mark(a, ws, 11);
-    coop_sort<1>(v, P2, tile, global_ws ? a.block_cap : 0);
-    if (requester) prof_mark(a, ws, 12);
+    if (!sample || !coop_weight_phase(v, d, bbuf, a.block_cap, cs, gbo)) {
+        const int P2 = next_pow2(d);
+        for (int i = d + tid; i < P2; i += nt) {
+            v.row[i] = ROW_SENTINEL; v.w[i] = __longlong_as_double((long long)WBITS_SENTINEL); v.mult[i] = 0;
+        }
+        __syncthreads();
+        coop_sort<1>(v, P2, tile, global_ws ? a.block_cap : 0);
+    }
+    mark(12);
 
     // ---------------------------------------------------------------- canonical suffix scan
     // each 32-lane tile of the reversed weights: Hillis-Steele within the tile
@@ -990,7 +1316,7 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     __syncthreads();
     const double Dk = v.S[0];
     if (tid == 0) a.D[k] = Dk;
-    if (requester) prof_mark(a, ws, 13);
+    mark(13);
 
     // ---------------------------------------------------------------- sample clique tree + append
     // For a working set in global memory, a coarse copy of M (every
@@ -1041,7 +1367,7 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
         if (!append_fill(a, act, lo, hi, c)) { ok = false; break; }
     }
     if (tid == 0) ws.n_fill += (unsigned long long)(d - 1);
-    if (requester) prof_mark(a, ws, 14);
+    mark(14);
 
     // ---------------------------------------------------------------- levels, release, decrements
     {
@@ -1060,7 +1386,7 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     }
     __syncthreads();
     if (tid == 0) cs.k = -1;
-    if (requester) prof_mark(a, ws, 15);
+    mark(15);
     return requester ? (keep >= 0 ? keep : -1) : -1;
 }
 

@@ -215,3 +215,15 @@ def test_warp_only_paths_match(P, monkeypatch):
     perm = W.random_ordering(n, 3)
     _check(P, A, perm, 5)
     _check(P, A, perm, 5, big_threshold=32)
+
+
+@pytest.mark.parametrize("sample_sort", ["1", "0"])
+def test_rmat_bit_identical(P, monkeypatch, sample_sort):
+    """R-MAT scale 15 (hubs of a few thousand neighbours, fill that piles up
+    on the last vertices): the cooperative path with working sets in global
+    memory, by sample sort and by the bitonic network, gives the oracle's
+    factor."""
+    monkeypatch.setenv("PARAC_SAMPLE_SORT", sample_sort)
+    A, perm, seed, _ = W.config("rmat-15")
+    _, st = _check(P, A, perm, seed)
+    assert st["vertices_global_path"] > 0
