@@ -56,7 +56,11 @@ typedef enum {
 } parac_status;
 
 enum { PARAC_KIND_AUTO = 0, PARAC_KIND_LAPLACIAN = 1, PARAC_KIND_SDDM = 2 };
-enum { PARAC_SPTRSV_AUTO = 0, PARAC_SPTRSV_SYNCFREE = 1, PARAC_SPTRSV_LEVELSET = 2 };
+/* Triangular-solve strategies (all sync-free, rows in dependency-level
+ * order): WARP gives each row a warp of 32 lanes (and a whole block to a row
+ * of more than 512 entries); SUB8 / SUB4 give each row 8 / 4 lanes, so a warp
+ * works on 4 / 8 short rows at once.  AUTO is WARP. */
+enum { PARAC_SPTRSV_AUTO = 0, PARAC_SPTRSV_WARP = 1, PARAC_SPTRSV_SUB8 = 2, PARAC_SPTRSV_SUB4 = 3 };
 
 /*
  * Options.  parac_opts_default() fills the defaults; a NULL opts pointer
@@ -197,6 +201,26 @@ parac_status parac_precond_apply(parac_factor_t G, const double *r, double *z);
  * Errors: EINVAL, ETIMEOUT, ECUDA.
  */
 parac_status parac_precond_apply_noalloc(parac_factor_t G, const double *r, double *z);
+
+/*
+ * parac_autotune -- choose the schedule for a class of inputs by timing
+ * candidates on representative systems (the batched form's autotuned
+ * schedule).  The factor never depends on the schedule, so tuning changes
+ * only time.
+ *   count, systems, seed   as for parac_factor_many (count >= 1)
+ *   base      options to start from (NULL: defaults); kind, precision,
+ *             workspace sizes and stream are kept
+ *   best      receives base with warps_per_block, queue_chunk, big_threshold
+ *             (timed on parac_factor_many) and sptrsv (timed on
+ *             parac_precond_apply with the fastest factor) set
+ *   report    optional JSON of every candidate's time, cap bytes (NULL / 0:
+ *             none)
+ * Factors and work space made while tuning are freed before returning.
+ * Errors: EINVAL (also when report is too small), and any error of
+ * parac_factor_many or parac_precond_apply.
+ */
+parac_status parac_autotune(int32_t count, const parac_system *systems, uint64_t seed, const parac_opts *base,
+                            parac_opts *best, char *report, size_t cap);
 
 /*
  * parac_factor_export -- copy the factor out (label space, ground removed).

@@ -1001,7 +1001,8 @@ SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, co
     A.prec = G->prec;
     const double n = G->n > 0 ? (double)G->n : 1.0;
     A.lanes_spmv = lanes_for((double)nnzL / n);
-    A.lanes_trsv = 32;      // one row per warp: measured fastest on the 128^3 grid (rows of ~11 entries)
+    // one row per warp unless the handle asks for sub-warp rows
+    A.lanes_trsv = G->sptrsv == PARAC_SPTRSV_SUB8 ? 8 : G->sptrsv == PARAC_SPTRSV_SUB4 ? 4 : 32;
     A.trsv_warps = SOLVE_WARPS;
     if (const char *e = getenv("PARAC_TRSV_LANES")) A.lanes_trsv = atoi(e);
     if (const char *e = getenv("PARAC_TRSV_WARPS")) A.trsv_warps = std::max(1, std::min(32, atoi(e)));
@@ -1409,6 +1410,102 @@ extern "C" parac_status parac_precond_apply(parac_factor_t G, const double *r, d
             }
         }
         if (read_dev_status(G, st) != ST_OK) { set_err("triangular solve wait exceeded the spin limit"); return PARAC_ETIMEOUT; }
+        return PARAC_OK;
+    });
+}
+
+// ------------------------------------------------------------------ autotuner
+// Times candidate schedules on the caller's systems and keeps the fastest.
+// The elimination candidates vary the worker warps per CTA, the ready-queue
+// claim size and the threshold between the per-warp and the CTA-cooperative
+// paths; the factor is the same for every candidate (the determinism of the
+// schedule), so only time decides.  The solve candidates are the sync-free
+// triangular-solve layouts, timed on preconditioner applies with the best
+// factor.
+extern "C" parac_status parac_autotune(int32_t count, const parac_system *systems, uint64_t seed,
+                                       const parac_opts *base, parac_opts *best, char *report, size_t cap)
+{
+    return guarded([&]() -> parac_status {
+        if (count < 1 || !systems || !best) { set_err("bad arguments to parac_autotune"); return PARAC_EINVAL; }
+        parac_opts b0;
+        parac_opts_default(&b0);
+        if (base) b0 = *base;
+        struct Cand { int warps, qc, big; double ms; };
+        std::vector<Cand> fc = {{8, 1, 0, 0}, {8, 2, 0, 0}, {8, 4, 0, 0}, {8, 1, 64, 0}, {8, 1, 256, 0}, {4, 1, 0, 0}};
+        std::vector<parac_factor_t> hs((size_t)count, nullptr);
+        auto free_all = [&]() { for (auto &h : hs) { parac_factor_free(h); h = nullptr; } };
+        auto run = [&](const parac_opts &o) -> double {
+            const auto t0 = std::chrono::steady_clock::now();
+            const parac_status r = parac_factor_many(count, systems, seed, &o, hs.data());
+            const auto t1 = std::chrono::steady_clock::now();
+            if (r != PARAC_OK) { free_all(); throw StatusFail{r}; }
+            return std::chrono::duration<double, std::milli>(t1 - t0).count();
+        };
+        {   // warm-up: allocations, module load
+            run(b0);
+            free_all();
+        }
+        int bi = 0;
+        for (size_t c = 0; c < fc.size(); ++c) {
+            parac_opts o = b0;
+            o.warps_per_block = fc[c].warps; o.queue_chunk = fc[c].qc; o.big_threshold = fc[c].big;
+            double t = run(o);
+            free_all();
+            t = std::min(t, run(o));
+            free_all();
+            fc[c].ms = t;
+            if (t < fc[(size_t)bi].ms) bi = (int)c;
+        }
+        parac_opts o = b0;
+        o.warps_per_block = fc[(size_t)bi].warps; o.queue_chunk = fc[(size_t)bi].qc; o.big_threshold = fc[(size_t)bi].big;
+        run(o);
+        // solve strategies on the best factor
+        int64_t nmax = 0;
+        for (auto h : hs) nmax = std::max<int64_t>(nmax, h->n);
+        cudaStream_t st = (cudaStream_t)b0.stream;
+        DBuf r = dalloc<double>((size_t)std::max<int64_t>(nmax, 1), st), z = dalloc<double>((size_t)std::max<int64_t>(nmax, 1), st);
+        CK(cudaMemsetAsync(r.p, 0x3f, 8 * (size_t)std::max<int64_t>(nmax, 1), st));   // every entry 0x3f3f...3f
+        CK(cudaStreamSynchronize(st));
+        struct SCand { int strat; double ms; };
+        std::vector<SCand> sc = {{PARAC_SPTRSV_WARP, 0}, {PARAC_SPTRSV_SUB8, 0}, {PARAC_SPTRSV_SUB4, 0}};
+        int si = 0;
+        for (size_t c = 0; c < sc.size(); ++c) {
+            for (auto h : hs) h->sptrsv = sc[c].strat;
+            double t = 1e300;
+            for (int rep = 0; rep < 3; ++rep) {
+                const auto t0 = std::chrono::steady_clock::now();
+                for (auto h : hs) {
+                    const parac_status q = parac_precond_apply(h, r.as<double>(), z.as<double>());
+                    if (q != PARAC_OK) { free_all(); throw StatusFail{q}; }
+                }
+                const auto t1 = std::chrono::steady_clock::now();
+                t = std::min(t, std::chrono::duration<double, std::milli>(t1 - t0).count());
+            }
+            sc[c].ms = t;
+            if (t < sc[(size_t)si].ms) si = (int)c;
+        }
+        free_all();
+        o.sptrsv = sc[(size_t)si].strat;
+        *best = o;
+        if (report && cap > 0) {
+            std::string js = "{\"factor\": [";
+            char buf[256];
+            for (size_t c = 0; c < fc.size(); ++c) {
+                snprintf(buf, sizeof buf, "%s{\"warps_per_block\": %d, \"queue_chunk\": %d, \"big_threshold\": %d, \"ms\": %.3f}",
+                         c ? ", " : "", fc[c].warps, fc[c].qc, fc[c].big, fc[c].ms);
+                js += buf;
+            }
+            js += "], \"solve\": [";
+            for (size_t c = 0; c < sc.size(); ++c) {
+                snprintf(buf, sizeof buf, "%s{\"sptrsv\": %d, \"ms\": %.3f}", c ? ", " : "", sc[c].strat, sc[c].ms);
+                js += buf;
+            }
+            snprintf(buf, sizeof buf, "], \"best\": {\"warps_per_block\": %d, \"queue_chunk\": %d, \"big_threshold\": %d, \"sptrsv\": %d}}",
+                     o.warps_per_block, o.queue_chunk, o.big_threshold, o.sptrsv);
+            js += buf;
+            if (js.size() + 1 > cap) { set_err("report buffer too small (%zu bytes needed)", js.size() + 1); return PARAC_EINVAL; }
+            memcpy(report, js.c_str(), js.size() + 1);
+        }
         return PARAC_OK;
     });
 }

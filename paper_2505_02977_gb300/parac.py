@@ -61,12 +61,15 @@ _lib.parac_status_string.argtypes = [C.c_int]
 _lib.parac_status_string.restype = C.c_char_p
 _lib.parac_last_error.argtypes = []
 _lib.parac_last_error.restype = C.c_char_p
+_lib.parac_autotune.argtypes = [C.c_int32, C.POINTER(parac_system), C.c_uint64, C.POINTER(parac_opts),
+                                C.POINTER(parac_opts), C.c_char_p, C.c_size_t]
+_lib.parac_autotune.restype = C.c_int
 _lib.parac_kernel_launches.argtypes = []
 _lib.parac_kernel_launches.restype = C.c_uint64
 
 EXPORTED = ("parac_opts_default", "parac_factor", "parac_pcg", "parac_factor_many", "parac_factor_export",
             "parac_factor_stats", "parac_factor_free", "parac_precond_apply", "parac_status_string",
-            "parac_last_error", "parac_kernel_launches", "parac_precond_apply_noalloc")
+            "parac_last_error", "parac_kernel_launches", "parac_precond_apply_noalloc", "parac_autotune")
 
 
 class ParacError(RuntimeError):
@@ -154,6 +157,28 @@ def parac_factor_many(systems, seed=0, opts=None):
     _check(_lib.parac_factor_many(len(systems), arr, seed, C.byref(opts) if opts is not None else None, out),
            "parac_factor_many")
     return [Factor(out[i]) for i in range(len(systems))]
+
+
+def _systems(systems):
+    keep = []
+    arr = (parac_system * len(systems))()
+    for i, (n, cp, ri, va, od) in enumerate(systems):
+        ptrs = []
+        for a, dt in ((cp, np.int64), (ri, np.int32), (va, np.float64), (od, np.int32)):
+            p, k = _ptr(a, dt)
+            ptrs.append(p); keep.append(k)
+        arr[i] = parac_system(n, *ptrs)
+    return arr, keep
+
+
+def parac_autotune(systems, seed=0, opts=None):
+    """Tuned options for systems like these: (opts, report dict)."""
+    arr, keep = _systems(systems)
+    best = parac_opts()
+    buf = C.create_string_buffer(8192)
+    _check(_lib.parac_autotune(len(systems), arr, seed, C.byref(opts) if opts is not None else None,
+                               C.byref(best), buf, 8192), "parac_autotune")
+    return best, json.loads(buf.value.decode())
 
 
 def parac_pcg(G, n, colptr, rowind, val, B, tol=1e-8, maxit=1000, X=None, nrhs=None, allow_noconv=True):

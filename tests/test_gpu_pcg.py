@@ -218,3 +218,39 @@ def test_grid3d_128_full_size(P):
     assert status == "PARAC_OK" and rr[0] <= 1e-8 and rro <= 1e-8
     assert abs(int(it[0]) - ito) <= 2
     G.free()
+
+
+@pytest.mark.parametrize("strategy", [1, 2, 3])
+def test_sptrsv_strategies(P, strategy):
+    """Every triangular-solve layout applies the same preconditioner (up to
+    the order of the row sums) and PCG reaches 1e-8 within one iteration of
+    the oracle."""
+    for case in (0, 1):
+        A, perm, seed, b = _cases()[case]
+        G = _factor(P, A, perm, seed, sptrsv=strategy)
+        F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)
+        r = np.random.default_rng(case).standard_normal(A.n)
+        z = P.parac_precond_apply(G, r)
+        zr = oracle.precond_apply(F, perm, r)
+        assert np.linalg.norm(z - zr) <= 1e-12 * np.linalg.norm(zr)
+        xo, ito, _ = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, b, 1e-8, 1000)
+        x, it, rr, status = P.parac_pcg(G, A.n, None, None, None, b, tol=1e-8, maxit=1000)
+        assert status == "PARAC_OK" and rr[0] <= 1e-8 and abs(int(it[0]) - ito) <= 1
+        G.free()
+
+
+def test_autotune(P):
+    """The tuner returns a complete schedule; factors made with it are the
+    default schedule's, bit for bit; every candidate was timed."""
+    from tests.helpers import same_factor
+    batch = W.sddm_batch(6, nmin=500, nmax=5000, seed=5)
+    systems = [(A.n, A.colptr, A.rowind, A.val, perm) for (A, perm, b) in batch]
+    best, rep = P.parac_autotune(systems, seed=7)
+    assert len(rep["factor"]) >= 4 and len(rep["solve"]) == 3
+    assert all(c["ms"] > 0 for c in rep["factor"] + rep["solve"])
+    assert best.sptrsv in (1, 2, 3) and best.warps_per_block in (4, 8) and best.queue_chunk >= 1
+    tuned = P.parac_factor_many(systems, seed=7, opts=best)
+    plain = P.parac_factor_many(systems, seed=7)
+    for Gt, Gp in zip(tuned, plain):
+        assert same_factor(Gt.export(), Gp.export())
+        Gt.free(); Gp.free()
