@@ -10,7 +10,12 @@ the setup time measured with CUDA events around parac_factor.  Time-to-solution
 (setup + PCG) is reported beside it.
 
   python bench.py [--steps K] [--warmup W] [--workload grid3d-128] [--prec 64|32]
+                  [--ordering random|nnz]
+  python bench.py --workload sddm-batch-200   # 200 SDDM systems: parac_factor_many vs a loop
   python bench.py --impl reference     # the CPU oracle on the same workload
+
+Workloads: grid3d-128 (default), grid2d-64, rmat-N (R-MAT scale N), rmat-24
+(32 right-hand sides, block PCG), sddm-batch-200.
 
 Under torchrun (--gpus N > 1) every rank factors and solves its own replica
 of the workload (the elimination does not shard; replicas only).
@@ -35,6 +40,10 @@ WORKLOAD_DESC = {
     "grid3d-128": "3D 7-point grid Laplacian 128^3 (n=2,097,152), weights U[1,10), random ordering",
     "grid2d-64": "2D 5-point grid Laplacian 64x64 (n=4096), unit weights, random ordering",
     "rmat-22": "R-MAT scale 22, edge factor 16, lognormal(0,1) weights, largest component, random ordering",
+    "rmat-24": "R-MAT scale 24, edge factor 16, lognormal(0,1) weights, largest component, random ordering, "
+               "32 right-hand sides",
+    "sddm-batch-200": "200 SDDM systems, n log-uniform in [1e3, 2e5] (2D grid / random geometric / Erdos-Renyi), "
+                      "factorised in one parac_factor_many launch, one right-hand side each",
 }
 
 
@@ -217,7 +226,11 @@ def run_ours(args, world, rank, local, pg):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    if args.workload.startswith("sddm-batch"):
+        return run_batch(args, world, rank, local, pg)
     A, perm, seed, b = W.config(args.workload)
+    if args.ordering == "nnz":
+        perm = W.nnz_sorted_ordering(A, seed + 1000)
     td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     cp, ri, va, od, bd = td(A.colptr), td(A.rowind), td(A.val), td(perm), td(b)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # > L2 (129 MB)
@@ -248,7 +261,7 @@ def run_ours(args, world, rank, local, pg):
         ev[s][1].record()
         x, it, rr, status = P.parac_pcg(G, A.n, None, None, None, bd, tol=args.tol, maxit=2000)
         ev[s][2].record()
-        iters.append(int(it[0])); relres.append(float(rr[0])); statuses.append(status)
+        iters.append(int(max(it))); relres.append(float(max(rr))); statuses.append(status)
         if stats is None:
             stats = G.stats()
         G.free()
@@ -266,7 +279,7 @@ def run_ours(args, world, rank, local, pg):
     # its launch) or the triangular-solve pair of the preconditioner (timed here)
     G = P.parac_factor(A.n, cp, ri, va, od, seed, opts)
     st_el = G.stats()
-    r = td(np.random.default_rng(0).standard_normal(A.n))
+    r = td(np.random.default_rng(0).standard_normal(A.n))      # one right-hand side: the single-vector solves
     z = torch.empty_like(r)
     P.parac_precond_apply(G, r, z)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -328,7 +341,8 @@ def run_ours(args, world, rank, local, pg):
         "ms_per_step": mean_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload), "n": A.n, "nnz_L": A.nnz,
-                   "nnz_G": nnzG, "G_precision": args.prec, "tol": args.tol,
+                   "nnz_G": nnzG, "G_precision": args.prec, "tol": args.tol, "ordering": args.ordering,
+                   "nrhs": 1 if b.ndim == 1 else int(b.shape[1]),
                    "l2": "flushed before every step (256 MB write)", "parallelism": f"replicas x{world}"},
         "tts_ms": statistics.median(step_ms), "setup_ms": statistics.median(setup_ms),
         "pcg_ms": statistics.median(pcg_ms), "pcg_iters": statistics.median(iters),
@@ -346,6 +360,94 @@ def run_ours(args, world, rank, local, pg):
     return 0
 
 
+def run_batch(args, world, rank, local, pg):
+    """sddm-batch-200: one step = parac_factor_many of the 200 systems (schedule
+    from parac_autotune on every 10th system, tuned once before the timed region)
+    and one PCG solve per system.  value = sum nnz(G) / factor_many time; the
+    same systems factored one parac_factor call at a time are timed beside it."""
+    import torch
+    from paper_2505_02977_gb300 import parac as P
+    from paper_2505_02977_gb300 import workloads as W
+    dev = torch.device("cuda", local)
+    batch = W.sddm_batch(200)
+    td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    systems = [(A.n, td(A.colptr), td(A.rowind), td(A.val), td(perm)) for (A, perm, b) in batch]
+    rhs = [td(b) for (A, perm, b) in batch]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    base = P.parac_opts_default(g_precision=args.prec)
+    opts, tune_report = P.parac_autotune(systems[::10], 31, base)
+    seed = 31
+
+    def solve_all(Gs):
+        its, rrs = [], []
+        for (A, perm, b), G, bd in zip(batch, Gs, rhs):
+            x, it, rr, st = P.parac_pcg(G, A.n, None, None, None, bd, tol=args.tol, maxit=2000)
+            its.append(int(it[0])); rrs.append(float(rr[0]))
+        return its, rrs
+
+    for _ in range(args.warmup):
+        Gs = P.parac_factor_many(systems, seed, opts)
+        solve_all(Gs)
+        for G in Gs: G.free()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    barrier(pg)
+    torch.cuda.synchronize()
+    launches0 = P.parac_kernel_launches()
+    clocks.start()
+    setup_ms, pcg_ms, its_all, rr_all, nnzG = [], [], [], [], 0
+    for s in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Gs = P.parac_factor_many(systems, seed, opts)
+        t1 = time.perf_counter()
+        its, rrs = solve_all(Gs)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        setup_ms.append(1e3 * (t1 - t0)); pcg_ms.append(1e3 * (t2 - t1))
+        its_all += its; rr_all += rrs
+        nnzG = sum(G.stats()["nnz_G"] for G in Gs)
+        for G in Gs: G.free()
+    clk = clocks.stop()
+    launches = P.parac_kernel_launches() - launches0
+    # one system at a time (same schedule), for the batched-vs-loop ratio
+    loop_ms = []
+    for _ in range(2):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Gs = [P.parac_factor(*sy, seed + i, opts) for i, sy in enumerate(systems)]
+        torch.cuda.synchronize()
+        loop_ms.append(1e3 * (time.perf_counter() - t0))
+        loop_nnz = sum(G.stats()["nnz_G"] for G in Gs)
+        for G in Gs: G.free()
+    total_setup_s = allreduce_max(pg, sum(setup_ms) * 1e-3)
+    value = world * nnzG * args.steps / total_setup_s / 1e6
+    loop_value = loop_nnz / (min(loop_ms) * 1e-3) / 1e6
+    line = {
+        "metric": "setup Mnnz(G)/s (batched parac_factor_many); time-to-solution to rel-res 1e-8 in tts_ms",
+        "value": value, "unit": "Mnnz(G)/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": allreduce_max(pg, statistics.mean([a + b for a, b in zip(setup_ms, pcg_ms)])),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC[args.workload], "systems": len(batch),
+                   "n_total": sum(A.n for A, _, _ in batch), "nnz_G": nnzG, "G_precision": args.prec,
+                   "tol": args.tol, "l2": "flushed before every step (256 MB write)",
+                   "parallelism": f"replicas x{world}", "schedule": tune_report["best"]},
+        "setup_ms": statistics.median(setup_ms), "pcg_ms": statistics.median(pcg_ms),
+        "tts_ms": statistics.median([a + b for a, b in zip(setup_ms, pcg_ms)]),
+        "pcg_iters_mean": float(np.mean(its_all)), "pcg_iters_max": int(max(its_all)),
+        "true_relres_max": max(rr_all),
+        "one_at_a_time": {"value": loop_value, "unit": "Mnnz(G)/s", "setup_ms": min(loop_ms), "nnz_G": loop_nnz,
+                          "batched_over_loop": value / world / loop_value},
+        "autotune": tune_report, "gpu_launches": int(launches), "clocks": clk,
+        "roofline": None, "cpu_baseline": None, "e2e": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,6 +459,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ordering", default="random", choices=["random", "nnz"])
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
     try:

@@ -1192,7 +1192,7 @@ void graph_key(uint64_t (&k)[GraphCache::KEY], const SolveArgs &A, int form, int
     k[i++] = (uint64_t)(uintptr_t)A.Fcp; k[i++] = (uint64_t)(uintptr_t)A.Frp;
     k[i++] = (uint64_t)A.n; k[i++] = (uint64_t)A.prec; k[i++] = (uint64_t)A.lanes_spmv; k[i++] = (uint64_t)A.lanes_trsv;
     k[i++] = (uint64_t)A.trsv_blocks; k[i++] = (uint64_t)A.trsv_warps; k[i++] = (uint64_t)A.spin_limit;
-    k[i++] = (uint64_t)(uintptr_t)A.status; k[i++] = (uint64_t)(uintptr_t)A.trace;
+    k[i++] = (uint64_t)(uintptr_t)A.status;
     k[i++] = (uint64_t)(uintptr_t)x; k[i++] = (uint64_t)(uintptr_t)y; k[i++] = (uint64_t)(uintptr_t)partials;
     k[i++] = (uint64_t)(uintptr_t)state; k[i++] = (uint64_t)vec_blocks; k[i++] = (uint64_t)pstride;
 }
@@ -1388,27 +1388,10 @@ extern "C" parac_status parac_precond_apply(parac_factor_t G, const double *r, d
         PcgBuffers &Bf = G->cache.B;
         CK(cudaMemsetAsync(G->status.p, 0, 4, st));
         const size_t bytes = 8 * (size_t)G->n;
-        // optional per-row trace of the forward solve, written to the file named by PARAC_TRSV_TRACE
-        const char *trace_path = getenv("PARAC_TRSV_TRACE");
-        DBuf trace;
-        if (trace_path) {
-            trace = dalloc<long long>((size_t)G->n * 8, st);
-            A.trace = trace.as<long long>();
-        }
         CK(cudaMemcpyAsync(Bf.r, r, bytes, cudaMemcpyDefault, st));
         CK(precond_apply(A, Bf, Bf.r, Bf.z, st));
         CK(cudaMemcpyAsync(z, Bf.z, bytes, cudaMemcpyDefault, st));
         CK(cudaStreamSynchronize(st));
-        if (trace_path) {
-            std::vector<long long> tr((size_t)G->n * 8);
-            CK(cudaMemcpy(tr.data(), trace.p, 64 * (size_t)G->n, cudaMemcpyDeviceToHost));
-            if (FILE *f = fopen(trace_path, "wb")) {
-                const long long nn = G->n;
-                fwrite(&nn, 8, 1, f);
-                fwrite(tr.data(), 8, tr.size(), f);
-                fclose(f);
-            }
-        }
         if (read_dev_status(G, st) != ST_OK) { set_err("triangular solve wait exceeded the spin limit"); return PARAC_ETIMEOUT; }
         return PARAC_OK;
     });

@@ -117,7 +117,6 @@ struct SolveArgs {
     int32_t trsv_warps;           // warps per block of the triangular solves
     long long spin_limit;
     int32_t *status;
-    long long *trace;             // optional per-row trace of the forward solve [n * 8]
     // optional row groups of the one-row-per-warp solves (row_groups with
     // LONG_ROW_SINGLE and trsv_warps warps); nullptr: fixed groups
     const int32_t *gs_f, *gs_b;

@@ -316,19 +316,96 @@ __device__ __forceinline__ XT block_row_sum(XT acc, XT *red)
 // with every row's dependencies at earlier positions and the rows of one
 // level contiguous.  operm[j] is the original index of position j.
 //
-// Forward: y[j] = rhs[operm[j]] - sum_{c<j} F(j,c) y[c] over CSR row j; also
-// resets the backward unknown z[j] to the sentinel.  Every load that does not
-// depend on other rows is issued before the dependency polls.
+// Each row is handled by S lanes (S = 32: a warp).  A warp works a row ahead:
+// it issues the loads of its current row's unknowns, then fetches the next
+// row's pointers, indices, values and right-hand side (which depend on no
+// other row), and only then waits for the current unknowns -- so when a row's
+// dependencies are published, its own data is already in registers and it
+// costs one round of polls.  Rows beyond S*RPF entries continue with
+// dot_ready.
 //
 // With a group table gs (one row per warp, S == 32), rows are handed out in
 // groups gs[g]..gs[g+1]: up to one row per warp, or one row longer than
 // LONG_ROW_SINGLE entries shared by every warp of the block (the rows that
 // collect the most fill, e.g. of hub vertices, would otherwise leave one warp
 // to walk them alone on the critical path).
+constexpr int RPF = 4;
+
+template <int S, bool REV, typename VT>
+__device__ __forceinline__ void fetch_chunk(int64_t b, int64_t e, int sl, const int32_t *idx, const VT *v,
+                                            int32_t (&cc)[RPF], VT (&vv)[RPF])
+{
+    const int64_t len = e - b;
+#pragma unroll
+    for (int r = 0; r < RPF; ++r) {
+        const int64_t u = sl + (int64_t)r * S;
+        const int64_t t = REV ? e - 1 - u : b + u;
+        cc[r] = u < len ? idx[t] : -1;
+        vv[r] = u < len ? v[t] : (VT)0;
+    }
+}
+
+template <typename XT>
+__device__ __forceinline__ void issue_x(const XT *x, const int32_t (&cc)[RPF], XT (&xx)[RPF])
+{
+#pragma unroll
+    for (int r = 0; r < RPF; ++r) xx[r] = cc[r] >= 0 ? ld_poll(x + cc[r]) : (XT)0;
+}
+
+// Wait until the chunk's unknowns are published (polls in rounds with
+// back-off), then add its terms in entry order.
+template <typename VT, typename XT>
+__device__ __forceinline__ bool finish_chunk(const XT *x, const int32_t (&cc)[RPF], const VT (&vv)[RPF],
+                                             XT (&xx)[RPF], XT &acc, long long spin_limit, const int32_t *status)
+{
+    long long spins = 0;
+    unsigned ns = 16;
+    for (;;) {
+        bool pending = false;
+#pragma unroll
+        for (int r = 0; r < RPF; ++r)
+            if (cc[r] >= 0 && is_sentinel(xx[r])) pending = true;
+        if (!pending) break;
+        ++spins;
+        if ((spins & 127) == 0 && (spins > spin_limit || read_status(status) != ST_OK)) return false;
+        __nanosleep(ns);
+        if (ns < g_poll_max_ns) ns <<= 1;
+#pragma unroll
+        for (int r = 0; r < RPF; ++r)
+            if (cc[r] >= 0 && is_sentinel(xx[r])) xx[r] = ld_poll(x + cc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < RPF; ++r) acc += (XT)vv[r] * xx[r];
+    return true;
+}
+
+// Row (position) of this lane group in group g, or -1; `shared` when the
+// group is one long row for the whole block (block-uniform).
+template <int S>
+__device__ __forceinline__ int64_t row_of(int64_t g, int64_t ngroups, const int32_t *gs, const int64_t *ptr,
+                                          int32_t n, int rows_per_group, int my, bool rev, bool &shared)
+{
+    shared = false;
+    if (g >= ngroups) return -1;
+    if (gs) {
+        const int32_t k0 = gs[g], k1 = gs[g + 1];
+        if (k1 - k0 == 1) {
+            const int64_t j0 = rev ? (int64_t)n - 1 - k0 : k0;
+            if (ptr[j0 + 1] - ptr[j0] > LONG_ROW_SINGLE) { shared = true; return j0; }
+        }
+        const int64_t kk = (int64_t)k0 + my;
+        return kk < k1 ? (rev ? (int64_t)n - 1 - kk : kk) : -1;
+    }
+    const int64_t kk = g * rows_per_group + my;
+    return kk < n ? (rev ? (int64_t)n - 1 - kk : kk) : -1;
+}
+
+// Forward: y[j] = rhs[operm[j]] - sum_{c<j} F(j,c) y[c] over CSR row j; also
+// resets the backward unknown z[j] to the sentinel.
 template <int S, typename VT, typename XT>
 __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, const VT *v, const int32_t *operm,
                            const double *rhs, XT *y, XT *zreset, const int32_t *gs, int32_t ngs,
-                           const PcgState *st, long long spin_limit, int32_t *status, long long *trace)
+                           const PcgState *st, long long spin_limit, int32_t *status)
 {
     __shared__ XT red[32];
     if (st && st->done) return;
@@ -338,75 +415,76 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
     const int rows_per_group = (blockDim.x / 32) * (32 / S);
     const int my = (threadIdx.x >> 5) * (32 / S) + sub;
     const int64_t ngroups = gs ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
-    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-        int64_t j;
-        if (gs) {
-            const int32_t p0 = gs[g], p1 = gs[g + 1];
-            if (p1 - p0 == 1 && rp[p0 + 1] - rp[p0] > LONG_ROW_SINGLE) {      // shared row (block-uniform)
-                const int64_t b = rp[p0], e = rp[p0 + 1];
-                const double rj = threadIdx.x == 0 ? rhs[operm[p0]] : 0.0;
-                XT acc = 0;
-                if (!dot_ready<false, VT, XT>(b, e, threadIdx.x, blockDim.x, ci, v, y, acc, spin_limit, status))
-                    set_status(status, ST_TIMEOUT);
-                const XT sum = block_row_sum(acc, red);
-                if (threadIdx.x == 0) {
-                    zreset[p0] = sentinel<XT>();
-                    st_pub(y + p0, to_x<XT>(rj) - sum);
-                }
-                __syncthreads();
-                continue;
+    int64_t g = blockIdx.x;
+    bool sh;
+    int64_t j = row_of<S>(g, ngroups, gs, rp, n, rows_per_group, my, false, sh);
+    int64_t b = 0, e = 0;
+    double rj = 0.0;
+    int32_t cc[RPF];
+    VT vv[RPF];
+    XT xx[RPF];
+    if (!sh && j >= 0) {
+        b = rp[j]; e = rp[j + 1];
+        if (sl == 0) rj = rhs[operm[j]];
+        fetch_chunk<S, false, VT>(b, e, sl, ci, v, cc, vv);
+    }
+    while (g < ngroups) {
+        const int64_t gn = g + gridDim.x;
+        if (sh) {                                      // one long row for the whole block
+            const int64_t bs = rp[j], es = rp[j + 1];
+            const double rs = threadIdx.x == 0 ? rhs[operm[j]] : 0.0;
+            XT acc = 0;
+            if (!dot_ready<false, VT, XT>(bs, es, threadIdx.x, blockDim.x, ci, v, y, acc, spin_limit, status))
+                set_status(status, ST_TIMEOUT);
+            const XT sum = block_row_sum(acc, red);
+            if (threadIdx.x == 0) {
+                zreset[j] = sentinel<XT>();
+                st_pub(y + j, to_x<XT>(rs) - sum);
             }
-            j = p0 + my;
-            if (j >= p1) continue;
-        } else {
-            j = g * rows_per_group + my;
-            if (j >= n) continue;
+            __syncthreads();
+            g = gn;
+            j = row_of<S>(g, ngroups, gs, rp, n, rows_per_group, my, false, sh);
+            if (!sh && j >= 0) {
+                b = rp[j]; e = rp[j + 1];
+                if (sl == 0) rj = rhs[operm[j]];
+                fetch_chunk<S, false, VT>(b, e, sl, ci, v, cc, vv);
+            }
+            continue;
         }
-        const long long t_arrive = trace ? global_ns() : 0;
-        const int64_t b = rp[j], e = rp[j + 1];
-        const double rj = (sl == 0) ? rhs[operm[j]] : 0.0;
-        XT acc = 0;
-        long long t_seen = 0;
-        int32_t seen_idx = -1;
-        const bool ok = trace ? dot_ready<false, VT, XT>(b, e, sl, S, ci, v, y, acc, spin_limit, status, &t_seen,
-                                                         &seen_idx)
-                              : dot_ready<false, VT, XT>(b, e, sl, S, ci, v, y, acc, spin_limit, status);
-        if (!ok) set_status(status, ST_TIMEOUT);
-        long long t_acc = 0;
-        if (trace) {                                   // latest dependency seen by any lane of the row
-            t_acc = global_ns();
+        if (j >= 0) issue_x(y, cc, xx);
+        bool shn;
+        const int64_t jn = row_of<S>(gn, ngroups, gs, rp, n, rows_per_group, my, false, shn);
+        int64_t bn = 0, en = 0;
+        double rjn = 0.0;
+        int32_t ccn[RPF];
+        VT vvn[RPF];
+        if (!shn && jn >= 0) {
+            bn = rp[jn]; en = rp[jn + 1];
+            if (sl == 0) rjn = rhs[operm[jn]];
+            fetch_chunk<S, false, VT>(bn, en, sl, ci, v, ccn, vvn);
+        }
+        if (j >= 0) {
+            XT acc = 0;
+            bool ok = finish_chunk<VT, XT>(y, cc, vv, xx, acc, spin_limit, status);
+            if (ok && e - b > (int64_t)RPF * S)
+                ok = dot_ready<false, VT, XT>(b, e, sl + RPF * S, S, ci, v, y, acc, spin_limit, status);
+            if (!ok) set_status(status, ST_TIMEOUT);
 #pragma unroll
-            for (int off = S / 2; off > 0; off >>= 1) {
-                const long long to = __shfl_xor_sync(smask, t_seen, off);
-                const int32_t io = __shfl_xor_sync(smask, seen_idx, off);
-                const long long ta = __shfl_xor_sync(smask, t_acc, off);
-                if (to > t_seen) { t_seen = to; seen_idx = io; }
-                if (ta > t_acc) t_acc = ta;
+            for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
+            if (sl == 0) {
+                zreset[j] = sentinel<XT>();
+                st_pub(y + j, to_x<XT>(rj) - acc);
             }
         }
-        const long long t_red0 = trace ? global_ns() : 0;
+        g = gn; j = jn; sh = shn; b = bn; e = en; rj = rjn;
 #pragma unroll
-        for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
-        const long long t_red = trace ? global_ns() : 0;
-        if (sl == 0) {
-            zreset[j] = sentinel<XT>();
-            st_pub(y + j, to_x<XT>(rj) - acc);
-            if (trace) {
-                trace[8 * j] = t_arrive;
-                trace[8 * j + 1] = t_seen;
-                trace[8 * j + 2] = global_ns();
-                trace[8 * j + 3] = seen_idx;
-                trace[8 * j + 4] = t_acc;
-                trace[8 * j + 5] = t_red0;
-                trace[8 * j + 6] = t_red;
-                trace[8 * j + 7] = e - b;
-            }
-        }
+        for (int r = 0; r < RPF; ++r) { cc[r] = ccn[r]; vv[r] = vvn[r]; }
     }
 }
 
 // Backward: z[j] = y[j] Dinv[j] - sum_{i>j} F(i,j) z[i] over CSC column j, in
-// decreasing position order; writes zout[operm[j]], resets y[j] to the
+// decreasing position order, walking each column from its last entry (whose
+// unknown was published first); writes zout[operm[j]], resets y[j] to the
 // sentinel, and accumulates r_orig . z into the block partial.
 template <int S, typename VT, typename XT>
 __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, const VT *v, const double *Dinv,
@@ -423,61 +501,92 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
     const int my = (threadIdx.x >> 5) * (32 / S) + sub;
     const int64_t ngroups = gs ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
     double dotacc = 0.0;
-    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-        int64_t kk;
-        if (gs) {
-            const int32_t k0 = gs[g], k1 = gs[g + 1];
-            const int64_t j0 = (int64_t)n - 1 - k0;
-            if (k1 - k0 == 1 && cp[j0 + 1] - cp[j0] > LONG_ROW_SINGLE) {      // shared column (block-uniform)
-                const int64_t b = cp[j0], e = cp[j0 + 1];
-                XT yj = 0;
-                double dj = 0.0, rj = 0.0;
-                int32_t o = 0;
-                if (threadIdx.x == 0) {
-                    yj = y[j0]; dj = Dinv[j0]; o = operm[j0];
-                    if (r_orig) rj = r_orig[o];
-                }
-                XT acc = 0;
-                if (!dot_ready<true, VT, XT>(b, e, threadIdx.x, blockDim.x, ri, v, z, acc, spin_limit, status))
-                    set_status(status, ST_TIMEOUT);
-                const XT sum = block_row_sum(acc, red);
-                if (threadIdx.x == 0) {
-                    const XT zj = to_x<XT>((double)yj * dj) - sum;
-                    y[j0] = sentinel<XT>();
-                    st_pub(z + j0, zj);
-                    zout[o] = (double)zj;
-                    dotacc += rj * (double)zj;
-                }
-                __syncthreads();
-                continue;
+    int64_t g = blockIdx.x;
+    bool sh;
+    int64_t j = row_of<S>(g, ngroups, gs, cp, n, rows_per_group, my, true, sh);
+    int64_t b = 0, e = 0;
+    XT yj = 0;
+    double dj = 0.0, rj = 0.0;
+    int32_t o = 0;
+    int32_t cc[RPF];
+    VT vv[RPF];
+    XT xx[RPF];
+    auto row_extras = [&](int64_t jj, XT &yv, double &dv, int32_t &ov, double &rv) {
+        if (sl == 0) {
+            yv = y[jj]; dv = Dinv[jj]; ov = operm[jj];
+            rv = r_orig ? r_orig[ov] : 0.0;
+        }
+    };
+    if (!sh && j >= 0) {
+        b = cp[j]; e = cp[j + 1];
+        row_extras(j, yj, dj, o, rj);
+        fetch_chunk<S, true, VT>(b, e, sl, ri, v, cc, vv);
+    }
+    while (g < ngroups) {
+        const int64_t gn = g + gridDim.x;
+        if (sh) {                                      // one long column for the whole block
+            const int64_t bs = cp[j], es = cp[j + 1];
+            XT ys = 0;
+            double ds = 0.0, rs = 0.0;
+            int32_t os = 0;
+            if (threadIdx.x == 0) {
+                ys = y[j]; ds = Dinv[j]; os = operm[j];
+                if (r_orig) rs = r_orig[os];
             }
-            kk = k0 + my;
-            if (kk >= k1) continue;
-        } else {
-            kk = g * rows_per_group + my;
-            if (kk >= n) continue;
+            XT acc = 0;
+            if (!dot_ready<true, VT, XT>(bs, es, threadIdx.x, blockDim.x, ri, v, z, acc, spin_limit, status))
+                set_status(status, ST_TIMEOUT);
+            const XT sum = block_row_sum(acc, red);
+            if (threadIdx.x == 0) {
+                const XT zj = to_x<XT>((double)ys * ds) - sum;
+                y[j] = sentinel<XT>();
+                st_pub(z + j, zj);
+                zout[os] = (double)zj;
+                dotacc += rs * (double)zj;
+            }
+            __syncthreads();
+            g = gn;
+            j = row_of<S>(g, ngroups, gs, cp, n, rows_per_group, my, true, sh);
+            if (!sh && j >= 0) {
+                b = cp[j]; e = cp[j + 1];
+                row_extras(j, yj, dj, o, rj);
+                fetch_chunk<S, true, VT>(b, e, sl, ri, v, cc, vv);
+            }
+            continue;
         }
-        const int64_t j = n - 1 - kk;
-        const int64_t b = cp[j], e = cp[j + 1];
-        XT yj = 0;
-        double dj = 0.0, rj = 0.0;
-        int32_t o = 0;
-        if (sl == 0) {
-            yj = y[j]; dj = Dinv[j]; o = operm[j];
-            if (r_orig) rj = r_orig[o];
+        if (j >= 0) issue_x(z, cc, xx);
+        bool shn;
+        const int64_t jn = row_of<S>(gn, ngroups, gs, cp, n, rows_per_group, my, true, shn);
+        int64_t bn = 0, en = 0;
+        XT yjn = 0;
+        double djn = 0.0, rjn = 0.0;
+        int32_t on = 0;
+        int32_t ccn[RPF];
+        VT vvn[RPF];
+        if (!shn && jn >= 0) {
+            bn = cp[jn]; en = cp[jn + 1];
+            row_extras(jn, yjn, djn, on, rjn);
+            fetch_chunk<S, true, VT>(bn, en, sl, ri, v, ccn, vvn);
         }
-        XT acc = 0;
-        const bool ok = dot_ready<true, VT, XT>(b, e, sl, S, ri, v, z, acc, spin_limit, status);
-        if (!ok) set_status(status, ST_TIMEOUT);
+        if (j >= 0) {
+            XT acc = 0;
+            bool ok = finish_chunk<VT, XT>(z, cc, vv, xx, acc, spin_limit, status);
+            if (ok && e - b > (int64_t)RPF * S)
+                ok = dot_ready<true, VT, XT>(b, e, sl + RPF * S, S, ri, v, z, acc, spin_limit, status);
+            if (!ok) set_status(status, ST_TIMEOUT);
 #pragma unroll
-        for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
-        if (sl == 0) {
-            const XT zj = to_x<XT>((double)yj * dj) - acc;
-            y[j] = sentinel<XT>();
-            st_pub(z + j, zj);
-            zout[o] = (double)zj;
-            dotacc += rj * (double)zj;
+            for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
+            if (sl == 0) {
+                const XT zj = to_x<XT>((double)yj * dj) - acc;
+                y[j] = sentinel<XT>();
+                st_pub(z + j, zj);
+                zout[o] = (double)zj;
+                dotacc += rj * (double)zj;
+            }
         }
+        g = gn; j = jn; sh = shn; b = bn; e = en; yj = yjn; dj = djn; o = on; rj = rjn;
+#pragma unroll
+        for (int r = 0; r < RPF; ++r) { cc[r] = ccn[r]; vv[r] = vvn[r]; }
     }
     if (partial) {
         const double s = block_sum(dotacc);
@@ -519,7 +628,7 @@ cudaError_t apply_t(const SolveArgs &A, const VT *vr, const VT *vc, XT *y, XT *z
     // group tables apply to one row per warp only
     const int32_t *gf = S == 32 ? A.gs_f : nullptr, *gb = S == 32 ? A.gs_b : nullptr;
     k_trsv_fwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Frp, A.Fcol, vr, A.operm, r, y, z, gf, A.ng_f,
-                                                             st, A.spin_limit, A.status, A.trace); count_launches(1);
+                                                             st, A.spin_limit, A.status); count_launches(1);
     k_trsv_bwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z,
                                                              zout, r, partial, gb, A.ng_b, st, A.spin_limit,
                                                              A.status); count_launches(1);

@@ -13,6 +13,8 @@ Stand-ins for the paper's matrices (Table I), which are not available here:
   * random geometric, Erdos-Renyi and grid SDDM systems with random diagonal
     excess for the 200 SDDM2023 "chimera" systems (Sec. V-C).
 """
+import os
+
 import numpy as np
 
 __all__ = [
@@ -268,6 +270,25 @@ def _rmat(scale, seeds):
 
 
 def config(name, side=None):
+    """Workload by name: returns (Matrix, ordering, factor seed, rhs); cached as
+    an .npz file in the directory named by PARAC_WORKLOAD_CACHE when that is set
+    (the generators are deterministic, so the cache only saves time)."""
+    cache = os.environ.get("PARAC_WORKLOAD_CACHE")
+    if cache:
+        path = os.path.join(cache, f"{name}.npz")
+        if os.path.exists(path):
+            z = np.load(path)
+            A = Matrix(int(z["n"]), z["colptr"], z["rowind"], z["val"])
+            return A, z["perm"], int(z["seed"]), z["b"]
+        out = _config(name)
+        os.makedirs(cache, exist_ok=True)
+        A, perm, seed, b = out
+        np.savez(path, n=A.n, colptr=A.colptr, rowind=A.rowind, val=A.val, perm=perm, seed=seed, b=b)
+        return out
+    return _config(name)
+
+
+def _config(name):
     """Workload by name: returns (Matrix, ordering, factor seed, rhs).
 
     grid2d-64     64x64 5-point grid, unit weights (n = 4096)
