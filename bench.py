@@ -56,13 +56,20 @@ def measured_peak_hbm():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def csrc_sha():
-    import glob
+# source files each timed kernel is built from: recorded DRAM traffic stays valid
+# while these are unchanged
+KERNEL_SOURCES = {
+    "k_trsv_fwd+k_trsv_bwd": ("solve.cu", "common.cuh", "kernels.h"),
+    "elim_kernel": ("elim.cu", "common.cuh", "kernels.h"),
+}
+
+
+def kernel_sha(kernel):
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2505_02977_gb300", "csrc", "*"))):
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for name in KERNEL_SOURCES[kernel]:
+        h.update(name.encode())
+        with open(os.path.join(ROOT, "paper_2505_02977_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -70,15 +77,16 @@ def csrc_sha():
 def recorded_traffic(kernel, alg_bytes):
     """DRAM bytes per launch from the last ncu capture of this kernel, scaled from the
     captured workload to this one by the ratio traffic / algorithmic bytes; None when
-    the kernel sources changed since the capture."""
+    the kernel's sources changed since the capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as f:
             rec = json.load(f)
     except Exception:
         return None
-    if rec.get("csrc_sha") != csrc_sha() or kernel not in rec.get("kernels", {}):
+    k = rec.get("kernels", {}).get(kernel)
+    if not k or k.get("src_sha") != kernel_sha(kernel):
         return None
-    return rec["kernels"][kernel]["ratio"] * alg_bytes
+    return k["ratio"] * alg_bytes
 
 
 def algorithmic_bytes_elim(st):
