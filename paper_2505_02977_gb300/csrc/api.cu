@@ -177,8 +177,10 @@ struct SolveCache {
 struct BlockCache {
     int32_t n = -1, nrhs = 0, prec = 0, pstride = 0;
     DBuf x, r, z, p, q, b, y, zl, partials, state;
-    DBuf gs_f, gs_b;                 // SpTRSM row groups (depend on the factor and the warps per block)
+    DBuf gt_f, gt_b;                 // SpTRSM group tables (depend on the factor and the warps per block)
     int32_t ng_f = 0, ng_b = 0, g_warps = 0;
+    DBuf part_f, part_b;             // partial sums of split rows, 32 columns per slot
+    int32_t nslot_f = 0, nslot_b = 0;
     BlockBuffers B{};
 };
 
@@ -237,8 +239,10 @@ struct parac_factor_s {
     std::string stats;
     SolveCache cache;
     int32_t max_row = 0;                               // longest row / column of F
-    DBuf sgs_f, sgs_b;                                 // row groups of the one-row-per-warp solves
+    DBuf sgt_f, sgt_b;                                 // group tables of the one-row-per-warp solves
     int32_t sng_f = 0, sng_b = 0;
+    DBuf spart_f, spart_b;                             // partial sums of their split rows
+    int32_t snslot_f = 0, snslot_b = 0;
     BlockCache bcache;
     DBuf status;
     SolveStream sstream;
@@ -674,15 +678,17 @@ void finish_handle(parac_factor_s *h, int64_t n, int64_t nnzF, const Opts &O)
         CK(cudaMemcpyAsync(rp.data(), h->Srp.p, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(cp.data(), h->Scp.p, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        const std::vector<int32_t> gf = row_groups(rp, false, SOLVE_WARPS, LONG_ROW_SINGLE),
-                                   gb = row_groups(cp, true, SOLVE_WARPS, LONG_ROW_SINGLE);
-        h->sgs_f = dalloc<int32_t>(gf.size(), st);
-        h->sgs_b = dalloc<int32_t>(gb.size(), st);
-        CK(cudaMemcpyAsync(h->sgs_f.p, gf.data(), 4 * gf.size(), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(h->sgs_b.p, gb.data(), 4 * gb.size(), cudaMemcpyHostToDevice, st));
+        const GroupTable gf = row_groups(rp, false, SOLVE_WARPS, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE),
+                         gb = row_groups(cp, true, SOLVE_WARPS, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
+        h->sgt_f = dalloc<int32_t>(gf.g.size(), st);
+        h->sgt_b = dalloc<int32_t>(gb.g.size(), st);
+        CK(cudaMemcpyAsync(h->sgt_f.p, gf.g.data(), 4 * gf.g.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(h->sgt_b.p, gb.g.data(), 4 * gb.g.size(), cudaMemcpyHostToDevice, st));
+        h->spart_f = dalloc<double>((size_t)std::max(gf.nslots, 1), st);
+        h->spart_b = dalloc<double>((size_t)std::max(gb.nslots, 1), st);
         CK(cudaStreamSynchronize(st));
-        h->sng_f = (int32_t)gf.size() - 1;
-        h->sng_b = (int32_t)gb.size() - 1;
+        h->sng_f = gf.ngroups; h->sng_b = gb.ngroups;
+        h->snslot_f = gf.nslots; h->snslot_b = gb.nslots;
     }
 }
 
@@ -1031,8 +1037,10 @@ SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, co
     A.spin_limit = G->spin_limit;
     A.status = G->status.as<int32_t>();
     if (G->sng_f > 0 && A.lanes_trsv == 32 && A.trsv_warps == SOLVE_WARPS) {
-        A.gs_f = G->sgs_f.as<int32_t>(); A.ng_f = G->sng_f;
-        A.gs_b = G->sgs_b.as<int32_t>(); A.ng_b = G->sng_b;
+        A.gt_f = (const int4 *)G->sgt_f.p; A.ng_f = G->sng_f;
+        A.gt_b = (const int4 *)G->sgt_b.p; A.ng_b = G->sng_b;
+        A.part_f = G->spart_f.p; A.nslot_f = G->snslot_f;
+        A.part_b = G->spart_b.p; A.nslot_b = G->snslot_b;
     }
     return A;
 }
@@ -1104,19 +1112,23 @@ void ensure_block_groups(parac_factor_s *G, int warps, cudaStream_t st)
         CK(cudaMemcpyAsync(rp.data(), G->Srp.p, 8 * (n + 1), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(cp.data(), G->Scp.p, 8 * (n + 1), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        const std::vector<int32_t> gf = row_groups(rp, false, warps, LONG_ROW_BLOCK),
-                                   gb = row_groups(cp, true, warps, LONG_ROW_BLOCK);
-        c.gs_f = dalloc<int32_t>(gf.size(), st);
-        c.gs_b = dalloc<int32_t>(gb.size(), st);
-        CK(cudaMemcpyAsync(c.gs_f.p, gf.data(), 4 * gf.size(), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(c.gs_b.p, gb.data(), 4 * gb.size(), cudaMemcpyHostToDevice, st));
+        const GroupTable gf = row_groups(rp, false, warps, LONG_ROW_BLOCK, SPLIT_ROW_BLOCK, CHUNK_BLOCK),
+                         gb = row_groups(cp, true, warps, LONG_ROW_BLOCK, SPLIT_ROW_BLOCK, CHUNK_BLOCK);
+        c.gt_f = dalloc<int32_t>(gf.g.size(), st);
+        c.gt_b = dalloc<int32_t>(gb.g.size(), st);
+        CK(cudaMemcpyAsync(c.gt_f.p, gf.g.data(), 4 * gf.g.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c.gt_b.p, gb.g.data(), 4 * gb.g.size(), cudaMemcpyHostToDevice, st));
+        c.part_f = dalloc<double>((size_t)std::max(gf.nslots, 1) * 32, st);
+        c.part_b = dalloc<double>((size_t)std::max(gb.nslots, 1) * 32, st);
         CK(cudaStreamSynchronize(st));       // the host vectors go out of scope
-        c.ng_f = (int32_t)gf.size() - 1;
-        c.ng_b = (int32_t)gb.size() - 1;
+        c.ng_f = gf.ngroups; c.ng_b = gb.ngroups;
+        c.nslot_f = gf.nslots; c.nslot_b = gb.nslots;
         c.g_warps = warps;
     }
-    c.B.gs_f = c.gs_f.as<int32_t>(); c.B.gs_b = c.gs_b.as<int32_t>();
+    c.B.gt_f = (const int4 *)c.gt_f.p; c.B.gt_b = (const int4 *)c.gt_b.p;
     c.B.ng_f = c.ng_f; c.B.ng_b = c.ng_b;
+    c.B.part_f = c.part_f.p; c.B.part_b = c.part_b.p;
+    c.B.nslot_f = c.nslot_f; c.B.nslot_b = c.nslot_b;
 }
 
 // The library's own solve stream for this handle, made to wait for the work

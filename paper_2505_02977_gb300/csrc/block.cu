@@ -316,26 +316,26 @@ __global__ void k_breopen(BlockState *st)
 constexpr int MAXW = 32;         // warps per block, at most
 constexpr int LONG_ROW = LONG_ROW_BLOCK;     // entries above which a row gets the whole block
 
-// Entries u = u0, u0+1, ..., in stages of 32 starting every `stride`, of the
+// Entries u in [u0, u_end), in stages of 32 starting every `stride`, of the
 // row [b, b+len): entry u is b+u, or b+len-1-u when REV (the backward solve
 // walks a column from its last entry, whose unknown was published first).
 template <bool REV, typename VT, typename XT>
-__device__ __forceinline__ bool brow_dot(int64_t b, int64_t len, int64_t u0, int64_t stride, int lane, int nrhs,
-                                         const int32_t *idx, const VT *v, const XT *x, XT &acc0, XT &acc1,
+__device__ __forceinline__ bool brow_dot(int64_t b, int64_t len, int64_t u0, int64_t u_end, int64_t stride, int lane,
+                                         int nrhs, const int32_t *idx, const VT *v, const XT *x, XT &acc0, XT &acc1,
                                          long long spin_limit, const int32_t *status, int32_t *s_c, VT *s_v)
 {
     constexpr int PF = 16;
     const bool col = lane < nrhs;
     bool ok = true;
     long long spins = 0;
-    for (int64_t base = u0; base < len && ok; base += stride) {
+    for (int64_t base = u0; base < u_end && ok; base += stride) {
         const int64_t u = base + lane;
         const int64_t t = REV ? b + len - 1 - u : b + u;
         __syncwarp();
-        s_c[lane] = u < len ? __ldg(idx + t) : -1;
-        s_v[lane] = u < len ? v[t] : (VT)0;
+        s_c[lane] = u < u_end ? __ldg(idx + t) : -1;
+        s_v[lane] = u < u_end ? v[t] : (VT)0;
         __syncwarp();
-        const int cnt = (int)(len - base < 32 ? len - base : 32);
+        const int cnt = (int)(u_end - base < 32 ? u_end - base : 32);
         for (int sub = 0; sub < cnt && ok; sub += PF) {
             const int m = cnt - sub < PF ? cnt - sub : PF;
             XT xx[PF];
@@ -371,12 +371,68 @@ __device__ __forceinline__ bool brow_dot(int64_t b, int64_t len, int64_t u0, int
     return ok;
 }
 
+// Block-wide part of a row of length len at b: the whole row (GK_SHARED) or
+// chunk `arg` (GK_CHUNK); every warp takes stages of 32 entries, the warps'
+// sums are added in warp order.  Valid for warp 0, lane = column.
+template <bool REV, typename VT, typename XT>
+__device__ __forceinline__ XT block_row_part(const int4 q, int64_t b, int64_t len, int lane, int my, int nw, int nrhs,
+                                             const int32_t *idx, const VT *v, const XT *x, long long spin_limit,
+                                             int32_t *status, int32_t *s_c, VT *s_v, XT (*red)[32])
+{
+    int64_t u0 = 0, u1 = len;
+    if (q.y == GK_CHUNK) {
+        u0 = (int64_t)q.z * CHUNK_BLOCK;
+        u1 = u0 + CHUNK_BLOCK < len ? u0 + CHUNK_BLOCK : len;
+    }
+    XT a0 = 0, a1 = 0;
+    if (!brow_dot<REV, VT, XT>(b, len, u0 + 32 * my, u1, 32 * nw, lane, nrhs, idx, v, x, a0, a1, spin_limit, status,
+                               s_c, s_v))
+        set_status(status, ST_TIMEOUT);
+    red[my][lane] = a0 + a1;
+    __syncthreads();
+    XT acc = 0;
+    if (my == 0)
+        for (int w = 0; w < nw; ++w) acc += red[w][lane];
+    return acc;
+}
+
+// GK_COMBINE, warp 0: the row's chunk partials (lane = column) summed in
+// chunk order, each awaited and then reset to the sentinel.
+template <typename XT>
+__device__ __forceinline__ XT block_combine(const int4 q, int lane, int nrhs, XT *part, long long spin_limit,
+                                            int32_t *status)
+{
+    XT acc = 0;
+    if (lane < nrhs) {
+        for (int c = 0; c < q.z; ++c) {
+            XT *p = part + (int64_t)(q.w + c) * 32 + lane;
+            XT x = ldp(p);
+            long long spins = 0;
+            unsigned ns = 16;
+            while (is_sent(x)) {
+                ++spins;
+                if ((spins & 127) == 0 && (spins > spin_limit || read_status(status) != ST_OK)) {
+                    set_status(status, ST_TIMEOUT);
+                    x = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+                x = ldp(p);
+            }
+            acc += x;
+            *p = sent<XT>();
+        }
+    }
+    return acc;
+}
+
 // Forward: y[j] = rhs[operm[j]] - sum_c F(j,c) y[c] over CSR row j (all
 // columns); also resets the backward unknowns z[j] to the sentinel.
 template <typename VT, typename XT>
 __global__ void k_btrsm_fwd(int32_t n, int nrhs, const int64_t *rp, const int32_t *ci, const VT *v,
-                            const int32_t *operm, const double *rhs, XT *y, XT *zreset, const int32_t *gs,
-                            int32_t ngroups, const BlockState *st, long long spin_limit, int32_t *status)
+                            const int32_t *operm, const double *rhs, XT *y, XT *zreset, const int4 *gt,
+                            int32_t ngroups, XT *part, const BlockState *st, long long spin_limit, int32_t *status)
 {
     __shared__ int32_t s_c[MAXW][32];
     __shared__ VT s_v[MAXW][32];
@@ -385,36 +441,38 @@ __global__ void k_btrsm_fwd(int32_t n, int nrhs, const int64_t *rp, const int32_
     const int lane = threadIdx.x & 31, my = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const bool col = lane < nrhs;
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-        const int32_t p0 = gs[g], p1 = gs[g + 1];
-        const int64_t b0 = rp[p0], e0 = rp[p0 + 1];
-        if (p1 - p0 == 1 && e0 - b0 > LONG_ROW) {          // shared row (block-uniform branch)
-            const double rj = col ? rhs[(int64_t)operm[p0] * nrhs + lane] : 0.0;
-            XT a0 = 0, a1 = 0;
-            if (!brow_dot<false, VT, XT>(b0, e0 - b0, 32 * my, 32 * nw, lane, nrhs, ci, v, y, a0, a1, spin_limit,
-                                         status, s_c[my], s_v[my]))
-                set_status(status, ST_TIMEOUT);
-            red[my][lane] = a0 + a1;
-            __syncthreads();
+        const int4 q = gt[g];
+        if (q.y != GK_ROWS) {                                   // block-wide group (block-uniform)
+            const int64_t j = q.x;
+            XT acc = 0;
+            if (q.y == GK_COMBINE) {
+                if (my == 0) acc = block_combine(q, lane, nrhs, part, spin_limit, status);
+            } else {
+                acc = block_row_part<false, VT, XT>(q, rp[j], rp[j + 1] - rp[j], lane, my, nw, nrhs, ci, v, y,
+                                                    spin_limit, status, s_c[my], s_v[my], red);
+            }
             if (my == 0 && col) {
-                XT acc = 0;
-                for (int w = 0; w < nw; ++w) acc += red[w][lane];
-                zreset[(int64_t)p0 * nrhs + lane] = sent<XT>();
-                stp(y + (int64_t)p0 * nrhs + lane, tox<XT>(rj) - acc);
+                if (q.y == GK_CHUNK) {
+                    stp(part + (int64_t)q.w * 32 + lane, acc);
+                } else {
+                    zreset[j * nrhs + lane] = sent<XT>();
+                    stp(y + j * nrhs + lane, tox<XT>(rhs[(int64_t)operm[j] * nrhs + lane]) - acc);
+                }
             }
             __syncthreads();
             continue;
         }
-        const int32_t j = p0 + my;
-        if (j >= p1) continue;
+        if (my >= q.z) continue;
+        const int64_t j = (int64_t)q.x + my;
         const int64_t b = rp[j], e = rp[j + 1];
         const double rj = col ? rhs[(int64_t)operm[j] * nrhs + lane] : 0.0;
         XT a0 = 0, a1 = 0;
-        if (!brow_dot<false, VT, XT>(b, e - b, 0, 32, lane, nrhs, ci, v, y, a0, a1, spin_limit, status, s_c[my],
-                                     s_v[my]))
+        if (!brow_dot<false, VT, XT>(b, e - b, 0, e - b, 32, lane, nrhs, ci, v, y, a0, a1, spin_limit, status,
+                                     s_c[my], s_v[my]))
             set_status(status, ST_TIMEOUT);
         if (col) {
-            zreset[(int64_t)j * nrhs + lane] = sent<XT>();
-            stp(y + (int64_t)j * nrhs + lane, tox<XT>(rj) - (a0 + a1));
+            zreset[j * nrhs + lane] = sent<XT>();
+            stp(y + j * nrhs + lane, tox<XT>(rj) - (a0 + a1));
         }
     }
 }
@@ -425,7 +483,7 @@ __global__ void k_btrsm_fwd(int32_t n, int nrhs, const int64_t *rp, const int32_
 template <typename VT, typename XT>
 __global__ void k_btrsm_bwd(int32_t n, int nrhs, const int64_t *cp, const int32_t *ri, const VT *v,
                             const double *Dinv, const int32_t *operm, XT *y, XT *z, double *zout,
-                            const double *r_orig, double *partial, const int32_t *gs, int32_t ngroups,
+                            const double *r_orig, double *partial, const int4 *gt, int32_t ngroups, XT *part,
                             const BlockState *st, long long spin_limit, int32_t *status)
 {
     __shared__ int32_t s_c[MAXW][32];
@@ -435,54 +493,41 @@ __global__ void k_btrsm_bwd(int32_t n, int nrhs, const int64_t *cp, const int32_
     const int lane = threadIdx.x & 31, my = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const bool col = lane < nrhs;
     double dot = 0.0;
+    auto publish = [&](int64_t j, XT acc) {
+        const int32_t o = operm[j];
+        const XT yj = y[j * nrhs + lane];
+        const XT zj = tox<XT>((double)yj * Dinv[j]) - acc;
+        y[j * nrhs + lane] = sent<XT>();
+        stp(z + j * nrhs + lane, zj);
+        zout[(int64_t)o * nrhs + lane] = (double)zj;
+        if (r_orig) dot += r_orig[(int64_t)o * nrhs + lane] * (double)zj;
+    };
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-        const int32_t k0 = gs[g], k1 = gs[g + 1];
-        const int64_t j0 = (int64_t)n - 1 - k0;
-        const int64_t b0 = cp[j0], e0 = cp[j0 + 1];
-        const bool shared_row = k1 - k0 == 1 && e0 - b0 > LONG_ROW;     // block-uniform
-        const int64_t j = shared_row ? j0 : (int64_t)n - 1 - (k0 + my);
-        const bool mine = shared_row || k0 + my < k1;
-        XT yj = 0;
-        double dj = 0.0, rj = 0.0;
-        int32_t o = 0;
-        if (mine) {
-            o = operm[j];
-            dj = Dinv[j];
-            if (col) {
-                yj = y[j * nrhs + lane];
-                rj = r_orig ? r_orig[(int64_t)o * nrhs + lane] : 0.0;
+        const int4 q = gt[g];
+        if (q.y != GK_ROWS) {                                   // block-wide group (block-uniform)
+            const int64_t j = (int64_t)n - 1 - q.x;
+            XT acc = 0;
+            if (q.y == GK_COMBINE) {
+                if (my == 0) acc = block_combine(q, lane, nrhs, part, spin_limit, status);
+            } else {
+                acc = block_row_part<true, VT, XT>(q, cp[j], cp[j + 1] - cp[j], lane, my, nw, nrhs, ri, v, z,
+                                                   spin_limit, status, s_c[my], s_v[my], red);
             }
-        }
-        XT a0 = 0, a1 = 0;
-        if (shared_row) {
-            if (!brow_dot<true, VT, XT>(b0, e0 - b0, 32 * my, 32 * nw, lane, nrhs, ri, v, z, a0, a1, spin_limit,
-                                        status, s_c[my], s_v[my]))
-                set_status(status, ST_TIMEOUT);
-            red[my][lane] = a0 + a1;
-            __syncthreads();
             if (my == 0 && col) {
-                XT acc = 0;
-                for (int w = 0; w < nw; ++w) acc += red[w][lane];
-                const XT zj = tox<XT>((double)yj * dj) - acc;
-                y[j * nrhs + lane] = sent<XT>();
-                stp(z + j * nrhs + lane, zj);
-                zout[(int64_t)o * nrhs + lane] = (double)zj;
-                dot += rj * (double)zj;
+                if (q.y == GK_CHUNK) stp(part + (int64_t)q.w * 32 + lane, acc);
+                else publish(j, acc);
             }
             __syncthreads();
             continue;
         }
-        if (!mine) continue;
-        if (!brow_dot<true, VT, XT>(cp[j], cp[j + 1] - cp[j], 0, 32, lane, nrhs, ri, v, z, a0, a1, spin_limit,
-                                    status, s_c[my], s_v[my]))
+        if (my >= q.z) continue;
+        const int64_t j = (int64_t)n - 1 - ((int64_t)q.x + my);
+        const int64_t b = cp[j], e = cp[j + 1];
+        XT a0 = 0, a1 = 0;
+        if (!brow_dot<true, VT, XT>(b, e - b, 0, e - b, 32, lane, nrhs, ri, v, z, a0, a1, spin_limit, status,
+                                    s_c[my], s_v[my]))
             set_status(status, ST_TIMEOUT);
-        if (col) {
-            const XT zj = tox<XT>((double)yj * dj) - (a0 + a1);
-            y[j * nrhs + lane] = sent<XT>();
-            stp(z + j * nrhs + lane, zj);
-            zout[(int64_t)o * nrhs + lane] = (double)zj;
-            dot += rj * (double)zj;
-        }
+        if (col) publish(j, a0 + a1);
     }
     if (partial) block_colsum(dot, partial);
 }
@@ -498,26 +543,40 @@ inline int grid_for(int64_t m, int maxb)
 
 size_t block_state_bytes() { return sizeof(BlockState); }
 
-std::vector<int32_t> row_groups(const std::vector<int64_t> &ptr, bool descending, int warps, int long_row)
+// Group table over positions in ascending (forward) or descending (backward)
+// order; ptr = row pointers [n+1] of the rows in that order's numbering.
+GroupTable row_groups(const std::vector<int64_t> &ptr, bool descending, int warps, int long_row, int split_row,
+                      int chunk)
 {
     const int64_t n = (int64_t)ptr.size() - 1;
-    std::vector<int32_t> gs;
-    gs.reserve((size_t)(n / (warps > 0 ? warps : 1) + 2));
-    gs.push_back(0);
+    GroupTable t;
+    t.g.reserve((size_t)(4 * (n / (warps > 0 ? warps : 1) + 2)));
+    auto push = [&](int64_t start, int32_t kind, int32_t arg, int32_t slot) {
+        t.g.push_back((int32_t)start); t.g.push_back(kind); t.g.push_back(arg); t.g.push_back(slot);
+        ++t.ngroups;
+    };
     int cur = 0;
+    int64_t start = 0;
     for (int64_t kk = 0; kk < n; ++kk) {
         const int64_t j = descending ? n - 1 - kk : kk;
-        if (ptr[j + 1] - ptr[j] > long_row) {
-            if (cur > 0) gs.push_back((int32_t)kk);
-            gs.push_back((int32_t)(kk + 1));
-            cur = 0;
-        } else if (++cur == warps) {
-            gs.push_back((int32_t)(kk + 1));
-            cur = 0;
+        const int64_t len = ptr[j + 1] - ptr[j];
+        if (len > long_row) {
+            if (cur > 0) { push(start, GK_ROWS, cur, 0); cur = 0; }
+            if (len > split_row) {
+                const int32_t nch = (int32_t)((len + chunk - 1) / chunk);
+                for (int32_t c = 0; c < nch; ++c) push(kk, GK_CHUNK, c, t.nslots + c);
+                push(kk, GK_COMBINE, nch, t.nslots);
+                t.nslots += nch;
+            } else {
+                push(kk, GK_SHARED, 0, 0);
+            }
+        } else {
+            if (cur == 0) start = kk;
+            if (++cur == warps) { push(start, GK_ROWS, cur, 0); cur = 0; }
         }
     }
-    if (cur > 0) gs.push_back((int32_t)n);
-    return gs;
+    if (cur > 0) push(start, GK_ROWS, cur, 0);
+    return t;
 }
 
 // resident blocks per SM of the two SpTRSM kernels at `warps` warps per block
@@ -559,11 +618,11 @@ cudaError_t bapply_t(const SolveArgs &A, const BlockBuffers &B, const VT *vr, co
     const int threads = A.trsv_warps * 32;
     const int gf = B.ng_f < A.trsv_blocks ? B.ng_f : A.trsv_blocks;
     const int gb = B.ng_b < A.trsv_blocks ? B.ng_b : A.trsv_blocks;
-    k_btrsm_fwd<VT, XT><<<gf, threads, 0, s>>>(A.n, B.nrhs, A.Frp, A.Fcol, vr, A.operm, r, y, z, B.gs_f, B.ng_f, st,
-                                               A.spin_limit, A.status);
+    k_btrsm_fwd<VT, XT><<<gf, threads, 0, s>>>(A.n, B.nrhs, A.Frp, A.Fcol, vr, A.operm, r, y, z, B.gt_f, B.ng_f,
+                                               (XT *)B.part_f, st, A.spin_limit, A.status);
     count_launches(1);
     k_btrsm_bwd<VT, XT><<<gb, threads, 0, s>>>(A.n, B.nrhs, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z, zout, r,
-                                               partial, B.gs_b, B.ng_b, st, A.spin_limit, A.status);
+                                               partial, B.gt_b, B.ng_b, (XT *)B.part_b, st, A.spin_limit, A.status);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -582,6 +641,17 @@ cudaError_t bfill(const SolveArgs &A, const BlockBuffers &B, cudaStream_t s)
     if (A.prec == 32) k_bfill_sentinel<float><<<grid_for(m, 4096), BT, 0, s>>>(m, B.yl32, B.zl32);
     else k_bfill_sentinel<double><<<grid_for(m, 4096), BT, 0, s>>>(m, B.yl64, B.zl64);
     count_launches(1);
+    const int64_t mf = (int64_t)B.nslot_f * 32, mb = (int64_t)B.nslot_b * 32;
+    if (mf > 0 || mb > 0) {          // split-row partials start unpublished
+        if (A.prec == 32) {
+            k_bfill_sentinel<float><<<grid_for(mf, 4096), BT, 0, s>>>(mf, (float *)B.part_f, (float *)B.part_f);
+            k_bfill_sentinel<float><<<grid_for(mb, 4096), BT, 0, s>>>(mb, (float *)B.part_b, (float *)B.part_b);
+        } else {
+            k_bfill_sentinel<double><<<grid_for(mf, 4096), BT, 0, s>>>(mf, (double *)B.part_f, (double *)B.part_f);
+            k_bfill_sentinel<double><<<grid_for(mb, 4096), BT, 0, s>>>(mb, (double *)B.part_b, (double *)B.part_b);
+        }
+        count_launches(2);
+    }
     return cudaGetLastError();
 }
 

@@ -690,8 +690,6 @@ __device__ int32_t eliminate_big(const ElimArgs &a, int32_t k, int64_t o0, int32
 // every other warp of the CTA joins at its next poll point, and the block runs
 // the same steps with block-wide networks.  One request at a time per CTA;
 // all barriers are bounded software barriers over the CTA's warps.
-constexpr int MAX_BIG_BUCKETS = 64;    // buckets above a warp's slice, sorted by the whole CTA
-
 struct CoopShared {
     int k;                       // vertex being eliminated cooperatively (-1: none)
     int gen;                     // bumped for every request
@@ -699,8 +697,7 @@ struct CoopShared {
     int arrive;                  // barrier arrivals (monotonic)
     int d, ntile, abort;
     int hcount[32];              // per-warp head counts of the merge
-    int nbig, maxcnt;            // sample sort: oversized buckets, largest bucket
-    int big[MAX_BIG_BUCKETS];
+    int nbig;                    // sample sort: buckets above a warp's slice
     unsigned long long fpos;
     unsigned long long sbase, scap;   // CTA scratch (global), reused across requests
     long long spin_limit;
@@ -869,11 +866,11 @@ __device__ __forceinline__ int bucket_of(const View &smp, int stride, int B, int
 }
 
 // Shared part of both sorts: sample, count, bucket offsets, scatter.  n >
-// cap entries (row, w, mult) of v; returns B, or 0 when a bucket exceeds the
-// CTA's buffer or more than MAX_BIG_BUCKETS exceed a warp's slice (nothing
-// has been moved then).
+// cap entries (row, w, mult) of v are moved to the temporaries in bucket
+// order; gbo[0..B] receives the bucket offsets and gbig[0..cs.nbig) the
+// buckets larger than a warp's slice.  Returns B.
 template <int KEY>
-__device__ int sample_partition(View v, int n, View tile, int cap, int wcap, CoopShared &cs, int *gbo)
+__device__ int sample_partition(View v, int n, View tile, int cap, int wcap, CoopShared &cs, int *gbo, int *gbig)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int SS = cap, lg = __ffs(SS) - 1;              // cap: a power of two
@@ -892,7 +889,7 @@ __device__ int sample_partition(View v, int n, View tile, int cap, int wcap, Coo
     const int stride = SS / B;
     int *cnt = (int *)tile.S, *cur = (int *)tile.S + cap, *off = (int *)tile.M;
     for (int b = tid; b < B; b += nt) { cnt[b] = 0; cur[b] = 0; }
-    if (tid == 0) { cs.nbig = 0; cs.maxcnt = 0; }
+    if (tid == 0) cs.nbig = 0;
     __syncthreads();
     for (int i = tid; i < n; i += nt) {
         const int32_t r = v.row[i];
@@ -900,16 +897,10 @@ __device__ int sample_partition(View v, int n, View tile, int cap, int wcap, Coo
         atomicAdd(cnt + bucket_of<KEY>(tile, stride, B, r, wb), 1);
     }
     __syncthreads();
-    for (int b = tid; b < B; b += nt) {
-        const int c = cnt[b];
-        atomicMax(&cs.maxcnt, c);
-        if (c > wcap) atomicAdd(&cs.nbig, 1);
-    }
+    for (int b = tid; b < B; b += nt)
+        if (cnt[b] > wcap) gbig[atomicAdd(&cs.nbig, 1)] = b;
     block_excl_scan(cnt, B, off, cs);
-    const bool fits = cs.maxcnt <= cap && cs.nbig <= MAX_BIG_BUCKETS;
-    __syncthreads();
-    if (!fits) return 0;
-    if (tid == 0) { off[B] = n; cs.nbig = 0; }
+    if (tid == 0) off[B] = n;
     __syncthreads();
     unsigned long long *tM = (unsigned long long *)v.M;
     for (int i = tid; i < n; i += nt) {
@@ -924,6 +915,35 @@ __device__ int sample_partition(View v, int n, View tile, int cap, int wcap, Coo
     for (int b = tid; b <= B; b += nt) gbo[b] = off[b];
     __syncthreads();
     return B;
+}
+
+// Sort one oversized bucket (temporaries [o, o + cb)) with the whole CTA: in
+// the shared buffer when it fits, else in v[0, P) (free once the entries are
+// scattered) with the tiled network.  Returns the view holding the sorted
+// bucket at [0, cb).
+template <int KEY>
+__device__ View sort_big_bucket(View v, View tile, int cap, int o, int cb)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const double *tS = v.S;
+    const unsigned long long *tM = (const unsigned long long *)v.M;
+    const int Pb = next_pow2(cb);
+    const View w = Pb <= cap ? tile : v;
+    const double wpad = KEY == 0 ? 0.0 : __longlong_as_double((long long)WBITS_SENTINEL);
+    for (int i = tid; i < Pb; i += nt) {
+        if (i < cb) {
+            const unsigned long long rm = tM[o + i];
+            const double x = tS[o + i];
+            w.row[i] = (int32_t)(uint32_t)rm; w.w[i] = x;
+            if (KEY == 1) w.mult[i] = (int32_t)(rm >> 32);
+        } else {
+            w.row[i] = ROW_SENTINEL; w.w[i] = wpad;
+            if (KEY == 1) w.mult[i] = 0;
+        }
+    }
+    __syncthreads();
+    coop_sort<KEY>(w, Pb, tile, Pb <= cap ? 0 : cap);
+    return w;
 }
 
 // Merge the sorted runs of a bucket held in a shared view (rows, weights in
@@ -960,26 +980,33 @@ __device__ __forceinline__ int warp_merge_bucket(View sv, int cb, double *tS, un
 
 // Row phase on a global working set: sort (row, weight bits), merge runs,
 // compact in bucket order into v[0, d) (row, w, mult) and store the F column
-// rows / merged weights.  Returns d, or -1 when the sample sort does not
-// apply (the caller takes the bitonic path; v is untouched).
+// rows / merged weights.  Returns d, or -2 on abort.
 __device__ int coop_row_phase(const ElimArgs &a, CoopShared &cs, View v, int g, unsigned char *bbuf, int cap,
-                              int *gbo, int *gbd, int32_t k)
+                              int *gbo, int *gbd, int *gbig, int32_t k)
 {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int wcap = cap / nw;
     const View tile = make_view(bbuf, cap);
-    const int B = sample_partition<0>(v, g, tile, cap, wcap, cs, gbo);
-    if (B == 0) return -1;
+    const int B = sample_partition<0>(v, g, tile, cap, wcap, cs, gbo, gbig);
     double *tS = v.S;
     unsigned long long *tM = (unsigned long long *)v.M;
-    // buckets that fit a warp's slice: one warp each
+    // oversized buckets first, by the whole CTA (their work space may be v itself)
+    const int nbig = cs.nbig;
+    for (int q = 0; q < nbig; ++q) {
+        const int b = gbig[q];
+        const int o = gbo[b], cb = gbo[b + 1] - o;
+        const View w = sort_big_bucket<0>(v, tile, cap, o, cb);
+        if (warp == 0) {
+            const int db = warp_merge_bucket(w, cb, tS, tM, o);
+            if (lane == 0) gbd[b] = db;
+        }
+        __syncthreads();
+    }
+    // the others: one warp each, in the warp's slice of the shared buffer
     const View sv = make_view(bbuf + (size_t)warp * wcap * ENTRY_BYTES, wcap);
     for (int b = warp; b < B; b += nw) {
         const int o = gbo[b], cb = gbo[b + 1] - o;
-        if (cb > wcap) {
-            if (lane == 0) cs.big[atomicAdd(&cs.nbig, 1)] = b;
-            continue;
-        }
+        if (cb > wcap) continue;
         int db = 0;
         if (cb > 0) {
             const int Pb = next_pow2(cb);
@@ -995,24 +1022,6 @@ __device__ int coop_row_phase(const ElimArgs &a, CoopShared &cs, View v, int g, 
         if (lane == 0) gbd[b] = db;
     }
     __syncthreads();
-    // oversized buckets: the whole CTA, one after another
-    const int nbig = cs.nbig;
-    for (int q = 0; q < nbig; ++q) {
-        const int b = cs.big[q];
-        const int o = gbo[b], cb = gbo[b + 1] - o;
-        const int Pb = next_pow2(cb);
-        for (int i = tid; i < Pb; i += nt) {
-            if (i < cb) { tile.row[i] = (int32_t)(uint32_t)tM[o + i]; tile.w[i] = tS[o + i]; }
-            else { tile.row[i] = ROW_SENTINEL; tile.w[i] = 0.0; }
-        }
-        __syncthreads();
-        coop_sort<0>(tile, Pb, tile, 0);
-        if (warp == 0) {
-            const int db = warp_merge_bucket(tile, cb, tS, tM, o);
-            if (lane == 0) gbd[b] = db;
-        }
-        __syncthreads();
-    }
     // compaction in bucket order, with the F column store
     int *pd = (int *)bbuf;
     for (int b = tid; b < B; b += nt) pd[b] = gbd[b];
@@ -1041,9 +1050,8 @@ __device__ int coop_row_phase(const ElimArgs &a, CoopShared &cs, View v, int g, 
 }
 
 // Weight phase on a global working set: sort v[0, d) by (weight bits, row)
-// carrying the multiplicity.  Returns false when the sample sort does not
-// apply (v untouched).
-__device__ bool coop_weight_phase(View v, int d, unsigned char *bbuf, int cap, CoopShared &cs, int *gbo)
+// carrying the multiplicity.
+__device__ void coop_weight_phase(View v, int d, unsigned char *bbuf, int cap, CoopShared &cs, int *gbo, int *gbig)
 {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int wcap = cap / nw;
@@ -1058,20 +1066,35 @@ __device__ bool coop_weight_phase(View v, int d, unsigned char *bbuf, int cap, C
         coop_sort<1>(tile, Pd, tile, 0);
         for (int i = tid; i < d; i += nt) { v.row[i] = tile.row[i]; v.w[i] = tile.w[i]; v.mult[i] = tile.mult[i]; }
         __syncthreads();
-        return true;
+        return;
     }
-    const int B = sample_partition<1>(v, d, tile, cap, wcap, cs, gbo);
-    if (B == 0) return false;
-    const double *tS = v.S;
-    const unsigned long long *tM = (const unsigned long long *)v.M;
+    const int B = sample_partition<1>(v, d, tile, cap, wcap, cs, gbo, gbig);
+    double *tS = v.S;
+    unsigned long long *tM = (unsigned long long *)v.M;
+    // oversized buckets first, sorted back into the temporaries (v may be their work space)
+    const int nbig = cs.nbig;
+    for (int q = 0; q < nbig; ++q) {
+        const int b = gbig[q];
+        const int o = gbo[b], cb = gbo[b + 1] - o;
+        const View w = sort_big_bucket<1>(v, tile, cap, o, cb);
+        for (int i = tid; i < cb; i += nt) {
+            tS[o + i] = w.w[i];
+            tM[o + i] = (unsigned long long)(uint32_t)w.row[i] | ((unsigned long long)(uint32_t)w.mult[i] << 32);
+        }
+        __syncthreads();
+    }
+    // every bucket to its final place: small ones sorted by one warp each, big ones copied
     const View sv = make_view(bbuf + (size_t)warp * wcap * ENTRY_BYTES, wcap);
     for (int b = warp; b < B; b += nw) {
         const int o = gbo[b], cb = gbo[b + 1] - o;
+        if (cb == 0) continue;
         if (cb > wcap) {
-            if (lane == 0) cs.big[atomicAdd(&cs.nbig, 1)] = b;
+            for (int i = lane; i < cb; i += 32) {
+                const unsigned long long rm = tM[o + i];
+                v.row[o + i] = (int32_t)(uint32_t)rm; v.mult[o + i] = (int32_t)(rm >> 32); v.w[o + i] = tS[o + i];
+            }
             continue;
         }
-        if (cb == 0) continue;
         const int Pb = next_pow2(cb);
         for (int i = lane; i < Pb; i += 32) {
             if (i < cb) {
@@ -1087,25 +1110,6 @@ __device__ bool coop_weight_phase(View v, int d, unsigned char *bbuf, int cap, C
         __syncwarp();
     }
     __syncthreads();
-    const int nbig = cs.nbig;
-    for (int q = 0; q < nbig; ++q) {
-        const int b = cs.big[q];
-        const int o = gbo[b], cb = gbo[b + 1] - o;
-        const int Pb = next_pow2(cb);
-        for (int i = tid; i < Pb; i += nt) {
-            if (i < cb) {
-                const unsigned long long rm = tM[o + i];
-                tile.row[i] = (int32_t)(uint32_t)rm; tile.mult[i] = (int32_t)(rm >> 32); tile.w[i] = tS[o + i];
-            } else {
-                tile.row[i] = ROW_SENTINEL; tile.mult[i] = 0; tile.w[i] = __longlong_as_double((long long)WBITS_SENTINEL);
-            }
-        }
-        __syncthreads();
-        coop_sort<1>(tile, Pb, tile, 0);
-        for (int i = tid; i < cb; i += nt) { v.row[o + i] = tile.row[i]; v.w[o + i] = tile.w[i]; v.mult[o + i] = tile.mult[i]; }
-        __syncthreads();
-    }
-    return true;
 }
 
 // Cooperative elimination of cs.k by every warp of the CTA (the callers have
@@ -1147,7 +1151,7 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
         tiles = (double *)(bbuf + (size_t)a.block_cap * ENTRY_BYTES);
     } else {
         const unsigned long long need = (unsigned long long)P * ENTRY_BYTES + ((unsigned long long)P / 32 + 1) * 8 +
-                                        16ull + 4ull * (2ull * (unsigned long long)a.block_cap + 2ull);
+                                        16ull + 4ull * (3ull * (unsigned long long)a.block_cap + 3ull);
         if (tid == 0 && cs.scap < need) {
             const unsigned long long base = atomicAdd(a.scratch_top, (need + 255ull) & ~255ull);
             if (base + need > a.scratch_cap) set_status(a.status, ST_POOL);
@@ -1160,6 +1164,7 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     // bucket offsets and merged counts of the sample sort (global working sets)
     int *gbo = (int *)(((uintptr_t)(tiles + (P / 32 + 1)) + 15) & ~(uintptr_t)15);
     int *gbd = gbo + a.block_cap + 1;
+    int *gbig = gbd + a.block_cap + 1;
 
     // ---------------------------------------------------------------- gather
     for (int i = tid; i < norig; i += nt) { v.row[i] = __ldg(a.lrow + o0 + i); v.w[i] = __ldg(a.lw + o0 + i); }
@@ -1196,9 +1201,9 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     int d = -1;
     const bool sample = global_ws && a.sample_sort && a.block_cap >= 256;
     if (sample) {
-        d = coop_row_phase(a, cs, v, g, bbuf, a.block_cap, gbo, gbd, k);
+        d = coop_row_phase(a, cs, v, g, bbuf, a.block_cap, gbo, gbd, gbig, k);
         if (d == -2) { __syncthreads(); if (tid == 0) cs.k = -1; return -2; }
-        if (d >= 0) { mark(10); mark(11); }
+        mark(10); mark(11);
     }
     if (d < 0) {                                   // bitonic network, merge in place, store
         coop_sort<0>(v, P, tile, global_ws ? a.block_cap : 0);
@@ -1249,7 +1254,9 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
 
     // ---------------------------------------------------------------- weight sort
     __syncthreads();
-    if (!sample || !coop_weight_phase(v, d, bbuf, a.block_cap, cs, gbo)) {
+    if (sample) {
+        coop_weight_phase(v, d, bbuf, a.block_cap, cs, gbo, gbig);
+    } else {
         const int P2 = next_pow2(d);
         for (int i = d + tid; i < P2; i += nt) {
             v.row[i] = ROW_SENTINEL; v.w[i] = __longlong_as_double((long long)WBITS_SENTINEL); v.mult[i] = 0;

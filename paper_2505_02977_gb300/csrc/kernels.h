@@ -117,16 +117,33 @@ struct SolveArgs {
     int32_t trsv_warps;           // warps per block of the triangular solves
     long long spin_limit;
     int32_t *status;
-    // optional row groups of the one-row-per-warp solves (row_groups with
-    // LONG_ROW_SINGLE and trsv_warps warps); nullptr: fixed groups
-    const int32_t *gs_f, *gs_b;
+    // optional group tables of the one-row-per-warp solves (row_groups with the
+    // _SINGLE sizes and trsv_warps warps); nullptr: fixed groups of rows
+    const int4 *gt_f, *gt_b;
     int32_t ng_f, ng_b;
+    void *part_f, *part_b;        // partial sums of split rows (XT), nslot_f / nslot_b
+    int32_t nslot_f, nslot_b;
 };
-// rows above this many entries are shared by a whole block in the
-// one-right-hand-side solves (LONG_ROW in the block solves)
-constexpr int LONG_ROW_SINGLE = 512;
+
+// Schedule of the solves: groups in position order, 4 ints each (first
+// position in walk order, kind, arg, slot).  GK_ROWS: arg rows, one per warp;
+// GK_SHARED: one row for the whole block; GK_CHUNK: entries [arg*chunk,
+// (arg+1)*chunk) of one row (in walk order) summed by the block into partial
+// slot `slot`; GK_COMBINE: the row's arg partials from `slot` on, summed in
+// order, finish the row.  Chunks come before their combine.
+enum : int32_t { GK_ROWS = 0, GK_SHARED = 1, GK_CHUNK = 2, GK_COMBINE = 3 };
+struct GroupTable {
+    std::vector<int32_t> g;       // 4 * ngroups
+    int32_t ngroups = 0, nslots = 0;
+};
+GroupTable row_groups(const std::vector<int64_t> &ptr, bool descending, int warps, int long_row, int split_row,
+                      int chunk);
+// one right-hand side: rows above LONG_ROW_SINGLE entries get a block, above
+// SPLIT_ROW_SINGLE they are split into chunks of CHUNK_SINGLE; block solves
+// (nrhs columns, 32 x the bytes per entry) use the _BLOCK sizes
+constexpr int LONG_ROW_SINGLE = 512, SPLIT_ROW_SINGLE = 32768, CHUNK_SINGLE = 8192;
+constexpr int LONG_ROW_BLOCK = 64, SPLIT_ROW_BLOCK = 1024, CHUNK_BLOCK = 512;
 constexpr int SOLVE_WARPS = 8;        // warps per block of the solves (default)
-constexpr int LONG_ROW_BLOCK = 64;
 
 struct PcgBuffers {
     double *x, *r, *z, *p, *q, *b;  // [n]
@@ -159,8 +176,10 @@ struct BlockBuffers {
     float *yl32, *zl32;             // [n * nrhs] (FP32 apply)
     double *partials;               // [3 * 32 * pstride]
     BlockState *state;
-    const int32_t *gs_f, *gs_b;     // row groups of the forward / backward SpTRSM
+    const int4 *gt_f, *gt_b;        // group tables of the forward / backward SpTRSM
     int32_t ng_f, ng_b;
+    void *part_f, *part_b;          // partial sums of split rows: nslot_* x 32 values (XT)
+    int32_t nslot_f, nslot_b;
     int32_t nrhs;
     int32_t vec_blocks;             // grid of the vector kernels
     int32_t pstride;                // >= max(vec_blocks, trsv grid)
@@ -171,10 +190,7 @@ struct BlockHostState {
     double bb[32], true_rr[32];
 };
 size_t block_state_bytes();
-// Row groups of the SpTRSM schedule over positions in ascending (forward) or
-// descending (backward) order: gs[g]..gs[g+1] is either up to `warps` rows of
-// at most long_row entries or a single longer row.  ptr = row pointers [n+1].
-std::vector<int32_t> row_groups(const std::vector<int64_t> &ptr, bool descending, int warps, int long_row);
+
 int btrsm_blocks_per_sm(int warps, int prec);
 cudaError_t bpack(int32_t n, int nrhs, const double *B, int64_t ldb, double *Bt, cudaStream_t st);
 cudaError_t bunpack(int32_t n, int nrhs, const double *Xt, double *X, int64_t ldx, cudaStream_t st);

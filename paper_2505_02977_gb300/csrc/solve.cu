@@ -193,6 +193,15 @@ __global__ void k_copy(int32_t n, const double *a, double *b)
 }
 
 template <typename T>
+__global__ void k_fill_part(T *a, int32_t na, T *b, int32_t nb)
+{
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (na > nb ? na : nb); i += gridDim.x * blockDim.x) {
+        if (i < na) a[i] = sentinel<T>();
+        if (i < nb) b[i] = sentinel<T>();
+    }
+}
+
+template <typename T>
 __global__ void k_fill_sentinel(int32_t n, T *a, T *b)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -379,32 +388,72 @@ __device__ __forceinline__ bool finish_chunk(const XT *x, const int32_t (&cc)[RP
     return true;
 }
 
-// Row (position) of this lane group in group g, or -1; `shared` when the
-// group is one long row for the whole block (block-uniform).
-template <int S>
-__device__ __forceinline__ int64_t row_of(int64_t g, int64_t ngroups, const int32_t *gs, const int64_t *ptr,
-                                          int32_t n, int rows_per_group, int my, bool rev, bool &shared)
+// Group g of the schedule as seen by one lane group: its row (position) for
+// GK_ROWS (-1: none), the group's row for the block-wide kinds.
+struct Grp {
+    int64_t j;
+    int32_t kind, arg, slot;
+};
+
+__device__ __forceinline__ Grp group_of(int64_t g, int64_t ngroups, const int4 *gt, int32_t n, int rows_per_group,
+                                        int my, bool rev)
 {
-    shared = false;
-    if (g >= ngroups) return -1;
-    if (gs) {
-        const int32_t k0 = gs[g], k1 = gs[g + 1];
-        if (k1 - k0 == 1) {
-            const int64_t j0 = rev ? (int64_t)n - 1 - k0 : k0;
-            if (ptr[j0 + 1] - ptr[j0] > LONG_ROW_SINGLE) { shared = true; return j0; }
+    Grp r{-1, GK_ROWS, 0, 0};
+    if (g >= ngroups) return r;
+    if (gt) {
+        const int4 q = gt[g];
+        r.kind = q.y; r.arg = q.z; r.slot = q.w;
+        if (q.y == GK_ROWS) {
+            const int64_t kk = (int64_t)q.x + my;
+            r.j = my < q.z ? (rev ? (int64_t)n - 1 - kk : kk) : -1;
+        } else {
+            r.j = rev ? (int64_t)n - 1 - q.x : (int64_t)q.x;
         }
-        const int64_t kk = (int64_t)k0 + my;
-        return kk < k1 ? (rev ? (int64_t)n - 1 - kk : kk) : -1;
+        return r;
     }
     const int64_t kk = g * rows_per_group + my;
-    return kk < n ? (rev ? (int64_t)n - 1 - kk : kk) : -1;
+    r.j = kk < n ? (rev ? (int64_t)n - 1 - kk : kk) : -1;
+    return r;
+}
+
+// A block-wide group of a row of [b, e): the whole row (GK_SHARED) or chunk
+// `arg` of it (GK_CHUNK, entries arg*CHUNK_SINGLE .. in walk order), summed by
+// every thread of the block in a fixed order; valid in thread 0.
+template <bool REV, typename VT, typename XT>
+__device__ __forceinline__ XT block_part(const Grp &q, int64_t b, int64_t e, const int32_t *idx, const VT *v,
+                                         const XT *x, XT *red, long long spin_limit, int32_t *status)
+{
+    int64_t lo = b, hi = e;
+    if (q.kind == GK_CHUNK) {
+        const int64_t c0 = (int64_t)q.arg * CHUNK_SINGLE, c1 = c0 + CHUNK_SINGLE < e - b ? c0 + CHUNK_SINGLE : e - b;
+        if (REV) { lo = e - c1; hi = e - c0; } else { lo = b + c0; hi = b + c1; }
+    }
+    XT acc = 0;
+    if (!dot_ready<REV, VT, XT>(lo, hi, threadIdx.x, blockDim.x, idx, v, x, acc, spin_limit, status))
+        set_status(status, ST_TIMEOUT);
+    return block_row_sum(acc, red);
+}
+
+// GK_COMBINE, thread 0: the row's chunk partials summed in chunk order (each
+// awaited, then reset to the sentinel for the next solve).
+template <typename XT>
+__device__ __forceinline__ XT combine_parts(const Grp &q, XT *part, long long spin_limit, int32_t *status)
+{
+    XT acc = 0;
+    for (int c = 0; c < q.arg; ++c) {
+        XT v;
+        if (!poll_ready(part + q.slot + c, v, spin_limit, status)) { set_status(status, ST_TIMEOUT); v = 0; }
+        acc += v;
+        part[q.slot + c] = sentinel<XT>();
+    }
+    return acc;
 }
 
 // Forward: y[j] = rhs[operm[j]] - sum_{c<j} F(j,c) y[c] over CSR row j; also
 // resets the backward unknown z[j] to the sentinel.
 template <int S, typename VT, typename XT>
 __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, const VT *v, const int32_t *operm,
-                           const double *rhs, XT *y, XT *zreset, const int32_t *gs, int32_t ngs,
+                           const double *rhs, XT *y, XT *zreset, const int4 *gt, int32_t ngs, XT *part,
                            const PcgState *st, long long spin_limit, int32_t *status)
 {
     __shared__ XT red[32];
@@ -414,55 +463,57 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
     const unsigned smask = (S == 32) ? FULL : (((1u << S) - 1u) << (sub * S));
     const int rows_per_group = (blockDim.x / 32) * (32 / S);
     const int my = (threadIdx.x >> 5) * (32 / S) + sub;
-    const int64_t ngroups = gs ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
+    const int64_t ngroups = gt ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
     int64_t g = blockIdx.x;
-    bool sh;
-    int64_t j = row_of<S>(g, ngroups, gs, rp, n, rows_per_group, my, false, sh);
+    Grp q = group_of(g, ngroups, gt, n, rows_per_group, my, false);
     int64_t b = 0, e = 0;
     double rj = 0.0;
     int32_t cc[RPF];
     VT vv[RPF];
     XT xx[RPF];
-    if (!sh && j >= 0) {
-        b = rp[j]; e = rp[j + 1];
-        if (sl == 0) rj = rhs[operm[j]];
-        fetch_chunk<S, false, VT>(b, e, sl, ci, v, cc, vv);
-    }
+    auto fetch = [&](const Grp &r, int64_t &bb, int64_t &ee, double &rr, int32_t (&c)[RPF], VT (&w)[RPF]) {
+        if (r.kind == GK_ROWS && r.j >= 0) {
+            bb = rp[r.j]; ee = rp[r.j + 1];
+            if (sl == 0) rr = rhs[operm[r.j]];
+            fetch_chunk<S, false, VT>(bb, ee, sl, ci, v, c, w);
+        }
+    };
+    fetch(q, b, e, rj, cc, vv);
     while (g < ngroups) {
         const int64_t gn = g + gridDim.x;
-        if (sh) {                                      // one long row for the whole block
-            const int64_t bs = rp[j], es = rp[j + 1];
-            const double rs = threadIdx.x == 0 ? rhs[operm[j]] : 0.0;
-            XT acc = 0;
-            if (!dot_ready<false, VT, XT>(bs, es, threadIdx.x, blockDim.x, ci, v, y, acc, spin_limit, status))
-                set_status(status, ST_TIMEOUT);
-            const XT sum = block_row_sum(acc, red);
-            if (threadIdx.x == 0) {
-                zreset[j] = sentinel<XT>();
-                st_pub(y + j, to_x<XT>(rs) - sum);
+        if (q.kind != GK_ROWS) {                      // block-wide group (block-uniform branch)
+            const int64_t j = q.j;
+            if (q.kind == GK_COMBINE) {
+                if (threadIdx.x == 0) {
+                    const XT sum = combine_parts(q, part, spin_limit, status);
+                    zreset[j] = sentinel<XT>();
+                    st_pub(y + j, to_x<XT>(rhs[operm[j]]) - sum);
+                }
+            } else {
+                const XT sum = block_part<false, VT, XT>(q, rp[j], rp[j + 1], ci, v, y, red, spin_limit, status);
+                if (threadIdx.x == 0) {
+                    if (q.kind == GK_CHUNK) {
+                        st_pub(part + q.slot, sum);
+                    } else {
+                        zreset[j] = sentinel<XT>();
+                        st_pub(y + j, to_x<XT>(rhs[operm[j]]) - sum);
+                    }
+                }
             }
             __syncthreads();
             g = gn;
-            j = row_of<S>(g, ngroups, gs, rp, n, rows_per_group, my, false, sh);
-            if (!sh && j >= 0) {
-                b = rp[j]; e = rp[j + 1];
-                if (sl == 0) rj = rhs[operm[j]];
-                fetch_chunk<S, false, VT>(b, e, sl, ci, v, cc, vv);
-            }
+            q = group_of(g, ngroups, gt, n, rows_per_group, my, false);
+            fetch(q, b, e, rj, cc, vv);
             continue;
         }
+        const int64_t j = q.j;
         if (j >= 0) issue_x(y, cc, xx);
-        bool shn;
-        const int64_t jn = row_of<S>(gn, ngroups, gs, rp, n, rows_per_group, my, false, shn);
+        const Grp qn = group_of(gn, ngroups, gt, n, rows_per_group, my, false);
         int64_t bn = 0, en = 0;
         double rjn = 0.0;
         int32_t ccn[RPF];
         VT vvn[RPF];
-        if (!shn && jn >= 0) {
-            bn = rp[jn]; en = rp[jn + 1];
-            if (sl == 0) rjn = rhs[operm[jn]];
-            fetch_chunk<S, false, VT>(bn, en, sl, ci, v, ccn, vvn);
-        }
+        fetch(qn, bn, en, rjn, ccn, vvn);
         if (j >= 0) {
             XT acc = 0;
             bool ok = finish_chunk<VT, XT>(y, cc, vv, xx, acc, spin_limit, status);
@@ -476,7 +527,7 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
                 st_pub(y + j, to_x<XT>(rj) - acc);
             }
         }
-        g = gn; j = jn; sh = shn; b = bn; e = en; rj = rjn;
+        g = gn; q = qn; b = bn; e = en; rj = rjn;
 #pragma unroll
         for (int r = 0; r < RPF; ++r) { cc[r] = ccn[r]; vv[r] = vvn[r]; }
     }
@@ -489,7 +540,7 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
 template <int S, typename VT, typename XT>
 __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, const VT *v, const double *Dinv,
                            const int32_t *operm, XT *y, XT *z, double *zout, const double *r_orig, double *partial,
-                           const int32_t *gs, int32_t ngs, const PcgState *st, long long spin_limit,
+                           const int4 *gt, int32_t ngs, XT *part, const PcgState *st, long long spin_limit,
                            int32_t *status)
 {
     __shared__ XT red[32];
@@ -499,11 +550,10 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
     const unsigned smask = (S == 32) ? FULL : (((1u << S) - 1u) << (sub * S));
     const int rows_per_group = (blockDim.x / 32) * (32 / S);
     const int my = (threadIdx.x >> 5) * (32 / S) + sub;
-    const int64_t ngroups = gs ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
+    const int64_t ngroups = gt ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
     double dotacc = 0.0;
     int64_t g = blockIdx.x;
-    bool sh;
-    int64_t j = row_of<S>(g, ngroups, gs, cp, n, rows_per_group, my, true, sh);
+    Grp q = group_of(g, ngroups, gt, n, rows_per_group, my, true);
     int64_t b = 0, e = 0;
     XT yj = 0;
     double dj = 0.0, rj = 0.0;
@@ -511,63 +561,60 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
     int32_t cc[RPF];
     VT vv[RPF];
     XT xx[RPF];
-    auto row_extras = [&](int64_t jj, XT &yv, double &dv, int32_t &ov, double &rv) {
-        if (sl == 0) {
-            yv = y[jj]; dv = Dinv[jj]; ov = operm[jj];
-            rv = r_orig ? r_orig[ov] : 0.0;
+    auto fetch = [&](const Grp &r, int64_t &bb, int64_t &ee, XT &yv, double &dv, int32_t &ov, double &rv,
+                     int32_t (&c)[RPF], VT (&w)[RPF]) {
+        if (r.kind == GK_ROWS && r.j >= 0) {
+            bb = cp[r.j]; ee = cp[r.j + 1];
+            if (sl == 0) {
+                yv = y[r.j]; dv = Dinv[r.j]; ov = operm[r.j];
+                rv = r_orig ? r_orig[ov] : 0.0;
+            }
+            fetch_chunk<S, true, VT>(bb, ee, sl, ri, v, c, w);
         }
     };
-    if (!sh && j >= 0) {
-        b = cp[j]; e = cp[j + 1];
-        row_extras(j, yj, dj, o, rj);
-        fetch_chunk<S, true, VT>(b, e, sl, ri, v, cc, vv);
-    }
+    // finish column j with the sum of its terms (thread / lane that owns it)
+    auto publish = [&](int64_t jj, XT yv, double dv, int32_t ov, double rv, XT sum) {
+        const XT zj = to_x<XT>((double)yv * dv) - sum;
+        y[jj] = sentinel<XT>();
+        st_pub(z + jj, zj);
+        zout[ov] = (double)zj;
+        dotacc += rv * (double)zj;
+    };
+    fetch(q, b, e, yj, dj, o, rj, cc, vv);
     while (g < ngroups) {
         const int64_t gn = g + gridDim.x;
-        if (sh) {                                      // one long column for the whole block
-            const int64_t bs = cp[j], es = cp[j + 1];
-            XT ys = 0;
-            double ds = 0.0, rs = 0.0;
-            int32_t os = 0;
-            if (threadIdx.x == 0) {
-                ys = y[j]; ds = Dinv[j]; os = operm[j];
-                if (r_orig) rs = r_orig[os];
+        if (q.kind != GK_ROWS) {                      // block-wide group (block-uniform branch)
+            const int64_t j = q.j;
+            XT sum = 0;
+            if (q.kind == GK_COMBINE) {
+                if (threadIdx.x == 0) sum = combine_parts(q, part, spin_limit, status);
+            } else {
+                sum = block_part<true, VT, XT>(q, cp[j], cp[j + 1], ri, v, z, red, spin_limit, status);
             }
-            XT acc = 0;
-            if (!dot_ready<true, VT, XT>(bs, es, threadIdx.x, blockDim.x, ri, v, z, acc, spin_limit, status))
-                set_status(status, ST_TIMEOUT);
-            const XT sum = block_row_sum(acc, red);
             if (threadIdx.x == 0) {
-                const XT zj = to_x<XT>((double)ys * ds) - sum;
-                y[j] = sentinel<XT>();
-                st_pub(z + j, zj);
-                zout[os] = (double)zj;
-                dotacc += rs * (double)zj;
+                if (q.kind == GK_CHUNK) {
+                    st_pub(part + q.slot, sum);
+                } else {
+                    const int32_t os = operm[j];
+                    publish(j, y[j], Dinv[j], os, r_orig ? r_orig[os] : 0.0, sum);
+                }
             }
             __syncthreads();
             g = gn;
-            j = row_of<S>(g, ngroups, gs, cp, n, rows_per_group, my, true, sh);
-            if (!sh && j >= 0) {
-                b = cp[j]; e = cp[j + 1];
-                row_extras(j, yj, dj, o, rj);
-                fetch_chunk<S, true, VT>(b, e, sl, ri, v, cc, vv);
-            }
+            q = group_of(g, ngroups, gt, n, rows_per_group, my, true);
+            fetch(q, b, e, yj, dj, o, rj, cc, vv);
             continue;
         }
+        const int64_t j = q.j;
         if (j >= 0) issue_x(z, cc, xx);
-        bool shn;
-        const int64_t jn = row_of<S>(gn, ngroups, gs, cp, n, rows_per_group, my, true, shn);
+        const Grp qn = group_of(gn, ngroups, gt, n, rows_per_group, my, true);
         int64_t bn = 0, en = 0;
         XT yjn = 0;
         double djn = 0.0, rjn = 0.0;
         int32_t on = 0;
         int32_t ccn[RPF];
         VT vvn[RPF];
-        if (!shn && jn >= 0) {
-            bn = cp[jn]; en = cp[jn + 1];
-            row_extras(jn, yjn, djn, on, rjn);
-            fetch_chunk<S, true, VT>(bn, en, sl, ri, v, ccn, vvn);
-        }
+        fetch(qn, bn, en, yjn, djn, on, rjn, ccn, vvn);
         if (j >= 0) {
             XT acc = 0;
             bool ok = finish_chunk<VT, XT>(z, cc, vv, xx, acc, spin_limit, status);
@@ -576,15 +623,9 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
             if (!ok) set_status(status, ST_TIMEOUT);
 #pragma unroll
             for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
-            if (sl == 0) {
-                const XT zj = to_x<XT>((double)yj * dj) - acc;
-                y[j] = sentinel<XT>();
-                st_pub(z + j, zj);
-                zout[o] = (double)zj;
-                dotacc += rj * (double)zj;
-            }
+            if (sl == 0) publish(j, yj, dj, o, rj, acc);
         }
-        g = gn; j = jn; sh = shn; b = bn; e = en; yj = yjn; dj = djn; o = on; rj = rjn;
+        g = gn; q = qn; b = bn; e = en; yj = yjn; dj = djn; o = on; rj = rjn;
 #pragma unroll
         for (int r = 0; r < RPF; ++r) { cc[r] = ccn[r]; vv[r] = vvn[r]; }
     }
@@ -626,12 +667,14 @@ cudaError_t apply_t(const SolveArgs &A, const VT *vr, const VT *vc, XT *y, XT *z
 {
     const int threads = A.trsv_warps * 32;
     // group tables apply to one row per warp only
-    const int32_t *gf = S == 32 ? A.gs_f : nullptr, *gb = S == 32 ? A.gs_b : nullptr;
+    const int4 *gf = S == 32 ? A.gt_f : nullptr, *gb = S == 32 ? A.gt_b : nullptr;
     k_trsv_fwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Frp, A.Fcol, vr, A.operm, r, y, z, gf, A.ng_f,
-                                                             st, A.spin_limit, A.status); count_launches(1);
+                                                             (XT *)A.part_f, st, A.spin_limit, A.status);
+    count_launches(1);
     k_trsv_bwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z,
-                                                             zout, r, partial, gb, A.ng_b, st, A.spin_limit,
-                                                             A.status); count_launches(1);
+                                                             zout, r, partial, gb, A.ng_b, (XT *)A.part_b, st,
+                                                             A.spin_limit, A.status);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -660,6 +703,12 @@ cudaError_t fill_sentinels(const SolveArgs &A, const PcgBuffers &B, cudaStream_t
     if (A.prec == 32) k_fill_sentinel<float><<<g, VEC_THREADS, 0, s>>>(A.n, B.yl32, B.zl32);
     else k_fill_sentinel<double><<<g, VEC_THREADS, 0, s>>>(A.n, B.yl64, B.zl64);
     count_launches(1);
+    if (A.gt_f && (A.nslot_f > 0 || A.nslot_b > 0)) {      // split-row partials start unpublished
+        const int32_t m = A.nslot_f > A.nslot_b ? A.nslot_f : A.nslot_b;
+        if (A.prec == 32) k_fill_part<float><<<vec_grid(m, 64), VEC_THREADS, 0, s>>>((float *)A.part_f, A.nslot_f, (float *)A.part_b, A.nslot_b);
+        else k_fill_part<double><<<vec_grid(m, 64), VEC_THREADS, 0, s>>>((double *)A.part_f, A.nslot_f, (double *)A.part_b, A.nslot_b);
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 

@@ -89,6 +89,17 @@ def grid3d_edges(nx, ny, nz):
     return a, b
 
 
+def _sorted_unique(x):
+    """np.unique(x) for an int64 array, by sort and neighbour comparison."""
+    x = np.sort(x)
+    if len(x) == 0:
+        return x
+    keep = np.empty(len(x), bool)
+    keep[0] = True
+    np.not_equal(x[1:], x[:-1], out=keep[1:])
+    return x[keep]
+
+
 def rmat_edges(scale, edge_factor, a=0.57, b=0.19, c=0.19, seed=0, chunk=1 << 24):
     """R-MAT (Chakrabarti et al.) edge list: symmetrised, self-loops dropped, deduplicated."""
     rng = np.random.default_rng(seed)
@@ -106,8 +117,8 @@ def rmat_edges(scale, edge_factor, a=0.57, b=0.19, c=0.19, seed=0, chunk=1 << 24
             dst |= jbit.astype(np.int64) << lvl
         keep = src != dst
         lo = np.minimum(src[keep], dst[keep]); hi = np.maximum(src[keep], dst[keep])
-        keys.append(np.unique(lo * n + hi))
-    key = np.unique(np.concatenate(keys))
+        keys.append(_sorted_unique(lo * n + hi))
+    key = _sorted_unique(np.concatenate(keys))
     return n, (key // n), (key % n)
 
 
