@@ -15,7 +15,7 @@ the setup time measured with CUDA events around parac_factor.  Time-to-solution
   python bench.py --impl reference     # the CPU oracle on the same workload
 
 Workloads: grid3d-128 (default), grid2d-64, rmat-N (R-MAT scale N), rmat-24
-(32 right-hand sides, block PCG), sddm-batch-200.
+(32 right-hand sides, block PCG), sddm-batch-200, poisson-{uniform,aniso,contrast}-N.
 
 Under torchrun (--gpus N > 1) every rank factors and solves its own replica
 of the workload (the elimination does not shard; replicas only).
@@ -42,6 +42,10 @@ WORKLOAD_DESC = {
     "rmat-22": "R-MAT scale 22, edge factor 16, lognormal(0,1) weights, largest component, random ordering",
     "rmat-24": "R-MAT scale 24, edge factor 16, lognormal(0,1) weights, largest component, random ordering, "
                "32 right-hand sides",
+    "poisson-uniform-128": "3D 7-point Dirichlet Poisson 128^3, unit coefficients, random ordering",
+    "poisson-aniso-128": "3D 7-point Dirichlet Poisson 128^3, weights 1, 1, 0.01 along x, y, z, random ordering",
+    "poisson-contrast-128": "3D 7-point Dirichlet Poisson 128^3, coefficients 1 / 1e4 on 8^3 blocks "
+                            "(harmonic means on edges), random ordering",
     "sddm-batch-200": "200 SDDM systems, n log-uniform in [1e3, 2e5] (2D grid / random geometric / Erdos-Renyi), "
                       "factorised in one parac_factor_many launch, one right-hand side each",
 }

@@ -43,6 +43,8 @@ def _declare(L):
     L.orc_philox4x64_10.argtypes = [u64p, u64p, u64p]
     L.orc_slot_uniform.argtypes = [C.c_uint64] * 4
     L.orc_slot_uniform.restype = C.c_double
+    L.orc_slot_uniform_s.argtypes = [C.c_uint64] * 5
+    L.orc_slot_uniform_s.restype = C.c_double
     L.orc_suffix_scan.argtypes = [C.c_int64, f64p, f64p]
     L.orc_pick_bruteforce.argtypes = [C.c_int64, f64p, C.c_int64, C.c_double]
     L.orc_pick_bruteforce.restype = C.c_int64
@@ -50,10 +52,14 @@ def _declare(L):
     L.orc_pick_search.restype = C.c_int64
     L.orc_eliminate_one.argtypes = [C.c_int64, i32p, f64p, C.c_uint64, C.c_uint64, C.c_uint64,
                                     i64p, f64p, i32p, f64p, i32p, f64p, i32p, i32p, f64p, i64p]
+    L.orc_eliminate_one_k.argtypes = [C.c_int64, i32p, f64p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int,
+                                      i64p, f64p, i32p, f64p, i32p, f64p, i32p, i32p, f64p, i64p]
     L.orc_ingest_dims.argtypes = [C.c_int64, i64p, i32p, f64p, i32p, C.c_int, i64p, i64p, P(C.c_int)]
     L.orc_ingest_copy.argtypes = [C.c_int64, i64p, i32p, f64p, i32p, C.c_int, i64p, i32p, f64p]
     L.orc_factor_run.argtypes = [C.c_int64, i64p, i32p, f64p, i32p, C.c_int, C.c_uint64, C.c_uint64,
                                  P(C.c_void_p)]
+    L.orc_factor_run_k.argtypes = [C.c_int64, i64p, i32p, f64p, i32p, C.c_int, C.c_uint64, C.c_uint64, C.c_int,
+                                   P(C.c_void_p)]
     L.orc_factor_tracked.argtypes = [C.c_int64, i64p, i32p, f64p, i32p, C.c_int, C.c_uint64, C.c_uint64,
                                      C.c_uint64, C.c_int, P(C.c_void_p)]
     L.orc_factor_dims.argtypes = [C.c_void_p, i64p, i64p, i64p]
@@ -98,9 +104,10 @@ def philox4x64_10(ctr, key, L=None):
     return o
 
 
-def slot_uniform(seed, k, p, sys=0, L=None):
+def slot_uniform(seed, k, p, sys=0, q=0, L=None):
+    """Uniform of sample q of slot p (q > 0 only for AC(k))."""
     L = L or lib()
-    return L.orc_slot_uniform(seed, k, p, sys)
+    return L.orc_slot_uniform(seed, k, p, sys) if q == 0 else L.orc_slot_uniform_s(seed, k, p, sys, q)
 
 
 def suffix_scan(w, L=None):
@@ -124,21 +131,28 @@ def pick_search(S, lo, R, L=None):
     return L.orc_pick_search(len(S), _p(M, C.c_double), lo, R)
 
 
-def eliminate_one(rows, w, seed, k, sys=0, L=None):
-    """Eliminate one pivot from its gathered entries; returns a dict."""
+def eliminate_one(rows, w, seed, k, sys=0, samples=1, L=None):
+    """Eliminate one pivot from its gathered entries; returns a dict.  With
+    samples > 1 (AC(samples)) the sampled edges are listed sample by sample:
+    sample q of slot p at q*(d-1) + p-1."""
     L = L or lib()
     rows = _arr(rows, np.int32); w = _arr(w, np.float64)
-    g = len(rows); m = max(g, 1)
+    g = len(rows); m = max(g, 1); ms = m * samples
     d = C.c_int64(); D = C.c_double()
     mrow = np.zeros(m, np.int32); mw = np.zeros(m); mmult = np.zeros(m, np.int32); fval = np.zeros(m)
-    slo = np.zeros(m, np.int32); shi = np.zeros(m, np.int32); sc = np.zeros(m); spick = np.zeros(m, np.int64)
-    rc = L.orc_eliminate_one(g, _p(rows, C.c_int32), _p(w, C.c_double), seed, k, sys, C.byref(d), C.byref(D),
-                             _p(mrow, C.c_int32), _p(mw, C.c_double), _p(mmult, C.c_int32), _p(fval, C.c_double),
-                             _p(slo, C.c_int32), _p(shi, C.c_int32), _p(sc, C.c_double), _p(spick, C.c_int64))
+    slo = np.zeros(ms, np.int32); shi = np.zeros(ms, np.int32); sc = np.zeros(ms); spick = np.zeros(ms, np.int64)
+    args = (_p(mrow, C.c_int32), _p(mw, C.c_double), _p(mmult, C.c_int32), _p(fval, C.c_double),
+            _p(slo, C.c_int32), _p(shi, C.c_int32), _p(sc, C.c_double), _p(spick, C.c_int64))
+    if samples == 1:
+        rc = L.orc_eliminate_one(g, _p(rows, C.c_int32), _p(w, C.c_double), seed, k, sys, C.byref(d),
+                                 C.byref(D), *args)
+    else:
+        rc = L.orc_eliminate_one_k(g, _p(rows, C.c_int32), _p(w, C.c_double), seed, k, sys, samples, C.byref(d),
+                                   C.byref(D), *args)
     if rc:
         raise OracleError(rc)
     dd = d.value
-    ns = max(dd - 1, 0)
+    ns = max(dd - 1, 0) * samples
     return dict(d=dd, D=D.value, rows=mrow[:dd].copy(), w=mw[:dd].copy(), mult=mmult[:dd].copy(),
                 fval=fval[:dd].copy(), lo=slo[:ns].copy(), hi=shi[:ns].copy(), c=sc[:ns].copy(),
                 pick=spick[:ns].copy())
@@ -175,14 +189,19 @@ def _collect(L, h):
                 depth=int(st[4]), violations=int(st[5]))
 
 
-def factor(colptr, rowind, val, ordering=None, seed=0, sys=0, kind=KIND_AUTO, L=None):
-    """Sequential rchol factor L ~ F D F^T in label space (Alg. 1 + Alg. 2)."""
+def factor(colptr, rowind, val, ordering=None, seed=0, sys=0, kind=KIND_AUTO, samples=1, L=None):
+    """Sequential rchol factor L ~ F D F^T in label space (Alg. 1 + Alg. 2;
+    samples > 1: AC(samples), every clique-tree slot drawing that many edges)."""
     L = L or lib()
     colptr = _arr(colptr, np.int64); rowind = _arr(rowind, np.int32); val = _arr(val, np.float64)
     ordp = None if ordering is None else _arr(ordering, np.int32)
     h = C.c_void_p()
-    rc = L.orc_factor_run(len(colptr) - 1, _p(colptr, C.c_int64), _p(rowind, C.c_int32), _p(val, C.c_double),
-                          _p(ordp, C.c_int32), kind, seed, sys, C.byref(h))
+    if samples == 1:
+        rc = L.orc_factor_run(len(colptr) - 1, _p(colptr, C.c_int64), _p(rowind, C.c_int32),
+                              _p(val, C.c_double), _p(ordp, C.c_int32), kind, seed, sys, C.byref(h))
+    else:
+        rc = L.orc_factor_run_k(len(colptr) - 1, _p(colptr, C.c_int64), _p(rowind, C.c_int32),
+                                _p(val, C.c_double), _p(ordp, C.c_int32), kind, seed, sys, samples, C.byref(h))
     if rc:
         raise OracleError(rc)
     return _collect(L, h)

@@ -98,13 +98,19 @@ void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint6
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* R4: the uniform in (0,1] drawn for slot p of pivot k of system sys. */
-double orc_slot_uniform(uint64_t seed, uint64_t k, uint64_t p, uint64_t sys)
+/* R4: the uniform in (0,1] drawn for sample q of slot p of pivot k of
+ * system sys (q = 0 for the plain method; AC(k) draws q = 0..k-1). */
+double orc_slot_uniform_s(uint64_t seed, uint64_t k, uint64_t p, uint64_t sys, uint64_t q)
 {
-    uint64_t ctr[4] = { k, p, sys, 0 }, key[2] = { seed, 0 }, o[4];
+    uint64_t ctr[4] = { k, p, sys, q }, key[2] = { seed, 0 }, o[4];
     orc_philox4x64_10(ctr, key, o);
     uint64_t m53 = o[0] >> 11;
     return (double)(m53 + 1) * 0x1.0p-53;
+}
+
+double orc_slot_uniform(uint64_t seed, uint64_t k, uint64_t p, uint64_t sys)
+{
+    return orc_slot_uniform_s(seed, k, p, sys, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -188,14 +194,18 @@ typedef struct {
     double  *mw;        /* merged weights                    [g] */
     int32_t *mmult;     /* multiplicities                    [g] */
     double  *fval;      /* F(u,k) for mrow order             [g] */
-    int32_t *slo, *shi; /* sampled edges (min, max label)    [g] */
-    double  *sc;        /* sampled edge weights              [g] */
-    int64_t *spick;     /* 0-based weight-order index picked [g] */
+    int32_t *slo, *shi; /* sampled edges (min, max label)    [ksamp * g], sample q of slot p at q*(d-1) + p-1 */
+    double  *sc;        /* sampled edge weights              [ksamp * g] */
+    int64_t *spick;     /* 0-based weight-order index picked [ksamp * g] */
 } orc_step;
 
-/* Eliminate pivot k whose gathered entries are (rows[i], w[i]), i < g. */
-int orc_eliminate(int64_t g, const int32_t *rows, const double *w, uint64_t seed,
-                  uint64_t k, uint64_t sys, orc_step *st)
+/* Eliminate pivot k whose gathered entries are (rows[i], w[i]), i < g.
+ * ksamp samples per slot (AC(ksamp), Sec. VI's AC(k) read as: every slot of
+ * the clique tree draws ksamp independent neighbours with counters
+ * (k, p, sys, q), q < ksamp, each edge weighted c_p / ksamp; ksamp = 1 is
+ * Alg. 2). */
+static int orc_eliminate_k(int64_t g, const int32_t *rows, const double *w, uint64_t seed,
+                           uint64_t k, uint64_t sys, int ksamp, orc_step *st)
 {
     orc_ent *e = malloc(sizeof(orc_ent) * (size_t)(g > 0 ? g : 1));
     orc_ent *s = malloc(sizeof(orc_ent) * (size_t)(g > 0 ? g : 1));
@@ -233,19 +243,29 @@ int orc_eliminate(int64_t g, const int32_t *rows, const double *w, uint64_t seed
     M[d - 1] = S[d - 1];
     for (int64_t j = d - 2; j >= 0; --j) M[j] = S[j] > M[j + 1] ? S[j] : M[j + 1];
 
-    for (int64_t p = 1; p <= d - 1; ++p) {                         /* R4, R5 */
-        double v = orc_slot_uniform(seed, k, (uint64_t)p, sys);
-        double R = S[p] * v;
-        int64_t j = orc_pick_search(d, M, p, R);
-        int32_t u = s[p - 1].row, x = s[j].row;
-        double c = (S[p] * s[p - 1].w) / D;
-        st->slo[p - 1] = u < x ? u : x;
-        st->shi[p - 1] = u < x ? x : u;
-        st->sc[p - 1] = c;
-        st->spick[p - 1] = j;
+    for (int q = 0; q < ksamp; ++q) {
+        for (int64_t p = 1; p <= d - 1; ++p) {                     /* R4, R5 */
+            double v = orc_slot_uniform_s(seed, k, (uint64_t)p, sys, (uint64_t)q);
+            double R = S[p] * v;
+            int64_t j = orc_pick_search(d, M, p, R);
+            int32_t u = s[p - 1].row, x = s[j].row;
+            double c = (S[p] * s[p - 1].w) / D;
+            if (ksamp > 1) c = c / (double)ksamp;
+            int64_t at = (int64_t)q * (d - 1) + (p - 1);
+            st->slo[at] = u < x ? u : x;
+            st->shi[at] = u < x ? x : u;
+            st->sc[at] = c;
+            st->spick[at] = j;
+        }
     }
     free(e); free(s); free(S); free(M);
     return ORC_OK;
+}
+
+int orc_eliminate(int64_t g, const int32_t *rows, const double *w, uint64_t seed,
+                  uint64_t k, uint64_t sys, orc_step *st)
+{
+    return orc_eliminate_k(g, rows, w, seed, k, sys, 1, st);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -389,6 +409,7 @@ typedef struct {
     double *D;
     int64_t *level;         /* dependency-DAG level per label */
     int64_t max_gather, nfill, nnz_all;
+    int ksamp;              /* samples per clique-tree slot (AC(ksamp)); 1 = Alg. 2 */
 } orc_state;
 
 static void state_free(orc_state *S)
@@ -421,13 +442,15 @@ static int state_eliminate(orc_state *S, int64_t k, uint64_t seed, uint64_t sys,
     int64_t g = (o1 - o0) + S->fill[k].cnt;
     if (g > S->max_gather) S->max_gather = g;
     size_t gg = (size_t)(g > 0 ? g : 1);
+    const int ks = S->ksamp > 0 ? S->ksamp : 1;
+    size_t gs = gg * (size_t)ks;
     int32_t *rows = malloc(sizeof(int32_t) * gg);
     double *w = malloc(sizeof(double) * gg);
     orc_step st;
     st.mrow = malloc(sizeof(int32_t) * gg); st.mw = malloc(sizeof(double) * gg);
     st.mmult = malloc(sizeof(int32_t) * gg); st.fval = malloc(sizeof(double) * gg);
-    st.slo = malloc(sizeof(int32_t) * gg); st.shi = malloc(sizeof(int32_t) * gg);
-    st.sc = malloc(sizeof(double) * gg); st.spick = malloc(sizeof(int64_t) * gg);
+    st.slo = malloc(sizeof(int32_t) * gs); st.shi = malloc(sizeof(int32_t) * gs);
+    st.sc = malloc(sizeof(double) * gs); st.spick = malloc(sizeof(int64_t) * gs);
     if (!rows || !w || !st.mrow || !st.mw || !st.mmult || !st.fval || !st.slo || !st.shi || !st.sc || !st.spick)
         return ORC_ENOMEM;
     int64_t t = 0;
@@ -435,7 +458,7 @@ static int state_eliminate(orc_state *S, int64_t k, uint64_t seed, uint64_t sys,
     for (int64_t q = 0; q < S->fill[k].cnt; ++q) { rows[t] = S->fill[k].row[q]; w[t] = S->fill[k].w[q]; ++t; }
     free(S->fill[k].row); free(S->fill[k].w); memset(&S->fill[k], 0, sizeof(orc_fillcol));
 
-    int rc = orc_eliminate(g, rows, w, seed, (uint64_t)k, sys, &st);
+    int rc = orc_eliminate_k(g, rows, w, seed, (uint64_t)k, sys, ks, &st);
     free(rows); free(w);
     if (rc) return rc;
     S->D[k] = st.D;
@@ -449,7 +472,8 @@ static int state_eliminate(orc_state *S, int64_t k, uint64_t seed, uint64_t sys,
     int64_t lk = S->level[k] + 1;
     for (int64_t i = 0; i < st.d; ++i)
         if (S->level[st.mrow[i]] < lk) S->level[st.mrow[i]] = lk;
-    for (int64_t p = 0; p + 1 < st.d; ++p) {
+    const int64_t nsamp = st.d > 0 ? (int64_t)ks * (st.d - 1) : 0;
+    for (int64_t p = 0; p < nsamp; ++p) {
         rc = fill_push(&S->fill[st.slo[p]], st.shi[p], st.sc[p]);
         if (rc) return rc;
         S->nfill++;
@@ -507,12 +531,14 @@ static int state_to_factor(orc_state *S, orc_factor **out)
     return ORC_OK;
 }
 
-int orc_factor_run(int64_t n, const int64_t *colptr, const int32_t *rowind, const double *val,
-                   const int32_t *ordering, int kind, uint64_t seed, uint64_t sys, orc_factor **out)
+int orc_factor_run_k(int64_t n, const int64_t *colptr, const int32_t *rowind, const double *val,
+                     const int32_t *ordering, int kind, uint64_t seed, uint64_t sys, int ksamp, orc_factor **out)
 {
     *out = NULL;
+    if (ksamp < 1) return ORC_EINVAL;
     orc_state S;
     memset(&S, 0, sizeof S);
+    S.ksamp = ksamp;
     int rc = orc_ingest(n, colptr, rowind, val, ordering, kind, &S.L);
     if (rc) return rc;
     rc = state_init(&S);
@@ -520,6 +546,12 @@ int orc_factor_run(int64_t n, const int64_t *colptr, const int32_t *rowind, cons
     if (!rc) rc = state_to_factor(&S, out);
     state_free(&S);
     return rc;
+}
+
+int orc_factor_run(int64_t n, const int64_t *colptr, const int32_t *rowind, const double *val,
+                   const int32_t *ordering, int kind, uint64_t seed, uint64_t sys, orc_factor **out)
+{
+    return orc_factor_run_k(n, colptr, rowind, val, ordering, kind, seed, sys, 1, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -576,6 +608,7 @@ int orc_factor_tracked(int64_t n, const int64_t *colptr, const int32_t *rowind, 
     *out = NULL;
     orc_state S;
     memset(&S, 0, sizeof S);
+    S.ksamp = 1;
     int rc = orc_ingest(n, colptr, rowind, val, ordering, kind, &S.L);
     if (rc) return rc;
     rc = state_init(&S);
@@ -673,6 +706,19 @@ int orc_eliminate_one(int64_t g, const int32_t *rows, const double *w, uint64_t 
 {
     orc_step st = { 0, 0.0, mrow, mw, mmult, fval, slo, shi, sc, spick };
     int rc = orc_eliminate(g, rows, w, seed, k, sys, &st);
+    *d_out = st.d; *D_out = st.D;
+    return rc;
+}
+
+/* As orc_eliminate_one with ksamp samples per slot; sampled-edge arrays need
+ * room for ksamp * g entries (sample q of slot p at q*(d-1) + p-1). */
+int orc_eliminate_one_k(int64_t g, const int32_t *rows, const double *w, uint64_t seed, uint64_t k,
+                        uint64_t sys, int ksamp, int64_t *d_out, double *D_out, int32_t *mrow, double *mw,
+                        int32_t *mmult, double *fval, int32_t *slo, int32_t *shi, double *sc, int64_t *spick)
+{
+    if (ksamp < 1) return ORC_EINVAL;
+    orc_step st = { 0, 0.0, mrow, mw, mmult, fval, slo, shi, sc, spick };
+    int rc = orc_eliminate_k(g, rows, w, seed, k, sys, ksamp, &st);
     *d_out = st.d; *D_out = st.D;
     return rc;
 }

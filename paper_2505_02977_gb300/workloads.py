@@ -273,6 +273,46 @@ def _grid3d(side, weights, seed):
     return laplacian_from_edges(side ** 3, a, b, w)
 
 
+def poisson3d(side, field="uniform", seed=0, eps=0.01, block=8, contrast=1e4):
+    """7-point finite-difference Poisson matrix on a side^3 grid with Dirichlet
+    boundary (a ghost neighbour beyond each face: SDDM, the boundary rows carry
+    the missing neighbours' weights as excess).  Coefficient fields:
+      uniform   every edge weight 1
+      aniso     weights 1, 1, eps along x, y, z (eps = 0.01: 100:1 anisotropy)
+      contrast  per-cell coefficient 1 or `contrast` (1e4) on block^3 cell blocks,
+                each block's value drawn with probability 1/2 (seed); an edge gets the
+                harmonic mean 2 k_a k_b / (k_a + k_b) of its cells' coefficients
+    The paper's anisotropy and contrast fields are not specified; these are
+    stated stand-ins."""
+    n = side ** 3
+    idx = np.arange(n).reshape(side, side, side)          # [z, y, x]
+    if field == "contrast":
+        nb = (side + block - 1) // block
+        kb = np.where(np.random.default_rng(seed).random((nb, nb, nb)) < 0.5, 1.0, contrast)
+        z, y, x = np.meshgrid(np.arange(side), np.arange(side), np.arange(side), indexing="ij")
+        kappa = kb[z // block, y // block, x // block].ravel()
+    else:
+        kappa = np.ones(n)
+    dir_w = {"x": 1.0, "y": 1.0, "z": eps if field == "aniso" else 1.0}
+    a_l, b_l, w_l = [], [], []
+    exc = np.zeros(n)
+    for axis, name in ((2, "x"), (1, "y"), (0, "z")):
+        lo = [slice(None)] * 3; hi = [slice(None)] * 3
+        lo[axis] = slice(0, side - 1); hi[axis] = slice(1, side)
+        a = idx[tuple(lo)].ravel(); b = idx[tuple(hi)].ravel()
+        ka, kb2 = kappa[a], kappa[b]
+        w = dir_w[name] * 2.0 * ka * kb2 / (ka + kb2)
+        a_l.append(a); b_l.append(b); w_l.append(w)
+        # ghost neighbours beyond the two faces along this axis
+        first = [slice(None)] * 3; last = [slice(None)] * 3
+        first[axis] = 0; last[axis] = side - 1
+        for face in (idx[tuple(first)].ravel(), idx[tuple(last)].ravel()):
+            exc[face] += dir_w[name] * kappa[face]
+    A = laplacian_from_edges(n, np.concatenate(a_l), np.concatenate(b_l), np.concatenate(w_l), excess=exc)
+    A.meta.update(field=field, side=side, kappa=kappa)
+    return A
+
+
 def _rmat(scale, seeds):
     n, a, b = rmat_edges(scale, 16, seed=seeds[0])
     n, a, b = largest_component(n, a, b)
@@ -307,6 +347,7 @@ def _config(name):
     rmat-22       R-MAT scale 22, edge factor 16, (.57,.19,.19,.05), lognormal(0,1) weights, LCC
     rmat-24       as rmat-22 at scale 24, 32 right-hand sides
     grid3d-N      N^3 grid as grid3d-128 (smaller cases for tests)
+    poisson-F-N   N^3 Dirichlet Poisson (F = uniform, aniso, contrast; see poisson3d)
     """
     if name == "grid2d-64":
         A = _grid2d(64, "unit", 0)
@@ -321,6 +362,10 @@ def _config(name):
     if name == "rmat-24":
         A = _rmat(24, (41, 42))
         return A, random_ordering(A.n, 43), 45, gaussian_rhs(A.n, 32, 44)
+    if name.startswith("poisson-"):                # poisson-{uniform,aniso,contrast}-N
+        _, field, side = name.split("-")
+        A = poisson3d(int(side), field, seed=51)
+        return A, random_ordering(A.n, 52), 53, gaussian_rhs(A.n, 1, 54, center=False)
     if name.startswith("rmat-"):
         s = int(name.split("-")[1])
         A = _rmat(s, (21 + s, 22 + s))

@@ -227,3 +227,12 @@ def test_rmat_bit_identical(P, monkeypatch, sample_sort):
     A, perm, seed, _ = W.config("rmat-15")
     _, st = _check(P, A, perm, seed)
     assert st["vertices_global_path"] > 0
+
+
+@pytest.mark.parametrize("field", ["uniform", "aniso", "contrast"])
+def test_poisson_stand_ins_bit_identical(P, field):
+    """Dirichlet Poisson stand-ins (SDDM: boundary rows ground through the
+    ground node) on a 24^3 grid."""
+    A, perm, seed, _ = W.config(f"poisson-{field}-24")
+    _, st = _check(P, A, perm, seed)
+    assert st["n"] == A.n

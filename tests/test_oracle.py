@@ -407,3 +407,96 @@ def test_pcg_path_converges_at_once():
     bvec = W.gaussian_rhs(n, 1, 3)
     _, it, rr = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, bvec, 1e-8, 50)
     assert it <= 2 and rr <= 1e-8
+
+
+# ----------------------------------------------------------------- AC(k)
+# AC(k) (Sec. VI, after Gao-Kyng-Spielman): every slot of the clique tree
+# draws k neighbours, sample q with Philox counter (k, p, sys, q), each edge
+# weighted c_p / k.  k = 1 is Alg. 2.
+
+def test_ac2_counter_word_and_weights():
+    """Sample q of slot p uses counter word 3 = q (checked against numpy's
+    Philox); sample 0 of AC(2) picks exactly AC(1)'s neighbour with half its
+    weight; sample 1 follows the literal "largest j >= p with S[j] >= R" rule
+    with its own uniform."""
+    rng = np.random.default_rng(17)
+    for trial in range(100):
+        d = int(rng.integers(2, 12))
+        rows = np.arange(10, 10 + d, dtype=np.int32)
+        w = rng.lognormal(0, 1, d)
+        k = int(rng.integers(1, 1000))
+        one = oracle.eliminate_one(rows, w, seed=trial, k=k)
+        two = oracle.eliminate_one(rows, w, seed=trial, k=k, samples=2)
+        m = d - 1
+        assert len(two["c"]) == 2 * m
+        assert np.array_equal(two["pick"][:m], one["pick"])
+        assert np.array_equal(two["c"][:m], one["c"] / 2)
+        order = np.lexsort((two["rows"], two["w"]))
+        ws = two["w"][order]
+        S = oracle.suffix_scan(ws)
+        for p in range(1, d):
+            raw = np.random.Philox(key=np.array([trial, 0], np.uint64),
+                                   counter=np.array([k - 1, p, 0, 1], np.uint64)).random_raw(1)[0]
+            v = ((int(raw) >> 11) + 1) * 2.0 ** -53
+            assert oracle.slot_uniform(trial, k, p, 0, q=1) == v
+            assert two["pick"][m + p - 1] == oracle.pick_bruteforce(S, p, S[p] * v)
+            assert two["c"][m + p - 1] == two["c"][p - 1]
+
+
+def test_ac2_unbiased_by_enumeration():
+    """AC(2): summed over all outcomes of both samples of every slot, the
+    expected update equals the exact Schur complement update, as for Alg. 2."""
+    rng = np.random.default_rng(19)
+    for trial in range(200):
+        d = int(rng.integers(1, 7))
+        rows = np.arange(100, 100 + d, dtype=np.int32)
+        w = rng.lognormal(0, 1, d)
+        out = oracle.eliminate_one(rows, w, seed=trial, k=3, samples=2)
+        order = np.lexsort((out["rows"], out["w"]))
+        ws = out["w"][order]; rs = out["rows"][order]
+        idx = {r: i for i, r in enumerate(out["rows"])}
+        S = np.cumsum(ws[::-1])[::-1]
+        E = np.zeros((d, d))
+        for q in range(2):
+            for p in range(1, d):
+                c = out["c"][q * (d - 1) + p - 1]
+                for j in range(p, d):
+                    prob = ws[j] / S[p]
+                    a, b = idx[rs[p - 1]], idx[rs[j]]
+                    E[a, a] += prob * c; E[b, b] += prob * c; E[a, b] -= prob * c; E[b, a] -= prob * c
+        wm = out["w"]; D = out["D"]
+        Cex = np.diag(wm) - np.outer(wm, wm) / D
+        assert np.allclose(E, Cex, rtol=0, atol=1e-14 * max(1.0, np.abs(Cex).max()))
+
+
+def test_ac2_factor_counts_mean_and_variance():
+    """AC(2) appends twice the fill edges of Alg. 2; paths stay exact; the mean
+    of F D F^T over seeds matches L within 4 standard errors, with a smaller
+    variance than Alg. 2's (the reason for more samples)."""
+    A = _mat(8, np.arange(7), np.arange(1, 8), np.linspace(0.5, 2.0, 7))
+    perm = W.random_ordering(8, 3)
+    F2 = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=1, samples=2)
+    assert np.allclose(reconstruct(F2, perm), A.dense(), rtol=0, atol=1e-13)
+    rng = np.random.default_rng(23)
+    n = 6
+    ia, ib = np.triu_indices(n, 1)
+    A = _mat(n, ia, ib, rng.uniform(0.2, 3, len(ia)))
+    perm = W.random_ordering(n, 77)
+    F1 = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=5)
+    F2 = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=5, samples=2)
+    assert F2["fill"] == 2 * F1["fill"]
+    L = oracle.lib()
+    nseeds = 20_000
+    stats = {}
+    for ks in (1, 2):
+        acc = np.zeros((n, n)); acc2 = np.zeros((n, n))
+        for s in range(nseeds):
+            G = reconstruct(oracle.factor(A.colptr, A.rowind, A.val, perm, seed=s, samples=ks, L=L), perm)
+            acc += G; acc2 += G * G
+        mean = acc / nseeds
+        var = np.maximum(acc2 / nseeds - mean ** 2, 0)
+        se = np.sqrt(var / nseeds)
+        Ad = A.dense()
+        assert np.all(np.abs(mean - Ad) <= 4 * se + 1e-10 * np.abs(Ad).max())
+        stats[ks] = var.sum()
+    assert stats[2] < stats[1]
