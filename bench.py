@@ -210,7 +210,7 @@ def run_reference(args, world, rank):
     times, nnzG = [], 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)
+        F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed, samples=args.samples)
         times.append(time.perf_counter() - t0)
         nnzG = len(F["row"]) + F["n"]
     value = nnzG * len(times) / sum(times) / 1e6
@@ -246,7 +246,7 @@ def run_ours(args, world, rank, local, pg):
     td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     cp, ri, va, od, bd = td(A.colptr), td(A.rowind), td(A.val), td(perm), td(b)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # > L2 (129 MB)
-    opts = P.parac_opts_default(g_precision=args.prec, timing=1)
+    opts = P.parac_opts_default(g_precision=args.prec, timing=1, samples=args.samples)
 
     def step():
         G = P.parac_factor(A.n, cp, ri, va, od, seed, opts)
@@ -341,7 +341,7 @@ def run_ours(args, world, rank, local, pg):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
-        F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)
+        F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed, samples=args.samples)
         tc = time.perf_counter() - t0
         cpu = {"value": (len(F["row"]) + F["n"]) / tc / 1e6, "unit": "Mnnz(G)/s", "cores": 1, "kind": "oracle",
                "sample": f"one full sequential oracle factorisation of {args.workload} ({tc:.1f} s)",
@@ -354,6 +354,7 @@ def run_ours(args, world, rank, local, pg):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload), "n": A.n, "nnz_L": A.nnz,
                    "nnz_G": nnzG, "G_precision": args.prec, "tol": args.tol, "ordering": args.ordering,
+                   "samples_per_slot": args.samples,
                    "nrhs": 1 if b.ndim == 1 else int(b.shape[1]),
                    "l2": "flushed before every step (256 MB write)", "parallelism": f"replicas x{world}"},
         "tts_ms": statistics.median(step_ms), "setup_ms": statistics.median(setup_ms),
@@ -472,6 +473,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ordering", default="random", choices=["random", "nnz"])
+    ap.add_argument("--samples", type=int, default=1, help="samples per clique-tree slot (AC(k); 1: Alg. 2)")
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
     try:

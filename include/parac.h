@@ -88,6 +88,10 @@ enum { PARAC_SPTRSV_AUTO = 0, PARAC_SPTRSV_WARP = 1, PARAC_SPTRSV_SUB8 = 2, PARA
  *   check_every     PCG iterations between host convergence checks (0 = 8).
  *   stream          cudaStream_t to order all work on.
  *   timing          Nonzero: record per-phase device times in the stats.
+ *   samples         Samples drawn per clique-tree slot (0 or 1: Alg. 2).  k > 1
+ *                   is AC(k) (Sec. VI): slot p draws k neighbours, sample q
+ *                   with Philox counter (k_label, p, sys, q), each edge weighted
+ *                   c_p / k -- a denser factor for possibly fewer iterations.
  */
 typedef struct {
     int32_t kind;
@@ -103,6 +107,7 @@ typedef struct {
     int32_t check_every;
     int32_t timing;
     void *stream;
+    int32_t samples;
 } parac_opts;
 
 void parac_opts_default(parac_opts *opts);

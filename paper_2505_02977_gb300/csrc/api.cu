@@ -269,6 +269,7 @@ Opts read_opts(const parac_opts *in)
     if (r.o.queue_chunk <= 0) r.o.queue_chunk = 1;
     if (r.o.check_every <= 0) r.o.check_every = 8;
     if (r.o.g_precision != 32) r.o.g_precision = 64;
+    if (r.o.samples <= 0) r.o.samples = 1;
     r.st = (cudaStream_t)r.o.stream;
     return r;
 }
@@ -288,6 +289,7 @@ struct FactorOut {
     unsigned long long stats[32] = {0};
     unsigned long long pool_used = 0, f_used = 0, scratch_used = 0;
     int32_t max_lower_column = 0;
+    int32_t samples = 1;
     int regrows = 0;
     double t_ingest = 0, t_elim = 0, t_compact = 0;
     int blocks = 0, warps = 0;
@@ -479,8 +481,11 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
     }
     DBuf pool_row, pool_w, f_row, f_val, scratch;
     for (int attempt = 0;; ++attempt) {
-        const unsigned long long pool_cap = (unsigned long long)std::ceil(mult * (double)nnz_low) + 4096ull;
-        const unsigned long long f_cap = (unsigned long long)std::ceil(std::max(mult, 4.0) * (double)nnz_low) +
+        // AC(k): k fill edges per slot, and the neighbour lists of later pivots
+        // grow with them -- AC(2) on 3D grids has 10-30x the fill of Alg. 2
+        const double ks = O.o.samples > 1 ? 4.0 * (double)O.o.samples * (double)O.o.samples : 1.0;
+        const unsigned long long pool_cap = (unsigned long long)std::ceil(mult * ks * (double)nnz_low) + 4096ull;
+        const unsigned long long f_cap = (unsigned long long)std::ceil(std::max(mult, 4.0) * ks * (double)nnz_low) +
                                          (unsigned long long)nl + (unsigned long long)total_warps * fchunk + 4096ull;
         pool_row = dalloc<int32_t>(pool_cap, st); pool_w = dalloc<double>(pool_cap, st);
         f_row = dalloc<int32_t>(f_cap, st); f_val = dalloc<double>(f_cap, st);
@@ -522,6 +527,8 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         a.idle_ns = 512;
         a.coop = 1;
         if (const char *e = getenv("PARAC_COOP")) a.coop = atoi(e) != 0;
+        a.samples = O.o.samples;
+        out.samples = O.o.samples;
         a.sample_sort = 1;
         if (const char *e = getenv("PARAC_SAMPLE_SORT")) a.sample_sort = atoi(e) != 0;
         if (const char *e = getenv("PARAC_IDLE_NS")) a.idle_ns = std::max(32, std::min(1000000, atoi(e)));
@@ -701,7 +708,7 @@ std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_ind
              "\"scratch_bytes_used\": %llu, \"vertices_warp_path\": %llu, \"vertices_block_path\": %llu, "
              "\"vertices_global_path\": %llu, \"vertices_register_path\": %llu, \"handoffs\": %llu, "
              "\"queue_spins\": %llu, \"regrows\": %d, \"max_lower_column\": %d, \"blocks\": %d, "
-             "\"warps_per_block\": %d, \"precision\": %d, \"system\": %d, \"t_ingest_ms\": %.4f, "
+             "\"warps_per_block\": %d, \"precision\": %d, \"samples\": %d, \"system\": %d, \"t_ingest_ms\": %.4f, "
              "\"t_elim_ms\": %.4f, \"t_compact_ms\": %.4f, \"depth\": %d, \"cycles\": {\"wait\": %llu, "
              "\"gather\": %llu, \"sort_merge\": %llu, \"store_sort_scan\": %llu, \"sample_append\": %llu, "
              "\"release\": %llu, \"reg_weight_sort\": %llu, \"reg_scan\": %llu, \"coop_join\": %llu, "
@@ -710,7 +717,7 @@ std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_ind
              "\"coop_release\": %llu}}",
              (long long)h->n, (long long)h->nnzF, (long long)(h->nnzF + h->n), (long long)fo.nl,
              (long long)fo.nnz_low, fo.stats[3], fo.pool_used, fo.f_used, fo.scratch_used, fo.stats[0], fo.stats[1],
-             fo.stats[2], fo.stats[5], fo.stats[6], fo.stats[4], fo.regrows, fo.max_lower_column, fo.blocks, fo.warps, h->prec, sys_index, fo.t_ingest, fo.t_elim,
+             fo.stats[2], fo.stats[5], fo.stats[6], fo.stats[4], fo.regrows, fo.max_lower_column, fo.blocks, fo.warps, h->prec, fo.samples, sys_index, fo.t_ingest, fo.t_elim,
              fo.t_compact, h->depth, fo.stats[8], fo.stats[9], fo.stats[10], fo.stats[11], fo.stats[12],
              fo.stats[13], fo.stats[14], fo.stats[15], fo.stats[16], fo.stats[17], fo.stats[18], fo.stats[19],
              fo.stats[20], fo.stats[21], fo.stats[22], fo.stats[23]);
@@ -764,6 +771,7 @@ void parac_opts_default(parac_opts *o)
     o->warps_per_block = 8;
     o->queue_chunk = 1;
     o->check_every = 8;
+    o->samples = 1;
 }
 
 const char *parac_status_string(parac_status s)

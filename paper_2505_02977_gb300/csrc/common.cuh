@@ -122,11 +122,13 @@ __device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_
     return o;
 }
 
-// Uniform in (0, 1] for sampling slot p of pivot k (local label) of system sys:
-// the top 53 bits of the first output word, plus one, times 2^-53.
-__device__ __forceinline__ double slot_uniform(uint64_t seed, uint64_t k, uint64_t p, uint64_t sys)
+// Uniform in (0, 1] for sample q of sampling slot p of pivot k (local label)
+// of system sys (q > 0 only with several samples per slot, AC(k)): the top 53
+// bits of the first output word, plus one, times 2^-53.
+__device__ __forceinline__ double slot_uniform(uint64_t seed, uint64_t k, uint64_t p, uint64_t sys,
+                                               uint64_t q = 0ull)
 {
-    const U64x4 o = philox4x64_10(k, p, sys, 0ull, seed, 0ull);
+    const U64x4 o = philox4x64_10(k, p, sys, q, seed, 0ull);
     return (double)((o.v[0] >> 11) + 1ull) * 0x1.0p-53;
 }
 
@@ -205,6 +207,7 @@ struct ElimArgs {
     int32_t *trace_parent;         // optional: pivot whose decrement made the vertex ready
     int32_t *trace_phase;          // optional: cycles of the cooperative path's 8 phases [nl * 8]
     int32_t sample_sort;           // cooperative path: sample sort for working sets in global memory
+    int32_t samples;               // samples per clique-tree slot (AC(k)); 1: Alg. 2
 };
 
 // Bytes of shared/scratch memory per entry of the per-vertex working set:

@@ -443,11 +443,28 @@ __device__ int32_t eliminate_small(const ElimArgs &a, int32_t k, int64_t o0, int
     int32_t lo = 0, hi = 0;
     if (act) {
         c = __ddiv_rn(__dmul_rn(Sp, wu), Dk);
+        if (a.samples > 1) c = __ddiv_rn(c, (double)a.samples);
         lo = u < xv ? u : xv;
         hi = u < xv ? xv : u;
     }
     if (!append_fill(a, act, lo, hi, c)) return -2;
-    ws.n_fill += (unsigned long long)(d - 1);
+    // further samples of every slot (AC(k)): own uniforms, the same weight
+    for (int q = 1; q < a.samples; ++q) {
+        const unsigned long long Rq = act ? dbits(__dmul_rn(Sp, slot_uniform(a.seed, klocal, (uint64_t)p, sys,
+                                                                                (uint64_t)q))) : 0ull;
+        int qlo = act ? p : 0, qhi = act ? d - 1 : 0;
+        for (int it = 0; it < steps; ++it) {
+            const int mid = qlo + ((qhi - qlo + 1) >> 1);
+            const unsigned long long Mm = __shfl_sync(FULL, mx, (d - 1 - mid) & 31);
+            if (qlo < qhi) {
+                if (Mm >= Rq) qlo = mid; else qhi = mid - 1;
+            }
+        }
+        const int32_t xq = __shfl_sync(FULL, mrow, qlo & 31);
+        if (act) { lo = u < xq ? u : xq; hi = u < xq ? xq : u; }
+        if (!append_fill(a, act, lo, hi, c)) return -2;
+    }
+    ws.n_fill += (unsigned long long)(d - 1) * (unsigned long long)a.samples;
     prof_mark(a, ws, 4);
 
     // dependency levels, release, decrements
@@ -639,30 +656,33 @@ __device__ int32_t eliminate_big(const ElimArgs &a, int32_t k, int64_t o0, int32
     // ---------------------------------------------------------------- sample clique tree + append
     uint64_t klocal, sys;
     sys_of(a, k, klocal, sys);
-    for (int pb = 1; pb < d; pb += 32) {
-        const int p = pb + lane;
-        const bool act = p < d;
-        int32_t lo = 0, hi = 0;
-        double c = 0.0;
-        if (act) {
-            const int32_t u = v.row[p - 1];
-            const double wu = v.w[p - 1];
-            const double Sp = v.S[p];
-            const double R = __dmul_rn(Sp, slot_uniform(a.seed, klocal, (uint64_t)p, sys));
-            const unsigned long long Rb = dbits(R);
-            int lo_j = p, hi_j = d - 1;            // largest j with M[j] >= R; M[p] >= R
-            while (lo_j < hi_j) {
-                const int mid = lo_j + ((hi_j - lo_j + 1) >> 1);
-                if (dbits(v.M[mid]) >= Rb) lo_j = mid; else hi_j = mid - 1;
+    for (int q = 0; q < a.samples; ++q) {                // sample q of every slot (q > 0: AC(k))
+        for (int pb = 1; pb < d; pb += 32) {
+            const int p = pb + lane;
+            const bool act = p < d;
+            int32_t lo = 0, hi = 0;
+            double c = 0.0;
+            if (act) {
+                const int32_t u = v.row[p - 1];
+                const double wu = v.w[p - 1];
+                const double Sp = v.S[p];
+                const double R = __dmul_rn(Sp, slot_uniform(a.seed, klocal, (uint64_t)p, sys, (uint64_t)q));
+                const unsigned long long Rb = dbits(R);
+                int lo_j = p, hi_j = d - 1;            // largest j with M[j] >= R; M[p] >= R
+                while (lo_j < hi_j) {
+                    const int mid = lo_j + ((hi_j - lo_j + 1) >> 1);
+                    if (dbits(v.M[mid]) >= Rb) lo_j = mid; else hi_j = mid - 1;
+                }
+                const int32_t x = v.row[lo_j];
+                c = __ddiv_rn(__dmul_rn(Sp, wu), Dk);
+                if (a.samples > 1) c = __ddiv_rn(c, (double)a.samples);
+                lo = u < x ? u : x;
+                hi = u < x ? x : u;
             }
-            const int32_t x = v.row[lo_j];
-            c = __ddiv_rn(__dmul_rn(Sp, wu), Dk);
-            lo = u < x ? u : x;
-            hi = u < x ? x : u;
+            if (!append_fill(a, act, lo, hi, c)) { release_block(); return -2; }
         }
-        if (!append_fill(a, act, lo, hi, c)) { release_block(); return -2; }
     }
-    ws.n_fill += (unsigned long long)(d - 1);
+    ws.n_fill += (unsigned long long)(d - 1) * (unsigned long long)a.samples;
     prof_mark(a, ws, 4);
 
     // ---------------------------------------------------------------- levels, release, decrements
@@ -1341,6 +1361,7 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     uint64_t klocal, sys;
     sys_of(a, k, klocal, sys);
     bool ok = true;
+    for (int q = 0; q < a.samples && ok; ++q)             // sample q of every slot (q > 0: AC(k))
     for (int pb = 1; pb < d; pb += nt) {
         const int p = pb + tid;
         const bool act = p < d;
@@ -1350,7 +1371,8 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
             const int32_t u = v.row[p - 1];
             const double wu = v.w[p - 1];
             const double Sp = v.S[p];
-            const unsigned long long Rb = dbits(__dmul_rn(Sp, slot_uniform(a.seed, klocal, (uint64_t)p, sys)));
+            const unsigned long long Rb = dbits(__dmul_rn(Sp, slot_uniform(a.seed, klocal, (uint64_t)p, sys,
+                                                                           (uint64_t)q)));
             int lo_j = p, hi_j = d - 1;
             if (global_ws) {                       // largest coarse index c with M[c * stride] >= R
                 int clo = 0, chi = ncoarse - 1;
@@ -1368,12 +1390,13 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
             }
             const int32_t x = v.row[lo_j];
             c = __ddiv_rn(__dmul_rn(Sp, wu), Dk);
+            if (a.samples > 1) c = __ddiv_rn(c, (double)a.samples);
             lo = u < x ? u : x;
             hi = u < x ? x : u;
         }
         if (!append_fill(a, act, lo, hi, c)) { ok = false; break; }
     }
-    if (tid == 0) ws.n_fill += (unsigned long long)(d - 1);
+    if (tid == 0) ws.n_fill += (unsigned long long)(d - 1) * (unsigned long long)a.samples;
     mark(14);
 
     // ---------------------------------------------------------------- levels, release, decrements

@@ -236,3 +236,31 @@ def test_poisson_stand_ins_bit_identical(P, field):
     A, perm, seed, _ = W.config(f"poisson-{field}-24")
     _, st = _check(P, A, perm, seed)
     assert st["n"] == A.n
+
+
+def test_ac2_bit_identical(P):
+    """AC(2) (two samples per clique-tree slot) on every elimination path:
+    register and warp paths (grid, random graphs), the CTA path with shared and
+    global working sets (hub graph, R-MAT scale 15), and a grounded SDDM."""
+    cases = [W.config("grid2d-64")[:3]]
+    rng = np.random.default_rng(12)
+    for s in range(2):
+        n = int(rng.integers(500, 3000))
+        a, b = W.sparse_random_edges(n, 4 * n, s)
+        cases.append((W.laplacian_from_edges(n, a, b, rng.lognormal(0, 1, len(a))), W.random_ordering(n, s), s))
+    n = 4000
+    a = np.concatenate([np.zeros(n - 1, np.int64), rng.integers(1, n, 3 * n)])
+    b = np.concatenate([np.arange(1, n), rng.integers(1, n, 3 * n)])
+    keep = a != b
+    lo = np.minimum(a[keep], b[keep]); hi = np.maximum(a[keep], b[keep])
+    key = np.unique(lo * n + hi)
+    cases.append((W.laplacian_from_edges(n, key // n, key % n, rng.uniform(0.5, 2, len(key))),
+                  W.random_ordering(n, 9), 9))
+    cases.append(W.config("rmat-15")[:3])
+    cases.append(W.config("poisson-contrast-16")[:3])
+    for A, perm, seed in cases:
+        ref = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed, samples=2)
+        one = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)
+        got, st = _gpu_factor(P, A, perm, seed, samples=2)
+        assert same_factor(got, ref), _first_diff(got, ref)
+        assert st["samples"] == 2 and ref["fill"] > one["fill"]
