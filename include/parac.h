@@ -228,6 +228,26 @@ parac_status parac_autotune(int32_t count, const parac_system *systems, uint64_t
                             parac_opts *best, char *report, size_t cap);
 
 /*
+ * parac_pcg_many -- parac_pcg (one right-hand side each, with the matrix kept
+ * in each handle) on several factored systems, e.g. the handles of one
+ * parac_factor_many call.  Host worker threads (4) run the systems' solves
+ * concurrently, each on its handle's own stream, so the GPU overlaps the
+ * small systems' dependency chains, each worker's solves on a share of the
+ * GPU's resident blocks.  Results equal separate parac_pcg calls (the dot
+ * products are reduced over grids fixed by n alone).
+ *   count     number of systems; G[count] distinct handles
+ *   b[s], x[s]   right-hand side / solution of system s (n_s entries; host or
+ *             device memory)
+ *   tol, maxit   as for parac_pcg
+ *   iters, true_relres   [count] outputs (may be NULL)
+ * Returns PARAC_OK when every system converged; otherwise the first error of
+ * the lowest-numbered failing system (PARAC_ENOCONV only if no other error),
+ * with every system's outputs written.
+ */
+parac_status parac_pcg_many(int32_t count, const parac_factor_t *G, const double *const *b, double *const *x,
+                            double tol, int32_t maxit, int32_t *iters, double *true_relres);
+
+/*
  * parac_factor_export -- copy the factor out (label space, ground removed).
  *   nnz       receives the strict-lower entry count of F
  *   colptr    int64[n+1], rowind int32[nnz], Fval double[nnz] (rows ascending

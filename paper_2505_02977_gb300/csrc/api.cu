@@ -9,7 +9,9 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <atomic>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/parac.h"
@@ -209,7 +211,7 @@ struct GraphCache {
 // legacy default stream.
 struct SolveStream {
     cudaStream_t s = nullptr;
-    cudaEvent_t in = nullptr, out = nullptr;
+    cudaEvent_t in = nullptr, out = nullptr, h = nullptr;
     SolveStream() = default;
     SolveStream(const SolveStream &) = delete;
     SolveStream &operator=(const SolveStream &) = delete;
@@ -218,6 +220,7 @@ struct SolveStream {
         if (s) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
         if (in) cudaEventDestroy(in);
         if (out) cudaEventDestroy(out);
+        if (h) cudaEventDestroy(h);
     }
 };
 
@@ -1002,6 +1005,15 @@ void parac_factor_free(parac_factor_t G)
 // ------------------------------------------------------------------ solve
 namespace {
 
+// Set by parac_pcg_many for its worker threads: the stream the worker's
+// solves are ordered on (instead of the handle's) and the number of solves
+// that run at once, which share the resident-block capacity -- the solve
+// kernels need their whole grid resident, so concurrent solves together must
+// fit on the GPU.
+thread_local cudaStream_t t_stream_override = nullptr;
+thread_local int t_grid_share = 0;
+thread_local bool t_no_graph = false;     // one-shot solves: capturing would cost more than it saves
+
 SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, const double *Lv, int64_t nnzL)
 {
     SolveArgs A{};
@@ -1023,7 +1035,8 @@ SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, co
     int bps = 0;
     trsv_configure(A.lanes_trsv, A.trsv_warps, &bps, A.prec);
     if (bps < 1) bps = 1;
-    const int max_blocks = num_sms() * bps;      // all co-resident: required by the static schedule
+    int max_blocks = num_sms() * bps;            // all co-resident: required by the static schedule
+    if (t_grid_share > 1) max_blocks = std::max(1, max_blocks / t_grid_share);
     A.trsv_blocks = max_blocks;
     // Grid sized to the dependency frontier: about two average levels of rows
     // in flight, so that waiting rows do not flood the memory system with polls.
@@ -1140,30 +1153,37 @@ void ensure_block_groups(parac_factor_s *G, int warps, cudaStream_t st)
 }
 
 // The library's own solve stream for this handle, made to wait for the work
-// already queued on the handle's stream.
-cudaStream_t enter_solve_stream(parac_factor_s *G)
+// already queued on the calling stream st (the handle's, or a worker's of
+// parac_pcg_many) and on the handle's stream.
+cudaStream_t enter_solve_stream(parac_factor_s *G, cudaStream_t st)
 {
     SolveStream &ss = G->sstream;
     if (!ss.s) {
         CK(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&ss.in, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ss.out, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ss.h, cudaEventDisableTiming));
     }
-    CK(cudaEventRecord(ss.in, G->stream));
+    CK(cudaEventRecord(ss.in, st));
     CK(cudaStreamWaitEvent(ss.s, ss.in, 0));
+    if (st != G->stream) {                   // the cached work space was made on the handle's stream
+        CK(cudaEventRecord(ss.h, G->stream));
+        CK(cudaStreamWaitEvent(ss.s, ss.h, 0));
+    }
     return ss.s;
 }
 
-// ... and the handle's stream made to wait for the solve stream's work.
-void leave_solve_stream(parac_factor_s *G)
+// ... and the calling stream made to wait for the solve stream's work.
+void leave_solve_stream(parac_factor_s *G, cudaStream_t st)
 {
     SolveStream &ss = G->sstream;
     CK(cudaEventRecord(ss.out, ss.s));
-    CK(cudaStreamWaitEvent(G->stream, ss.out, 0));
+    CK(cudaStreamWaitEvent(st, ss.out, 0));
 }
 
 bool graphs_enabled()
 {
+    if (t_no_graph) return false;
     const char *e = getenv("PARAC_GRAPH");
     return !(e && e[0] == '0');
 }
@@ -1264,9 +1284,9 @@ parac_status pcg_block(parac_factor_s *G, SolveArgs A, int nrhs, const double *B
 {
     // the SpTRSM kernels' own co-residency bound
     const int bps = std::max(1, btrsm_blocks_per_sm(A.trsv_warps, A.prec));
-    A.trsv_blocks = std::min(A.trsv_blocks, num_sms() * bps);
-    ensure_block_cache(G, A, nrhs, st);
-    ensure_block_groups(G, A.trsv_warps, st);
+    A.trsv_blocks = std::min(A.trsv_blocks, std::max(1, num_sms() * bps / std::max(1, t_grid_share)));
+    ensure_block_cache(G, A, nrhs, G->stream);
+    ensure_block_groups(G, A.trsv_warps, G->stream);
     const BlockBuffers &B = G->bcache.B;
     CK(bpack((int32_t)A.n, nrhs, Bcm, ldb, B.b, ps));
     CK(bpcg_init(A, B, tol, maxit, ps));
@@ -1317,7 +1337,7 @@ extern "C" parac_status parac_pcg(parac_factor_t G, int64_t n, const int64_t *co
             set_err("bad arguments to parac_pcg");
             return PARAC_EINVAL;
         }
-        cudaStream_t st = G->stream;
+        cudaStream_t st = t_stream_override ? t_stream_override : G->stream;
         DView<int64_t> cp; DView<int32_t> ri; DView<double> va;
         const int64_t *Lp = G->Lp.as<int64_t>();
         const int32_t *Li = G->Li.as<int32_t>();
@@ -1359,25 +1379,25 @@ extern "C" parac_status parac_pcg(parac_factor_t G, int64_t n, const int64_t *co
         bool all_conv = true;
         parac_status rs = PARAC_OK;
         if (nrhs == 1) {
-            ensure_cache(G, A, st);
-            cudaStream_t ps = enter_solve_stream(G);
+            ensure_cache(G, A, G->stream);        // cached work space lives on the handle's stream
+            cudaStream_t ps = enter_solve_stream(G, st);
             bool conv = true;
             rs = pcg_single(G, A, Bd, Xd, tol, maxit, ps, &it[0], &rel[0], &conv);
             all_conv = conv;
-            leave_solve_stream(G);
+            leave_solve_stream(G, st);
         } else {
             cudaStream_t ps = nullptr;
             {
                 // buffers are allocated on the handle's stream before the join
                 const int bps = std::max(1, btrsm_blocks_per_sm(A.trsv_warps, A.prec));
                 SolveArgs Ab = A;
-                Ab.trsv_blocks = std::min(A.trsv_blocks, num_sms() * bps);
-                ensure_block_cache(G, Ab, nrhs, st);
-                ensure_block_groups(G, A.trsv_warps, st);
+                Ab.trsv_blocks = std::min(A.trsv_blocks, std::max(1, num_sms() * bps / std::max(1, t_grid_share)));
+                ensure_block_cache(G, Ab, nrhs, G->stream);
+                ensure_block_groups(G, A.trsv_warps, G->stream);
             }
-            ps = enter_solve_stream(G);
+            ps = enter_solve_stream(G, st);
             rs = pcg_block(G, A, nrhs, Bd, ldbd, Xd, ldxd, tol, maxit, st, ps, it.data(), rel.data(), &all_conv);
-            leave_solve_stream(G);
+            leave_solve_stream(G, st);
         }
         if (rs == PARAC_ETIMEOUT) {
             CK(cudaStreamSynchronize(st));
@@ -1394,6 +1414,79 @@ extern "C" parac_status parac_pcg(parac_factor_t G, int64_t n, const int64_t *co
         }
         if (!all_conv) { set_err("PCG reached maxit"); return PARAC_ENOCONV; }
         return PARAC_OK;
+    });
+}
+
+// PCG on several systems at once: worker threads each take the next system
+// and run parac_pcg on it; every handle solves on its own library stream, so
+// the GPU runs the systems' kernels side by side.
+extern "C" parac_status parac_pcg_many(int32_t count, const parac_factor_t *G, const double *const *b,
+                                       double *const *x, double tol, int32_t maxit, int32_t *iters,
+                                       double *true_relres)
+{
+    return guarded([&]() -> parac_status {
+        if (count < 0 || (count > 0 && (!G || !b || !x))) { set_err("bad arguments to parac_pcg_many"); return PARAC_EINVAL; }
+        for (int32_t i = 0; i < count; ++i)
+            for (int32_t j = 0; j < i && j < 64; ++j)
+                if (G[i] == G[j]) { set_err("parac_pcg_many: handle %d repeats handle %d", i, j); return PARAC_EINVAL; }
+        std::vector<parac_status> st((size_t)count, PARAC_OK);
+        std::vector<std::string> msg((size_t)count);
+        std::vector<int32_t> it((size_t)count, 0);
+        std::vector<double> rr((size_t)count, 0.0);
+        std::atomic<int32_t> next{0};
+        int workers = 4;           // measured best on 200 SDDM systems (1: 1.65 s, 4: 0.89 s, 16: 1.72 s)
+        if (const char *e = getenv("PARAC_PCG_WORKERS")) workers = std::max(1, std::min(64, atoi(e)));
+        const int nth = (int)std::min<int32_t>(count, workers);
+        auto worker = [&]() {
+            // each worker orders its systems on its own stream and gets 1/nth
+            // of the resident-block capacity for its solves
+            cudaStream_t ws = nullptr;
+            int wdev = -1;
+            t_grid_share = nth;
+            t_no_graph = true;
+            for (;;) {
+                const int32_t i = next.fetch_add(1);
+                if (i >= count) break;
+                if (!G[i]) { st[(size_t)i] = PARAC_EINVAL; msg[(size_t)i] = "null handle"; continue; }
+                cudaSetDevice(G[i]->device);
+                if (wdev != G[i]->device) {
+                    if (ws) { cudaStreamSynchronize(ws); cudaStreamDestroy(ws); }
+                    ws = nullptr;
+                    if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); ws = nullptr; }
+                    wdev = G[i]->device;
+                    // start after the work already queued on the handles' stream
+                    cudaEvent_t e0 = nullptr;
+                    if (ws && cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) == cudaSuccess) {
+                        cudaEventRecord(e0, G[i]->stream);
+                        cudaStreamWaitEvent(ws, e0, 0);
+                        cudaEventDestroy(e0);
+                    }
+                }
+                t_stream_override = ws;
+                st[(size_t)i] = parac_pcg(G[i], G[i]->n, nullptr, nullptr, nullptr, b[i], 1, G[i]->n, tol, maxit, x[i],
+                                          G[i]->n, &it[(size_t)i], &rr[(size_t)i]);
+                if (st[(size_t)i] != PARAC_OK) msg[(size_t)i] = parac_last_error();
+            }
+            t_stream_override = nullptr;
+            t_grid_share = 0;
+            t_no_graph = false;
+            if (ws) { cudaStreamSynchronize(ws); cudaStreamDestroy(ws); }
+        };
+        std::vector<std::thread> th;
+        for (int t = 1; t < nth; ++t) th.emplace_back(worker);
+        if (nth > 0) worker();
+        for (auto &t : th) t.join();
+        parac_status out = PARAC_OK;
+        int32_t first = -1;
+        for (int32_t i = 0; i < count; ++i) {
+            if (iters) iters[i] = it[(size_t)i];
+            if (true_relres) true_relres[i] = rr[(size_t)i];
+            // errors before non-convergence, the first system's first
+            const parac_status s2 = st[(size_t)i];
+            if (s2 != PARAC_OK && (out == PARAC_OK || (out == PARAC_ENOCONV && s2 != PARAC_ENOCONV))) { out = s2; first = i; }
+        }
+        if (first >= 0) set_err("system %d: %s", first, msg[(size_t)first].c_str());
+        return out;
     });
 }
 

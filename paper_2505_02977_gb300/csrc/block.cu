@@ -160,6 +160,20 @@ __global__ void k_bupdate_xr(int32_t n, int nrhs, double *X, double *R, const do
     block_colsum(acc, partial_rr);
 }
 
+// per-column partials of r . z (warp per row, lane = column) over a grid that
+// depends only on n, so the rounding does not depend on the solves' launch shape
+__global__ void k_bdot(int32_t n, int nrhs, const double *R, const double *Z, double *partial, const BlockState *st)
+{
+    if (st && st->all_done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double acc = 0.0;
+    if (lane < nrhs)
+        for (int64_t i = w0; i < n; i += nw) acc += R[i * nrhs + lane] * Z[i * nrhs + lane];
+    block_colsum(acc, partial);
+}
+
 __global__ void k_bupdate_p(int32_t n, int nrhs, double *P, const double *Z, const BlockState *st)
 {
     if (st->all_done) return;
@@ -621,8 +635,9 @@ cudaError_t bapply_t(const SolveArgs &A, const BlockBuffers &B, const VT *vr, co
     k_btrsm_fwd<VT, XT><<<gf, threads, 0, s>>>(A.n, B.nrhs, A.Frp, A.Fcol, vr, A.operm, r, y, z, B.gt_f, B.ng_f,
                                                (XT *)B.part_f, st, A.spin_limit, A.status);
     count_launches(1);
-    k_btrsm_bwd<VT, XT><<<gb, threads, 0, s>>>(A.n, B.nrhs, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z, zout, r,
-                                               partial, B.gt_b, B.ng_b, (XT *)B.part_b, st, A.spin_limit, A.status);
+    k_btrsm_bwd<VT, XT><<<gb, threads, 0, s>>>(A.n, B.nrhs, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z, zout,
+                                               partial ? r : nullptr, partial, B.gt_b, B.ng_b, (XT *)B.part_b, st,
+                                               A.spin_limit, A.status);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -665,9 +680,11 @@ cudaError_t bpcg_init(const SolveArgs &A, const BlockBuffers &B, double tol, int
     count_launches(1);
     cudaError_t e = bfill(A, B, s);
     if (e != cudaSuccess) return e;
-    e = bapply(A, B, B.r, B.z, p_rz, nullptr, s);
+    e = bapply(A, B, B.r, B.z, nullptr, nullptr, s);
     if (e != cudaSuccess) return e;
-    k_binit_scalars<<<1, ST, 0, s>>>(B.state, B.nrhs, p_bb, nb, p_rz, A.trsv_blocks, tol, maxit);
+    k_bdot<<<nb, BT, 0, s>>>(A.n, B.nrhs, B.r, B.z, p_rz, nullptr);
+    count_launches(1);
+    k_binit_scalars<<<1, ST, 0, s>>>(B.state, B.nrhs, p_bb, nb, p_rz, nb, tol, maxit);
     k_bcopy<<<grid_for((int64_t)A.n * B.nrhs, 4096), BT, 0, s>>>((int64_t)A.n * B.nrhs, B.z, B.p);
     count_launches(2);
     return cudaGetLastError();
@@ -683,9 +700,11 @@ cudaError_t bpcg_iteration(const SolveArgs &A, const BlockBuffers &B, cudaStream
     k_bupdate_xr<<<nb, BT, 0, s>>>(A.n, B.nrhs, B.x, B.r, B.p, B.q, p_rr, B.state);
     k_bcheck<<<1, ST, 0, s>>>(B.state, p_rr, nb);
     count_launches(4);
-    cudaError_t e = bapply(A, B, B.r, B.z, p_rz, B.state, s);
+    cudaError_t e = bapply(A, B, B.r, B.z, nullptr, B.state, s);
     if (e != cudaSuccess) return e;
-    k_bbeta<<<1, ST, 0, s>>>(B.state, p_rz, A.trsv_blocks);
+    k_bdot<<<nb, BT, 0, s>>>(A.n, B.nrhs, B.r, B.z, p_rz, B.state);
+    count_launches(1);
+    k_bbeta<<<1, ST, 0, s>>>(B.state, p_rz, nb);
     k_bupdate_p<<<nb, BT, 0, s>>>(A.n, B.nrhs, B.p, B.z, B.state);
     count_launches(2);
     return cudaGetLastError();
@@ -705,12 +724,15 @@ cudaError_t bpcg_true_residual(const SolveArgs &A, const BlockBuffers &B, cudaSt
 // precondition their residual and update their search direction.
 cudaError_t bpcg_reopen(const SolveArgs &A, const BlockBuffers &B, cudaStream_t s)
 {
+    const int nb = B.vec_blocks;
     k_breopen<<<1, 32, 0, s>>>(B.state);
     count_launches(1);
     double *p_rz = B.partials + 64 * (size_t)B.pstride;
-    cudaError_t e = bapply(A, B, B.r, B.z, p_rz, B.state, s);
+    cudaError_t e = bapply(A, B, B.r, B.z, nullptr, B.state, s);
     if (e != cudaSuccess) return e;
-    k_bbeta<<<1, ST, 0, s>>>(B.state, p_rz, A.trsv_blocks);
+    k_bdot<<<nb, BT, 0, s>>>(A.n, B.nrhs, B.r, B.z, p_rz, B.state);
+    count_launches(1);
+    k_bbeta<<<1, ST, 0, s>>>(B.state, p_rz, nb);
     k_bupdate_p<<<B.vec_blocks, BT, 0, s>>>(A.n, B.nrhs, B.p, B.z, B.state);
     count_launches(2);
     return cudaGetLastError();

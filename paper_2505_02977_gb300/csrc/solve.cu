@@ -210,6 +210,18 @@ __global__ void k_fill_sentinel(int32_t n, T *a, T *b)
     }
 }
 
+// block partials of r . z over a grid that depends only on n (vec_blocks), so
+// the dot product's rounding does not depend on the solves' launch shape
+__global__ void k_dot(int32_t n, const double *a, const double *b, double *partial, const PcgState *st)
+{
+    if (st && st->done) return;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += a[i] * b[i];
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
 __global__ void k_resid_sq(int32_t n, const double *b, const double *Lx, double *partial)
 {
     double acc = 0.0;
@@ -672,7 +684,7 @@ cudaError_t apply_t(const SolveArgs &A, const VT *vr, const VT *vc, XT *y, XT *z
                                                              (XT *)A.part_f, st, A.spin_limit, A.status);
     count_launches(1);
     k_trsv_bwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z,
-                                                             zout, r, partial, gb, A.ng_b, (XT *)A.part_b, st,
+                                                             zout, partial ? r : nullptr, partial, gb, A.ng_b, (XT *)A.part_b, st,
                                                              A.spin_limit, A.status);
     count_launches(1);
     return cudaGetLastError();
@@ -718,7 +730,18 @@ size_t pcg_state_bytes() { return sizeof(PcgState); }
 
 cudaError_t set_poll_backoff(unsigned max_ns)
 {
-    return cudaMemcpyToSymbol(g_poll_max_ns, &max_ns, sizeof max_ns);
+    // written only when it changes, per device (the copy is synchronous and
+    // would otherwise serialise concurrent solves)
+    static std::mutex mu;
+    static unsigned last[NOALLOC_MAX_DEVICES] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < NOALLOC_MAX_DEVICES && last[dev] == max_ns) return cudaSuccess;
+    e = cudaMemcpyToSymbol(g_poll_max_ns, &max_ns, sizeof max_ns);
+    if (e == cudaSuccess && dev >= 0 && dev < NOALLOC_MAX_DEVICES) last[dev] = max_ns;
+    return e;
 }
 
 int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec)
@@ -817,9 +840,10 @@ cudaError_t pcg_init(const SolveArgs &A, const PcgBuffers &B, double tol, int32_
     k_init_vectors<<<nb, VEC_THREADS, 0, s>>>(A.n, B.b, B.x, B.r, p_bb); count_launches(1);
     cudaError_t e = fill_sentinels(A, B, s);
     if (e != cudaSuccess) return e;
-    e = apply(A, B, B.r, B.z, p_rz, nullptr, s);
+    e = apply(A, B, B.r, B.z, nullptr, nullptr, s);
     if (e != cudaSuccess) return e;
-    k_init_scalars<<<1, 256, 0, s>>>(B.state, p_bb, nb, p_rz, A.trsv_blocks, tol, maxit); count_launches(1);
+    k_dot<<<nb, VEC_THREADS, 0, s>>>(A.n, B.r, B.z, p_rz, nullptr); count_launches(1);
+    k_init_scalars<<<1, 256, 0, s>>>(B.state, p_bb, nb, p_rz, nb, tol, maxit); count_launches(1);
     k_copy<<<nb, VEC_THREADS, 0, s>>>(A.n, B.z, B.p); count_launches(1);
     return cudaGetLastError();
 }
@@ -833,9 +857,10 @@ cudaError_t pcg_iteration(const SolveArgs &A, const PcgBuffers &B, cudaStream_t 
     k_alpha<<<1, 256, 0, s>>>(B.state, p_pq, nb); count_launches(1);
     k_update_xr<<<nb, VEC_THREADS, 0, s>>>(A.n, B.x, B.r, B.p, B.q, p_rr, B.state); count_launches(1);
     k_check<<<1, 256, 0, s>>>(B.state, p_rr, nb); count_launches(1);
-    e = apply(A, B, B.r, B.z, p_rz, B.state, s);
+    e = apply(A, B, B.r, B.z, nullptr, B.state, s);
     if (e != cudaSuccess) return e;
-    k_beta<<<1, 256, 0, s>>>(B.state, p_rz, A.trsv_blocks); count_launches(1);
+    k_dot<<<nb, VEC_THREADS, 0, s>>>(A.n, B.r, B.z, p_rz, B.state); count_launches(1);
+    k_beta<<<1, 256, 0, s>>>(B.state, p_rz, nb); count_launches(1);
     k_update_p<<<nb, VEC_THREADS, 0, s>>>(A.n, B.p, B.z, B.state); count_launches(1);
     return cudaGetLastError();
 }
@@ -854,9 +879,10 @@ cudaError_t pcg_resume(const SolveArgs &A, const PcgBuffers &B, cudaStream_t s)
 {
     const int nb = B.vec_blocks;
     double *p_rz = B.partials + 2 * B.pstride;
-    cudaError_t e = apply(A, B, B.r, B.z, p_rz, B.state, s);
+    cudaError_t e = apply(A, B, B.r, B.z, nullptr, B.state, s);
     if (e != cudaSuccess) return e;
-    k_beta<<<1, 256, 0, s>>>(B.state, p_rz, A.trsv_blocks); count_launches(1);
+    k_dot<<<nb, VEC_THREADS, 0, s>>>(A.n, B.r, B.z, p_rz, B.state); count_launches(1);
+    k_beta<<<1, 256, 0, s>>>(B.state, p_rz, nb); count_launches(1);
     k_update_p<<<nb, VEC_THREADS, 0, s>>>(A.n, B.p, B.z, B.state); count_launches(1);
     return cudaGetLastError();
 }

@@ -64,12 +64,16 @@ _lib.parac_last_error.restype = C.c_char_p
 _lib.parac_autotune.argtypes = [C.c_int32, C.POINTER(parac_system), C.c_uint64, C.POINTER(parac_opts),
                                 C.POINTER(parac_opts), C.c_char_p, C.c_size_t]
 _lib.parac_autotune.restype = C.c_int
+_lib.parac_pcg_many.argtypes = [C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                C.c_double, C.c_int32, C.c_void_p, C.c_void_p]
+_lib.parac_pcg_many.restype = C.c_int
 _lib.parac_kernel_launches.argtypes = []
 _lib.parac_kernel_launches.restype = C.c_uint64
 
 EXPORTED = ("parac_opts_default", "parac_factor", "parac_pcg", "parac_factor_many", "parac_factor_export",
             "parac_factor_stats", "parac_factor_free", "parac_precond_apply", "parac_status_string",
-            "parac_last_error", "parac_kernel_launches", "parac_precond_apply_noalloc", "parac_autotune")
+            "parac_last_error", "parac_kernel_launches", "parac_precond_apply_noalloc", "parac_autotune",
+            "parac_pcg_many")
 
 
 class ParacError(RuntimeError):
@@ -230,6 +234,33 @@ def parac_pcg(G, n, colptr, rowind, val, B, tol=1e-8, maxit=1000, X=None, nrhs=N
     code = _lib.parac_pcg(G.handle, n, *ps, pb, nrhs, ldb, tol, maxit, px, ldx, iters.ctypes.data, rel.ctypes.data)
     _check(code, "parac_pcg", allow=(7,) if allow_noconv else ())
     return Xout, iters, rel, STATUS[code]
+
+
+def parac_pcg_many(Gs, bs, tol=1e-8, maxit=1000, xs=None, allow_noconv=True):
+    """PCG on several systems at once (one right-hand side each).  bs: list of
+    n_s-vectors (numpy or torch CUDA); returns (xs, iters, relres, status)."""
+    m = len(Gs)
+    keep = []
+    if xs is None:
+        xs = []
+        for b in bs:
+            if hasattr(b, "data_ptr"):
+                import torch
+                xs.append(torch.empty_like(b))
+            else:
+                xs.append(np.zeros(len(b)))
+    bp = (C.c_void_p * m)(); xp = (C.c_void_p * m)(); hp = (C.c_void_p * m)()
+    for i, (G, b, x) in enumerate(zip(Gs, bs, xs)):
+        if hasattr(b, "data_ptr"):
+            bp[i] = b.data_ptr(); keep.append(b)
+        else:
+            bb = np.ascontiguousarray(b, np.float64); keep.append(bb); bp[i] = bb.ctypes.data
+        xp[i] = x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+        hp[i] = G.handle.value
+    iters = np.zeros(m, np.int32); rel = np.zeros(m)
+    code = _lib.parac_pcg_many(m, hp, bp, xp, tol, maxit, iters.ctypes.data, rel.ctypes.data)
+    _check(code, "parac_pcg_many", allow=(7,) if allow_noconv else ())
+    return xs, iters, rel, STATUS[code]
 
 
 def parac_precond_apply(G, r, z=None):

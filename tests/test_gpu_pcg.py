@@ -287,3 +287,23 @@ def test_split_rows(P):
         assert abs(int(itj[0]) - int(it[j])) <= 1
         assert np.linalg.norm((xj - xj.mean()) - (X[:, j] - X[:, j].mean())) <= 1e-6 * np.linalg.norm(xj)
     G.free()
+
+
+def test_pcg_many_matches_single_calls(P):
+    """parac_pcg_many on the handles of one parac_factor_many call: every
+    system's result is bit-identical to its own parac_pcg call (host and
+    device right-hand sides)."""
+    import torch
+    batch = W.sddm_batch(12, nmin=500, nmax=20000, seed=13)
+    systems = [(A.n, A.colptr, A.rowind, A.val, perm) for (A, perm, b) in batch]
+    Gs = P.parac_factor_many(systems, seed=3)
+    bs = [b for (A, perm, b) in batch]
+    xs, its, rrs, status = P.parac_pcg_many(Gs, bs, tol=1e-8, maxit=500)
+    assert status == "PARAC_OK" and np.all(rrs <= 1e-8)
+    xd, itd, rrd, _ = P.parac_pcg_many(Gs, [torch.from_numpy(b).cuda() for b in bs], tol=1e-8, maxit=500)
+    for i, ((A, perm, b), G) in enumerate(zip(batch, Gs)):
+        x1, it1, rr1, _ = P.parac_pcg(G, A.n, None, None, None, b, tol=1e-8, maxit=500)
+        assert it1[0] == its[i] == itd[i] and rr1[0] == rrs[i]
+        assert np.array_equal(x1, xs[i]) and np.array_equal(x1, xd[i].cpu().numpy())
+    for G in Gs:
+        G.free()
