@@ -73,7 +73,9 @@ enum { PARAC_SPTRSV_AUTO = 0, PARAC_SPTRSV_WARP = 1, PARAC_SPTRSV_SUB8 = 2, PARA
  *                   FP32 and the triangular solves run in FP32, while PCG's
  *                   SpMV, residual update and dot products stay FP64.
  *   pool_mult       Initial fill-workspace capacity, in units of the strict
- *                   lower input entries (Sec. IV-A uses 4-6).
+ *                   lower input entries (default 10: grids use ~3.5, R-MAT
+ *                   graphs ~8 with the overflow slabs' rounding; an overflow
+ *                   reruns the whole elimination with a larger workspace).
  *   max_pool_regrow Reruns with a 2x larger workspace after an overflow (the
  *                   rerun gives the same factor).
  *   spin_limit      Polls any device wait may take before PARAC_ETIMEOUT
@@ -92,6 +94,12 @@ enum { PARAC_SPTRSV_AUTO = 0, PARAC_SPTRSV_WARP = 1, PARAC_SPTRSV_SUB8 = 2, PARA
  *                   is AC(k) (Sec. VI): slot p draws k neighbours, sample q
  *                   with Philox counter (k_label, p, sys, q), each edge weighted
  *                   c_p / k -- a denser factor for possibly fewer iterations.
+ *   fill_store      Where fill waits for its column's pivot: 0 = per-column
+ *                   slabs (inline 16 entries, then geometrically growing
+ *                   overflow slabs); 1 = the hashmap W of Sec. IV-C (open
+ *                   addressing, insert from hash(col) + fill_count(col) to
+ *                   the right, gathered by parallel scans).  The factor is the
+ *                   same either way.
  */
 typedef struct {
     int32_t kind;
@@ -108,6 +116,7 @@ typedef struct {
     int32_t timing;
     void *stream;
     int32_t samples;
+    int32_t fill_store;
 } parac_opts;
 
 void parac_opts_default(parac_opts *opts);

@@ -264,7 +264,7 @@ Opts read_opts(const parac_opts *in)
     Opts r;
     parac_opts_default(&r.o);
     if (in) r.o = *in;
-    if (r.o.pool_mult <= 0) r.o.pool_mult = 4.0;
+    if (r.o.pool_mult <= 0) r.o.pool_mult = 10.0;
     if (r.o.max_pool_regrow < 0) r.o.max_pool_regrow = 0;
     if (r.o.spin_limit <= 0) r.o.spin_limit = 1ll << 24;
     if (r.o.warps_per_block <= 0) r.o.warps_per_block = 8;
@@ -273,6 +273,7 @@ Opts read_opts(const parac_opts *in)
     if (r.o.check_every <= 0) r.o.check_every = 8;
     if (r.o.g_precision != 32) r.o.g_precision = 64;
     if (r.o.samples <= 0) r.o.samples = 1;
+    if (r.o.fill_store != 1) r.o.fill_store = 0;
     r.st = (cudaStream_t)r.o.stream;
     return r;
 }
@@ -292,7 +293,7 @@ struct FactorOut {
     unsigned long long stats[32] = {0};
     unsigned long long pool_used = 0, f_used = 0, scratch_used = 0;
     int32_t max_lower_column = 0;
-    int32_t samples = 1;
+    int32_t samples = 1, fill_store = 0;
     int regrows = 0;
     double t_ingest = 0, t_elim = 0, t_compact = 0;
     int blocks = 0, warps = 0;
@@ -482,7 +483,7 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         scratch_cap = std::max(scratch_cap, std::min<unsigned long long>(want, freeb / 4));
         out.max_lower_column = maxlow;
     }
-    DBuf pool_row, pool_w, f_row, f_val, scratch;
+    DBuf pool_row, pool_w, f_row, f_val, scratch, w_col, w_row, w_w;
     for (int attempt = 0;; ++attempt) {
         // AC(k): k fill edges per slot, and the neighbour lists of later pivots
         // grow with them -- AC(2) on 3D grids has 10-30x the fill of Alg. 2
@@ -490,7 +491,15 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         const unsigned long long pool_cap = (unsigned long long)std::ceil(mult * ks * (double)nnz_low) + 4096ull;
         const unsigned long long f_cap = (unsigned long long)std::ceil(std::max(mult, 4.0) * ks * (double)nnz_low) +
                                          (unsigned long long)nl + (unsigned long long)total_warps * fchunk + 4096ull;
-        pool_row = dalloc<int32_t>(pool_cap, st); pool_w = dalloc<double>(pool_cap, st);
+        const unsigned long long wcap = 2ull * pool_cap;     // load factor about 1/2 of the slab estimate
+        if (O.o.fill_store == 1) {                // hashmap W (Sec. IV-C)
+            pool_row = dalloc<int32_t>(1, st); pool_w = dalloc<double>(1, st);
+            w_col = dalloc<int32_t>(wcap, st); w_row = dalloc<int32_t>(wcap, st);
+            w_w = dalloc<double>(wcap, st);
+            CK(cudaMemsetAsync(w_col.p, 0xff, 4 * (size_t)wcap, st));      // every slot free (-1)
+        } else {
+            pool_row = dalloc<int32_t>(pool_cap, st); pool_w = dalloc<double>(pool_cap, st);
+        }
         f_row = dalloc<int32_t>(f_cap, st); f_val = dalloc<double>(f_cap, st);
         scratch.alloc(scratch_cap, st);
         CK(cudaMemcpyAsync(dp.p, dp0.p, 4 * nl, cudaMemcpyDeviceToDevice, st));
@@ -531,7 +540,11 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         a.coop = 1;
         if (const char *e = getenv("PARAC_COOP")) a.coop = atoi(e) != 0;
         a.samples = O.o.samples;
+        a.hash_store = O.o.fill_store == 1 ? 1 : 0;
+        a.wcol = w_col.as<int32_t>(); a.wrow = w_row.as<int32_t>(); a.ww = w_w.as<double>();
+        a.wcap = O.o.fill_store == 1 ? wcap : 0;
         out.samples = O.o.samples;
+        out.fill_store = O.o.fill_store;
         a.sample_sort = 1;
         if (const char *e = getenv("PARAC_SAMPLE_SORT")) a.sample_sort = atoi(e) != 0;
         if (const char *e = getenv("PARAC_IDLE_NS")) a.idle_ns = std::max(32, std::min(1000000, atoi(e)));
@@ -559,7 +572,7 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
             set_err("device wait exceeded spin_limit");
         throw StatusFail{map_status(hst)};
     }
-    scratch.release(); pool_row.release(); pool_w.release();
+    scratch.release(); pool_row.release(); pool_w.release(); w_col.release(); w_row.release(); w_w.release();
     out.t_elim = t_el.stop();
     if (trace_path) {
         std::vector<long long> tr((size_t)nl * 4);
@@ -711,7 +724,7 @@ std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_ind
              "\"scratch_bytes_used\": %llu, \"vertices_warp_path\": %llu, \"vertices_block_path\": %llu, "
              "\"vertices_global_path\": %llu, \"vertices_register_path\": %llu, \"handoffs\": %llu, "
              "\"queue_spins\": %llu, \"regrows\": %d, \"max_lower_column\": %d, \"blocks\": %d, "
-             "\"warps_per_block\": %d, \"precision\": %d, \"samples\": %d, \"system\": %d, \"t_ingest_ms\": %.4f, "
+             "\"warps_per_block\": %d, \"precision\": %d, \"samples\": %d, \"fill_store\": %d, \"system\": %d, \"t_ingest_ms\": %.4f, "
              "\"t_elim_ms\": %.4f, \"t_compact_ms\": %.4f, \"depth\": %d, \"cycles\": {\"wait\": %llu, "
              "\"gather\": %llu, \"sort_merge\": %llu, \"store_sort_scan\": %llu, \"sample_append\": %llu, "
              "\"release\": %llu, \"reg_weight_sort\": %llu, \"reg_scan\": %llu, \"coop_join\": %llu, "
@@ -720,7 +733,7 @@ std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_ind
              "\"coop_release\": %llu}}",
              (long long)h->n, (long long)h->nnzF, (long long)(h->nnzF + h->n), (long long)fo.nl,
              (long long)fo.nnz_low, fo.stats[3], fo.pool_used, fo.f_used, fo.scratch_used, fo.stats[0], fo.stats[1],
-             fo.stats[2], fo.stats[5], fo.stats[6], fo.stats[4], fo.regrows, fo.max_lower_column, fo.blocks, fo.warps, h->prec, fo.samples, sys_index, fo.t_ingest, fo.t_elim,
+             fo.stats[2], fo.stats[5], fo.stats[6], fo.stats[4], fo.regrows, fo.max_lower_column, fo.blocks, fo.warps, h->prec, fo.samples, fo.fill_store, sys_index, fo.t_ingest, fo.t_elim,
              fo.t_compact, h->depth, fo.stats[8], fo.stats[9], fo.stats[10], fo.stats[11], fo.stats[12],
              fo.stats[13], fo.stats[14], fo.stats[15], fo.stats[16], fo.stats[17], fo.stats[18], fo.stats[19],
              fo.stats[20], fo.stats[21], fo.stats[22], fo.stats[23]);
@@ -768,7 +781,7 @@ void parac_opts_default(parac_opts *o)
     std::memset(o, 0, sizeof *o);
     o->kind = PARAC_KIND_AUTO;
     o->g_precision = 64;
-    o->pool_mult = 4.0;
+    o->pool_mult = 10.0;
     o->max_pool_regrow = 2;
     o->spin_limit = 1ll << 24;
     o->warps_per_block = 8;

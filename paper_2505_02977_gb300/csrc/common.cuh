@@ -63,6 +63,11 @@ __device__ __forceinline__ void st_relaxed_f64(double *p, double v)
     asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_relaxed_i32(int32_t *p, int32_t v)
+{
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ float ld_relaxed_f32(const float *p)
 {
     float v;
@@ -130,6 +135,21 @@ __device__ __forceinline__ double slot_uniform(uint64_t seed, uint64_t k, uint64
 {
     const U64x4 o = philox4x64_10(k, p, sys, q, seed, 0ull);
     return (double)((o.v[0] >> 11) + 1ull) * 0x1.0p-53;
+}
+
+// ---------------------------------------------------------------- hashmap fill store
+// Base slot of column c in W: a fixed bijective mix of the label (a
+// pseudo-random permutation of 32-bit labels, independent of the elimination
+// order) scaled to the table.
+constexpr int32_t W_FREE = -1, W_BUSY = -2;
+
+__host__ __device__ __forceinline__ unsigned long long w_base(int32_t c, unsigned long long wcap)
+{
+    uint32_t x = (uint32_t)c;
+    x ^= x >> 16; x *= 0x7feb352du;
+    x ^= x >> 15; x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return ((unsigned long long)x * wcap) >> 32;
 }
 
 // ---------------------------------------------------------------- fill store geometry
@@ -208,6 +228,12 @@ struct ElimArgs {
     int32_t *trace_phase;          // optional: cycles of the cooperative path's 8 phases [nl * 8]
     int32_t sample_sort;           // cooperative path: sample sort for working sets in global memory
     int32_t samples;               // samples per clique-tree slot (AC(k)); 1: Alg. 2
+    // hashmap fill store (Sec. IV-C): slot state / column tag, entry row and weight
+    int32_t hash_store;            // 1: fill goes to the hashmap W instead of slabs
+    int32_t *wcol;                 // [wcap] -1 free, -2 busy, else the column the entry belongs to
+    int32_t *wrow;
+    double *ww;
+    unsigned long long wcap;
 };
 
 // Bytes of shared/scratch memory per entry of the per-vertex working set:

@@ -219,8 +219,35 @@ __device__ __forceinline__ bool reserve_factor(const ElimArgs &a, WarpState &ws,
 // that takes the first index of an overflow level allocates that level's slab
 // and publishes it; the other lanes of the level wait for it.  Warp-uniform
 // result; false means the kernel must stop.
+constexpr unsigned long long W_MAX_PROBE = 1ull << 16;   // probes before an insert counts as overflow
+
 __device__ bool append_fill(const ElimArgs &a, bool act, int32_t lo, int32_t hi, double c)
 {
+    if (a.hash_store) {
+        // hashmap W (Sec. IV-C): probe right from base(lo) + fill_count(lo) for a
+        // free slot, claim it (free -> busy), write the entry, publish the tag
+        bool ok = true;
+        if (act) {
+            const uint32_t idx = atomicAdd(a.fcnt + lo, 1u);
+            unsigned long long i = (w_base(lo, a.wcap) + idx) % a.wcap;
+            const unsigned long long lim = a.wcap < W_MAX_PROBE ? a.wcap : W_MAX_PROBE;
+            bool placed = false;
+            for (unsigned long long step = 0; step < lim; ++step) {
+                if (*(volatile const int32_t *)(a.wcol + i) == W_FREE && atomicCAS(a.wcol + i, W_FREE, W_BUSY) == W_FREE) {
+                    a.wrow[i] = hi;
+                    a.ww[i] = c;
+                    __threadfence();
+                    st_release(a.wcol + i, lo);
+                    placed = true;
+                    break;
+                }
+                if (++i == a.wcap) i = 0;
+            }
+            if (!placed) { set_status(a.status, ST_POOL); ok = false; }
+            red_add_relaxed(a.dp + hi, 1);
+        }
+        return !__any_sync(FULL, !ok);
+    }
     uint32_t idx = 0;
     if (act) {
         idx = atomicAdd(a.fcnt + lo, 1u);
@@ -308,6 +335,33 @@ __device__ __forceinline__ void sys_of(const ElimArgs &a, int32_t k, uint64_t &k
     }
 }
 
+// Fill entries of column k from the hashmap W: the warp scans right from k's
+// base slot, 32 slots at a time, until all cnt entries tagged k are found.
+// Every entry of k was published (release) before k became ready, so a busy
+// slot is never k's.  put(pos, row, w) receives the entry of scan rank pos;
+// the slot is freed for reuse.  false if the scan wrapped the whole table.
+template <typename Put>
+__device__ __forceinline__ bool warp_hash_gather(const ElimArgs &a, int32_t k, uint32_t cnt, Put &&put)
+{
+    const unsigned lane = lane_id();
+    const unsigned long long base = w_base(k, a.wcap);
+    uint32_t found = 0;
+    unsigned long long off = 0;
+    while (found < cnt) {
+        if (off >= a.wcap) return false;
+        const unsigned long long i = (base + off + lane) % a.wcap;
+        const bool mine = off + lane < a.wcap && ld_acquire(a.wcol + i) == k;
+        const unsigned bal = __ballot_sync(FULL, mine);
+        if (mine) {
+            put(found + __popc(bal & ((1u << lane) - 1u)), a.wrow[i], a.ww[i]);
+            st_release(a.wcol + i, W_FREE);          // after the entry was read
+        }
+        found += __popc(bal);
+        off += 32;
+    }
+    return true;
+}
+
 // Pivot k whose working set fits in registers (g <= 32).  Returns the vertex
 // this warp keeps for itself (-1: none), or -2 if the kernel must stop.
 // FP64 is slow on this part, so only the canonical arithmetic runs in FP64
@@ -327,7 +381,42 @@ __device__ int32_t eliminate_small(const ElimArgs &a, int32_t k, int64_t o0, int
     if ((int)lane < norig) {
         row = __ldg(a.lrow + o0 + lane);
         w = __ldg(a.lw + o0 + lane);
-    } else if ((int)lane < g) {
+    }
+    if (a.hash_store) {
+        // fill entries from W to lanes norig.. (scan rank order): each round, the
+        // lane of the p-th entry found hands it to lane norig + found + p
+        const unsigned long long base = w_base(k, a.wcap);
+        uint32_t found = 0;
+        unsigned long long off = 0;
+        while (found < cnt) {
+            if (off >= a.wcap) { bad = true; break; }
+            const unsigned long long i = (base + off + lane) % a.wcap;
+            const bool mine = off + lane < a.wcap && ld_acquire(a.wcol + i) == k;
+            const unsigned bal = __ballot_sync(FULL, mine);
+            int32_t fr = 0;
+            double fw = 0.0;
+            if (mine) {
+                fr = a.wrow[i]; fw = a.ww[i];
+                st_release(a.wcol + i, W_FREE);          // after the entry was read
+            }
+            const int nb = __popc(bal);
+            const int p = (int)lane - norig - (int)found;
+            int src = 0;
+            if (p >= 0 && p < nb) {                       // lane of the (p+1)-th set bit
+                int blo = 0, bhi = 31;
+                while (blo < bhi) {
+                    const int mid = (blo + bhi) >> 1;
+                    if (__popc(bal & ((2u << mid) - 1u)) >= p + 1) bhi = mid; else blo = mid + 1;
+                }
+                src = blo;
+            }
+            const int32_t rr = __shfl_sync(FULL, fr, src);
+            const double wv = __shfl_sync(FULL, fw, src);
+            if (p >= 0 && p < nb) { row = rr; w = wv; }
+            found += (uint32_t)nb;
+            off += 32;
+        }
+    } else if ((int)lane < g && (int)lane >= norig) {
         const uint32_t f = lane - (uint32_t)norig;       // fill index
         if (f < (uint32_t)FILL_C0) {
             row = __ldcg(a.in_row + (size_t)k * FILL_C0 + f);
@@ -543,7 +632,14 @@ __device__ int32_t eliminate_big(const ElimArgs &a, int32_t k, int64_t o0, int32
         v.row[i] = __ldg(a.lrow + o0 + i);
         v.w[i] = __ldg(a.lw + o0 + i);
     }
-    {
+    if (a.hash_store) {
+        if (!warp_hash_gather(a, k, cnt, [&](uint32_t pos, int32_t r, double x) {
+                v.row[norig + pos] = r; v.w[norig + pos] = x; })) {
+            set_status(a.status, ST_INVAL);
+            release_block();
+            return -2;
+        }
+    } else {
         const int ninl = cnt < (uint32_t)FILL_C0 ? (int)cnt : FILL_C0;
         const size_t ib = (size_t)k * FILL_C0;
         for (int i = lane; i < ninl; i += 32) {
@@ -1188,7 +1284,31 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
 
     // ---------------------------------------------------------------- gather
     for (int i = tid; i < norig; i += nt) { v.row[i] = __ldg(a.lrow + o0 + i); v.w[i] = __ldg(a.lw + o0 + i); }
-    {
+    if (a.hash_store) {
+        // fill from W: the CTA scans right from k's base slot, nt slots a round
+        const unsigned long long base = w_base(k, a.wcap);
+        uint32_t found = 0;
+        unsigned long long off = 0;
+        while (found < cnt) {
+            if (off >= a.wcap) { if (tid == 0) set_status(a.status, ST_INVAL); break; }
+            const unsigned long long i = (base + off + tid) % a.wcap;
+            const bool mine = off + tid < a.wcap && ld_acquire(a.wcol + i) == k;
+            const unsigned bal = __ballot_sync(FULL, mine);
+            if (lane == 0) cs.hcount[warp] = __popc(bal);
+            __syncthreads();
+            int before = 0, total = 0;
+            for (int w2 = 0; w2 < nw; ++w2) { const int c2 = cs.hcount[w2]; if (w2 < warp) before += c2; total += c2; }
+            if (mine) {
+                const uint32_t pos = found + before + __popc(bal & ((1u << lane) - 1u));
+                v.row[norig + pos] = a.wrow[i];
+                v.w[norig + pos] = a.ww[i];
+                st_release(a.wcol + i, W_FREE);          // after the entry was read
+            }
+            found += (uint32_t)total;
+            off += (unsigned long long)nt;
+            __syncthreads();
+        }
+    } else {
         const int ninl = cnt < (uint32_t)FILL_C0 ? (int)cnt : FILL_C0;
         for (int i = tid; i < ninl; i += nt) {
             v.row[norig + i] = __ldcg(a.in_row + (size_t)k * FILL_C0 + i);

@@ -28,7 +28,7 @@ class parac_opts(C.Structure):
                 ("max_pool_regrow", C.c_int32), ("warps_per_block", C.c_int32), ("spin_limit", C.c_int64),
                 ("blocks", C.c_int32), ("queue_chunk", C.c_int32), ("big_threshold", C.c_int32),
                 ("sptrsv", C.c_int32), ("check_every", C.c_int32), ("timing", C.c_int32),
-                ("stream", C.c_void_p), ("samples", C.c_int32)]
+                ("stream", C.c_void_p), ("samples", C.c_int32), ("fill_store", C.c_int32)]
 
 
 class parac_system(C.Structure):

@@ -264,3 +264,39 @@ def test_ac2_bit_identical(P):
         got, st = _gpu_factor(P, A, perm, seed, samples=2)
         assert same_factor(got, ref), _first_diff(got, ref)
         assert st["samples"] == 2 and ref["fill"] > one["fill"]
+
+
+def test_hashmap_fill_store_bit_identical(P):
+    """The hashmap fill store W (Sec. IV-C) instead of the per-column slabs: the
+    same factor on every elimination path (register, warp, CTA with shared and
+    global working sets), with AC(2), SDDM, a batch, and a small table that
+    forces regrowth."""
+    cases = [W.config("grid2d-64")[:3], W.config("rmat-15")[:3], W.config("poisson-contrast-16")[:3]]
+    rng = np.random.default_rng(31)
+    n = 4000
+    a = np.concatenate([np.zeros(n - 1, np.int64), rng.integers(1, n, 3 * n)])
+    b = np.concatenate([np.arange(1, n), rng.integers(1, n, 3 * n)])
+    keep = a != b
+    lo = np.minimum(a[keep], b[keep]); hi = np.maximum(a[keep], b[keep])
+    key = np.unique(lo * n + hi)
+    cases.append((W.laplacian_from_edges(n, key // n, key % n, rng.uniform(0.5, 2, len(key))),
+                  W.random_ordering(n, 9), 9))
+    for A, perm, seed in cases:
+        ref = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)
+        got, st = _gpu_factor(P, A, perm, seed, fill_store=1)
+        assert same_factor(got, ref), _first_diff(got, ref)
+        assert st["fill_store"] == 1
+    A, perm, seed = cases[0]
+    ref = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed, samples=2)
+    got, _ = _gpu_factor(P, A, perm, seed, fill_store=1, samples=2)
+    assert same_factor(got, ref)
+    A, perm, seed = cases[1]                      # R-MAT: a table far too small for its live fill
+    got, st = _gpu_factor(P, A, perm, seed, fill_store=1, pool_mult=0.02, max_pool_regrow=10)
+    assert same_factor(got, oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)) and st["regrows"] > 0
+    batch = W.sddm_batch(5, nmin=300, nmax=3000, seed=4)
+    systems = [(Ab.n, Ab.colptr, Ab.rowind, Ab.val, pb) for (Ab, pb, bb) in batch]
+    Gs = P.parac_factor_many(systems, seed=99, opts=P.parac_opts_default(fill_store=1))
+    for s, ((Ab, pb, bb), G) in enumerate(zip(batch, Gs)):
+        ref = oracle.factor(Ab.colptr, Ab.rowind, Ab.val, pb, seed=99, sys=s)
+        assert same_factor(G.export(), ref)
+        G.free()
