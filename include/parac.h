@@ -73,9 +73,10 @@ enum { PARAC_SPTRSV_AUTO = 0, PARAC_SPTRSV_WARP = 1, PARAC_SPTRSV_SUB8 = 2, PARA
  *                   FP32 and the triangular solves run in FP32, while PCG's
  *                   SpMV, residual update and dot products stay FP64.
  *   pool_mult       Initial fill-workspace capacity, in units of the strict
- *                   lower input entries (default 10: grids use ~3.5, R-MAT
- *                   graphs ~8 with the overflow slabs' rounding; an overflow
- *                   reruns the whole elimination with a larger workspace).
+ *                   lower input entries; 0 (default) picks 5, or 10 when the
+ *                   longest lower column exceeds 16x the average (grids use
+ *                   ~3.5, R-MAT graphs ~8 with the overflow slabs' rounding;
+ *                   an overflow reruns the whole elimination, larger).
  *   max_pool_regrow Reruns with a 2x larger workspace after an overflow (the
  *                   rerun gives the same factor).
  *   spin_limit      Polls any device wait may take before PARAC_ETIMEOUT

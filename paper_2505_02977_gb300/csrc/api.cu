@@ -264,7 +264,7 @@ Opts read_opts(const parac_opts *in)
     Opts r;
     parac_opts_default(&r.o);
     if (in) r.o = *in;
-    if (r.o.pool_mult <= 0) r.o.pool_mult = 10.0;
+    if (r.o.pool_mult < 0) r.o.pool_mult = 0.0;        // 0: chosen from the input (run_factor)
     if (r.o.max_pool_regrow < 0) r.o.max_pool_regrow = 0;
     if (r.o.spin_limit <= 0) r.o.spin_limit = 1ll << 24;
     if (r.o.warps_per_block <= 0) r.o.warps_per_block = 8;
@@ -461,7 +461,7 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         trace_ph = dalloc<int32_t>((size_t)nl * 8, st);
         CK(cudaMemsetAsync(trace_ph.p, 0, 32 * (size_t)nl, st));
     }
-    double mult = O.o.pool_mult;
+    double mult = O.o.pool_mult;                        // set below when 0 (automatic)
     // Global scratch of the cooperative (CTA-per-vertex) path: every CTA may
     // hold a working set of next_pow2(gather) entries, and a vertex's gather
     // is its original lower column plus the fill it receives.  Sized from the
@@ -482,6 +482,13 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) { cudaGetLastError(); freeb = 0; }
         scratch_cap = std::max(scratch_cap, std::min<unsigned long long>(want, freeb / 4));
         out.max_lower_column = maxlow;
+        // Fill workspace: bounded-degree inputs (grids) use ~3.5x their lower
+        // entries, power-law graphs ~8x (hub columns' overflow slabs); an
+        // overflow reruns the whole elimination, so hub-dominated inputs start at 10x.
+        if (mult <= 0.0) {
+            const double avg = nl > 0 ? (double)nnz_low / (double)nl : 0.0;
+            mult = (double)maxlow > 16.0 * std::max(avg, 1.0) ? 10.0 : 5.0;
+        }
     }
     DBuf pool_row, pool_w, f_row, f_val, scratch, w_col, w_row, w_w;
     for (int attempt = 0;; ++attempt) {
@@ -781,7 +788,7 @@ void parac_opts_default(parac_opts *o)
     std::memset(o, 0, sizeof *o);
     o->kind = PARAC_KIND_AUTO;
     o->g_precision = 64;
-    o->pool_mult = 10.0;
+    o->pool_mult = 0.0;
     o->max_pool_regrow = 2;
     o->spin_limit = 1ll << 24;
     o->warps_per_block = 8;
