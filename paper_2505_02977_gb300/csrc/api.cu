@@ -135,6 +135,24 @@ void copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s)
     CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
 }
 
+// Device memory size, queried once per device (a per-call cudaMemGetInfo
+// would add a device-wide query to every factorisation).
+unsigned long long device_memory_bytes()
+{
+    static std::atomic<unsigned long long> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 0;
+    unsigned long long v = cache[dev].load();
+    if (v == 0) {
+        cudaDeviceProp p;
+        if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) v = (unsigned long long)p.totalGlobalMem;
+        else cudaGetLastError();
+        cache[dev].store(v);
+    }
+    return v;
+}
+
 int num_sms()
 {
     int dev = 0, sms = 0;
@@ -478,9 +496,7 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         unsigned long long p2 = 1;
         while (p2 < 4ull * (unsigned long long)maxlow + 64ull) p2 <<= 1;
         const unsigned long long want = (unsigned long long)blocks * 2ull * (ENTRY_BYTES + 1) * p2 + (256ull << 20);
-        size_t freeb = 0, totalb = 0;
-        if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) { cudaGetLastError(); freeb = 0; }
-        scratch_cap = std::max(scratch_cap, std::min<unsigned long long>(want, freeb / 4));
+        scratch_cap = std::max(scratch_cap, std::min<unsigned long long>(want, device_memory_bytes() / 8));
         out.max_lower_column = maxlow;
         // Fill workspace: bounded-degree inputs (grids) use ~3.5x their lower
         // entries, power-law graphs ~8x (hub columns' overflow slabs); an
@@ -699,11 +715,13 @@ void finish_handle(parac_factor_s *h, int64_t n, int64_t nnzF, const Opts &O)
         CK(launch_to_f32(h->Svalr.as<double>(), h->Svalr32.as<float>(), nnzF, st));
     }
     h->status = dalloc<int32_t>(1, st);
-    // Row groups of the one-row-per-warp solves, only when some row is long
-    // enough to be shared by a block (else the fixed groups are the same).
+    // Group tables of the one-row-per-warp solves, only when some row is long
+    // enough to matter: up to 4x LONG_ROW_SINGLE entries a warp still walks a
+    // row in a few rounds of its chunked dot, and the fixed groups avoid
+    // building the table (a host pass over the rows) at setup.
     CK(cudaStreamSynchronize(st));
     h->max_row = maxlen;
-    if (maxlen > LONG_ROW_SINGLE) {
+    if (maxlen > 4 * LONG_ROW_SINGLE) {
         std::vector<int64_t> rp((size_t)n + 1), cp((size_t)n + 1);
         CK(cudaMemcpyAsync(rp.data(), h->Srp.p, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(cp.data(), h->Scp.p, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));

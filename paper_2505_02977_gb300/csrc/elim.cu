@@ -1314,12 +1314,16 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
             v.row[norig + i] = __ldcg(a.in_row + (size_t)k * FILL_C0 + i);
             v.w[norig + i] = __ldcg(a.in_w + (size_t)k * FILL_C0 + i);
         }
+        uint32_t gl[FILL_LEVELS];               // directory entries of the used levels, loaded together
+#pragma unroll
+        for (int j = 1; j <= FILL_LEVELS; ++j)
+            gl[j - 1] = cnt > fill_level_start(j) ? __ldcg(a.dir + (size_t)k * FILL_LEVELS + (j - 1)) : 0u;
         for (int j = 1; j <= FILL_LEVELS; ++j) {
             const uint32_t start = fill_level_start(j);
             if (cnt <= start) break;
             const uint32_t capj = fill_level_cap(j);
             const uint32_t len = (cnt - start) < capj ? (cnt - start) : capj;
-            const uint32_t gidx = __ldcg(a.dir + (size_t)k * FILL_LEVELS + (j - 1));
+            const uint32_t gidx = gl[j - 1];
             if (gidx == 0u || gidx == 0xffffffffu) {          // never published
                 if (tid == 0) set_status(a.status, ST_INVAL);
                 break;
@@ -1423,12 +1427,15 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
         if (lane == 31) tiles[j] = x;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0) {            // serial carry chain; the tile totals are loaded 8 at a time
         double carry = 0.0;
-        for (int j = 0; j < ntile; ++j) {
-            const double tot = tiles[j];
-            tiles[j] = carry;
-            carry = __dadd_rn(tot, carry);
+        for (int j0 = 0; j0 < ntile; j0 += 8) {
+            double tot[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) tot[q] = j0 + q < ntile ? tiles[j0 + q] : 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (j0 + q < ntile) { tiles[j0 + q] = carry; carry = __dadd_rn(tot[q], carry); }
         }
     }
     __syncthreads();
@@ -1449,10 +1456,13 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     __syncthreads();
     if (tid == 0) {
         unsigned long long run = 0ull;
-        for (int j = 0; j < ntile; ++j) {
-            const unsigned long long tm = dbits(tiles[j]);
-            tiles[j] = __longlong_as_double((long long)run);
-            if (tm > run) run = tm;
+        for (int j0 = 0; j0 < ntile; j0 += 8) {
+            unsigned long long tm[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) tm[q] = j0 + q < ntile ? dbits(tiles[j0 + q]) : 0ull;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (j0 + q < ntile) { tiles[j0 + q] = __longlong_as_double((long long)run); if (tm[q] > run) run = tm[q]; }
         }
     }
     __syncthreads();
