@@ -465,13 +465,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="grid3d-128")
-    ap.add_argument("--prec", type=int, default=64, choices=[64, 32])
+    ap.add_argument("--prec", type=int, default=None, choices=[64, 32],
+                    help="precision G is stored and applied in (default: 32 for sddm-batch-200 and rmat-24, "
+                         "whose configurations specify it, else 64)")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ordering", default="random", choices=["random", "nnz"])
     ap.add_argument("--samples", type=int, default=1, help="samples per clique-tree slot (AC(k); 1: Alg. 2)")
     args = ap.parse_args()
+    if args.prec is None:
+        args.prec = 32 if args.workload in ("sddm-batch-200", "rmat-24") else 64
     world, rank, local, pg = dist_setup()
     try:
         if args.impl == "reference":

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libparac.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "elim.cu", "ingest.cu", "compact.cu", "solve.cu", "block.cu"]
+SOURCES = ["api.cu", "elim.cu", "ingest.cu", "compact.cu", "solve.cu", "block.cu", "batch.cu"]
 
 
 def nvcc():

@@ -256,6 +256,7 @@ struct parac_factor_s {
     // solve arrays: F relabelled into dependency-level order (positions)
     DBuf Scp, Srow, Sval, Sval32, Srp, Scol, Svalr, Svalr32, Sdinv, Sperm;
     int32_t depth = 0;
+    std::vector<int64_t> lstart;                       // first position of each level (depth + 1)
     int64_t nnzL = 0;
     std::string stats;
     SolveCache cache;
@@ -667,6 +668,8 @@ void finish_handle(parac_factor_s *h, int64_t n, int64_t nnzF, const Opts &O)
         CK(launch_row_count(n, h->Lev.as<int32_t>(), hist.as<int32_t>(), st));
         DBuf tmp2(scan_tmp_bytes(hmax + 2), st);
         CK(scan_i32_to_i64(hist.as<int32_t>(), lstart.as<int64_t>(), hmax + 1, tmp2.p, st));
+        h->lstart.assign((size_t)hmax + 2, 0);
+        CK(cudaMemcpyAsync(h->lstart.data(), lstart.p, 8 * ((size_t)hmax + 2), cudaMemcpyDeviceToHost, st));
         CK(cudaMemsetAsync(hist.p, 0, 4 * ((size_t)hmax + 1), st));
         CK(launch_level_scatter((int32_t)n, h->Lev.as<int32_t>(), lstart.as<int64_t>(), hist.as<int32_t>(),
                                 order.as<int32_t>(), st));
@@ -1455,9 +1458,254 @@ extern "C" parac_status parac_pcg(parac_factor_t G, int64_t n, const int64_t *co
     });
 }
 
-// PCG on several systems at once: worker threads each take the next system
-// and run parac_pcg on it; every handle solves on its own library stream, so
-// the GPU runs the systems' kernels side by side.
+namespace {
+
+// ------------------------------------------------------------------ batched PCG
+// The systems of one parac_pcg_many call solved as one block-diagonal system:
+// their matrices, factors and vectors concatenated (system s holds rows
+// off[s] .. off[s+1]), one schedule of the triangular solves interleaving the
+// systems' dependency levels, and per-system CG scalars and stopping (batch.cu).
+// A system's preconditioner apply is the same arithmetic, entry for entry, as
+// its own parac_pcg's; only the dot products' reduction trees differ.
+constexpr int64_t BATCH_CHUNK_ROWS = 4096;
+
+struct BatchRun {
+    DBuf Lp, Li, Lv, Fcp, Frow, Fval, Frp, Fcol, Fvalr, Dinv, operm;
+    DBuf gt_f, gt_b, part_f, part_b;
+    DBuf x, r, z, p, q, b, yl, zl, partials, sys, state, status, clo, csys, sys_c0, seg;
+};
+
+unsigned poll_ns_default()
+{
+    unsigned ns = 256;
+    if (const char *e = getenv("PARAC_POLL_NS")) ns = (unsigned)std::max(16, std::min(100000, atoi(e)));
+    return ns;
+}
+
+// Every handle on one device with one precision, and the concatenation within
+// the solves' 32-bit positions.
+bool batchable(int32_t count, const parac_factor_t *G)
+{
+    if (count < 2) return false;
+    if (const char *e = getenv("PARAC_PCG_MANY")) if (!strcmp(e, "threads")) return false;
+    int64_t n = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        if (!G[i] || G[i]->device != G[0]->device || G[i]->prec != G[0]->prec) return false;
+        if ((G[i]->n > 0 && (int64_t)G[i]->lstart.size() != (int64_t)G[i]->depth + 1)) return false;
+        n += G[i]->n;
+    }
+    return n > 0 && n < INT32_MAX;
+}
+
+parac_status pcg_batch(int32_t count, const parac_factor_t *G, const double *const *bv, double *const *xv,
+                       double tol, int32_t maxit, int32_t *iters, double *true_relres)
+{
+    cudaSetDevice(G[0]->device);
+    cudaStream_t st = G[0]->stream;
+    set_mempool_keep();
+    // start after the work queued on every handle's stream
+    for (int32_t i = 1; i < count; ++i) {
+        if (G[i]->stream == st) continue;
+        cudaEvent_t e0 = nullptr;
+        CK(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
+        CK(cudaEventRecord(e0, G[i]->stream));
+        CK(cudaStreamWaitEvent(st, e0, 0));
+        CK(cudaEventDestroy(e0));
+    }
+    const int prec = G[0]->prec;
+    const size_t xs = prec == 32 ? 4 : 8;
+    std::vector<int64_t> off((size_t)count + 1, 0), offL((size_t)count + 1, 0), offF((size_t)count + 1, 0);
+    int32_t depth = 0;
+    long long spin = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        off[(size_t)i + 1] = off[(size_t)i] + G[i]->n;
+        offL[(size_t)i + 1] = offL[(size_t)i] + (G[i]->n > 0 ? G[i]->nnzL : 0);
+        offF[(size_t)i + 1] = offF[(size_t)i] + (G[i]->n > 0 ? G[i]->nnzF : 0);
+        depth = std::max(depth, G[i]->depth);
+        spin = std::max(spin, G[i]->spin_limit);
+    }
+    const int64_t n = off.back(), nnzL = offL.back(), nnzF = offF.back();
+    BatchRun R;
+    const size_t n1 = (size_t)n + 1, L1 = (size_t)std::max<int64_t>(nnzL, 1), F1 = (size_t)std::max<int64_t>(nnzF, 1);
+    R.Lp = dalloc<int64_t>(n1, st); R.Li = dalloc<int32_t>(L1, st); R.Lv = dalloc<double>(L1, st);
+    R.Fcp = dalloc<int64_t>(n1, st); R.Frow = dalloc<int32_t>(F1, st); R.Fval = DBuf(xs * F1, st);
+    R.Frp = dalloc<int64_t>(n1, st); R.Fcol = dalloc<int32_t>(F1, st); R.Fvalr = DBuf(xs * F1, st);
+    R.Dinv = dalloc<double>((size_t)n, st); R.operm = dalloc<int32_t>((size_t)n, st);
+    // concatenation: 11 arrays, one segment per system each
+    enum { C_LP, C_LI, C_LV, C_FCP, C_FROW, C_FVAL, C_FRP, C_FCOL, C_FVALR, C_DINV, C_PERM, C_KINDS };
+    std::vector<CatSeg> seg((size_t)C_KINDS * count);
+    int64_t maxn = 0, maxL = 0, maxF = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        const parac_factor_s *h = G[i];
+        const int64_t ni = h->n, li = ni > 0 ? h->nnzL : 0, fi = ni > 0 ? h->nnzF : 0;
+        const int64_t o = off[(size_t)i], oL = offL[(size_t)i], oF = offF[(size_t)i];
+        maxn = std::max(maxn, ni); maxL = std::max(maxL, li); maxF = std::max(maxF, fi);
+        auto at = [&](int k) -> CatSeg & { return seg[(size_t)k * count + i]; };
+        const bool f32 = prec == 32;
+        at(C_LP) = {h->Lp.p, ni, o, oL};
+        at(C_LI) = {h->Li.p, li, oL, o};
+        at(C_LV) = {h->Lv.p, li, oL, 0};
+        at(C_FCP) = {h->Scp.p, ni, o, oF};
+        at(C_FROW) = {h->Srow.p, fi, oF, o};
+        at(C_FVAL) = {f32 ? h->Sval32.p : h->Sval.p, fi, oF, 0};
+        at(C_FRP) = {h->Srp.p, ni, o, oF};
+        at(C_FCOL) = {h->Scol.p, fi, oF, o};
+        at(C_FVALR) = {f32 ? h->Svalr32.p : h->Svalr.p, fi, oF, 0};
+        at(C_DINV) = {h->Sdinv.p, ni, o, 0};
+        at(C_PERM) = {h->Sperm.p, ni, o, o};
+    }
+    R.seg = DBuf(sizeof(CatSeg) * seg.size(), st);
+    CK(cudaMemcpyAsync(R.seg.p, seg.data(), sizeof(CatSeg) * seg.size(), cudaMemcpyHostToDevice, st));
+    const CatSeg *ds = R.seg.as<CatSeg>();
+    auto cat = [&](int k, int64_t mx, int elem, bool fl, DBuf &dst) {
+        CK(launch_cat(ds + (size_t)k * count, count, mx, elem, fl, dst.p, st));
+    };
+    cat(C_LP, maxn, 8, false, R.Lp); cat(C_LI, maxL, 4, false, R.Li); cat(C_LV, maxL, 8, true, R.Lv);
+    cat(C_FCP, maxn, 8, false, R.Fcp); cat(C_FROW, maxF, 4, false, R.Frow); cat(C_FVAL, maxF, (int)xs, true, R.Fval);
+    cat(C_FRP, maxn, 8, false, R.Frp); cat(C_FCOL, maxF, 4, false, R.Fcol); cat(C_FVALR, maxF, (int)xs, true, R.Fvalr);
+    cat(C_DINV, maxn, 8, true, R.Dinv); cat(C_PERM, maxn, 4, false, R.operm);
+    // closing pointers (host values, copied before this function returns)
+    const int64_t ends[3] = {nnzL, nnzF, nnzF};
+    CK(cudaMemcpyAsync(R.Lp.as<int64_t>() + n, &ends[0], 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(R.Fcp.as<int64_t>() + n, &ends[1], 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(R.Frp.as<int64_t>() + n, &ends[2], 8, cudaMemcpyHostToDevice, st));
+    // schedule of the solves: levels interleaved over the systems
+    std::vector<std::vector<int64_t>> rps, cps;
+    std::vector<BatchSysLevels> fw, bw;
+    rps.reserve((size_t)count); cps.reserve((size_t)count);
+    for (int32_t i = 0; i < count; ++i) {
+        const parac_factor_s *h = G[i];
+        if (h->n == 0) continue;
+        const std::vector<int64_t> *rp = nullptr, *cp = nullptr;
+        if (h->max_row > 4 * LONG_ROW_SINGLE) {     // rows that need the block-wide kinds
+            rps.emplace_back((size_t)h->n + 1); cps.emplace_back((size_t)h->n + 1);
+            CK(cudaMemcpyAsync(rps.back().data(), h->Srp.p, 8 * ((size_t)h->n + 1), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(cps.back().data(), h->Scp.p, 8 * ((size_t)h->n + 1), cudaMemcpyDeviceToHost, st));
+            rp = &rps.back(); cp = &cps.back();
+        }
+        fw.push_back({off[(size_t)i], h->lstart, rp});
+        bw.push_back({off[(size_t)i], h->lstart, cp});
+    }
+    CK(cudaStreamSynchronize(st));
+    const GroupTable gf = batch_groups(fw, n, false, SOLVE_WARPS, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
+    const GroupTable gb = batch_groups(bw, n, true, SOLVE_WARPS, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
+    R.gt_f = dalloc<int32_t>(std::max<size_t>(gf.g.size(), 4), st);
+    R.gt_b = dalloc<int32_t>(std::max<size_t>(gb.g.size(), 4), st);
+    CK(cudaMemcpyAsync(R.gt_f.p, gf.g.data(), 4 * gf.g.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(R.gt_b.p, gb.g.data(), 4 * gb.g.size(), cudaMemcpyHostToDevice, st));
+    R.part_f = DBuf(xs * (size_t)std::max(gf.nslots, 1), st);
+    R.part_b = DBuf(xs * (size_t)std::max(gb.nslots, 1), st);
+    // row chunks of the dot products (never across systems)
+    std::vector<int64_t> clo;
+    std::vector<int32_t> csys, c0((size_t)count + 1, 0);
+    for (int32_t i = 0; i < count; ++i) {
+        c0[(size_t)i] = (int32_t)csys.size();
+        for (int64_t a = off[(size_t)i]; a < off[(size_t)i + 1]; a += BATCH_CHUNK_ROWS) { clo.push_back(a); csys.push_back(i); }
+    }
+    c0[(size_t)count] = (int32_t)csys.size();
+    clo.push_back(n);
+    const int32_t nch = (int32_t)csys.size();
+    R.clo = dalloc<int64_t>(clo.size(), st); R.csys = dalloc<int32_t>(std::max<size_t>(csys.size(), 1), st);
+    R.sys_c0 = dalloc<int32_t>(c0.size(), st);
+    CK(cudaMemcpyAsync(R.clo.p, clo.data(), 8 * clo.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(R.csys.p, csys.data(), 4 * csys.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(R.sys_c0.p, c0.data(), 4 * c0.size(), cudaMemcpyHostToDevice, st));
+    // vectors and state
+    R.x = dalloc<double>((size_t)n, st); R.r = dalloc<double>((size_t)n, st); R.z = dalloc<double>((size_t)n, st);
+    R.p = dalloc<double>((size_t)n, st); R.q = dalloc<double>((size_t)n, st); R.b = dalloc<double>((size_t)n, st);
+    R.yl = DBuf(xs * (size_t)n, st); R.zl = DBuf(xs * (size_t)n, st);
+    R.partials = dalloc<double>(3 * (size_t)std::max(nch, 1), st);
+    R.sys = DBuf(sizeof(SysState) * (size_t)count, st);
+    R.state = DBuf(batch_state_bytes(), st);
+    R.status = dalloc<int32_t>(1, st);
+    CK(cudaMemsetAsync(R.status.p, 0, 4, st));
+    for (int32_t i = 0; i < count; ++i)
+        if (G[i]->n > 0)
+            CK(cudaMemcpyAsync(R.b.as<double>() + off[(size_t)i], bv[i], 8 * (size_t)G[i]->n, cudaMemcpyDefault, st));
+    // solve arguments of the concatenated system
+    SolveArgs A{};
+    A.n = (int32_t)n;
+    A.Lp = R.Lp.as<int64_t>(); A.Li = R.Li.as<int32_t>(); A.Lv = R.Lv.as<double>();
+    A.Fcp = R.Fcp.as<int64_t>(); A.Frow = R.Frow.as<int32_t>();
+    A.Frp = R.Frp.as<int64_t>(); A.Fcol = R.Fcol.as<int32_t>();
+    if (prec == 32) { A.Fval32 = R.Fval.as<float>(); A.Fvalr32 = R.Fvalr.as<float>(); }
+    else { A.Fval64 = R.Fval.as<double>(); A.Fvalr64 = R.Fvalr.as<double>(); }
+    A.Dinv = R.Dinv.as<double>(); A.operm = R.operm.as<int32_t>();
+    A.prec = prec;
+    A.lanes_spmv = lanes_for((double)nnzL / (double)n);
+    A.lanes_trsv = 32;
+    A.trsv_warps = SOLVE_WARPS;
+    int bps = 0;
+    trsv_configure(32, SOLVE_WARPS, &bps, prec);
+    const int64_t max_blocks = (int64_t)num_sms() * std::max(bps, 1);   // all co-resident
+    const int64_t want = (2 * n / std::max(depth, 1) + SOLVE_WARPS - 1) / SOLVE_WARPS;
+    int64_t tb = std::max<int64_t>(std::min<int64_t>(num_sms(), max_blocks), std::min<int64_t>(max_blocks, want));
+    tb = std::min<int64_t>(tb, std::max<int64_t>(std::max(gf.ngroups, gb.ngroups), 1));
+    A.trsv_blocks = (int32_t)tb;
+    CK(set_poll_backoff(poll_ns_default()));
+    A.spin_limit = spin;
+    A.status = R.status.as<int32_t>();
+    A.gt_f = (const int4 *)R.gt_f.p; A.ng_f = gf.ngroups; A.part_f = R.part_f.p; A.nslot_f = gf.nslots;
+    A.gt_b = (const int4 *)R.gt_b.p; A.ng_b = gb.ngroups; A.part_b = R.part_b.p; A.nslot_b = gb.nslots;
+    BatchBuffers B{};
+    B.count = count; B.nchunks = nch;
+    B.clo = R.clo.as<int64_t>(); B.csys = R.csys.as<int32_t>(); B.sys_c0 = R.sys_c0.as<int32_t>();
+    B.x = R.x.as<double>(); B.r = R.r.as<double>(); B.z = R.z.as<double>(); B.p = R.p.as<double>();
+    B.q = R.q.as<double>(); B.b = R.b.as<double>();
+    if (prec == 32) { B.solve.yl32 = R.yl.as<float>(); B.solve.zl32 = R.zl.as<float>(); }
+    else { B.solve.yl64 = R.yl.as<double>(); B.solve.zl64 = R.zl.as<double>(); }
+    B.partials = R.partials.as<double>(); B.sys = R.sys.as<SysState>(); B.st = R.state.as<BatchState>();
+    B.spmv_blocks = (int32_t)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8));
+    // the iteration: rounds of check_every steps, then the stopping tests
+    const int every = G[0]->check_every;
+    CK(spcg_init(A, B, tol, maxit, st));
+    std::vector<SysState> hs((size_t)count);
+    auto batch_status = [&]() {
+        int32_t s = 0;
+        CK(cudaMemcpyAsync(&s, R.status.p, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return s;
+    };
+    for (;;) {
+        BatchState bs{};
+        CK(cudaMemcpyAsync(&bs, R.state.p, sizeof bs, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (batch_status() != ST_OK) { set_err("triangular solve wait exceeded the spin limit"); return PARAC_ETIMEOUT; }
+        if (!bs.gate.done) {
+            for (int c = 0; c < every; ++c) CK(spcg_iteration(A, B, st));
+            continue;
+        }
+        CK(spcg_true_residual(A, B, st));
+        CK(cudaMemcpyAsync(hs.data(), R.sys.p, sizeof(SysState) * (size_t)count, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        bool reopen = false;
+        for (const SysState &y : hs)
+            if (y.converged && !(y.true_rr <= y.tol2bb) && y.iters < maxit) reopen = true;
+        if (!reopen) break;
+        CK(spcg_reopen(A, B, st));
+    }
+    if (batch_status() != ST_OK) { set_err("triangular solve wait exceeded the spin limit"); return PARAC_ETIMEOUT; }
+    for (int32_t i = 0; i < count; ++i)
+        if (G[i]->n > 0)
+            CK(cudaMemcpyAsync(xv[i], R.x.as<double>() + off[(size_t)i], 8 * (size_t)G[i]->n, cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    int32_t first = -1;
+    for (int32_t i = 0; i < count; ++i) {
+        const SysState &y = hs[(size_t)i];
+        if (iters) iters[i] = y.iters;
+        if (true_relres) true_relres[i] = y.bb > 0.0 ? std::sqrt(y.true_rr / y.bb) : 0.0;
+        if (first < 0 && y.bb > 0.0 && !(y.true_rr <= tol * tol * y.bb)) first = i;
+    }
+    if (first >= 0) { set_err("system %d: PCG reached maxit", first); return PARAC_ENOCONV; }
+    return PARAC_OK;
+}
+
+}  // namespace
+
+// PCG on several systems at once: as one block-diagonal system (pcg_batch)
+// when the handles share a device and a precision; otherwise worker threads
+// each take the next system and run parac_pcg on it, every handle on its own
+// library stream, so the GPU runs the systems' kernels side by side.
 extern "C" parac_status parac_pcg_many(int32_t count, const parac_factor_t *G, const double *const *b,
                                        double *const *x, double tol, int32_t maxit, int32_t *iters,
                                        double *true_relres)
@@ -1467,6 +1715,7 @@ extern "C" parac_status parac_pcg_many(int32_t count, const parac_factor_t *G, c
         for (int32_t i = 0; i < count; ++i)
             for (int32_t j = 0; j < i && j < 64; ++j)
                 if (G[i] == G[j]) { set_err("parac_pcg_many: handle %d repeats handle %d", i, j); return PARAC_EINVAL; }
+        if (batchable(count, G)) return pcg_batch(count, G, b, x, tol, maxit, iters, true_relres);
         std::vector<parac_status> st((size_t)count, PARAC_OK);
         std::vector<std::string> msg((size_t)count);
         std::vector<int32_t> it((size_t)count, 0);

@@ -99,7 +99,11 @@ cudaError_t launch_sys_of_label(int32_t S, const int32_t *sys_lbase, int32_t nl,
                                 cudaStream_t st);
 
 // ---------------------------------------------------------------- solve.cu
-struct PcgState;   // device-resident scalars of one PCG run (solve.cu)
+// device-resident scalars of one PCG run (solve.cu)
+struct PcgState {
+    double rz, alpha, beta, bb, rr, tol2bb, true_rr, pad0;
+    int32_t done, iters, maxit, converged;
+};
 
 struct SolveArgs {
     int32_t n;                    // rows (original numbering)
@@ -199,6 +203,58 @@ cudaError_t bpcg_iteration(const SolveArgs &A, const BlockBuffers &B, cudaStream
 cudaError_t bpcg_true_residual(const SolveArgs &A, const BlockBuffers &B, cudaStream_t st);
 cudaError_t bpcg_reopen(const SolveArgs &A, const BlockBuffers &B, cudaStream_t st);
 cudaError_t bpcg_read_state(const BlockBuffers &B, BlockHostState *h, cudaStream_t st);
+
+cudaError_t solve_spmv(const SolveArgs &A, const double *x, double *y, const PcgState *st, int blocks, cudaStream_t s);
+cudaError_t solve_apply(const SolveArgs &A, const PcgBuffers &B, const double *r, double *z, const PcgState *st,
+                        cudaStream_t s);
+cudaError_t solve_fill_sentinels(const SolveArgs &A, const PcgBuffers &B, cudaStream_t s);
+
+// ---------------------------------------------------------------- batch.cu
+// PCG on many systems at once (one right-hand side each): the systems' factors
+// concatenated (global positions, rows interleaved by dependency level in the
+// schedule table), per-system scalars and stopping, dot products over fixed
+// row chunks that never straddle two systems.
+struct SysState {
+    double rz, alpha, beta, bb, rr, tol2bb, true_rr, pad0;
+    int32_t done, iters, converged, pad1;
+};
+struct BatchState {
+    PcgState gate;                // gate.done = every system stopped (gates the shared kernels)
+    int32_t count, maxit, pad0, pad1;
+};
+struct BatchBuffers {
+    int32_t count;                // systems
+    int32_t nchunks;              // row chunks
+    const int64_t *clo;           // [nchunks + 1] chunk row bounds (original order)
+    const int32_t *csys;          // [nchunks] system of each chunk
+    const int32_t *sys_c0;        // [count + 1] first chunk of each system
+    double *x, *r, *z, *p, *q, *b;   // [n] concatenated vectors
+    PcgBuffers solve;             // yl/zl work of the solves
+    double *partials;             // [3 * nchunks]
+    SysState *sys;                // [count]
+    BatchState *st;
+    int32_t spmv_blocks;
+};
+size_t batch_state_bytes();
+cudaError_t spcg_init(const SolveArgs &A, const BatchBuffers &B, double tol, int32_t maxit, cudaStream_t st);
+cudaError_t spcg_iteration(const SolveArgs &A, const BatchBuffers &B, cudaStream_t st);
+cudaError_t spcg_true_residual(const SolveArgs &A, const BatchBuffers &B, cudaStream_t st);
+cudaError_t spcg_reopen(const SolveArgs &A, const BatchBuffers &B, cudaStream_t st);
+// dst[seg.dst + i] = src[i] + seg.add for every segment (elem 4 or 8 bytes;
+// integer add, or a plain copy of floats); seg[] in device memory
+struct CatSeg { const void *src; int64_t count, dst, add; };
+cudaError_t launch_cat(const CatSeg *seg, int32_t nseg, int64_t max_count, int elem, bool is_float, void *dst,
+                       cudaStream_t st);
+// one system of a concatenated solve: its first global position, its level
+// starts (positions, depth + 1 entries) and, for systems with rows longer than
+// the block-wide threshold, its row (forward) or column (backward) pointers
+struct BatchSysLevels {
+    int64_t off;
+    std::vector<int64_t> lstart;
+    const std::vector<int64_t> *ptr;
+};
+GroupTable batch_groups(const std::vector<BatchSysLevels> &sys, int64_t n_tot, bool descending, int warps,
+                        int long_row, int split_row, int chunk);
 
 // Allocation-free variant: work vectors in a fixed device array (n <= NOALLOC_MAX_N).
 constexpr int NOALLOC_MAX_N = 1 << 18;

@@ -22,11 +22,6 @@
 
 namespace parac {
 
-struct PcgState {
-    double rz, alpha, beta, bb, rr, tol2bb, true_rr, pad0;
-    int32_t done, iters, maxit, converged;
-};
-
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -725,6 +720,24 @@ cudaError_t fill_sentinels(const SolveArgs &A, const PcgBuffers &B, cudaStream_t
 }
 
 }  // namespace
+
+// the SpMV, the preconditioner apply and the sentinel reset, for the batched
+// PCG (batch.cu); st gates the launches (st->done: nothing to do)
+cudaError_t solve_spmv(const SolveArgs &A, const double *x, double *y, const PcgState *st, int blocks, cudaStream_t s)
+{
+    return spmv(A, x, y, nullptr, st, blocks, s);
+}
+
+cudaError_t solve_apply(const SolveArgs &A, const PcgBuffers &B, const double *r, double *z, const PcgState *st,
+                        cudaStream_t s)
+{
+    return apply(A, B, r, z, nullptr, st, s);
+}
+
+cudaError_t solve_fill_sentinels(const SolveArgs &A, const PcgBuffers &B, cudaStream_t s)
+{
+    return fill_sentinels(A, B, s);
+}
 
 size_t pcg_state_bytes() { return sizeof(PcgState); }
 

@@ -289,11 +289,33 @@ def test_split_rows(P):
     G.free()
 
 
-def test_pcg_many_matches_single_calls(P):
-    """parac_pcg_many on the handles of one parac_factor_many call: every
-    system's result is bit-identical to its own parac_pcg call (host and
-    device right-hand sides)."""
+def _hub_system(n, seed):
+    """A hub adjacent to every vertex, eliminated last: one factor row of about
+    n entries (split into chunks by the solves)."""
+    rng = np.random.default_rng(seed)
+    a = np.concatenate([np.zeros(n - 1, np.int64), rng.integers(1, n, 2 * n)])
+    b = np.concatenate([np.arange(1, n), rng.integers(1, n, 2 * n)])
+    keep = a != b
+    lo = np.minimum(a[keep], b[keep]); hi = np.maximum(a[keep], b[keep])
+    key = np.unique(lo * n + hi)
+    A = W.laplacian_from_edges(n, key // n, key % n, rng.uniform(0.5, 2.0, len(key)),
+                               excess=rng.uniform(0.0, 0.1, n))
+    perm = np.concatenate([rng.permutation(np.arange(1, n)), [0]]).astype(np.int32)
+    return A, perm, W.gaussian_rhs(n, 1, seed + 1, center=False)
+
+
+def _relres(A, x, b):
+    import scipy.sparse as sp
+    M = sp.csc_matrix((A.val, A.rowind, A.colptr), shape=(A.n, A.n))
+    return np.linalg.norm(b - M @ x) / np.linalg.norm(b)
+
+
+def test_pcg_many_thread_path_matches_single_calls(P, monkeypatch):
+    """With the per-system worker threads (PARAC_PCG_MANY=threads) every
+    system's result is bit-identical to its own parac_pcg call (host and device
+    right-hand sides)."""
     import torch
+    monkeypatch.setenv("PARAC_PCG_MANY", "threads")
     batch = W.sddm_batch(12, nmin=500, nmax=20000, seed=13)
     systems = [(A.n, A.colptr, A.rowind, A.val, perm) for (A, perm, b) in batch]
     Gs = P.parac_factor_many(systems, seed=3)
@@ -305,5 +327,50 @@ def test_pcg_many_matches_single_calls(P):
         x1, it1, rr1, _ = P.parac_pcg(G, A.n, None, None, None, b, tol=1e-8, maxit=500)
         assert it1[0] == its[i] == itd[i] and rr1[0] == rrs[i]
         assert np.array_equal(x1, xs[i]) and np.array_equal(x1, xd[i].cpu().numpy())
+    for G in Gs:
+        G.free()
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_pcg_many_batched(P, prec):
+    """The batched PCG (all systems as one block-diagonal system, levels
+    interleaved in one schedule, per-system scalars): each system converges to
+    the tolerance (true residual recomputed here), within one iteration of its
+    own parac_pcg call (the systems' preconditioner applies are the same
+    arithmetic; only the dot products' reduction order differs), and the
+    result does not depend on where the right-hand sides live.  The batch
+    includes a system with a split factor row (hub) and mixes sizes."""
+    import torch
+    batch = W.sddm_batch(11, nmin=300, nmax=30000, seed=17)
+    batch.append(_hub_system(40000, 5))
+    systems = [(A.n, A.colptr, A.rowind, A.val, perm) for (A, perm, b) in batch]
+    Gs = P.parac_factor_many(systems, seed=9, opts=P.parac_opts_default(g_precision=prec))
+    bs = [b for (A, perm, b) in batch]
+    xs, its, rrs, status = P.parac_pcg_many(Gs, bs, tol=1e-8, maxit=800)
+    assert status == "PARAC_OK" and np.all(rrs <= 1e-8)
+    xd, itd, rrd, _ = P.parac_pcg_many(Gs, [torch.from_numpy(b).cuda() for b in bs], tol=1e-8, maxit=800)
+    for i, ((A, perm, b), G) in enumerate(zip(batch, Gs)):
+        assert np.array_equal(xs[i], xd[i].cpu().numpy()) and its[i] == itd[i] and rrs[i] == rrd[i]
+        assert _relres(A, xs[i], b) <= 1.0001e-8
+        assert abs(_relres(A, xs[i], b) - rrs[i]) <= 1e-3 * rrs[i] + 1e-14
+        x1, it1, rr1, _ = P.parac_pcg(G, A.n, None, None, None, b, tol=1e-8, maxit=800)
+        assert abs(int(it1[0]) - int(its[i])) <= 1
+        assert np.linalg.norm(x1 - xs[i]) <= 1e-5 * np.linalg.norm(x1)
+    for G in Gs:
+        G.free()
+
+
+def test_pcg_many_batched_maxit(P):
+    """A batched run stopped by maxit reports PARAC_ENOCONV with every system's
+    iterations (= maxit unless it converged first) and true residual written."""
+    batch = W.sddm_batch(6, nmin=2000, nmax=20000, seed=19)
+    systems = [(A.n, A.colptr, A.rowind, A.val, perm) for (A, perm, b) in batch]
+    Gs = P.parac_factor_many(systems, seed=4)
+    bs = [b for (A, perm, b) in batch]
+    xs, its, rrs, status = P.parac_pcg_many(Gs, bs, tol=1e-12, maxit=3)
+    assert status == "PARAC_ENOCONV"
+    for i, (A, perm, b) in enumerate(batch):
+        assert its[i] == 3
+        assert abs(_relres(A, xs[i], b) - rrs[i]) <= 1e-6 * rrs[i]
     for G in Gs:
         G.free()
