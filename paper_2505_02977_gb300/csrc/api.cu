@@ -1587,8 +1587,12 @@ parac_status pcg_batch(int32_t count, const parac_factor_t *G, const double *con
         bw.push_back({off[(size_t)i], h->lstart, cp});
     }
     CK(cudaStreamSynchronize(st));
-    const GroupTable gf = batch_groups(fw, n, false, SOLVE_WARPS, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
-    const GroupTable gb = batch_groups(bw, n, true, SOLVE_WARPS, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
+    int lanes = 32;
+    if (const char *e = getenv("PARAC_TRSV_LANES")) lanes = atoi(e);
+    if (lanes != 4 && lanes != 8 && lanes != 16) lanes = 32;
+    const int rows_per_group = SOLVE_WARPS * (32 / lanes);
+    const GroupTable gf = batch_groups(fw, n, false, rows_per_group, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
+    const GroupTable gb = batch_groups(bw, n, true, rows_per_group, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
     R.gt_f = dalloc<int32_t>(std::max<size_t>(gf.g.size(), 4), st);
     R.gt_b = dalloc<int32_t>(std::max<size_t>(gb.g.size(), 4), st);
     CK(cudaMemcpyAsync(R.gt_f.p, gf.g.data(), 4 * gf.g.size(), cudaMemcpyHostToDevice, st));
@@ -1633,13 +1637,14 @@ parac_status pcg_batch(int32_t count, const parac_factor_t *G, const double *con
     A.Dinv = R.Dinv.as<double>(); A.operm = R.operm.as<int32_t>();
     A.prec = prec;
     A.lanes_spmv = lanes_for((double)nnzL / (double)n);
-    A.lanes_trsv = 32;
+    A.lanes_trsv = lanes;
     A.trsv_warps = SOLVE_WARPS;
     int bps = 0;
-    trsv_configure(32, SOLVE_WARPS, &bps, prec);
+    trsv_configure(lanes, SOLVE_WARPS, &bps, prec);
     const int64_t max_blocks = (int64_t)num_sms() * std::max(bps, 1);   // all co-resident
-    const int64_t want = (2 * n / std::max(depth, 1) + SOLVE_WARPS - 1) / SOLVE_WARPS;
+    const int64_t want = (2 * n / std::max(depth, 1) + rows_per_group - 1) / rows_per_group;
     int64_t tb = std::max<int64_t>(std::min<int64_t>(num_sms(), max_blocks), std::min<int64_t>(max_blocks, want));
+    if (const char *e = getenv("PARAC_TRSV_BLOCKS")) tb = std::max<int64_t>(1, std::min<int64_t>(max_blocks, atoll(e)));
     tb = std::min<int64_t>(tb, std::max<int64_t>(std::max(gf.ngroups, gb.ngroups), 1));
     A.trsv_blocks = (int32_t)tb;
     CK(set_poll_backoff(poll_ns_default()));

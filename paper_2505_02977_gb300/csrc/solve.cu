@@ -402,24 +402,26 @@ struct Grp {
     int32_t kind, arg, slot;
 };
 
-__device__ __forceinline__ Grp group_of(int64_t g, int64_t ngroups, const int4 *gt, int32_t n, int rows_per_group,
-                                        int my, bool rev)
+// Table entry of group g: from the table, or the fixed group of
+// rows_per_group consecutive positions; past the end, an empty group.
+__device__ __forceinline__ int4 group_entry(int64_t g, int64_t ngroups, const int4 *gt, int32_t n, int rows_per_group)
 {
-    Grp r{-1, GK_ROWS, 0, 0};
-    if (g >= ngroups) return r;
-    if (gt) {
-        const int4 q = gt[g];
-        r.kind = q.y; r.arg = q.z; r.slot = q.w;
-        if (q.y == GK_ROWS) {
-            const int64_t kk = (int64_t)q.x + my;
-            r.j = my < q.z ? (rev ? (int64_t)n - 1 - kk : kk) : -1;
-        } else {
-            r.j = rev ? (int64_t)n - 1 - q.x : (int64_t)q.x;
-        }
-        return r;
+    if (g >= ngroups) return make_int4(0, GK_ROWS, 0, 0);
+    if (gt) return __ldg(gt + g);
+    const int64_t k0 = g * rows_per_group;
+    const int64_t cnt = (int64_t)n - k0 < rows_per_group ? (int64_t)n - k0 : rows_per_group;
+    return make_int4((int32_t)k0, GK_ROWS, (int32_t)cnt, 0);
+}
+
+__device__ __forceinline__ Grp group_decode(int4 t, int32_t n, int my, bool rev)
+{
+    Grp r{-1, t.y, t.z, t.w};
+    if (t.y == GK_ROWS) {
+        const int64_t kk = (int64_t)t.x + my;
+        r.j = my < t.z ? (rev ? (int64_t)n - 1 - kk : kk) : -1;
+    } else {
+        r.j = rev ? (int64_t)n - 1 - t.x : (int64_t)t.x;
     }
-    const int64_t kk = g * rows_per_group + my;
-    r.j = kk < n ? (rev ? (int64_t)n - 1 - kk : kk) : -1;
     return r;
 }
 
@@ -458,6 +460,13 @@ __device__ __forceinline__ XT combine_parts(const Grp &q, XT *part, long long sp
 
 // Forward: y[j] = rhs[operm[j]] - sum_{c<j} F(j,c) y[c] over CSR row j; also
 // resets the backward unknown z[j] to the sentinel.
+//
+// Loads are pipelined over a lane group's successive groups g, g+G, g+2G,
+// g+3G (G = gridDim.x): while row g waits for its unknowns, the lanes fetch
+// the indices and values of row g+G, the bounds (and operm) of row g+2G and
+// the table entry of group g+3G, so each load is issued a step before its
+// consumer needs it.  (Unrolling the loop by two over two register sets that
+// swap roles was measured slower: more registers, no fewer stalls.)
 template <int S, typename VT, typename XT>
 __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, const VT *v, const int32_t *operm,
                            const double *rhs, XT *y, XT *zreset, const int4 *gt, int32_t ngs, XT *part,
@@ -471,25 +480,47 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
     const int rows_per_group = (blockDim.x / 32) * (32 / S);
     const int my = (threadIdx.x >> 5) * (32 / S) + sub;
     const int64_t ngroups = gt ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
+    const int64_t G = gridDim.x;
+    auto bounds = [&](const Grp &r, int64_t &bb, int64_t &ee, int32_t &o) {
+        if (r.kind == GK_ROWS && r.j >= 0) {
+            bb = rp[r.j]; ee = rp[r.j + 1];
+            if (sl == 0) o = operm[r.j];
+        }
+    };
+    auto data = [&](const Grp &r, int64_t bb, int64_t ee, int32_t o, double &rr, int32_t (&c)[RPF], VT (&w)[RPF]) {
+        if (r.kind == GK_ROWS && r.j >= 0) {
+            if (sl == 0) rr = rhs[o];
+            fetch_chunk<S, false, VT>(bb, ee, sl, ci, v, c, w);
+        }
+    };
     int64_t g = blockIdx.x;
-    Grp q = group_of(g, ngroups, gt, n, rows_per_group, my, false);
-    int64_t b = 0, e = 0;
+    Grp q = group_decode(group_entry(g, ngroups, gt, n, rows_per_group), n, my, false);
+    Grp q1 = group_decode(group_entry(g + G, ngroups, gt, n, rows_per_group), n, my, false);
+    int4 t2 = group_entry(g + 2 * G, ngroups, gt, n, rows_per_group);
+    int64_t b = 0, e = 0, b1 = 0, e1 = 0;
+    int32_t o = 0, o1 = 0;
     double rj = 0.0;
     int32_t cc[RPF];
     VT vv[RPF];
     XT xx[RPF];
-    auto fetch = [&](const Grp &r, int64_t &bb, int64_t &ee, double &rr, int32_t (&c)[RPF], VT (&w)[RPF]) {
-        if (r.kind == GK_ROWS && r.j >= 0) {
-            bb = rp[r.j]; ee = rp[r.j + 1];
-            if (sl == 0) rr = rhs[operm[r.j]];
-            fetch_chunk<S, false, VT>(bb, ee, sl, ci, v, c, w);
-        }
-    };
-    fetch(q, b, e, rj, cc, vv);
+    bounds(q, b, e, o);
+    bounds(q1, b1, e1, o1);
+    data(q, b, e, o, rj, cc, vv);
     while (g < ngroups) {
-        const int64_t gn = g + gridDim.x;
-        if (q.kind != GK_ROWS) {                      // block-wide group (block-uniform branch)
-            const int64_t j = q.j;
+        const int64_t j = q.j;
+        const bool rows = q.kind == GK_ROWS;
+        if (rows && j >= 0) issue_x(y, cc, xx);
+        // advance the pipeline: data of g+G, bounds of g+2G, entry of g+3G
+        int32_t ccn[RPF];
+        VT vvn[RPF];
+        double rjn = 0.0;
+        data(q1, b1, e1, o1, rjn, ccn, vvn);
+        const Grp q2 = group_decode(t2, n, my, false);
+        int64_t b2 = 0, e2 = 0;
+        int32_t o2 = 0;
+        bounds(q2, b2, e2, o2);
+        const int4 t3 = group_entry(g + 3 * G, ngroups, gt, n, rows_per_group);
+        if (!rows) {                                  // block-wide group (block-uniform branch)
             if (q.kind == GK_COMBINE) {
                 if (threadIdx.x == 0) {
                     const XT sum = combine_parts(q, part, spin_limit, status);
@@ -508,20 +539,7 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
                 }
             }
             __syncthreads();
-            g = gn;
-            q = group_of(g, ngroups, gt, n, rows_per_group, my, false);
-            fetch(q, b, e, rj, cc, vv);
-            continue;
-        }
-        const int64_t j = q.j;
-        if (j >= 0) issue_x(y, cc, xx);
-        const Grp qn = group_of(gn, ngroups, gt, n, rows_per_group, my, false);
-        int64_t bn = 0, en = 0;
-        double rjn = 0.0;
-        int32_t ccn[RPF];
-        VT vvn[RPF];
-        fetch(qn, bn, en, rjn, ccn, vvn);
-        if (j >= 0) {
+        } else if (j >= 0) {
             XT acc = 0;
             bool ok = finish_chunk<VT, XT>(y, cc, vv, xx, acc, spin_limit, status);
             if (ok && e - b > (int64_t)RPF * S)
@@ -534,16 +552,20 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
                 st_pub(y + j, to_x<XT>(rj) - acc);
             }
         }
-        g = gn; q = qn; b = bn; e = en; rj = rjn;
+        g += G;
+        q = q1; b = b1; e = e1; rj = rjn;
 #pragma unroll
         for (int r = 0; r < RPF; ++r) { cc[r] = ccn[r]; vv[r] = vvn[r]; }
+        q1 = q2; b1 = b2; e1 = e2; o1 = o2;
+        t2 = t3;
     }
 }
 
 // Backward: z[j] = y[j] Dinv[j] - sum_{i>j} F(i,j) z[i] over CSC column j, in
 // decreasing position order, walking each column from its last entry (whose
 // unknown was published first); writes zout[operm[j]], resets y[j] to the
-// sentinel, and accumulates r_orig . z into the block partial.
+// sentinel, and accumulates r_orig . z into the block partial.  Loads are
+// pipelined as in the forward solve.
 template <int S, typename VT, typename XT>
 __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, const VT *v, const double *Dinv,
                            const int32_t *operm, XT *y, XT *z, double *zout, const double *r_orig, double *partial,
@@ -558,23 +580,20 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
     const int rows_per_group = (blockDim.x / 32) * (32 / S);
     const int my = (threadIdx.x >> 5) * (32 / S) + sub;
     const int64_t ngroups = gt ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
+    const int64_t G = gridDim.x;
     double dotacc = 0.0;
-    int64_t g = blockIdx.x;
-    Grp q = group_of(g, ngroups, gt, n, rows_per_group, my, true);
-    int64_t b = 0, e = 0;
-    XT yj = 0;
-    double dj = 0.0, rj = 0.0;
-    int32_t o = 0;
-    int32_t cc[RPF];
-    VT vv[RPF];
-    XT xx[RPF];
-    auto fetch = [&](const Grp &r, int64_t &bb, int64_t &ee, XT &yv, double &dv, int32_t &ov, double &rv,
-                     int32_t (&c)[RPF], VT (&w)[RPF]) {
+    auto bounds = [&](const Grp &r, int64_t &bb, int64_t &ee, int32_t &o) {
         if (r.kind == GK_ROWS && r.j >= 0) {
             bb = cp[r.j]; ee = cp[r.j + 1];
+            if (sl == 0) o = operm[r.j];
+        }
+    };
+    auto data = [&](const Grp &r, int64_t bb, int64_t ee, int32_t o, XT &yv, double &dv, double &rv,
+                    int32_t (&c)[RPF], VT (&w)[RPF]) {
+        if (r.kind == GK_ROWS && r.j >= 0) {
             if (sl == 0) {
-                yv = y[r.j]; dv = Dinv[r.j]; ov = operm[r.j];
-                rv = r_orig ? r_orig[ov] : 0.0;
+                yv = y[r.j]; dv = Dinv[r.j];
+                rv = r_orig ? r_orig[o] : 0.0;
             }
             fetch_chunk<S, true, VT>(bb, ee, sl, ri, v, c, w);
         }
@@ -587,11 +606,35 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
         zout[ov] = (double)zj;
         dotacc += rv * (double)zj;
     };
-    fetch(q, b, e, yj, dj, o, rj, cc, vv);
+    int64_t g = blockIdx.x;
+    Grp q = group_decode(group_entry(g, ngroups, gt, n, rows_per_group), n, my, true);
+    Grp q1 = group_decode(group_entry(g + G, ngroups, gt, n, rows_per_group), n, my, true);
+    int4 t2 = group_entry(g + 2 * G, ngroups, gt, n, rows_per_group);
+    int64_t b = 0, e = 0, b1 = 0, e1 = 0;
+    int32_t o = 0, o1 = 0;
+    XT yj = 0;
+    double dj = 0.0, rj = 0.0;
+    int32_t cc[RPF];
+    VT vv[RPF];
+    XT xx[RPF];
+    bounds(q, b, e, o);
+    bounds(q1, b1, e1, o1);
+    data(q, b, e, o, yj, dj, rj, cc, vv);
     while (g < ngroups) {
-        const int64_t gn = g + gridDim.x;
-        if (q.kind != GK_ROWS) {                      // block-wide group (block-uniform branch)
-            const int64_t j = q.j;
+        const int64_t j = q.j;
+        const bool rows = q.kind == GK_ROWS;
+        if (rows && j >= 0) issue_x(z, cc, xx);
+        int32_t ccn[RPF];
+        VT vvn[RPF];
+        XT yjn = 0;
+        double djn = 0.0, rjn = 0.0;
+        data(q1, b1, e1, o1, yjn, djn, rjn, ccn, vvn);
+        const Grp q2 = group_decode(t2, n, my, true);
+        int64_t b2 = 0, e2 = 0;
+        int32_t o2 = 0;
+        bounds(q2, b2, e2, o2);
+        const int4 t3 = group_entry(g + 3 * G, ngroups, gt, n, rows_per_group);
+        if (!rows) {                                  // block-wide group (block-uniform branch)
             XT sum = 0;
             if (q.kind == GK_COMBINE) {
                 if (threadIdx.x == 0) sum = combine_parts(q, part, spin_limit, status);
@@ -607,22 +650,7 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
                 }
             }
             __syncthreads();
-            g = gn;
-            q = group_of(g, ngroups, gt, n, rows_per_group, my, true);
-            fetch(q, b, e, yj, dj, o, rj, cc, vv);
-            continue;
-        }
-        const int64_t j = q.j;
-        if (j >= 0) issue_x(z, cc, xx);
-        const Grp qn = group_of(gn, ngroups, gt, n, rows_per_group, my, true);
-        int64_t bn = 0, en = 0;
-        XT yjn = 0;
-        double djn = 0.0, rjn = 0.0;
-        int32_t on = 0;
-        int32_t ccn[RPF];
-        VT vvn[RPF];
-        fetch(qn, bn, en, yjn, djn, on, rjn, ccn, vvn);
-        if (j >= 0) {
+        } else if (j >= 0) {
             XT acc = 0;
             bool ok = finish_chunk<VT, XT>(z, cc, vv, xx, acc, spin_limit, status);
             if (ok && e - b > (int64_t)RPF * S)
@@ -632,9 +660,12 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
             for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
             if (sl == 0) publish(j, yj, dj, o, rj, acc);
         }
-        g = gn; q = qn; b = bn; e = en; yj = yjn; dj = djn; o = on; rj = rjn;
+        g += G;
+        q = q1; b = b1; e = e1; o = o1; yj = yjn; dj = djn; rj = rjn;
 #pragma unroll
         for (int r = 0; r < RPF; ++r) { cc[r] = ccn[r]; vv[r] = vvn[r]; }
+        q1 = q2; b1 = b2; e1 = e2; o1 = o2;
+        t2 = t3;
     }
     if (partial) {
         const double s = block_sum(dotacc);
@@ -673,8 +704,8 @@ cudaError_t apply_t(const SolveArgs &A, const VT *vr, const VT *vc, XT *y, XT *z
                     double *partial, const PcgState *st, cudaStream_t s)
 {
     const int threads = A.trsv_warps * 32;
-    // group tables apply to one row per warp only
-    const int4 *gf = S == 32 ? A.gt_f : nullptr, *gb = S == 32 ? A.gt_b : nullptr;
+    // a group table is built for the launch's rows per group (trsv_warps * 32 / S)
+    const int4 *gf = A.gt_f, *gb = A.gt_b;
     k_trsv_fwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Frp, A.Fcol, vr, A.operm, r, y, z, gf, A.ng_f,
                                                              (XT *)A.part_f, st, A.spin_limit, A.status);
     count_launches(1);
