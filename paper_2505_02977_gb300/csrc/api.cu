@@ -1472,7 +1472,7 @@ constexpr int64_t BATCH_CHUNK_ROWS = 4096;
 struct BatchRun {
     DBuf Lp, Li, Lv, Fcp, Frow, Fval, Frp, Fcol, Fvalr, Dinv, operm;
     DBuf gt_f, gt_b, part_f, part_b;
-    DBuf x, r, z, p, q, b, yl, zl, partials, sys, state, status, clo, csys, sys_c0, seg;
+    DBuf x, r, z, p, q, b, yl, zl, partials, sys, stop, state, status, clo, csys, sys_c0, seg;
 };
 
 unsigned poll_ns_default()
@@ -1583,14 +1583,13 @@ parac_status pcg_batch(int32_t count, const parac_factor_t *G, const double *con
             CK(cudaMemcpyAsync(cps.back().data(), h->Scp.p, 8 * ((size_t)h->n + 1), cudaMemcpyDeviceToHost, st));
             rp = &rps.back(); cp = &cps.back();
         }
-        fw.push_back({off[(size_t)i], h->lstart, rp});
-        bw.push_back({off[(size_t)i], h->lstart, cp});
+        fw.push_back({i, off[(size_t)i], h->lstart, rp});
+        bw.push_back({i, off[(size_t)i], h->lstart, cp});
     }
     CK(cudaStreamSynchronize(st));
-    int lanes = 32;
-    if (const char *e = getenv("PARAC_TRSV_LANES")) lanes = atoi(e);
-    if (lanes != 4 && lanes != 8 && lanes != 16) lanes = 32;
-    const int rows_per_group = SOLVE_WARPS * (32 / lanes);
+    // one row per warp (the stop-flag solves; sub-warp rows measured slower here)
+    const int lanes = 32;
+    const int rows_per_group = SOLVE_WARPS;
     const GroupTable gf = batch_groups(fw, n, false, rows_per_group, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
     const GroupTable gb = batch_groups(bw, n, true, rows_per_group, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
     R.gt_f = dalloc<int32_t>(std::max<size_t>(gf.g.size(), 4), st);
@@ -1620,6 +1619,7 @@ parac_status pcg_batch(int32_t count, const parac_factor_t *G, const double *con
     R.yl = DBuf(xs * (size_t)n, st); R.zl = DBuf(xs * (size_t)n, st);
     R.partials = dalloc<double>(3 * (size_t)std::max(nch, 1), st);
     R.sys = DBuf(sizeof(SysState) * (size_t)count, st);
+    R.stop = dalloc<int32_t>((size_t)count, st);
     R.state = DBuf(batch_state_bytes(), st);
     R.status = dalloc<int32_t>(1, st);
     CK(cudaMemsetAsync(R.status.p, 0, 4, st));
@@ -1640,7 +1640,7 @@ parac_status pcg_batch(int32_t count, const parac_factor_t *G, const double *con
     A.lanes_trsv = lanes;
     A.trsv_warps = SOLVE_WARPS;
     int bps = 0;
-    trsv_configure(lanes, SOLVE_WARPS, &bps, prec);
+    trsv_configure(lanes, SOLVE_WARPS, &bps, prec, true);
     const int64_t max_blocks = (int64_t)num_sms() * std::max(bps, 1);   // all co-resident
     const int64_t want = (2 * n / std::max(depth, 1) + rows_per_group - 1) / rows_per_group;
     int64_t tb = std::max<int64_t>(std::min<int64_t>(num_sms(), max_blocks), std::min<int64_t>(max_blocks, want));
@@ -1652,11 +1652,12 @@ parac_status pcg_batch(int32_t count, const parac_factor_t *G, const double *con
     A.status = R.status.as<int32_t>();
     A.gt_f = (const int4 *)R.gt_f.p; A.ng_f = gf.ngroups; A.part_f = R.part_f.p; A.nslot_f = gf.nslots;
     A.gt_b = (const int4 *)R.gt_b.p; A.ng_b = gb.ngroups; A.part_b = R.part_b.p; A.nslot_b = gb.nslots;
+    A.skip = R.stop.as<int32_t>();
     BatchBuffers B{};
     B.count = count; B.nchunks = nch;
     B.clo = R.clo.as<int64_t>(); B.csys = R.csys.as<int32_t>(); B.sys_c0 = R.sys_c0.as<int32_t>();
     B.x = R.x.as<double>(); B.r = R.r.as<double>(); B.z = R.z.as<double>(); B.p = R.p.as<double>();
-    B.q = R.q.as<double>(); B.b = R.b.as<double>();
+    B.q = R.q.as<double>(); B.b = R.b.as<double>(); B.stop = R.stop.as<int32_t>();
     if (prec == 32) { B.solve.yl32 = R.yl.as<float>(); B.solve.zl32 = R.zl.as<float>(); }
     else { B.solve.yl64 = R.yl.as<double>(); B.solve.zl64 = R.zl.as<double>(); }
     B.partials = R.partials.as<double>(); B.sys = R.sys.as<SysState>(); B.st = R.state.as<BatchState>();

@@ -124,8 +124,8 @@ __device__ __forceinline__ double sys_sum(const double *partial, const int32_t *
     return acc;
 }
 
-__global__ void k_sinit(int32_t count, const int32_t *c0, SysState *sys, const double *pbb, const double *prz,
-                        double tol, int32_t maxit)
+__global__ void k_sinit(int32_t count, const int32_t *c0, SysState *sys, int32_t *stop, const double *pbb,
+                        const double *prz, double tol, int32_t maxit)
 {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < count; s += gridDim.x * blockDim.x) {
         SysState &y = sys[s];
@@ -135,6 +135,7 @@ __global__ void k_sinit(int32_t count, const int32_t *c0, SysState *sys, const d
         y.iters = 0;
         y.converged = bb == 0.0;
         y.done = bb == 0.0 || maxit <= 0;
+        stop[s] = y.done;
     }
 }
 
@@ -147,7 +148,8 @@ __global__ void k_salpha(int32_t count, const int32_t *c0, SysState *sys, const 
     }
 }
 
-__global__ void k_scheck(int32_t count, const int32_t *c0, SysState *sys, const double *prr, const BatchState *st)
+__global__ void k_scheck(int32_t count, const int32_t *c0, SysState *sys, int32_t *stop, const double *prr,
+                         const BatchState *st)
 {
     if (st->gate.done) return;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < count; s += gridDim.x * blockDim.x) {
@@ -158,6 +160,7 @@ __global__ void k_scheck(int32_t count, const int32_t *c0, SysState *sys, const 
         y.iters += 1;
         if (rr <= y.tol2bb) { y.done = 1; y.converged = 1; }
         else if (y.iters >= st->maxit) y.done = 1;
+        stop[s] = y.done;
     }
 }
 
@@ -180,12 +183,12 @@ __global__ void k_strue(int32_t count, const int32_t *c0, SysState *sys, const d
 }
 
 // reopen the systems whose true residual failed the test (recurrence drift)
-__global__ void k_sreopen(int32_t count, SysState *sys, const BatchState *st)
+__global__ void k_sreopen(int32_t count, SysState *sys, int32_t *stop, const BatchState *st)
 {
     const int32_t maxit = st->maxit;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < count; s += gridDim.x * blockDim.x) {
         SysState &y = sys[s];
-        if (y.converged && !(y.true_rr <= y.tol2bb) && y.iters < maxit) { y.converged = 0; y.done = 0; }
+        if (y.converged && !(y.true_rr <= y.tol2bb) && y.iters < maxit) { y.converged = 0; y.done = 0; stop[s] = 0; }
     }
 }
 
@@ -220,6 +223,8 @@ cudaError_t spcg_init(const SolveArgs &A, const BatchBuffers &B, double tol, int
 {
     double *pbb = B.partials, *prz = B.partials + B.nchunks;
     k_sstate<<<1, 1, 0, s>>>(B.st, B.count, maxit);
+    cudaError_t e0 = cudaMemsetAsync(B.stop, 0, sizeof(int32_t) * (size_t)B.count, s);
+    if (e0 != cudaSuccess) return e0;
     k_cinit<<<cgrid(B.nchunks), BT, 0, s>>>(B.nchunks, B.clo, B.b, B.x, B.r, pbb);
     count_launches(2);
     cudaError_t e = solve_fill_sentinels(A, B.solve, s);
@@ -227,7 +232,7 @@ cudaError_t spcg_init(const SolveArgs &A, const BatchBuffers &B, double tol, int
     e = solve_apply(A, B.solve, B.r, B.z, nullptr, s);
     if (e != cudaSuccess) return e;
     k_cdot<<<cgrid(B.nchunks), BT, 0, s>>>(B.nchunks, B.clo, B.r, B.z, prz, nullptr);
-    k_sinit<<<sgrid(B.count), BT, 0, s>>>(B.count, B.sys_c0, B.sys, pbb, prz, tol, maxit);
+    k_sinit<<<sgrid(B.count), BT, 0, s>>>(B.count, B.sys_c0, B.sys, B.stop, pbb, prz, tol, maxit);
     k_sall<<<1, BT, 0, s>>>(B.count, B.sys, B.st);
     k_ccopy<<<cgrid(B.nchunks), BT, 0, s>>>(A.n, B.z, B.p);
     count_launches(4);
@@ -243,7 +248,7 @@ cudaError_t spcg_iteration(const SolveArgs &A, const BatchBuffers &B, cudaStream
     k_cdot<<<cgrid(B.nchunks), BT, 0, s>>>(B.nchunks, B.clo, B.p, B.q, ppq, B.st);
     k_salpha<<<sgrid(B.count), BT, 0, s>>>(B.count, B.sys_c0, B.sys, ppq, B.st);
     k_cupdate_xr<<<cgrid(B.nchunks), BT, 0, s>>>(B.nchunks, B.clo, B.csys, B.sys, B.x, B.r, B.p, B.q, prr, B.st);
-    k_scheck<<<sgrid(B.count), BT, 0, s>>>(B.count, B.sys_c0, B.sys, prr, B.st);
+    k_scheck<<<sgrid(B.count), BT, 0, s>>>(B.count, B.sys_c0, B.sys, B.stop, prr, B.st);
     k_sall<<<1, BT, 0, s>>>(B.count, B.sys, B.st);
     count_launches(5);
     e = solve_apply(A, B.solve, B.r, B.z, gate, s);
@@ -271,7 +276,7 @@ cudaError_t spcg_true_residual(const SolveArgs &A, const BatchBuffers &B, cudaSt
 cudaError_t spcg_reopen(const SolveArgs &A, const BatchBuffers &B, cudaStream_t s)
 {
     double *prz = B.partials + 2 * (size_t)B.nchunks;
-    k_sreopen<<<sgrid(B.count), BT, 0, s>>>(B.count, B.sys, B.st);
+    k_sreopen<<<sgrid(B.count), BT, 0, s>>>(B.count, B.sys, B.stop, B.st);
     k_sall<<<1, BT, 0, s>>>(B.count, B.sys, B.st);
     count_launches(2);
     cudaError_t e = solve_apply(A, B.solve, B.r, B.z, &B.st->gate, s);
@@ -322,7 +327,9 @@ cudaError_t launch_cat(const CatSeg *seg, int32_t nseg, int64_t max_count, int e
 // dependencies sit at strictly lower levels going forward and strictly higher
 // ones going back).  Each (level, system) range is cut into GK_ROWS groups of
 // up to `warps` consecutive positions; a row longer than long_row entries
-// (ptr given) gets the block-wide kinds of row_groups.
+// (ptr given) gets the block-wide kinds of row_groups.  Every entry's kind
+// carries its system (kind | sys << GK_SYS_SHIFT), so that the solves can
+// skip the groups of systems that stopped.
 GroupTable batch_groups(const std::vector<BatchSysLevels> &sys, int64_t n_tot, bool descending, int warps,
                         int long_row, int split_row, int chunk)
 {
@@ -334,14 +341,16 @@ GroupTable batch_groups(const std::vector<BatchSysLevels> &sys, int64_t n_tot, b
         approx += (y.lstart.empty() ? 0 : y.lstart.back()) / std::max(1, warps) + (int64_t)y.lstart.size();
     }
     t.g.reserve((size_t)(4 * approx));
+    int32_t sysbits = 0;
     auto push = [&](int64_t start, int32_t kind, int32_t arg, int32_t slot) {
-        t.g.push_back((int32_t)start); t.g.push_back(kind); t.g.push_back(arg); t.g.push_back(slot);
+        t.g.push_back((int32_t)start); t.g.push_back(kind | sysbits); t.g.push_back(arg); t.g.push_back(slot);
         ++t.ngroups;
     };
     for (int32_t li = 0; li < depth; ++li) {
         const int32_t l = descending ? depth - 1 - li : li;
         for (const auto &y : sys) {
             if (l + 1 >= (int32_t)y.lstart.size()) continue;
+            sysbits = y.sys << GK_SYS_SHIFT;
             const int64_t a = y.off + y.lstart[(size_t)l], b = y.off + y.lstart[(size_t)l + 1];
             // walk positions kk of this range: forward j = kk, backward j = n_tot - 1 - kk
             const int64_t k0 = descending ? n_tot - b : a, k1 = descending ? n_tot - a : b;

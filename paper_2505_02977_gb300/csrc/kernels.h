@@ -127,6 +127,10 @@ struct SolveArgs {
     int32_t ng_f, ng_b;
     void *part_f, *part_b;        // partial sums of split rows (XT), nslot_f / nslot_b
     int32_t nslot_f, nslot_b;
+    // batched solves: stop flag of each system (groups of a stopped system are
+    // skipped); the tables then carry the system in the kind's upper bits and
+    // the solves run one row per warp.  nullptr: none.
+    const int32_t *skip;
 };
 
 // Schedule of the solves: groups in position order, 4 ints each (first
@@ -136,6 +140,7 @@ struct SolveArgs {
 // slot `slot`; GK_COMBINE: the row's arg partials from `slot` on, summed in
 // order, finish the row.  Chunks come before their combine.
 enum : int32_t { GK_ROWS = 0, GK_SHARED = 1, GK_CHUNK = 2, GK_COMBINE = 3 };
+constexpr int32_t GK_KIND_MASK = 0xff, GK_SYS_SHIFT = 8;   // kind | system << GK_SYS_SHIFT
 struct GroupTable {
     std::vector<int32_t> g;       // 4 * ngroups
     int32_t ngroups = 0, nslots = 0;
@@ -229,6 +234,7 @@ struct BatchBuffers {
     const int32_t *csys;          // [nchunks] system of each chunk
     const int32_t *sys_c0;        // [count + 1] first chunk of each system
     double *x, *r, *z, *p, *q, *b;   // [n] concatenated vectors
+    int32_t *stop;                // [count] 1 once a system stopped (read by the solves)
     PcgBuffers solve;             // yl/zl work of the solves
     double *partials;             // [3 * nchunks]
     SysState *sys;                // [count]
@@ -249,6 +255,7 @@ cudaError_t launch_cat(const CatSeg *seg, int32_t nseg, int64_t max_count, int e
 // starts (positions, depth + 1 entries) and, for systems with rows longer than
 // the block-wide threshold, its row (forward) or column (backward) pointers
 struct BatchSysLevels {
+    int32_t sys;
     int64_t off;
     std::vector<int64_t> lstart;
     const std::vector<int64_t> *ptr;
@@ -260,6 +267,6 @@ GroupTable batch_groups(const std::vector<BatchSysLevels> &sys, int64_t n_tot, b
 constexpr int NOALLOC_MAX_N = 1 << 18;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 cudaError_t precond_apply_noalloc(const SolveArgs &A, const double *r, double *z, cudaStream_t st);
-int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec);
+int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec, bool skip = false);
 
 }  // namespace parac

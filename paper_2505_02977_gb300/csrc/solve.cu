@@ -15,6 +15,7 @@
 // earlier position, so the smallest unfinished group never waits on an
 // unfinished group and the solve always progresses; every wait is bounded by
 // the spin limit.
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -400,6 +401,7 @@ __device__ __forceinline__ bool finish_chunk(const XT *x, const int32_t (&cc)[RP
 struct Grp {
     int64_t j;
     int32_t kind, arg, slot;
+    int32_t aux;              // SKIP solves: the group's system, then its stop flag
 };
 
 // Table entry of group g: from the table, or the fixed group of
@@ -415,8 +417,8 @@ __device__ __forceinline__ int4 group_entry(int64_t g, int64_t ngroups, const in
 
 __device__ __forceinline__ Grp group_decode(int4 t, int32_t n, int my, bool rev)
 {
-    Grp r{-1, t.y, t.z, t.w};
-    if (t.y == GK_ROWS) {
+    Grp r{-1, t.y & GK_KIND_MASK, t.z, t.w, t.y >> GK_SYS_SHIFT};
+    if (r.kind == GK_ROWS) {
         const int64_t kk = (int64_t)t.x + my;
         r.j = my < t.z ? (rev ? (int64_t)n - 1 - kk : kk) : -1;
     } else {
@@ -467,10 +469,10 @@ __device__ __forceinline__ XT combine_parts(const Grp &q, XT *part, long long sp
 // the table entry of group g+3G, so each load is issued a step before its
 // consumer needs it.  (Unrolling the loop by two over two register sets that
 // swap roles was measured slower: more registers, no fewer stalls.)
-template <int S, typename VT, typename XT>
+template <int S, typename VT, typename XT, bool SKIP>
 __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, const VT *v, const int32_t *operm,
                            const double *rhs, XT *y, XT *zreset, const int4 *gt, int32_t ngs, XT *part,
-                           const PcgState *st, long long spin_limit, int32_t *status)
+                           const PcgState *st, long long spin_limit, int32_t *status, const int32_t *skip)
 {
     __shared__ XT red[32];
     if (st && st->done) return;
@@ -481,13 +483,16 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
     const int my = (threadIdx.x >> 5) * (32 / S) + sub;
     const int64_t ngroups = gt ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
     const int64_t G = gridDim.x;
-    auto bounds = [&](const Grp &r, int64_t &bb, int64_t &ee, int32_t &o) {
+    auto bounds = [&](Grp &r, int64_t &bb, int64_t &ee, int32_t &o) {
+        if constexpr (SKIP) r.aux = skip[r.aux];
         if (r.kind == GK_ROWS && r.j >= 0) {
             bb = rp[r.j]; ee = rp[r.j + 1];
             if (sl == 0) o = operm[r.j];
         }
     };
-    auto data = [&](const Grp &r, int64_t bb, int64_t ee, int32_t o, double &rr, int32_t (&c)[RPF], VT (&w)[RPF]) {
+    auto data = [&](Grp &r, int64_t bb, int64_t ee, int32_t o, double &rr, int32_t (&c)[RPF], VT (&w)[RPF]) {
+        if constexpr (SKIP)
+            if (r.aux) { r.kind = GK_ROWS; r.j = -1; }      // a stopped system's group: nothing to do
         if (r.kind == GK_ROWS && r.j >= 0) {
             if (sl == 0) rr = rhs[o];
             fetch_chunk<S, false, VT>(bb, ee, sl, ci, v, c, w);
@@ -515,7 +520,7 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
         VT vvn[RPF];
         double rjn = 0.0;
         data(q1, b1, e1, o1, rjn, ccn, vvn);
-        const Grp q2 = group_decode(t2, n, my, false);
+        Grp q2 = group_decode(t2, n, my, false);
         int64_t b2 = 0, e2 = 0;
         int32_t o2 = 0;
         bounds(q2, b2, e2, o2);
@@ -566,11 +571,11 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
 // unknown was published first); writes zout[operm[j]], resets y[j] to the
 // sentinel, and accumulates r_orig . z into the block partial.  Loads are
 // pipelined as in the forward solve.
-template <int S, typename VT, typename XT>
+template <int S, typename VT, typename XT, bool SKIP>
 __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, const VT *v, const double *Dinv,
                            const int32_t *operm, XT *y, XT *z, double *zout, const double *r_orig, double *partial,
                            const int4 *gt, int32_t ngs, XT *part, const PcgState *st, long long spin_limit,
-                           int32_t *status)
+                           int32_t *status, const int32_t *skip)
 {
     __shared__ XT red[32];
     if (st && st->done) return;
@@ -582,14 +587,17 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
     const int64_t ngroups = gt ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
     const int64_t G = gridDim.x;
     double dotacc = 0.0;
-    auto bounds = [&](const Grp &r, int64_t &bb, int64_t &ee, int32_t &o) {
+    auto bounds = [&](Grp &r, int64_t &bb, int64_t &ee, int32_t &o) {
+        if constexpr (SKIP) r.aux = skip[r.aux];
         if (r.kind == GK_ROWS && r.j >= 0) {
             bb = cp[r.j]; ee = cp[r.j + 1];
             if (sl == 0) o = operm[r.j];
         }
     };
-    auto data = [&](const Grp &r, int64_t bb, int64_t ee, int32_t o, XT &yv, double &dv, double &rv,
+    auto data = [&](Grp &r, int64_t bb, int64_t ee, int32_t o, XT &yv, double &dv, double &rv,
                     int32_t (&c)[RPF], VT (&w)[RPF]) {
+        if constexpr (SKIP)
+            if (r.aux) { r.kind = GK_ROWS; r.j = -1; }
         if (r.kind == GK_ROWS && r.j >= 0) {
             if (sl == 0) {
                 yv = y[r.j]; dv = Dinv[r.j];
@@ -629,7 +637,7 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
         XT yjn = 0;
         double djn = 0.0, rjn = 0.0;
         data(q1, b1, e1, o1, yjn, djn, rjn, ccn, vvn);
-        const Grp q2 = group_decode(t2, n, my, true);
+        Grp q2 = group_decode(t2, n, my, true);
         int64_t b2 = 0, e2 = 0;
         int32_t o2 = 0;
         bounds(q2, b2, e2, o2);
@@ -706,12 +714,26 @@ cudaError_t apply_t(const SolveArgs &A, const VT *vr, const VT *vc, XT *y, XT *z
     const int threads = A.trsv_warps * 32;
     // a group table is built for the launch's rows per group (trsv_warps * 32 / S)
     const int4 *gf = A.gt_f, *gb = A.gt_b;
-    k_trsv_fwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Frp, A.Fcol, vr, A.operm, r, y, z, gf, A.ng_f,
-                                                             (XT *)A.part_f, st, A.spin_limit, A.status);
+    if constexpr (S == 32) {
+        if (A.skip) {                 // per-system stop flags (batched solves, one row per warp)
+            k_trsv_fwd<S, VT, XT, true><<<A.trsv_blocks, threads, 0, s>>>(
+                A.n, A.Frp, A.Fcol, vr, A.operm, r, y, z, gf, A.ng_f, (XT *)A.part_f, st, A.spin_limit, A.status,
+                A.skip);
+            k_trsv_bwd<S, VT, XT, true><<<A.trsv_blocks, threads, 0, s>>>(
+                A.n, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z, zout, partial ? r : nullptr, partial, gb, A.ng_b,
+                (XT *)A.part_b, st, A.spin_limit, A.status, A.skip);
+            count_launches(2);
+            return cudaGetLastError();
+        }
+    }
+    k_trsv_fwd<S, VT, XT, false><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Frp, A.Fcol, vr, A.operm, r, y, z, gf,
+                                                                    A.ng_f, (XT *)A.part_f, st, A.spin_limit,
+                                                                    A.status, nullptr);
     count_launches(1);
-    k_trsv_bwd<S, VT, XT><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z,
-                                                             zout, partial ? r : nullptr, partial, gb, A.ng_b, (XT *)A.part_b, st,
-                                                             A.spin_limit, A.status);
+    k_trsv_bwd<S, VT, XT, false><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z,
+                                                                    zout, partial ? r : nullptr, partial, gb, A.ng_b,
+                                                                    (XT *)A.part_b, st, A.spin_limit, A.status,
+                                                                    nullptr);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -788,36 +810,42 @@ cudaError_t set_poll_backoff(unsigned max_ns)
     return e;
 }
 
-int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec)
+int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec, bool skip)
 {
     cudaError_t e;
     const int threads = warps * 32;
     switch (lanes) {
     case 4:
-        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<4, float, float>, threads, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<4, double, double>, threads, 0);
+        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<4, float, float, false>, threads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<4, double, double, false>, threads, 0);
         break;
     case 8:
-        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<8, float, float>, threads, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<8, double, double>, threads, 0);
+        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<8, float, float, false>, threads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<8, double, double, false>, threads, 0);
         break;
     case 16:
-        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<16, float, float>, threads, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<16, double, double>, threads, 0);
+        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<16, float, float, false>, threads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<16, double, double, false>, threads, 0);
         break;
     default:
-        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<32, float, float>, threads, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<32, double, double>, threads, 0);
+        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<32, float, float, false>, threads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<32, double, double, false>, threads, 0);
     }
     int b2 = 0;
     // the backward kernel must fit the same grid
     switch (lanes) {
-    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<4, float, float> : (const void *)k_trsv_bwd<4, double, double>, threads, 0); break;
-    case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<8, float, float> : (const void *)k_trsv_bwd<8, double, double>, threads, 0); break;
-    case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<16, float, float> : (const void *)k_trsv_bwd<16, double, double>, threads, 0); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<32, float, float> : (const void *)k_trsv_bwd<32, double, double>, threads, 0);
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<4, float, float, false> : (const void *)k_trsv_bwd<4, double, double, false>, threads, 0); break;
+    case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<8, float, float, false> : (const void *)k_trsv_bwd<8, double, double, false>, threads, 0); break;
+    case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<16, float, float, false> : (const void *)k_trsv_bwd<16, double, double, false>, threads, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<32, float, float, false> : (const void *)k_trsv_bwd<32, double, double, false>, threads, 0);
     }
     if (b2 < *blocks_per_sm) *blocks_per_sm = b2;
+    if (skip) {                       // the per-system stop-flag solves (one row per warp) are launched instead
+        int a = 0, c = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, prec == 32 ? (const void *)k_trsv_fwd<32, float, float, true> : (const void *)k_trsv_fwd<32, double, double, true>, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, prec == 32 ? (const void *)k_trsv_bwd<32, float, float, true> : (const void *)k_trsv_bwd<32, double, double, true>, threads, 0);
+        *blocks_per_sm = std::min(a, c);
+    }
     return e == cudaSuccess ? 0 : -1;
 }
 
