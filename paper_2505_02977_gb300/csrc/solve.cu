@@ -27,7 +27,7 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int VEC_THREADS = 256;
-__constant__ unsigned g_poll_max_ns = 256;   // cap of the polling back-off
+__constant__ unsigned g_poll_max_ns = 64;    // cap of the polling back-off
 
 __device__ __forceinline__ double sentinel64() { return __longlong_as_double((long long)0xfff7ffffffffffffull); }
 __device__ __forceinline__ float sentinel32() { return __int_as_float((int)0xffbfffffu); }
@@ -60,6 +60,13 @@ __device__ double block_sum(double v)
 }
 
 // ---------------------------------------------------------------- SpMV: y = L x (+ partial x.y)
+// S lanes per row; a lane group owns rows i, i + R, i + 2R, ... (R = lane
+// groups in the grid) and works SPMV_ROWS of them at a time, so that their
+// pointer, index/value and x loads are in flight together.  Each row's sum
+// is the same in any case: lane sl adds entries sl, sl + S, ... in order,
+// then the lanes' sums meet in a fixed shuffle tree.
+constexpr int SPMV_ROWS = 4;
+
 template <int S>
 __global__ void k_spmv(int32_t n, const int64_t *Lp, const int32_t *Li, const double *Lv, const double *x, double *y,
                        double *partial, const PcgState *st)
@@ -68,16 +75,45 @@ __global__ void k_spmv(int32_t n, const int64_t *Lp, const int32_t *Li, const do
     const unsigned lane = threadIdx.x & 31;
     const int sub = lane / S, sl = lane % S;
     const unsigned smask = (S == 32) ? FULL : (((1u << S) - 1u) << (sub * S));
-    const int64_t rows_per_iter = ((int64_t)gridDim.x * blockDim.x) / S;
+    const int64_t R = ((int64_t)gridDim.x * blockDim.x) / S;
     double dotacc = 0.0;
-    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / S; i < n; i += rows_per_iter) {
-        double acc = 0.0;
-        for (int64_t t = Lp[i] + sl; t < Lp[i + 1]; t += S) acc += Lv[t] * __ldg(x + Li[t]);
+    for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / S; i0 < n; i0 += SPMV_ROWS * R) {
+        int64_t b[SPMV_ROWS], e[SPMV_ROWS];
+        double acc[SPMV_ROWS];
+        int64_t len = 0;
 #pragma unroll
-        for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
-        if (sl == 0) {
-            y[i] = acc;
-            dotacc += acc * x[i];
+        for (int u = 0; u < SPMV_ROWS; ++u) {
+            const int64_t i = i0 + u * R;
+            b[u] = i < n ? Lp[i] : 0;
+            e[u] = i < n ? Lp[i + 1] : 0;
+            acc[u] = 0.0;
+            len = max(len, e[u] - b[u]);
+        }
+        for (int64_t k = sl; k < len; k += S) {
+            double vv[SPMV_ROWS], xv[SPMV_ROWS];
+            int32_t cc[SPMV_ROWS];
+#pragma unroll
+            for (int u = 0; u < SPMV_ROWS; ++u) {
+                const bool in = k < e[u] - b[u];
+                cc[u] = in ? Li[b[u] + k] : -1;
+                vv[u] = in ? Lv[b[u] + k] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < SPMV_ROWS; ++u) xv[u] = cc[u] >= 0 ? __ldg(x + cc[u]) : 0.0;
+#pragma unroll
+            for (int u = 0; u < SPMV_ROWS; ++u)
+                if (cc[u] >= 0) acc[u] += vv[u] * xv[u];
+        }
+#pragma unroll
+        for (int u = 0; u < SPMV_ROWS; ++u) {
+            double a = acc[u];
+#pragma unroll
+            for (int off = S / 2; off > 0; off >>= 1) a += __shfl_xor_sync(smask, a, off);
+            const int64_t i = i0 + u * R;
+            if (sl == 0 && i < n) {
+                y[i] = a;
+                dotacc += a * x[i];
+            }
         }
     }
     if (partial) {
