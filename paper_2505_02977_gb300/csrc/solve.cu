@@ -382,7 +382,7 @@ __device__ __forceinline__ XT block_row_sum(XT acc, XT *red)
 // LONG_ROW_SINGLE entries shared by every warp of the block (the rows that
 // collect the most fill, e.g. of hub vertices, would otherwise leave one warp
 // to walk them alone on the critical path).
-constexpr int RPF = 4;
+constexpr int RPF = 1;     // measured: 1 beats 2 and 4 (fewer instructions per row; long rows go on in dot_ready)
 
 template <int S, bool REV, typename VT>
 __device__ __forceinline__ void fetch_chunk(int64_t b, int64_t e, int sl, const int32_t *idx, const VT *v,
