@@ -354,14 +354,16 @@ GroupTable batch_groups(const std::vector<BatchSysLevels> &sys, int64_t n_tot, b
             const int64_t a = y.off + y.lstart[(size_t)l], b = y.off + y.lstart[(size_t)l + 1];
             // walk positions kk of this range: forward j = kk, backward j = n_tot - 1 - kk
             const int64_t k0 = descending ? n_tot - b : a, k1 = descending ? n_tot - a : b;
+            if (!y.ptr) {                      // no long rows: groups of `warps` positions
+                for (int64_t kk = k0; kk < k1; kk += warps)
+                    push(kk, GK_ROWS, (int32_t)std::min<int64_t>(warps, k1 - kk), 0);
+                continue;
+            }
             int cur = 0;
             int64_t start = k0;
             for (int64_t kk = k0; kk < k1; ++kk) {
-                int64_t len = 0;
-                if (y.ptr) {
-                    const int64_t j = (descending ? n_tot - 1 - kk : kk) - y.off;
-                    len = (*y.ptr)[(size_t)j + 1] - (*y.ptr)[(size_t)j];
-                }
+                const int64_t j = (descending ? n_tot - 1 - kk : kk) - y.off;
+                const int64_t len = (*y.ptr)[(size_t)j + 1] - (*y.ptr)[(size_t)j];
                 if (len > long_row) {
                     if (cur > 0) { push(start, GK_ROWS, cur, 0); cur = 0; }
                     if (len > split_row) {
