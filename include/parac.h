@@ -240,11 +240,18 @@ parac_status parac_autotune(int32_t count, const parac_system *systems, uint64_t
 /*
  * parac_pcg_many -- parac_pcg (one right-hand side each, with the matrix kept
  * in each handle) on several factored systems, e.g. the handles of one
- * parac_factor_many call.  Host worker threads (4) run the systems' solves
- * concurrently, each on its handle's own stream, so the GPU overlaps the
- * small systems' dependency chains, each worker's solves on a share of the
- * GPU's resident blocks.  Results equal separate parac_pcg calls (the dot
- * products are reduced over grids fixed by n alone).
+ * parac_factor_many call.  Handles on one device with one g_precision are
+ * solved as one block-diagonal system: their matrices, factors and vectors
+ * are concatenated for the call, every SpMV and triangular-solve launch
+ * advances all systems (the solves' schedule interleaves the systems'
+ * dependency levels, and skips the systems that already stopped), and each
+ * system keeps its own CG scalars, stopping test and true-residual check.  A
+ * system's preconditioner applies are the same arithmetic as in its own
+ * parac_pcg call; its dot products are reduced over row chunks of its own, so
+ * iterates agree with separate calls up to rounding (iteration counts within
+ * one).  Otherwise (mixed devices or precisions, or PARAC_PCG_MANY=threads in
+ * the environment) host worker threads run the systems' parac_pcg calls
+ * concurrently, with results equal to separate calls.
  *   count     number of systems; G[count] distinct handles
  *   b[s], x[s]   right-hand side / solution of system s (n_s entries; host or
  *             device memory)
@@ -252,7 +259,9 @@ parac_status parac_autotune(int32_t count, const parac_system *systems, uint64_t
  *   iters, true_relres   [count] outputs (may be NULL)
  * Returns PARAC_OK when every system converged; otherwise the first error of
  * the lowest-numbered failing system (PARAC_ENOCONV only if no other error),
- * with every system's outputs written.
+ * with every system's outputs written.  Device memory for the concatenated
+ * system is allocated for the call (about the factors' and matrices' size
+ * again) and released before it returns.
  */
 parac_status parac_pcg_many(int32_t count, const parac_factor_t *G, const double *const *b, double *const *x,
                             double tol, int32_t maxit, int32_t *iters, double *true_relres);
