@@ -1719,7 +1719,12 @@ extern "C" parac_status parac_pcg_many(int32_t count, const parac_factor_t *G, c
         for (int32_t i = 0; i < count; ++i)
             for (int32_t j = 0; j < i && j < 64; ++j)
                 if (G[i] == G[j]) { set_err("parac_pcg_many: handle %d repeats handle %d", i, j); return PARAC_EINVAL; }
-        if (batchable(count, G)) return pcg_batch(count, G, b, x, tol, maxit, iters, true_relres);
+        if (batchable(count, G)) {
+            // the batch runs on the handles' device; the caller's current device is restored after it
+            struct Restore { int dev = -1; ~Restore() { if (dev >= 0) cudaSetDevice(dev); } } restore;
+            CK(cudaGetDevice(&restore.dev));
+            return pcg_batch(count, G, b, x, tol, maxit, iters, true_relres);
+        }
         std::vector<parac_status> st((size_t)count, PARAC_OK);
         std::vector<std::string> msg((size_t)count);
         std::vector<int32_t> it((size_t)count, 0);

@@ -313,7 +313,7 @@ __global__ void k_breopen(BlockState *st)
 // Rows (positions) are handed out in groups, in position order (ascending for
 // the forward solve, descending for the backward one), round-robin over a
 // co-resident grid as in solve.cu.  A group is either up to one row per warp
-// of the block, or a single long row (more than LONG_ROW entries) that all
+// of the block, or a single long row (more than LONG_ROW_BLOCK entries) that all
 // warps of the block share: the rows at the end of the elimination order
 // collect the most fill and form a chain of long rows, which one warp would
 // walk alone, 32 entries at a time for every column.
@@ -328,7 +328,6 @@ __global__ void k_breopen(BlockState *st)
 // late ones are awaited.  Two accumulators (even / odd entries of a stage) and
 // a fixed cross-warp order for shared rows keep the result deterministic.
 constexpr int MAXW = 32;         // warps per block, at most
-constexpr int LONG_ROW = LONG_ROW_BLOCK;     // entries above which a row gets the whole block
 
 // Entries u in [u0, u_end), in stages of 32 starting every `stride`, of the
 // row [b, b+len): entry u is b+u, or b+len-1-u when REV (the backward solve
