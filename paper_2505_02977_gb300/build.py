@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libparac.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "elim.cu", "ingest.cu", "compact.cu", "solve.cu", "block.cu", "batch.cu"]
+SOURCES = ["api.cu", "elim.cu", "ingest.cu", "compact.cu", "solve.cu", "block.cu", "batch.cu", "schedule.cpp"]
 
 
 def nvcc():
@@ -44,7 +44,7 @@ def build(force=False, verbose=False, ptxas_verbose=False):
         flags += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         cmd = [cc, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

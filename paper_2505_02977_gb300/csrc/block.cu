@@ -556,42 +556,6 @@ inline int grid_for(int64_t m, int maxb)
 
 size_t block_state_bytes() { return sizeof(BlockState); }
 
-// Group table over positions in ascending (forward) or descending (backward)
-// order; ptr = row pointers [n+1] of the rows in that order's numbering.
-GroupTable row_groups(const std::vector<int64_t> &ptr, bool descending, int warps, int long_row, int split_row,
-                      int chunk)
-{
-    const int64_t n = (int64_t)ptr.size() - 1;
-    GroupTable t;
-    t.g.reserve((size_t)(4 * (n / (warps > 0 ? warps : 1) + 2)));
-    auto push = [&](int64_t start, int32_t kind, int32_t arg, int32_t slot) {
-        t.g.push_back((int32_t)start); t.g.push_back(kind); t.g.push_back(arg); t.g.push_back(slot);
-        ++t.ngroups;
-    };
-    int cur = 0;
-    int64_t start = 0;
-    for (int64_t kk = 0; kk < n; ++kk) {
-        const int64_t j = descending ? n - 1 - kk : kk;
-        const int64_t len = ptr[j + 1] - ptr[j];
-        if (len > long_row) {
-            if (cur > 0) { push(start, GK_ROWS, cur, 0); cur = 0; }
-            if (len > split_row) {
-                const int32_t nch = (int32_t)((len + chunk - 1) / chunk);
-                for (int32_t c = 0; c < nch; ++c) push(kk, GK_CHUNK, c, t.nslots + c);
-                push(kk, GK_COMBINE, nch, t.nslots);
-                t.nslots += nch;
-            } else {
-                push(kk, GK_SHARED, 0, 0);
-            }
-        } else {
-            if (cur == 0) start = kk;
-            if (++cur == warps) { push(start, GK_ROWS, cur, 0); cur = 0; }
-        }
-    }
-    if (cur > 0) push(start, GK_ROWS, cur, 0);
-    return t;
-}
-
 // resident blocks per SM of the two SpTRSM kernels at `warps` warps per block
 // (the static row schedule needs the whole grid co-resident)
 int btrsm_blocks_per_sm(int warps, int prec)

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <vector>
 
+#include "schedule.h"
+
 namespace parac {
 
 struct ElimArgs;
@@ -133,20 +135,6 @@ struct SolveArgs {
     const int32_t *skip;
 };
 
-// Schedule of the solves: groups in position order, 4 ints each (first
-// position in walk order, kind, arg, slot).  GK_ROWS: arg rows, one per warp;
-// GK_SHARED: one row for the whole block; GK_CHUNK: entries [arg*chunk,
-// (arg+1)*chunk) of one row (in walk order) summed by the block into partial
-// slot `slot`; GK_COMBINE: the row's arg partials from `slot` on, summed in
-// order, finish the row.  Chunks come before their combine.
-enum : int32_t { GK_ROWS = 0, GK_SHARED = 1, GK_CHUNK = 2, GK_COMBINE = 3 };
-constexpr int32_t GK_KIND_MASK = 0xff, GK_SYS_SHIFT = 8;   // kind | system << GK_SYS_SHIFT
-struct GroupTable {
-    std::vector<int32_t> g;       // 4 * ngroups
-    int32_t ngroups = 0, nslots = 0;
-};
-GroupTable row_groups(const std::vector<int64_t> &ptr, bool descending, int warps, int long_row, int split_row,
-                      int chunk);
 // one right-hand side: rows above LONG_ROW_SINGLE entries get a block, above
 // SPLIT_ROW_SINGLE they are split into chunks of CHUNK_SINGLE; block solves
 // (nrhs columns, 32 x the bytes per entry) use the _BLOCK sizes
@@ -251,18 +239,6 @@ cudaError_t spcg_reopen(const SolveArgs &A, const BatchBuffers &B, cudaStream_t 
 struct CatSeg { const void *src; int64_t count, dst, add; };
 cudaError_t launch_cat(const CatSeg *seg, int32_t nseg, int64_t max_count, int elem, bool is_float, void *dst,
                        cudaStream_t st);
-// one system of a concatenated solve: its first global position, its level
-// starts (positions, depth + 1 entries) and, for systems with rows longer than
-// the block-wide threshold, its row (forward) or column (backward) pointers
-struct BatchSysLevels {
-    int32_t sys;
-    int64_t off;
-    std::vector<int64_t> lstart;
-    const std::vector<int64_t> *ptr;
-};
-GroupTable batch_groups(const std::vector<BatchSysLevels> &sys, int64_t n_tot, bool descending, int warps,
-                        int long_row, int split_row, int chunk);
-
 // Allocation-free variant: work vectors in a fixed device array (n <= NOALLOC_MAX_N).
 constexpr int NOALLOC_MAX_N = 1 << 18;
 constexpr int NOALLOC_MAX_DEVICES = 64;

@@ -1,0 +1,47 @@
+// C entry points over the solves' schedule builders (csrc/schedule.cpp), for
+// the CPU tests: tables are written as 4 ints per group.
+#include <cstring>
+#include <vector>
+
+#include "schedule.h"
+
+using namespace parac;
+
+static int64_t emit(const GroupTable &t, int32_t *out, int64_t cap, int32_t *nslots)
+{
+    if (nslots) *nslots = t.nslots;
+    if (out && (int64_t)t.g.size() <= cap) std::memcpy(out, t.g.data(), 4 * t.g.size());
+    return t.ngroups;
+}
+
+extern "C" int64_t sched_row_groups(const int64_t *ptr, int64_t n, int descending, int warps, int long_row,
+                                    int split_row, int chunk, int32_t *out, int64_t cap, int32_t *nslots)
+{
+    std::vector<int64_t> p(ptr, ptr + n + 1);
+    return emit(row_groups(p, descending != 0, warps, long_row, split_row, chunk), out, cap, nslots);
+}
+
+// System s: first position off[s], level starts lstart[lo[s] .. lo[s+1]),
+// pointers ptr[po[s] .. po[s] + n_s + 1) when po[s] >= 0.
+extern "C" int64_t sched_batch_groups(int32_t count, const int64_t *off, const int64_t *lstart, const int64_t *lo,
+                                      const int64_t *ptr, const int64_t *po, int64_t n_tot, int descending,
+                                      int warps, int long_row, int split_row, int chunk, int32_t *out, int64_t cap,
+                                      int32_t *nslots)
+{
+    std::vector<std::vector<int64_t>> ptrs((size_t)count);
+    std::vector<BatchSysLevels> sys;
+    for (int32_t s = 0; s < count; ++s) {
+        BatchSysLevels y;
+        y.sys = s;
+        y.off = off[s];
+        y.lstart.assign(lstart + lo[s], lstart + lo[s + 1]);
+        y.ptr = nullptr;
+        if (po[s] >= 0) {
+            const int64_t ns = off[s + 1] - off[s];
+            ptrs[(size_t)s].assign(ptr + po[s], ptr + po[s] + ns + 1);
+            y.ptr = &ptrs[(size_t)s];
+        }
+        sys.push_back(y);
+    }
+    return emit(batch_groups(sys, n_tot, descending != 0, warps, long_row, split_row, chunk), out, cap, nslots);
+}
