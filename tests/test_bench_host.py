@@ -59,3 +59,15 @@ def test_reference_arm_runs_the_oracle():
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "Mnnz(G)/s"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_batch_sample():
+    """The batch workload's reference arm factors a bounded sample of the 200
+    systems (in order) with the oracle and says which."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "sddm-batch-200", "--steps", "1", "--warmup", "0", "--cpu-budget", "0.2"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["config"]["systems"] == 200
+    assert line["cpu_baseline"]["kind"] == "oracle" and "of 200 systems" in line["cpu_baseline"]["sample"]
