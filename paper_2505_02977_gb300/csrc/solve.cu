@@ -369,19 +369,19 @@ __device__ __forceinline__ XT block_row_sum(XT acc, XT *red)
 // with every row's dependencies at earlier positions and the rows of one
 // level contiguous.  operm[j] is the original index of position j.
 //
-// Each row is handled by S lanes (S = 32: a warp).  A warp works a row ahead:
-// it issues the loads of its current row's unknowns, then fetches the next
-// row's pointers, indices, values and right-hand side (which depend on no
-// other row), and only then waits for the current unknowns -- so when a row's
-// dependencies are published, its own data is already in registers and it
-// costs one round of polls.  Rows beyond S*RPF entries continue with
-// dot_ready.
+// Each row is handled by S lanes (S = 32: a warp).  A warp works ahead: it
+// issues the loads of its current row's unknowns, then the loads its next
+// rows need (which depend on no other row; see k_trsv_fwd), and only then
+// waits for the current unknowns -- so when a row's dependencies are
+// published, its own data is already in registers and it costs one round of
+// polls.  Each lane prefetches RPF entries of a row; rows beyond S*RPF
+// entries continue with dot_ready.
 //
-// With a group table gs (one row per warp, S == 32), rows are handed out in
-// groups gs[g]..gs[g+1]: up to one row per warp, or one row longer than
-// LONG_ROW_SINGLE entries shared by every warp of the block (the rows that
-// collect the most fill, e.g. of hub vertices, would otherwise leave one warp
-// to walk them alone on the critical path).
+// With a group table (schedule.h), rows are handed out in its groups: up to
+// one row per lane group, or one row longer than LONG_ROW_SINGLE entries
+// shared by every warp of the block (the rows that collect the most fill,
+// e.g. of hub vertices, would otherwise leave one warp to walk them alone on
+// the critical path), or chunks of a longer row and their combine.
 constexpr int RPF = 1;     // measured: 1 beats 2 and 4 (fewer instructions per row; long rows go on in dot_ready)
 
 template <int S, bool REV, typename VT>
