@@ -1080,8 +1080,12 @@ SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, co
     // one row per warp unless the handle asks for sub-warp rows
     A.lanes_trsv = G->sptrsv == PARAC_SPTRSV_SUB8 ? 8 : G->sptrsv == PARAC_SPTRSV_SUB4 ? 4 : 32;
     A.trsv_warps = SOLVE_WARPS;
-    if (const char *e = getenv("PARAC_TRSV_LANES")) A.lanes_trsv = atoi(e);
-    if (const char *e = getenv("PARAC_TRSV_WARPS")) A.trsv_warps = std::max(1, std::min(32, atoi(e)));
+    if (const char *e = getenv("PARAC_TRSV_LANES")) {
+        const int l = atoi(e);
+        if (l == 4 || l == 8 || l == 16 || l == 32) A.lanes_trsv = l;
+    }
+    // at most 8 warps: a 256-thread block of the solves fits the register file twice
+    if (const char *e = getenv("PARAC_TRSV_WARPS")) A.trsv_warps = std::max(1, std::min(SOLVE_WARPS, atoi(e)));
     int bps = 0;
     trsv_configure(A.lanes_trsv, A.trsv_warps, &bps, A.prec);
     if (bps < 1) bps = 1;
