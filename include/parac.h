@@ -261,7 +261,8 @@ parac_status parac_autotune(int32_t count, const parac_system *systems, uint64_t
  * the lowest-numbered failing system (PARAC_ENOCONV only if no other error),
  * with every system's outputs written.  Device memory for the concatenated
  * system is allocated for the call (about the factors' and matrices' size
- * again) and released before it returns.
+ * again) and released before it returns; when it cannot be allocated, the
+ * systems are solved by the worker threads instead.
  */
 parac_status parac_pcg_many(int32_t count, const parac_factor_t *G, const double *const *b, double *const *x,
                             double tol, int32_t maxit, int32_t *iters, double *true_relres);

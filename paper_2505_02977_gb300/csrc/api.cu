@@ -1727,7 +1727,14 @@ extern "C" parac_status parac_pcg_many(int32_t count, const parac_factor_t *G, c
             // the batch runs on the handles' device; the caller's current device is restored after it
             struct Restore { int dev = -1; ~Restore() { if (dev >= 0) cudaSetDevice(dev); } } restore;
             CK(cudaGetDevice(&restore.dev));
-            return pcg_batch(count, G, b, x, tol, maxit, iters, true_relres);
+            try {
+                return pcg_batch(count, G, b, x, tol, maxit, iters, true_relres);
+            } catch (const StatusFail &e) {
+                // no room for the concatenated copy: solve system by system instead
+                if (e.s != PARAC_ENOMEM) throw;
+                cudaGetLastError();
+                g_err.clear();
+            }
         }
         std::vector<parac_status> st((size_t)count, PARAC_OK);
         std::vector<std::string> msg((size_t)count);
