@@ -1086,10 +1086,8 @@ SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, co
     }
     // at most 8 warps: a 256-thread block of the solves fits the register file twice
     if (const char *e = getenv("PARAC_TRSV_WARPS")) A.trsv_warps = std::max(1, std::min(SOLVE_WARPS, atoi(e)));
-    // the handle's group tables serve one row per warp at the default block size
-    const bool table = G->sng_f > 0 && A.lanes_trsv == 32 && A.trsv_warps == SOLVE_WARPS;
     int bps = 0;
-    trsv_configure(A.lanes_trsv, A.trsv_warps, &bps, A.prec, table);
+    trsv_configure(A.lanes_trsv, A.trsv_warps, &bps, A.prec);
     if (bps < 1) bps = 1;
     int max_blocks = num_sms() * bps;            // all co-resident: required by the static schedule
     if (t_grid_share > 1) max_blocks = std::max(1, max_blocks / t_grid_share);
@@ -1109,7 +1107,7 @@ SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, co
     if (groups < A.trsv_blocks) A.trsv_blocks = (int)std::max<int64_t>(groups, 1);
     A.spin_limit = G->spin_limit;
     A.status = G->status.as<int32_t>();
-    if (table) {
+    if (G->sng_f > 0 && A.lanes_trsv == 32 && A.trsv_warps == SOLVE_WARPS) {
         A.gt_f = (const int4 *)G->sgt_f.p; A.ng_f = G->sng_f;
         A.gt_b = (const int4 *)G->sgt_b.p; A.ng_b = G->sng_b;
         A.part_f = G->spart_f.p; A.nslot_f = G->snslot_f;
@@ -1644,7 +1642,7 @@ parac_status pcg_batch(int32_t count, const parac_factor_t *G, const double *con
     A.lanes_trsv = lanes;
     A.trsv_warps = SOLVE_WARPS;
     int bps = 0;
-    trsv_configure(lanes, SOLVE_WARPS, &bps, prec, true, true);
+    trsv_configure(lanes, SOLVE_WARPS, &bps, prec, true);
     const int64_t max_blocks = (int64_t)num_sms() * std::max(bps, 1);   // all co-resident
     const int64_t want = (2 * n / std::max(depth, 1) + rows_per_group - 1) / rows_per_group;
     int64_t tb = std::max<int64_t>(std::min<int64_t>(num_sms(), max_blocks), std::min<int64_t>(max_blocks, want));

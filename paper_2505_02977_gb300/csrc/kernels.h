@@ -243,6 +243,6 @@ cudaError_t launch_cat(const CatSeg *seg, int32_t nseg, int64_t max_count, int e
 constexpr int NOALLOC_MAX_N = 1 << 18;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 cudaError_t precond_apply_noalloc(const SolveArgs &A, const double *r, double *z, cudaStream_t st);
-int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec, bool table = false, bool skip = false);
+int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec, bool skip = false);
 
 }  // namespace parac

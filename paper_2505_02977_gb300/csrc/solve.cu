@@ -442,11 +442,10 @@ struct Grp {
 
 // Table entry of group g: from the table, or the fixed group of
 // rows_per_group consecutive positions; past the end, an empty group.
-template <bool TAB>
 __device__ __forceinline__ int4 group_entry(int64_t g, int64_t ngroups, const int4 *gt, int32_t n, int rows_per_group)
 {
     if (g >= ngroups) return make_int4(0, GK_ROWS, 0, 0);
-    if constexpr (TAB) return __ldg(gt + g);
+    if (gt) return __ldg(gt + g);
     const int64_t k0 = g * rows_per_group;
     const int64_t cnt = (int64_t)n - k0 < rows_per_group ? (int64_t)n - k0 : rows_per_group;
     return make_int4((int32_t)k0, GK_ROWS, (int32_t)cnt, 0);
@@ -506,7 +505,7 @@ __device__ __forceinline__ XT combine_parts(const Grp &q, XT *part, long long sp
 // the table entry of group g+3G, so each load is issued a step before its
 // consumer needs it.  (Unrolling the loop by two over two register sets that
 // swap roles was measured slower: more registers, no fewer stalls.)
-template <int S, typename VT, typename XT, bool TAB, bool SKIP>
+template <int S, typename VT, typename XT, bool SKIP>
 __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, const VT *v, const int32_t *operm,
                            const double *rhs, XT *y, XT *zreset, const int4 *gt, int32_t ngs, XT *part,
                            const PcgState *st, long long spin_limit, int32_t *status, const int32_t *skip)
@@ -518,7 +517,7 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
     const unsigned smask = (S == 32) ? FULL : (((1u << S) - 1u) << (sub * S));
     const int rows_per_group = (blockDim.x / 32) * (32 / S);
     const int my = (threadIdx.x >> 5) * (32 / S) + sub;
-    const int64_t ngroups = TAB ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
+    const int64_t ngroups = gt ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
     const int64_t G = gridDim.x;
     auto bounds = [&](Grp &r, int64_t &bb, int64_t &ee, int32_t &o) {
         if constexpr (SKIP) r.aux = skip[r.aux];
@@ -536,9 +535,9 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
         }
     };
     int64_t g = blockIdx.x;
-    Grp q = group_decode(group_entry<TAB>(g, ngroups, gt, n, rows_per_group), n, my, false);
-    Grp q1 = group_decode(group_entry<TAB>(g + G, ngroups, gt, n, rows_per_group), n, my, false);
-    int4 t2 = group_entry<TAB>(g + 2 * G, ngroups, gt, n, rows_per_group);
+    Grp q = group_decode(group_entry(g, ngroups, gt, n, rows_per_group), n, my, false);
+    Grp q1 = group_decode(group_entry(g + G, ngroups, gt, n, rows_per_group), n, my, false);
+    int4 t2 = group_entry(g + 2 * G, ngroups, gt, n, rows_per_group);
     int64_t b = 0, e = 0, b1 = 0, e1 = 0;
     int32_t o = 0, o1 = 0;
     double rj = 0.0;
@@ -550,7 +549,7 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
     data(q, b, e, o, rj, cc, vv);
     while (g < ngroups) {
         const int64_t j = q.j;
-        const bool rows = !TAB || q.kind == GK_ROWS;     // fixed groups: rows only
+        const bool rows = q.kind == GK_ROWS;
         if (rows && j >= 0) issue_x(y, cc, xx);
         // advance the pipeline: data of g+G, bounds of g+2G, entry of g+3G
         int32_t ccn[RPF];
@@ -561,7 +560,7 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
         int64_t b2 = 0, e2 = 0;
         int32_t o2 = 0;
         bounds(q2, b2, e2, o2);
-        const int4 t3 = group_entry<TAB>(g + 3 * G, ngroups, gt, n, rows_per_group);
+        const int4 t3 = group_entry(g + 3 * G, ngroups, gt, n, rows_per_group);
         if (!rows) {                                  // block-wide group (block-uniform branch)
             if (q.kind == GK_COMBINE) {
                 if (threadIdx.x == 0) {
@@ -608,7 +607,7 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
 // unknown was published first); writes zout[operm[j]], resets y[j] to the
 // sentinel, and accumulates r_orig . z into the block partial.  Loads are
 // pipelined as in the forward solve.
-template <int S, typename VT, typename XT, bool TAB, bool SKIP>
+template <int S, typename VT, typename XT, bool SKIP>
 __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, const VT *v, const double *Dinv,
                            const int32_t *operm, XT *y, XT *z, double *zout, const double *r_orig, double *partial,
                            const int4 *gt, int32_t ngs, XT *part, const PcgState *st, long long spin_limit,
@@ -621,7 +620,7 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
     const unsigned smask = (S == 32) ? FULL : (((1u << S) - 1u) << (sub * S));
     const int rows_per_group = (blockDim.x / 32) * (32 / S);
     const int my = (threadIdx.x >> 5) * (32 / S) + sub;
-    const int64_t ngroups = TAB ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
+    const int64_t ngroups = gt ? (int64_t)ngs : ((int64_t)n + rows_per_group - 1) / rows_per_group;
     const int64_t G = gridDim.x;
     double dotacc = 0.0;
     auto bounds = [&](Grp &r, int64_t &bb, int64_t &ee, int32_t &o) {
@@ -652,9 +651,9 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
         dotacc += rv * (double)zj;
     };
     int64_t g = blockIdx.x;
-    Grp q = group_decode(group_entry<TAB>(g, ngroups, gt, n, rows_per_group), n, my, true);
-    Grp q1 = group_decode(group_entry<TAB>(g + G, ngroups, gt, n, rows_per_group), n, my, true);
-    int4 t2 = group_entry<TAB>(g + 2 * G, ngroups, gt, n, rows_per_group);
+    Grp q = group_decode(group_entry(g, ngroups, gt, n, rows_per_group), n, my, true);
+    Grp q1 = group_decode(group_entry(g + G, ngroups, gt, n, rows_per_group), n, my, true);
+    int4 t2 = group_entry(g + 2 * G, ngroups, gt, n, rows_per_group);
     int64_t b = 0, e = 0, b1 = 0, e1 = 0;
     int32_t o = 0, o1 = 0;
     XT yj = 0;
@@ -667,7 +666,7 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
     data(q, b, e, o, yj, dj, rj, cc, vv);
     while (g < ngroups) {
         const int64_t j = q.j;
-        const bool rows = !TAB || q.kind == GK_ROWS;     // fixed groups: rows only
+        const bool rows = q.kind == GK_ROWS;
         if (rows && j >= 0) issue_x(z, cc, xx);
         int32_t ccn[RPF];
         VT vvn[RPF];
@@ -678,7 +677,7 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
         int64_t b2 = 0, e2 = 0;
         int32_t o2 = 0;
         bounds(q2, b2, e2, o2);
-        const int4 t3 = group_entry<TAB>(g + 3 * G, ngroups, gt, n, rows_per_group);
+        const int4 t3 = group_entry(g + 3 * G, ngroups, gt, n, rows_per_group);
         if (!rows) {                                  // block-wide group (block-uniform branch)
             XT sum = 0;
             if (q.kind == GK_COMBINE) {
@@ -744,35 +743,34 @@ cudaError_t spmv(const SolveArgs &A, const double *x, double *y, double *partial
     }
 }
 
-template <int S, typename VT, typename XT, bool TAB, bool SKIP>
-void launch_pair(const SolveArgs &A, const VT *vr, const VT *vc, XT *y, XT *z, const double *r, double *zout,
-                 double *partial, const PcgState *st, cudaStream_t s)
-{
-    const int threads = A.trsv_warps * 32;
-    k_trsv_fwd<S, VT, XT, TAB, SKIP><<<A.trsv_blocks, threads, 0, s>>>(
-        A.n, A.Frp, A.Fcol, vr, A.operm, r, y, z, A.gt_f, A.ng_f, (XT *)A.part_f, st, A.spin_limit, A.status,
-        A.skip);
-    k_trsv_bwd<S, VT, XT, TAB, SKIP><<<A.trsv_blocks, threads, 0, s>>>(
-        A.n, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z, zout, partial ? r : nullptr, partial, A.gt_b, A.ng_b,
-        (XT *)A.part_b, st, A.spin_limit, A.status, A.skip);
-    count_launches(2);
-}
-
-// The group tables, when given, are built for the launch's rows per group
-// (trsv_warps * 32 / S); per-system stop flags come with tables and one row
-// per warp (batched solves).
 template <int S, typename VT, typename XT>
 cudaError_t apply_t(const SolveArgs &A, const VT *vr, const VT *vc, XT *y, XT *z, const double *r, double *zout,
                     double *partial, const PcgState *st, cudaStream_t s)
 {
+    const int threads = A.trsv_warps * 32;
+    // a group table is built for the launch's rows per group (trsv_warps * 32 / S)
+    const int4 *gf = A.gt_f, *gb = A.gt_b;
     if constexpr (S == 32) {
-        if (A.skip) {
-            launch_pair<S, VT, XT, true, true>(A, vr, vc, y, z, r, zout, partial, st, s);
+        if (A.skip) {                 // per-system stop flags (batched solves, one row per warp)
+            k_trsv_fwd<S, VT, XT, true><<<A.trsv_blocks, threads, 0, s>>>(
+                A.n, A.Frp, A.Fcol, vr, A.operm, r, y, z, gf, A.ng_f, (XT *)A.part_f, st, A.spin_limit, A.status,
+                A.skip);
+            k_trsv_bwd<S, VT, XT, true><<<A.trsv_blocks, threads, 0, s>>>(
+                A.n, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z, zout, partial ? r : nullptr, partial, gb, A.ng_b,
+                (XT *)A.part_b, st, A.spin_limit, A.status, A.skip);
+            count_launches(2);
             return cudaGetLastError();
         }
     }
-    if (A.gt_f) launch_pair<S, VT, XT, true, false>(A, vr, vc, y, z, r, zout, partial, st, s);
-    else launch_pair<S, VT, XT, false, false>(A, vr, vc, y, z, r, zout, partial, st, s);
+    k_trsv_fwd<S, VT, XT, false><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Frp, A.Fcol, vr, A.operm, r, y, z, gf,
+                                                                    A.ng_f, (XT *)A.part_f, st, A.spin_limit,
+                                                                    A.status, nullptr);
+    count_launches(1);
+    k_trsv_bwd<S, VT, XT, false><<<A.trsv_blocks, threads, 0, s>>>(A.n, A.Fcp, A.Frow, vc, A.Dinv, A.operm, y, z,
+                                                                    zout, partial ? r : nullptr, partial, gb, A.ng_b,
+                                                                    (XT *)A.part_b, st, A.spin_limit, A.status,
+                                                                    nullptr);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -848,43 +846,43 @@ cudaError_t set_poll_backoff(unsigned max_ns)
     return e;
 }
 
-namespace {
-
-template <int S, typename VT, typename XT, bool TAB, bool SKIP>
-int pair_blocks_per_sm(int threads)
+int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec, bool skip)
 {
-    int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trsv_fwd<S, VT, XT, TAB, SKIP>, threads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trsv_bwd<S, VT, XT, TAB, SKIP>, threads, 0);
-    return a < b ? a : b;
-}
-
-template <int S, bool TAB>
-int pair_blocks_per_sm(int threads, int prec)
-{
-    return prec == 32 ? pair_blocks_per_sm<S, float, float, TAB, false>(threads)
-                      : pair_blocks_per_sm<S, double, double, TAB, false>(threads);
-}
-
-}  // namespace
-
-// Resident blocks per SM of the solve pair that apply_t launches for these
-// arguments (the static schedule needs the whole grid co-resident).
-int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec, bool table, bool skip)
-{
+    cudaError_t e;
     const int threads = warps * 32;
-    if (skip) {
-        *blocks_per_sm = prec == 32 ? pair_blocks_per_sm<32, float, float, true, true>(threads)
-                                    : pair_blocks_per_sm<32, double, double, true, true>(threads);
-    } else {
-        switch (lanes) {
-        case 4: *blocks_per_sm = table ? pair_blocks_per_sm<4, true>(threads, prec) : pair_blocks_per_sm<4, false>(threads, prec); break;
-        case 8: *blocks_per_sm = table ? pair_blocks_per_sm<8, true>(threads, prec) : pair_blocks_per_sm<8, false>(threads, prec); break;
-        case 16: *blocks_per_sm = table ? pair_blocks_per_sm<16, true>(threads, prec) : pair_blocks_per_sm<16, false>(threads, prec); break;
-        default: *blocks_per_sm = table ? pair_blocks_per_sm<32, true>(threads, prec) : pair_blocks_per_sm<32, false>(threads, prec);
-        }
+    switch (lanes) {
+    case 4:
+        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<4, float, float, false>, threads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<4, double, double, false>, threads, 0);
+        break;
+    case 8:
+        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<8, float, float, false>, threads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<8, double, double, false>, threads, 0);
+        break;
+    case 16:
+        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<16, float, float, false>, threads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<16, double, double, false>, threads, 0);
+        break;
+    default:
+        e = prec == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<32, float, float, false>, threads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trsv_fwd<32, double, double, false>, threads, 0);
     }
-    return *blocks_per_sm > 0 ? 0 : -1;
+    int b2 = 0;
+    // the backward kernel must fit the same grid
+    switch (lanes) {
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<4, float, float, false> : (const void *)k_trsv_bwd<4, double, double, false>, threads, 0); break;
+    case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<8, float, float, false> : (const void *)k_trsv_bwd<8, double, double, false>, threads, 0); break;
+    case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<16, float, float, false> : (const void *)k_trsv_bwd<16, double, double, false>, threads, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, prec == 32 ? (const void *)k_trsv_bwd<32, float, float, false> : (const void *)k_trsv_bwd<32, double, double, false>, threads, 0);
+    }
+    if (b2 < *blocks_per_sm) *blocks_per_sm = b2;
+    if (skip) {                       // the per-system stop-flag solves (one row per warp) are launched instead
+        int a = 0, c = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, prec == 32 ? (const void *)k_trsv_fwd<32, float, float, true> : (const void *)k_trsv_fwd<32, double, double, true>, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, prec == 32 ? (const void *)k_trsv_bwd<32, float, float, true> : (const void *)k_trsv_bwd<32, double, double, true>, threads, 0);
+        *blocks_per_sm = std::min(a, c);
+    }
+    return e == cudaSuccess ? 0 : -1;
 }
 
 cudaError_t precond_apply(const SolveArgs &A, const PcgBuffers &B, const double *r, double *z, cudaStream_t st)
