@@ -1720,9 +1720,14 @@ extern "C" parac_status parac_pcg_many(int32_t count, const parac_factor_t *G, c
 {
     return guarded([&]() -> parac_status {
         if (count < 0 || (count > 0 && (!G || !b || !x))) { set_err("bad arguments to parac_pcg_many"); return PARAC_EINVAL; }
-        for (int32_t i = 0; i < count; ++i)
+        for (int32_t i = 0; i < count; ++i) {
+            if (G[i] && G[i]->n > 0 && (!b[i] || !x[i])) {
+                set_err("parac_pcg_many: null right-hand side or solution of system %d", i);
+                return PARAC_EINVAL;
+            }
             for (int32_t j = 0; j < i && j < 64; ++j)
                 if (G[i] == G[j]) { set_err("parac_pcg_many: handle %d repeats handle %d", i, j); return PARAC_EINVAL; }
+        }
         if (batchable(count, G)) {
             // the batch runs on the handles' device; the caller's current device is restored after it
             struct Restore { int dev = -1; ~Restore() { if (dev >= 0) cudaSetDevice(dev); } } restore;

@@ -240,6 +240,8 @@ def parac_pcg_many(Gs, bs, tol=1e-8, maxit=1000, xs=None, allow_noconv=True):
     """PCG on several systems at once (one right-hand side each).  bs: list of
     n_s-vectors (numpy or torch CUDA); returns (xs, iters, relres, status)."""
     m = len(Gs)
+    if len(bs) != m or (xs is not None and len(xs) != m):
+        raise ValueError("parac_pcg_many: one right-hand side (and solution) per handle")
     keep = []
     if xs is None:
         xs = []

@@ -44,3 +44,26 @@ def test_binding_names_match_header():
     assert sorted(parac.EXPORTED) == _declared()
     for n in parac.EXPORTED:
         assert callable(getattr(parac, n))
+
+
+def test_pcg_many_argument_checks_without_gpu(lib):
+    """parac_pcg_many rejects malformed arguments before touching a device:
+    a negative count, null arrays, a null handle (reported per system)."""
+    V = ctypes.c_void_p
+    lib.parac_pcg_many.argtypes = [ctypes.c_int32, ctypes.POINTER(V), ctypes.POINTER(V), ctypes.POINTER(V),
+                                   ctypes.c_double, ctypes.c_int32, V, V]
+    lib.parac_pcg_many.restype = ctypes.c_int
+    EINVAL = 1
+    assert lib.parac_pcg_many(-1, None, None, None, 1e-8, 10, None, None) == EINVAL
+    assert lib.parac_pcg_many(2, None, None, None, 1e-8, 10, None, None) == EINVAL
+    hs, bs, xs = (V * 1)(), (V * 1)(), (V * 1)()
+    it = (ctypes.c_int32 * 1)(-5)
+    assert lib.parac_pcg_many(1, hs, bs, xs, 1e-8, 10, ctypes.cast(it, V), None) == EINVAL
+    assert it[0] == 0                                   # outputs written for every system
+    assert lib.parac_pcg_many(0, None, None, None, 1e-8, 10, None, None) == 0
+
+
+def test_pcg_many_binding_checks_lengths():
+    from paper_2505_02977_gb300 import parac
+    with pytest.raises(ValueError):
+        parac.parac_pcg_many([object(), object()], [None])
