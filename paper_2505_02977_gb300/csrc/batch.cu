@@ -3,7 +3,8 @@
 // and vectors are concatenated; the shared SpMV and triangular-solve kernels
 // run once per step over all of them (the solves' schedule interleaves the
 // systems' rows by dependency level, so one launch advances every system's
-// chain).  Each system keeps its own CG scalars and stopping test.  Every dot
+// chain, and its groups of stopped systems are skipped through per-system
+// stop flags).  Each system keeps its own CG scalars and stopping test.  Every dot
 // product is reduced over fixed row chunks that never straddle two systems,
 // then per system over its chunks in order: deterministic, and independent of
 // the launch shape.
