@@ -1601,14 +1601,9 @@ parac_status pcg_batch(int32_t count, const parac_factor_t *G, const double *con
     R.part_f = DBuf(xs * (size_t)std::max(gf.nslots, 1), st);
     R.part_b = DBuf(xs * (size_t)std::max(gb.nslots, 1), st);
     // row chunks of the dot products (never across systems)
-    std::vector<int64_t> clo;
-    std::vector<int32_t> csys, c0((size_t)count + 1, 0);
-    for (int32_t i = 0; i < count; ++i) {
-        c0[(size_t)i] = (int32_t)csys.size();
-        for (int64_t a = off[(size_t)i]; a < off[(size_t)i + 1]; a += BATCH_CHUNK_ROWS) { clo.push_back(a); csys.push_back(i); }
-    }
-    c0[(size_t)count] = (int32_t)csys.size();
-    clo.push_back(n);
+    const RowChunks chunks = row_chunks(off, BATCH_CHUNK_ROWS);
+    const std::vector<int64_t> &clo = chunks.lo;
+    const std::vector<int32_t> &csys = chunks.sys, &c0 = chunks.first;
     const int32_t nch = (int32_t)csys.size();
     R.clo = dalloc<int64_t>(clo.size(), st); R.csys = dalloc<int32_t>(std::max<size_t>(csys.size(), 1), st);
     R.sys_c0 = dalloc<int32_t>(c0.size(), st);

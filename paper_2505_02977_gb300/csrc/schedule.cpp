@@ -107,4 +107,21 @@ GroupTable batch_groups(const std::vector<BatchSysLevels> &sys, int64_t n_tot, b
     return t;
 }
 
+RowChunks row_chunks(const std::vector<int64_t> &off, int64_t rows)
+{
+    RowChunks c;
+    const int32_t count = (int32_t)off.size() - 1;
+    c.first.assign((size_t)std::max(count, 0) + 1, 0);
+    for (int32_t s = 0; s < count; ++s) {
+        c.first[(size_t)s] = (int32_t)c.sys.size();
+        for (int64_t a = off[(size_t)s]; a < off[(size_t)s + 1]; a += rows) {
+            c.lo.push_back(a);
+            c.sys.push_back(s);
+        }
+    }
+    c.first[(size_t)std::max(count, 0)] = (int32_t)c.sys.size();
+    c.lo.push_back(count > 0 ? off[(size_t)count] : 0);
+    return c;
+}
+
 }  // namespace parac

@@ -33,4 +33,14 @@ struct BatchSysLevels {
 GroupTable batch_groups(const std::vector<BatchSysLevels> &sys, int64_t n_tot, bool descending, int warps,
                         int long_row, int split_row, int chunk);
 
+// Row chunks of the batched PCG's dot products: system s holds rows off[s] ..
+// off[s+1]; chunk c covers rows lo[c] .. lo[c+1] (at most `rows`, never two
+// systems), sys[c] is its system, and system s owns chunks first[s] ..
+// first[s+1].  lo ends with the total row count.
+struct RowChunks {
+    std::vector<int64_t> lo;
+    std::vector<int32_t> sys, first;
+};
+RowChunks row_chunks(const std::vector<int64_t> &off, int64_t rows);
+
 }  // namespace parac

@@ -45,3 +45,17 @@ extern "C" int64_t sched_batch_groups(int32_t count, const int64_t *off, const i
     }
     return emit(batch_groups(sys, n_tot, descending != 0, warps, long_row, split_row, chunk), out, cap, nslots);
 }
+
+// Writes lo (nchunks + 1), sys (nchunks), first (count + 1); returns nchunks.
+extern "C" int64_t sched_row_chunks(const int64_t *off, int32_t count, int64_t rows, int64_t *lo, int32_t *sys,
+                                    int32_t *first, int64_t cap)
+{
+    const RowChunks c = row_chunks(std::vector<int64_t>(off, off + count + 1), rows);
+    const int64_t nch = (int64_t)c.sys.size();
+    if (nch + 1 <= cap) {
+        std::memcpy(lo, c.lo.data(), 8 * c.lo.size());
+        std::memcpy(sys, c.sys.data(), 4 * c.sys.size());
+        std::memcpy(first, c.first.data(), 4 * c.first.size());
+    }
+    return nch;
+}

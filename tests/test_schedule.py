@@ -38,6 +38,8 @@ def lib(tmp_path_factory):
     L.sched_batch_groups.restype = C.c_int64
     L.sched_batch_groups.argtypes = [C.c_int32, P64, P64, P64, P64, P64, C.c_int64, C.c_int, C.c_int, C.c_int,
                                      C.c_int, C.c_int, P32, C.c_int64, P32]
+    L.sched_row_chunks.restype = C.c_int64
+    L.sched_row_chunks.argtypes = [P64, C.c_int32, C.c_int64, P64, P32, P32, C.c_int64]
     return L
 
 
@@ -208,3 +210,30 @@ def test_batch_groups(lib, seed):
                         assert done_at[n - 1 - b] > done_at[n - 1 - a]
                     else:
                         assert done_at[b] < done_at[a]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_row_chunks(lib, seed):
+    """The batched PCG's dot-product chunks partition the rows, never cross a
+    system, hold at most `rows` rows, and each system owns a contiguous run
+    of them (systems without rows own none)."""
+    rng = np.random.default_rng(200 + seed)
+    count = int(rng.integers(1, 12))
+    ns = rng.integers(0, 50, count)
+    ns[rng.random(count) < 0.2] = 0
+    off = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    rows = int(rng.integers(1, 9))
+    cap = int(off[-1]) + count + 2
+    lo = np.zeros(cap, np.int64); sy = np.zeros(cap, np.int32); first = np.zeros(count + 1, np.int32)
+    nch = lib.sched_row_chunks(_p(off, C.c_int64), count, rows, _p(lo, C.c_int64), _p(sy, C.c_int32),
+                               _p(first, C.c_int32), cap)
+    assert nch == sum(-(-int(k) // rows) for k in ns)
+    lo, sy = lo[:nch + 1], sy[:nch]
+    assert lo[0] == 0 and lo[-1] == off[-1] and np.all(np.diff(lo) >= 1) and np.all(np.diff(lo) <= rows)
+    for c in range(nch):
+        s = sy[c]
+        assert off[s] <= lo[c] and lo[c + 1] <= off[s + 1]
+    for s in range(count):
+        assert np.all(sy[first[s]:first[s + 1]] == s)
+        assert (first[s + 1] - first[s]) == -(-int(ns[s]) // rows)
+    assert first[count] == nch
