@@ -70,6 +70,9 @@ def _declare(L):
     L.orc_precond_apply.argtypes = [C.c_int64, i64p, i32p, f64p, f64p, i32p, f64p, f64p, f64p]
     L.orc_pcg.argtypes = [C.c_int64, i64p, i32p, f64p, i64p, i32p, f64p, f64p, i32p, f64p,
                           C.c_double, C.c_int32, f64p, i32p, f64p]
+    L.orc_precond_apply32.argtypes = [C.c_int64, i64p, i32p, f64p, f64p, i32p, f64p, f64p, f64p]
+    L.orc_pcg_prec.argtypes = [C.c_int64, i64p, i32p, f64p, i64p, i32p, f64p, f64p, i32p, f64p,
+                               C.c_double, C.c_int32, C.c_int, f64p, i32p, f64p]
 
 
 def lib(path=None):
@@ -234,7 +237,15 @@ def dp_update(dp, samples, nbrs, mults, deletes_first=False, L=None):
     return dp, enq[:ne].copy()
 
 
-def precond_apply(F, ordering, r, L=None):
+def precond_apply(F, ordering, r, prec=64, bound=False, L=None):
+    """z = P^T F^{-T} D^+ F^{-1} P r.  prec=32: the mixed form (F and the
+    solves in FP32, D^+ in FP64; readings M1-M5 of rchol_oracle.c).  With
+    bound=True (prec=32 only) also returns the componentwise bound on
+    |z - z_exact| that holds for any summation order of the FP32 sums."""
+    if prec == 32:
+        return _precond_apply32(F, ordering, r, bound, L)
+    if prec != 64:
+        raise ValueError("prec must be 64 or 32")
     L = L or lib()
     n = F["n"]
     r = _arr(r, np.float64); z = np.zeros(n); work = np.zeros(max(n, 1))
@@ -245,19 +256,35 @@ def precond_apply(F, ordering, r, L=None):
     return z
 
 
-def pcg(colptr, rowind, val, F, ordering, b, tol=1e-8, maxit=1000, L=None):
-    """Oracle PCG (FP64); returns (x, iterations, true relative residual)."""
+def _precond_apply32(F, ordering, r, bound, L):
+    L = L or lib()
+    n = F["n"]
+    r = _arr(r, np.float64); z = np.zeros(n); bd = np.zeros(max(n, 1)) if bound else None
+    ordp = None if ordering is None else _arr(ordering, np.int32)
+    rc = L.orc_precond_apply32(n, _p(F["colptr"], C.c_int64), _p(_arr(F["row"], np.int32), C.c_int32),
+                               _p(_arr(F["val"], np.float64), C.c_double),
+                               _p(_arr(F["D"], np.float64), C.c_double), _p(ordp, C.c_int32),
+                               _p(r, C.c_double), _p(z, C.c_double), _p(bd, C.c_double))
+    if rc:
+        raise OracleError(rc)
+    return (z, bd[:n].copy()) if bound else z
+
+
+def pcg(colptr, rowind, val, F, ordering, b, tol=1e-8, maxit=1000, prec=64, L=None):
+    """Oracle PCG with FP64 recurrences, the factor applied in FP64 (prec=64)
+    or in the mixed FP32 form (prec=32); returns (x, iterations, true
+    relative residual)."""
     L = L or lib()
     colptr = _arr(colptr, np.int64); rowind = _arr(rowind, np.int32); val = _arr(val, np.float64)
     n = len(colptr) - 1
     b = _arr(b, np.float64); x = np.zeros(n)
     ordp = None if ordering is None else _arr(ordering, np.int32)
     it = C.c_int32(); rr = C.c_double()
-    rc = L.orc_pcg(n, _p(colptr, C.c_int64), _p(rowind, C.c_int32), _p(val, C.c_double),
-                   _p(F["colptr"], C.c_int64), _p(_arr(F["row"], np.int32), C.c_int32),
-                   _p(_arr(F["val"], np.float64), C.c_double), _p(_arr(F["D"], np.float64), C.c_double),
-                   _p(ordp, C.c_int32), _p(b, C.c_double), tol, maxit, _p(x, C.c_double),
-                   C.byref(it), C.byref(rr))
+    rc = L.orc_pcg_prec(n, _p(colptr, C.c_int64), _p(rowind, C.c_int32), _p(val, C.c_double),
+                        _p(F["colptr"], C.c_int64), _p(_arr(F["row"], np.int32), C.c_int32),
+                        _p(_arr(F["val"], np.float64), C.c_double), _p(_arr(F["D"], np.float64), C.c_double),
+                        _p(ordp, C.c_int32), _p(b, C.c_double), tol, maxit, prec, _p(x, C.c_double),
+                        C.byref(it), C.byref(rr))
     if rc:
         raise OracleError(rc)
     return x, it.value, rr.value

@@ -31,7 +31,9 @@
  *               vertex may be picked next (a seeded random choice); Sec. III
  *               "Distribution Preservation" says the result cannot depend on it.
  *   pcg         Standard preconditioned conjugate gradients (Sec. V) with
- *               M^{-1} = P^T F^{-T} D^+ F^{-1} P.
+ *               M^{-1} = P^T F^{-T} D^+ F^{-1} P, the factor applied in FP64
+ *               or, in the mixed form (readings M1-M5 below, next to the
+ *               code), stored and applied in FP32 inside FP64 recurrences.
  *
  * Readings of points the paper leaves open (each is a definition here, and
  * the CUDA path must reproduce it exactly):
@@ -771,6 +773,127 @@ void orc_precond_apply(int64_t n, const int64_t *fcp, const int32_t *frow, const
     for (int64_t k = 0; k < n; ++k) z[ordering ? ordering[k] : k] = y[k];
 }
 
+/* ------------------------------------------------------------------------ */
+/* Mixed precision: the factor stored and applied in FP32 inside FP64 PCG.   */
+/* ------------------------------------------------------------------------ */
+/* The paper runs the whole method in FP64.  The mixed form keeps the
+ * elimination and PCG's recurrences in FP64 and applies the factor in FP32,
+ * read as follows (the same reading as the FP64 apply above otherwise):
+ *   M1  F32 = RN32(F) entry by entry (round to nearest even); the right-hand
+ *       side enters the forward solve as RN32(r).
+ *   M2  forward solve in dot form: y_j = RN32(r_j) - t_j, where t_j is the
+ *       FP32 sum of the FP32 products F32(j,c) * y_c over c < j (every
+ *       product and every addition rounded to FP32).
+ *   M3  scale by D^+: D^+_k = 1 / D_k in FP64 (0 where D_k = 0); the scaled
+ *       unknown is s_k = RN32(y_k * D^+_k) with the product formed in FP64.
+ *   M4  backward solve in dot form: z_j = s_j - (FP32 sum of the FP32
+ *       products F32(i,j) * z_i over i > j).
+ *   M5  z is returned widened to FP64 (exact).
+ * The order of the FP32 sums in M2/M4 is not part of the reading: any order
+ * is a correct evaluation (this file adds in ascending index order).  The
+ * componentwise bound computed alongside holds for every order, so another
+ * evaluation is compared with this one through it; when every sum has at
+ * most two terms all orders give the same bits.
+ *
+ * Error bound (running error analysis, u = 2^-24, gamma_m = m u/(1 - m u)):
+ * with F = I + N and exact FP64 data (F, D, r), the computed forward
+ * unknowns satisfy |y^_j - (r_j - sum_c F_jc y^_c)| <= rho_j with
+ *   rho_j = gamma_{m_j+2} (|r_j| + |y^_j| + sum_c |F_jc| |y^_c|),
+ * m_j the row length; so |y^ - y| <= |F^{-1}| rho <= (I - |N|)^{-1} rho
+ * (|F^{-1}| = |sum_k (-N)^k| <= sum_k |N|^k, N nilpotent).  The scale adds
+ * D^+_k (u + 2^-51) |y^_k|; the backward solve adds, through
+ * (I - |N|^T)^{-1}, rho'_j = gamma_{m'_j+1} (|z^_j| + sum_i |F_ij| |z^_i|).
+ * Both positive triangular solves are done here in FP64 and the result is
+ * inflated by 2^-40 relative to cover their own rounding. */
+static double orc_gamma32(int64_t m)
+{
+    const double mu = (double)m * 0x1.0p-24;
+    return mu / (1.0 - mu);
+}
+
+int orc_precond_apply32(int64_t n, const int64_t *fcp, const int32_t *frow, const double *fval,
+                        const double *D, const int32_t *ordering, const double *r, double *z, double *bound)
+{
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    int64_t nnz = fcp[n];
+    size_t mm = (size_t)(nnz > 0 ? nnz : 1);
+    int64_t *rp = calloc(nn + 1, sizeof(int64_t)), *next = malloc(sizeof(int64_t) * nn);
+    int32_t *rc = malloc(sizeof(int32_t) * mm);
+    float *cv = malloc(sizeof(float) * mm), *rv = malloc(sizeof(float) * mm);
+    double *rv64 = malloc(sizeof(double) * mm);
+    float *y = malloc(sizeof(float) * nn), *s = malloc(sizeof(float) * nn), *zz = malloc(sizeof(float) * nn);
+    double *dplus = malloc(sizeof(double) * nn);
+    if (!rp || !next || !rc || !cv || !rv || !rv64 || !y || !s || !zz || !dplus) {
+        free(rp); free(next); free(rc); free(cv); free(rv); free(rv64); free(y); free(s); free(zz); free(dplus);
+        return ORC_ENOMEM;
+    }
+    for (int64_t q = 0; q < nnz; ++q) cv[q] = (float)fval[q];                       /* M1 */
+    /* rows of F (the forward solve's dot products), columns ascending */
+    for (int64_t q = 0; q < nnz; ++q) rp[frow[q] + 1]++;
+    for (int64_t j = 0; j < n; ++j) rp[j + 1] += rp[j];
+    for (int64_t j = 0; j < n; ++j) next[j] = rp[j];
+    for (int64_t k = 0; k < n; ++k)
+        for (int64_t q = fcp[k]; q < fcp[k + 1]; ++q) {
+            int64_t at = next[frow[q]]++;
+            rc[at] = (int32_t)k; rv[at] = cv[q]; rv64[at] = fval[q];
+        }
+    for (int64_t j = 0; j < n; ++j) {                                               /* M2 */
+        float t = 0.0f;
+        for (int64_t a = rp[j]; a < rp[j + 1]; ++a) {
+            float prod = rv[a] * y[rc[a]];
+            t = t + prod;
+        }
+        float rj = (float)r[ordering ? ordering[j] : j];
+        y[j] = rj - t;
+    }
+    for (int64_t k = 0; k < n; ++k) {                                               /* M3 */
+        dplus[k] = D[k] > 0.0 ? 1.0 / D[k] : 0.0;
+        s[k] = (float)((double)y[k] * dplus[k]);
+    }
+    for (int64_t j = n - 1; j >= 0; --j) {                                          /* M4 */
+        float t = 0.0f;
+        for (int64_t q = fcp[j]; q < fcp[j + 1]; ++q) {
+            float prod = cv[q] * zz[frow[q]];
+            t = t + prod;
+        }
+        zz[j] = s[j] - t;
+    }
+    for (int64_t k = 0; k < n; ++k) z[ordering ? ordering[k] : k] = (double)zz[k];  /* M5 */
+
+    if (bound) {
+        double *ey = malloc(sizeof(double) * nn), *ez = malloc(sizeof(double) * nn);
+        if (!ey || !ez) {
+            free(ey); free(ez);
+            free(rp); free(next); free(rc); free(cv); free(rv); free(rv64); free(y); free(s); free(zz); free(dplus);
+            return ORC_ENOMEM;
+        }
+        for (int64_t j = 0; j < n; ++j) {
+            double fy = 0.0, fe = 0.0;
+            for (int64_t a = rp[j]; a < rp[j + 1]; ++a) {
+                fy += fabs(rv64[a]) * fabs((double)y[rc[a]]);
+                fe += fabs(rv64[a]) * ey[rc[a]];
+            }
+            double rj = fabs(r[ordering ? ordering[j] : j]);
+            double rho = orc_gamma32(rp[j + 1] - rp[j] + 2) * (rj + fabs((double)y[j]) + fy);
+            ey[j] = rho + fe;
+        }
+        for (int64_t j = n - 1; j >= 0; --j) {
+            double es = dplus[j] * (ey[j] + (0x1.0p-24 + 0x1.0p-51) * fabs((double)y[j]));
+            double fz = 0.0, fe = 0.0;
+            for (int64_t q = fcp[j]; q < fcp[j + 1]; ++q) {
+                fz += fabs(fval[q]) * fabs((double)zz[frow[q]]);
+                fe += fabs(fval[q]) * ez[frow[q]];
+            }
+            double rho = orc_gamma32(fcp[j + 1] - fcp[j] + 1) * (fabs((double)zz[j]) + fz);
+            ez[j] = es + rho + fe;
+        }
+        for (int64_t k = 0; k < n; ++k) bound[ordering ? ordering[k] : k] = ez[k] * (1.0 + 0x1.0p-40);
+        free(ey); free(ez);
+    }
+    free(rp); free(next); free(rc); free(cv); free(rv); free(rv64); free(y); free(s); free(zz); free(dplus);
+    return ORC_OK;
+}
+
 static void spmv(int64_t n, const int64_t *cp, const int32_t *ri, const double *v, const double *x, double *y)
 {
     /* L is symmetric, so its CSC is also its CSR: y_i = sum over column i. */
@@ -792,11 +915,22 @@ static double dot(int64_t n, const double *a, const double *b)
  * ||r|| <= tol ||b|| AND the recomputed true residual ||b - L x|| <= tol ||b||,
  * or after maxit iterations.  tol <= 0 runs exactly maxit iterations.
  * Returns iterations through *iters and the true relative residual. */
-int orc_pcg(int64_t n, const int64_t *cp, const int32_t *ri, const double *v,
-            const int64_t *fcp, const int32_t *frow, const double *fval, const double *D,
-            const int32_t *ordering, const double *b, double tol, int32_t maxit,
-            double *x, int32_t *iters, double *true_relres)
+static int apply_prec(int prec, int64_t n, const int64_t *fcp, const int32_t *frow, const double *fval,
+                      const double *D, const int32_t *ordering, const double *r, double *z, double *work)
 {
+    if (prec == 32) return orc_precond_apply32(n, fcp, frow, fval, D, ordering, r, z, NULL);
+    orc_precond_apply(n, fcp, frow, fval, D, ordering, r, z, work);
+    return ORC_OK;
+}
+
+/* prec = 64: the FP64 apply; prec = 32: the mixed form (M1-M5 above) inside
+ * the same FP64 recurrences. */
+int orc_pcg_prec(int64_t n, const int64_t *cp, const int32_t *ri, const double *v,
+                 const int64_t *fcp, const int32_t *frow, const double *fval, const double *D,
+                 const int32_t *ordering, const double *b, double tol, int32_t maxit, int prec,
+                 double *x, int32_t *iters, double *true_relres)
+{
+    if (prec != 32 && prec != 64) return ORC_EINVAL;
     size_t nn = (size_t)(n > 0 ? n : 1);
     double *r = malloc(sizeof(double) * nn), *z = malloc(sizeof(double) * nn);
     double *p = malloc(sizeof(double) * nn), *q = malloc(sizeof(double) * nn);
@@ -807,7 +941,9 @@ int orc_pcg(int64_t n, const int64_t *cp, const int32_t *ri, const double *v,
     int32_t it = 0;
     double relres = nb > 0.0 ? 1.0 : 0.0;
     if (nb > 0.0) {
-        orc_precond_apply(n, fcp, frow, fval, D, ordering, r, z, work);
+        if (apply_prec(prec, n, fcp, frow, fval, D, ordering, r, z, work)) {
+            free(r); free(z); free(p); free(q); free(work); return ORC_ENOMEM;
+        }
         for (int64_t i = 0; i < n; ++i) p[i] = z[i];
         double rz = dot(n, r, z);
         while (it < maxit) {
@@ -821,7 +957,9 @@ int orc_pcg(int64_t n, const int64_t *cp, const int32_t *ri, const double *v,
                 for (int64_t i = 0; i < n; ++i) q[i] = b[i] - q[i];
                 if (sqrt(dot(n, q, q)) <= tol * nb) break;
             }
-            orc_precond_apply(n, fcp, frow, fval, D, ordering, r, z, work);
+            if (apply_prec(prec, n, fcp, frow, fval, D, ordering, r, z, work)) {
+                free(r); free(z); free(p); free(q); free(work); return ORC_ENOMEM;
+            }
             double rz2 = dot(n, r, z);
             double beta = rz2 / rz;
             rz = rz2;
@@ -835,4 +973,12 @@ int orc_pcg(int64_t n, const int64_t *cp, const int32_t *ri, const double *v,
     *true_relres = relres;
     free(r); free(z); free(p); free(q); free(work);
     return ORC_OK;
+}
+
+int orc_pcg(int64_t n, const int64_t *cp, const int32_t *ri, const double *v,
+            const int64_t *fcp, const int32_t *frow, const double *fval, const double *D,
+            const int32_t *ordering, const double *b, double tol, int32_t maxit,
+            double *x, int32_t *iters, double *true_relres)
+{
+    return orc_pcg_prec(n, cp, ri, v, fcp, frow, fval, D, ordering, b, tol, maxit, 64, x, iters, true_relres);
 }

@@ -409,6 +409,133 @@ def test_pcg_path_converges_at_once():
     assert it <= 2 and rr <= 1e-8
 
 
+# ----------------------------------------------------------------- mixed precision (FP32 factor)
+# The mixed form keeps the elimination and PCG's recurrences in FP64 and
+# applies the factor in FP32: F rounded to FP32, FP32 triangular solves, D^+
+# applied in FP64 with the product rounded to FP32 (readings M1-M5 in the
+# oracle's source).
+
+U32 = 2.0 ** -24
+
+
+def _path_identity(n, w):
+    """Path 0-1-...-(n-1) with edge weights w, eliminated in label order: every
+    pivot has one neighbour, so the factor is exact with F(j+1,j) = -1 and
+    D_j = w_j (D_{n-1} = 0), and every solve row and column has one entry."""
+    a, b = W.path_edges(n)
+    A = _mat(n, a, b, w)
+    return A, oracle.factor(A.colptr, A.rowind, A.val, None, seed=1)
+
+
+def test_fp32_apply_exact_when_the_arithmetic_is_exact():
+    """Unit-weight path, integer residual: every FP32 operation is exact, so
+    the mixed apply equals the FP64 apply bit for bit, and both equal the
+    closed form (prefix sums, then suffix sums of all but the last)."""
+    n = 200
+    A, F = _path_identity(n, np.ones(n - 1))
+    assert np.all(F["val"] == -1.0) and np.all(F["D"][:-1] == 1.0) and F["D"][-1] == 0.0
+    r = np.random.default_rng(3).integers(-10, 11, n).astype(float)
+    z64 = oracle.precond_apply(F, None, r)
+    z32 = oracle.precond_apply(F, None, r, prec=32)
+    s = np.cumsum(r); s[-1] = 0.0
+    closed = np.cumsum(s[::-1])[::-1]
+    assert np.array_equal(z32, z64) and np.array_equal(z64, closed)
+
+
+def test_fp32_apply_error_on_a_path_grows_with_its_length():
+    """Exact path factor with weights in [1, 2): F = -1 exactly, so the only
+    roundings are r -> FP32, one addition per forward step, the FP32 scale
+    and one addition per backward step.  With R1 = sum |r| bounding every
+    forward partial sum and Z1 = sum |s| every backward one,
+      |y^_j - y_j| <= (j+1) 2u R1,   |s^_j - s_j| <= (|y^_j - y_j| + 2u R1)/w_j,
+      |z^_j - z_j| <= sum_{i>=j} |s^_i - s_i| + (n-j) 2u Z1,
+    a bound linear in the path length per solve.  The FP32 apply stays within
+    it, and within the oracle's own running-error bound."""
+    for n in (10, 300, 3000):
+        rng = np.random.default_rng(n)
+        w = rng.uniform(1, 2, n - 1)
+        A, F = _path_identity(n, w)
+        r = rng.standard_normal(n)
+        z64 = oracle.precond_apply(F, None, r)
+        z32, bd = oracle.precond_apply(F, None, r, prec=32, bound=True)
+        R1 = np.abs(r).sum()
+        ey = (np.arange(n) + 1) * 2 * U32 * R1
+        s = np.cumsum(r)[:-1] / w
+        Z1 = np.abs(s).sum() * (1 + 1e-6)
+        es = np.append((ey[:-1] + 2 * U32 * R1) / w, 0.0)
+        ez = np.cumsum(es[::-1])[::-1] + (n - np.arange(n)) * 2 * U32 * Z1
+        err = np.abs(z32 - z64)
+        assert np.all(err <= ez * (1 + 1e-6))
+        assert np.all(err <= bd * (1 + 2.0 ** -20))
+        assert err.max() > 0.0 or n == 10
+
+
+def _fp32_cases():
+    out = [W.config("grid2d-64")[:2]]
+    rng = np.random.default_rng(8)
+    for s in range(3):
+        n = int(rng.integers(200, 2000))
+        a, b = W.sparse_random_edges(n, 4 * n, 30 + s)
+        exc = rng.uniform(0, 0.5, n) if s == 1 else None
+        out.append((_mat(n, a, b, rng.lognormal(0, 1, len(a)), exc), W.random_ordering(n, s)))
+    n = 500
+    a, b = W.path_edges(n)
+    out.append((_mat(n, a, b, rng.uniform(1, 2, n - 1)), W.random_ordering(n, 9)))
+    return out
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_fp32_apply_within_running_error_bound(case):
+    """On grids, random (also SDDM) graphs and a randomly ordered path, the
+    mixed apply differs from the FP64 apply by at most the componentwise
+    running-error bound, which is not vacuous (below 1% of |z|), and the
+    difference is FP32-sized (FP32 arithmetic was really used)."""
+    A, perm = _fp32_cases()[case]
+    F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=case)
+    r = np.random.default_rng(case).standard_normal(A.n)
+    z64 = oracle.precond_apply(F, perm, r)
+    z32, bd = oracle.precond_apply(F, perm, r, prec=32, bound=True)
+    err = np.abs(z32 - z64)
+    assert np.all(err <= bd * (1 + 2.0 ** -20))
+    assert bd.max() <= 1e-2 * np.abs(z64).max()
+    assert 1e-10 * np.abs(z64).max() < err.max()
+
+
+def test_fp32_bound_catches_a_dropped_term():
+    """A factor with one entry removed (a plausible kernel mistake, planted
+    here on the CPU) moves the apply far outside the bound."""
+    A, perm = _fp32_cases()[1]
+    F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=1)
+    r = np.random.default_rng(5).standard_normal(A.n)
+    z64 = oracle.precond_apply(F, perm, r)
+    Fm = dict(F); Fm["val"] = F["val"].copy()
+    Fm["val"][len(F["val"]) // 2] = 0.0
+    zb, _ = oracle.precond_apply(Fm, perm, r, prec=32, bound=True)
+    _, bd = oracle.precond_apply(F, perm, r, prec=32, bound=True)
+    assert np.any(np.abs(zb - z64) > bd)
+
+
+def test_fp32_pcg():
+    """PCG with the FP32 factor keeps FP64 recurrences and reaches the same
+    true relative residual.  With an exact factor (a path) the FP64 apply is
+    L's pseudo-inverse on the range, so PCG stops after one iteration; the FP32
+    apply is that inverse perturbed by an FP32-sized error, which one more
+    iteration removes to 1e-8."""
+    for A, perm in _fp32_cases()[:4]:
+        F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=4)
+        sddm = A.dense().sum(axis=1).max() > 1e-9
+        b = W.gaussian_rhs(A.n, 1, 6, center=not sddm)
+        _, it64, rr64 = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, b, 1e-8, 1000)
+        _, it32, rr32 = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, b, 1e-8, 1000, prec=32)
+        assert rr64 <= 1e-8 and rr32 <= 1e-8
+    n = 200
+    A, F = _path_identity(n, np.ones(n - 1))
+    b = np.random.default_rng(1).integers(-10, 11, n).astype(float); b -= b.mean()
+    x64, i64, r64 = oracle.pcg(A.colptr, A.rowind, A.val, F, None, b, 1e-8, 50)
+    x32, i32, r32 = oracle.pcg(A.colptr, A.rowind, A.val, F, None, b, 1e-8, 50, prec=32)
+    assert i64 == 1 and r64 <= 1e-8 and i32 <= 2 and r32 <= 1e-8
+
+
 # ----------------------------------------------------------------- AC(k)
 # AC(k) (Sec. VI, after Gao-Kyng-Spielman): every slot of the clique tree
 # draws k neighbours, sample q with Philox counter (k, p, sys, q), each edge
