@@ -75,6 +75,20 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Device memory the given device can use directly: memory allocated on it,
+// or managed memory.
+bool on_device(const void *p, int device)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == device;
+}
+
 // Stream-ordered device buffer.
 struct DBuf {
     void *p = nullptr;
@@ -1714,6 +1728,10 @@ extern "C" parac_status parac_pcg_many(int32_t count, const parac_factor_t *G, c
                                        double *true_relres)
 {
     return guarded([&]() -> parac_status {
+        // both paths switch to the handles' device (the batch on this thread,
+        // the last worker on this thread too); the caller's device comes back
+        struct Restore { int dev = -1; ~Restore() { if (dev >= 0) cudaSetDevice(dev); } } restore;
+        CK(cudaGetDevice(&restore.dev));
         if (count < 0 || (count > 0 && (!G || !b || !x))) { set_err("bad arguments to parac_pcg_many"); return PARAC_EINVAL; }
         for (int32_t i = 0; i < count; ++i) {
             if (G[i] && G[i]->n > 0 && (!b[i] || !x[i])) {
@@ -1724,9 +1742,6 @@ extern "C" parac_status parac_pcg_many(int32_t count, const parac_factor_t *G, c
                 if (G[i] == G[j]) { set_err("parac_pcg_many: handle %d repeats handle %d", i, j); return PARAC_EINVAL; }
         }
         if (batchable(count, G)) {
-            // the batch runs on the handles' device; the caller's current device is restored after it
-            struct Restore { int dev = -1; ~Restore() { if (dev >= 0) cudaSetDevice(dev); } } restore;
-            CK(cudaGetDevice(&restore.dev));
             try {
                 return pcg_batch(count, G, b, x, tol, maxit, iters, true_relres);
             } catch (const StatusFail &e) {
@@ -1926,17 +1941,19 @@ extern "C" parac_status parac_precond_apply_noalloc(parac_factor_t G, const doub
             return PARAC_EINVAL;
         }
         if (G->n == 0) return PARAC_OK;
-        if (!is_device_ptr(r) || !is_device_ptr(z)) { set_err("r and z must be device memory"); return PARAC_EINVAL; }
-        int cur = 0;
-        CK(cudaGetDevice(&cur));
-        if (cur != G->device) CK(cudaSetDevice(G->device));
+        if (!on_device(r, G->device) || !on_device(z, G->device)) {
+            set_err("r and z must be device memory of the factor's device %d", G->device);
+            return PARAC_EINVAL;
+        }
+        // the caller's current device comes back on every return, errors included
+        struct Restore { int dev = -1; ~Restore() { if (dev >= 0) cudaSetDevice(dev); } } restore;
+        CK(cudaGetDevice(&restore.dev));
+        if (restore.dev != G->device) CK(cudaSetDevice(G->device));
         cudaStream_t st = G->stream;
         SolveArgs A = solve_args(G, G->Lp.as<int64_t>(), G->Li.as<int32_t>(), G->Lv.as<double>(), G->nnzL);
         CK(cudaMemsetAsync(G->status.p, 0, 4, st));
         CK(precond_apply_noalloc(A, r, z, st));
-        const int32_t dst = read_dev_status(G, st);
-        if (cur != G->device) CK(cudaSetDevice(cur));
-        if (dst != ST_OK) { set_err("triangular solve wait exceeded the spin limit"); return PARAC_ETIMEOUT; }
+        if (read_dev_status(G, st) != ST_OK) { set_err("triangular solve wait exceeded the spin limit"); return PARAC_ETIMEOUT; }
         return PARAC_OK;
     });
 }
