@@ -1,18 +1,26 @@
 #!/usr/bin/env python
 """Benchmark of the randomized approximate-Cholesky setup and PCG solve.
 
-One step = the whole hot path on one synthetic system already resident in
-HBM: parac_factor (ingest, persistent elimination, compaction, solve-schedule
-analysis) followed by parac_pcg to a true relative residual of 1e-8, then the
-handle is released.  Headline value: setup throughput in Mnnz(G)/s, with
-nnz(G) = nnz(F) + n (strict-lower factor entries plus the unit diagonal) and
-the setup time measured with CUDA events around parac_factor.  Time-to-solution
-(setup + PCG) is reported beside it.
+Metric: setup throughput in Mnnz(G)/s and time to solution (setup + PCG to a
+true relative residual of 1e-8), for the FP64 method and beside it for the
+mixed form (FP32-stored factor) and the batched form (many systems in one
+parac_factor_many launch against one parac_factor call per system).
+nnz(G) = nnz(F) + n (strict-lower factor entries plus the unit diagonal).
+
+One step of the default run (inputs already resident in HBM, L2 flushed
+before every phase, every phase timed with CUDA events):
+  1. parac_factor of the 128^3 grid with the factor in FP64, then parac_pcg;
+  2. the same with the factor stored and applied in FP32 (mixed form);
+  3. parac_factor_many of the 200-system SDDM batch (FP32 factors), then
+     parac_pcg_many on all of them;
+  4. the same 200 systems factored one parac_factor call at a time.
+value = nnz(G) of step 1 over its setup time; mixed_over_fp64_tts and
+batched_over_loop are the ratios of steps 1/2 and 3/4.
 
   python bench.py [--steps K] [--warmup W] [--workload grid3d-128] [--prec 64|32]
-                  [--ordering random|nnz]
-  python bench.py --workload sddm-batch-200   # 200 SDDM systems: parac_factor_many vs a loop
-  python bench.py --impl reference     # the CPU oracle on the same workload
+                  [--ordering random|nnz] [--no-mixed] [--batch auto|on|off]
+  python bench.py --workload sddm-batch-200   # the batch alone
+  python bench.py --impl reference            # the CPU oracle on the same workload
 
 Workloads: grid3d-128 (default), grid2d-64, rmat-N (R-MAT scale N), rmat-24
 (32 right-hand sides, block PCG), sddm-batch-200, poisson-{uniform,aniso,contrast}-N.
@@ -197,22 +205,83 @@ def aggregate(values_per_rank_units, times_per_rank):
     return sum(values_per_rank_units) / max(times_per_rank)
 
 
+# --------------------------------------------------------------------------- shared by both arms
+METRIC = "setup Mnnz(G)/s; time-to-solution to rel-res 1e-8, mixed/batched vs FP64"
+MIXED_DESC = "FP32-stored factor applied by FP32 triangular solves; FP64 elimination and PCG recurrences"
+BATCH_SEED = 31
+
+
+def use_batch(args):
+    return args.batch == "on" or (args.batch == "auto" and args.workload == "grid3d-128")
+
+
+def use_mixed(args):
+    return not args.no_mixed and args.prec == 64 and not args.workload.startswith("sddm-batch")
+
+
+def line_config(args, A, nrhs, world):
+    """The workload description both arms print."""
+    cfg = {"workload": WORKLOAD_DESC.get(args.workload, args.workload), "n": A.n, "nnz_L": A.nnz,
+           "G_precision": args.prec, "tol": args.tol, "ordering": args.ordering,
+           "samples_per_slot": args.samples, "nrhs": nrhs}
+    if use_mixed(args):
+        cfg["mixed"] = MIXED_DESC
+    if use_batch(args):
+        cfg["batch"] = WORKLOAD_DESC["sddm-batch-200"] + "; FP32-stored factors; vs one parac_factor call each"
+    cfg["l2"] = "flushed before every timed phase (256 MB write)"
+    cfg["parallelism"] = f"replicas x{world}"
+    return cfg
+
+
+def same_bits(Fa, Fb):
+    """Bitwise equality of two exported factors (structure, values, pivots)."""
+    return (Fa["n"] == Fb["n"] and np.array_equal(Fa["colptr"], Fb["colptr"])
+            and np.array_equal(Fa["row"], Fb["row"])
+            and np.array_equal(np.asarray(Fa["val"]).view(np.uint64), np.asarray(Fb["val"]).view(np.uint64))
+            and np.array_equal(np.asarray(Fa["D"]).view(np.uint64), np.asarray(Fb["D"]).view(np.uint64)))
+
+
+def oracle_solve(A, perm, seed, b, args, gpu_factor=None):
+    """The oracle as it stands on one host core: one sequential factorisation
+    and one PCG solve of the workload (FP64), timed separately; with the GPU's
+    exported factor, a bitwise comparison of the two."""
+    import oracle
+    t0 = time.perf_counter()
+    F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed, samples=args.samples)
+    tf = time.perf_counter() - t0
+    nnzG = len(F["row"]) + F["n"]
+    bb = b if b.ndim == 1 else np.ascontiguousarray(b[:, 0])
+    t0 = time.perf_counter()
+    _, it, rr = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, bb, args.tol, 2000)
+    tp = time.perf_counter() - t0
+    out = {"value": nnzG / tf / 1e6, "unit": "Mnnz(G)/s", "cores": 1, "kind": "oracle",
+           "sample": f"one full sequential oracle factorisation ({tf:.1f} s) and one FP64 PCG solve "
+                     f"({tp:.1f} s, first right-hand side) of {args.workload}",
+           "fact_s": tf, "pcg_s": tp, "pcg_iters": int(it), "true_relres": float(rr), "tts_s": tf + tp,
+           "nnz_G": nnzG}
+    if gpu_factor is not None:
+        out["bit_identical"] = bool(same_bits(gpu_factor, F))
+    return out
+
+
 # --------------------------------------------------------------------------- reference arm (CPU oracle)
-def oracle_batch_sample(batch, seed, budget_s):
+def oracle_batch_sample(batch, seed, budget_s, gpu_factors=None):
     """The oracle on the batch's systems in order, system s keyed as in
     parac_factor_many (Philox counter word 2 = s), until budget_s seconds of
     host time are spent (at least one system); returns (nnz(G) of each system
-    factored, seconds)."""
+    factored, seconds, all bitwise equal to gpu_factors[s] or None)."""
     import oracle
-    nnz, t = [], 0.0
+    nnz, t, same = [], 0.0, None if gpu_factors is None else True
     for s, (A, perm, b) in enumerate(batch):
         t0 = time.perf_counter()
         F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed, sys=s)
         t += time.perf_counter() - t0
         nnz.append(len(F["row"]) + F["n"])
+        if gpu_factors is not None:
+            same = same and same_bits(gpu_factors[s], F)
         if t >= budget_s:
             break
-    return nnz, t
+    return nnz, t, same
 
 
 def run_reference_batch(args, world, rank):
@@ -221,20 +290,20 @@ def run_reference_batch(args, world, rank):
     from paper_2505_02977_gb300 import workloads as W
     batch = W.sddm_batch(200)
     for _ in range(args.warmup):
-        oracle_batch_sample(batch[:1], 31, 0.0)
+        oracle_batch_sample(batch[:1], BATCH_SEED, 0.0)
     vals, steps_s, last = [], [], None
     for _ in range(args.steps):
-        nnz, t = oracle_batch_sample(batch, 31, args.cpu_budget)
+        nnz, t, _ = oracle_batch_sample(batch, BATCH_SEED, args.cpu_budget)
         vals.append(sum(nnz) / t / 1e6); steps_s.append(t); last = nnz
     value = sum(vals) / len(vals)
     sample = (f"the first {len(last)} of 200 systems in order (nnz(G) {sum(last)}), about {args.cpu_budget:g} s "
               "of sequential oracle work per step")
     line = {
-        "impl": "reference", "metric": "setup Mnnz(G)/s", "value": value, "unit": "Mnnz(G)/s",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mnnz(G)/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(steps_s) / len(steps_s), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC[args.workload], "systems": 200},
+        "config": batch_config(args, batch, world),
         "cpu_baseline": {"value": value, "unit": "Mnnz(G)/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "Mnnz(G)/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -243,6 +312,9 @@ def run_reference_batch(args, world, rank):
 
 
 def run_reference(args, world, rank):
+    """The oracle on our arm's workload: each step is one full sequential
+    factorisation (the metric's setup); one FP64 PCG solve after the steps
+    gives the oracle's time to solution."""
     if rank != 0:
         return 0
     if args.workload == "sddm-batch-200":
@@ -250,6 +322,8 @@ def run_reference(args, world, rank):
     import oracle
     from paper_2505_02977_gb300 import workloads as W
     A, perm, seed, b = W.config(args.workload)
+    if args.ordering == "nnz":
+        perm = W.nnz_sorted_ordering(A, seed + 1000)
     small = W.config("grid2d-64")
     for _ in range(args.warmup):                     # untimed warm-up on a small case
         oracle.factor(small[0].colptr, small[0].rowind, small[0].val, small[1], seed=small[2])
@@ -260,14 +334,23 @@ def run_reference(args, world, rank):
         times.append(time.perf_counter() - t0)
         nnzG = len(F["row"]) + F["n"]
     value = nnzG * len(times) / sum(times) / 1e6
+    bb = b if b.ndim == 1 else np.ascontiguousarray(b[:, 0])
+    t0 = time.perf_counter()
+    _, it, rr = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, bb, args.tol, 2000)
+    tp = time.perf_counter() - t0
+    tf = sum(times) / len(times)
     line = {
-        "impl": "reference", "metric": "setup Mnnz(G)/s", "value": value, "unit": "Mnnz(G)/s",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mnnz(G)/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * tf, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload), "nnz_G": nnzG},
+        "config": line_config(args, A, 1 if b.ndim == 1 else int(b.shape[1]), world),
+        "nnz_G": nnzG, "tts_ms": 1e3 * (tf + tp), "setup_ms": 1e3 * tf, "pcg_ms": 1e3 * tp,
+        "pcg_iters": int(it), "true_relres": float(rr),
         "cpu_baseline": {"value": value, "unit": "Mnnz(G)/s", "cores": 1, "kind": "oracle",
-                         "sample": f"full sequential oracle factorisation of {args.workload} per step"},
+                         "sample": f"full sequential oracle factorisation of {args.workload} per step; "
+                                   f"one FP64 PCG solve ({tp:.1f} s) after the steps",
+                         "fact_s": tf, "pcg_s": tp, "pcg_iters": int(it), "tts_s": tf + tp},
         "e2e": {"value": value, "unit": "Mnnz(G)/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -275,6 +358,26 @@ def run_reference(args, world, rank):
 
 
 # --------------------------------------------------------------------------- our arm
+class Phases:
+    """CUDA events around the named phases of every timed step (all on the
+    stream the library runs on: the legacy default stream)."""
+
+    def __init__(self, names, steps):
+        import torch
+        self.names = names
+        self.ev = {nm: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                        for _ in range(steps)] for nm in names}
+
+    def start(self, nm, s):
+        self.ev[nm][s][0].record()
+
+    def stop(self, nm, s):
+        self.ev[nm][s][1].record()
+
+    def ms(self, nm):
+        return [a.elapsed_time(b) for a, b in self.ev[nm]]
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
     from paper_2505_02977_gb300 import build as B
@@ -289,53 +392,92 @@ def run_ours(args, world, rank, local, pg):
     A, perm, seed, b = W.config(args.workload)
     if args.ordering == "nnz":
         perm = W.nnz_sorted_ordering(A, seed + 1000)
+    nrhs = 1 if b.ndim == 1 else int(b.shape[1])
     td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     cp, ri, va, od, bd = td(A.colptr), td(A.rowind), td(A.val), td(perm), td(b)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # > L2 (129 MB)
-    opts = P.parac_opts_default(g_precision=args.prec, timing=1, samples=args.samples)
+    precs = [args.prec] + ([32] if use_mixed(args) else [])
+    opts = {p: P.parac_opts_default(g_precision=p, timing=1, samples=args.samples) for p in precs}
 
-    def step():
-        G = P.parac_factor(A.n, cp, ri, va, od, seed, opts)
-        x, it, rr, status = P.parac_pcg(G, A.n, None, None, None, bd, tol=args.tol, maxit=2000)
-        return G, it[0], rr[0], status
+    bsys = brhs = bopts = tune = None
+    if use_batch(args):
+        batch = W.sddm_batch(200)
+        bsys = [(Ab.n, td(Ab.colptr), td(Ab.rowind), td(Ab.val), td(pb)) for (Ab, pb, _) in batch]
+        brhs = [td(bb) for (_, _, bb) in batch]
+        bopts, tune = P.parac_autotune(bsys[::10], BATCH_SEED, P.parac_opts_default(g_precision=32))
+
+    phases = ["setup", "pcg"] + (["setup_mixed", "pcg_mixed"] if len(precs) > 1 else [])
+    if bsys:
+        phases += ["batch_setup", "batch_pcg", "loop_setup"]
+    res = {"iters": {p: [] for p in precs}, "relres": {p: [] for p in precs}, "status": set(), "stats": {},
+           "b_its": [], "b_rr": [], "b_nnz": 0, "loop_nnz": 0}
+
+    def step(ph, s):
+        for p in precs:
+            flush.zero_()
+            tag = "" if p == args.prec else "_mixed"
+            if ph: ph.start("setup" + tag, s)
+            G = P.parac_factor(A.n, cp, ri, va, od, seed, opts[p])
+            if ph: ph.stop("setup" + tag, s); ph.start("pcg" + tag, s)
+            _, it, rr, status = P.parac_pcg(G, A.n, None, None, None, bd, tol=args.tol, maxit=2000)
+            if ph:
+                ph.stop("pcg" + tag, s)
+                res["iters"][p].append(int(max(it))); res["relres"][p].append(float(max(rr)))
+                res["status"].add(status)
+                if p not in res["stats"]:
+                    res["stats"][p] = G.stats()
+            G.free()
+        if bsys:
+            flush.zero_()
+            if ph: ph.start("batch_setup", s)
+            Gs = P.parac_factor_many(bsys, BATCH_SEED, bopts)
+            if ph: ph.stop("batch_setup", s); ph.start("batch_pcg", s)
+            _, its, rrs, bstat = P.parac_pcg_many(Gs, brhs, tol=args.tol, maxit=2000)
+            if ph:
+                ph.stop("batch_pcg", s)
+                res["b_its"] += [int(v) for v in its]; res["b_rr"] += [float(v) for v in rrs]
+                res["status"].add(bstat)
+                if not res["b_nnz"]:
+                    res["b_nnz"] = sum(G.stats()["nnz_G"] for G in Gs)
+            for G in Gs:
+                G.free()
+            flush.zero_()
+            if ph: ph.start("loop_setup", s)
+            Gl = [P.parac_factor(*sy, BATCH_SEED + i, bopts) for i, sy in enumerate(bsys)]
+            if ph:
+                ph.stop("loop_setup", s)
+                if not res["loop_nnz"]:
+                    res["loop_nnz"] = sum(G.stats()["nnz_G"] for G in Gl)
+            for G in Gl:
+                G.free()
 
     for _ in range(args.warmup):
-        G, *_ = step()
-        G.free()
+        step(None, 0)
     torch.cuda.synchronize()
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    ph = Phases(phases, args.steps)
     clocks = ClockSampler(local)
     barrier(pg)
     torch.cuda.synchronize()
     launches0 = P.parac_kernel_launches()
     clocks.start()
     t_wall0 = time.perf_counter()
-    iters, relres, stats, statuses = [], [], None, []
     for s in range(args.steps):
-        flush.zero_()
-        ev[s][0].record()
-        G = P.parac_factor(A.n, cp, ri, va, od, seed, opts)
-        ev[s][1].record()
-        x, it, rr, status = P.parac_pcg(G, A.n, None, None, None, bd, tol=args.tol, maxit=2000)
-        ev[s][2].record()
-        iters.append(int(max(it))); relres.append(float(max(rr))); statuses.append(status)
-        if stats is None:
-            stats = G.stats()
-        G.free()
+        step(ph, s)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     launches = P.parac_kernel_launches() - launches0
     barrier(pg)
-    setup_ms = [ev[s][0].elapsed_time(ev[s][1]) for s in range(args.steps)]
-    pcg_ms = [ev[s][1].elapsed_time(ev[s][2]) for s in range(args.steps)]
-    step_ms = [a + b for a, b in zip(setup_ms, pcg_ms)]
-    nnzG = stats["nnz_G"]
+    ms = {nm: ph.ms(nm) for nm in phases}
+    step_ms = [sum(ms[nm][s] for nm in phases) for s in range(args.steps)]
+    med = {nm: statistics.median(v) for nm, v in ms.items()}
+    st64 = res["stats"][args.prec]
+    nnzG = st64["nnz_G"]
 
     # dominant kernel: the elimination (timed by the library with events around
     # its launch) or the triangular-solve pair of the preconditioner (timed here)
-    G = P.parac_factor(A.n, cp, ri, va, od, seed, opts)
+    G = P.parac_factor(A.n, cp, ri, va, od, seed, opts[args.prec])
     st_el = G.stats()
     r = td(np.random.default_rng(0).standard_normal(A.n))      # one right-hand side: the single-vector solves
     z = torch.empty_like(r)
@@ -348,75 +490,97 @@ def run_ours(args, world, rank, local, pg):
     e1.record()
     torch.cuda.synchronize()
     trsv_ms = e0.elapsed_time(e1) / reps
+    gpu_factor = G.export() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     G.free()
     elim_ms = st_el["t_elim_ms"]
     peak, peak_kind = measured_peak_hbm()
-    applies = statistics.median(iters) + 1
+    applies = statistics.median(res["iters"][args.prec]) + 1
     if elim_ms >= trsv_ms * applies:
         name, t_ms, alg = "elim_kernel", elim_ms, algorithmic_bytes_elim(st_el)
     else:
         name, t_ms, alg = "k_trsv_fwd+k_trsv_bwd", trsv_ms, algorithmic_bytes_trsv_pair(st_el, args.prec)
     achieved = alg / (t_ms * 1e-3) / 1e9
 
-    # end to end through the public API with host buffers
+    # end to end through the public API: inputs from pinned host memory every
+    # step, the solution read back to the host
     e2e = None
     if not args.no_e2e:
-        b_host = np.ascontiguousarray(b)
-        P.parac_factor(A.n, A.colptr, A.rowind, A.val, perm, seed, opts).free()
+        hp = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hcp, hri, hva, hod, hb = hp(A.colptr), hp(A.rowind), hp(A.val), hp(perm), hp(b)
+        xh = torch.empty(hb.shape[::-1] if nrhs > 1 else hb.shape, dtype=torch.float64).pin_memory()
+        if nrhs > 1:
+            xh = xh.t()
+        P.parac_factor(A.n, hcp, hri, hva, hod, seed, opts[args.prec]).free()
         e2e_setup, e2e_tts = [], []
-        for _ in range(2):
+        for _ in range(3):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            G = P.parac_factor(A.n, A.colptr, A.rowind, A.val, perm, seed, opts)
-            G.stats()
+            G = P.parac_factor(A.n, hcp, hri, hva, hod, seed, opts[args.prec])
             t1 = time.perf_counter()
-            xh, _, _, _ = P.parac_pcg(G, A.n, None, None, None, b_host, tol=args.tol, maxit=2000)
+            P.parac_pcg(G, A.n, None, None, None, hb, tol=args.tol, maxit=2000, X=xh)
             t2 = time.perf_counter()
             G.free()
             e2e_setup.append(t1 - t0); e2e_tts.append(t2 - t0)
-        h2d = A.colptr.nbytes + A.rowind.nbytes + A.val.nbytes + perm.nbytes
+        h2d = A.colptr.nbytes + A.rowind.nbytes + A.val.nbytes + perm.nbytes + b.nbytes
         e2e = {"value": nnzG / statistics.median(e2e_setup) / 1e6, "unit": "Mnnz(G)/s",
-               "h2d_bytes_per_step": int(h2d + b_host.nbytes), "d2h_bytes_per_step": int(b_host.nbytes + 4096),
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(8 * A.n * nrhs + 4096),
                "tts_ms": 1e3 * statistics.median(e2e_tts)}
 
-    total_setup_s = allreduce_max(pg, sum(setup_ms) * 1e-3)
+    total_setup_s = allreduce_max(pg, sum(ms["setup"]) * 1e-3)
     mean_step = allreduce_max(pg, statistics.mean(step_ms))
     value = world * nnzG * args.steps / total_setup_s / 1e6
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        t0 = time.perf_counter()
-        F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed, samples=args.samples)
-        tc = time.perf_counter() - t0
-        cpu = {"value": (len(F["row"]) + F["n"]) / tc / 1e6, "unit": "Mnnz(G)/s", "cores": 1, "kind": "oracle",
-               "sample": f"one full sequential oracle factorisation of {args.workload} ({tc:.1f} s)",
-               "bit_identical": bool(len(F["row"]) + F["n"] == nnzG)}
+    if gpu_factor is not None:
+        cpu = oracle_solve(A, perm, seed, b, args, gpu_factor)
+        gpu_factor = None
 
+    tts64 = med["setup"] + med["pcg"]
     line = {
-        "metric": "setup Mnnz(G)/s; time-to-solution to rel-res 1e-8 in tts_ms",
-        "value": value, "unit": "Mnnz(G)/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": mean_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload), "n": A.n, "nnz_L": A.nnz,
-                   "nnz_G": nnzG, "G_precision": args.prec, "tol": args.tol, "ordering": args.ordering,
-                   "samples_per_slot": args.samples,
-                   "nrhs": 1 if b.ndim == 1 else int(b.shape[1]),
-                   "l2": "flushed before every step (256 MB write)", "parallelism": f"replicas x{world}"},
-        "tts_ms": statistics.median(step_ms), "setup_ms": statistics.median(setup_ms),
-        "pcg_ms": statistics.median(pcg_ms), "pcg_iters": statistics.median(iters),
-        "true_relres": max(relres), "pcg_status": sorted(set(statuses)),
-        "vertices_per_s": A.n / (statistics.median(setup_ms) * 1e-3),
-        "elim_ms": elim_ms, "depth": st_el.get("depth"),
+        "metric": METRIC, "value": value, "unit": "Mnnz(G)/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.prec == 64 else "f64+f32G", "data": "synthetic",
+        "config": line_config(args, A, nrhs, world),
+        "nnz_G": nnzG, "tts_ms": tts64, "setup_ms": med["setup"], "pcg_ms": med["pcg"],
+        "pcg_iters": statistics.median(res["iters"][args.prec]), "true_relres": max(res["relres"][args.prec]),
+        "pcg_status": sorted(res["status"]),
+        "vertices_per_s": A.n / (med["setup"] * 1e-3), "elim_ms": elim_ms, "depth": st_el.get("depth"),
+    }
+    if "setup_mixed" in med:
+        tts32 = med["setup_mixed"] + med["pcg_mixed"]
+        line["mixed"] = {"dtype": "f64+f32G", "tts_ms": tts32, "setup_ms": med["setup_mixed"], "pcg_ms": med["pcg_mixed"],
+                         "pcg_iters": statistics.median(res["iters"][32]), "true_relres": max(res["relres"][32]),
+                         "nnz_G": res["stats"][32]["nnz_G"]}
+        line["mixed_over_fp64_tts"] = tts64 / tts32
+        line["mixed_over_fp64_pcg"] = med["pcg"] / med["pcg_mixed"]
+    if bsys:
+        bval = res["b_nnz"] / (med["batch_setup"] * 1e-3) / 1e6
+        lval = res["loop_nnz"] / (med["loop_setup"] * 1e-3) / 1e6
+        line["batched"] = {"dtype": "f64+f32G", "systems": len(bsys), "n_total": int(sum(s[0] for s in bsys)),
+                           "nnz_G": res["b_nnz"], "value": bval, "unit": "Mnnz(G)/s",
+                           "setup_ms": med["batch_setup"], "pcg_ms": med["batch_pcg"],
+                           "tts_ms": med["batch_setup"] + med["batch_pcg"],
+                           "pcg_iters_mean": float(np.mean(res["b_its"])), "pcg_iters_max": int(max(res["b_its"])),
+                           "true_relres_max": max(res["b_rr"]),
+                           "one_at_a_time": {"value": lval, "setup_ms": med["loop_setup"], "nnz_G": res["loop_nnz"]},
+                           "schedule": tune["best"]}
+        line["batched_over_loop"] = bval / lval
+    line.update({
         "roofline": {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind, "traffic": recorded_traffic(name, alg),
                      "algorithmic_bytes": alg, "kernel_ms": t_ms},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-        "wall_s": t_wall,
-    }
+        "phases_ms": med, "wall_s": t_wall,
+    })
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def batch_config(args, batch, world):
+    return {"workload": WORKLOAD_DESC["sddm-batch-200"], "systems": len(batch),
+            "n_total": int(sum(A.n for A, _, _ in batch)), "G_precision": args.prec, "tol": args.tol,
+            "l2": "flushed before every timed phase (256 MB write)", "parallelism": f"replicas x{world}"}
 
 
 def run_batch(args, world, rank, local, pg):
@@ -434,8 +598,8 @@ def run_batch(args, world, rank, local, pg):
     rhs = [td(b) for (A, perm, b) in batch]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     base = P.parac_opts_default(g_precision=args.prec)
-    opts, tune_report = P.parac_autotune(systems[::10], 31, base)
-    seed = 31
+    opts, tune_report = P.parac_autotune(systems[::10], BATCH_SEED, base)
+    seed = BATCH_SEED
 
     def solve_all(Gs):
         xs, it, rr, st = P.parac_pcg_many(Gs, rhs, tol=args.tol, maxit=2000)
@@ -446,31 +610,33 @@ def run_batch(args, world, rank, local, pg):
         solve_all(Gs)
         for G in Gs: G.free()
     torch.cuda.synchronize()
+    ph = Phases(["setup", "pcg"], args.steps)
     clocks = ClockSampler(local)
     barrier(pg)
     torch.cuda.synchronize()
     launches0 = P.parac_kernel_launches()
     clocks.start()
-    setup_ms, pcg_ms, its_all, rr_all, nnzG = [], [], [], [], 0
+    its_all, rr_all, nnzG, gpu_factors = [], [], 0, None
     for s in range(args.steps):
         flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        ph.start("setup", s)
         Gs = P.parac_factor_many(systems, seed, opts)
-        t1 = time.perf_counter()
+        ph.stop("setup", s); ph.start("pcg", s)
         its, rrs = solve_all(Gs)
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        setup_ms.append(1e3 * (t1 - t0)); pcg_ms.append(1e3 * (t2 - t1))
+        ph.stop("pcg", s)
         its_all += its; rr_all += rrs
-        nnz_sys = [G.stats()["nnz_G"] for G in Gs]
-        nnzG = sum(nnz_sys)
+        if s == 0:
+            nnzG = sum(G.stats()["nnz_G"] for G in Gs)
+            if rank == 0 and world == 1 and not args.no_cpu_baseline:
+                gpu_factors = [G.export() for G in Gs[:40]]
         for G in Gs: G.free()
+    torch.cuda.synchronize()
     clk = clocks.stop()
     launches = P.parac_kernel_launches() - launches0
+    setup_ms, pcg_ms = ph.ms("setup"), ph.ms("pcg")
     # one system at a time (same schedule), for the batched-vs-loop ratio
     loop_ms = []
-    for _ in range(2):
+    for _ in range(3):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -481,28 +647,27 @@ def run_batch(args, world, rank, local, pg):
         for G in Gs: G.free()
     total_setup_s = allreduce_max(pg, sum(setup_ms) * 1e-3)
     value = world * nnzG * args.steps / total_setup_s / 1e6
-    loop_value = loop_nnz / (min(loop_ms) * 1e-3) / 1e6
+    loop_value = loop_nnz / (statistics.median(loop_ms) * 1e-3) / 1e6
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        nnz, tc = oracle_batch_sample(batch, seed, args.cpu_budget)
+    if gpu_factors is not None:
+        nnz, tc, same = oracle_batch_sample(batch, seed, args.cpu_budget, gpu_factors)
         cpu = {"value": sum(nnz) / tc / 1e6, "unit": "Mnnz(G)/s", "cores": 1, "kind": "oracle",
                "sample": f"the first {len(nnz)} of 200 systems in order, sequential oracle ({tc:.1f} s)",
-               "bit_identical": nnz == nnz_sys[:len(nnz)]}
+               "bit_identical": bool(same)}
     line = {
-        "metric": "setup Mnnz(G)/s (batched parac_factor_many); time-to-solution to rel-res 1e-8 in tts_ms",
-        "value": value, "unit": "Mnnz(G)/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC, "value": value, "unit": "Mnnz(G)/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup,
         "ms_per_step": allreduce_max(pg, statistics.mean([a + b for a, b in zip(setup_ms, pcg_ms)])),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC[args.workload], "systems": len(batch),
-                   "n_total": sum(A.n for A, _, _ in batch), "nnz_G": nnzG, "G_precision": args.prec,
-                   "tol": args.tol, "l2": "flushed before every step (256 MB write)",
-                   "parallelism": f"replicas x{world}", "schedule": tune_report["best"]},
-        "setup_ms": statistics.median(setup_ms), "pcg_ms": statistics.median(pcg_ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32G" if args.prec == 32 else "f64", "data": "synthetic",
+        "config": dict(batch_config(args, batch, world), schedule=tune_report["best"]),
+        "nnz_G": nnzG, "setup_ms": statistics.median(setup_ms), "pcg_ms": statistics.median(pcg_ms),
         "tts_ms": statistics.median([a + b for a, b in zip(setup_ms, pcg_ms)]),
         "pcg_iters_mean": float(np.mean(its_all)), "pcg_iters_max": int(max(its_all)),
         "true_relres_max": max(rr_all),
-        "one_at_a_time": {"value": loop_value, "unit": "Mnnz(G)/s", "setup_ms": min(loop_ms), "nnz_G": loop_nnz,
-                          "batched_over_loop": value / world / loop_value},
+        "one_at_a_time": {"value": loop_value, "unit": "Mnnz(G)/s", "setup_ms": statistics.median(loop_ms),
+                          "nnz_G": loop_nnz},
+        "batched_over_loop": value / world / loop_value,
         "autotune": tune_report, "gpu_launches": int(launches), "clocks": clk,
         "roofline": None, "cpu_baseline": cpu, "e2e": None,
     }
@@ -526,6 +691,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ordering", default="random", choices=["random", "nnz"])
     ap.add_argument("--samples", type=int, default=1, help="samples per clique-tree slot (AC(k); 1: Alg. 2)")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision pass (FP32-stored factor) run beside the FP64 one")
+    ap.add_argument("--batch", default="auto", choices=["auto", "on", "off"],
+                    help="also run the 200-system SDDM batch (parac_factor_many vs one call per system) in every "
+                         "step; auto: with the default workload only")
     ap.add_argument("--cpu-budget", type=float, default=10.0,
                     help="seconds of oracle work per step when the oracle runs on a sample of a batch")
     args = ap.parse_args()

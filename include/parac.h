@@ -59,8 +59,14 @@ enum { PARAC_KIND_AUTO = 0, PARAC_KIND_LAPLACIAN = 1, PARAC_KIND_SDDM = 2 };
 /* Triangular-solve strategies (all sync-free, rows in dependency-level
  * order): WARP gives each row a warp of 32 lanes (and a whole block to a row
  * of more than 512 entries); SUB8 / SUB4 give each row 8 / 4 lanes, so a warp
- * works on 4 / 8 short rows at once.  AUTO is WARP. */
-enum { PARAC_SPTRSV_AUTO = 0, PARAC_SPTRSV_WARP = 1, PARAC_SPTRSV_SUB8 = 2, PARAC_SPTRSV_SUB4 = 3 };
+ * works on 4 / 8 short rows at once; THREAD gives each row one lane, runs of
+ * up to 32 rows of one dependency level to a warp, and rows of more than 64
+ * entries to the whole warp (for factors without rows or columns of more than
+ * 2048 entries; others fall back to WARP).  AUTO is WARP. */
+enum { PARAC_SPTRSV_AUTO = 0, PARAC_SPTRSV_WARP = 1, PARAC_SPTRSV_SUB8 = 2, PARAC_SPTRSV_SUB4 = 3,
+       PARAC_SPTRSV_THREAD = 4 };
+/* Tri-state switches of parac_opts: 0 = the library default. */
+enum { PARAC_DEFAULT = 0, PARAC_ON = 1, PARAC_OFF = 2 };
 
 /*
  * Options.  parac_opts_default() fills the defaults; a NULL opts pointer
@@ -101,6 +107,30 @@ enum { PARAC_SPTRSV_AUTO = 0, PARAC_SPTRSV_WARP = 1, PARAC_SPTRSV_SUB8 = 2, PARA
  *                   addressing, insert from hash(col) + fill_count(col) to
  *                   the right, gathered by parallel scans).  The factor is the
  *                   same either way.
+ * Finer elimination schedule (0 = default; none changes the factor):
+ *   block_cap       entries of a CTA's shared working-set buffer, rounded up
+ *                   to a power of two in [256, 8192] (default: 2048, or less
+ *                   when it would cost resident blocks)
+ *   coop            PARAC_ON / PARAC_OFF: a working set above the warp buffer
+ *                   is eliminated by all warps of the CTA (default on) or by
+ *                   its warp alone through global scratch
+ *   sample_sort     PARAC_ON / PARAC_OFF: sample sort for working sets held
+ *                   in global scratch (default on) instead of bitonic sorts
+ *   idle_ns         sleep of a worker that found no ready vertex (default 512)
+ *   trace_path      NULL (default), or a file that receives one line per
+ *                   vertex: ready / start / end times, gathered and merged
+ *                   sizes, the pivot that made it ready and its level
+ * Solve schedule (kept in the handle; none changes the preconditioner beyond
+ * the order of the row sums):
+ *   trsv_blocks     persistent grid of the triangular solves (0: sized to
+ *                   the dependency frontier; capped at the co-resident blocks)
+ *   poll_ns         cap of the solves' polling back-off in ns (0: 64)
+ *   pcg_graph       PARAC_ON / PARAC_OFF: parac_pcg replays its iterations
+ *                   from a captured CUDA graph (default on) or launches them
+ *   pcg_many        parac_pcg_many (read from the first handle): PARAC_ON /
+ *                   default = one block-diagonal solve when the handles allow
+ *                   it; PARAC_OFF = one parac_pcg per system on worker threads
+ *   pcg_workers     worker threads of that per-system path (0: 4)
  */
 typedef struct {
     int32_t kind;
@@ -118,6 +148,16 @@ typedef struct {
     void *stream;
     int32_t samples;
     int32_t fill_store;
+    int32_t block_cap;
+    int32_t coop;
+    int32_t sample_sort;
+    int32_t idle_ns;
+    const char *trace_path;
+    int32_t trsv_blocks;
+    int32_t poll_ns;
+    int32_t pcg_graph;
+    int32_t pcg_many;
+    int32_t pcg_workers;
 } parac_opts;
 
 void parac_opts_default(parac_opts *opts);
@@ -249,9 +289,10 @@ parac_status parac_autotune(int32_t count, const parac_system *systems, uint64_t
  * system's preconditioner applies are the same arithmetic as in its own
  * parac_pcg call; its dot products are reduced over row chunks of its own, so
  * iterates agree with separate calls up to rounding (iteration counts within
- * one).  Otherwise (mixed devices or precisions, or PARAC_PCG_MANY=threads in
- * the environment) host worker threads run the systems' parac_pcg calls
- * concurrently, with results equal to separate calls.
+ * one).  Otherwise (mixed devices or precisions, or pcg_many = PARAC_OFF in
+ * the options the first handle was made with) host worker threads run the
+ * systems' parac_pcg calls concurrently, with results equal to separate
+ * calls.
  *   count     number of systems; G[count] distinct handles
  *   b[s], x[s]   right-hand side / solution of system s (n_s entries; host or
  *             device memory)

@@ -264,6 +264,8 @@ struct parac_factor_s {
     long long spin_limit = 0;
     int32_t sptrsv = 0;
     int32_t check_every = 8;
+    int32_t trsv_blocks = 0, poll_ns = 64;             // solve schedule (parac_opts)
+    int32_t pcg_graph = 0, pcg_many = 0, pcg_workers = 4;
     cudaStream_t stream = nullptr;
     DBuf perm, Fcp, Frow, Fval, D, Lp, Li, Lv;          // label space (export) and the matrix
     DBuf Lev;                                          // dependency level of each column
@@ -275,6 +277,8 @@ struct parac_factor_s {
     std::string stats;
     SolveCache cache;
     int32_t max_row = 0;                               // longest row / column of F
+    DBuf tpr_chunks;                                   // chunks of the thread-per-row solves (int2)
+    int32_t ntpr = 0;
     DBuf sgt_f, sgt_b;                                 // group tables of the one-row-per-warp solves
     int32_t sng_f = 0, sng_b = 0;
     DBuf spart_f, spart_b;                             // partial sums of their split rows
@@ -307,6 +311,10 @@ Opts read_opts(const parac_opts *in)
     if (r.o.g_precision != 32) r.o.g_precision = 64;
     if (r.o.samples <= 0) r.o.samples = 1;
     if (r.o.fill_store != 1) r.o.fill_store = 0;
+    if (r.o.idle_ns < 0) r.o.idle_ns = 0;
+    if (r.o.trsv_blocks < 0) r.o.trsv_blocks = 0;
+    r.o.poll_ns = r.o.poll_ns <= 0 ? 64 : std::max(16, std::min(100000, r.o.poll_ns));
+    r.o.pcg_workers = r.o.pcg_workers <= 0 ? 4 : std::min(64, r.o.pcg_workers);
     r.st = (cudaStream_t)r.o.stream;
     return r;
 }
@@ -457,9 +465,9 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         block_cap = 1024;
         if (block_cap < 2 * warp_cap) block_cap = 2 * warp_cap;
     }
-    if (const char *e = getenv("PARAC_BLOCK_CAP")) {
+    if (O.o.block_cap > 0) {
         int b = 256;
-        while (b < atoi(e) && b < 8192) b <<= 1;
+        while (b < O.o.block_cap && b < 8192) b <<= 1;
         block_cap = std::max(b, 2 * warp_cap);
     }
     int bps = 0;
@@ -483,8 +491,8 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
     DBuf lvl = dalloc<int32_t>(nl, st);
     DBuf tops = dalloc<unsigned long long>(3, st), status = dalloc<int32_t>(1, st), stats = dalloc<unsigned long long>(32, st);
 
-    // optional per-vertex trace, written to the file named by PARAC_TRACE
-    const char *trace_path = getenv("PARAC_TRACE");
+    // optional per-vertex trace, written to the file opts->trace_path names
+    const char *trace_path = O.o.trace_path;
     DBuf trace_buf, trace_par, trace_ph;
     if (trace_path) {
         trace_buf = dalloc<long long>((size_t)nl * 4, st);
@@ -576,7 +584,7 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         a.trace_phase = trace_ph.as<int32_t>();
         a.idle_ns = 512;
         a.coop = 1;
-        if (const char *e = getenv("PARAC_COOP")) a.coop = atoi(e) != 0;
+        if (O.o.coop == PARAC_OFF) a.coop = 0;
         a.samples = O.o.samples;
         a.hash_store = O.o.fill_store == 1 ? 1 : 0;
         a.wcol = w_col.as<int32_t>(); a.wrow = w_row.as<int32_t>(); a.ww = w_w.as<double>();
@@ -584,8 +592,8 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         out.samples = O.o.samples;
         out.fill_store = O.o.fill_store;
         a.sample_sort = 1;
-        if (const char *e = getenv("PARAC_SAMPLE_SORT")) a.sample_sort = atoi(e) != 0;
-        if (const char *e = getenv("PARAC_IDLE_NS")) a.idle_ns = std::max(32, std::min(1000000, atoi(e)));
+        if (O.o.sample_sort == PARAC_OFF) a.sample_sort = 0;
+        if (O.o.idle_ns > 0) a.idle_ns = std::max(32, std::min(1000000, O.o.idle_ns));
         if (nl > 0) CK(elim_launch(a, blocks, warps, fchunk, st));
         int32_t hst = 0;
         unsigned long long htops[3];
@@ -684,9 +692,14 @@ void finish_handle(parac_factor_s *h, int64_t n, int64_t nnzF, const Opts &O)
         CK(scan_i32_to_i64(hist.as<int32_t>(), lstart.as<int64_t>(), hmax + 1, tmp2.p, st));
         h->lstart.assign((size_t)hmax + 2, 0);
         CK(cudaMemcpyAsync(h->lstart.data(), lstart.p, 8 * ((size_t)hmax + 2), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemsetAsync(hist.p, 0, 4 * ((size_t)hmax + 1), st));
-        CK(launch_level_scatter((int32_t)n, h->Lev.as<int32_t>(), lstart.as<int64_t>(), hist.as<int32_t>(),
-                                order.as<int32_t>(), st));
+        // positions: columns sorted by level, stably (a level's columns in
+        // label order), so that the solve arrays are the same on every run
+        DBuf keys = dalloc<int32_t>(n1, st), rtmp(radix_tmp_bytes(n), st);
+        CK(cudaMemcpyAsync(keys.p, h->Lev.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        CK(launch_iota_i32(order.as<int32_t>(), n, 0, st));
+        int bits = 0;
+        while (bits < 31 && (hmax >> bits) != 0) ++bits;
+        CK(stable_sort_pairs((int32_t)n, keys.as<int32_t>(), order.as<int32_t>(), bits, rtmp.p, st));
     }
     DBuf posof = dalloc<int32_t>(n1, st), len = dalloc<int32_t>(n1, st);
     CK(launch_inverse_perm((int32_t)n, order.as<int32_t>(), posof.as<int32_t>(), st));
@@ -718,6 +731,7 @@ void finish_handle(parac_factor_s *h, int64_t n, int64_t nnzF, const Opts &O)
     CK(launch_transpose_scatter((int32_t)n, h->Scp.as<int64_t>(), h->Srow.as<int32_t>(), h->Sval.as<double>(),
                                 h->Srp.as<int64_t>(), cnt.as<int32_t>(), h->Scol.as<int32_t>(), h->Svalr.as<double>(), st));
     CK(launch_sort_rows((int32_t)n, h->Srp.as<int64_t>(), h->Scol.as<int32_t>(), h->Svalr.as<double>(), st));
+    CK(launch_sort_long_rows((int32_t)n, h->Srp.as<int64_t>(), h->Scol.as<int32_t>(), h->Svalr.as<double>(), st));
     // pivots and original indices by position
     DBuf Dpos = dalloc<double>(n1, st);
     CK(launch_gather_f64((int32_t)n, order.as<int32_t>(), h->D.as<double>(), Dpos.as<double>(), st));
@@ -738,6 +752,27 @@ void finish_handle(parac_factor_s *h, int64_t n, int64_t nnzF, const Opts &O)
     // building the table (a host pass over the rows) at setup.
     CK(cudaStreamSynchronize(st));
     h->max_row = maxlen;
+    if (maxlen <= TPR_MAX_ROW && n > 0) {
+        // table of the hybrid solves, in level order: a level with more rows
+        // than the solve grid has warps is cut into runs of at most 32 rows
+        // (a lane per row), a narrower one lists its rows (a warp per row);
+        // O(depth + n / 32 + rows of narrow levels) host work on the level starts
+        const int64_t wide = (int64_t)num_sms() * std::max(1, tpr_blocks_per_sm(h->prec)) * (TPR_THREADS / 32);
+        std::vector<int2> ch;
+        ch.reserve((size_t)(n / 32 + h->depth + 1));
+        for (int32_t l = 0; l < h->depth; ++l) {
+            const int64_t q0 = h->lstart[(size_t)l], q1 = h->lstart[(size_t)l + 1];
+            if (q1 - q0 > wide) {
+                for (int64_t q = q0; q < q1; q += 32) ch.push_back(make_int2((int)q, (int)std::min<int64_t>(32, q1 - q)));
+            } else {
+                for (int64_t q = q0; q < q1; ++q) ch.push_back(make_int2((int)q, 0));
+            }
+        }
+        h->ntpr = (int32_t)ch.size();
+        h->tpr_chunks = DBuf(sizeof(int2) * ch.size(), st);
+        CK(cudaMemcpyAsync(h->tpr_chunks.p, ch.data(), sizeof(int2) * ch.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
     if (maxlen > 4 * LONG_ROW_SINGLE) {
         std::vector<int64_t> rp((size_t)n + 1), cp((size_t)n + 1);
         CK(cudaMemcpyAsync(rp.data(), h->Srp.p, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
@@ -867,6 +902,8 @@ parac_status parac_factor(int64_t n, const int64_t *colptr, const int32_t *rowin
         cudaGetDevice(&h->device);
         h->n = n; h->prec = O.o.g_precision; h->spin_limit = O.o.spin_limit; h->sptrsv = O.o.sptrsv;
         h->check_every = O.o.check_every; h->stream = st;
+        h->trsv_blocks = O.o.trsv_blocks; h->poll_ns = O.o.poll_ns; h->pcg_graph = O.o.pcg_graph;
+        h->pcg_many = O.o.pcg_many; h->pcg_workers = O.o.pcg_workers;
         DView<int64_t> cp; cp.set(colptr, (size_t)n + 1, st);
         int64_t nnz = 0;
         if (n > 0) {
@@ -985,6 +1022,8 @@ parac_status parac_factor_many(int32_t count, const parac_system *systems, uint6
             cudaGetDevice(&h->device);
             h->n = n; h->prec = O.o.g_precision; h->spin_limit = O.o.spin_limit; h->sptrsv = O.o.sptrsv;
             h->check_every = O.o.check_every; h->stream = st;
+            h->trsv_blocks = O.o.trsv_blocks; h->poll_ns = O.o.poll_ns; h->pcg_graph = O.o.pcg_graph;
+            h->pcg_many = O.o.pcg_many; h->pcg_workers = O.o.pcg_workers;
             const int64_t f0 = fcp_h[ob], f1 = fcp_h[ob + n];
             h->nnzF = f1 - f0;
             h->Fcp = dalloc<int64_t>(n + 1, st);
@@ -1069,14 +1108,9 @@ thread_local cudaStream_t t_stream_override = nullptr;
 thread_local int t_grid_share = 0;
 thread_local bool t_no_graph = false;     // one-shot solves: capturing would cost more than it saves
 
-// Cap of the solves' polling back-off: 64 ns measured best on the 128^3 grid
-// (266 ms PCG vs 271 at 256 ns and 319 at 1024); the SDDM batch is indifferent.
-unsigned poll_ns_default()
-{
-    unsigned ns = 64;
-    if (const char *e = getenv("PARAC_POLL_NS")) ns = (unsigned)std::max(16, std::min(100000, atoi(e)));
-    return ns;
-}
+// Cap of the solves' polling back-off (parac_opts.poll_ns): 64 ns measured
+// best on the 128^3 grid with a warp per row (266 ms PCG vs 271 at 256 ns and
+// 319 at 1024); the SDDM batch is indifferent.
 
 SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, const double *Lv, int64_t nnzL)
 {
@@ -1094,12 +1128,6 @@ SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, co
     // one row per warp unless the handle asks for sub-warp rows
     A.lanes_trsv = G->sptrsv == PARAC_SPTRSV_SUB8 ? 8 : G->sptrsv == PARAC_SPTRSV_SUB4 ? 4 : 32;
     A.trsv_warps = SOLVE_WARPS;
-    if (const char *e = getenv("PARAC_TRSV_LANES")) {
-        const int l = atoi(e);
-        if (l == 4 || l == 8 || l == 16 || l == 32) A.lanes_trsv = l;
-    }
-    // at most 8 warps: a 256-thread block of the solves fits the register file twice
-    if (const char *e = getenv("PARAC_TRSV_WARPS")) A.trsv_warps = std::max(1, std::min(SOLVE_WARPS, atoi(e)));
     int bps = 0;
     trsv_configure(A.lanes_trsv, A.trsv_warps, &bps, A.prec);
     if (bps < 1) bps = 1;
@@ -1114,11 +1142,24 @@ SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, co
         A.trsv_blocks = (int)std::max<int64_t>(std::min<int64_t>(num_sms(), max_blocks),
                                                std::min<int64_t>(max_blocks, want));
     }
-    if (const char *e = getenv("PARAC_TRSV_BLOCKS")) A.trsv_blocks = std::max(1, std::min(max_blocks, atoi(e)));
-    set_poll_backoff(poll_ns_default());
+    if (G->trsv_blocks > 0) A.trsv_blocks = std::max(1, std::min(max_blocks, G->trsv_blocks));
+    set_poll_backoff((unsigned)G->poll_ns);
     const int64_t rows_per_group = (int64_t)A.trsv_warps * (32 / A.lanes_trsv);
     const int64_t groups = (G->n + rows_per_group - 1) / rows_per_group;
     if (groups < A.trsv_blocks) A.trsv_blocks = (int)std::max<int64_t>(groups, 1);
+    // one lane per row (THREAD) when no row or column is long
+    const bool tpr = G->ntpr > 0 && G->sng_f == 0 && G->sptrsv == PARAC_SPTRSV_THREAD;
+    if (tpr) {
+        const int tb = std::max(1, tpr_blocks_per_sm(A.prec));
+        const int64_t tmax = std::max<int64_t>(1, (int64_t)num_sms() * tb / std::max(1, t_grid_share));  // all co-resident
+        const int64_t wpb = TPR_THREADS / 32;
+        int64_t want = tmax;                         // every resident warp: narrow rows get a warp each
+        if (G->trsv_blocks > 0) want = G->trsv_blocks;
+        want = std::min<int64_t>(want, ((int64_t)G->ntpr + wpb - 1) / wpb);
+        A.tpr_blocks = (int32_t)std::max<int64_t>(1, std::min<int64_t>(tmax, want));
+        A.tpr_chunks = (const int2 *)G->tpr_chunks.p;
+        A.ntpr = G->ntpr;
+    }
     A.spin_limit = G->spin_limit;
     A.status = G->status.as<int32_t>();
     if (G->sng_f > 0 && A.lanes_trsv == 32 && A.trsv_warps == SOLVE_WARPS) {
@@ -1245,11 +1286,9 @@ void leave_solve_stream(parac_factor_s *G, cudaStream_t st)
     CK(cudaStreamWaitEvent(st, ss.out, 0));
 }
 
-bool graphs_enabled()
+bool graphs_enabled(const parac_factor_s *G)
 {
-    if (t_no_graph) return false;
-    const char *e = getenv("PARAC_GRAPH");
-    return !(e && e[0] == '0');
+    return !t_no_graph && G->pcg_graph != PARAC_OFF;
 }
 
 // Run `iters` iterations given by `launch(stream)`: replay the cached graph
@@ -1259,7 +1298,7 @@ template <class Launch>
 cudaError_t run_iterations(parac_factor_s *G, const uint64_t (&key)[GraphCache::KEY], Launch &&launch,
                            cudaStream_t ps)
 {
-    if (!graphs_enabled()) return launch(ps);
+    if (!graphs_enabled(G)) return launch(ps);
     GraphCache &gc = G->graph;
     if (!gc.exec || memcmp(gc.key, key, sizeof key) != 0) {
         gc.reset();
@@ -1503,7 +1542,7 @@ struct BatchRun {
 bool batchable(int32_t count, const parac_factor_t *G)
 {
     if (count < 2) return false;
-    if (const char *e = getenv("PARAC_PCG_MANY")) if (!strcmp(e, "threads")) return false;
+    if (G[0] && G[0]->pcg_many == PARAC_OFF) return false;
     int64_t n = 0;
     for (int32_t i = 0; i < count; ++i) {
         if (!G[i] || G[i]->device != G[0]->device || G[i]->prec != G[0]->prec) return false;
@@ -1655,10 +1694,10 @@ parac_status pcg_batch(int32_t count, const parac_factor_t *G, const double *con
     const int64_t max_blocks = (int64_t)num_sms() * std::max(bps, 1);   // all co-resident
     const int64_t want = (2 * n / std::max(depth, 1) + rows_per_group - 1) / rows_per_group;
     int64_t tb = std::max<int64_t>(std::min<int64_t>(num_sms(), max_blocks), std::min<int64_t>(max_blocks, want));
-    if (const char *e = getenv("PARAC_TRSV_BLOCKS")) tb = std::max<int64_t>(1, std::min<int64_t>(max_blocks, atoll(e)));
+    if (G[0]->trsv_blocks > 0) tb = std::max<int64_t>(1, std::min<int64_t>(max_blocks, G[0]->trsv_blocks));
     tb = std::min<int64_t>(tb, std::max<int64_t>(std::max(gf.ngroups, gb.ngroups), 1));
     A.trsv_blocks = (int32_t)tb;
-    CK(set_poll_backoff(poll_ns_default()));
+    CK(set_poll_backoff((unsigned)G[0]->poll_ns));
     A.spin_limit = spin;
     A.status = R.status.as<int32_t>();
     A.gt_f = (const int4 *)R.gt_f.p; A.ng_f = gf.ngroups; A.part_f = R.part_f.p; A.nslot_f = gf.nslots;
@@ -1728,10 +1767,6 @@ extern "C" parac_status parac_pcg_many(int32_t count, const parac_factor_t *G, c
                                        double *true_relres)
 {
     return guarded([&]() -> parac_status {
-        // both paths switch to the handles' device (the batch on this thread,
-        // the last worker on this thread too); the caller's device comes back
-        struct Restore { int dev = -1; ~Restore() { if (dev >= 0) cudaSetDevice(dev); } } restore;
-        CK(cudaGetDevice(&restore.dev));
         if (count < 0 || (count > 0 && (!G || !b || !x))) { set_err("bad arguments to parac_pcg_many"); return PARAC_EINVAL; }
         for (int32_t i = 0; i < count; ++i) {
             if (G[i] && G[i]->n > 0 && (!b[i] || !x[i])) {
@@ -1741,6 +1776,12 @@ extern "C" parac_status parac_pcg_many(int32_t count, const parac_factor_t *G, c
             for (int32_t j = 0; j < i && j < 64; ++j)
                 if (G[i] == G[j]) { set_err("parac_pcg_many: handle %d repeats handle %d", i, j); return PARAC_EINVAL; }
         }
+        // both paths switch to the handles' device (the batch on this thread,
+        // one of the workers on this thread too); the caller's device comes back
+        struct Restore { int dev = -1; ~Restore() { if (dev >= 0) cudaSetDevice(dev); } } restore;
+        bool any = false;
+        for (int32_t i = 0; i < count; ++i) any = any || G[i];
+        if (any) CK(cudaGetDevice(&restore.dev));
         if (batchable(count, G)) {
             try {
                 return pcg_batch(count, G, b, x, tol, maxit, iters, true_relres);
@@ -1756,8 +1797,8 @@ extern "C" parac_status parac_pcg_many(int32_t count, const parac_factor_t *G, c
         std::vector<int32_t> it((size_t)count, 0);
         std::vector<double> rr((size_t)count, 0.0);
         std::atomic<int32_t> next{0};
-        int workers = 4;           // measured best on 200 SDDM systems (1: 1.65 s, 4: 0.89 s, 16: 1.72 s)
-        if (const char *e = getenv("PARAC_PCG_WORKERS")) workers = std::max(1, std::min(64, atoi(e)));
+        // 4 by default: measured best on 200 SDDM systems (1: 1.65 s, 4: 0.89 s, 16: 1.72 s)
+        const int workers = count > 0 && G[0] ? G[0]->pcg_workers : 4;
         const int nth = (int)std::min<int32_t>(count, workers);
         auto worker = [&]() {
             // each worker orders its systems on its own stream and gets 1/nth

@@ -4,6 +4,8 @@
 // with F(u,k) = -w_u / D_k (Sec. IV scaled form), ground rows/columns
 // removed (Sec. V SDDM handling), plus CSR(F) by transposition for the
 // forward triangular solve and optional FP32 copies.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -151,11 +153,93 @@ __global__ void k_max_i32(const int32_t *a, int64_t n, int32_t *mx)
     if ((threadIdx.x & 31) == 0) atomicMax(mx, m);
 }
 
-__global__ void k_level_scatter(int32_t n, const int32_t *lev, const int64_t *lstart, int32_t *cursor, int32_t *order)
+// ---------------------------------------------------------------- stable radix sort (key, value) pairs
+// One 8-bit digit per pass, least significant first; every pass is stable, so
+// after the passes the pairs are ordered by key and, within a key, keep their
+// input order.  A tile of RADIX_TILE pairs per block: the per-tile digit
+// histograms (digit-major) are scanned into each (digit, tile)'s output
+// offset, and each tile scatters its pairs in input order: RADIX_TILE / 256
+// rounds of 256 pairs, a pair's rank among its round's equal digits found from
+// its warp's match mask plus the counts of the warps before it.
+constexpr int RADIX_THREADS = 256, RADIX_ROUNDS = 8, RADIX_TILE = RADIX_THREADS * RADIX_ROUNDS;
+
+__global__ void __launch_bounds__(RADIX_THREADS) k_radix_hist(int32_t n, const int32_t *keys, int shift, int32_t ntiles,
+                                                              int32_t *hist)
 {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t L = lev[t];
-        order[lstart[L] + atomicAdd(cursor + L, 1)] = (int32_t)t;
+    __shared__ int32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RADIX_TILE;
+    for (int r = 0; r < RADIX_ROUNDS; ++r) {
+        const int64_t i = base + r * RADIX_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RADIX_THREADS) k_radix_scatter(int32_t n, const int32_t *keys, const int32_t *vals,
+                                                                 int shift, int32_t ntiles, const int64_t *offs,
+                                                                 int32_t *keys_out, int32_t *vals_out)
+{
+    __shared__ int32_t run[256];                  // pairs of each digit placed by earlier rounds
+    __shared__ int32_t wcnt[RADIX_THREADS / 32][256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    run[threadIdx.x] = 0;
+    const int64_t base = (int64_t)blockIdx.x * RADIX_TILE;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < RADIX_ROUNDS; ++r) {
+        for (int w = 0; w < RADIX_THREADS / 32; ++w) wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t i = base + r * RADIX_THREADS + threadIdx.x;
+        const bool in = i < n;
+        const int32_t k = in ? keys[i] : 0;
+        const int d = in ? (k >> shift) & 255 : 256;           // 256: no pair
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (in && (peers & lt) == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (in) {
+            int32_t rank = run[d] + __popc(peers & lt);
+            for (int w = 0; w < warp; ++w) rank += wcnt[w][d];
+            const int64_t at = offs[(int64_t)d * ntiles + blockIdx.x] + rank;
+            keys_out[at] = k;
+            vals_out[at] = vals[i];
+        }
+        __syncthreads();
+        int32_t add = 0;
+        for (int w = 0; w < RADIX_THREADS / 32; ++w) add += wcnt[w][threadIdx.x];
+        run[threadIdx.x] += add;
+    }
+}
+
+__global__ void k_copy_i32(int64_t n, const int32_t *a, int32_t *b)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        b[t] = a[t];
+}
+
+// Sort rows of more than SORT_STAGE and at most SORT_LONG entries by column,
+// one block per row staged in shared memory (rank = entries with a smaller
+// column; the columns of a row are distinct).
+constexpr int SORT_LONG = 2048;
+
+__global__ void __launch_bounds__(256) k_sort_long_rows(int32_t n, const int64_t *rp, int32_t *cols, double *vals)
+{
+    __shared__ int32_t sc[SORT_LONG];
+    __shared__ double sv[SORT_LONG];
+    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+        const int64_t b = rp[r], len = rp[r + 1] - b;
+        if (len <= SORT_STAGE || len > SORT_LONG) continue;
+        for (int64_t i = threadIdx.x; i < len; i += blockDim.x) { sc[i] = cols[b + i]; sv[i] = vals[b + i]; }
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+            const int32_t c = sc[i];
+            int64_t rank = 0;
+            for (int64_t q = 0; q < len; ++q) rank += sc[q] < c;
+            cols[b + rank] = c;
+            vals[b + rank] = sv[i];
+        }
+        __syncthreads();
     }
 }
 
@@ -281,6 +365,48 @@ cudaError_t launch_sort_rows(int32_t n, const int64_t *rp, int32_t *cols, double
     return cudaGetLastError();
 }
 
+size_t radix_tmp_bytes(int64_t n)
+{
+    const int64_t ntiles = (n + RADIX_TILE - 1) / RADIX_TILE;
+    const int64_t nh = 256 * std::max<int64_t>(ntiles, 1);
+    return 8 * (size_t)n + 4 * (size_t)nh + 8 * (size_t)(nh + 1) + scan_tmp_bytes(nh + 1) + 512;
+}
+
+cudaError_t stable_sort_pairs(int32_t n, int32_t *keys, int32_t *vals, int key_bits, void *tmp, cudaStream_t st)
+{
+    if (n <= 1) return cudaSuccess;
+    const int32_t ntiles = (int32_t)((n + RADIX_TILE - 1) / RADIX_TILE);
+    const int64_t nh = 256 * (int64_t)ntiles;
+    char *p = (char *)tmp;
+    int32_t *k2 = (int32_t *)p; p += 4 * (size_t)n;
+    int32_t *v2 = (int32_t *)p; p += 4 * (size_t)n;
+    int32_t *hist = (int32_t *)p; p += 4 * (size_t)nh;
+    p = (char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    int64_t *offs = (int64_t *)p; p += 8 * (size_t)(nh + 1);
+    void *stmp = (void *)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+    int32_t *ki = keys, *vi = vals, *ko = k2, *vo = v2;
+    int passes = 0;
+    for (int shift = 0; shift < std::max(key_bits, 1); shift += 8, ++passes) {
+        k_radix_hist<<<ntiles, RADIX_THREADS, 0, st>>>(n, ki, shift, ntiles, hist); count_launches(1);
+        cudaError_t e = scan_i32_to_i64(hist, offs, nh, stmp, st);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<ntiles, RADIX_THREADS, 0, st>>>(n, ki, vi, shift, ntiles, offs, ko, vo); count_launches(1);
+        std::swap(ki, ko); std::swap(vi, vo);
+    }
+    if (passes & 1) {            // the sorted pairs are in the scratch arrays
+        k_copy_i32<<<grid_for(n, 256), 256, 0, st>>>(n, ki, keys); count_launches(1);
+        k_copy_i32<<<grid_for(n, 256), 256, 0, st>>>(n, vi, vals); count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_long_rows(int32_t n, const int64_t *rp, int32_t *cols, double *vals, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_sort_long_rows<<<std::min(n, 1024), 256, 0, st>>>(n, rp, cols, vals); count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scatter_levels(int32_t nl, const int32_t *out_of_label, const int32_t *lvl, int32_t *lev_out,
                                   cudaStream_t st)
 {
@@ -293,14 +419,6 @@ cudaError_t launch_max_i32(const int32_t *a, int64_t n, int32_t *mx, cudaStream_
 {
     if (n == 0) return cudaSuccess;
     k_max_i32<<<grid_for(n, 256) < 1024 ? grid_for(n, 256) : 1024, 256, 0, st>>>(a, n, mx); count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_level_scatter(int32_t n, const int32_t *lev, const int64_t *lstart, int32_t *cursor,
-                                 int32_t *order, cudaStream_t st)
-{
-    if (n == 0) return cudaSuccess;
-    k_level_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, lev, lstart, cursor, order); count_launches(1);
     return cudaGetLastError();
 }
 

@@ -83,11 +83,16 @@ cudaError_t launch_transpose_scatter(int32_t n, const int64_t *cp, const int32_t
                                      const int64_t *rp, int32_t *cursor, int32_t *cols_out, double *vals_out,
                                      cudaStream_t st);
 cudaError_t launch_sort_rows(int32_t n, const int64_t *rp, int32_t *cols, double *vals, cudaStream_t st);
+// rows of 257..2048 entries (launch_sort_rows sorts those up to 256)
+cudaError_t launch_sort_long_rows(int32_t n, const int64_t *rp, int32_t *cols, double *vals, cudaStream_t st);
+// Stable sort of n (key, value) pairs by the low key_bits bits of the
+// non-negative keys (LSD radix, 8 bits per pass), in place; tmp holds
+// radix_tmp_bytes(n) bytes.
+size_t radix_tmp_bytes(int64_t n);
+cudaError_t stable_sort_pairs(int32_t n, int32_t *keys, int32_t *vals, int key_bits, void *tmp, cudaStream_t st);
 cudaError_t launch_scatter_levels(int32_t nl, const int32_t *out_of_label, const int32_t *lvl, int32_t *lev_out,
                                   cudaStream_t st);
 cudaError_t launch_max_i32(const int32_t *a, int64_t n, int32_t *mx, cudaStream_t st);
-cudaError_t launch_level_scatter(int32_t n, const int32_t *lev, const int64_t *lstart, int32_t *cursor,
-                                 int32_t *order, cudaStream_t st);
 cudaError_t launch_inverse_perm(int32_t n, const int32_t *order, int32_t *posof, cudaStream_t st);
 cudaError_t launch_relabel_lengths(int32_t n, const int32_t *order, const int64_t *cp, int32_t *len, cudaStream_t st);
 cudaError_t launch_relabel_gather(int32_t n, const int32_t *order, const int32_t *posof, const int64_t *cp,
@@ -121,6 +126,9 @@ struct SolveArgs {
     int32_t lanes_trsv;           // lanes per row for the triangular solves
     int32_t trsv_blocks;          // persistent grid of the triangular solves
     int32_t trsv_warps;           // warps per block of the triangular solves
+    int32_t tpr_blocks;           // > 0: one lane per row (thread-per-row solves) on this many blocks of 256
+    const int2 *tpr_chunks;       // their chunks: (first position, rows <= 32), never across a level
+    int32_t ntpr;
     long long spin_limit;
     int32_t *status;
     // optional group tables of the one-row-per-warp solves (row_groups with the
@@ -141,6 +149,10 @@ struct SolveArgs {
 constexpr int LONG_ROW_SINGLE = 512, SPLIT_ROW_SINGLE = 32768, CHUNK_SINGLE = 8192;
 constexpr int LONG_ROW_BLOCK = 64, SPLIT_ROW_BLOCK = 1024, CHUNK_BLOCK = 512;
 constexpr int SOLVE_WARPS = 8;        // warps per block of the solves (default)
+// thread-per-row solves: used for factors whose rows and columns all have at
+// most TPR_MAX_ROW entries; blocks of 256 threads
+constexpr int TPR_MAX_ROW = 2048, TPR_THREADS = 256;
+int tpr_blocks_per_sm(int prec);
 
 struct PcgBuffers {
     double *x, *r, *z, *p, *q, *b;  // [n]

@@ -432,6 +432,46 @@ __device__ __forceinline__ bool finish_chunk(const XT *x, const int32_t (&cc)[RP
     return true;
 }
 
+// A row's last TAIL entries in walk order (forward: the highest positions;
+// backward, walked from its last entry: the lowest) hold its dependencies
+// published last.  The lanes sum the other entries (their dependencies are
+// usually published long before) and reduce them while the row still waits;
+// lane 0 then adds the tail entries one by one in walk order, each as soon as
+// its unknown is published.  So after the last dependency arrives only an FMA
+// and the publication remain, not a batch of FMAs and the shuffle tree (an
+// FP64 add costs ~100 cycles on this chip).  The order of the sum is fixed:
+// the tree over the head, then the tail in order.
+constexpr int TAIL = 4;
+
+__device__ __forceinline__ int64_t head_len(int64_t len) { return len > TAIL ? len - TAIL : 0; }
+
+template <bool REV, typename VT, typename XT>
+__device__ __forceinline__ bool tail_sum(int64_t b, int64_t e, const int32_t *idx, const VT *v, const XT *x, XT &acc,
+                                         long long spin_limit, int32_t *status)
+{
+    const int64_t len = e - b, h = head_len(len);
+    int32_t c[TAIL];
+    VT w[TAIL];
+    XT xv[TAIL];
+#pragma unroll
+    for (int k = 0; k < TAIL; ++k) {
+        const int64_t u = h + k;
+        const int64_t t = REV ? e - 1 - u : b + u;
+        c[k] = u < len ? idx[t] : -1;
+        w[k] = u < len ? v[t] : (VT)0;
+    }
+#pragma unroll
+    for (int k = 0; k < TAIL; ++k) xv[k] = c[k] >= 0 ? ld_poll(x + c[k]) : (XT)0;
+#pragma unroll
+    for (int k = 0; k < TAIL; ++k) {
+        if (c[k] >= 0) {
+            if (is_sentinel(xv[k]) && !poll_ready(x + c[k], xv[k], spin_limit, status)) return false;
+            acc += (XT)w[k] * xv[k];
+        }
+    }
+    return true;
+}
+
 // Group g of the schedule as seen by one lane group: its row (position) for
 // GK_ROWS (-1: none), the group's row for the block-wide kinds.
 struct Grp {
@@ -531,7 +571,7 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
             if (r.aux) { r.kind = GK_ROWS; r.j = -1; }      // a stopped system's group: nothing to do
         if (r.kind == GK_ROWS && r.j >= 0) {
             if (sl == 0) rr = rhs[o];
-            fetch_chunk<S, false, VT>(bb, ee, sl, ci, v, c, w);
+            fetch_chunk<S, false, VT>(bb, bb + head_len(ee - bb), sl, ci, v, c, w);
         }
     };
     int64_t g = blockIdx.x;
@@ -582,16 +622,20 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
             __syncthreads();
         } else if (j >= 0) {
             XT acc = 0;
+            const int64_t h = head_len(e - b);
             bool ok = finish_chunk<VT, XT>(y, cc, vv, xx, acc, spin_limit, status);
-            if (ok && e - b > (int64_t)RPF * S)
-                ok = dot_ready<false, VT, XT>(b, e, sl + RPF * S, S, ci, v, y, acc, spin_limit, status);
-            if (!ok) set_status(status, ST_TIMEOUT);
+            if (ok && h > (int64_t)RPF * S)
+                ok = dot_ready<false, VT, XT>(b, b + h, sl + RPF * S, S, ci, v, y, acc, spin_limit, status);
+            if (h > 0) {
 #pragma unroll
-            for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
+                for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
+            }
             if (sl == 0) {
+                if (ok) ok = tail_sum<false, VT, XT>(b, e, ci, v, y, acc, spin_limit, status);
                 zreset[j] = sentinel<XT>();
                 st_pub(y + j, to_x<XT>(rj) - acc);
             }
+            if (!ok) set_status(status, ST_TIMEOUT);
         }
         g += G;
         q = q1; b = b1; e = e1; rj = rjn;
@@ -639,7 +683,7 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
                 yv = y[r.j]; dv = Dinv[r.j];
                 rv = r_orig ? r_orig[o] : 0.0;
             }
-            fetch_chunk<S, true, VT>(bb, ee, sl, ri, v, c, w);
+            fetch_chunk<S, true, VT>(ee - head_len(ee - bb), ee, sl, ri, v, c, w);
         }
     };
     // finish column j with the sum of its terms (thread / lane that owns it)
@@ -696,13 +740,19 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
             __syncthreads();
         } else if (j >= 0) {
             XT acc = 0;
+            const int64_t h = head_len(e - b);
             bool ok = finish_chunk<VT, XT>(z, cc, vv, xx, acc, spin_limit, status);
-            if (ok && e - b > (int64_t)RPF * S)
-                ok = dot_ready<true, VT, XT>(b, e, sl + RPF * S, S, ri, v, z, acc, spin_limit, status);
-            if (!ok) set_status(status, ST_TIMEOUT);
+            if (ok && h > (int64_t)RPF * S)
+                ok = dot_ready<true, VT, XT>(e - h, e, sl + RPF * S, S, ri, v, z, acc, spin_limit, status);
+            if (h > 0) {
 #pragma unroll
-            for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
-            if (sl == 0) publish(j, yj, dj, o, rj, acc);
+                for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
+            }
+            if (sl == 0) {
+                if (ok) ok = tail_sum<true, VT, XT>(b, e, ri, v, z, acc, spin_limit, status);
+                publish(j, yj, dj, o, rj, acc);
+            }
+            if (!ok) set_status(status, ST_TIMEOUT);
         }
         g += G;
         q = q1; b = b1; e = e1; o = o1; yj = yjn; dj = djn; rj = rjn;
@@ -714,6 +764,180 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
     if (partial) {
         const double s = block_sum(dotacc);
         if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------- hybrid solves
+// Measured on a 128^3 grid (per-row publication times): two thirds of a
+// warp-per-row solve went to the wide dependency levels (thousands of rows,
+// most of them short), where one row per warp makes the warps' row
+// throughput the limit -- a warp spends ~460 instructions on a row -- and one
+// third to hundreds of narrow levels of a few long rows each, where the
+// latency from a row's last dependency to its publication is the limit.  So
+// each level is handled by the form that suits it: a table lists, in level
+// order, runs of up to 32 rows of a wide level (one lane per row: lane l of
+// the warp takes the run's l-th row, fetches its entries PF at a time, waits
+// for their unknowns and adds the products in entry order) and the single
+// rows of the narrow levels (one warp per row: lanes sum the head entries in
+// lane-strided order and reduce them, lane 0 adds the tail, see tail_sum).
+// Rows of more than TPR_LONG entries inside a run are taken by the whole warp
+// the same way, one after another.  Entry c goes to warp c mod W; a run never
+// crosses a level, so no row waits on a row of its own entry, and every
+// dependency sits in an earlier entry: with the grid fully co-resident the
+// smallest unfinished entry never waits on an unfinished entry.  The bounds
+// and right-hand side of the warp's next entry are loaded before the waits,
+// its first indices and values prefetched to L2.
+constexpr int TPR_LONG = 64;
+
+// Bring a row's first indices and values towards L2 ahead of use.
+template <typename VT>
+__device__ __forceinline__ void prefetch_l2(const int32_t *idx, const VT *val)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(idx));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(val));
+}
+
+// One row [b, e) of the solve done by the whole warp; the sum is valid in lane 0.
+template <bool REV, typename VT, typename XT>
+__device__ __forceinline__ XT warp_row(int64_t b, int64_t e, int lane, const int32_t *idx, const VT *v, const XT *x,
+                                       long long spin_limit, int32_t *status)
+{
+    const int64_t h = head_len(e - b);
+    XT acc = 0;
+    bool ok = true;
+    if (h > 0) {
+        ok = REV ? dot_ready<true, VT, XT>(e - h, e, lane, 32, idx, v, x, acc, spin_limit, status)
+                 : dot_ready<false, VT, XT>(b, b + h, lane, 32, idx, v, x, acc, spin_limit, status);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+    }
+    if (lane == 0 && ok) ok = tail_sum<REV, VT, XT>(b, e, idx, v, x, acc, spin_limit, status);
+    if (!ok) set_status(status, ST_TIMEOUT);
+    return acc;
+}
+
+// Table entry: (first position, rows) for a run of one wide level, or
+// (position, 0) for a row of a narrow level.
+template <typename VT, typename XT>
+__global__ void __launch_bounds__(256) k_trsv_fwd_h(const int2 *tab, int32_t nt, const int64_t *rp,
+                                                    const int32_t *ci, const VT *v, const int32_t *operm,
+                                                    const double *rhs, XT *y, XT *zreset, const PcgState *st,
+                                                    long long spin_limit, int32_t *status)
+{
+    if (st && st->done) return;
+    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int lane = threadIdx.x & 31;
+    int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int2 t = c < nt ? tab[c] : make_int2(0, 0);
+    bool has = c < nt && (t.y == 0 || lane < t.y);
+    int64_t j = (int64_t)t.x + (t.y > 0 ? lane : 0), b = 0, e = 0;
+    double rj = 0.0;
+    if (has) { b = rp[j]; e = rp[j + 1]; rj = rhs[operm[j]]; }
+    for (; c < nt; c += W) {
+        const int2 tn = c + W < nt ? tab[c + W] : make_int2(0, 0);
+        const bool hasn = c + W < nt && (tn.y == 0 || lane < tn.y);
+        const int64_t jn = (int64_t)tn.x + (tn.y > 0 ? lane : 0);
+        int64_t bn = 0, en = 0;
+        double rn = 0.0;
+        if (hasn) {
+            bn = rp[jn]; en = rp[jn + 1]; rn = rhs[operm[jn]];
+            if (tn.y > 0 || lane == 0) prefetch_l2(ci + bn, v + bn);
+        }
+        if (t.y == 0) {                                   // a narrow level's row: the whole warp
+            const XT acc = warp_row<false, VT, XT>(b, e, lane, ci, v, y, spin_limit, status);
+            if (lane == 0) {
+                zreset[j] = sentinel<XT>();
+                st_pub(y + j, to_x<XT>(rj) - acc);
+            }
+        } else {                                          // a run of a wide level: a lane per row
+            const bool lng = has && e - b > TPR_LONG;
+            if (has && !lng) {
+                XT acc = 0;
+                if (!dot_ready<false, VT, XT>(b, e, 0, 1, ci, v, y, acc, spin_limit, status))
+                    set_status(status, ST_TIMEOUT);
+                zreset[j] = sentinel<XT>();
+                st_pub(y + j, to_x<XT>(rj) - acc);
+            }
+            for (unsigned lm = __ballot_sync(FULL, lng); lm; lm &= lm - 1) {
+                const int src = __ffs(lm) - 1;
+                const int64_t bb = __shfl_sync(FULL, b, src), ee = __shfl_sync(FULL, e, src);
+                XT acc = warp_row<false, VT, XT>(bb, ee, lane, ci, v, y, spin_limit, status);
+                acc = __shfl_sync(FULL, acc, 0);
+                if (lane == src) {
+                    zreset[j] = sentinel<XT>();
+                    st_pub(y + j, to_x<XT>(rj) - acc);
+                }
+            }
+        }
+        t = tn; has = hasn; j = jn; b = bn; e = en; rj = rn;
+    }
+}
+
+// Backward solve over the same table from its end: z[j] = RN(y[j] Dinv[j]) -
+// sum_{i>j} F(i,j) z[i], each column walked from its last entry (whose unknown
+// was published first); writes zout[operm[j]] and resets y[j] to the sentinel.
+template <typename VT, typename XT>
+__global__ void __launch_bounds__(256) k_trsv_bwd_h(const int2 *tab, int32_t nt, const int64_t *cp,
+                                                    const int32_t *ri, const VT *v, const double *Dinv,
+                                                    const int32_t *operm, XT *y, XT *z, double *zout,
+                                                    const PcgState *st, long long spin_limit, int32_t *status)
+{
+    if (st && st->done) return;
+    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int lane = threadIdx.x & 31;
+    int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int2 t = c < nt ? tab[nt - 1 - c] : make_int2(0, 0);
+    bool has = c < nt && (t.y == 0 || lane < t.y);
+    int64_t j = (int64_t)t.x + (t.y > 0 ? lane : 0), b = 0, e = 0;
+    int32_t o = 0;
+    XT yj = 0;
+    double dj = 0.0;
+    if (has) { b = cp[j]; e = cp[j + 1]; o = operm[j]; yj = y[j]; dj = Dinv[j]; }
+    for (; c < nt; c += W) {
+        const int2 tn = c + W < nt ? tab[nt - 1 - (c + W)] : make_int2(0, 0);
+        const bool hasn = c + W < nt && (tn.y == 0 || lane < tn.y);
+        const int64_t jn = (int64_t)tn.x + (tn.y > 0 ? lane : 0);
+        int64_t bn = 0, en = 0;
+        int32_t on = 0;
+        XT yn = 0;
+        double dn = 0.0;
+        if (hasn) {
+            bn = cp[jn]; en = cp[jn + 1]; on = operm[jn]; yn = y[jn]; dn = Dinv[jn];
+            if ((tn.y > 0 || lane == 0) && en > bn) prefetch_l2(ri + en - 1, v + en - 1);
+        }
+        if (t.y == 0) {
+            const XT acc = warp_row<true, VT, XT>(b, e, lane, ri, v, z, spin_limit, status);
+            if (lane == 0) {
+                const XT zj = to_x<XT>((double)yj * dj) - acc;
+                y[j] = sentinel<XT>();
+                st_pub(z + j, zj);
+                zout[o] = (double)zj;
+            }
+        } else {
+            const bool lng = has && e - b > TPR_LONG;
+            if (has && !lng) {
+                XT acc = 0;
+                if (!dot_ready<true, VT, XT>(b, e, 0, 1, ri, v, z, acc, spin_limit, status))
+                    set_status(status, ST_TIMEOUT);
+                const XT zj = to_x<XT>((double)yj * dj) - acc;
+                y[j] = sentinel<XT>();
+                st_pub(z + j, zj);
+                zout[o] = (double)zj;
+            }
+            for (unsigned lm = __ballot_sync(FULL, lng); lm; lm &= lm - 1) {
+                const int src = __ffs(lm) - 1;
+                const int64_t bb = __shfl_sync(FULL, b, src), ee = __shfl_sync(FULL, e, src);
+                XT acc = warp_row<true, VT, XT>(bb, ee, lane, ri, v, z, spin_limit, status);
+                acc = __shfl_sync(FULL, acc, 0);
+                if (lane == src) {
+                    const XT zj = to_x<XT>((double)yj * dj) - acc;
+                    y[j] = sentinel<XT>();
+                    st_pub(z + j, zj);
+                    zout[o] = (double)zj;
+                }
+            }
+        }
+        t = tn; has = hasn; j = jn; b = bn; e = en; o = on; yj = yn; dj = dn;
     }
 }
 
@@ -782,9 +1006,25 @@ cudaError_t apply_s(const SolveArgs &A, const PcgBuffers &B, const double *r, do
     return apply_t<S, double, double>(A, A.Fvalr64, A.Fval64, B.yl64, B.zl64, r, zout, partial, st, s);
 }
 
+template <typename VT, typename XT>
+cudaError_t apply_tpr(const SolveArgs &A, const VT *vr, const VT *vc, XT *y, XT *z, const double *r, double *zout,
+                      const PcgState *st, cudaStream_t s)
+{
+    k_trsv_fwd_h<VT, XT><<<A.tpr_blocks, TPR_THREADS, 0, s>>>(A.tpr_chunks, A.ntpr, A.Frp, A.Fcol, vr, A.operm, r,
+                                                              y, z, st, A.spin_limit, A.status);
+    k_trsv_bwd_h<VT, XT><<<A.tpr_blocks, TPR_THREADS, 0, s>>>(A.tpr_chunks, A.ntpr, A.Fcp, A.Frow, vc, A.Dinv,
+                                                              A.operm, y, z, zout, st, A.spin_limit, A.status);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
 cudaError_t apply(const SolveArgs &A, const PcgBuffers &B, const double *r, double *zout, double *partial,
                   const PcgState *st, cudaStream_t s)
 {
+    if (A.tpr_blocks > 0 && A.tpr_chunks && !A.skip && !A.gt_f && !partial) {
+        if (A.prec == 32) return apply_tpr<float, float>(A, A.Fvalr32, A.Fval32, B.yl32, B.zl32, r, zout, st, s);
+        return apply_tpr<double, double>(A, A.Fvalr64, A.Fval64, B.yl64, B.zl64, r, zout, st, s);
+    }
     switch (A.lanes_trsv) {
     case 4: return apply_s<4>(A, B, r, zout, partial, st, s);
     case 8: return apply_s<8>(A, B, r, zout, partial, st, s);
@@ -883,6 +1123,19 @@ int trsv_configure(int lanes, int warps, int *blocks_per_sm, int prec, bool skip
         *blocks_per_sm = std::min(a, c);
     }
     return e == cudaSuccess ? 0 : -1;
+}
+
+int tpr_blocks_per_sm(int prec)
+{
+    int a = 0, b = 0;
+    if (prec == 32) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trsv_fwd_h<float, float>, TPR_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trsv_bwd_h<float, float>, TPR_THREADS, 0);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trsv_fwd_h<double, double>, TPR_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trsv_bwd_h<double, double>, TPR_THREADS, 0);
+    }
+    return std::min(a, b);
 }
 
 cudaError_t precond_apply(const SolveArgs &A, const PcgBuffers &B, const double *r, double *z, cudaStream_t st)

@@ -28,7 +28,13 @@ class parac_opts(C.Structure):
                 ("max_pool_regrow", C.c_int32), ("warps_per_block", C.c_int32), ("spin_limit", C.c_int64),
                 ("blocks", C.c_int32), ("queue_chunk", C.c_int32), ("big_threshold", C.c_int32),
                 ("sptrsv", C.c_int32), ("check_every", C.c_int32), ("timing", C.c_int32),
-                ("stream", C.c_void_p), ("samples", C.c_int32), ("fill_store", C.c_int32)]
+                ("stream", C.c_void_p), ("samples", C.c_int32), ("fill_store", C.c_int32),
+                ("block_cap", C.c_int32), ("coop", C.c_int32), ("sample_sort", C.c_int32), ("idle_ns", C.c_int32),
+                ("trace_path", C.c_char_p), ("trsv_blocks", C.c_int32), ("poll_ns", C.c_int32),
+                ("pcg_graph", C.c_int32), ("pcg_many", C.c_int32), ("pcg_workers", C.c_int32)]
+
+DEFAULT, ON, OFF = 0, 1, 2
+SPTRSV_AUTO, SPTRSV_WARP, SPTRSV_SUB8, SPTRSV_SUB4, SPTRSV_THREAD = 0, 1, 2, 3, 4
 
 
 class parac_system(C.Structure):
@@ -108,6 +114,8 @@ def parac_opts_default(**kw):
     for k, v in kw.items():
         if k == "stream" and v is not None and not isinstance(v, int):
             v = v.cuda_stream if hasattr(v, "cuda_stream") else int(v)
+        if k == "trace_path" and isinstance(v, str):
+            v = v.encode()
         setattr(o, k, v)
     return o
 

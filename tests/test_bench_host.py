@@ -59,6 +59,12 @@ def test_reference_arm_runs_the_oracle():
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "Mnnz(G)/s"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    # the same metric string and workload description as the GPU arm prints
+    sys.path.insert(0, ROOT)
+    import bench
+    assert line["metric"] == bench.METRIC
+    assert line["config"]["workload"] == bench.WORKLOAD_DESC["grid2d-64"]
+    assert line["pcg_iters"] > 0 and line["true_relres"] <= 1e-8 and line["cpu_baseline"]["tts_s"] > 0
 
 
 def test_reference_arm_batch_sample():

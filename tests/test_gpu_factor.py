@@ -198,11 +198,10 @@ def test_batched_factor_matches_per_system_oracle(P):
         G.free()
 
 
-def test_warp_only_paths_match(P, monkeypatch):
+def test_warp_only_paths_match(P):
     """With the CTA-cooperative path switched off every working set is handled
     by single warps (shared buffer, CTA buffer under a lock, global scratch):
     the factor must not change."""
-    monkeypatch.setenv("PARAC_COOP", "0")
     rng = np.random.default_rng(8)
     n = 3000
     hub = np.zeros(n - 1, np.int64)
@@ -213,19 +212,18 @@ def test_warp_only_paths_match(P, monkeypatch):
     key = np.unique(lo * n + hi)
     A = W.laplacian_from_edges(n, key // n, key % n, rng.uniform(0.5, 2, len(key)))
     perm = W.random_ordering(n, 3)
-    _check(P, A, perm, 5)
-    _check(P, A, perm, 5, big_threshold=32)
+    _check(P, A, perm, 5, coop=P.OFF)
+    _check(P, A, perm, 5, big_threshold=32, coop=P.OFF)
 
 
-@pytest.mark.parametrize("sample_sort", ["1", "0"])
-def test_rmat_bit_identical(P, monkeypatch, sample_sort):
+@pytest.mark.parametrize("sample_sort", ["on", "off"])
+def test_rmat_bit_identical(P, sample_sort):
     """R-MAT scale 15 (hubs of a few thousand neighbours, fill that piles up
     on the last vertices): the cooperative path with working sets in global
     memory, by sample sort and by the bitonic network, gives the oracle's
     factor."""
-    monkeypatch.setenv("PARAC_SAMPLE_SORT", sample_sort)
     A, perm, seed, _ = W.config("rmat-15")
-    _, st = _check(P, A, perm, seed)
+    _, st = _check(P, A, perm, seed, sample_sort=P.ON if sample_sort == "on" else P.OFF)
     assert st["vertices_global_path"] > 0
 
 

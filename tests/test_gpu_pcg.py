@@ -180,7 +180,7 @@ def test_block_pcg_device_arrays(P):
 
 
 @pytest.mark.parametrize("nrhs", [1, 6])
-def test_graph_replay_matches_direct_launches(P, monkeypatch, nrhs):
+def test_graph_replay_matches_direct_launches(P, nrhs):
     """The captured-graph replay of the PCG iterations runs the same kernels
     in the same order as direct launches: identical bits."""
     A, perm, seed, _ = W.config("grid2d-64")
@@ -188,8 +188,9 @@ def test_graph_replay_matches_direct_launches(P, monkeypatch, nrhs):
     G = _factor(P, A, perm, seed)
     Xg, itg, rrg, _ = P.parac_pcg(G, A.n, None, None, None, B, tol=1e-10, maxit=500)
     Xg2, itg2, _, _ = P.parac_pcg(G, A.n, None, None, None, B, tol=1e-10, maxit=500)    # replay of a cached graph
-    monkeypatch.setenv("PARAC_GRAPH", "0")
-    Xd, itd, rrd, _ = P.parac_pcg(G, A.n, None, None, None, B, tol=1e-10, maxit=500)
+    Gd = _factor(P, A, perm, seed, pcg_graph=P.OFF)          # same factor, iterations launched directly
+    Xd, itd, rrd, _ = P.parac_pcg(Gd, A.n, None, None, None, B, tol=1e-10, maxit=500)
+    Gd.free()
     assert np.array_equal(itg, itd) and np.array_equal(Xg, Xd) and np.array_equal(rrg, rrd)
     assert np.array_equal(itg2, itd) and np.array_equal(Xg2, Xd)
     G.free()
@@ -220,7 +221,7 @@ def test_grid3d_128_full_size(P):
     G.free()
 
 
-@pytest.mark.parametrize("strategy", [1, 2, 3])
+@pytest.mark.parametrize("strategy", [1, 2, 3, 4])
 def test_sptrsv_strategies(P, strategy):
     """Every triangular-solve layout applies the same preconditioner (up to
     the order of the row sums) and PCG reaches 1e-8 within one iteration of
@@ -310,15 +311,14 @@ def _relres(A, x, b):
     return np.linalg.norm(b - M @ x) / np.linalg.norm(b)
 
 
-def test_pcg_many_thread_path_matches_single_calls(P, monkeypatch):
-    """With the per-system worker threads (PARAC_PCG_MANY=threads) every
+def test_pcg_many_thread_path_matches_single_calls(P):
+    """With the per-system worker threads (pcg_many = PARAC_OFF) every
     system's result is bit-identical to its own parac_pcg call (host and device
     right-hand sides)."""
     import torch
-    monkeypatch.setenv("PARAC_PCG_MANY", "threads")
     batch = W.sddm_batch(12, nmin=500, nmax=20000, seed=13)
     systems = [(A.n, A.colptr, A.rowind, A.val, perm) for (A, perm, b) in batch]
-    Gs = P.parac_factor_many(systems, seed=3)
+    Gs = P.parac_factor_many(systems, seed=3, opts=P.parac_opts_default(pcg_many=P.OFF))
     bs = [b for (A, perm, b) in batch]
     xs, its, rrs, status = P.parac_pcg_many(Gs, bs, tol=1e-8, maxit=500)
     assert status == "PARAC_OK" and np.all(rrs <= 1e-8)
