@@ -59,10 +59,12 @@ enum { PARAC_KIND_AUTO = 0, PARAC_KIND_LAPLACIAN = 1, PARAC_KIND_SDDM = 2 };
 /* Triangular-solve strategies (all sync-free, rows in dependency-level
  * order): WARP gives each row a warp of 32 lanes (and a whole block to a row
  * of more than 512 entries); SUB8 / SUB4 give each row 8 / 4 lanes, so a warp
- * works on 4 / 8 short rows at once; THREAD gives each row one lane, runs of
- * up to 32 rows of one dependency level to a warp, and rows of more than 64
- * entries to the whole warp (for factors without rows or columns of more than
- * 2048 entries; others fall back to WARP).  AUTO is WARP. */
+ * works on 4 / 8 short rows at once; THREAD is the hybrid: a dependency level
+ * with more rows than the solve grid has warps is cut into runs of up to 32
+ * rows, one lane per row (rows of more than 64 entries go to the whole warp),
+ * and every row of a narrower level gets a warp (for factors without rows or
+ * columns of more than 2048 entries; others fall back to WARP).  AUTO is
+ * THREAD where it applies, else WARP. */
 enum { PARAC_SPTRSV_AUTO = 0, PARAC_SPTRSV_WARP = 1, PARAC_SPTRSV_SUB8 = 2, PARAC_SPTRSV_SUB4 = 3,
        PARAC_SPTRSV_THREAD = 4 };
 /* Tri-state switches of parac_opts: 0 = the library default. */

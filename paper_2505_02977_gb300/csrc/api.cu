@@ -277,8 +277,9 @@ struct parac_factor_s {
     std::string stats;
     SolveCache cache;
     int32_t max_row = 0;                               // longest row / column of F
-    DBuf tpr_chunks;                                   // chunks of the thread-per-row solves (int2)
+    DBuf tpr_chunks;                                   // table of the hybrid solves (int2), built lazily
     int32_t ntpr = 0;
+    bool tpr_tried = false;
     DBuf sgt_f, sgt_b;                                 // group tables of the one-row-per-warp solves
     int32_t sng_f = 0, sng_b = 0;
     DBuf spart_f, spart_b;                             // partial sums of their split rows
@@ -752,27 +753,6 @@ void finish_handle(parac_factor_s *h, int64_t n, int64_t nnzF, const Opts &O)
     // building the table (a host pass over the rows) at setup.
     CK(cudaStreamSynchronize(st));
     h->max_row = maxlen;
-    if (maxlen <= TPR_MAX_ROW && n > 0) {
-        // table of the hybrid solves, in level order: a level with more rows
-        // than the solve grid has warps is cut into runs of at most 32 rows
-        // (a lane per row), a narrower one lists its rows (a warp per row);
-        // O(depth + n / 32 + rows of narrow levels) host work on the level starts
-        const int64_t wide = (int64_t)num_sms() * std::max(1, tpr_blocks_per_sm(h->prec)) * (TPR_THREADS / 32);
-        std::vector<int2> ch;
-        ch.reserve((size_t)(n / 32 + h->depth + 1));
-        for (int32_t l = 0; l < h->depth; ++l) {
-            const int64_t q0 = h->lstart[(size_t)l], q1 = h->lstart[(size_t)l + 1];
-            if (q1 - q0 > wide) {
-                for (int64_t q = q0; q < q1; q += 32) ch.push_back(make_int2((int)q, (int)std::min<int64_t>(32, q1 - q)));
-            } else {
-                for (int64_t q = q0; q < q1; ++q) ch.push_back(make_int2((int)q, 0));
-            }
-        }
-        h->ntpr = (int32_t)ch.size();
-        h->tpr_chunks = DBuf(sizeof(int2) * ch.size(), st);
-        CK(cudaMemcpyAsync(h->tpr_chunks.p, ch.data(), sizeof(int2) * ch.size(), cudaMemcpyHostToDevice, st));
-        CK(cudaStreamSynchronize(st));
-    }
     if (maxlen > 4 * LONG_ROW_SINGLE) {
         std::vector<int64_t> rp((size_t)n + 1), cp((size_t)n + 1);
         CK(cudaMemcpyAsync(rp.data(), h->Srp.p, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
@@ -1112,6 +1092,34 @@ thread_local bool t_no_graph = false;     // one-shot solves: capturing would co
 // best on the 128^3 grid with a warp per row (266 ms PCG vs 271 at 256 ns and
 // 319 at 1024); the SDDM batch is indifferent.
 
+// Table of the hybrid solves, built on a handle's first single-system solve
+// (the batched solves of parac_pcg_many do not use it): in level order, a
+// level with more rows than the solve grid has warps is cut into runs of at
+// most 32 rows (a lane per row), a narrower one lists its rows (a warp per
+// row); O(depth + n / 32 + rows of narrow levels) host work on the level starts.
+void ensure_tpr_table(parac_factor_s *h)
+{
+    if (h->tpr_tried || h->n <= 0) return;
+    h->tpr_tried = true;
+    if (h->max_row > TPR_MAX_ROW || h->sng_f > 0 || (int64_t)h->lstart.size() != (int64_t)h->depth + 1) return;
+    const int64_t blocks = h->trsv_blocks > 0 ? h->trsv_blocks : (int64_t)num_sms();
+    const int64_t wide = blocks * (TPR_THREADS / 32);
+    std::vector<int2> ch;
+    ch.reserve((size_t)(h->n / 32 + h->depth + 1));
+    for (int32_t l = 0; l < h->depth; ++l) {
+        const int64_t q0 = h->lstart[(size_t)l], q1 = h->lstart[(size_t)l + 1];
+        if (q1 - q0 > wide) {
+            for (int64_t q = q0; q < q1; q += 32) ch.push_back(make_int2((int)q, (int)std::min<int64_t>(32, q1 - q)));
+        } else {
+            for (int64_t q = q0; q < q1; ++q) ch.push_back(make_int2((int)q, 0));
+        }
+    }
+    h->tpr_chunks = DBuf(sizeof(int2) * ch.size(), h->stream);
+    CK(cudaMemcpyAsync(h->tpr_chunks.p, ch.data(), sizeof(int2) * ch.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->ntpr = (int32_t)ch.size();
+}
+
 SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, const double *Lv, int64_t nnzL)
 {
     SolveArgs A{};
@@ -1147,13 +1155,17 @@ SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, co
     const int64_t rows_per_group = (int64_t)A.trsv_warps * (32 / A.lanes_trsv);
     const int64_t groups = (G->n + rows_per_group - 1) / rows_per_group;
     if (groups < A.trsv_blocks) A.trsv_blocks = (int)std::max<int64_t>(groups, 1);
-    // one lane per row (THREAD) when no row or column is long
-    const bool tpr = G->ntpr > 0 && G->sng_f == 0 && G->sptrsv == PARAC_SPTRSV_THREAD;
+    // the hybrid solves (THREAD, and AUTO) when no row or column is long
+    if (G->sptrsv == PARAC_SPTRSV_THREAD || G->sptrsv == PARAC_SPTRSV_AUTO) ensure_tpr_table(G);
+    const bool tpr = G->ntpr > 0 && G->sng_f == 0 &&
+                     (G->sptrsv == PARAC_SPTRSV_THREAD || G->sptrsv == PARAC_SPTRSV_AUTO);
     if (tpr) {
         const int tb = std::max(1, tpr_blocks_per_sm(A.prec));
         const int64_t tmax = std::max<int64_t>(1, (int64_t)num_sms() * tb / std::max(1, t_grid_share));  // all co-resident
         const int64_t wpb = TPR_THREADS / 32;
-        int64_t want = tmax;                         // every resident warp: narrow rows get a warp each
+        // one block of 8 warps per SM: measured best on the 128^3 grid (FP64
+        // apply 3.45 ms against 3.86 with 1.5 blocks and 4.13 with 2 per SM)
+        int64_t want = num_sms();
         if (G->trsv_blocks > 0) want = G->trsv_blocks;
         want = std::min<int64_t>(want, ((int64_t)G->ntpr + wpb - 1) / wpb);
         A.tpr_blocks = (int32_t)std::max<int64_t>(1, std::min<int64_t>(tmax, want));
@@ -1926,7 +1938,8 @@ extern "C" parac_status parac_autotune(int32_t count, const parac_system *system
         CK(cudaMemsetAsync(r.p, 0x3f, 8 * (size_t)std::max<int64_t>(nmax, 1), st));   // every entry 0x3f3f...3f
         CK(cudaStreamSynchronize(st));
         struct SCand { int strat; double ms; };
-        std::vector<SCand> sc = {{PARAC_SPTRSV_WARP, 0}, {PARAC_SPTRSV_SUB8, 0}, {PARAC_SPTRSV_SUB4, 0}};
+        std::vector<SCand> sc = {{PARAC_SPTRSV_THREAD, 0}, {PARAC_SPTRSV_WARP, 0}, {PARAC_SPTRSV_SUB8, 0},
+                                 {PARAC_SPTRSV_SUB4, 0}};
         int si = 0;
         for (size_t c = 0; c < sc.size(); ++c) {
             for (auto h : hs) h->sptrsv = sc[c].strat;

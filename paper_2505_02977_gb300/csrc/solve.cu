@@ -441,9 +441,12 @@ __device__ __forceinline__ bool finish_chunk(const XT *x, const int32_t (&cc)[RP
 // and the publication remain, not a batch of FMAs and the shuffle tree (an
 // FP64 add costs ~100 cycles on this chip).  The order of the sum is fixed:
 // the tree over the head, then the tail in order.
+// The batched solves (many systems' levels interleaved: thousands of rows in
+// flight, throughput-bound) keep the plain lane-strided sum (TN = 0).
 constexpr int TAIL = 4;
 
-__device__ __forceinline__ int64_t head_len(int64_t len) { return len > TAIL ? len - TAIL : 0; }
+template <int TN = TAIL>
+__device__ __forceinline__ int64_t head_len(int64_t len) { return len > TN ? len - TN : 0; }
 
 template <bool REV, typename VT, typename XT>
 __device__ __forceinline__ bool tail_sum(int64_t b, int64_t e, const int32_t *idx, const VT *v, const XT *x, XT &acc,
@@ -571,7 +574,7 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
             if (r.aux) { r.kind = GK_ROWS; r.j = -1; }      // a stopped system's group: nothing to do
         if (r.kind == GK_ROWS && r.j >= 0) {
             if (sl == 0) rr = rhs[o];
-            fetch_chunk<S, false, VT>(bb, bb + head_len(ee - bb), sl, ci, v, c, w);
+            fetch_chunk<S, false, VT>(bb, bb + head_len<SKIP ? 0 : TAIL>(ee - bb), sl, ci, v, c, w);
         }
     };
     int64_t g = blockIdx.x;
@@ -622,7 +625,7 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
             __syncthreads();
         } else if (j >= 0) {
             XT acc = 0;
-            const int64_t h = head_len(e - b);
+            const int64_t h = head_len<SKIP ? 0 : TAIL>(e - b);
             bool ok = finish_chunk<VT, XT>(y, cc, vv, xx, acc, spin_limit, status);
             if (ok && h > (int64_t)RPF * S)
                 ok = dot_ready<false, VT, XT>(b, b + h, sl + RPF * S, S, ci, v, y, acc, spin_limit, status);
@@ -631,7 +634,7 @@ __global__ void k_trsv_fwd(int32_t n, const int64_t *rp, const int32_t *ci, cons
                 for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
             }
             if (sl == 0) {
-                if (ok) ok = tail_sum<false, VT, XT>(b, e, ci, v, y, acc, spin_limit, status);
+                if (ok && !SKIP) ok = tail_sum<false, VT, XT>(b, e, ci, v, y, acc, spin_limit, status);
                 zreset[j] = sentinel<XT>();
                 st_pub(y + j, to_x<XT>(rj) - acc);
             }
@@ -683,7 +686,7 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
                 yv = y[r.j]; dv = Dinv[r.j];
                 rv = r_orig ? r_orig[o] : 0.0;
             }
-            fetch_chunk<S, true, VT>(ee - head_len(ee - bb), ee, sl, ri, v, c, w);
+            fetch_chunk<S, true, VT>(ee - head_len<SKIP ? 0 : TAIL>(ee - bb), ee, sl, ri, v, c, w);
         }
     };
     // finish column j with the sum of its terms (thread / lane that owns it)
@@ -740,7 +743,7 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
             __syncthreads();
         } else if (j >= 0) {
             XT acc = 0;
-            const int64_t h = head_len(e - b);
+            const int64_t h = head_len<SKIP ? 0 : TAIL>(e - b);
             bool ok = finish_chunk<VT, XT>(z, cc, vv, xx, acc, spin_limit, status);
             if (ok && h > (int64_t)RPF * S)
                 ok = dot_ready<true, VT, XT>(e - h, e, sl + RPF * S, S, ri, v, z, acc, spin_limit, status);
@@ -749,7 +752,7 @@ __global__ void k_trsv_bwd(int32_t n, const int64_t *cp, const int32_t *ri, cons
                 for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(smask, acc, off);
             }
             if (sl == 0) {
-                if (ok) ok = tail_sum<true, VT, XT>(b, e, ri, v, z, acc, spin_limit, status);
+                if (ok && !SKIP) ok = tail_sum<true, VT, XT>(b, e, ri, v, z, acc, spin_limit, status);
                 publish(j, yj, dj, o, rj, acc);
             }
             if (!ok) set_status(status, ST_TIMEOUT);
@@ -843,11 +846,12 @@ __global__ void __launch_bounds__(256) k_trsv_fwd_h(const int2 *tab, int32_t nt,
             bn = rp[jn]; en = rp[jn + 1]; rn = rhs[operm[jn]];
             if (tn.y > 0 || lane == 0) prefetch_l2(ci + bn, v + bn);
         }
+        const XT rx = to_x<XT>(rj);                      // converted before any wait
         if (t.y == 0) {                                   // a narrow level's row: the whole warp
             const XT acc = warp_row<false, VT, XT>(b, e, lane, ci, v, y, spin_limit, status);
             if (lane == 0) {
                 zreset[j] = sentinel<XT>();
-                st_pub(y + j, to_x<XT>(rj) - acc);
+                st_pub(y + j, rx - acc);
             }
         } else {                                          // a run of a wide level: a lane per row
             const bool lng = has && e - b > TPR_LONG;
@@ -856,7 +860,7 @@ __global__ void __launch_bounds__(256) k_trsv_fwd_h(const int2 *tab, int32_t nt,
                 if (!dot_ready<false, VT, XT>(b, e, 0, 1, ci, v, y, acc, spin_limit, status))
                     set_status(status, ST_TIMEOUT);
                 zreset[j] = sentinel<XT>();
-                st_pub(y + j, to_x<XT>(rj) - acc);
+                st_pub(y + j, rx - acc);
             }
             for (unsigned lm = __ballot_sync(FULL, lng); lm; lm &= lm - 1) {
                 const int src = __ffs(lm) - 1;
@@ -865,7 +869,7 @@ __global__ void __launch_bounds__(256) k_trsv_fwd_h(const int2 *tab, int32_t nt,
                 acc = __shfl_sync(FULL, acc, 0);
                 if (lane == src) {
                     zreset[j] = sentinel<XT>();
-                    st_pub(y + j, to_x<XT>(rj) - acc);
+                    st_pub(y + j, rx - acc);
                 }
             }
         }
@@ -905,10 +909,11 @@ __global__ void __launch_bounds__(256) k_trsv_bwd_h(const int2 *tab, int32_t nt,
             bn = cp[jn]; en = cp[jn + 1]; on = operm[jn]; yn = y[jn]; dn = Dinv[jn];
             if ((tn.y > 0 || lane == 0) && en > bn) prefetch_l2(ri + en - 1, v + en - 1);
         }
+        const XT sj = to_x<XT>((double)yj * dj);         // D^+ y, rounded, before any wait
         if (t.y == 0) {
             const XT acc = warp_row<true, VT, XT>(b, e, lane, ri, v, z, spin_limit, status);
             if (lane == 0) {
-                const XT zj = to_x<XT>((double)yj * dj) - acc;
+                const XT zj = sj - acc;
                 y[j] = sentinel<XT>();
                 st_pub(z + j, zj);
                 zout[o] = (double)zj;
@@ -919,7 +924,7 @@ __global__ void __launch_bounds__(256) k_trsv_bwd_h(const int2 *tab, int32_t nt,
                 XT acc = 0;
                 if (!dot_ready<true, VT, XT>(b, e, 0, 1, ri, v, z, acc, spin_limit, status))
                     set_status(status, ST_TIMEOUT);
-                const XT zj = to_x<XT>((double)yj * dj) - acc;
+                const XT zj = sj - acc;
                 y[j] = sentinel<XT>();
                 st_pub(z + j, zj);
                 zout[o] = (double)zj;
@@ -930,7 +935,7 @@ __global__ void __launch_bounds__(256) k_trsv_bwd_h(const int2 *tab, int32_t nt,
                 XT acc = warp_row<true, VT, XT>(bb, ee, lane, ri, v, z, spin_limit, status);
                 acc = __shfl_sync(FULL, acc, 0);
                 if (lane == src) {
-                    const XT zj = to_x<XT>((double)yj * dj) - acc;
+                    const XT zj = sj - acc;
                     y[j] = sentinel<XT>();
                     st_pub(z + j, zj);
                     zout[o] = (double)zj;
