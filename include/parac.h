@@ -69,6 +69,10 @@ enum { PARAC_SPTRSV_AUTO = 0, PARAC_SPTRSV_WARP = 1, PARAC_SPTRSV_SUB8 = 2, PARA
        PARAC_SPTRSV_THREAD = 4 };
 /* Tri-state switches of parac_opts: 0 = the library default. */
 enum { PARAC_DEFAULT = 0, PARAC_ON = 1, PARAC_OFF = 2 };
+/* Elimination order: the caller's ordering array (NULL = identity), or Sec.
+ * V's NNZ-sorted ordering computed on the device (the ordering array must
+ * then be NULL). */
+enum { PARAC_ORDER_GIVEN = 0, PARAC_ORDER_NNZ = 1 };
 
 /*
  * Options.  parac_opts_default() fills the defaults; a NULL opts pointer
@@ -133,6 +137,12 @@ enum { PARAC_DEFAULT = 0, PARAC_ON = 1, PARAC_OFF = 2 };
  *                   default = one block-diagonal solve when the handles allow
  *                   it; PARAC_OFF = one parac_pcg per system on worker threads
  *   pcg_workers     worker threads of that per-system path (0: 4)
+ *   order           PARAC_ORDER_GIVEN (default) or PARAC_ORDER_NNZ: vertices
+ *                   by ascending count of stored entries in their column
+ *                   (Sec. V, the paper's choice for the GPU), ties by the top
+ *                   31 bits of the (v+1)-th output of a splitmix64 generator
+ *                   started from `seed` (v = the vertex's index in its
+ *                   system), then by v; each system of a batch separately.
  */
 typedef struct {
     int32_t kind;
@@ -160,6 +170,7 @@ typedef struct {
     int32_t pcg_graph;
     int32_t pcg_many;
     int32_t pcg_workers;
+    int32_t order;
 } parac_opts;
 
 void parac_opts_default(parac_opts *opts);

@@ -312,6 +312,7 @@ Opts read_opts(const parac_opts *in)
     if (r.o.g_precision != 32) r.o.g_precision = 64;
     if (r.o.samples <= 0) r.o.samples = 1;
     if (r.o.fill_store != 1) r.o.fill_store = 0;
+    if (r.o.order != PARAC_ORDER_NNZ) r.o.order = PARAC_ORDER_GIVEN;
     if (r.o.idle_ns < 0) r.o.idle_ns = 0;
     if (r.o.trsv_blocks < 0) r.o.trsv_blocks = 0;
     r.o.poll_ns = r.o.poll_ns <= 0 ? 64 : std::max(16, std::min(100000, r.o.poll_ns));
@@ -897,7 +898,18 @@ parac_status parac_factor(int64_t n, const int64_t *colptr, const int32_t *rowin
         h->nnzL = nnz;
         DView<int32_t> ri; ri.set(rowind, (size_t)nnz, st);
         DView<double> va; va.set(val, (size_t)nnz, st);
+        if (O.o.order == PARAC_ORDER_NNZ && ordering) {
+            set_err("an ordering array and order = PARAC_ORDER_NNZ exclude each other");
+            return PARAC_EINVAL;
+        }
         DView<int32_t> od; od.set(ordering, (size_t)n, st);
+        DBuf nnz_ord;
+        if (O.o.order == PARAC_ORDER_NNZ && n > 0) {     // Sec. V NNZ-sorted ordering, on the device
+            nnz_ord = dalloc<int32_t>((size_t)n, st);
+            DBuf tmp(nnz_order_tmp_bytes(n), st);
+            CK(nnz_sorted_order(n, cp.p, nullptr, nullptr, 1, seed, nnz_ord.as<int32_t>(), tmp.p, st));
+            od.p = nnz_ord.as<int32_t>();
+        }
         std::vector<SysDesc> sys(1);
         sys[0].n = n; sys[0].obase = 0; sys[0].lbase = 0;
         sys[0].ground = O.o.kind == PARAC_KIND_LAPLACIAN ? -1 : (int32_t)n;
@@ -914,7 +926,7 @@ parac_status parac_factor(int64_t n, const int64_t *colptr, const int32_t *rowin
         h->Lev = std::move(fo.Lev);
         if (n == 0) h->Lev = dalloc<int32_t>(1, st);
         h->perm = dalloc<int32_t>(std::max<int64_t>(n, 1), st);
-        if (ordering) copy_out(h->perm.p, od.p, 4 * (size_t)n, st);
+        if (od.p) copy_out(h->perm.p, od.p, 4 * (size_t)n, st);
         else CK(launch_iota_i32(h->perm.as<int32_t>(), n, 0, st));
         h->Lp = dalloc<int64_t>(n + 1, st); h->Li = dalloc<int32_t>(std::max<int64_t>(nnz, 1), st);
         h->Lv = dalloc<double>(std::max<int64_t>(nnz, 1), st);
@@ -960,6 +972,12 @@ parac_status parac_factor_many(int32_t count, const parac_system *systems, uint6
             N += y.n; NNZ += z; NL += y.n + (sys[s].ground >= 0 ? 1 : 0);
         }
         if (NL >= 0x7fffffffLL) { set_err("batch too large for 32-bit labels"); return PARAC_EINVAL; }
+        if (O.o.order == PARAC_ORDER_NNZ)
+            for (int s = 0; s < count; ++s)
+                if (systems[s].ordering) {
+                    set_err("system %d: an ordering array and order = PARAC_ORDER_NNZ exclude each other", s);
+                    return PARAC_EINVAL;
+                }
         // concatenated device input with global indices
         DBuf cp = dalloc<int64_t>(N + 1, st), ri = dalloc<int32_t>(std::max<int64_t>(NNZ, 1), st),
              va = dalloc<double>(std::max<int64_t>(NNZ, 1), st), ord = dalloc<int32_t>(std::max<int64_t>(N, 1), st),
@@ -975,19 +993,30 @@ parac_status parac_factor_many(int32_t count, const parac_system *systems, uint6
             CK(launch_add_offset_i64(c.p, cp.as<int64_t>() + sys[s].obase, n, zb, st));
             CK(launch_add_offset_i32(r.p, ri.as<int32_t>() + zb, nnz[s], (int32_t)sys[s].obase, st));
             copy_out(va.as<double>() + zb, v.p, 8 * (size_t)nnz[s], st);
+            // (host inputs were staged by their copies before those returned, and
+            // the staging buffers are freed in stream order: no sync per system)
             if (y.ordering) {
                 DView<int32_t> o; o.set(y.ordering, (size_t)n, st);
                 CK(launch_add_offset_i32(o.p, ord.as<int32_t>() + sys[s].obase, n, (int32_t)sys[s].obase, st));
-                CK(cudaStreamSynchronize(st));
             } else {
                 CK(launch_iota_i32(ord.as<int32_t>() + sys[s].obase, n, (int32_t)sys[s].obase, st));
             }
             CK(launch_iota_i32(lab.as<int32_t>() + sys[s].obase, n, (int32_t)sys[s].lbase, st));
             zb += nnz[s];
-            CK(cudaStreamSynchronize(st));   // host views of this system can go
         }
         const int64_t total = zb;
         CK(cudaMemcpyAsync(cp.as<int64_t>() + N, &total, 8, cudaMemcpyHostToDevice, st));
+        if (O.o.order == PARAC_ORDER_NNZ && N > 0) {     // every system's NNZ-sorted ordering at once
+            std::vector<int32_t> ob_h((size_t)count);
+            for (int s = 0; s < count; ++s) ob_h[(size_t)s] = (int32_t)sys[s].obase;
+            DBuf obase = dalloc<int32_t>((size_t)count, st), sys_of_v = dalloc<int32_t>((size_t)N, st);
+            CK(cudaMemcpyAsync(obase.p, ob_h.data(), 4 * (size_t)count, cudaMemcpyHostToDevice, st));
+            CK(launch_sys_of_label(count, obase.as<int32_t>(), (int32_t)N, sys_of_v.as<int32_t>(), st));
+            DBuf tmp(nnz_order_tmp_bytes(N), st);
+            CK(nnz_sorted_order(N, cp.as<int64_t>(), sys_of_v.as<int32_t>(), obase.as<int32_t>(), count, seed,
+                                ord.as<int32_t>(), tmp.p, st));
+            CK(cudaStreamSynchronize(st));
+        }
         FactorOut fo;
         run_factor(N, cp.as<int64_t>(), ri.as<int32_t>(), va.as<double>(), ord.as<int32_t>(), lab.as<int32_t>(), sys,
                    O.o.kind, seed, O, fo);

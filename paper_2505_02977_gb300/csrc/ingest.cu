@@ -239,6 +239,39 @@ __global__ void k_iota_i32(int32_t *p, int64_t n, int32_t base)
         p[k] = base + (int32_t)k;
 }
 
+// ---------------------------------------------------------------- NNZ-sorted ordering
+// Sec. V's "NNZ-sorted" ordering (the paper's recommendation for the GPU):
+// vertices by ascending count of stored entries in their column; ties by a
+// seeded key, then by vertex index.  The key of local vertex v is the top 31
+// bits of the (v+1)-th output of the splitmix64 generator started from state
+// `seed` (Steele, Lea, Flood: "Fast splittable pseudorandom number
+// generators", OOPSLA 2014).
+__device__ __forceinline__ uint64_t splitmix64_output(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + i * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_order_keys(int64_t n, const int64_t *colptr, const int32_t *sys_of_v, const int32_t *sys_obase,
+                             uint64_t seed, int32_t *tie, int32_t *deg, int32_t *ord)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lv = sys_of_v ? v - sys_obase[sys_of_v[v]] : v;
+        tie[v] = (int32_t)(splitmix64_output(seed, (uint64_t)lv + 1) >> 33);
+        const int64_t d = colptr[v + 1] - colptr[v];
+        deg[v] = (int32_t)(d < 0x7fffffff ? d : 0x7fffffff);
+        ord[v] = (int32_t)v;
+    }
+}
+
+__global__ void k_gather_keys(int64_t n, const int32_t *src, const int32_t *ord, int32_t *dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[ord[i]];
+}
+
 inline int grid_for(int64_t n, int threads)
 {
     int64_t b = (n + threads - 1) / threads;
@@ -333,6 +366,28 @@ cudaError_t launch_iota_i32(int32_t *p, int64_t n, int32_t base, cudaStream_t st
     if (n == 0) return cudaSuccess;
     k_iota_i32<<<grid_for(n, 256), 256, 0, st>>>(p, n, base); count_launches(1);
     return cudaGetLastError();
+}
+
+size_t nnz_order_tmp_bytes(int64_t n) { return 12 * (size_t)n + radix_tmp_bytes(n) + 256; }
+
+cudaError_t nnz_sorted_order(int64_t n, const int64_t *colptr, const int32_t *sys_of_v, const int32_t *sys_obase,
+                             int32_t nsys, uint64_t seed, int32_t *ord, void *tmp, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    int32_t *tie = (int32_t *)tmp, *deg = tie + n, *key = deg + n;
+    void *rtmp = (void *)(((uintptr_t)(key + n) + 255) & ~(uintptr_t)255);
+    const int g = grid_for(n, 256);
+    k_order_keys<<<g, 256, 0, st>>>(n, colptr, sys_of_v, sys_obase, seed, tie, deg, ord); count_launches(1);
+    // stable passes from the least significant key: tie, then degree, then system
+    cudaError_t e = stable_sort_pairs((int32_t)n, tie, ord, 31, rtmp, st);
+    if (e != cudaSuccess) return e;
+    k_gather_keys<<<g, 256, 0, st>>>(n, deg, ord, key); count_launches(1);
+    e = stable_sort_pairs((int32_t)n, key, ord, 31, rtmp, st);
+    if (e != cudaSuccess || !sys_of_v) return e;
+    int bits = 0;
+    while (bits < 31 && ((nsys - 1) >> bits) != 0) ++bits;
+    k_gather_keys<<<g, 256, 0, st>>>(n, sys_of_v, ord, key); count_launches(1);
+    return stable_sort_pairs((int32_t)n, key, ord, bits, rtmp, st);
 }
 
 }  // namespace parac

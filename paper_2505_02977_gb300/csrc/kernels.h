@@ -61,6 +61,13 @@ cudaError_t launch_add_offset_i32(const int32_t *in, int32_t *out, int64_t n, in
 cudaError_t launch_add_offset_i64(const int64_t *in, int64_t *out, int64_t n, int64_t off, cudaStream_t st);
 cudaError_t launch_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t st);
 cudaError_t launch_iota_i32(int32_t *p, int64_t n, int32_t base, cudaStream_t st);
+// NNZ-sorted ordering (ascending stored entries per column, ties by a seeded
+// splitmix64 key, then index) of n vertices, or of each system of a batch
+// (sys_of_v / sys_obase non-null: keys use local indices, systems stay in
+// order); ord receives global vertex indices; tmp holds nnz_order_tmp_bytes(n).
+size_t nnz_order_tmp_bytes(int64_t n);
+cudaError_t nnz_sorted_order(int64_t n, const int64_t *colptr, const int32_t *sys_of_v, const int32_t *sys_obase,
+                             int32_t nsys, uint64_t seed, int32_t *ord, void *tmp, cudaStream_t st);
 
 // ---------------------------------------------------------------- elim.cu
 size_t elim_smem_bytes(int warps_per_block, int warp_cap, int block_cap);

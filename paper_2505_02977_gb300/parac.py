@@ -31,9 +31,11 @@ class parac_opts(C.Structure):
                 ("stream", C.c_void_p), ("samples", C.c_int32), ("fill_store", C.c_int32),
                 ("block_cap", C.c_int32), ("coop", C.c_int32), ("sample_sort", C.c_int32), ("idle_ns", C.c_int32),
                 ("trace_path", C.c_char_p), ("trsv_blocks", C.c_int32), ("poll_ns", C.c_int32),
-                ("pcg_graph", C.c_int32), ("pcg_many", C.c_int32), ("pcg_workers", C.c_int32)]
+                ("pcg_graph", C.c_int32), ("pcg_many", C.c_int32), ("pcg_workers", C.c_int32),
+                ("order", C.c_int32)]
 
 DEFAULT, ON, OFF = 0, 1, 2
+ORDER_GIVEN, ORDER_NNZ = 0, 1
 SPTRSV_AUTO, SPTRSV_WARP, SPTRSV_SUB8, SPTRSV_SUB4, SPTRSV_THREAD = 0, 1, 2, 3, 4
 
 

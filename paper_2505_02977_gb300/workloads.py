@@ -239,12 +239,24 @@ def random_ordering(n, seed):
     return np.random.default_rng(seed).permutation(n).astype(np.int32)
 
 
+def splitmix64_outputs(seed, count):
+    """Outputs 1..count of the splitmix64 generator started from state `seed`
+    (Steele, Lea, Flood, OOPSLA 2014), as uint64."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + np.arange(1, count + 1, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
 def nnz_sorted_ordering(mat, seed):
-    """Columns by ascending stored-entry count, ties broken randomly (Sec. V 'NNZ-Sorted')."""
+    """Sec. V 'NNZ-Sorted' ordering: columns by ascending stored-entry count,
+    ties by the top 31 bits of the (v+1)-th splitmix64 output from state
+    `seed`, then by index v."""
     n = mat.n
     deg = np.diff(mat.colptr)
-    tie = np.random.default_rng(seed).permutation(n)
-    return np.lexsort((tie, deg)).astype(np.int32)
+    tie = (splitmix64_outputs(seed, n) >> np.uint64(33)).astype(np.int64)
+    return np.lexsort((np.arange(n), tie, deg)).astype(np.int32)
 
 
 def gaussian_rhs(n, nrhs=1, seed=0, center=True):

@@ -1,0 +1,78 @@
+"""Parity at the benchmark configurations' own sizes.
+
+* The power-law workload at R-MAT scale 20 (the largest scale the sequential
+  oracle factors in seconds): the GPU factor is bit-identical to the oracle's.
+* The full 200-system SDDM batch factored in one parac_factor_many launch:
+  the largest and the smallest system of each family are bit-identical to the
+  oracle's factor of that system with its batch index.
+* Block PCG with 32 right-hand sides and the FP32-stored factor on R-MAT scale
+  15 (the shape of the 32-right-hand-side power-law workload): every column
+  converges to 1e-8 within one iteration of the oracle's mixed-form PCG on
+  that column, and after the same number of iterations its iterate agrees
+  with the oracle's to 1e-5 relative (the FP32 sums are reduced in another
+  order; see test_gpu_mixed.py).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_02977_gb300 import workloads as W
+from tests.helpers import same_factor
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2505_02977_gb300 import parac
+    return parac
+
+
+def test_rmat20_bit_identical(P):
+    A, perm, seed, _ = W.config("rmat-20")
+    G = P.parac_factor(A.n, A.colptr, A.rowind, A.val, perm, seed)
+    ref = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)
+    assert same_factor(G.export(), ref)
+    G.free()
+
+
+def test_sddm_batch_200_extremes_bit_identical(P):
+    batch = W.sddm_batch(200)
+    systems = [(A.n, A.colptr, A.rowind, A.val, perm) for (A, perm, b) in batch]
+    seed = 31
+    Gs = P.parac_factor_many(systems, seed=seed, opts=P.parac_opts_default(g_precision=32))
+    picks = []
+    for fam in range(3):
+        idx = list(range(fam, 200, 3))
+        sizes = [batch[i][0].n for i in idx]
+        picks += [idx[int(np.argmax(sizes))], idx[int(np.argmin(sizes))]]
+    for s in picks:
+        A, perm, _ = batch[s]
+        ref = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed, sys=s)
+        assert same_factor(Gs[s].export(), ref), s
+    for G in Gs:
+        G.free()
+
+
+def test_block_pcg_32_rhs_fp32_rmat15(P):
+    A, perm, seed, _ = W.config("rmat-15")
+    B = W.gaussian_rhs(A.n, 32, 44)
+    G = P.parac_factor(A.n, A.colptr, A.rowind, A.val, perm, seed, P.parac_opts_default(g_precision=32))
+    F = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)
+    X, it, rr, status = P.parac_pcg(G, A.n, None, None, None, B, tol=1e-8, maxit=1000)
+    assert status == "PARAC_OK" and np.all(rr <= 1e-8)
+    ito = []
+    for j in range(32):
+        _, itj, rrj = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, B[:, j], 1e-8, 1000, prec=32)
+        assert rrj <= 1e-8 and abs(int(it[j]) - itj) <= 1, (j, int(it[j]), itj)
+        ito.append(itj)
+    k = min(ito)
+    X2, it2, _, _ = P.parac_pcg(G, A.n, None, None, None, B, tol=0.0, maxit=k)
+    assert np.all(it2 == k)
+    for j in range(0, 32, 4):
+        xo, _, _ = oracle.pcg(A.colptr, A.rowind, A.val, F, perm, B[:, j], 0.0, k, prec=32)
+        xa, xb = X2[:, j] - X2[:, j].mean(), xo - xo.mean()
+        assert np.linalg.norm(xa - xb) <= 1e-5 * np.linalg.norm(xb), j
+    G.free()

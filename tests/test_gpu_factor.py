@@ -298,3 +298,32 @@ def test_hashmap_fill_store_bit_identical(P):
         ref = oracle.factor(Ab.colptr, Ab.rowind, Ab.val, pb, seed=99, sys=s)
         assert same_factor(G.export(), ref)
         G.free()
+
+
+@pytest.mark.parametrize("name", ["grid3d-32", "rmat-15"])
+def test_nnz_sorted_ordering_on_device(P, name):
+    """order = PARAC_ORDER_NNZ builds Sec. V's NNZ-sorted ordering on the
+    device: the factor is bit-identical to the oracle's under the numpy
+    definition of that ordering (any other permutation would change it)."""
+    A, _, seed, _ = W.config(name)
+    G = P.parac_factor(A.n, A.colptr, A.rowind, A.val, None, seed, P.parac_opts_default(order=P.ORDER_NNZ))
+    ref = oracle.factor(A.colptr, A.rowind, A.val, W.nnz_sorted_ordering(A, seed), seed=seed)
+    got = G.export()
+    assert same_factor(got, ref), _first_diff(got, ref)
+    G.free()
+    with pytest.raises(P.ParacError) as e:     # an ordering array as well: refused
+        P.parac_factor(A.n, A.colptr, A.rowind, A.val, np.arange(A.n, dtype=np.int32), seed,
+                       P.parac_opts_default(order=P.ORDER_NNZ))
+    assert e.value.status == "PARAC_EINVAL"
+
+
+def test_nnz_sorted_ordering_batch(P):
+    """The batched form orders every system by its own NNZ-sorted ordering."""
+    batch = W.sddm_batch(8, nmin=300, nmax=6000, seed=23)
+    systems = [(A.n, A.colptr, A.rowind, A.val, None) for (A, perm, b) in batch]
+    Gs = P.parac_factor_many(systems, seed=11, opts=P.parac_opts_default(order=P.ORDER_NNZ))
+    for s, ((A, perm, b), G) in enumerate(zip(batch, Gs)):
+        ref = oracle.factor(A.colptr, A.rowind, A.val, W.nnz_sorted_ordering(A, 11), seed=11, sys=s)
+        got = G.export()
+        assert same_factor(got, ref), (s, _first_diff(got, ref))
+        G.free()
