@@ -694,7 +694,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ordering", default="random", choices=["random", "nnz"])
-    ap.add_argument("--samples", type=int, default=1, help="samples per clique-tree slot (AC(k); 1: Alg. 2)")
+    ap.add_argument("--samples", type=int, default=1, help="samples per clique-tree slot (per-slot multi-sampling MS(k); 1: Alg. 2)")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision pass (FP32-stored factor) run beside the FP64 one")
     ap.add_argument("--batch", default="auto", choices=["auto", "on", "off"],

@@ -104,9 +104,13 @@ enum { PARAC_ORDER_GIVEN = 0, PARAC_ORDER_NNZ = 1 };
  *   stream          cudaStream_t to order all work on.
  *   timing          Nonzero: record per-phase device times in the stats.
  *   samples         Samples drawn per clique-tree slot (0 or 1: Alg. 2).  k > 1
- *                   is AC(k) (Sec. VI): slot p draws k neighbours, sample q
- *                   with Philox counter (k_label, p, sys, q), each edge weighted
- *                   c_p / k -- a denser factor for possibly fewer iterations.
+ *                   is per-slot multi-sampling MS(k): every slot p of every
+ *                   pivot draws k neighbours, sample q with Philox counter
+ *                   (k_label, p, sys, q), each edge weighted c_p / k -- a denser
+ *                   factor for fewer iterations.  MS(k) is this library's
+ *                   variant, not Sec. VI's AC(2), which doubles the samples
+ *                   of the input's own entries only: MS(k) also multiplies
+ *                   the samples of fill entries.
  *   fill_store      Where fill waits for its column's pivot: 0 = per-column
  *                   slabs (inline 16 entries, then geometrically growing
  *                   overflow slabs); 1 = the hashmap W of Sec. IV-C (open

@@ -108,7 +108,7 @@ def philox4x64_10(ctr, key, L=None):
 
 
 def slot_uniform(seed, k, p, sys=0, q=0, L=None):
-    """Uniform of sample q of slot p (q > 0 only for AC(k))."""
+    """Uniform of sample q of slot p (q > 0 only for per-slot multi-sampling MS(k))."""
     L = L or lib()
     return L.orc_slot_uniform(seed, k, p, sys) if q == 0 else L.orc_slot_uniform_s(seed, k, p, sys, q)
 
@@ -136,7 +136,7 @@ def pick_search(S, lo, R, L=None):
 
 def eliminate_one(rows, w, seed, k, sys=0, samples=1, L=None):
     """Eliminate one pivot from its gathered entries; returns a dict.  With
-    samples > 1 (AC(samples)) the sampled edges are listed sample by sample:
+    samples > 1 (per-slot multi-sampling MS(samples)) the sampled edges are listed sample by sample:
     sample q of slot p at q*(d-1) + p-1."""
     L = L or lib()
     rows = _arr(rows, np.int32); w = _arr(w, np.float64)
@@ -194,7 +194,8 @@ def _collect(L, h):
 
 def factor(colptr, rowind, val, ordering=None, seed=0, sys=0, kind=KIND_AUTO, samples=1, L=None):
     """Sequential rchol factor L ~ F D F^T in label space (Alg. 1 + Alg. 2;
-    samples > 1: AC(samples), every clique-tree slot drawing that many edges)."""
+    samples > 1: per-slot multi-sampling MS(samples), every clique-tree slot
+    drawing that many edges -- not Sec. VI's AC(2))."""
     L = L or lib()
     colptr = _arr(colptr, np.int64); rowind = _arr(rowind, np.int32); val = _arr(val, np.float64)
     ordp = None if ordering is None else _arr(ordering, np.int32)

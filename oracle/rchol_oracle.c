@@ -101,7 +101,7 @@ void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint6
 }
 
 /* R4: the uniform in (0,1] drawn for sample q of slot p of pivot k of
- * system sys (q = 0 for the plain method; AC(k) draws q = 0..k-1). */
+ * system sys (q = 0 for the plain method; MS(k) draws q = 0..k-1). */
 double orc_slot_uniform_s(uint64_t seed, uint64_t k, uint64_t p, uint64_t sys, uint64_t q)
 {
     uint64_t ctr[4] = { k, p, sys, q }, key[2] = { seed, 0 }, o[4];
@@ -202,10 +202,13 @@ typedef struct {
 } orc_step;
 
 /* Eliminate pivot k whose gathered entries are (rows[i], w[i]), i < g.
- * ksamp samples per slot (AC(ksamp), Sec. VI's AC(k) read as: every slot of
- * the clique tree draws ksamp independent neighbours with counters
- * (k, p, sys, q), q < ksamp, each edge weighted c_p / ksamp; ksamp = 1 is
- * Alg. 2). */
+ * ksamp samples per slot: per-slot multi-sampling MS(ksamp), where every slot
+ * of the clique tree, at every pivot, draws ksamp independent neighbours with
+ * counters (k, p, sys, q), q < ksamp, each edge weighted c_p / ksamp; ksamp =
+ * 1 is Alg. 2.  This is NOT Sec. VI's AC(2) (after Gao-Kyng-Spielman), which
+ * doubles the samples of the input matrix's own entries only:
+ * MS(k) also multiplies the samples of fill-derived entries, so its fill
+ * compounds from pivot to pivot. */
 static int orc_eliminate_k(int64_t g, const int32_t *rows, const double *w, uint64_t seed,
                            uint64_t k, uint64_t sys, int ksamp, orc_step *st)
 {
@@ -411,7 +414,7 @@ typedef struct {
     double *D;
     int64_t *level;         /* dependency-DAG level per label */
     int64_t max_gather, nfill, nnz_all;
-    int ksamp;              /* samples per clique-tree slot (AC(ksamp)); 1 = Alg. 2 */
+    int ksamp;              /* samples per clique-tree slot (MS(ksamp)); 1 = Alg. 2 */
 } orc_state;
 
 static void state_free(orc_state *S)

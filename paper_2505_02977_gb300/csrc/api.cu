@@ -533,8 +533,9 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
     }
     DBuf pool_row, pool_w, f_row, f_val, scratch, w_col, w_row, w_w;
     for (int attempt = 0;; ++attempt) {
-        // AC(k): k fill edges per slot, and the neighbour lists of later pivots
-        // grow with them -- AC(2) on 3D grids has 10-30x the fill of Alg. 2
+        // per-slot multi-sampling MS(k): k fill edges per slot, and the neighbour
+        // lists of later pivots grow with them -- MS(2) on 3D grids has 10-30x
+        // the fill of Alg. 2
         const double ks = O.o.samples > 1 ? 4.0 * (double)O.o.samples * (double)O.o.samples : 1.0;
         const unsigned long long pool_cap = (unsigned long long)std::ceil(mult * ks * (double)nnz_low) + 4096ull;
         const unsigned long long f_cap = (unsigned long long)std::ceil(std::max(mult, 4.0) * ks * (double)nnz_low) +

@@ -128,7 +128,7 @@ __device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_
 }
 
 // Uniform in (0, 1] for sample q of sampling slot p of pivot k (local label)
-// of system sys (q > 0 only with several samples per slot, AC(k)): the top 53
+// of system sys (q > 0 only with several samples per slot, MS(k)): the top 53
 // bits of the first output word, plus one, times 2^-53.
 __device__ __forceinline__ double slot_uniform(uint64_t seed, uint64_t k, uint64_t p, uint64_t sys,
                                                uint64_t q = 0ull)
@@ -227,7 +227,7 @@ struct ElimArgs {
     int32_t *trace_parent;         // optional: pivot whose decrement made the vertex ready
     int32_t *trace_phase;          // optional: cycles of the cooperative path's 8 phases [nl * 8]
     int32_t sample_sort;           // cooperative path: sample sort for working sets in global memory
-    int32_t samples;               // samples per clique-tree slot (AC(k)); 1: Alg. 2
+    int32_t samples;               // samples per clique-tree slot (MS(k)); 1: Alg. 2
     // hashmap fill store (Sec. IV-C): slot state / column tag, entry row and weight
     int32_t hash_store;            // 1: fill goes to the hashmap W instead of slabs
     int32_t *wcol;                 // [wcap] -1 free, -2 busy, else the column the entry belongs to

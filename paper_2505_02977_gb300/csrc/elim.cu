@@ -537,7 +537,7 @@ __device__ int32_t eliminate_small(const ElimArgs &a, int32_t k, int64_t o0, int
         hi = u < xv ? xv : u;
     }
     if (!append_fill(a, act, lo, hi, c)) return -2;
-    // further samples of every slot (AC(k)): own uniforms, the same weight
+    // further samples of every slot (MS(k)): own uniforms, the same weight
     for (int q = 1; q < a.samples; ++q) {
         const unsigned long long Rq = act ? dbits(__dmul_rn(Sp, slot_uniform(a.seed, klocal, (uint64_t)p, sys,
                                                                                 (uint64_t)q))) : 0ull;
@@ -752,7 +752,7 @@ __device__ int32_t eliminate_big(const ElimArgs &a, int32_t k, int64_t o0, int32
     // ---------------------------------------------------------------- sample clique tree + append
     uint64_t klocal, sys;
     sys_of(a, k, klocal, sys);
-    for (int q = 0; q < a.samples; ++q) {                // sample q of every slot (q > 0: AC(k))
+    for (int q = 0; q < a.samples; ++q) {                // sample q of every slot (q > 0: MS(k))
         for (int pb = 1; pb < d; pb += 32) {
             const int p = pb + lane;
             const bool act = p < d;
@@ -1491,7 +1491,7 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     uint64_t klocal, sys;
     sys_of(a, k, klocal, sys);
     bool ok = true;
-    for (int q = 0; q < a.samples && ok; ++q)             // sample q of every slot (q > 0: AC(k))
+    for (int q = 0; q < a.samples && ok; ++q)             // sample q of every slot (q > 0: MS(k))
     for (int pb = 1; pb < d; pb += nt) {
         const int p = pb + tid;
         const bool act = p < d;

@@ -237,7 +237,7 @@ def test_poisson_stand_ins_bit_identical(P, field):
 
 
 def test_ac2_bit_identical(P):
-    """AC(2) (two samples per clique-tree slot) on every elimination path:
+    """MS(2) (two samples per clique-tree slot) on every elimination path:
     register and warp paths (grid, random graphs), the CTA path with shared and
     global working sets (hub graph, R-MAT scale 15), and a grounded SDDM."""
     cases = [W.config("grid2d-64")[:3]]
@@ -267,7 +267,7 @@ def test_ac2_bit_identical(P):
 def test_hashmap_fill_store_bit_identical(P):
     """The hashmap fill store W (Sec. IV-C) instead of the per-column slabs: the
     same factor on every elimination path (register, warp, CTA with shared and
-    global working sets), with AC(2), SDDM, a batch, and a small table that
+    global working sets), with MS(2), SDDM, a batch, and a small table that
     forces regrowth."""
     cases = [W.config("grid2d-64")[:3], W.config("rmat-15")[:3], W.config("poisson-contrast-16")[:3]]
     rng = np.random.default_rng(31)

@@ -536,14 +536,15 @@ def test_fp32_pcg():
     assert i64 == 1 and r64 <= 1e-8 and i32 <= 2 and r32 <= 1e-8
 
 
-# ----------------------------------------------------------------- AC(k)
-# AC(k) (Sec. VI, after Gao-Kyng-Spielman): every slot of the clique tree
-# draws k neighbours, sample q with Philox counter (k, p, sys, q), each edge
-# weighted c_p / k.  k = 1 is Alg. 2.
+# ----------------------------------------------------------------- per-slot multi-sampling MS(k)
+# MS(k): every slot of the clique tree, at every pivot, draws k neighbours,
+# sample q with Philox counter (k, p, sys, q), each edge weighted c_p / k.
+# k = 1 is Alg. 2.  Not Sec. VI's AC(2), which doubles the samples of the
+# input matrix's own entries only.
 
 def test_ac2_counter_word_and_weights():
     """Sample q of slot p uses counter word 3 = q (checked against numpy's
-    Philox); sample 0 of AC(2) picks exactly AC(1)'s neighbour with half its
+    Philox); sample 0 of MS(2) picks exactly Alg. 2's neighbour with half its
     weight; sample 1 follows the literal "largest j >= p with S[j] >= R" rule
     with its own uniform."""
     rng = np.random.default_rng(17)
@@ -571,7 +572,7 @@ def test_ac2_counter_word_and_weights():
 
 
 def test_ac2_unbiased_by_enumeration():
-    """AC(2): summed over all outcomes of both samples of every slot, the
+    """MS(2): summed over all outcomes of both samples of every slot, the
     expected update equals the exact Schur complement update, as for Alg. 2."""
     rng = np.random.default_rng(19)
     for trial in range(200):
@@ -597,7 +598,7 @@ def test_ac2_unbiased_by_enumeration():
 
 
 def test_ac2_factor_counts_mean_and_variance():
-    """AC(2) appends twice the fill edges of Alg. 2; paths stay exact; the mean
+    """MS(2) appends twice the fill edges of Alg. 2; paths stay exact; the mean
     of F D F^T over seeds matches L within 4 standard errors, with a smaller
     variance than Alg. 2's (the reason for more samples)."""
     A = _mat(8, np.arange(7), np.arange(1, 8), np.linspace(0.5, 2.0, 7))
