@@ -114,9 +114,11 @@ enum { PARAC_ORDER_GIVEN = 0, PARAC_ORDER_NNZ = 1 };
  *   fill_store      Where fill waits for its column's pivot: 0 = per-column
  *                   slabs (inline 16 entries, then geometrically growing
  *                   overflow slabs); 1 = the hashmap W of Sec. IV-C (open
- *                   addressing, insert from hash(col) + fill_count(col) to
- *                   the right, gathered by parallel scans).  The factor is the
- *                   same either way.
+ *                   addressing: an entry of column c is inserted from step
+ *                   fill_count(c) of c's probe sequence hash(c), hash(c) + s_c,
+ *                   ... with a per-column odd stride s_c, and gathered by
+ *                   parallel scans of that sequence).  The factor is the same
+ *                   either way.
  * Finer elimination schedule (0 = default; none changes the factor):
  *   block_cap       entries of a CTA's shared working-set buffer, rounded up
  *                   to a power of two in [256, 8192] (default: 2048, or less

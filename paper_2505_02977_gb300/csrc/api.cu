@@ -540,7 +540,10 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         const unsigned long long pool_cap = (unsigned long long)std::ceil(mult * ks * (double)nnz_low) + 4096ull;
         const unsigned long long f_cap = (unsigned long long)std::ceil(std::max(mult, 4.0) * ks * (double)nnz_low) +
                                          (unsigned long long)nl + (unsigned long long)total_warps * fchunk + 4096ull;
-        const unsigned long long wcap = 2ull * pool_cap;     // load factor about 1/2 of the slab estimate
+        // load factor at most 1/2 of the slab estimate; a power of two, so that
+        // every odd probe stride reaches every slot (w_stride)
+        unsigned long long wcap = 2;
+        while (wcap < 2ull * pool_cap) wcap <<= 1;
         if (O.o.fill_store == 1) {                // hashmap W (Sec. IV-C)
             pool_row = dalloc<int32_t>(1, st); pool_w = dalloc<double>(1, st);
             w_col = dalloc<int32_t>(wcap, st); w_row = dalloc<int32_t>(wcap, st);
@@ -1122,32 +1125,22 @@ thread_local bool t_no_graph = false;     // one-shot solves: capturing would co
 // best on the 128^3 grid with a warp per row (266 ms PCG vs 271 at 256 ns and
 // 319 at 1024); the SDDM batch is indifferent.
 
-// Table of the hybrid solves, built on a handle's first single-system solve
-// (the batched solves of parac_pcg_many do not use it): in level order, a
-// level with more rows than the solve grid has warps is cut into runs of at
-// most 32 rows (a lane per row), a narrower one lists its rows (a warp per
-// row); O(depth + n / 32 + rows of narrow levels) host work on the level starts.
+// Table of the hybrid solves (schedule.h, hybrid_table), built on a handle's
+// first single-system solve: a level with more rows than the solve grid has
+// warps is cut into runs of at most 32 rows (a lane per row), a narrower one
+// lists its rows (a warp per row); O(depth + n / 32 + rows of narrow levels)
+// host work on the level starts.
 void ensure_tpr_table(parac_factor_s *h)
 {
     if (h->tpr_tried || h->n <= 0) return;
     h->tpr_tried = true;
     if (h->max_row > TPR_MAX_ROW || h->sng_f > 0 || (int64_t)h->lstart.size() != (int64_t)h->depth + 1) return;
     const int64_t blocks = h->trsv_blocks > 0 ? h->trsv_blocks : (int64_t)num_sms();
-    const int64_t wide = blocks * (TPR_THREADS / 32);
-    std::vector<int2> ch;
-    ch.reserve((size_t)(h->n / 32 + h->depth + 1));
-    for (int32_t l = 0; l < h->depth; ++l) {
-        const int64_t q0 = h->lstart[(size_t)l], q1 = h->lstart[(size_t)l + 1];
-        if (q1 - q0 > wide) {
-            for (int64_t q = q0; q < q1; q += 32) ch.push_back(make_int2((int)q, (int)std::min<int64_t>(32, q1 - q)));
-        } else {
-            for (int64_t q = q0; q < q1; ++q) ch.push_back(make_int2((int)q, 0));
-        }
-    }
-    h->tpr_chunks = DBuf(sizeof(int2) * ch.size(), h->stream);
-    CK(cudaMemcpyAsync(h->tpr_chunks.p, ch.data(), sizeof(int2) * ch.size(), cudaMemcpyHostToDevice, h->stream));
+    const std::vector<int32_t> t = hybrid_table({BatchSysLevels{0, 0, h->lstart, nullptr}}, blocks * (TPR_THREADS / 32));
+    h->tpr_chunks = DBuf(4 * std::max<size_t>(t.size(), 2), h->stream);
+    CK(cudaMemcpyAsync(h->tpr_chunks.p, t.data(), 4 * t.size(), cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    h->ntpr = (int32_t)ch.size();
+    h->ntpr = (int32_t)(t.size() / 2);
 }
 
 SolveArgs solve_args(parac_factor_s *G, const int64_t *Lp, const int32_t *Li, const double *Lv, int64_t nnzL)
@@ -1576,6 +1569,8 @@ constexpr int64_t BATCH_CHUNK_ROWS = 4096;
 struct BatchRun {
     DBuf Lp, Li, Lv, Fcp, Frow, Fval, Frp, Fcol, Fvalr, Dinv, operm;
     DBuf gt_f, gt_b, part_f, part_b;
+    DBuf hy;                          // hybrid-solve table (int2 entries), when used
+    int32_t nhy = 0, hy_blocks = 0;
     DBuf x, r, z, p, q, b, yl, zl, partials, sys, stop, state, status, clo, csys, sys_c0, seg;
 };
 
@@ -1684,11 +1679,24 @@ parac_status pcg_batch(int32_t count, const parac_factor_t *G, const double *con
         bw.push_back({i, off[(size_t)i], h->lstart, cp});
     }
     CK(cudaStreamSynchronize(st));
-    // one row per warp (the stop-flag solves; sub-warp rows measured slower here)
+    // the hybrid solves when no handle has a long row and the handles ask for
+    // them (THREAD or AUTO): the systems' levels interleaved in one table
+    bool hybrid = G[0]->sptrsv == PARAC_SPTRSV_THREAD || G[0]->sptrsv == PARAC_SPTRSV_AUTO;
+    for (int32_t i = 0; i < count && hybrid; ++i) hybrid = G[i]->max_row <= TPR_MAX_ROW;
+    if (hybrid) {
+        const int64_t hb = G[0]->trsv_blocks > 0 ? G[0]->trsv_blocks : (int64_t)num_sms();
+        const std::vector<int32_t> t = hybrid_table(fw, hb * (TPR_THREADS / 32));
+        R.hy = DBuf(4 * std::max<size_t>(t.size(), 2), st);
+        CK(cudaMemcpyAsync(R.hy.p, t.data(), 4 * t.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        R.nhy = (int32_t)(t.size() / 2);
+        R.hy_blocks = (int32_t)std::max<int64_t>(1, std::min<int64_t>(hb, (int64_t)num_sms() * std::max(1, tpr_blocks_per_sm(prec))));
+    }
+    // otherwise one row per warp (the stop-flag solves; sub-warp rows measured slower here)
     const int lanes = 32;
     const int rows_per_group = SOLVE_WARPS;
-    const GroupTable gf = batch_groups(fw, n, false, rows_per_group, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
-    const GroupTable gb = batch_groups(bw, n, true, rows_per_group, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
+    const GroupTable gf = hybrid ? GroupTable{} : batch_groups(fw, n, false, rows_per_group, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
+    const GroupTable gb = hybrid ? GroupTable{} : batch_groups(bw, n, true, rows_per_group, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
     R.gt_f = dalloc<int32_t>(std::max<size_t>(gf.g.size(), 4), st);
     R.gt_b = dalloc<int32_t>(std::max<size_t>(gb.g.size(), 4), st);
     CK(cudaMemcpyAsync(R.gt_f.p, gf.g.data(), 4 * gf.g.size(), cudaMemcpyHostToDevice, st));
@@ -1742,8 +1750,12 @@ parac_status pcg_batch(int32_t count, const parac_factor_t *G, const double *con
     CK(set_poll_backoff((unsigned)G[0]->poll_ns));
     A.spin_limit = spin;
     A.status = R.status.as<int32_t>();
-    A.gt_f = (const int4 *)R.gt_f.p; A.ng_f = gf.ngroups; A.part_f = R.part_f.p; A.nslot_f = gf.nslots;
-    A.gt_b = (const int4 *)R.gt_b.p; A.ng_b = gb.ngroups; A.part_b = R.part_b.p; A.nslot_b = gb.nslots;
+    if (hybrid) {
+        A.tpr_chunks = (const int2 *)R.hy.p; A.ntpr = R.nhy; A.tpr_blocks = R.hy_blocks;
+    } else {
+        A.gt_f = (const int4 *)R.gt_f.p; A.ng_f = gf.ngroups; A.part_f = R.part_f.p; A.nslot_f = gf.nslots;
+        A.gt_b = (const int4 *)R.gt_b.p; A.ng_b = gb.ngroups; A.part_b = R.part_b.p; A.nslot_b = gb.nslots;
+    }
     A.skip = R.stop.as<int32_t>();
     BatchBuffers B{};
     B.count = count; B.nchunks = nch;

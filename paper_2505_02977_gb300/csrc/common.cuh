@@ -152,6 +152,27 @@ __host__ __device__ __forceinline__ unsigned long long w_base(int32_t c, unsigne
     return ((unsigned long long)x * wcap) >> 32;
 }
 
+// Probe stride of column c: odd, so that over the power-of-two table every
+// column's probe sequence base, base + s, base + 2s, ... visits every slot.
+// With one stride for all columns (plain linear probing) a hub column's
+// hundreds of thousands of fill entries form one run of occupied slots, and
+// any column whose base lands in it probes through the whole run; with a
+// stride per column the columns' sequences cross only at single slots.
+__host__ __device__ __forceinline__ unsigned long long w_stride(int32_t c, unsigned long long wcap)
+{
+    uint32_t x = (uint32_t)c * 0x9e3779b9u;
+    x ^= x >> 15; x *= 0x2c1b3c6du;
+    x ^= x >> 12;
+    return (((unsigned long long)x * wcap) >> 32) | 1ull;
+}
+
+// Slot of step m of column c's probe sequence (wcap a power of two).
+__host__ __device__ __forceinline__ unsigned long long w_slot(unsigned long long base, unsigned long long stride,
+                                                             unsigned long long m, unsigned long long wcap)
+{
+    return (base + m * stride) & (wcap - 1);
+}
+
 // ---------------------------------------------------------------- fill store geometry
 // Column c's fill entries: indices [0, C0) live in an inline slab of the
 // column; index i >= C0 lives in overflow level j = 1 + floor(log4(i / C0)),

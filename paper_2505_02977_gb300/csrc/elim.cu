@@ -224,12 +224,14 @@ constexpr unsigned long long W_MAX_PROBE = 1ull << 16;   // probes before an ins
 __device__ bool append_fill(const ElimArgs &a, bool act, int32_t lo, int32_t hi, double c)
 {
     if (a.hash_store) {
-        // hashmap W (Sec. IV-C): probe right from base(lo) + fill_count(lo) for a
-        // free slot, claim it (free -> busy), write the entry, publish the tag
+        // hashmap W (Sec. IV-C): probe from step fill_count(lo) of lo's sequence
+        // (see w_stride) for a free slot, claim it (free -> busy), write the
+        // entry, publish the tag
         bool ok = true;
         if (act) {
             const uint32_t idx = atomicAdd(a.fcnt + lo, 1u);
-            unsigned long long i = (w_base(lo, a.wcap) + idx) % a.wcap;
+            const unsigned long long stride = w_stride(lo, a.wcap);
+            unsigned long long i = w_slot(w_base(lo, a.wcap), stride, idx, a.wcap);
             const unsigned long long lim = a.wcap < W_MAX_PROBE ? a.wcap : W_MAX_PROBE;
             bool placed = false;
             for (unsigned long long step = 0; step < lim; ++step) {
@@ -241,7 +243,7 @@ __device__ bool append_fill(const ElimArgs &a, bool act, int32_t lo, int32_t hi,
                     placed = true;
                     break;
                 }
-                if (++i == a.wcap) i = 0;
+                i = (i + stride) & (a.wcap - 1);
             }
             if (!placed) { set_status(a.status, ST_POOL); ok = false; }
             red_add_relaxed(a.dp + hi, 1);
@@ -335,8 +337,8 @@ __device__ __forceinline__ void sys_of(const ElimArgs &a, int32_t k, uint64_t &k
     }
 }
 
-// Fill entries of column k from the hashmap W: the warp scans right from k's
-// base slot, 32 slots at a time, until all cnt entries tagged k are found.
+// Fill entries of column k from the hashmap W: the warp scans k's probe
+// sequence, 32 slots at a time, until all cnt entries tagged k are found.
 // Every entry of k was published (release) before k became ready, so a busy
 // slot is never k's.  put(pos, row, w) receives the entry of scan rank pos;
 // the slot is freed for reuse.  false if the scan wrapped the whole table.
@@ -344,12 +346,12 @@ template <typename Put>
 __device__ __forceinline__ bool warp_hash_gather(const ElimArgs &a, int32_t k, uint32_t cnt, Put &&put)
 {
     const unsigned lane = lane_id();
-    const unsigned long long base = w_base(k, a.wcap);
+    const unsigned long long base = w_base(k, a.wcap), stride = w_stride(k, a.wcap);
     uint32_t found = 0;
     unsigned long long off = 0;
     while (found < cnt) {
         if (off >= a.wcap) return false;
-        const unsigned long long i = (base + off + lane) % a.wcap;
+        const unsigned long long i = w_slot(base, stride, off + lane, a.wcap);
         const bool mine = off + lane < a.wcap && ld_acquire(a.wcol + i) == k;
         const unsigned bal = __ballot_sync(FULL, mine);
         if (mine) {
@@ -385,12 +387,12 @@ __device__ int32_t eliminate_small(const ElimArgs &a, int32_t k, int64_t o0, int
     if (a.hash_store) {
         // fill entries from W to lanes norig.. (scan rank order): each round, the
         // lane of the p-th entry found hands it to lane norig + found + p
-        const unsigned long long base = w_base(k, a.wcap);
+        const unsigned long long base = w_base(k, a.wcap), stride = w_stride(k, a.wcap);
         uint32_t found = 0;
         unsigned long long off = 0;
         while (found < cnt) {
             if (off >= a.wcap) { bad = true; break; }
-            const unsigned long long i = (base + off + lane) % a.wcap;
+            const unsigned long long i = w_slot(base, stride, off + lane, a.wcap);
             const bool mine = off + lane < a.wcap && ld_acquire(a.wcol + i) == k;
             const unsigned bal = __ballot_sync(FULL, mine);
             int32_t fr = 0;
@@ -1285,13 +1287,13 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     // ---------------------------------------------------------------- gather
     for (int i = tid; i < norig; i += nt) { v.row[i] = __ldg(a.lrow + o0 + i); v.w[i] = __ldg(a.lw + o0 + i); }
     if (a.hash_store) {
-        // fill from W: the CTA scans right from k's base slot, nt slots a round
-        const unsigned long long base = w_base(k, a.wcap);
+        // fill from W: the CTA scans k's probe sequence, nt slots a round
+        const unsigned long long base = w_base(k, a.wcap), stride = w_stride(k, a.wcap);
         uint32_t found = 0;
         unsigned long long off = 0;
         while (found < cnt) {
             if (off >= a.wcap) { if (tid == 0) set_status(a.status, ST_INVAL); break; }
-            const unsigned long long i = (base + off + tid) % a.wcap;
+            const unsigned long long i = w_slot(base, stride, off + tid, a.wcap);
             const bool mine = off + tid < a.wcap && ld_acquire(a.wcol + i) == k;
             const unsigned bal = __ballot_sync(FULL, mine);
             if (lane == 0) cs.hcount[warp] = __popc(bal);

@@ -124,4 +124,36 @@ RowChunks row_chunks(const std::vector<int64_t> &off, int64_t rows)
     return c;
 }
 
+std::vector<int32_t> hybrid_table(const std::vector<BatchSysLevels> &sys, int64_t wide)
+{
+    size_t depth = 0;
+    int64_t n = 0;
+    for (const auto &y : sys) {
+        if (y.lstart.size() > depth + 1) depth = y.lstart.size() - 1;
+        if (!y.lstart.empty()) n += y.lstart.back() - y.lstart.front();
+    }
+    std::vector<int32_t> t;
+    t.reserve((size_t)(2 * (n / 16 + (int64_t)depth * (int64_t)sys.size() + 2)));
+    for (size_t l = 0; l < depth; ++l) {
+        int64_t width = 0;
+        for (const auto &y : sys)
+            if (l + 1 < y.lstart.size()) width += y.lstart[l + 1] - y.lstart[l];
+        const bool runs = width > wide;
+        for (const auto &y : sys) {
+            if (l + 1 >= y.lstart.size()) continue;
+            const int64_t q0 = y.off + y.lstart[l], q1 = y.off + y.lstart[l + 1];
+            const int32_t tag = y.sys << HY_SYS_SHIFT;
+            if (runs) {
+                for (int64_t q = q0; q < q1; q += 32) {
+                    t.push_back((int32_t)q);
+                    t.push_back((int32_t)std::min<int64_t>(32, q1 - q) | tag);
+                }
+            } else {
+                for (int64_t q = q0; q < q1; ++q) { t.push_back((int32_t)q); t.push_back(tag); }
+            }
+        }
+    }
+    return t;
+}
+
 }  // namespace parac

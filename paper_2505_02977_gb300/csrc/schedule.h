@@ -33,6 +33,16 @@ struct BatchSysLevels {
 GroupTable batch_groups(const std::vector<BatchSysLevels> &sys, int64_t n_tot, bool descending, int warps,
                         int long_row, int split_row, int chunk);
 
+// Table of the hybrid solves over one system or several (their levels
+// interleaved): entries in level order, systems in order within a level; a
+// level with more than `wide` rows (all systems together) is cut into runs of
+// at most 32 consecutive rows of one system, entry {first position, rows |
+// sys << HY_SYS_SHIFT}; a narrower level lists its rows one per entry,
+// {position, 0 | sys << HY_SYS_SHIFT}.  Two ints per entry.  The backward
+// solve walks the same table from its end.
+constexpr int32_t HY_COUNT_MASK = 63, HY_SYS_SHIFT = 6;
+std::vector<int32_t> hybrid_table(const std::vector<BatchSysLevels> &sys, int64_t wide);
+
 // Row chunks of the batched PCG's dot products: system s holds rows off[s] ..
 // off[s+1]; chunk c covers rows lo[c] .. lo[c+1] (at most `rows`, never two
 // systems), sys[c] is its system, and system s owns chunks first[s] ..

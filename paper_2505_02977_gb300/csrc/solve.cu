@@ -819,48 +819,68 @@ __device__ __forceinline__ XT warp_row(int64_t b, int64_t e, int lane, const int
     return acc;
 }
 
-// Table entry: (first position, rows) for a run of one wide level, or
-// (position, 0) for a row of a narrow level.
-template <typename VT, typename XT>
+// Table entry (schedule.h, hybrid_table): {first position, rows | sys <<
+// HY_SYS_SHIFT} for a run of a wide level, {position, 0 | sys << ...} for a
+// row of a narrow level.  SKIP: entries of systems whose stop flag is set are
+// skipped (the flag is read when the entry is prefetched).
+struct HyEntry {
+    int64_t j;      // this lane's position (its run row, or the warp's row)
+    int32_t cnt;    // rows of the run; 0: one row for the whole warp
+    bool has;       // this lane has work in the entry
+};
+
+template <bool SKIP>
+__device__ __forceinline__ HyEntry hy_decode(int64_t c, int32_t nt, const int2 *tab, bool rev, int lane,
+                                             const int32_t *skip)
+{
+    HyEntry h{0, 0, false};
+    if (c >= nt) return h;
+    const int2 t = __ldg(tab + (rev ? nt - 1 - c : c));
+    h.cnt = t.y & HY_COUNT_MASK;
+    if constexpr (SKIP)
+        if (__ldg(skip + (t.y >> HY_SYS_SHIFT))) return h;     // a stopped system: nothing to do
+    h.j = (int64_t)t.x + (h.cnt > 0 ? lane : 0);
+    h.has = h.cnt == 0 || lane < h.cnt;
+    return h;
+}
+
+template <typename VT, typename XT, bool SKIP>
 __global__ void __launch_bounds__(256) k_trsv_fwd_h(const int2 *tab, int32_t nt, const int64_t *rp,
                                                     const int32_t *ci, const VT *v, const int32_t *operm,
                                                     const double *rhs, XT *y, XT *zreset, const PcgState *st,
-                                                    long long spin_limit, int32_t *status)
+                                                    long long spin_limit, int32_t *status, const int32_t *skip)
 {
     if (st && st->done) return;
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int lane = threadIdx.x & 31;
     int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int2 t = c < nt ? tab[c] : make_int2(0, 0);
-    bool has = c < nt && (t.y == 0 || lane < t.y);
-    int64_t j = (int64_t)t.x + (t.y > 0 ? lane : 0), b = 0, e = 0;
+    HyEntry h = hy_decode<SKIP>(c, nt, tab, false, lane, skip);
+    int64_t b = 0, e = 0;
     double rj = 0.0;
-    if (has) { b = rp[j]; e = rp[j + 1]; rj = rhs[operm[j]]; }
+    if (h.has) { b = rp[h.j]; e = rp[h.j + 1]; rj = rhs[operm[h.j]]; }
     for (; c < nt; c += W) {
-        const int2 tn = c + W < nt ? tab[c + W] : make_int2(0, 0);
-        const bool hasn = c + W < nt && (tn.y == 0 || lane < tn.y);
-        const int64_t jn = (int64_t)tn.x + (tn.y > 0 ? lane : 0);
+        const HyEntry hn = hy_decode<SKIP>(c + W, nt, tab, false, lane, skip);
         int64_t bn = 0, en = 0;
         double rn = 0.0;
-        if (hasn) {
-            bn = rp[jn]; en = rp[jn + 1]; rn = rhs[operm[jn]];
-            if (tn.y > 0 || lane == 0) prefetch_l2(ci + bn, v + bn);
+        if (hn.has) {
+            bn = rp[hn.j]; en = rp[hn.j + 1]; rn = rhs[operm[hn.j]];
+            if (hn.cnt > 0 || lane == 0) prefetch_l2(ci + bn, v + bn);
         }
         const XT rx = to_x<XT>(rj);                      // converted before any wait
-        if (t.y == 0) {                                   // a narrow level's row: the whole warp
+        if (h.has && h.cnt == 0) {                        // a narrow level's row: the whole warp
             const XT acc = warp_row<false, VT, XT>(b, e, lane, ci, v, y, spin_limit, status);
             if (lane == 0) {
-                zreset[j] = sentinel<XT>();
-                st_pub(y + j, rx - acc);
+                zreset[h.j] = sentinel<XT>();
+                st_pub(y + h.j, rx - acc);
             }
-        } else {                                          // a run of a wide level: a lane per row
-            const bool lng = has && e - b > TPR_LONG;
-            if (has && !lng) {
+        } else if (h.cnt > 0) {                           // a run of a wide level: a lane per row
+            const bool lng = h.has && e - b > TPR_LONG;
+            if (h.has && !lng) {
                 XT acc = 0;
                 if (!dot_ready<false, VT, XT>(b, e, 0, 1, ci, v, y, acc, spin_limit, status))
                     set_status(status, ST_TIMEOUT);
-                zreset[j] = sentinel<XT>();
-                st_pub(y + j, rx - acc);
+                zreset[h.j] = sentinel<XT>();
+                st_pub(y + h.j, rx - acc);
             }
             for (unsigned lm = __ballot_sync(FULL, lng); lm; lm &= lm - 1) {
                 const int src = __ffs(lm) - 1;
@@ -868,65 +888,63 @@ __global__ void __launch_bounds__(256) k_trsv_fwd_h(const int2 *tab, int32_t nt,
                 XT acc = warp_row<false, VT, XT>(bb, ee, lane, ci, v, y, spin_limit, status);
                 acc = __shfl_sync(FULL, acc, 0);
                 if (lane == src) {
-                    zreset[j] = sentinel<XT>();
-                    st_pub(y + j, rx - acc);
+                    zreset[h.j] = sentinel<XT>();
+                    st_pub(y + h.j, rx - acc);
                 }
             }
         }
-        t = tn; has = hasn; j = jn; b = bn; e = en; rj = rn;
+        h = hn; b = bn; e = en; rj = rn;
     }
 }
 
 // Backward solve over the same table from its end: z[j] = RN(y[j] Dinv[j]) -
 // sum_{i>j} F(i,j) z[i], each column walked from its last entry (whose unknown
 // was published first); writes zout[operm[j]] and resets y[j] to the sentinel.
-template <typename VT, typename XT>
+template <typename VT, typename XT, bool SKIP>
 __global__ void __launch_bounds__(256) k_trsv_bwd_h(const int2 *tab, int32_t nt, const int64_t *cp,
                                                     const int32_t *ri, const VT *v, const double *Dinv,
                                                     const int32_t *operm, XT *y, XT *z, double *zout,
-                                                    const PcgState *st, long long spin_limit, int32_t *status)
+                                                    const PcgState *st, long long spin_limit, int32_t *status,
+                                                    const int32_t *skip)
 {
     if (st && st->done) return;
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int lane = threadIdx.x & 31;
     int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int2 t = c < nt ? tab[nt - 1 - c] : make_int2(0, 0);
-    bool has = c < nt && (t.y == 0 || lane < t.y);
-    int64_t j = (int64_t)t.x + (t.y > 0 ? lane : 0), b = 0, e = 0;
+    HyEntry h = hy_decode<SKIP>(c, nt, tab, true, lane, skip);
+    int64_t b = 0, e = 0;
     int32_t o = 0;
     XT yj = 0;
     double dj = 0.0;
-    if (has) { b = cp[j]; e = cp[j + 1]; o = operm[j]; yj = y[j]; dj = Dinv[j]; }
+    if (h.has) { b = cp[h.j]; e = cp[h.j + 1]; o = operm[h.j]; yj = y[h.j]; dj = Dinv[h.j]; }
     for (; c < nt; c += W) {
-        const int2 tn = c + W < nt ? tab[nt - 1 - (c + W)] : make_int2(0, 0);
-        const bool hasn = c + W < nt && (tn.y == 0 || lane < tn.y);
-        const int64_t jn = (int64_t)tn.x + (tn.y > 0 ? lane : 0);
+        const HyEntry hn = hy_decode<SKIP>(c + W, nt, tab, true, lane, skip);
         int64_t bn = 0, en = 0;
         int32_t on = 0;
         XT yn = 0;
         double dn = 0.0;
-        if (hasn) {
-            bn = cp[jn]; en = cp[jn + 1]; on = operm[jn]; yn = y[jn]; dn = Dinv[jn];
-            if ((tn.y > 0 || lane == 0) && en > bn) prefetch_l2(ri + en - 1, v + en - 1);
+        if (hn.has) {
+            bn = cp[hn.j]; en = cp[hn.j + 1]; on = operm[hn.j]; yn = y[hn.j]; dn = Dinv[hn.j];
+            if ((hn.cnt > 0 || lane == 0) && en > bn) prefetch_l2(ri + en - 1, v + en - 1);
         }
         const XT sj = to_x<XT>((double)yj * dj);         // D^+ y, rounded, before any wait
-        if (t.y == 0) {
+        if (h.has && h.cnt == 0) {
             const XT acc = warp_row<true, VT, XT>(b, e, lane, ri, v, z, spin_limit, status);
             if (lane == 0) {
                 const XT zj = sj - acc;
-                y[j] = sentinel<XT>();
-                st_pub(z + j, zj);
+                y[h.j] = sentinel<XT>();
+                st_pub(z + h.j, zj);
                 zout[o] = (double)zj;
             }
-        } else {
-            const bool lng = has && e - b > TPR_LONG;
-            if (has && !lng) {
+        } else if (h.cnt > 0) {
+            const bool lng = h.has && e - b > TPR_LONG;
+            if (h.has && !lng) {
                 XT acc = 0;
                 if (!dot_ready<true, VT, XT>(b, e, 0, 1, ri, v, z, acc, spin_limit, status))
                     set_status(status, ST_TIMEOUT);
                 const XT zj = sj - acc;
-                y[j] = sentinel<XT>();
-                st_pub(z + j, zj);
+                y[h.j] = sentinel<XT>();
+                st_pub(z + h.j, zj);
                 zout[o] = (double)zj;
             }
             for (unsigned lm = __ballot_sync(FULL, lng); lm; lm &= lm - 1) {
@@ -936,13 +954,13 @@ __global__ void __launch_bounds__(256) k_trsv_bwd_h(const int2 *tab, int32_t nt,
                 acc = __shfl_sync(FULL, acc, 0);
                 if (lane == src) {
                     const XT zj = sj - acc;
-                    y[j] = sentinel<XT>();
-                    st_pub(z + j, zj);
+                    y[h.j] = sentinel<XT>();
+                    st_pub(z + h.j, zj);
                     zout[o] = (double)zj;
                 }
             }
         }
-        t = tn; has = hasn; j = jn; b = bn; e = en; o = on; yj = yn; dj = dn;
+        h = hn; b = bn; e = en; o = on; yj = yn; dj = dn;
     }
 }
 
@@ -1011,14 +1029,15 @@ cudaError_t apply_s(const SolveArgs &A, const PcgBuffers &B, const double *r, do
     return apply_t<S, double, double>(A, A.Fvalr64, A.Fval64, B.yl64, B.zl64, r, zout, partial, st, s);
 }
 
-template <typename VT, typename XT>
+template <typename VT, typename XT, bool SKIP>
 cudaError_t apply_tpr(const SolveArgs &A, const VT *vr, const VT *vc, XT *y, XT *z, const double *r, double *zout,
                       const PcgState *st, cudaStream_t s)
 {
-    k_trsv_fwd_h<VT, XT><<<A.tpr_blocks, TPR_THREADS, 0, s>>>(A.tpr_chunks, A.ntpr, A.Frp, A.Fcol, vr, A.operm, r,
-                                                              y, z, st, A.spin_limit, A.status);
-    k_trsv_bwd_h<VT, XT><<<A.tpr_blocks, TPR_THREADS, 0, s>>>(A.tpr_chunks, A.ntpr, A.Fcp, A.Frow, vc, A.Dinv,
-                                                              A.operm, y, z, zout, st, A.spin_limit, A.status);
+    k_trsv_fwd_h<VT, XT, SKIP><<<A.tpr_blocks, TPR_THREADS, 0, s>>>(A.tpr_chunks, A.ntpr, A.Frp, A.Fcol, vr, A.operm,
+                                                                    r, y, z, st, A.spin_limit, A.status, A.skip);
+    k_trsv_bwd_h<VT, XT, SKIP><<<A.tpr_blocks, TPR_THREADS, 0, s>>>(A.tpr_chunks, A.ntpr, A.Fcp, A.Frow, vc, A.Dinv,
+                                                                    A.operm, y, z, zout, st, A.spin_limit, A.status,
+                                                                    A.skip);
     count_launches(2);
     return cudaGetLastError();
 }
@@ -1026,9 +1045,13 @@ cudaError_t apply_tpr(const SolveArgs &A, const VT *vr, const VT *vc, XT *y, XT 
 cudaError_t apply(const SolveArgs &A, const PcgBuffers &B, const double *r, double *zout, double *partial,
                   const PcgState *st, cudaStream_t s)
 {
-    if (A.tpr_blocks > 0 && A.tpr_chunks && !A.skip && !A.gt_f && !partial) {
-        if (A.prec == 32) return apply_tpr<float, float>(A, A.Fvalr32, A.Fval32, B.yl32, B.zl32, r, zout, st, s);
-        return apply_tpr<double, double>(A, A.Fvalr64, A.Fval64, B.yl64, B.zl64, r, zout, st, s);
+    if (A.tpr_blocks > 0 && A.tpr_chunks && !A.gt_f && !partial) {
+        if (A.skip) {
+            if (A.prec == 32) return apply_tpr<float, float, true>(A, A.Fvalr32, A.Fval32, B.yl32, B.zl32, r, zout, st, s);
+            return apply_tpr<double, double, true>(A, A.Fvalr64, A.Fval64, B.yl64, B.zl64, r, zout, st, s);
+        }
+        if (A.prec == 32) return apply_tpr<float, float, false>(A, A.Fvalr32, A.Fval32, B.yl32, B.zl32, r, zout, st, s);
+        return apply_tpr<double, double, false>(A, A.Fvalr64, A.Fval64, B.yl64, B.zl64, r, zout, st, s);
     }
     switch (A.lanes_trsv) {
     case 4: return apply_s<4>(A, B, r, zout, partial, st, s);
@@ -1134,11 +1157,11 @@ int tpr_blocks_per_sm(int prec)
 {
     int a = 0, b = 0;
     if (prec == 32) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trsv_fwd_h<float, float>, TPR_THREADS, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trsv_bwd_h<float, float>, TPR_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trsv_fwd_h<float, float, false>, TPR_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trsv_bwd_h<float, float, false>, TPR_THREADS, 0);
     } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trsv_fwd_h<double, double>, TPR_THREADS, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trsv_bwd_h<double, double>, TPR_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trsv_fwd_h<double, double, false>, TPR_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trsv_bwd_h<double, double, false>, TPR_THREADS, 0);
     }
     return std::min(a, b);
 }

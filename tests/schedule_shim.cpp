@@ -59,3 +59,22 @@ extern "C" int64_t sched_row_chunks(const int64_t *off, int32_t count, int64_t r
     }
     return nch;
 }
+
+// Hybrid-solve table of `count` systems (off / lstart / lo as for
+// sched_batch_groups); writes 2 ints per entry, returns the entry count.
+extern "C" int64_t sched_hybrid_table(int32_t count, const int64_t *off, const int64_t *lstart, const int64_t *lo,
+                                      int64_t wide, int32_t *out, int64_t cap)
+{
+    std::vector<BatchSysLevels> sys;
+    for (int32_t s = 0; s < count; ++s) {
+        BatchSysLevels y;
+        y.sys = s;
+        y.off = off[s];
+        y.lstart.assign(lstart + lo[s], lstart + lo[s + 1]);
+        y.ptr = nullptr;
+        sys.push_back(y);
+    }
+    const std::vector<int32_t> t = hybrid_table(sys, wide);
+    if (out && (int64_t)t.size() <= cap) std::memcpy(out, t.data(), 4 * t.size());
+    return (int64_t)t.size() / 2;
+}

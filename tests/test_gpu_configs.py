@@ -1,7 +1,8 @@
 """Parity at the benchmark configurations' own sizes.
 
 * The power-law workload at R-MAT scale 20 (the largest scale the sequential
-  oracle factors in seconds): the GPU factor is bit-identical to the oracle's.
+  oracle factors in seconds): the GPU factor is bit-identical to the oracle's,
+  with either fill store.
 * The full 200-system SDDM batch factored in one parac_factor_many launch:
   the largest and the smallest system of each family are bit-identical to the
   oracle's factor of that system with its batch index.
@@ -31,11 +32,16 @@ def P():
 
 
 def test_rmat20_bit_identical(P):
+    """Both fill stores: the per-column slabs and the hashmap W of Sec. IV-C,
+    whose hub columns (hundreds of thousands of fill entries) must not block
+    the other columns' inserts."""
     A, perm, seed, _ = W.config("rmat-20")
-    G = P.parac_factor(A.n, A.colptr, A.rowind, A.val, perm, seed)
     ref = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)
-    assert same_factor(G.export(), ref)
-    G.free()
+    for store in (0, 1):
+        G = P.parac_factor(A.n, A.colptr, A.rowind, A.val, perm, seed, P.parac_opts_default(fill_store=store))
+        assert same_factor(G.export(), ref), store
+        assert G.stats()["fill_store"] == store
+        G.free()
 
 
 def test_sddm_batch_200_extremes_bit_identical(P):

@@ -38,6 +38,8 @@ def lib(tmp_path_factory):
     L.sched_batch_groups.restype = C.c_int64
     L.sched_batch_groups.argtypes = [C.c_int32, P64, P64, P64, P64, P64, C.c_int64, C.c_int, C.c_int, C.c_int,
                                      C.c_int, C.c_int, P32, C.c_int64, P32]
+    L.sched_hybrid_table.restype = C.c_int64
+    L.sched_hybrid_table.argtypes = [C.c_int32, P64, P64, P64, C.c_int64, P32, C.c_int64]
     L.sched_row_chunks.restype = C.c_int64
     L.sched_row_chunks.argtypes = [P64, C.c_int32, C.c_int64, P64, P32, P32, C.c_int64]
     return L
@@ -237,3 +239,56 @@ def test_row_chunks(lib, seed):
         assert np.all(sy[first[s]:first[s + 1]] == s)
         assert (first[s + 1] - first[s]) == -(-int(ns[s]) // rows)
     assert first[count] == nch
+
+
+HY_COUNT_MASK, HY_SYS_SHIFT = 63, 6
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_hybrid_table(lib, seed):
+    """The hybrid solves' table: every position in exactly one entry; entries
+    in level order with systems in order within a level; a run holds at most
+    32 consecutive positions of one (system, level) segment and is used only
+    where the level (all systems) is wider than `wide`, single rows elsewhere;
+    each entry carries its system; and every dependency of a row sits in an
+    earlier entry, so walking the table from its end (the backward solve)
+    meets every dependent before its dependencies."""
+    rng = np.random.default_rng(300 + seed)
+    count = int(rng.integers(1, 7))
+    systems, levels, deps = _batch_case(rng, count, with_ptr=False)
+    off = np.zeros(count + 1, np.int64)
+    lst, lo = [], [0]
+    for s_, (ns, ls, _) in enumerate(systems):
+        off[s_ + 1] = off[s_] + ns
+        lst.append(np.asarray(ls, np.int64)); lo.append(lo[-1] + len(ls))
+    n = int(off[-1])
+    if n == 0:
+        return
+    lst = np.concatenate(lst); lo = np.asarray(lo, np.int64)
+    wide = int(rng.integers(0, 12))
+    cap = 2 * (n + 8)
+    out = np.zeros(cap, np.int32)
+    ne = lib.sched_hybrid_table(count, _p(off, C.c_int64), _p(lst, C.c_int64), _p(lo, C.c_int64), wide,
+                                _p(out, C.c_int32), cap)
+    tab = out[:2 * ne].reshape(ne, 2)
+    sysof = np.zeros(n, np.int64); lvof = np.zeros(n, np.int64)
+    for s_, (ns, ls, _) in enumerate(systems):
+        sysof[off[s_]:off[s_ + 1]] = s_; lvof[off[s_]:off[s_ + 1]] = levels[s_]
+    width = np.bincount(lvof, minlength=lvof.max() + 1)
+    entry_of = -np.ones(n, np.int64)
+    keys = []
+    for e, (x, y) in enumerate(tab):
+        cnt, sy = y & HY_COUNT_MASK, y >> HY_SYS_SHIFT
+        span = range(x, x + cnt) if cnt > 0 else [x]
+        assert 1 <= len(span) <= 32
+        assert len({(sysof[k], lvof[k]) for k in span}) == 1 and sysof[x] == sy
+        assert (cnt > 0) == (width[lvof[x]] > wide)
+        for k in span:
+            assert entry_of[k] < 0
+            entry_of[k] = e
+        keys.append((lvof[x], sy))
+    assert np.all(entry_of >= 0) and keys == sorted(keys)
+    for s_, (ns, ls, _) in enumerate(systems):
+        for j in range(ns):
+            for d in deps[s_][j]:
+                assert entry_of[off[s_] + d] < entry_of[off[s_] + j]
