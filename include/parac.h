@@ -308,7 +308,10 @@ parac_status parac_autotune(int32_t count, const parac_system *systems, uint64_t
  * system's preconditioner applies are the same arithmetic as in its own
  * parac_pcg call; its dot products are reduced over row chunks of its own, so
  * iterates agree with separate calls up to rounding (iteration counts within
- * one).  Otherwise (mixed devices or precisions, or pcg_many = PARAC_OFF in
+ * one).  The batched solves use the hybrid layout of PARAC_SPTRSV_THREAD
+ * whenever no handle's factor has a row or column of more than 2048 entries
+ * (whatever the handles' sptrsv), else one row per warp.  Otherwise (mixed
+ * devices or precisions, or pcg_many = PARAC_OFF in
  * the options the first handle was made with) host worker threads run the
  * systems' parac_pcg calls concurrently, with results equal to separate
  * calls.

@@ -787,7 +787,7 @@ std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_ind
              "\"vertices_global_path\": %llu, \"vertices_register_path\": %llu, \"handoffs\": %llu, "
              "\"queue_spins\": %llu, \"regrows\": %d, \"max_lower_column\": %d, \"blocks\": %d, "
              "\"warps_per_block\": %d, \"precision\": %d, \"samples\": %d, \"fill_store\": %d, \"system\": %d, \"t_ingest_ms\": %.4f, "
-             "\"t_elim_ms\": %.4f, \"t_compact_ms\": %.4f, \"depth\": %d, \"cycles\": {\"wait\": %llu, "
+             "\"t_elim_ms\": %.4f, \"t_compact_ms\": %.4f, \"depth\": %d, \"max_row_F\": %d, \"cycles\": {\"wait\": %llu, "
              "\"gather\": %llu, \"sort_merge\": %llu, \"store_sort_scan\": %llu, \"sample_append\": %llu, "
              "\"release\": %llu, \"reg_weight_sort\": %llu, \"reg_scan\": %llu, \"coop_join\": %llu, "
              "\"coop_gather\": %llu, \"coop_row_sort\": %llu, \"coop_merge_store\": %llu, "
@@ -796,7 +796,7 @@ std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_ind
              (long long)h->n, (long long)h->nnzF, (long long)(h->nnzF + h->n), (long long)fo.nl,
              (long long)fo.nnz_low, fo.stats[3], fo.pool_used, fo.f_used, fo.scratch_used, fo.stats[0], fo.stats[1],
              fo.stats[2], fo.stats[5], fo.stats[6], fo.stats[4], fo.regrows, fo.max_lower_column, fo.blocks, fo.warps, h->prec, fo.samples, fo.fill_store, sys_index, fo.t_ingest, fo.t_elim,
-             fo.t_compact, h->depth, fo.stats[8], fo.stats[9], fo.stats[10], fo.stats[11], fo.stats[12],
+             fo.t_compact, h->depth, h->max_row, fo.stats[8], fo.stats[9], fo.stats[10], fo.stats[11], fo.stats[12],
              fo.stats[13], fo.stats[14], fo.stats[15], fo.stats[16], fo.stats[17], fo.stats[18], fo.stats[19],
              fo.stats[20], fo.stats[21], fo.stats[22], fo.stats[23]);
     return buf;
@@ -1679,9 +1679,11 @@ parac_status pcg_batch(int32_t count, const parac_factor_t *G, const double *con
         bw.push_back({i, off[(size_t)i], h->lstart, cp});
     }
     CK(cudaStreamSynchronize(st));
-    // the hybrid solves when no handle has a long row and the handles ask for
-    // them (THREAD or AUTO): the systems' levels interleaved in one table
-    bool hybrid = G[0]->sptrsv == PARAC_SPTRSV_THREAD || G[0]->sptrsv == PARAC_SPTRSV_AUTO;
+    // the hybrid solves, the systems' levels interleaved in one table, when no
+    // handle has a row of more than TPR_MAX_ROW entries (measured on the
+    // 200-system batch: 150 ms PCG against 272 ms with a warp per row; the
+    // handles' sptrsv choice, timed on single-system applies, does not apply)
+    bool hybrid = true;
     for (int32_t i = 0; i < count && hybrid; ++i) hybrid = G[i]->max_row <= TPR_MAX_ROW;
     if (hybrid) {
         const int64_t hb = G[0]->trsv_blocks > 0 ? G[0]->trsv_blocks : (int64_t)num_sms();
