@@ -674,6 +674,31 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
     out.t_compact = t_cp.stop();
 }
 
+std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_index);
+
+// Group tables of the one-row-per-warp solves for a factor with rows longer
+// than 4 x LONG_ROW_SINGLE entries (a host pass over the relabelled factor's
+// row and column pointers).
+void build_group_tables(parac_factor_s *h, cudaStream_t st)
+{
+    const int64_t n = h->n;
+    std::vector<int64_t> rp((size_t)n + 1), cp((size_t)n + 1);
+    CK(cudaMemcpyAsync(rp.data(), h->Srp.p, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(cp.data(), h->Scp.p, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const GroupTable gf = row_groups(rp, false, SOLVE_WARPS, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE),
+                     gb = row_groups(cp, true, SOLVE_WARPS, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
+    h->sgt_f = dalloc<int32_t>(gf.g.size(), st);
+    h->sgt_b = dalloc<int32_t>(gb.g.size(), st);
+    CK(cudaMemcpyAsync(h->sgt_f.p, gf.g.data(), 4 * gf.g.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->sgt_b.p, gb.g.data(), 4 * gb.g.size(), cudaMemcpyHostToDevice, st));
+    h->spart_f = dalloc<double>((size_t)std::max(gf.nslots, 1), st);
+    h->spart_b = dalloc<double>((size_t)std::max(gb.nslots, 1), st);
+    CK(cudaStreamSynchronize(st));
+    h->sng_f = gf.ngroups; h->sng_b = gb.ngroups;
+    h->snslot_f = gf.nslots; h->snslot_b = gb.nslots;
+}
+
 // Build the solve-side arrays of a handle from its label-space CSC(F): sort
 // the columns by dependency level, relabel F into that order (positions),
 // and build the CSR of the relabelled factor for the forward solve.
@@ -758,22 +783,172 @@ void finish_handle(parac_factor_s *h, int64_t n, int64_t nnzF, const Opts &O)
     // building the table (a host pass over the rows) at setup.
     CK(cudaStreamSynchronize(st));
     h->max_row = maxlen;
-    if (maxlen > 4 * LONG_ROW_SINGLE) {
-        std::vector<int64_t> rp((size_t)n + 1), cp((size_t)n + 1);
-        CK(cudaMemcpyAsync(rp.data(), h->Srp.p, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(cp.data(), h->Scp.p, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        const GroupTable gf = row_groups(rp, false, SOLVE_WARPS, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE),
-                         gb = row_groups(cp, true, SOLVE_WARPS, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE);
-        h->sgt_f = dalloc<int32_t>(gf.g.size(), st);
-        h->sgt_b = dalloc<int32_t>(gb.g.size(), st);
-        CK(cudaMemcpyAsync(h->sgt_f.p, gf.g.data(), 4 * gf.g.size(), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(h->sgt_b.p, gb.g.data(), 4 * gb.g.size(), cudaMemcpyHostToDevice, st));
-        h->spart_f = dalloc<double>((size_t)std::max(gf.nslots, 1), st);
-        h->spart_b = dalloc<double>((size_t)std::max(gb.nslots, 1), st);
-        CK(cudaStreamSynchronize(st));
-        h->sng_f = gf.ngroups; h->sng_b = gb.ngroups;
-        h->snslot_f = gf.nslots; h->snslot_b = gb.nslots;
+    if (maxlen > 4 * LONG_ROW_SINGLE) build_group_tables(h, st);
+}
+
+// The complete set of solve arrays of several systems at once (the batched
+// form): the same steps as finish_handle, run once over the concatenation of
+// the systems' factors (their labels are contiguous, so a stable sort by
+// (system, level, label) keeps every system in its own position range and the
+// CSC / CSR of the relabelled block-diagonal factor are the systems' own
+// arrays side by side), then split into the handles with one segmented copy
+// per array.  Three small device-to-host reads (entry offsets and depths,
+// level histograms, longest rows) replace the per-system synchronisations.
+void finish_batch(std::vector<std::unique_ptr<parac_factor_s>> &hs, FactorOut &fo, const std::vector<SysDesc> &sys,
+                  const std::vector<int64_t> &nnzL, const DBuf &cp, const DBuf &ri, const DBuf &va, const DBuf &ord,
+                  const Opts &O)
+{
+    cudaStream_t st = O.st;
+    const int32_t count = (int32_t)sys.size();
+    const int64_t N = sys.back().obase + sys.back().n;
+    const int64_t nnzF = fo.nnzF;
+    const size_t n1 = (size_t)std::max<int64_t>(N, 1), z1 = (size_t)std::max<int64_t>(nnzF, 1);
+    const int prec = O.o.g_precision;
+    // system of every label (= position: both keep the systems' ranges)
+    std::vector<int32_t> ob_h((size_t)count + 1);
+    std::vector<int64_t> ob64((size_t)count + 1);
+    for (int32_t s = 0; s < count; ++s) { ob_h[(size_t)s] = (int32_t)sys[(size_t)s].obase; ob64[(size_t)s] = sys[(size_t)s].obase; }
+    ob_h[(size_t)count] = (int32_t)N; ob64[(size_t)count] = N;
+    DBuf obase = dalloc<int32_t>((size_t)count + 1, st), ob64d = dalloc<int64_t>((size_t)count + 1, st);
+    CK(cudaMemcpyAsync(obase.p, ob_h.data(), 4 * ob_h.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ob64d.p, ob64.data(), 8 * ob64.size(), cudaMemcpyHostToDevice, st));
+    DBuf sysv = dalloc<int32_t>(n1, st);
+    if (N > 0) CK(launch_sys_of_label(count, obase.as<int32_t>(), (int32_t)N, sysv.as<int32_t>(), st));
+    // entry offset of every system (Fcp at its first column) and its depth
+    std::vector<const int64_t *> fptr((size_t)count + 1, fo.Fcp.as<int64_t>());
+    DBuf fptr_d = DBuf(sizeof(void *) * fptr.size(), st), f0d = dalloc<int64_t>((size_t)count + 1, st);
+    DBuf dmax = dalloc<int32_t>((size_t)count, st);
+    CK(cudaMemcpyAsync(fptr_d.p, fptr.data(), sizeof(void *) * fptr.size(), cudaMemcpyHostToDevice, st));
+    CK(launch_gather_ends((const int64_t *const *)fptr_d.p, ob64d.as<int64_t>(), count + 1, f0d.as<int64_t>(), st));
+    CK(cudaMemsetAsync(dmax.p, 0, 4 * (size_t)count, st));
+    CK(launch_seg_max(N, fo.Lev.as<int32_t>(), sysv.as<int32_t>(), dmax.as<int32_t>(), st));
+    std::vector<int64_t> f0((size_t)count + 1);
+    std::vector<int32_t> dm((size_t)count);
+    CK(cudaMemcpyAsync(f0.data(), f0d.p, 8 * f0.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(dm.data(), dmax.p, 4 * dm.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<int64_t> hoff((size_t)count + 1, 0);
+    int32_t maxdepth = 1;
+    for (int32_t s = 0; s < count; ++s) {
+        const int32_t depth = sys[(size_t)s].n > 0 ? dm[(size_t)s] + 1 : 0;
+        hoff[(size_t)s + 1] = hoff[(size_t)s] + depth;
+        maxdepth = std::max(maxdepth, depth);
+    }
+    // level histograms of every system -> level starts
+    DBuf hoffd = dalloc<int64_t>(hoff.size(), st), hist = dalloc<int32_t>((size_t)std::max<int64_t>(hoff.back(), 1), st);
+    CK(cudaMemcpyAsync(hoffd.p, hoff.data(), 8 * hoff.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(hist.p, 0, 4 * (size_t)std::max<int64_t>(hoff.back(), 1), st));
+    CK(launch_seg_hist(N, fo.Lev.as<int32_t>(), sysv.as<int32_t>(), hoffd.as<int64_t>(), hist.as<int32_t>(), st));
+    std::vector<int32_t> hh((size_t)std::max<int64_t>(hoff.back(), 1));
+    CK(cudaMemcpyAsync(hh.data(), hist.p, 4 * hh.size(), cudaMemcpyDeviceToHost, st));
+    // positions: stable sort by level, then by system
+    DBuf order = dalloc<int32_t>(n1, st), keys = dalloc<int32_t>(n1, st), rtmp(radix_tmp_bytes(N), st);
+    CK(cudaMemcpyAsync(keys.p, fo.Lev.p, 4 * (size_t)N, cudaMemcpyDeviceToDevice, st));
+    CK(launch_iota_i32(order.as<int32_t>(), N, 0, st));
+    auto bits_of = [](int64_t v) { int b = 0; while (b < 31 && (v >> b) != 0) ++b; return b; };
+    CK(stable_sort_pairs((int32_t)N, keys.as<int32_t>(), order.as<int32_t>(), bits_of(maxdepth - 1), rtmp.p, st));
+    CK(launch_gather_i32((int32_t)N, order.as<int32_t>(), sysv.as<int32_t>(), keys.as<int32_t>(), st));
+    CK(stable_sort_pairs((int32_t)N, keys.as<int32_t>(), order.as<int32_t>(), bits_of(count - 1), rtmp.p, st));
+    // relabelled CSC (backward) and CSR (forward) of the block-diagonal factor
+    DBuf posof = dalloc<int32_t>(n1, st), len = dalloc<int32_t>(n1, st);
+    CK(launch_inverse_perm((int32_t)N, order.as<int32_t>(), posof.as<int32_t>(), st));
+    CK(launch_relabel_lengths((int32_t)N, order.as<int32_t>(), fo.Fcp.as<int64_t>(), len.as<int32_t>(), st));
+    DBuf tmp(scan_tmp_bytes(N + 1), st);
+    DBuf Scp = dalloc<int64_t>((size_t)N + 1, st), Srow = dalloc<int32_t>(z1, st), Sval = dalloc<double>(z1, st);
+    CK(scan_i32_to_i64(len.as<int32_t>(), Scp.as<int64_t>(), N, tmp.p, st));
+    CK(launch_relabel_gather((int32_t)N, order.as<int32_t>(), posof.as<int32_t>(), fo.Fcp.as<int64_t>(),
+                             fo.Frow.as<int32_t>(), fo.Fval.as<double>(), Scp.as<int64_t>(), Srow.as<int32_t>(),
+                             Sval.as<double>(), st));
+    DBuf Srp = dalloc<int64_t>((size_t)N + 1, st), Scol = dalloc<int32_t>(z1, st), Svalr = dalloc<double>(z1, st);
+    DBuf cnt = dalloc<int32_t>(n1, st), rmax = dalloc<int32_t>((size_t)count, st);
+    CK(cudaMemsetAsync(cnt.p, 0, 4 * n1, st));
+    CK(launch_row_count(nnzF, Srow.as<int32_t>(), cnt.as<int32_t>(), st));
+    CK(scan_i32_to_i64(cnt.as<int32_t>(), Srp.as<int64_t>(), N, tmp.p, st));
+    CK(cudaMemsetAsync(rmax.p, 0, 4 * (size_t)count, st));
+    CK(launch_seg_max(N, cnt.as<int32_t>(), sysv.as<int32_t>(), rmax.as<int32_t>(), st));
+    CK(launch_seg_max(N, len.as<int32_t>(), sysv.as<int32_t>(), rmax.as<int32_t>(), st));
+    std::vector<int32_t> rm((size_t)count);
+    CK(cudaMemcpyAsync(rm.data(), rmax.p, 4 * rm.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemsetAsync(cnt.p, 0, 4 * n1, st));
+    CK(launch_transpose_scatter((int32_t)N, Scp.as<int64_t>(), Srow.as<int32_t>(), Sval.as<double>(), Srp.as<int64_t>(),
+                                cnt.as<int32_t>(), Scol.as<int32_t>(), Svalr.as<double>(), st));
+    CK(launch_sort_rows((int32_t)N, Srp.as<int64_t>(), Scol.as<int32_t>(), Svalr.as<double>(), st));
+    CK(launch_sort_long_rows((int32_t)N, Srp.as<int64_t>(), Scol.as<int32_t>(), Svalr.as<double>(), st));
+    DBuf Dpos = dalloc<double>(n1, st), Sdinv = dalloc<double>(n1, st), Sperm = dalloc<int32_t>(n1, st);
+    CK(launch_gather_f64((int32_t)N, order.as<int32_t>(), fo.D.as<double>(), Dpos.as<double>(), st));
+    CK(launch_dinv((int32_t)N, Dpos.as<double>(), Sdinv.as<double>(), st));
+    CK(launch_gather_i32((int32_t)N, order.as<int32_t>(), ord.as<int32_t>(), Sperm.as<int32_t>(), st));
+    DBuf Sval32, Svalr32;
+    if (prec == 32) {
+        Sval32 = dalloc<float>(z1, st); Svalr32 = dalloc<float>(z1, st);
+        CK(launch_to_f32(Sval.as<double>(), Sval32.as<float>(), nnzF, st));
+        CK(launch_to_f32(Svalr.as<double>(), Svalr32.as<float>(), nnzF, st));
+    }
+    CK(cudaStreamSynchronize(st));             // level histograms and longest rows on the host
+    // the handles and their slices
+    enum { A_FCP, A_FROW, A_FVAL, A_D, A_LEV, A_PERM, A_LP, A_LI, A_LV, A_SCP, A_SROW, A_SVAL, A_SRP, A_SCOL,
+           A_SVALR, A_SDINV, A_SPERM, A_SVAL32, A_SVALR32, A_KINDS };
+    std::vector<SplitSeg> seg((size_t)A_KINDS * count);
+    int64_t zoff = 0, maxn = 0, maxf = 0, maxl = 0;
+    for (int32_t s = 0; s < count; ++s) {
+        const int64_t n = sys[(size_t)s].n, ob = sys[(size_t)s].obase, fo0 = f0[(size_t)s], nf = f0[(size_t)s + 1] - fo0;
+        const int64_t nl = nnzL[(size_t)s];
+        maxn = std::max(maxn, n + 1); maxf = std::max(maxf, nf); maxl = std::max(maxl, nl);
+        std::unique_ptr<parac_factor_s> h(new parac_factor_s());
+        cudaGetDevice(&h->device);
+        h->n = n; h->prec = prec; h->spin_limit = O.o.spin_limit; h->sptrsv = O.o.sptrsv;
+        h->check_every = O.o.check_every; h->stream = st;
+        h->trsv_blocks = O.o.trsv_blocks; h->poll_ns = O.o.poll_ns; h->pcg_graph = O.o.pcg_graph;
+        h->pcg_many = O.o.pcg_many; h->pcg_workers = O.o.pcg_workers;
+        h->nnzF = nf; h->nnzL = nl;
+        const size_t m1 = (size_t)std::max<int64_t>(n, 1), f1 = (size_t)std::max<int64_t>(nf, 1), l1 = (size_t)std::max<int64_t>(nl, 1);
+        h->Fcp = dalloc<int64_t>((size_t)n + 1, st); h->Frow = dalloc<int32_t>(f1, st); h->Fval = dalloc<double>(f1, st);
+        h->D = dalloc<double>(m1, st); h->Lev = dalloc<int32_t>(m1, st); h->perm = dalloc<int32_t>(m1, st);
+        h->Lp = dalloc<int64_t>((size_t)n + 1, st); h->Li = dalloc<int32_t>(l1, st); h->Lv = dalloc<double>(l1, st);
+        h->Scp = dalloc<int64_t>((size_t)n + 1, st); h->Srow = dalloc<int32_t>(f1, st); h->Sval = dalloc<double>(f1, st);
+        h->Srp = dalloc<int64_t>((size_t)n + 1, st); h->Scol = dalloc<int32_t>(f1, st); h->Svalr = dalloc<double>(f1, st);
+        h->Sdinv = dalloc<double>(m1, st); h->Sperm = dalloc<int32_t>(m1, st);
+        if (prec == 32) { h->Sval32 = dalloc<float>(f1, st); h->Svalr32 = dalloc<float>(f1, st); }
+        h->status = dalloc<int32_t>(1, st);
+        auto at = [&](int k) -> SplitSeg & { return seg[(size_t)k * count + s]; };
+        at(A_FCP) = {h->Fcp.p, n + 1, ob, -fo0};       at(A_FROW) = {h->Frow.p, nf, fo0, -ob};
+        at(A_FVAL) = {h->Fval.p, nf, fo0, 0};         at(A_D) = {h->D.p, n, ob, 0};
+        at(A_LEV) = {h->Lev.p, n, ob, 0};             at(A_PERM) = {h->perm.p, n, ob, -ob};
+        at(A_LP) = {h->Lp.p, n + 1, ob, -zoff};        at(A_LI) = {h->Li.p, nl, zoff, -ob};
+        at(A_LV) = {h->Lv.p, nl, zoff, 0};            at(A_SCP) = {h->Scp.p, n + 1, ob, -fo0};
+        at(A_SROW) = {h->Srow.p, nf, fo0, -ob};       at(A_SVAL) = {h->Sval.p, nf, fo0, 0};
+        at(A_SRP) = {h->Srp.p, n + 1, ob, -fo0};       at(A_SCOL) = {h->Scol.p, nf, fo0, -ob};
+        at(A_SVALR) = {h->Svalr.p, nf, fo0, 0};       at(A_SDINV) = {h->Sdinv.p, n, ob, 0};
+        at(A_SPERM) = {h->Sperm.p, n, ob, -ob};
+        at(A_SVAL32) = {h->Sval32.p, prec == 32 ? nf : 0, fo0, 0};
+        at(A_SVALR32) = {h->Svalr32.p, prec == 32 ? nf : 0, fo0, 0};
+        zoff += nl;
+        // level starts of the system's positions, depth and longest row / column
+        const int32_t depth = (int32_t)(hoff[(size_t)s + 1] - hoff[(size_t)s]);
+        h->depth = depth;
+        h->lstart.assign((size_t)depth + 1, 0);
+        for (int32_t l = 0; l < depth; ++l) h->lstart[(size_t)l + 1] = h->lstart[(size_t)l] + hh[(size_t)(hoff[(size_t)s] + l)];
+        h->max_row = rm[(size_t)s];
+        hs[(size_t)s] = std::move(h);
+    }
+    DBuf segd(sizeof(SplitSeg) * seg.size(), st);
+    CK(cudaMemcpyAsync(segd.p, seg.data(), sizeof(SplitSeg) * seg.size(), cudaMemcpyHostToDevice, st));
+    const SplitSeg *sd = segd.as<SplitSeg>();
+    auto split = [&](int k, int64_t mx, int elem, bool fl, const void *src) {
+        CK(launch_split(sd + (size_t)k * count, count, mx, elem, fl, src, st));
+    };
+    split(A_FCP, maxn, 8, false, fo.Fcp.p); split(A_FROW, maxf, 4, false, fo.Frow.p); split(A_FVAL, maxf, 8, true, fo.Fval.p);
+    split(A_D, maxn, 8, true, fo.D.p); split(A_LEV, maxn, 4, false, fo.Lev.p); split(A_PERM, maxn, 4, false, ord.p);
+    split(A_LP, maxn, 8, false, cp.p); split(A_LI, maxl, 4, false, ri.p); split(A_LV, maxl, 8, true, va.p);
+    split(A_SCP, maxn, 8, false, Scp.p); split(A_SROW, maxf, 4, false, Srow.p); split(A_SVAL, maxf, 8, true, Sval.p);
+    split(A_SRP, maxn, 8, false, Srp.p); split(A_SCOL, maxf, 4, false, Scol.p); split(A_SVALR, maxf, 8, true, Svalr.p);
+    split(A_SDINV, maxn, 8, true, Sdinv.p); split(A_SPERM, maxn, 4, false, Sperm.p);
+    if (prec == 32) { split(A_SVAL32, maxf, 4, true, Sval32.p); split(A_SVALR32, maxf, 4, true, Svalr32.p); }
+    CK(cudaStreamSynchronize(st));             // every slice written before the global arrays are freed
+    for (int32_t s = 0; s < count; ++s) {
+        parac_factor_s *h = hs[(size_t)s].get();
+        if (h->max_row > 4 * LONG_ROW_SINGLE) build_group_tables(h, st);
+        h->stats = stats_json(h, fo, s);
     }
 }
 
@@ -959,21 +1134,37 @@ parac_status parac_factor_many(int32_t count, const parac_system *systems, uint6
         std::vector<SysDesc> sys(count);
         std::vector<int64_t> nnz(count);
         int64_t N = 0, NNZ = 0, NL = 0;
+        // entry counts: colptr[n] of every system, the device-resident ones read
+        // by one gather kernel and one copy
+        std::vector<const int64_t *> dptr;
+        std::vector<int64_t> didx;
+        std::vector<int32_t> dsys;
         for (int s = 0; s < count; ++s) {
             const parac_system &y = systems[s];
             if (y.n < 0 || (y.n > 0 && (!y.colptr || !y.rowind || !y.val))) { set_err("system %d: bad arrays", s); return PARAC_EINVAL; }
             if (!check_csc_host(y.n, y.colptr)) { set_err("system %d: bad colptr", s); return PARAC_EINVAL; }
-            int64_t z = 0;
+            nnz[s] = 0;
             if (y.n > 0) {
-                if (is_device_ptr(y.colptr)) {
-                    CK(cudaMemcpyAsync(&z, y.colptr + y.n, 8, cudaMemcpyDeviceToHost, st));
-                    CK(cudaStreamSynchronize(st));
-                } else z = y.colptr[y.n];
+                if (is_device_ptr(y.colptr)) { dptr.push_back(y.colptr); didx.push_back(y.n); dsys.push_back(s); }
+                else nnz[s] = y.colptr[y.n];
             }
-            nnz[s] = z;
+        }
+        if (!dptr.empty()) {
+            const int32_t m = (int32_t)dptr.size();
+            DBuf pd = DBuf(sizeof(void *) * (size_t)m, st), id = dalloc<int64_t>((size_t)m, st), od = dalloc<int64_t>((size_t)m, st);
+            CK(cudaMemcpyAsync(pd.p, dptr.data(), sizeof(void *) * (size_t)m, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(id.p, didx.data(), 8 * (size_t)m, cudaMemcpyHostToDevice, st));
+            CK(launch_gather_ends((const int64_t *const *)pd.p, id.as<int64_t>(), m, od.as<int64_t>(), st));
+            std::vector<int64_t> ends((size_t)m);
+            CK(cudaMemcpyAsync(ends.data(), od.p, 8 * (size_t)m, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            for (int32_t i = 0; i < m; ++i) nnz[(size_t)dsys[(size_t)i]] = ends[(size_t)i];
+        }
+        for (int s = 0; s < count; ++s) {
+            const parac_system &y = systems[s];
             sys[s].n = y.n; sys[s].obase = N; sys[s].lbase = NL;
             sys[s].ground = O.o.kind == PARAC_KIND_LAPLACIAN ? -1 : (int32_t)(NL + y.n);
-            N += y.n; NNZ += z; NL += y.n + (sys[s].ground >= 0 ? 1 : 0);
+            N += y.n; NNZ += nnz[s]; NL += y.n + (sys[s].ground >= 0 ? 1 : 0);
         }
         if (NL >= 0x7fffffffLL) { set_err("batch too large for 32-bit labels"); return PARAC_EINVAL; }
         if (O.o.order == PARAC_ORDER_NNZ)
@@ -982,32 +1173,43 @@ parac_status parac_factor_many(int32_t count, const parac_system *systems, uint6
                     set_err("system %d: an ordering array and order = PARAC_ORDER_NNZ exclude each other", s);
                     return PARAC_EINVAL;
                 }
-        // concatenated device input with global indices
+        // concatenated device input with global indices: one segmented copy per
+        // array (host inputs are staged to the device first; a system without
+        // an ordering takes the shared 0, 1, 2, ... array)
         DBuf cp = dalloc<int64_t>(N + 1, st), ri = dalloc<int32_t>(std::max<int64_t>(NNZ, 1), st),
              va = dalloc<double>(std::max<int64_t>(NNZ, 1), st), ord = dalloc<int32_t>(std::max<int64_t>(N, 1), st),
              lab = dalloc<int32_t>(std::max<int64_t>(N, 1), st);
+        int64_t maxn = 1, maxz = 1;
+        for (int s = 0; s < count; ++s) { maxn = std::max(maxn, sys[s].n); maxz = std::max(maxz, nnz[s]); }
+        DBuf iota = dalloc<int32_t>((size_t)maxn, st);
+        CK(launch_iota_i32(iota.as<int32_t>(), maxn, 0, st));
+        enum { K_CP, K_RI, K_VA, K_ORD, K_LAB, K_KINDS };
+        std::vector<CatSeg> cs((size_t)K_KINDS * count);
+        std::vector<DView<int64_t>> vc(count);
+        std::vector<DView<int32_t>> vr(count), vo(count);
+        std::vector<DView<double>> vv(count);
         int64_t zb = 0;
         for (int s = 0; s < count; ++s) {
             const parac_system &y = systems[s];
-            const int64_t n = y.n;
-            if (n == 0) continue;
-            DView<int64_t> c; c.set(y.colptr, (size_t)n + 1, st);
-            DView<int32_t> r; r.set(y.rowind, (size_t)nnz[s], st);
-            DView<double> v; v.set(y.val, (size_t)nnz[s], st);
-            CK(launch_add_offset_i64(c.p, cp.as<int64_t>() + sys[s].obase, n, zb, st));
-            CK(launch_add_offset_i32(r.p, ri.as<int32_t>() + zb, nnz[s], (int32_t)sys[s].obase, st));
-            copy_out(va.as<double>() + zb, v.p, 8 * (size_t)nnz[s], st);
-            // (host inputs were staged by their copies before those returned, and
-            // the staging buffers are freed in stream order: no sync per system)
-            if (y.ordering) {
-                DView<int32_t> o; o.set(y.ordering, (size_t)n, st);
-                CK(launch_add_offset_i32(o.p, ord.as<int32_t>() + sys[s].obase, n, (int32_t)sys[s].obase, st));
-            } else {
-                CK(launch_iota_i32(ord.as<int32_t>() + sys[s].obase, n, (int32_t)sys[s].obase, st));
-            }
-            CK(launch_iota_i32(lab.as<int32_t>() + sys[s].obase, n, (int32_t)sys[s].lbase, st));
+            const int64_t n = y.n, ob = sys[s].obase;
+            vc[s].set(y.colptr, (size_t)n + 1, st); vr[s].set(y.rowind, (size_t)nnz[s], st);
+            vv[s].set(y.val, (size_t)nnz[s], st); vo[s].set(y.ordering, (size_t)n, st);
+            auto at = [&](int k) -> CatSeg & { return cs[(size_t)k * count + s]; };
+            at(K_CP) = {vc[s].p, n, ob, zb};
+            at(K_RI) = {vr[s].p, nnz[s], zb, ob};
+            at(K_VA) = {vv[s].p, nnz[s], zb, 0};
+            at(K_ORD) = {vo[s].p ? (const void *)vo[s].p : (const void *)iota.p, n, ob, ob};
+            at(K_LAB) = {iota.p, n, ob, sys[s].lbase};
             zb += nnz[s];
         }
+        DBuf csd(sizeof(CatSeg) * cs.size(), st);
+        CK(cudaMemcpyAsync(csd.p, cs.data(), sizeof(CatSeg) * cs.size(), cudaMemcpyHostToDevice, st));
+        const CatSeg *cd = csd.as<CatSeg>();
+        CK(launch_cat(cd + (size_t)K_CP * count, count, maxn, 8, false, cp.p, st));
+        CK(launch_cat(cd + (size_t)K_RI * count, count, maxz, 4, false, ri.p, st));
+        CK(launch_cat(cd + (size_t)K_VA * count, count, maxz, 8, true, va.p, st));
+        CK(launch_cat(cd + (size_t)K_ORD * count, count, maxn, 4, false, ord.p, st));
+        CK(launch_cat(cd + (size_t)K_LAB * count, count, maxn, 4, false, lab.p, st));
         const int64_t total = zb;
         CK(cudaMemcpyAsync(cp.as<int64_t>() + N, &total, 8, cudaMemcpyHostToDevice, st));
         if (O.o.order == PARAC_ORDER_NNZ && N > 0) {     // every system's NNZ-sorted ordering at once
@@ -1024,44 +1226,8 @@ parac_status parac_factor_many(int32_t count, const parac_system *systems, uint6
         FactorOut fo;
         run_factor(N, cp.as<int64_t>(), ri.as<int32_t>(), va.as<double>(), ord.as<int32_t>(), lab.as<int32_t>(), sys,
                    O.o.kind, seed, O, fo);
-        std::vector<int64_t> fcp_h(N + 1);
-        CK(cudaMemcpyAsync(fcp_h.data(), fo.Fcp.p, 8 * (N + 1), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
         std::vector<std::unique_ptr<parac_factor_s>> hs(count);
-        int64_t zoff = 0;
-        for (int s = 0; s < count; ++s) {
-            const int64_t n = sys[s].n, ob = sys[s].obase;
-            std::unique_ptr<parac_factor_s> h(new parac_factor_s());
-            cudaGetDevice(&h->device);
-            h->n = n; h->prec = O.o.g_precision; h->spin_limit = O.o.spin_limit; h->sptrsv = O.o.sptrsv;
-            h->check_every = O.o.check_every; h->stream = st;
-            h->trsv_blocks = O.o.trsv_blocks; h->poll_ns = O.o.poll_ns; h->pcg_graph = O.o.pcg_graph;
-            h->pcg_many = O.o.pcg_many; h->pcg_workers = O.o.pcg_workers;
-            const int64_t f0 = fcp_h[ob], f1 = fcp_h[ob + n];
-            h->nnzF = f1 - f0;
-            h->Fcp = dalloc<int64_t>(n + 1, st);
-            CK(launch_add_offset_i64(fo.Fcp.as<int64_t>() + ob, h->Fcp.as<int64_t>(), n + 1, -f0, st));
-            h->Frow = dalloc<int32_t>(std::max<int64_t>(h->nnzF, 1), st);
-            CK(launch_add_offset_i32(fo.Frow.as<int32_t>() + f0, h->Frow.as<int32_t>(), h->nnzF, -(int32_t)ob, st));
-            h->Fval = dalloc<double>(std::max<int64_t>(h->nnzF, 1), st);
-            copy_out(h->Fval.p, fo.Fval.as<double>() + f0, 8 * (size_t)h->nnzF, st);
-            h->D = dalloc<double>(std::max<int64_t>(n, 1), st);
-            copy_out(h->D.p, fo.D.as<double>() + ob, 8 * (size_t)n, st);
-            h->Lev = dalloc<int32_t>(std::max<int64_t>(n, 1), st);
-            copy_out(h->Lev.p, fo.Lev.as<int32_t>() + ob, 4 * (size_t)n, st);
-            h->perm = dalloc<int32_t>(std::max<int64_t>(n, 1), st);
-            CK(launch_add_offset_i32(ord.as<int32_t>() + ob, h->perm.as<int32_t>(), n, -(int32_t)ob, st));
-            h->nnzL = nnz[s];
-            h->Lp = dalloc<int64_t>(n + 1, st); h->Li = dalloc<int32_t>(std::max<int64_t>(nnz[s], 1), st);
-            h->Lv = dalloc<double>(std::max<int64_t>(nnz[s], 1), st);
-            CK(launch_add_offset_i64(cp.as<int64_t>() + ob, h->Lp.as<int64_t>(), n + 1, -zoff, st));
-            CK(launch_add_offset_i32(ri.as<int32_t>() + zoff, h->Li.as<int32_t>(), nnz[s], -(int32_t)ob, st));
-            copy_out(h->Lv.p, va.as<double>() + zoff, 8 * (size_t)nnz[s], st);
-            zoff += nnz[s];
-            finish_handle(h.get(), n, h->nnzF, O);
-            h->stats = stats_json(h.get(), fo, s);
-            hs[s] = std::move(h);
-        }
+        finish_batch(hs, fo, sys, nnz, cp, ri, va, ord, O);
         CK(cudaStreamSynchronize(st));
         for (int s = 0; s < count; ++s) out[s] = hs[s].release();
         return PARAC_OK;

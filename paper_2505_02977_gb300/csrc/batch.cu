@@ -302,7 +302,80 @@ __global__ void k_cat(const CatSeg *seg, int32_t nseg, T *dst)
     }
 }
 
+// dst_k[i] = src[q.src + i] + q.add for every segment k (the inverse of k_cat)
+template <typename T>
+__global__ void k_split(const SplitSeg *seg, int32_t nseg, const T *src)
+{
+    for (int32_t k = blockIdx.y; k < nseg; k += gridDim.y) {
+        const SplitSeg q = seg[k];
+        T *dst = (T *)q.dst;
+        const T add = (T)q.add;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < q.count; i += (int64_t)gridDim.x * blockDim.x)
+            dst[i] = src[q.src + i] + add;
+    }
+}
+
+__global__ void k_gather_ends(const int64_t *const *ptr, const int64_t *idx, int32_t m, int64_t *out)
+{
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) out[i] = ptr[i][idx[i]];
+}
+
+__global__ void k_seg_max(int64_t n, const int32_t *val, const int32_t *seg_of, int32_t *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicMax(out + seg_of[i], val[i]);
+}
+
+__global__ void k_seg_hist(int64_t n, const int32_t *val, const int32_t *seg_of, const int64_t *seg_off, int32_t *hist)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(hist + seg_off[seg_of[i]] + val[i], 1);
+}
+
+inline int grid1(int64_t n)
+{
+    int64_t b = (n + BT - 1) / BT;
+    return (int)(b < 1 ? 1 : b > 4096 ? 4096 : b);
+}
+
 }  // namespace
+
+cudaError_t launch_split(const SplitSeg *seg, int32_t nseg, int64_t max_count, int elem, bool is_float,
+                         const void *src, cudaStream_t s)
+{
+    if (nseg <= 0) return cudaSuccess;
+    int64_t bx = (max_count + BT - 1) / BT;
+    bx = bx < 1 ? 1 : bx > 64 ? 64 : bx;
+    const dim3 grid((unsigned)bx, (unsigned)(nseg < 65535 ? nseg : 65535));
+    if (elem == 8 && is_float) k_split<double><<<grid, BT, 0, s>>>(seg, nseg, (const double *)src);
+    else if (elem == 8) k_split<int64_t><<<grid, BT, 0, s>>>(seg, nseg, (const int64_t *)src);
+    else if (is_float) k_split<float><<<grid, BT, 0, s>>>(seg, nseg, (const float *)src);
+    else k_split<int32_t><<<grid, BT, 0, s>>>(seg, nseg, (const int32_t *)src);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_ends(const int64_t *const *ptr, const int64_t *idx, int32_t m, int64_t *out, cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    k_gather_ends<<<grid1(m), BT, 0, s>>>(ptr, idx, m, out); count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_max(int64_t n, const int32_t *val, const int32_t *seg_of, int32_t *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_seg_max<<<grid1(n), BT, 0, s>>>(n, val, seg_of, out); count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_hist(int64_t n, const int32_t *val, const int32_t *seg_of, const int64_t *seg_off,
+                            int32_t *hist, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_seg_hist<<<grid1(n), BT, 0, s>>>(n, val, seg_of, seg_off, hist); count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_cat(const CatSeg *seg, int32_t nseg, int64_t max_count, int elem, bool is_float, void *dst,
                        cudaStream_t s)

@@ -258,6 +258,17 @@ cudaError_t spcg_reopen(const SolveArgs &A, const BatchBuffers &B, cudaStream_t 
 struct CatSeg { const void *src; int64_t count, dst, add; };
 cudaError_t launch_cat(const CatSeg *seg, int32_t nseg, int64_t max_count, int elem, bool is_float, void *dst,
                        cudaStream_t st);
+// the inverse: dst_k[i] = src[seg_k.src + i] + seg_k.add, i < seg_k.count (seg[] in device memory)
+struct SplitSeg { void *dst; int64_t count, src, add; };
+cudaError_t launch_split(const SplitSeg *seg, int32_t nseg, int64_t max_count, int elem, bool is_float,
+                         const void *src, cudaStream_t st);
+// out[i] = ptr[i][idx[i]] for i < m (ptr, idx, out in device memory)
+cudaError_t launch_gather_ends(const int64_t *const *ptr, const int64_t *idx, int32_t m, int64_t *out,
+                               cudaStream_t st);
+// out[seg_of[i]] = max(out[..], val[i]); hist[seg_off[seg_of[i]] + val[i]] += 1
+cudaError_t launch_seg_max(int64_t n, const int32_t *val, const int32_t *seg_of, int32_t *out, cudaStream_t st);
+cudaError_t launch_seg_hist(int64_t n, const int32_t *val, const int32_t *seg_of, const int64_t *seg_off,
+                            int32_t *hist, cudaStream_t st);
 // Allocation-free variant: work vectors in a fixed device array (n <= NOALLOC_MAX_N).
 constexpr int NOALLOC_MAX_N = 1 << 18;
 constexpr int NOALLOC_MAX_DEVICES = 64;
