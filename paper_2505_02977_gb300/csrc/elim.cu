@@ -927,11 +927,12 @@ __device__ void coop_sort(View v, int P, View tile, int T)
 
 // ---------------------------------------------------------------- sample sort
 // Sorting a working set that lives in global memory (more entries than the
-// CTA's shared buffer): a sorted sample of cap entries in shared memory gives
-// B-1 splitters, every entry is counted into its bucket and scattered to the
-// temporary arrays (weights in v.S, row | mult << 32 in v.M), and each bucket
-// is sorted in shared memory -- by one warp when it fits the warp's slice of
-// the buffer, else by the whole CTA.  Bucket boundaries are a deterministic
+// CTA's shared buffer): a sorted sample in shared memory (8 entries per
+// bucket, 256 to cap entries) gives B-1 splitters, every entry is counted into
+// its bucket and scattered to the temporary arrays (weights in v.S, row |
+// mult << 32 in v.M), and each bucket is sorted -- by one warp when it fits
+// the warp's slice of the buffer (in registers up to 256 entries), else by the
+// whole CTA.  Bucket boundaries are a deterministic
 // function of the keys and every bucket is fully sorted, so the result is the
 // sorted sequence itself, as from any other exact sort.  The bucket offsets
 // and merged counts live in global scratch (gbo[B+1], gbd[B]).
@@ -991,7 +992,15 @@ template <int KEY>
 __device__ int sample_partition(View v, int n, View tile, int cap, int wcap, CoopShared &cs, int *gbo, int *gbig)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int SS = cap, lg = __ffs(SS) - 1;              // cap: a power of two
+    // B a power of two, buckets half a warp's slice on average; 8 samples per
+    // bucket (at least 256, at most cap: a power of two), so at least 4
+    int B = next_pow2((2 * n + wcap - 1) / wcap);
+    if (B > cap / 4) B = cap / 4;
+    if (B < 1) B = 1;
+    int SS = 8 * B;
+    if (SS < 256) SS = 256;
+    if (SS > cap) SS = cap;
+    const int lg = __ffs(SS) - 1;
     for (int s2 = tid; s2 < SS; s2 += nt) {
         const int i = (int)(((long long)s2 * n) >> lg);
         tile.row[s2] = v.row[i];
@@ -1000,19 +1009,23 @@ __device__ int sample_partition(View v, int n, View tile, int cap, int wcap, Coo
     }
     __syncthreads();
     coop_sort<KEY>(tile, SS, tile, 0);
-    // B a power of two, at least 4 samples per bucket, buckets half a warp's slice on average
-    int B = next_pow2((2 * n + wcap - 1) / wcap);
-    if (B > SS / 4) B = SS / 4;
-    if (B < 1) B = 1;
     const int stride = SS / B;
     int *cnt = (int *)tile.S, *cur = (int *)tile.S + cap, *off = (int *)tile.M;
     for (int b = tid; b < B; b += nt) { cnt[b] = 0; cur[b] = 0; }
     if (tid == 0) cs.nbig = 0;
     __syncthreads();
-    for (int i = tid; i < n; i += nt) {
-        const int32_t r = v.row[i];
-        const unsigned long long wb = KEY == 1 ? dbits(v.w[i]) : 0ull;
-        atomicAdd(cnt + bucket_of<KEY>(tile, stride, B, r, wb), 1);
+    for (int i0 = tid; i0 < n; i0 += 4 * nt) {
+        int32_t r[4];
+        unsigned long long wb[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + q * nt;
+            r[q] = i < n ? v.row[i] : 0;
+            wb[q] = KEY == 1 && i < n ? dbits(v.w[i]) : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (i0 + q * nt < n) atomicAdd(cnt + bucket_of<KEY>(tile, stride, B, r[q], wb[q]), 1);
     }
     __syncthreads();
     for (int b = tid; b < B; b += nt)
@@ -1021,14 +1034,24 @@ __device__ int sample_partition(View v, int n, View tile, int cap, int wcap, Coo
     if (tid == 0) off[B] = n;
     __syncthreads();
     unsigned long long *tM = (unsigned long long *)v.M;
-    for (int i = tid; i < n; i += nt) {
-        const int32_t r = v.row[i];
-        const double w = v.w[i];
-        const int32_t m = KEY == 1 ? v.mult[i] : 0;
-        const int b = bucket_of<KEY>(tile, stride, B, r, KEY == 1 ? dbits(w) : 0ull);
-        const int pos = off[b] + atomicAdd(cur + b, 1);
-        v.S[pos] = w;
-        tM[pos] = (unsigned long long)(uint32_t)r | ((unsigned long long)(uint32_t)m << 32);
+    for (int i0 = tid; i0 < n; i0 += 4 * nt) {
+        int32_t r[4], m[4];
+        double w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + q * nt;
+            r[q] = i < n ? v.row[i] : 0;
+            w[q] = i < n ? v.w[i] : 0.0;
+            m[q] = KEY == 1 && i < n ? v.mult[i] : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (i0 + q * nt >= n) continue;
+            const int b = bucket_of<KEY>(tile, stride, B, r[q], KEY == 1 ? dbits(w[q]) : 0ull);
+            const int pos = off[b] + atomicAdd(cur + b, 1);
+            v.S[pos] = w[q];
+            tM[pos] = (unsigned long long)(uint32_t)r[q] | ((unsigned long long)(uint32_t)m[q] << 32);
+        }
     }
     for (int b = tid; b <= B; b += nt) gbo[b] = off[b];
     __syncthreads();
@@ -1063,6 +1086,108 @@ __device__ View sort_big_bucket(View v, View tile, int cap, int o, int cb)
     coop_sort<KEY>(w, Pb, tile, Pb <= cap ? 0 : cap);
     return w;
 }
+
+// Buckets of up to 256 entries are sorted by one warp in registers: lane l
+// holds positions lE .. lE + E - 1 of the list padded to 32E entries (a power
+// of two); the bitonic stages with stride j < E compare two slots of one
+// lane, the others pair lane l with lane l ^ (j / E) through shuffles.  It is
+// the network of the shared-memory sorts, so the sorted list is the same.
+template <int KEY>
+__device__ __forceinline__ bool key_gt(int32_t ra, unsigned long long ba, int32_t rb, unsigned long long bb)
+{
+    return KEY == 0 ? (ra > rb || (ra == rb && ba > bb)) : (ba > bb || (ba == bb && ra > rb));
+}
+
+template <int KEY, int E>
+__device__ __forceinline__ void reg_bucket_net(int32_t (&r)[E], unsigned long long (&b)[E], int32_t (&m)[E])
+{
+    const int lane = (int)lane_id();
+#pragma unroll
+    for (int kk = 2; kk <= 32 * E; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            if (j >= E) {
+                const int lj = j / E;
+                const bool lower = (lane & lj) == 0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const bool asc = ((lane * E + e) & kk) == 0;
+                    const int32_t ro = __shfl_xor_sync(FULL, r[e], lj);
+                    const unsigned long long bo = __shfl_xor_sync(FULL, b[e], lj);
+                    const int32_t mo = KEY == 1 ? __shfl_xor_sync(FULL, m[e], lj) : 0;
+                    const bool take = lower == asc ? key_gt<KEY>(r[e], b[e], ro, bo) : key_gt<KEY>(ro, bo, r[e], b[e]);
+                    if (take) { r[e] = ro; b[e] = bo; if (KEY == 1) m[e] = mo; }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if (e & j) continue;
+                    const bool asc = ((lane * E + e) & kk) == 0;
+                    if (key_gt<KEY>(r[e], b[e], r[e + j], b[e + j]) == asc) {
+                        const int32_t rt = r[e]; r[e] = r[e + j]; r[e + j] = rt;
+                        const unsigned long long bt = b[e]; b[e] = b[e + j]; b[e + j] = bt;
+                        if (KEY == 1) { const int32_t mt = m[e]; m[e] = m[e + j]; m[e + j] = mt; }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Load bucket [o, o + cb) of the temporaries (weights tS, row | mult << 32 in
+// tM) into the lanes' slots, sentinels past cb.
+template <int KEY, int E>
+__device__ __forceinline__ void reg_bucket_load(const double *tS, const unsigned long long *tM, int o, int cb,
+                                                int32_t (&r)[E], unsigned long long (&b)[E], int32_t (&m)[E])
+{
+    const int lane = (int)lane_id();
+    unsigned long long rm[E], wb[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane * E + e;
+        rm[e] = i < cb ? tM[o + i] : (unsigned long long)(uint32_t)ROW_SENTINEL;
+        wb[e] = i < cb ? dbits(tS[o + i]) : (KEY == 0 ? 0ull : WBITS_SENTINEL);
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) { r[e] = (int32_t)(uint32_t)rm[e]; m[e] = (int32_t)(rm[e] >> 32); b[e] = wb[e]; }
+}
+
+// Row phase: sort the bucket by (row, weight bits) and leave it at [0, cb) of
+// the warp's shared slice for the run merge.
+template <int E>
+__device__ __noinline__ void reg_bucket_rows(const double *tS, const unsigned long long *tM, int o, int cb, View sv)
+{
+    int32_t r[E], m[E];
+    unsigned long long b[E];
+    reg_bucket_load<0, E>(tS, tM, o, cb, r, b, m);
+    reg_bucket_net<0, E>(r, b, m);
+    const int lane = (int)lane_id();
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane * E + e;
+        if (i < cb) { sv.row[i] = r[e]; sv.w[i] = __longlong_as_double((long long)b[e]); }
+    }
+    __syncwarp();
+}
+
+// Weight phase: sort the bucket by (weight bits, row) and store it at
+// [o, o + cb) of v.
+template <int E>
+__device__ __noinline__ void reg_bucket_weights(const double *tS, const unsigned long long *tM, int o, int cb, View v)
+{
+    int32_t r[E], m[E];
+    unsigned long long b[E];
+    reg_bucket_load<1, E>(tS, tM, o, cb, r, b, m);
+    reg_bucket_net<1, E>(r, b, m);
+    const int lane = (int)lane_id();
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane * E + e;
+        if (i < cb) { v.row[o + i] = r[e]; v.w[o + i] = __longlong_as_double((long long)b[e]); v.mult[o + i] = m[e]; }
+    }
+}
+
+constexpr int REG_BUCKET_MAX = 256;
 
 // Merge the sorted runs of a bucket held in a shared view (rows, weights in
 // [0, cb)), writing (sum, row | len << 32) to [o, o + d_b) of the temporaries
@@ -1128,12 +1253,19 @@ __device__ int coop_row_phase(const ElimArgs &a, CoopShared &cs, View v, int g, 
         int db = 0;
         if (cb > 0) {
             const int Pb = next_pow2(cb);
-            for (int i = lane; i < Pb; i += 32) {
-                if (i < cb) { sv.row[i] = (int32_t)(uint32_t)tM[o + i]; sv.w[i] = tS[o + i]; }
-                else { sv.row[i] = ROW_SENTINEL; sv.w[i] = 0.0; }
+            if (Pb <= REG_BUCKET_MAX) {
+                if (Pb <= 32) reg_bucket_rows<1>(tS, tM, o, cb, sv);
+                else if (Pb == 64) reg_bucket_rows<2>(tS, tM, o, cb, sv);
+                else if (Pb == 128) reg_bucket_rows<4>(tS, tM, o, cb, sv);
+                else reg_bucket_rows<8>(tS, tM, o, cb, sv);
+            } else {
+                for (int i = lane; i < Pb; i += 32) {
+                    if (i < cb) { sv.row[i] = (int32_t)(uint32_t)tM[o + i]; sv.w[i] = tS[o + i]; }
+                    else { sv.row[i] = ROW_SENTINEL; sv.w[i] = 0.0; }
+                }
+                __syncwarp();
+                sort_row_bits(sv, Pb);
             }
-            __syncwarp();
-            sort_row_bits(sv, Pb);
             db = warp_merge_bucket(sv, cb, tS, tM, o);
             __syncwarp();
         }
@@ -1214,6 +1346,13 @@ __device__ void coop_weight_phase(View v, int d, unsigned char *bbuf, int cap, C
             continue;
         }
         const int Pb = next_pow2(cb);
+        if (Pb <= REG_BUCKET_MAX) {
+            if (Pb <= 32) reg_bucket_weights<1>(tS, tM, o, cb, v);
+            else if (Pb == 64) reg_bucket_weights<2>(tS, tM, o, cb, v);
+            else if (Pb == 128) reg_bucket_weights<4>(tS, tM, o, cb, v);
+            else reg_bucket_weights<8>(tS, tM, o, cb, v);
+            continue;
+        }
         for (int i = lane; i < Pb; i += 32) {
             if (i < cb) {
                 const unsigned long long rm = tM[o + i];
