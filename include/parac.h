@@ -149,6 +149,16 @@ enum { PARAC_ORDER_GIVEN = 0, PARAC_ORDER_NNZ = 1 };
  *                   31 bits of the (v+1)-th output of a splitmix64 generator
  *                   started from `seed` (v = the vertex's index in its
  *                   system), then by v; each system of a batch separately.
+ *   grid_help       a vertex whose working set lives in global scratch (more
+ *                   gathered entries than the CTA buffer) is offered to the
+ *                   grid's idle warps, which take chunks of its gather,
+ *                   sorts, scan, sampling and counter releases while its CTA
+ *                   runs the serial steps; one such vertex at a time.
+ *                   Default: on for hub-dominated inputs (longest lower
+ *                   column above 16x the average); PARAC_ON / PARAC_OFF
+ *                   force it.  The factor is the same either way.
+ *   grid_help_min   gathered entries from which a vertex is offered (0: every
+ *                   working set in global scratch)
  */
 typedef struct {
     int32_t kind;
@@ -177,6 +187,8 @@ typedef struct {
     int32_t pcg_many;
     int32_t pcg_workers;
     int32_t order;
+    int32_t grid_help;
+    int32_t grid_help_min;
 } parac_opts;
 
 void parac_opts_default(parac_opts *opts);

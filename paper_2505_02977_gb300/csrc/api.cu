@@ -314,6 +314,7 @@ Opts read_opts(const parac_opts *in)
     if (r.o.fill_store != 1) r.o.fill_store = 0;
     if (r.o.order != PARAC_ORDER_NNZ) r.o.order = PARAC_ORDER_GIVEN;
     if (r.o.idle_ns < 0) r.o.idle_ns = 0;
+    if (r.o.grid_help_min < 0) r.o.grid_help_min = 0;
     if (r.o.trsv_blocks < 0) r.o.trsv_blocks = 0;
     r.o.poll_ns = r.o.poll_ns <= 0 ? 64 : std::max(16, std::min(100000, r.o.poll_ns));
     r.o.pcg_workers = r.o.pcg_workers <= 0 ? 4 : std::min(64, r.o.pcg_workers);
@@ -333,7 +334,7 @@ struct FactorOut {
     DBuf Fcp, Frow, Fval, D, Lev;
     int64_t nnzF = 0;
     int64_t nl = 0, nnz_low = 0;
-    unsigned long long stats[32] = {0};
+    unsigned long long stats[160] = {0};
     unsigned long long pool_used = 0, f_used = 0, scratch_used = 0;
     int32_t max_lower_column = 0;
     int32_t samples = 1, fill_store = 0;
@@ -491,7 +492,11 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
          in_w = dalloc<double>((size_t)nl * FILL_C0, st), dir = dalloc<uint32_t>((size_t)nl * FILL_LEVELS, st);
     DBuf f_start = dalloc<int64_t>(nl, st), f_len = dalloc<int32_t>(nl, st), Dl = dalloc<double>(nl, st);
     DBuf lvl = dalloc<int32_t>(nl, st);
-    DBuf tops = dalloc<unsigned long long>(3, st), status = dalloc<int32_t>(1, st), stats = dalloc<unsigned long long>(32, st);
+    DBuf tops = dalloc<unsigned long long>(3, st), status = dalloc<int32_t>(1, st), stats = dalloc<unsigned long long>(160, st);
+    // grid-help board: word, hints and done counters one 128-byte line each, lock, task ring
+    constexpr size_t GH_WORD = 0, GH_HINT = 128, GH_DONE = GH_HINT + 128 * GH_HINTS, GH_LOCK = GH_DONE + 128 * GH_RING,
+                     GH_TASK = GH_LOCK + 128, GH_BYTES = GH_TASK + sizeof(GhTask) * GH_RING;
+    DBuf ghb(GH_BYTES, st);
 
     // optional per-vertex trace, written to the file opts->trace_path names
     const char *trace_path = O.o.trace_path;
@@ -561,8 +566,9 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         CK(cudaMemsetAsync(dir.p, 0, 4 * (size_t)nl * FILL_LEVELS, st));
         CK(cudaMemsetAsync(tops.p, 0, 24, st));
         CK(cudaMemsetAsync(status.p, 0, 4, st));
-        CK(cudaMemsetAsync(stats.p, 0, 256, st));
+        CK(cudaMemsetAsync(stats.p, 0, 1280, st));
         CK(cudaMemsetAsync(lvl.p, 0, 4 * nl, st));
+        CK(cudaMemsetAsync(ghb.p, 0, GH_BYTES, st));
         CK(launch_queue_init((int32_t)nl, dp.as<int32_t>(), queue.as<int32_t>(), ctrs.as<uint32_t>() + 1, st));
 
         ElimArgs a{};
@@ -598,6 +604,21 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         out.samples = O.o.samples;
         out.fill_store = O.o.fill_store;
         a.sample_sort = 1;
+        {
+            unsigned char *gb = ghb.as<unsigned char>();
+            a.gh_word = (unsigned long long *)(gb + GH_WORD);
+            a.gh_hint = (uint32_t *)(gb + GH_HINT);
+            a.gh_done = (uint32_t *)(gb + GH_DONE);
+            a.gh_lock = (int32_t *)(gb + GH_LOCK);
+            a.gh_task = (GhTask *)(gb + GH_TASK);
+            // default: only for hub-dominated inputs (longest lower column above 16x the
+            // average, as for the fill workspace), whose late vertices gather thousands of entries
+            const double avg_low = nl > 0 ? (double)nnz_low / (double)nl : 0.0;
+            const bool hubs = (double)out.max_lower_column > 16.0 * std::max(avg_low, 1.0);
+            const bool gh = O.o.grid_help == PARAC_ON || (O.o.grid_help == PARAC_DEFAULT && hubs);
+            a.grid_help = !gh || warp_cap < 128 ? 0 : std::max(1, O.o.grid_help_min);
+            a.gh_mask = 3;                                  // one warp in four
+        }
         if (O.o.sample_sort == PARAC_OFF) a.sample_sort = 0;
         if (O.o.idle_ns > 0) a.idle_ns = std::max(32, std::min(1000000, O.o.idle_ns));
         if (nl > 0) CK(elim_launch(a, blocks, warps, fchunk, st));
@@ -605,7 +626,7 @@ void run_factor(int64_t N, const int64_t *colptr, const int32_t *rowind, const d
         unsigned long long htops[3];
         CK(cudaMemcpyAsync(&hst, status.p, 4, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(htops, tops.p, 24, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(out.stats, stats.p, 256, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(out.stats, stats.p, 1280, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         out.pool_used = htops[0]; out.f_used = htops[1]; out.scratch_used = htops[2];
         if (hst == ST_OK) break;
@@ -967,14 +988,31 @@ std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_ind
              "\"release\": %llu, \"reg_weight_sort\": %llu, \"reg_scan\": %llu, \"coop_join\": %llu, "
              "\"coop_gather\": %llu, \"coop_row_sort\": %llu, \"coop_merge_store\": %llu, "
              "\"coop_weight_sort\": %llu, \"coop_scan\": %llu, \"coop_sample_append\": %llu, "
-             "\"coop_release\": %llu}}",
+             "\"coop_release\": %llu}, \"grid_help_vertices\": %llu, \"grid_help_chunks_helpers\": %llu, "
+             "\"grid_help_chunks_owner\": %llu}",
              (long long)h->n, (long long)h->nnzF, (long long)(h->nnzF + h->n), (long long)fo.nl,
              (long long)fo.nnz_low, fo.stats[3], fo.pool_used, fo.f_used, fo.scratch_used, fo.stats[0], fo.stats[1],
              fo.stats[2], fo.stats[5], fo.stats[6], fo.stats[4], fo.regrows, fo.max_lower_column, fo.blocks, fo.warps, h->prec, fo.samples, fo.fill_store, sys_index, fo.t_ingest, fo.t_elim,
              fo.t_compact, h->depth, h->max_row, fo.stats[8], fo.stats[9], fo.stats[10], fo.stats[11], fo.stats[12],
              fo.stats[13], fo.stats[14], fo.stats[15], fo.stats[16], fo.stats[17], fo.stats[18], fo.stats[19],
-             fo.stats[20], fo.stats[21], fo.stats[22], fo.stats[23]);
-    return buf;
+             fo.stats[20], fo.stats[21], fo.stats[22], fo.stats[23], fo.stats[24], fo.stats[25], fo.stats[26]);
+    std::string out = buf;
+    if (fo.stats[24] > 0 && (fo.stats[32] | fo.stats[33] | fo.stats[34]) != 0) {
+        // grid-help step profile (timing >= 2): per step, the owner's post /
+        // own chunks / wait cycles and the helpers' chunk cycles and count
+        out.pop_back();
+        out += ", \"grid_help_steps\": [";
+        for (int op = 1; op <= 12; ++op) {
+            char e[256];
+            snprintf(e, sizeof e, "%s[%llu, %llu, %llu, %llu, %llu, %llu, %llu, %llu]", op > 1 ? ", " : "",
+                     fo.stats[32 + 4 * (op - 1)], fo.stats[33 + 4 * (op - 1)], fo.stats[34 + 4 * (op - 1)],
+                     fo.stats[35 + 4 * (op - 1)], fo.stats[80 + op], fo.stats[96 + op], fo.stats[112 + op],
+                     fo.stats[128 + op]);
+            out += e;
+        }
+        out += "]}";
+    }
+    return out;
 }
 
 template <typename F>

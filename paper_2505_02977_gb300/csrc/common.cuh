@@ -197,6 +197,32 @@ __host__ __device__ __forceinline__ int fill_level(uint32_t i)
 __host__ __device__ __forceinline__ uint32_t fill_level_start(int j) { return (uint32_t)FILL_C0 << (2 * (j - 1)); }
 __host__ __device__ __forceinline__ uint32_t fill_level_cap(int j) { return 3u * ((uint32_t)FILL_C0 << (2 * (j - 1))); }
 
+// ---------------------------------------------------------------- grid help
+// One step of a large vertex's elimination posted for idle warps: the items
+// [0, n) cut into nch chunks of `chunk`, claimed one at a time.
+constexpr int GH_RING = 4;       // task descriptors / done counters in flight
+constexpr int GH_HINTS = 16;     // copies of the posting hint (one 128-byte line each)
+struct __align__(16) GhTask {
+    int32_t gen, op, k, n;            // generation, step, vertex, items
+    int32_t chunk, nch, B, d;         // items per chunk, chunks, buckets, merged entries
+    int32_t cap, norig, bmax, lk;     // working-set capacity, original entries, helper bucket limit, level + 1
+    uint32_t cnt;                     // fill entries of k
+    int32_t spl_shared, slice, nco;   // splitters staged in the warp slice; slice bytes; coarse entries
+    int64_t o0;                       // first original entry of k
+    unsigned long long fpos;          // F column position
+    double Dk;
+    uint64_t klocal, sys;
+    unsigned char *vbase;             // working set: make_view(vbase, cap)
+    double *tiles;                    // suffix-scan tile totals, then carries
+    unsigned long long *tmax;         // tile maxima of S, then their running maxima
+    int32_t *gbo, *gbd, *pd;          // bucket offsets, merged counts, compacted offsets
+    int32_t *cnt_b, *cur_b;           // bucket counts and scatter cursors
+    int32_t *spl_row;                 // splitters b = 1 .. B-1
+    unsigned long long *spl_wb;
+    unsigned long long *coarse;       // running maximum at every cstride-th position (sampling)
+    int32_t cstride, pad0, pad1, pad2;
+};
+
 // ---------------------------------------------------------------- elimination arguments
 struct ElimArgs {
     int32_t nl;                    // labels (all systems, ground labels included)
@@ -255,6 +281,14 @@ struct ElimArgs {
     int32_t *wrow;
     double *ww;
     unsigned long long wcap;
+    // grid help: idle warps take chunks of a large vertex's data-parallel steps
+    int32_t grid_help;             // gathered entries from which a vertex is offered (0: never)
+    int32_t gh_mask;               // warps with (grid index & gh_mask) == 0 serve as helpers
+    unsigned long long *gh_word;   // generation << 48 | chunks << 32 | next chunk
+    uint32_t *gh_hint;             // GH_HINTS copies, one per 128-byte line: generation | 1 << 16
+    uint32_t *gh_done;             // GH_RING done counters, one per 128-byte line
+    int32_t *gh_lock;              // 0 free, 1 held by the vertex being helped
+    GhTask *gh_task;               // GH_RING task descriptors
 };
 
 // Bytes of shared/scratch memory per entry of the per-vertex working set:

@@ -294,6 +294,10 @@ __device__ bool append_fill(const ElimArgs &a, bool act, int32_t lo, int32_t hi,
 // u, m when valid).  A positive-to-zero transition makes u ready: the first
 // such vertex is kept in `keep` when it is -1 (empty; -2 means never keep)
 // for this warp, the others are published on the queue.
+// Counter decrements of one group of up to 32 merged neighbours (lane holds
+// u, m when valid).  A positive-to-zero transition makes u ready: the first
+// such vertex is kept in `keep` when it is -1 (empty; -2 means never keep)
+// for this warp, the others are published on the queue.
 __device__ void decrement_group(const ElimArgs &a, int32_t pivot, bool valid, int32_t u, int32_t m, int32_t &keep)
 {
     const unsigned lane = lane_id();
@@ -819,9 +823,33 @@ struct CoopShared {
     unsigned long long fpos;
     unsigned long long sbase, scap;   // CTA scratch (global), reused across requests
     long long spin_limit;
+    GhTask *gt;                  // grid help: the step being posted (in the CTA's global scratch)
+    uint32_t gh_gen;             // last generation posted on the board
+    int gh;                      // this vertex holds the board
+    int gh_req;                  // the posted request asks for grid help
 };
+// Static shared memory stays small: two CTAs of 8 warps (98,824 bytes of
+// dynamic shared memory each) fit the SM's 196 KB shared-memory carve-out
+// only with at most 504 bytes of static shared memory per CTA; beyond it the
+// 228 KB carve-out halves the L1 cache (measured: the whole elimination ~9%
+// slower).
+static_assert(sizeof(CoopShared) <= 320, "static shared memory of the elimination kernel");
 
 __device__ __forceinline__ volatile int &vol(int &x) { return *(volatile int *)&x; }
+
+constexpr int GH_COARSE = 512;   // coarse entries of the sampling search (one 4 KB warp slice)
+
+// Bytes of a CTA's global working set of P entries: the entries, the scan
+// tiles, bucket offsets / merged counts / oversized list; with grid help
+// also the tile maxima, splitters (rows, weight bits), bucket counters,
+// compacted offsets and the coarse search table.
+__device__ __forceinline__ unsigned long long coop_scratch_bytes(int P, int cap, bool gh)
+{
+    const unsigned long long p = (unsigned long long)P, c = (unsigned long long)cap;
+    unsigned long long need = p * ENTRY_BYTES + (p / 32 + 1) * 8 + 16ull + 4ull * (3ull * c + 3ull);
+    if (gh) need += 16ull + sizeof(GhTask) + (p / 32 + 1) * 8 + 12ull * c + 4ull * (3ull * c + 1ull) + 16ull + 8ull * GH_COARSE;
+    return need;
+}
 
 // Bounded barrier over the CTA's warps; false if it gave up (status set).
 __device__ bool cta_barrier(CoopShared &cs, const ElimArgs &a)
@@ -1087,24 +1115,55 @@ __device__ View sort_big_bucket(View v, View tile, int cap, int o, int cb)
     return w;
 }
 
-// Buckets of up to 256 entries are sorted by one warp in registers: lane l
-// holds positions lE .. lE + E - 1 of the list padded to 32E entries (a power
-// of two); the bitonic stages with stride j < E compare two slots of one
-// lane, the others pair lane l with lane l ^ (j / E) through shuffles.  It is
-// the network of the shared-memory sorts, so the sorted list is the same.
+// Buckets of up to 256 entries are sorted by one warp with a rank sort: the
+// keys go to the warp's shared slice, and every entry's place is the number
+// of entries with a smaller key, counted against all of them (equal keys,
+// i.e. identical (row, weight) entries, by their index).  The places form a
+// permutation that sorts the bucket, the same sorted list as any exact sort;
+// a lane holds entries lane + 32e, e < E.
+template <int KEY>
+__device__ __forceinline__ bool key_lt(int32_t ra, unsigned long long ba, int32_t rb, unsigned long long bb)
+{
+    return KEY == 0 ? (ra < rb || (ra == rb && ba < bb)) : (ba < bb || (ba == bb && ra < rb));
+}
+
+// Buckets of 65 to 256 entries go through a bitonic network in registers
+// instead (lane l holds positions lE .. lE + E - 1 of the list padded to 32E
+// entries; stages with stride j < E compare two slots of a lane, the others
+// pair lane l with lane l ^ (j / E) through shuffles): its cost grows with
+// log^2 of the size where the rank sort's grows with the square.
 template <int KEY>
 __device__ __forceinline__ bool key_gt(int32_t ra, unsigned long long ba, int32_t rb, unsigned long long bb)
 {
     return KEY == 0 ? (ra > rb || (ra == rb && ba > bb)) : (ba > bb || (ba == bb && ra > rb));
 }
 
+// Stages with stride J < E: slots e and e + J of one lane.
+template <int KEY, int E, int J>
+__device__ __forceinline__ void reg_bucket_intra(int32_t (&r)[E], unsigned long long (&b)[E], int32_t (&m)[E],
+                                                 int lane, int kk)
+{
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        if (e & J) continue;
+        const bool asc = ((lane * E + e) & kk) == 0;
+        if (key_gt<KEY>(r[e], b[e], r[e + J], b[e + J]) == asc) {
+            const int32_t rt = r[e]; r[e] = r[e + J]; r[e + J] = rt;
+            const unsigned long long bt = b[e]; b[e] = b[e + J]; b[e + J] = bt;
+            if (KEY == 1) { const int32_t mt = m[e]; m[e] = m[e + J]; m[e + J] = mt; }
+        }
+    }
+}
+
+// The stage loops stay loops (only the slots of one stage are unrolled):
+// the network runs rarely on any one SM, so its code is kept small.
 template <int KEY, int E>
 __device__ __forceinline__ void reg_bucket_net(int32_t (&r)[E], unsigned long long (&b)[E], int32_t (&m)[E])
 {
     const int lane = (int)lane_id();
-#pragma unroll
+#pragma unroll 1
     for (int kk = 2; kk <= 32 * E; kk <<= 1) {
-#pragma unroll
+#pragma unroll 1
         for (int j = kk >> 1; j > 0; j >>= 1) {
             if (j >= E) {
                 const int lj = j / E;
@@ -1118,17 +1177,12 @@ __device__ __forceinline__ void reg_bucket_net(int32_t (&r)[E], unsigned long lo
                     const bool take = lower == asc ? key_gt<KEY>(r[e], b[e], ro, bo) : key_gt<KEY>(ro, bo, r[e], b[e]);
                     if (take) { r[e] = ro; b[e] = bo; if (KEY == 1) m[e] = mo; }
                 }
+            } else if (j == 1) {
+                if (E > 1) reg_bucket_intra<KEY, E, (E > 1 ? 1 : 0)>(r, b, m, lane, kk);
+            } else if (j == 2) {
+                if (E > 2) reg_bucket_intra<KEY, E, (E > 2 ? 2 : 0)>(r, b, m, lane, kk);
             } else {
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    if (e & j) continue;
-                    const bool asc = ((lane * E + e) & kk) == 0;
-                    if (key_gt<KEY>(r[e], b[e], r[e + j], b[e + j]) == asc) {
-                        const int32_t rt = r[e]; r[e] = r[e + j]; r[e + j] = rt;
-                        const unsigned long long bt = b[e]; b[e] = b[e + j]; b[e + j] = bt;
-                        if (KEY == 1) { const int32_t mt = m[e]; m[e] = m[e + j]; m[e + j] = mt; }
-                    }
-                }
+                if (E > 4) reg_bucket_intra<KEY, E, (E > 4 ? 4 : 0)>(r, b, m, lane, kk);
             }
         }
     }
@@ -1145,46 +1199,107 @@ __device__ __forceinline__ void reg_bucket_load(const double *tS, const unsigned
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int i = lane * E + e;
-        rm[e] = i < cb ? tM[o + i] : (unsigned long long)(uint32_t)ROW_SENTINEL;
-        wb[e] = i < cb ? dbits(tS[o + i]) : (KEY == 0 ? 0ull : WBITS_SENTINEL);
+        rm[e] = i < cb ? __ldcg(tM + o + i) : (unsigned long long)(uint32_t)ROW_SENTINEL;
+        wb[e] = i < cb ? dbits(__ldcg(tS + o + i)) : (KEY == 0 ? 0ull : WBITS_SENTINEL);
     }
 #pragma unroll
     for (int e = 0; e < E; ++e) { r[e] = (int32_t)(uint32_t)rm[e]; m[e] = (int32_t)(rm[e] >> 32); b[e] = wb[e]; }
 }
 
-// Row phase: sort the bucket by (row, weight bits) and leave it at [0, cb) of
-// the warp's shared slice for the run merge.
+// Load bucket [o, o + cb) of the temporaries (weights tS, row | mult << 32 in
+// tM), put its keys in sv and return every held entry's place.
+template <int KEY, int E>
+__device__ __forceinline__ void rank_bucket(const double *tS, const unsigned long long *tM, int o, int cb, View sv,
+                                            int32_t (&r)[E], unsigned long long (&b)[E], int32_t (&m)[E],
+                                            int (&place)[E])
+{
+    const int lane = (int)lane_id();
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        const unsigned long long rm = i < cb ? __ldcg(tM + o + i) : 0ull;
+        b[e] = i < cb ? dbits(__ldcg(tS + o + i)) : 0ull;
+        r[e] = (int32_t)(uint32_t)rm;
+        m[e] = (int32_t)(rm >> 32);
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        if (i < cb) { sv.row[i] = r[e]; sv.w[i] = __longlong_as_double((long long)b[e]); }
+        place[e] = 0;
+    }
+    __syncwarp();
+    for (int j = 0; j < cb; ++j) {
+        const int32_t rj = sv.row[j];
+        const unsigned long long bj = dbits(sv.w[j]);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = lane + 32 * e;
+            place[e] += (key_lt<KEY>(rj, bj, r[e], b[e]) || (rj == r[e] && bj == b[e] && j < i)) ? 1 : 0;
+        }
+    }
+    __syncwarp();
+}
+
+// Row phase: sort the bucket by (row, weight bits) into [0, cb) of the warp's
+// shared slice, for the run merge.
 template <int E>
 __device__ __noinline__ void reg_bucket_rows(const double *tS, const unsigned long long *tM, int o, int cb, View sv)
 {
     int32_t r[E], m[E];
     unsigned long long b[E];
-    reg_bucket_load<0, E>(tS, tM, o, cb, r, b, m);
-    reg_bucket_net<0, E>(r, b, m);
+    if (E >= 4) {                                         // network: lane l holds positions lE + e
+        reg_bucket_load<0, E>(tS, tM, o, cb, r, b, m);
+        reg_bucket_net<0, E>(r, b, m);
+        const int lane = (int)lane_id();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = lane * E + e;
+            if (i < cb) { sv.row[i] = r[e]; sv.w[i] = __longlong_as_double((long long)b[e]); }
+        }
+        __syncwarp();
+        return;
+    }
+    int place[E];
+    rank_bucket<0, E>(tS, tM, o, cb, sv, r, b, m, place);
     const int lane = (int)lane_id();
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int i = lane * E + e;
-        if (i < cb) { sv.row[i] = r[e]; sv.w[i] = __longlong_as_double((long long)b[e]); }
+        if (lane + 32 * e < cb) { sv.row[place[e]] = r[e]; sv.w[place[e]] = __longlong_as_double((long long)b[e]); }
     }
     __syncwarp();
 }
 
-// Weight phase: sort the bucket by (weight bits, row) and store it at
-// [o, o + cb) of v.
+// Weight phase: sort the bucket by (weight bits, row) into [o, o + cb) of v
+// (sv is the warp's shared slice for the keys).
 template <int E>
-__device__ __noinline__ void reg_bucket_weights(const double *tS, const unsigned long long *tM, int o, int cb, View v)
+__device__ __noinline__ void reg_bucket_weights(const double *tS, const unsigned long long *tM, int o, int cb, View sv,
+                                                View v)
 {
     int32_t r[E], m[E];
     unsigned long long b[E];
-    reg_bucket_load<1, E>(tS, tM, o, cb, r, b, m);
-    reg_bucket_net<1, E>(r, b, m);
+    if (E >= 4) {
+        reg_bucket_load<1, E>(tS, tM, o, cb, r, b, m);
+        reg_bucket_net<1, E>(r, b, m);
+        const int lane = (int)lane_id();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = lane * E + e;
+            if (i < cb) { v.row[o + i] = r[e]; v.w[o + i] = __longlong_as_double((long long)b[e]); v.mult[o + i] = m[e]; }
+        }
+        return;
+    }
+    int place[E];
+    rank_bucket<1, E>(tS, tM, o, cb, sv, r, b, m, place);
     const int lane = (int)lane_id();
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int i = lane * E + e;
-        if (i < cb) { v.row[o + i] = r[e]; v.w[o + i] = __longlong_as_double((long long)b[e]); v.mult[o + i] = m[e]; }
+        if (lane + 32 * e < cb) {
+            const int q = o + place[e];
+            v.row[q] = r[e]; v.w[q] = __longlong_as_double((long long)b[e]); v.mult[q] = m[e];
+        }
     }
+    __syncwarp();
 }
 
 constexpr int REG_BUCKET_MAX = 256;
@@ -1347,10 +1462,10 @@ __device__ void coop_weight_phase(View v, int d, unsigned char *bbuf, int cap, C
         }
         const int Pb = next_pow2(cb);
         if (Pb <= REG_BUCKET_MAX) {
-            if (Pb <= 32) reg_bucket_weights<1>(tS, tM, o, cb, v);
-            else if (Pb == 64) reg_bucket_weights<2>(tS, tM, o, cb, v);
-            else if (Pb == 128) reg_bucket_weights<4>(tS, tM, o, cb, v);
-            else reg_bucket_weights<8>(tS, tM, o, cb, v);
+            if (Pb <= 32) reg_bucket_weights<1>(tS, tM, o, cb, sv, v);
+            else if (Pb == 64) reg_bucket_weights<2>(tS, tM, o, cb, sv, v);
+            else if (Pb == 128) reg_bucket_weights<4>(tS, tM, o, cb, sv, v);
+            else reg_bucket_weights<8>(tS, tM, o, cb, sv, v);
             continue;
         }
         for (int i = lane; i < Pb; i += 32) {
@@ -1367,6 +1482,827 @@ __device__ void coop_weight_phase(View v, int d, unsigned char *bbuf, int cap, C
         __syncwarp();
     }
     __syncthreads();
+}
+
+// ---------------------------------------------------------------- grid help
+// A vertex whose working set lives in global scratch is eliminated by its
+// CTA, but every data-parallel step of it (gather, bucket counts, scatter,
+// bucket sorts, compaction, scan tiles, sampling, decrements) is posted on a
+// global board and cut into chunks that any idle warp of the grid may claim.
+// The owning CTA claims chunks too and waits (bounded) until every claimed
+// chunk is done; the serial steps between them (the sample of splitters,
+// bucket scans, the carry chains) stay with the owner.  Only who computes a
+// chunk changes, never what it computes, so the factor is the same.
+//
+// Board: gh_word = generation << 48 | chunks << 32 | next chunk.  A claim is
+// an atomicAdd of 1; it is valid when the old next is below the old chunk
+// count, for the generation it shows, whose descriptor stays in place until
+// all its chunks are done.  A helper releases its writes (fence) before it
+// counts its chunk done; the owner acquires the done count before the next
+// step.  Data that other SMs wrote are read through L2 (ld.cg).
+enum : int32_t {
+    GH_GATHER = 1, GH_COUNT0, GH_COUNT1, GH_SCATTER0, GH_SCATTER1, GH_ROWB, GH_COMPACT, GH_WB, GH_TILES,
+    GH_CARRYMAX, GH_SAMPLE, GH_DECR
+};
+static_assert(sizeof(GhTask) % 16 == 0, "task descriptors are copied in 16-byte units");
+
+// Compact view of a warp's slice for a bucket of up to 256 entries: weights,
+// then rows (3 KB).
+__device__ __forceinline__ View slice_view(unsigned char *slice)
+{
+    View v;
+    v.w = (double *)slice;
+    v.row = (int32_t *)(slice + 8 * REG_BUCKET_MAX);
+    v.S = v.M = nullptr;
+    v.mult = nullptr;
+    return v;
+}
+
+// Bucket of an entry among splitters sr/sw[1 .. B-1] (in the warp's slice, or
+// in global memory when they do not fit): as bucket_of.
+template <int KEY>
+__device__ __forceinline__ int gh_bucket(const int32_t *sr, const unsigned long long *sw, int B, bool glob,
+                                         int32_t r, unsigned long long wb)
+{
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int32_t s = glob ? __ldcg(sr + mid) : sr[mid];
+        bool below;
+        if (KEY == 0) {
+            below = s < r;
+        } else {
+            const unsigned long long w = glob ? __ldcg(sw + mid) : sw[mid];
+            below = w < wb || (w == wb && s < r);
+        }
+        if (below) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Count (SCATTER = false) or scatter one chunk of entries into their buckets.
+template <int KEY, bool SCATTER>
+__device__ void gh_partition_chunk(const GhTask &t, int lo, int hi, unsigned char *slice)
+{
+    const int lane = (int)lane_id();
+    const View v = make_view(t.vbase, t.cap);
+    const int32_t *sr = t.spl_row;
+    const unsigned long long *sw = t.spl_wb;
+    const bool glob = !t.spl_shared;
+    if (!glob) {                                   // stage the splitters in the slice
+        int32_t *lr = (int32_t *)slice;
+        unsigned long long *lw = (unsigned long long *)(slice + 4 * (size_t)REG_BUCKET_MAX * 2);
+        for (int b = lane; b < t.B; b += 32) {
+            lr[b] = __ldcg(t.spl_row + b);
+            if (KEY == 1) lw[b] = __ldcg(t.spl_wb + b);
+        }
+        __syncwarp();
+        sr = lr; sw = lw;
+    }
+    double *tS = v.S;
+    unsigned long long *tM = (unsigned long long *)v.M;
+    for (int i0 = lo; i0 < hi; i0 += 8 * 32) {
+        int32_t r[8], m[8], bk[8];
+        double w[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = i0 + 32 * q + lane;
+            r[q] = i < hi ? __ldcg(v.row + i) : 0;
+            w[q] = (KEY == 1 || SCATTER) && i < hi ? __ldcg(v.w + i) : 0.0;
+            m[q] = KEY == 1 && SCATTER && i < hi ? __ldcg(v.mult + i) : 0;
+        }
+        unsigned grp[8];
+        int base[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = i0 + 32 * q + lane;
+            bk[q] = i < hi ? gh_bucket<KEY>(sr, sw, t.B, glob, r[q], KEY == 1 ? dbits(w[q]) : 0ull) : -1;
+            grp[q] = __match_any_sync(FULL, bk[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {                      // all of the batch's atomics in flight together
+            const int leader = __ffs(grp[q]) - 1;
+            base[q] = 0;
+            if (bk[q] >= 0 && lane == leader) {
+                if (!SCATTER) atomicAdd(t.cnt_b + bk[q], __popc(grp[q]));
+                else base[q] = atomicAdd(t.cur_b + bk[q], __popc(grp[q]));
+            }
+        }
+        if (SCATTER) {
+            int off[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) off[q] = bk[q] >= 0 ? __ldcg(t.gbo + bk[q]) : 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int bq = __shfl_sync(FULL, base[q], __ffs(grp[q]) - 1);
+                if (bk[q] >= 0) {
+                    const int pos = off[q] + bq + __popc(grp[q] & ((1u << lane) - 1u));
+                    tS[pos] = w[q];
+                    tM[pos] = (unsigned long long)(uint32_t)r[q] | ((unsigned long long)(uint32_t)m[q] << 32);
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// One chunk of a posted step, by one warp.  keep: as decrement_group.
+// Returns false when the kernel must stop.
+__device__ __noinline__ bool gh_do(const ElimArgs &a, const GhTask &t, int idx, unsigned char *slice, int32_t &keep)
+{
+    const int lane = (int)lane_id();
+    if (idx < 0 || idx >= t.nch || (long long)idx * t.chunk >= (long long)t.n) {
+        set_status(a.status, ST_INVAL);
+        return false;
+    }
+    const int lo = idx * t.chunk, hi = lo + t.chunk < t.n ? lo + t.chunk : t.n;
+    const View v = make_view(t.vbase, t.cap);
+    double *tS = v.S;
+    unsigned long long *tM = (unsigned long long *)v.M;
+    const int d = t.d;
+    switch (t.op) {
+    case GH_GATHER: {                                         // 8 entries per lane in flight
+        const int k = t.k, norig = t.norig, g = t.norig + (int)t.cnt;
+        for (int base = lo; base < hi; base += 256) {
+            uint32_t gi[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = base + 32 * q + lane;
+                const uint32_t f = (uint32_t)(i - norig);
+                gi[q] = 0u;
+                if (i < hi && i >= norig && i < g && f >= (uint32_t)FILL_C0) {
+                    const int j = fill_level(f);
+                    gi[q] = j <= FILL_LEVELS ? __ldcg(a.dir + (size_t)k * FILL_LEVELS + (j - 1)) : 0u;
+                }
+            }
+            int32_t r[8];
+            double w[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = base + 32 * q + lane;
+                r[q] = ROW_SENTINEL; w[q] = 0.0;
+                if (i >= hi) continue;
+                if (i < norig) {
+                    r[q] = __ldg(a.lrow + t.o0 + i); w[q] = __ldg(a.lw + t.o0 + i);
+                } else if (i < g) {
+                    const uint32_t f = (uint32_t)(i - norig);
+                    if (f < (uint32_t)FILL_C0) {
+                        r[q] = __ldcg(a.in_row + (size_t)k * FILL_C0 + f); w[q] = __ldcg(a.in_w + (size_t)k * FILL_C0 + f);
+                    } else if (gi[q] == 0u || gi[q] == 0xffffffffu) {
+                        set_status(a.status, ST_INVAL);
+                    } else {
+                        const int j = fill_level(f);
+                        const unsigned long long at = (unsigned long long)(gi[q] - 1u) * FILL_GRANULE + (f - fill_level_start(j));
+                        r[q] = __ldcg(a.pool_row + at); w[q] = __ldcg(a.pool_w + at);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = base + 32 * q + lane;
+                if (i < hi) { v.row[i] = r[q]; v.w[i] = w[q]; }
+            }
+        }
+        return true;
+    }
+    case GH_COUNT0: gh_partition_chunk<0, false>(t, lo, hi, slice); return true;
+    case GH_COUNT1: gh_partition_chunk<1, false>(t, lo, hi, slice); return true;
+    case GH_SCATTER0: gh_partition_chunk<0, true>(t, lo, hi, slice); return true;
+    case GH_SCATTER1: gh_partition_chunk<1, true>(t, lo, hi, slice); return true;
+    case GH_ROWB: {
+        const View sv = slice_view(slice);
+        for (int b = lo; b < hi; ++b) {
+            const int o = __ldcg(t.gbo + b), cb = __ldcg(t.gbo + b + 1) - o;
+            if (cb > t.bmax) continue;                       // sorted and merged by the owner
+            int db = 0;
+            if (cb > 0) {
+                const int Pb = next_pow2(cb);
+                if (Pb <= 32) reg_bucket_rows<1>(tS, tM, o, cb, sv);
+                else if (Pb == 64) reg_bucket_rows<2>(tS, tM, o, cb, sv);
+                else if (Pb == 128) reg_bucket_rows<4>(tS, tM, o, cb, sv);
+                else reg_bucket_rows<8>(tS, tM, o, cb, sv);
+                db = warp_merge_bucket(sv, cb, tS, tM, o);
+                __syncwarp();
+            }
+            if (lane == 0) t.gbd[b] = db;
+        }
+        return true;
+    }
+    case GH_COMPACT: {
+        for (int b = lo; b < hi; ++b) {
+            const int o = __ldcg(t.gbo + b), db = __ldcg(t.gbd + b), p0 = __ldcg(t.pd + b);
+            for (int i0 = 0; i0 < db; i0 += 256) {
+                unsigned long long rm[8];
+                double x[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int i = i0 + 32 * q + lane;
+                    rm[q] = i < db ? __ldcg(tM + o + i) : 0ull;
+                    x[q] = i < db ? __ldcg(tS + o + i) : 0.0;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int i = i0 + 32 * q + lane;
+                    if (i >= db) continue;
+                    const int32_t r = (int32_t)(uint32_t)rm[q];
+                    v.row[p0 + i] = r; v.w[p0 + i] = x[q]; v.mult[p0 + i] = (int32_t)(rm[q] >> 32);
+                    a.f_row[t.fpos + p0 + i] = r; a.f_val[t.fpos + p0 + i] = x[q];
+                }
+            }
+        }
+        return true;
+    }
+    case GH_WB: {
+        for (int b = lo; b < hi; ++b) {
+            const int o = __ldcg(t.gbo + b), cb = __ldcg(t.gbo + b + 1) - o;
+            if (cb == 0) continue;
+            if (cb > t.bmax) {                               // sorted by the owner: to its place
+                for (int i = lane; i < cb; i += 32) {
+                    const unsigned long long rm = __ldcg(tM + o + i);
+                    v.row[o + i] = (int32_t)(uint32_t)rm; v.mult[o + i] = (int32_t)(rm >> 32);
+                    v.w[o + i] = __ldcg(tS + o + i);
+                }
+                continue;
+            }
+            const int Pb = next_pow2(cb);
+            const View sv = slice_view(slice);
+            if (Pb <= 32) reg_bucket_weights<1>(tS, tM, o, cb, sv, v);
+            else if (Pb == 64) reg_bucket_weights<2>(tS, tM, o, cb, sv, v);
+            else if (Pb == 128) reg_bucket_weights<4>(tS, tM, o, cb, sv, v);
+            else reg_bucket_weights<8>(tS, tM, o, cb, sv, v);
+        }
+        return true;
+    }
+    case GH_TILES: {                                          // scan of each 32-entry tile of the reversed weights
+        for (int j0 = lo; j0 < hi; j0 += 4) {
+            double x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int tt = 32 * (j0 + q) + lane;
+                x[q] = j0 + q < hi && tt < d ? __ldcg(v.w + (d - 1 - tt)) : 0.0;
+            }
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const double y = __shfl_up_sync(FULL, x[q], off);
+                    if (lane >= off) x[q] = __dadd_rn(x[q], y);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (j0 + q >= hi) continue;
+                const int tt = 32 * (j0 + q) + lane;
+                if (tt < d) v.S[d - 1 - tt] = x[q];
+                if (lane == 31) t.tiles[j0 + q] = x[q];
+            }
+        }
+        return true;
+    }
+    case GH_CARRYMAX: {                                       // tile carry, then the tile's running maximum
+        for (int j0 = lo; j0 < hi; j0 += 4) {
+            double sv[4], c[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int tt = 32 * (j0 + q) + lane;
+                const bool in = j0 + q < hi && tt < d;
+                c[q] = j0 + q < hi ? __ldcg(t.tiles + j0 + q) : 0.0;
+                sv[q] = in ? __ldcg(v.S + (d - 1 - tt)) : 0.0;
+            }
+            unsigned long long m[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int tt = 32 * (j0 + q) + lane;
+                const bool in = j0 + q < hi && tt < d;
+                if (in) { sv[q] = __dadd_rn(sv[q], c[q]); v.S[d - 1 - tt] = sv[q]; }
+                m[q] = in ? dbits(sv[q]) : 0ull;
+            }
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const unsigned long long y = __shfl_up_sync(FULL, m[q], off);
+                    if (lane >= off && y > m[q]) m[q] = y;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (j0 + q >= hi) continue;
+                const int tt = 32 * (j0 + q) + lane;
+                if (tt < d) v.M[d - 1 - tt] = __longlong_as_double((long long)m[q]);
+                if (lane == 31) t.tmax[j0 + q] = m[q];
+            }
+        }
+        return true;
+    }
+    case GH_SAMPLE: {
+        // levels of the merged rows, then slots p = i >= 1, two per lane with
+        // their searches interleaved.  M_final[j] = max(M[j], running maximum
+        // of the tiles before j's tile) is non-increasing; the largest j in
+        // [p, d) with M_final[j] >= R is sampled: first among the coarse
+        // entries coarse[c] = M_final[c * cstride] (staged in the slice),
+        // then within that stride.
+        bool ok = true;
+        for (int i = lo + lane; i < hi; i += 32) red_max_relaxed(a.lvl + __ldcg(v.row + i), t.lk);
+        unsigned long long *co = (unsigned long long *)slice;
+        const int nco = t.nco, cst = t.cstride;
+        for (int c0 = 0; c0 < nco; c0 += 256) {
+            unsigned long long x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) { const int c = c0 + 32 * q + lane; x[q] = c < nco ? __ldcg(t.coarse + c) : 0ull; }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) { const int c = c0 + 32 * q + lane; if (c < nco) co[c] = x[q]; }
+        }
+        __syncwarp();
+        const int samples = a.samples;
+        for (int base = lo; base < hi && ok; base += 64)
+        for (int q = 0; q < samples && ok; ++q) {
+            int p[2], jl[2], jh[2];
+            unsigned long long Rb[2];
+            double Sp[2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                p[s] = base + 32 * s + lane;
+                const bool act = p[s] >= 1 && p[s] < hi;
+                Sp[s] = act ? __ldcg(v.S + p[s]) : 0.0;
+                Rb[s] = act ? dbits(__dmul_rn(Sp[s], slot_uniform(a.seed, t.klocal, (uint64_t)p[s], t.sys, (uint64_t)q))) : 0ull;
+                jl[s] = 0; jh[s] = 0;
+                if (act) {                                   // largest coarse c with coarse[c] >= R (c = p / cst qualifies)
+                    int clo = p[s] / cst, chi = nco - 1;
+                    while (clo < chi) {
+                        const int mid = clo + ((chi - clo + 1) >> 1);
+                        if (co[mid] >= Rb[s]) clo = mid; else chi = mid - 1;
+                    }
+                    jl[s] = clo * cst > p[s] ? clo * cst : p[s];
+                    jh[s] = (clo + 1) * cst - 1 < d - 1 ? (clo + 1) * cst - 1 : d - 1;
+                }
+            }
+            while (jl[0] < jh[0] || jl[1] < jh[1]) {
+                unsigned long long mv[2] = {0ull, 0ull}, tv[2] = {0ull, 0ull};
+                int mid[2];
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    mid[s] = jl[s] + ((jh[s] - jl[s] + 1) >> 1);
+                    if (jl[s] < jh[s]) {
+                        mv[s] = dbits(__ldcg(v.M + mid[s]));
+                        tv[s] = __ldcg(t.tmax + ((d - 1 - mid[s]) >> 5));
+                    }
+                }
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    if (jl[s] < jh[s]) {
+                        const unsigned long long mf = mv[s] > tv[s] ? mv[s] : tv[s];
+                        if (mf >= Rb[s]) jl[s] = mid[s]; else jh[s] = mid[s] - 1;
+                    }
+                }
+            }
+            int32_t u[2], x[2];
+            double wu[2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const bool act = p[s] >= 1 && p[s] < hi;
+                u[s] = act ? __ldcg(v.row + p[s] - 1) : 0;
+                wu[s] = act ? __ldcg(v.w + p[s] - 1) : 0.0;
+                x[s] = act ? __ldcg(v.row + jl[s]) : 0;
+            }
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const bool act = p[s] >= 1 && p[s] < hi;
+                double c = 0.0;
+                if (act) {
+                    c = __ddiv_rn(__dmul_rn(Sp[s], wu[s]), t.Dk);
+                    if (samples > 1) c = __ddiv_rn(c, (double)samples);
+                }
+                const int32_t lo_v = u[s] < x[s] ? u[s] : x[s], hi_v = u[s] < x[s] ? x[s] : u[s];
+                if (!append_fill(a, act, lo_v, hi_v, c)) ok = false;
+            }
+        }
+        __syncwarp();
+        return ok;
+    }
+    case GH_DECR: {
+        for (int ib = lo; ib < hi; ib += 128) {
+            int32_t u[4], m[4], r[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = ib + 32 * q + lane;
+                u[q] = i < hi ? __ldcg(v.row + i) : 0;
+                m[q] = i < hi ? __ldcg(v.mult + i) : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) r[q] = ib + 32 * q + lane < hi ? atomicSub(a.dp + u[q], m[q]) : 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                bool ready = ib + 32 * q + lane < hi && r[q] == m[q];
+                if (ready && a.trace) { a.trace[4 * (size_t)u[q]] = global_ns(); a.trace_parent[u[q]] = t.k; }
+                unsigned bal = __ballot_sync(FULL, ready);      // as decrement_group, after its atomic
+                if (!bal) continue;
+                if (keep == -1) {
+                    const int kl = __ffs(bal) - 1;
+                    keep = __shfl_sync(FULL, u[q], kl);
+                    bal &= ~(1u << kl);
+                    if (lane == kl) ready = false;
+                }
+                if (!bal) continue;
+                const int leader = __ffs(bal) - 1;
+                uint32_t qb = 0;
+                if (lane == leader) qb = atomicAdd(a.q_tail, (uint32_t)__popc(bal));
+                qb = __shfl_sync(FULL, qb, leader);
+                if (ready) {
+                    const uint32_t at = qb + __popc(bal & ((1u << lane) - 1u));
+                    if (at < (uint32_t)a.nl) { fence_acq_rel(); st_release(a.queue + at, u[q]); }
+                    else set_status(a.status, ST_INVAL);
+                }
+            }
+        }
+        return true;
+    }
+    default:
+        set_status(a.status, ST_INVAL);
+        return false;
+    }
+}
+
+// Claim and run chunks of generation gen (any generation when gen < 0) until
+// none is left.  Warp-uniform; returns the number of chunks run.
+__device__ __noinline__ int gh_claim_loop(const ElimArgs &a, const GhTask *own, int gen, unsigned char *slice, int32_t &keep,
+                                          int *seen_gen = nullptr)
+{
+    const int lane = (int)lane_id();
+    int runs = 0;
+    GhTask t;
+    for (;;) {
+        unsigned long long old = 0;
+        if (lane == 0) {
+            // a plain read first: once a step's chunks are all claimed, the
+            // late helpers do not queue atomics in front of the real claims
+            const unsigned long long cur = *(volatile const unsigned long long *)a.gh_word;
+            const bool open = (uint32_t)cur < (uint32_t)((cur >> 32) & 0xffffull) && (gen < 0 || (int)(cur >> 48) == gen);
+            old = open ? atomicAdd(a.gh_word, 1ull) : cur | 0xffffffffull;
+        }
+        old = __shfl_sync(FULL, old, 0);
+        const int g = (int)(old >> 48);
+        const uint32_t nch = (uint32_t)((old >> 32) & 0xffffull), idx = (uint32_t)old;   // unsigned: a closed step reads 0xffffffff
+        if (seen_gen) *seen_gen = g;
+        if (idx >= nch || (gen >= 0 && g != gen)) break;
+        const int slot = g & (GH_RING - 1);
+        const GhTask *tp = own;
+        if (!own) {
+            fence_acq_rel();                              // acquire: the post precedes the chunk's reads
+            const uint4 *src = (const uint4 *)(a.gh_task + slot);
+            uint4 *dst = (uint4 *)&t;
+#pragma unroll
+            for (int i = 0; i < (int)(sizeof(GhTask) / 16); ++i) dst[i] = __ldcg(src + i);
+            tp = &t;
+        }
+        bool ok = tp->gen == g;
+        if (!ok) set_status(a.status, ST_INVAL);
+        else if (idx >= (uint32_t)tp->nch) { set_status(a.status, ST_INVAL); ok = false; }
+        else {
+            const long long c0 = a.profile && !own ? clock64() : 0;
+            ok = gh_do(a, *tp, (int)idx, slice, keep);
+            if (a.profile && !own && lane == 0 && a.stats && tp->op >= 1 && tp->op <= 12) {
+                const unsigned long long dc = (unsigned long long)(clock64() - c0);
+                atomicAdd(a.stats + 80 + tp->op, dc);
+                atomicAdd(a.stats + 96 + tp->op, 1ull);
+                if (runs > 0) { atomicAdd(a.stats + 112 + tp->op, dc); atomicAdd(a.stats + 128 + tp->op, 1ull); }
+            }
+        }
+        __threadfence();                                  // release the chunk's writes
+        __syncwarp();
+        if (lane == 0) atomicAdd(a.gh_done + 32 * slot, 1u);
+        ++runs;
+        if (!ok || read_status(a.status) != ST_OK) break;
+    }
+    return runs;
+}
+
+// Helper side, from an idle worker's poll loop: the hint is read inline, the
+// claims run out of line only when a post was seen.
+__device__ __noinline__ int gh_help(const ElimArgs &a, unsigned char *slice, int *seen_gen)
+{
+    int32_t keep = -2;
+    const int runs = gh_claim_loop(a, nullptr, -1, slice, keep, seen_gen);
+    if (a.stats && lane_id() == 0 && runs > 0) atomicAdd(a.stats + 25, (unsigned long long)runs);
+    return runs;
+}
+
+__device__ __forceinline__ int gh_serve(const ElimArgs &a, unsigned char *slice, uint32_t &seen, uint32_t h)
+{
+    if (h == 0u || h == seen) return 0;
+    int g = -1;
+    const int runs = gh_help(a, slice, &g);
+    if (g == (int)(h & 0xffffu)) seen = h;     // the word had reached the hinted step (else look again)
+    return runs;
+}
+
+// Owner side: post step `op` over n items in chunks of `chunk` (from the
+// task in cs.gt), run chunks with every warp of the CTA, wait for the rest.
+// false: the kernel must stop.
+__device__ __noinline__ bool gh_phase(const ElimArgs &a, CoopShared &cs, int op, int n, int chunk, unsigned char *slice,
+                         int32_t &keep)
+{
+    const int tid = threadIdx.x;
+    if (n <= 0) return true;
+    if ((n + chunk - 1) / chunk > 0xffff) chunk = (n + 0xfffe) / 0xffff;
+    const int nch = (n + chunk - 1) / chunk;
+    const long long c0 = a.profile ? clock64() : 0;
+    if (tid == 0) {
+        const int gen = (int)((cs.gh_gen + 1u) & 0xffffu);
+        cs.gh_gen = (uint32_t)gen;
+        GhTask &t = *cs.gt;
+        t.gen = gen; t.op = op; t.n = n; t.chunk = chunk; t.nch = nch;
+        const int slot = gen & (GH_RING - 1);
+        const uint4 *src = (const uint4 *)&t;
+        uint4 *dst = (uint4 *)(a.gh_task + slot);
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(GhTask) / 16); ++i) dst[i] = src[i];
+        a.gh_done[32 * slot] = 0u;
+        __threadfence();                                  // release: the step's inputs and descriptor
+        atomicExch(a.gh_word, ((unsigned long long)gen << 48) | ((unsigned long long)nch << 32));
+        // relaxed hints: a helper that sees one before the word counts the
+        // step as seen only once the word shows its generation
+        for (int h = 0; h < GH_HINTS; ++h) *(volatile uint32_t *)(a.gh_hint + 32 * h) = (uint32_t)gen | 0x10000u;
+    }
+    __syncthreads();
+    const int gen = (int)cs.gh_gen;
+    const long long c1 = a.profile ? clock64() : 0;
+    const int runs = gh_claim_loop(a, cs.gt, gen, slice, keep);
+    if (a.stats && lane_id() == 0 && runs > 0) atomicAdd(a.stats + 26, (unsigned long long)runs);
+    const long long c2 = a.profile ? clock64() : 0;
+    if (tid == 0) {
+        const uint32_t *done = a.gh_done + 32 * (gen & (GH_RING - 1));
+        long long spins = 0;
+        while (ld_acquire_u32(done) < (uint32_t)nch) {
+            ++spins;
+            if ((spins & 63) == 0) {
+                if (read_status(a.status) != ST_OK) break;
+                if (spins > a.spin_limit) { set_status(a.status, ST_TIMEOUT); break; }
+            }
+            if (spins > 256) __nanosleep(32);
+        }
+        fence_acq_rel();                                  // acquire: the helpers' results
+        if (a.profile && a.stats && op >= 1 && op <= 12) {
+            unsigned long long *ps = a.stats + 32 + 4 * (op - 1);
+            atomicAdd(ps + 0, (unsigned long long)(c1 - c0));
+            atomicAdd(ps + 1, (unsigned long long)(c2 - c1));
+            atomicAdd(ps + 2, (unsigned long long)(clock64() - c2));
+            atomicAdd(ps + 3, 1ull);
+        }
+    }
+    return !__syncthreads_or(read_status(a.status) != ST_OK);
+}
+
+// Splitters of a sample sort posted for helpers: SS evenly spaced entries of
+// v[0, n) sorted in the CTA's shared tile, every stride-th one kept.  Zeroes
+// the bucket counters.  Returns B.
+template <int KEY>
+__device__ __noinline__ int gh_splitters(const GhTask &t, View v, int n, View tile, int cap, int wcap, int slice_bytes,
+                            CoopShared &cs)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    int B = next_pow2((2 * n + wcap - 1) / wcap);
+    if (B > cap / 4) B = cap / 4;
+    if (B < 1) B = 1;
+    int SS = 8 * B;
+    if (SS < 256) SS = 256;
+    if (SS > cap) SS = cap;
+    const int lg = __ffs(SS) - 1;
+    for (int s2 = tid; s2 < SS; s2 += nt) {
+        const int i = (int)(((long long)s2 * n) >> lg);
+        tile.row[s2] = __ldcg(v.row + i);
+        tile.w[s2] = __ldcg(v.w + i);
+        if (KEY == 1) tile.mult[s2] = __ldcg(v.mult + i);
+    }
+    __syncthreads();
+    coop_sort<KEY>(tile, SS, tile, 0);
+    const int stride = SS / B;
+    for (int b = tid; b < B; b += nt) {
+        t.spl_row[b] = tile.row[b * stride];
+        t.spl_wb[b] = dbits(tile.w[b * stride]);
+        t.cnt_b[b] = 0;
+        t.cur_b[b] = 0;
+    }
+    if (tid == 0) {
+        cs.gt->B = B;
+        cs.gt->spl_shared = (KEY == 0 ? 4 * B : 12 * B) <= slice_bytes && B <= 2 * REG_BUCKET_MAX ? 1 : 0;
+    }
+    __syncthreads();
+    return B;
+}
+
+// Bucket offsets from the counts (gbo[0..B]), the oversized buckets (gbig)
+// listed in cs.nbig.
+__device__ __noinline__ void gh_bucket_scan(const GhTask &t, int n, int B, int bmax, int *gbig, CoopShared &cs)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) cs.nbig = 0;
+    __syncthreads();
+    for (int b = tid; b < B; b += nt) {
+        const int c = __ldcg(t.cnt_b + b);          // counted by other SMs: read through L2
+        t.gbo[b] = c;
+        if (c > bmax) gbig[atomicAdd(&cs.nbig, 1)] = b;
+    }
+    __syncthreads();
+    block_excl_scan(t.gbo, B, t.gbo, cs);
+    if (tid == 0) t.gbo[B] = n;
+    __syncthreads();
+}
+
+// Cooperative elimination of a vertex offered to the grid (the CTA holds the
+// board's lock).  Same results as coop_eliminate's global-memory path.
+__device__ __noinline__ int32_t gh_eliminate(const ElimArgs &a, CoopShared &cs, unsigned char *bbuf, WarpState &ws,
+                                             long long &tp)
+{
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    // the working set and its arrays in the CTA's scratch, laid out as by coop_eliminate
+    const int32_t k = cs.k;
+    const int64_t o0 = __ldg(a.lcp + k);
+    const int32_t norig = (int32_t)(__ldg(a.lcp + k + 1) - o0);
+    const uint32_t cnt = __ldcg(a.fcnt + k);
+    const int P = next_pow2(norig + (int)cnt);
+    const View v = make_view(a.scratch + cs.sbase, P);
+    double *tiles = (double *)(a.scratch + cs.sbase + (size_t)P * ENTRY_BYTES);
+    int *gbo = (int *)(((uintptr_t)(tiles + (P / 32 + 1)) + 15) & ~(uintptr_t)15);
+    int *gbd = gbo + a.block_cap + 1;
+    int *gbig = gbd + a.block_cap + 1;
+    unsigned char *ghx = (unsigned char *)(((uintptr_t)(gbig + a.block_cap + 1) + 15) & ~(uintptr_t)15);
+    const bool requester = warp == cs.req_warp;
+    auto mark = [&](int phase) {
+        if (!requester) return;
+        prof_mark(a, ws, phase);
+        if (a.trace_phase && lane == 0) {
+            const long long t = clock64();
+            a.trace_phase[8 * (size_t)k + (phase - 8)] = (int32_t)(t - tp);
+            tp = t;
+        }
+    };
+    const int cap = a.block_cap, wcap = cap / nw;
+    const int slice_bytes = a.warp_cap * ENTRY_BYTES;
+    unsigned char *slice = bbuf - (size_t)(nw - warp) * slice_bytes;
+    const View tile = make_view(bbuf, cap);
+    const int g = norig + (int)cnt;
+    int32_t keep = requester ? -1 : -2;
+    // extra scratch: tile maxima, splitters, bucket counters, compacted offsets
+    const int ntile_cap = P / 32 + 1;
+    GhTask *gtask = (GhTask *)ghx;
+    unsigned long long *tmax = (unsigned long long *)(ghx + sizeof(GhTask));
+    unsigned long long *spl_wb = tmax + ntile_cap;
+    int32_t *spl_row = (int32_t *)(spl_wb + cap);
+    int32_t *cnt_b = spl_row + cap, *cur_b = cnt_b + cap, *pd = cur_b + cap;
+    unsigned long long *coarse = (unsigned long long *)(((uintptr_t)(pd + cap) + 15) & ~(uintptr_t)15);
+    if (tid == 0) cs.gt = gtask;
+    __syncthreads();
+    if (tid == 0) {
+        GhTask &t = *cs.gt;
+        t.k = k; t.d = 0; t.cap = P; t.norig = norig; t.cnt = cnt; t.o0 = o0;
+        t.bmax = wcap < REG_BUCKET_MAX ? wcap : REG_BUCKET_MAX;
+        t.slice = slice_bytes; t.lk = 0; t.fpos = 0; t.Dk = 0.0; t.klocal = 0; t.sys = 0;
+        t.vbase = (unsigned char *)v.w; t.tiles = tiles; t.tmax = tmax;
+        t.gbo = gbo; t.gbd = gbd; t.pd = pd; t.cnt_b = cnt_b; t.cur_b = cur_b; t.spl_row = spl_row; t.spl_wb = spl_wb;
+        t.coarse = coarse; t.nco = 0; t.cstride = 1;
+        t.B = 0; t.spl_shared = 0;
+    }
+    if (tid == 0 && a.stats) atomicAdd(a.stats + 24, 1ull);
+    __syncthreads();
+    const int bmax = cs.gt->bmax;
+    auto fail = [&]() -> int32_t {
+        __syncthreads();
+        if (tid == 0) { __threadfence(); atomicExch(a.gh_lock, 0); cs.k = -1; }
+        return -2;
+    };
+    double *tS = v.S;
+    unsigned long long *tM = (unsigned long long *)v.M;
+
+    // ---------------------------------------------------------------- gather
+    if (!gh_phase(a, cs, GH_GATHER, P, 256, slice, keep)) return fail();
+    mark(9);
+
+    // ---------------------------------------------------------------- rows: sort, merge, compact, store
+    const int wcap_gh = wcap < 128 ? wcap : 128;          // buckets of ~64 entries for the helpers' rank sorts
+    int B = gh_splitters<0>(*cs.gt, v, g, tile, cap, wcap_gh, slice_bytes, cs);
+    if (!gh_phase(a, cs, GH_COUNT0, g, 128, slice, keep)) return fail();
+    gh_bucket_scan(*cs.gt, g, B, bmax, gbig, cs);
+    if (!gh_phase(a, cs, GH_SCATTER0, g, 128, slice, keep)) return fail();
+    for (int q = 0; q < cs.nbig; ++q) {                     // oversized buckets: the whole CTA
+        const int b = gbig[q];
+        const int o = gbo[b], cb = gbo[b + 1] - o;
+        const View w = sort_big_bucket<0>(v, tile, cap, o, cb);
+        if (warp == 0) {
+            const int db = warp_merge_bucket(w, cb, tS, tM, o);
+            if (lane == 0) gbd[b] = db;
+        }
+        __syncthreads();
+    }
+    if (!gh_phase(a, cs, GH_ROWB, B, 1, slice, keep)) return fail();
+    for (int b = tid; b < B; b += nt) pd[b] = __ldcg(gbd + b);
+    __syncthreads();
+    const int d = block_excl_scan(pd, B, pd, cs);
+    if (tid == 0) {
+        const unsigned long long base = d > 0 ? atomicAdd(a.f_top, (unsigned long long)d) : 0ull;
+        if (d > 0 && base + d > a.f_cap) set_status(a.status, ST_POOL);
+        cs.gt->fpos = base; cs.gt->d = d;
+    }
+    if (__syncthreads_or(read_status(a.status) != ST_OK)) return fail();
+    if (!gh_phase(a, cs, GH_COMPACT, B, 1, slice, keep)) return fail();
+    if (tid == 0) { a.f_start[k] = (int64_t)cs.gt->fpos; a.f_len[k] = d; }
+    mark(10); mark(11);
+    if (d == 0) {
+        if (tid == 0) a.D[k] = 0.0;
+        __syncthreads();
+        if (tid == 0) { __threadfence(); atomicExch(a.gh_lock, 0); cs.k = -1; }
+        return -1;
+    }
+
+    // ---------------------------------------------------------------- weights
+    if (d <= (cap < 1024 ? cap : 1024)) {                 // one shared tile
+        const int Pd = next_pow2(d);
+        for (int i = tid; i < Pd; i += nt) {
+            if (i < d) { tile.row[i] = __ldcg(v.row + i); tile.w[i] = __ldcg(v.w + i); tile.mult[i] = __ldcg(v.mult + i); }
+            else { tile.row[i] = ROW_SENTINEL; tile.w[i] = __longlong_as_double((long long)WBITS_SENTINEL); tile.mult[i] = 0; }
+        }
+        __syncthreads();
+        coop_sort<1>(tile, Pd, tile, 0);
+        for (int i = tid; i < d; i += nt) { v.row[i] = tile.row[i]; v.w[i] = tile.w[i]; v.mult[i] = tile.mult[i]; }
+        __syncthreads();
+    } else {
+        B = gh_splitters<1>(*cs.gt, v, d, tile, cap, wcap_gh, slice_bytes, cs);
+        if (!gh_phase(a, cs, GH_COUNT1, d, 128, slice, keep)) return fail();
+        gh_bucket_scan(*cs.gt, d, B, bmax, gbig, cs);
+        if (!gh_phase(a, cs, GH_SCATTER1, d, 128, slice, keep)) return fail();
+        for (int q = 0; q < cs.nbig; ++q) {
+            const int b = gbig[q];
+            const int o = gbo[b], cb = gbo[b + 1] - o;
+            const View w = sort_big_bucket<1>(v, tile, cap, o, cb);
+            for (int i = tid; i < cb; i += nt) {
+                tS[o + i] = w.w[i];
+                tM[o + i] = (unsigned long long)(uint32_t)w.row[i] | ((unsigned long long)(uint32_t)w.mult[i] << 32);
+            }
+            __syncthreads();
+        }
+        if (!gh_phase(a, cs, GH_WB, B, 1, slice, keep)) return fail();
+    }
+    mark(12);
+
+    // ---------------------------------------------------------------- canonical suffix scan, running maximum
+    const int ntile = (d + 31) / 32;
+    if (!gh_phase(a, cs, GH_TILES, ntile, 4, slice, keep)) return fail();
+    if (tid == 0) {            // serial carry chain over the tile totals
+        double carry = 0.0;
+        for (int j0 = 0; j0 < ntile; j0 += 8) {
+            double tot[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) tot[q] = j0 + q < ntile ? __ldcg(tiles + j0 + q) : 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (j0 + q < ntile) { tiles[j0 + q] = carry; carry = __dadd_rn(tot[q], carry); }
+        }
+    }
+    __syncthreads();
+    if (!gh_phase(a, cs, GH_CARRYMAX, ntile, 4, slice, keep)) return fail();
+    if (tid == 0) {            // running maximum over the tiles before each tile
+        unsigned long long run = 0ull;
+        for (int j0 = 0; j0 < ntile; j0 += 8) {
+            unsigned long long tm[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) tm[q] = j0 + q < ntile ? __ldcg(tmax + j0 + q) : 0ull;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (j0 + q < ntile) { tmax[j0 + q] = run; if (tm[q] > run) run = tm[q]; }
+        }
+        const double Dk = __ldcg(v.S);
+        a.D[k] = Dk;
+        cs.gt->Dk = Dk;
+        cs.gt->lk = __ldcg(a.lvl + k) + 1;
+        uint64_t klocal, sys;
+        sys_of(a, k, klocal, sys);
+        cs.gt->klocal = klocal; cs.gt->sys = sys;
+        const int cst = (d + GH_COARSE - 1) / GH_COARSE;
+        cs.gt->cstride = cst; cs.gt->nco = (d + cst - 1) / cst;
+    }
+    __syncthreads();
+    {                          // coarse copy of M_final for the sampling searches
+        const int cst = cs.gt->cstride, nco = cs.gt->nco;
+        for (int c = tid; c < nco; c += nt) {
+            const int j = c * cst;
+            const unsigned long long m = dbits(__ldcg(v.M + j)), tm = tmax[(d - 1 - j) >> 5];
+            coarse[c] = m > tm ? m : tm;
+        }
+    }
+    __syncthreads();
+    mark(13);
+
+    // ---------------------------------------------------------------- sampling, fill, levels
+    if (!gh_phase(a, cs, GH_SAMPLE, d, 32, slice, keep)) return fail();
+    if (tid == 0) ws.n_fill += (unsigned long long)(d - 1) * (unsigned long long)a.samples;
+    mark(14);
+
+    // ---------------------------------------------------------------- decrements (every append is done and released)
+    if (!gh_phase(a, cs, GH_DECR, d, 64, slice, keep)) return fail();
+    __syncthreads();
+    if (tid == 0) { __threadfence(); atomicExch(a.gh_lock, 0); cs.k = -1; }
+    mark(15);
+    return requester ? (keep >= 0 ? keep : -1) : -1;
 }
 
 // Cooperative elimination of cs.k by every warp of the CTA (the callers have
@@ -1407,8 +2343,7 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
         v = make_view(bbuf, a.block_cap);
         tiles = (double *)(bbuf + (size_t)a.block_cap * ENTRY_BYTES);
     } else {
-        const unsigned long long need = (unsigned long long)P * ENTRY_BYTES + ((unsigned long long)P / 32 + 1) * 8 +
-                                        16ull + 4ull * (3ull * (unsigned long long)a.block_cap + 3ull);
+        const unsigned long long need = coop_scratch_bytes(P, a.block_cap, false);
         if (tid == 0 && cs.scap < need) {
             const unsigned long long base = atomicAdd(a.scratch_top, (need + 255ull) & ~255ull);
             if (base + need > a.scratch_cap) set_status(a.status, ST_POOL);
@@ -1422,6 +2357,7 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     int *gbo = (int *)(((uintptr_t)(tiles + (P / 32 + 1)) + 15) & ~(uintptr_t)15);
     int *gbd = gbo + a.block_cap + 1;
     int *gbig = gbd + a.block_cap + 1;
+
 
     // ---------------------------------------------------------------- gather
     for (int i = tid; i < norig; i += nt) { v.row[i] = __ldg(a.lrow + o0 + i); v.w[i] = __ldg(a.lw + o0 + i); }
@@ -1691,9 +2627,57 @@ __device__ __noinline__ int32_t coop_eliminate(const ElimArgs &a, CoopShared &cs
     return requester ? (keep >= 0 ? keep : -1) : -1;
 }
 
+// A cooperative request flagged for grid help: join as coop_eliminate does,
+// take the board (else eliminate the vertex in the CTA alone), set up the
+// larger working set and run gh_eliminate.
+__device__ __noinline__ int32_t gh_entry(const ElimArgs &a, CoopShared &cs, unsigned char *bbuf, WarpState &ws)
+{
+    const int tid = threadIdx.x;
+    long long tp = 0;
+    if (a.trace_phase) tp = clock64();
+    if (!cta_barrier(cs, a)) return -2;
+    __syncthreads();
+    if (tid == 0) {
+        cs.gh = atomicCAS(a.gh_lock, 0, 1) == 0 ? 1 : 0;
+        if (cs.gh) { fence_acq_rel(); cs.gh_gen = (uint32_t)(__ldcg(a.gh_word) >> 48); }
+    }
+    __syncthreads();
+    if (!cs.gh) return coop_eliminate(a, cs, bbuf, ws);     // every warp; it joins again
+    const int32_t k = cs.k;
+    const int warp = tid >> 5, lane = tid & 31;
+    if (warp == cs.req_warp) {
+        prof_mark(a, ws, 8);
+        if (a.trace_phase && lane == 0) {
+            const long long t = clock64();
+            a.trace_phase[8 * (size_t)k] = (int32_t)(t - tp);
+            tp = t;
+        }
+    }
+    const int P = next_pow2((int)(__ldg(a.lcp + k + 1) - __ldg(a.lcp + k)) + (int)__ldcg(a.fcnt + k));
+    const unsigned long long need = coop_scratch_bytes(P, a.block_cap, true);
+    if (tid == 0 && cs.scap < need) {
+        const unsigned long long base = atomicAdd(a.scratch_top, (need + 255ull) & ~255ull);
+        if (base + need > a.scratch_cap) set_status(a.status, ST_POOL);
+        cs.sbase = base; cs.scap = need;
+    }
+    if (__syncthreads_or(read_status(a.status) != ST_OK)) {
+        __syncthreads();
+        if (tid == 0) { __threadfence(); atomicExch(a.gh_lock, 0); cs.k = -1; }
+        return -2;
+    }
+    return gh_eliminate(a, cs, bbuf, ws, tp);
+}
+
+// Dispatch of a joined cooperative request.
+__device__ __forceinline__ int32_t coop_dispatch(const ElimArgs &a, CoopShared &cs, unsigned char *bbuf, WarpState &ws)
+{
+    return vol(cs.gh_req) ? gh_entry(a, cs, bbuf, ws) : coop_eliminate(a, cs, bbuf, ws);
+}
+
 // Join a pending cooperative request of this CTA, if there is one this warp
 // has not served yet.  Returns -3 if there was none, else coop_eliminate's
 // result for a helper (-1, or -2 on abort).
+template <bool GH>
 __device__ __forceinline__ int32_t serve_help(const ElimArgs &a, CoopShared &cs, int &seen_gen, unsigned char *bbuf,
                                               WarpState &ws)
 {
@@ -1701,17 +2685,22 @@ __device__ __forceinline__ int32_t serve_help(const ElimArgs &a, CoopShared &cs,
     if (g == seen_gen) return -3;
     seen_gen = g;
     ++ws.n_block;
-    return coop_eliminate(a, cs, bbuf, ws);
+    return GH ? coop_dispatch(a, cs, bbuf, ws) : coop_eliminate(a, cs, bbuf, ws);
 }
 
+// GH: the instantiation with grid help (idle warps serve the board, large
+// working sets are offered to it); the other one has none of that code.
+template <bool GH>
 __global__ void __launch_bounds__(256, 2) elim_kernel(ElimArgs a, int fchunk)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int block_lock;
     __shared__ CoopShared cs;
+    __shared__ uint32_t gh_seen[8];        // grid help: last posting hint each warp has served
     const int warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const unsigned lane = lane_id();
+    if (threadIdx.x < 8) gh_seen[threadIdx.x] = 0u;
     if (threadIdx.x == 0) {
         block_lock = 0;
         cs.k = -1; cs.gen = 0; cs.req_warp = -1; cs.arrive = 0; cs.sbase = 0; cs.scap = 0;
@@ -1737,7 +2726,7 @@ __global__ void __launch_bounds__(256, 2) elim_kernel(ElimArgs a, int fchunk)
     int32_t next = -1;                     // vertex handed to this warp by its last pivot
     for (;;) {
         if (a.coop) {
-            const int32_t h = serve_help(a, cs, seen_gen, bbuf, ws);
+            const int32_t h = serve_help<GH>(a, cs, seen_gen, bbuf, ws);
             if (h == -2) break;
         }
         int32_t k;
@@ -1767,16 +2756,23 @@ __global__ void __launch_bounds__(256, 2) elim_kernel(ElimArgs a, int fchunk)
             // never enter the queue): the wait ends when every vertex has
             // been eliminated.
             k = -1;
+            // grid help: one warp in gh_mask + 1 reads the posting hint, in
+            // the same round trip as its queue slot
+            const int gwarp = (int)blockIdx.x * nw + warp;
+            const bool gh_on = GH && a.grid_help > 0 && (gwarp & a.gh_mask) == 0;
             for (;;) {
+                uint32_t hint = 0u;
+                if (!claims_done) k = *(volatile const int32_t *)(a.queue + slot);
+                if (gh_on && lane == 0) hint = *(volatile const uint32_t *)(a.gh_hint + 32 * (gwarp & (GH_HINTS - 1)));
                 if (!claims_done) {
-                    k = *(volatile const int32_t *)(a.queue + slot);
                     if (__shfl_sync(FULL, k, 0) >= 0) { k = __shfl_sync(FULL, k, 0); break; }
                 }
                 if (a.coop) {
-                    const int32_t h = serve_help(a, cs, seen_gen, bbuf, ws);
+                    const int32_t h = serve_help<GH>(a, cs, seen_gen, bbuf, ws);
                     if (h == -2) { stop = true; break; }
                     if (h != -3) spins = 0;
                 }
+                if (GH && gh_on && gh_serve(a, wbuf, gh_seen[warp], __shfl_sync(FULL, hint, 0)) > 0) spins = 0;
                 if ((++spins & 63) == 0) {
                     if (read_status(a.status) != ST_OK) { stop = true; break; }
                     const uint32_t t = *(volatile const uint32_t *)a.q_tail;
@@ -1815,16 +2811,19 @@ __global__ void __launch_bounds__(256, 2) elim_kernel(ElimArgs a, int fchunk)
                 int posted = 0;
                 if (lane == 0 && atomicCAS(&cs.k, -1, k) == -1) {
                     cs.req_warp = warp;
+                    // grid help for working sets in global scratch (large enough)
+                    cs.gh_req = GH && a.grid_help > 0 && g >= a.grid_help && next_pow2(g) > a.block_cap &&
+                                a.sample_sort && a.block_cap >= 256 && !a.hash_store;
                     __threadfence_block();
                     posted = atomicAdd(&cs.gen, 1) + 1;
                 }
                 posted = __shfl_sync(FULL, posted, 0);
                 if (posted) {
                     seen_gen = posted;
-                    r = coop_eliminate(a, cs, bbuf, ws);
+                    r = GH ? coop_dispatch(a, cs, bbuf, ws) : coop_eliminate(a, cs, bbuf, ws);
                     ++ws.n_global;
                 } else {
-                    const int32_t h = serve_help(a, cs, seen_gen, bbuf, ws);
+                    const int32_t h = serve_help<GH>(a, cs, seen_gen, bbuf, ws);
                     if (h == -2) { r = -2; break; }
                     if (h == -3) __nanosleep(32);
                 }
@@ -1875,15 +2874,23 @@ size_t elim_smem_bytes(int warps_per_block, int warp_cap, int block_cap)
 cudaError_t elim_configure(int warps_per_block, int warp_cap, int block_cap, int *blocks_per_sm)
 {
     const size_t smem = elim_smem_bytes(warps_per_block, warp_cap, block_cap);
-    cudaError_t e = cudaFuncSetAttribute(elim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(elim_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, elim_kernel, warps_per_block * 32, smem);
+    e = cudaFuncSetAttribute(elim_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int b0 = 0, b1 = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, elim_kernel<false>, warps_per_block * 32, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, elim_kernel<true>, warps_per_block * 32, smem);
+    *blocks_per_sm = b0 < b1 ? b0 : b1;
+    return e;
 }
 
 cudaError_t elim_launch(const ElimArgs &a, int blocks, int warps_per_block, int fchunk, cudaStream_t st)
 {
     const size_t smem = elim_smem_bytes(warps_per_block, a.warp_cap, a.block_cap);
-    elim_kernel<<<blocks, warps_per_block * 32, smem, st>>>(a, fchunk);
+    if (a.grid_help > 0) elim_kernel<true><<<blocks, warps_per_block * 32, smem, st>>>(a, fchunk);
+    else elim_kernel<false><<<blocks, warps_per_block * 32, smem, st>>>(a, fchunk);
     count_launches(1);
     return cudaGetLastError();
 }
