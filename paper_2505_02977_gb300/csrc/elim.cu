@@ -1540,25 +1540,96 @@ __device__ __forceinline__ int gh_bucket(const int32_t *sr, const unsigned long 
     return lo;
 }
 
+// Splitters 1..B-1 of the posted sample sort into the warp's slice when they
+// fit (rows from the slice's start, weight bits from byte 2048), a lane's
+// loads in flight together.  Returns true when they stay in global memory.
+template <int KEY>
+__device__ __forceinline__ bool gh_stage(const GhTask &t, unsigned char *slice, const int32_t *&sr,
+                                         const unsigned long long *&sw)
+{
+    sr = t.spl_row; sw = t.spl_wb;
+    if (!t.spl_shared) return true;
+    const int lane = (int)lane_id();
+    int32_t *lr = (int32_t *)slice;
+    unsigned long long *lw = (unsigned long long *)(slice + 8 * REG_BUCKET_MAX);
+    for (int b0 = 0; b0 < t.B; b0 += 256) {
+        int32_t x[8];
+        unsigned long long y[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int b = b0 + 32 * q + lane;
+            x[q] = b < t.B ? __ldcg(t.spl_row + b) : 0;
+            y[q] = KEY == 1 && b < t.B ? __ldcg(t.spl_wb + b) : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int b = b0 + 32 * q + lane;
+            if (b < t.B) { lr[b] = x[q]; if (KEY == 1) lw[b] = y[q]; }
+        }
+    }
+    __syncwarp();
+    sr = lr; sw = lw;
+    return false;
+}
+
+// Count Q entries per lane (ok[q]: the entry exists) into their buckets:
+// one atomic per bucket and warp step, all in flight together.
+template <int KEY, int Q>
+__device__ __forceinline__ void gh_count(const GhTask &t, const int32_t *sr, const unsigned long long *sw, bool glob,
+                                         const int32_t (&r)[Q], const unsigned long long (&wb)[Q], const bool (&ok)[Q])
+{
+    const int lane = (int)lane_id();
+    int bk[Q];
+    unsigned grp[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        bk[q] = ok[q] ? gh_bucket<KEY>(sr, sw, t.B, glob, r[q], wb[q]) : -1;
+        grp[q] = __match_any_sync(FULL, bk[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+        if (bk[q] >= 0 && lane == __ffs(grp[q]) - 1) atomicAdd(t.cnt_b + bk[q], __popc(grp[q]));
+}
+
+// Entry i of column k's gathered list: its original lower entries, then its
+// fill by append index (inline slab, then the overflow levels; gi is the
+// level's directory entry, loaded beforehand).
+__device__ __forceinline__ uint32_t gh_fill_dir(const ElimArgs &a, int32_t k, int norig, int g, int i)
+{
+    const uint32_t f = (uint32_t)(i - norig);
+    if (i < norig || i >= g || f < (uint32_t)FILL_C0) return 0u;
+    const int j = fill_level(f);
+    return j <= FILL_LEVELS ? __ldcg(a.dir + (size_t)k * FILL_LEVELS + (j - 1)) : 0u;
+}
+
+__device__ __forceinline__ void gh_src_entry(const ElimArgs &a, int32_t k, int norig, int g, int64_t o0, int i,
+                                             uint32_t gi, int32_t &r, double &w)
+{
+    r = ROW_SENTINEL; w = 0.0;
+    if (i < norig) {
+        r = __ldg(a.lrow + o0 + i); w = __ldg(a.lw + o0 + i);
+    } else if (i < g) {
+        const uint32_t f = (uint32_t)(i - norig);
+        if (f < (uint32_t)FILL_C0) {
+            r = __ldcg(a.in_row + (size_t)k * FILL_C0 + f); w = __ldcg(a.in_w + (size_t)k * FILL_C0 + f);
+        } else if (gi == 0u || gi == 0xffffffffu) {
+            set_status(a.status, ST_INVAL);
+        } else {
+            const unsigned long long at = (unsigned long long)(gi - 1u) * FILL_GRANULE + (f - fill_level_start(fill_level(f)));
+            r = __ldcg(a.pool_row + at); w = __ldcg(a.pool_w + at);
+        }
+    }
+}
+
 // Count (SCATTER = false) or scatter one chunk of entries into their buckets.
 template <int KEY, bool SCATTER>
 __device__ void gh_partition_chunk(const GhTask &t, int lo, int hi, unsigned char *slice)
 {
     const int lane = (int)lane_id();
     const View v = make_view(t.vbase, t.cap);
-    const int32_t *sr = t.spl_row;
-    const unsigned long long *sw = t.spl_wb;
-    const bool glob = !t.spl_shared;
-    if (!glob) {                                   // stage the splitters in the slice
-        int32_t *lr = (int32_t *)slice;
-        unsigned long long *lw = (unsigned long long *)(slice + 4 * (size_t)REG_BUCKET_MAX * 2);
-        for (int b = lane; b < t.B; b += 32) {
-            lr[b] = __ldcg(t.spl_row + b);
-            if (KEY == 1) lw[b] = __ldcg(t.spl_wb + b);
-        }
-        __syncwarp();
-        sr = lr; sw = lw;
-    }
+    const int32_t *sr;
+    const unsigned long long *sw;
+    const bool glob = gh_stage<KEY>(t, slice, sr, sw);
     double *tS = v.S;
     unsigned long long *tM = (unsigned long long *)v.M;
     for (int i0 = lo; i0 < hi; i0 += 8 * 32) {
@@ -1621,52 +1692,39 @@ __device__ __noinline__ bool gh_do(const ElimArgs &a, const GhTask &t, int idx, 
     unsigned long long *tM = (unsigned long long *)v.M;
     const int d = t.d;
     switch (t.op) {
-    case GH_GATHER: {                                         // 8 entries per lane in flight
+    case GH_GATHER: {                                         // gather, and count the row sort's buckets
+        const int32_t *sr;
+        const unsigned long long *sw;
+        const bool glob = gh_stage<0>(t, slice, sr, sw);
         const int k = t.k, norig = t.norig, g = t.norig + (int)t.cnt;
-        for (int base = lo; base < hi; base += 256) {
-            uint32_t gi[8];
+        for (int base = lo; base < hi; base += 128) {
+            uint32_t gi[4];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < 4; ++q) {
                 const int i = base + 32 * q + lane;
-                const uint32_t f = (uint32_t)(i - norig);
-                gi[q] = 0u;
-                if (i < hi && i >= norig && i < g && f >= (uint32_t)FILL_C0) {
-                    const int j = fill_level(f);
-                    gi[q] = j <= FILL_LEVELS ? __ldcg(a.dir + (size_t)k * FILL_LEVELS + (j - 1)) : 0u;
-                }
+                gi[q] = i < hi ? gh_fill_dir(a, k, norig, g, i) : 0u;
             }
-            int32_t r[8];
-            double w[8];
+            int32_t r[4];
+            double w[4];
+            unsigned long long wb[4];
+            bool ok[4];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < 4; ++q) {
                 const int i = base + 32 * q + lane;
-                r[q] = ROW_SENTINEL; w[q] = 0.0;
-                if (i >= hi) continue;
-                if (i < norig) {
-                    r[q] = __ldg(a.lrow + t.o0 + i); w[q] = __ldg(a.lw + t.o0 + i);
-                } else if (i < g) {
-                    const uint32_t f = (uint32_t)(i - norig);
-                    if (f < (uint32_t)FILL_C0) {
-                        r[q] = __ldcg(a.in_row + (size_t)k * FILL_C0 + f); w[q] = __ldcg(a.in_w + (size_t)k * FILL_C0 + f);
-                    } else if (gi[q] == 0u || gi[q] == 0xffffffffu) {
-                        set_status(a.status, ST_INVAL);
-                    } else {
-                        const int j = fill_level(f);
-                        const unsigned long long at = (unsigned long long)(gi[q] - 1u) * FILL_GRANULE + (f - fill_level_start(j));
-                        r[q] = __ldcg(a.pool_row + at); w[q] = __ldcg(a.pool_w + at);
-                    }
-                }
+                gh_src_entry(a, k, norig, g, t.o0, i < hi ? i : g, gi[q], r[q], w[q]);
+                wb[q] = 0ull;
+                ok[q] = i < hi && i < g;
             }
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < 4; ++q) {
                 const int i = base + 32 * q + lane;
                 if (i < hi) { v.row[i] = r[q]; v.w[i] = w[q]; }
             }
+            gh_count<0, 4>(t, sr, sw, glob, r, wb, ok);
         }
+        __syncwarp();
         return true;
     }
-    case GH_COUNT0: gh_partition_chunk<0, false>(t, lo, hi, slice); return true;
-    case GH_COUNT1: gh_partition_chunk<1, false>(t, lo, hi, slice); return true;
     case GH_SCATTER0: gh_partition_chunk<0, true>(t, lo, hi, slice); return true;
     case GH_SCATTER1: gh_partition_chunk<1, true>(t, lo, hi, slice); return true;
     case GH_ROWB: {
@@ -1688,28 +1746,39 @@ __device__ __noinline__ bool gh_do(const ElimArgs &a, const GhTask &t, int idx, 
         }
         return true;
     }
-    case GH_COMPACT: {
+    case GH_COMPACT: {                                        // compaction + F store (+ the weight sort's counts)
+        const int32_t *sr = nullptr;
+        const unsigned long long *sw = nullptr;
+        const bool count = t.B > 0;
+        const bool glob = count ? gh_stage<1>(t, slice, sr, sw) : true;
         for (int b = lo; b < hi; ++b) {
             const int o = __ldcg(t.gbo + b), db = __ldcg(t.gbd + b), p0 = __ldcg(t.pd + b);
-            for (int i0 = 0; i0 < db; i0 += 256) {
-                unsigned long long rm[8];
-                double x[8];
+            for (int i0 = 0; i0 < db; i0 += 128) {
+                unsigned long long rm[4];
+                double x[4];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
+                for (int q = 0; q < 4; ++q) {
                     const int i = i0 + 32 * q + lane;
                     rm[q] = i < db ? __ldcg(tM + o + i) : 0ull;
                     x[q] = i < db ? __ldcg(tS + o + i) : 0.0;
                 }
+                int32_t r[4];
+                unsigned long long wb[4];
+                bool ok[4];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
+                for (int q = 0; q < 4; ++q) {
                     const int i = i0 + 32 * q + lane;
+                    r[q] = (int32_t)(uint32_t)rm[q];
+                    wb[q] = dbits(x[q]);
+                    ok[q] = i < db;
                     if (i >= db) continue;
-                    const int32_t r = (int32_t)(uint32_t)rm[q];
-                    v.row[p0 + i] = r; v.w[p0 + i] = x[q]; v.mult[p0 + i] = (int32_t)(rm[q] >> 32);
-                    a.f_row[t.fpos + p0 + i] = r; a.f_val[t.fpos + p0 + i] = x[q];
+                    v.row[p0 + i] = r[q]; v.w[p0 + i] = x[q]; v.mult[p0 + i] = (int32_t)(rm[q] >> 32);
+                    a.f_row[t.fpos + p0 + i] = r[q]; a.f_val[t.fpos + p0 + i] = x[q];
                 }
+                if (count) gh_count<1, 4>(t, sr, sw, glob, r, wb, ok);
             }
         }
+        __syncwarp();
         return true;
     }
     case GH_WB: {
@@ -2054,11 +2123,15 @@ __device__ __noinline__ bool gh_phase(const ElimArgs &a, CoopShared &cs, int op,
 }
 
 // Splitters of a sample sort posted for helpers: SS evenly spaced entries of
-// v[0, n) sorted in the CTA's shared tile, every stride-th one kept.  Zeroes
-// the bucket counters.  Returns B.
-template <int KEY>
-__device__ __noinline__ int gh_splitters(const GhTask &t, View v, int n, View tile, int cap, int wcap, int slice_bytes,
-                            CoopShared &cs)
+// the n to be sorted, sorted in the CTA's shared tile, every stride-th one
+// kept; zeroes the bucket counters.  The entries are read from v (SRC 0),
+// from the column's sources before the gather (SRC 1: original entries, then
+// fill by append index), or from the merged row buckets before compaction
+// (SRC 2: entry i lies in the last bucket b with pd[b] <= i, at gbo[b] + i -
+// pd[b] of the temporaries).  Returns B.
+template <int KEY, int SRC>
+__device__ __noinline__ int gh_splitters(const ElimArgs &a, const GhTask &t, View v, int n, View tile, int cap, int wcap,
+                                         int slice_bytes, CoopShared &cs, int nrow = 0)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     int B = next_pow2((2 * n + wcap - 1) / wcap);
@@ -2068,11 +2141,36 @@ __device__ __noinline__ int gh_splitters(const GhTask &t, View v, int n, View ti
     if (SS < 256) SS = 256;
     if (SS > cap) SS = cap;
     const int lg = __ffs(SS) - 1;
+    int *spd = (int *)tile.S, *sbo = (int *)tile.M;       // SRC 2: bucket offsets staged in unused tile arrays
+    if (SRC == 2) {
+        for (int b = tid; b < nrow; b += nt) { spd[b] = t.pd[b]; sbo[b] = t.gbo[b]; }
+        __syncthreads();
+    }
     for (int s2 = tid; s2 < SS; s2 += nt) {
         const int i = (int)(((long long)s2 * n) >> lg);
-        tile.row[s2] = __ldcg(v.row + i);
-        tile.w[s2] = __ldcg(v.w + i);
-        if (KEY == 1) tile.mult[s2] = __ldcg(v.mult + i);
+        if (SRC == 0) {
+            tile.row[s2] = __ldcg(v.row + i);
+            tile.w[s2] = __ldcg(v.w + i);
+            if (KEY == 1) tile.mult[s2] = __ldcg(v.mult + i);
+        } else if (SRC == 1) {
+            const int g = t.norig + (int)t.cnt;
+            int32_t r;
+            double w;
+            gh_src_entry(a, t.k, t.norig, g, t.o0, i, gh_fill_dir(a, t.k, t.norig, g, i), r, w);
+            tile.row[s2] = r; tile.w[s2] = w;
+            if (KEY == 1) tile.mult[s2] = 1;
+        } else {
+            int lo = 0, hi = nrow - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (spd[mid] <= i) lo = mid; else hi = mid - 1;
+            }
+            const int pos = sbo[lo] + (i - spd[lo]);
+            const unsigned long long rm = __ldcg((const unsigned long long *)v.M + pos);
+            tile.row[s2] = (int32_t)(uint32_t)rm;
+            tile.w[s2] = __ldcg(v.S + pos);
+            if (KEY == 1) tile.mult[s2] = (int32_t)(rm >> 32);
+        }
     }
     __syncthreads();
     coop_sort<KEY>(tile, SS, tile, 0);
@@ -2174,14 +2272,14 @@ __device__ __noinline__ int32_t gh_eliminate(const ElimArgs &a, CoopShared &cs, 
     double *tS = v.S;
     unsigned long long *tM = (unsigned long long *)v.M;
 
-    // ---------------------------------------------------------------- gather
-    if (!gh_phase(a, cs, GH_GATHER, P, 256, slice, keep)) return fail();
+    // ---------------------------------------------------------------- gather, with the row sort's counts
+    // (its splitters sampled from the column's sources)
+    const int wcap_gh = wcap < 128 ? wcap : 128;          // buckets of ~64 entries for the helpers' rank sorts
+    int B = gh_splitters<0, 1>(a, *cs.gt, v, g, tile, cap, wcap_gh, slice_bytes, cs);
+    if (!gh_phase(a, cs, GH_GATHER, P, 128, slice, keep)) return fail();
     mark(9);
 
     // ---------------------------------------------------------------- rows: sort, merge, compact, store
-    const int wcap_gh = wcap < 128 ? wcap : 128;          // buckets of ~64 entries for the helpers' rank sorts
-    int B = gh_splitters<0>(*cs.gt, v, g, tile, cap, wcap_gh, slice_bytes, cs);
-    if (!gh_phase(a, cs, GH_COUNT0, g, 128, slice, keep)) return fail();
     gh_bucket_scan(*cs.gt, g, B, bmax, gbig, cs);
     if (!gh_phase(a, cs, GH_SCATTER0, g, 128, slice, keep)) return fail();
     for (int q = 0; q < cs.nbig; ++q) {                     // oversized buckets: the whole CTA
@@ -2204,18 +2302,27 @@ __device__ __noinline__ int32_t gh_eliminate(const ElimArgs &a, CoopShared &cs, 
         cs.gt->fpos = base; cs.gt->d = d;
     }
     if (__syncthreads_or(read_status(a.status) != ST_OK)) return fail();
-    if (!gh_phase(a, cs, GH_COMPACT, B, 1, slice, keep)) return fail();
     if (tid == 0) { a.f_start[k] = (int64_t)cs.gt->fpos; a.f_len[k] = d; }
-    mark(10); mark(11);
     if (d == 0) {
+        mark(10); mark(11);
         if (tid == 0) a.D[k] = 0.0;
         __syncthreads();
         if (tid == 0) { __threadfence(); atomicExch(a.gh_lock, 0); cs.k = -1; }
         return -1;
     }
+    const bool small_d = d <= (cap < 1024 ? cap : 1024);
+    const int Brow = B;
+    if (small_d) {                                         // compaction alone
+        if (tid == 0) cs.gt->B = 0;
+        __syncthreads();
+    } else {                                               // the weight sort's splitters, sampled from the row buckets
+        B = gh_splitters<1, 2>(a, *cs.gt, v, d, tile, cap, wcap_gh, slice_bytes, cs, Brow);
+    }
+    if (!gh_phase(a, cs, GH_COMPACT, Brow, 1, slice, keep)) return fail();
+    mark(10); mark(11);
 
     // ---------------------------------------------------------------- weights
-    if (d <= (cap < 1024 ? cap : 1024)) {                 // one shared tile
+    if (small_d) {                                         // one shared tile
         const int Pd = next_pow2(d);
         for (int i = tid; i < Pd; i += nt) {
             if (i < d) { tile.row[i] = __ldcg(v.row + i); tile.w[i] = __ldcg(v.w + i); tile.mult[i] = __ldcg(v.mult + i); }
@@ -2226,8 +2333,6 @@ __device__ __noinline__ int32_t gh_eliminate(const ElimArgs &a, CoopShared &cs, 
         for (int i = tid; i < d; i += nt) { v.row[i] = tile.row[i]; v.w[i] = tile.w[i]; v.mult[i] = tile.mult[i]; }
         __syncthreads();
     } else {
-        B = gh_splitters<1>(*cs.gt, v, d, tile, cap, wcap_gh, slice_bytes, cs);
-        if (!gh_phase(a, cs, GH_COUNT1, d, 128, slice, keep)) return fail();
         gh_bucket_scan(*cs.gt, d, B, bmax, gbig, cs);
         if (!gh_phase(a, cs, GH_SCATTER1, d, 128, slice, keep)) return fail();
         for (int q = 0; q < cs.nbig; ++q) {
