@@ -838,6 +838,7 @@ static_assert(sizeof(CoopShared) <= 320, "static shared memory of the eliminatio
 __device__ __forceinline__ volatile int &vol(int &x) { return *(volatile int *)&x; }
 
 constexpr int GH_COARSE = 512;   // coarse entries of the sampling search (one 4 KB warp slice)
+constexpr long long GH_GRACE_NS = 3000;   // the owner's warps leave a step's chunks to the helpers this long
 
 // Bytes of a CTA's global working set of P entries: the entries, the scan
 // tiles, bucket offsets / merged counts / oversized list; with grid help
@@ -2096,6 +2097,19 @@ __device__ __noinline__ bool gh_phase(const ElimArgs &a, CoopShared &cs, int op,
     __syncthreads();
     const int gen = (int)cs.gh_gen;
     const long long c1 = a.profile ? clock64() : 0;
+    // the helpers take the chunks; the owner's warps claim only what is still
+    // unclaimed GH_GRACE_NS after the post (so a step never depends on helpers)
+    {
+        const long long t0 = global_ns();
+        for (;;) {
+            unsigned long long cur = 0;
+            if (lane_id() == 0) cur = *(volatile const unsigned long long *)a.gh_word;
+            cur = __shfl_sync(FULL, cur, 0);
+            if ((uint32_t)cur >= (uint32_t)nch || read_status(a.status) != ST_OK) break;
+            if (global_ns() - t0 > GH_GRACE_NS) break;
+            __nanosleep(100);
+        }
+    }
     const int runs = gh_claim_loop(a, cs.gt, gen, slice, keep);
     if (a.stats && lane_id() == 0 && runs > 0) atomicAdd(a.stats + 26, (unsigned long long)runs);
     const long long c2 = a.profile ? clock64() : 0;
