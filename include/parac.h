@@ -159,6 +159,10 @@ enum { PARAC_ORDER_GIVEN = 0, PARAC_ORDER_NNZ = 1 };
  *                   force it.  The factor is the same either way.
  *   grid_help_min   gathered entries from which a vertex is offered (0: every
  *                   working set in global scratch)
+ *   host_tables     PARAC_ON: the group tables of the warp-per-row solves
+ *                   (factors with rows of more than 2,048 entries) are built
+ *                   by a host pass over the factor's pointers, as a reference
+ *                   for the default device builder; the tables are the same.
  */
 typedef struct {
     int32_t kind;
@@ -189,6 +193,7 @@ typedef struct {
     int32_t order;
     int32_t grid_help;
     int32_t grid_help_min;
+    int32_t host_tables;
 } parac_opts;
 
 void parac_opts_default(parac_opts *opts);

@@ -266,6 +266,7 @@ struct parac_factor_s {
     int32_t check_every = 8;
     int32_t trsv_blocks = 0, poll_ns = 64;             // solve schedule (parac_opts)
     int32_t pcg_graph = 0, pcg_many = 0, pcg_workers = 4;
+    bool host_tables = false;                          // solve group tables built on the host (reference builder)
     cudaStream_t stream = nullptr;
     DBuf perm, Fcp, Frow, Fval, D, Lp, Li, Lv;          // label space (export) and the matrix
     DBuf Lev;                                          // dependency level of each column
@@ -315,6 +316,7 @@ Opts read_opts(const parac_opts *in)
     if (r.o.order != PARAC_ORDER_NNZ) r.o.order = PARAC_ORDER_GIVEN;
     if (r.o.idle_ns < 0) r.o.idle_ns = 0;
     if (r.o.grid_help_min < 0) r.o.grid_help_min = 0;
+    if (r.o.host_tables != PARAC_ON) r.o.host_tables = PARAC_DEFAULT;
     if (r.o.trsv_blocks < 0) r.o.trsv_blocks = 0;
     r.o.poll_ns = r.o.poll_ns <= 0 ? 64 : std::max(16, std::min(100000, r.o.poll_ns));
     r.o.pcg_workers = r.o.pcg_workers <= 0 ? 4 : std::min(64, r.o.pcg_workers);
@@ -703,6 +705,26 @@ std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_ind
 void build_group_tables(parac_factor_s *h, cudaStream_t st)
 {
     const int64_t n = h->n;
+    if (!h->host_tables) {                 // built on the device by scans (row_groups_count / _write)
+        DBuf tmp(row_groups_tmp_bytes(n), st);
+        int64_t ngf = 0, nsf = 0, ngb = 0, nsb = 0;
+        CK(row_groups_count(h->Srp.as<int64_t>(), n, false, SOLVE_WARPS, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE,
+                            tmp.p, &ngf, &nsf, st));
+        h->sgt_f = dalloc<int32_t>((size_t)(4 * ngf), st);
+        CK(row_groups_write(h->Srp.as<int64_t>(), n, false, SOLVE_WARPS, SPLIT_ROW_SINGLE, CHUNK_SINGLE, tmp.p,
+                            h->sgt_f.as<int32_t>(), st));
+        CK(row_groups_count(h->Scp.as<int64_t>(), n, true, SOLVE_WARPS, LONG_ROW_SINGLE, SPLIT_ROW_SINGLE, CHUNK_SINGLE,
+                            tmp.p, &ngb, &nsb, st));
+        h->sgt_b = dalloc<int32_t>((size_t)(4 * ngb), st);
+        CK(row_groups_write(h->Scp.as<int64_t>(), n, true, SOLVE_WARPS, SPLIT_ROW_SINGLE, CHUNK_SINGLE, tmp.p,
+                            h->sgt_b.as<int32_t>(), st));
+        h->spart_f = dalloc<double>((size_t)std::max<int64_t>(nsf, 1), st);
+        h->spart_b = dalloc<double>((size_t)std::max<int64_t>(nsb, 1), st);
+        CK(cudaStreamSynchronize(st));     // tmp is released on return
+        h->sng_f = (int32_t)ngf; h->sng_b = (int32_t)ngb;
+        h->snslot_f = (int32_t)nsf; h->snslot_b = (int32_t)nsb;
+        return;
+    }
     std::vector<int64_t> rp((size_t)n + 1), cp((size_t)n + 1);
     CK(cudaMemcpyAsync(rp.data(), h->Srp.p, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(cp.data(), h->Scp.p, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
@@ -920,7 +942,7 @@ void finish_batch(std::vector<std::unique_ptr<parac_factor_s>> &hs, FactorOut &f
         h->n = n; h->prec = prec; h->spin_limit = O.o.spin_limit; h->sptrsv = O.o.sptrsv;
         h->check_every = O.o.check_every; h->stream = st;
         h->trsv_blocks = O.o.trsv_blocks; h->poll_ns = O.o.poll_ns; h->pcg_graph = O.o.pcg_graph;
-        h->pcg_many = O.o.pcg_many; h->pcg_workers = O.o.pcg_workers;
+        h->pcg_many = O.o.pcg_many; h->pcg_workers = O.o.pcg_workers; h->host_tables = O.o.host_tables == PARAC_ON;
         h->nnzF = nf; h->nnzL = nl;
         const size_t m1 = (size_t)std::max<int64_t>(n, 1), f1 = (size_t)std::max<int64_t>(nf, 1), l1 = (size_t)std::max<int64_t>(nl, 1);
         h->Fcp = dalloc<int64_t>((size_t)n + 1, st); h->Frow = dalloc<int32_t>(f1, st); h->Fval = dalloc<double>(f1, st);
@@ -989,13 +1011,14 @@ std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_ind
              "\"coop_gather\": %llu, \"coop_row_sort\": %llu, \"coop_merge_store\": %llu, "
              "\"coop_weight_sort\": %llu, \"coop_scan\": %llu, \"coop_sample_append\": %llu, "
              "\"coop_release\": %llu}, \"grid_help_vertices\": %llu, \"grid_help_chunks_helpers\": %llu, "
-             "\"grid_help_chunks_owner\": %llu}",
+             "\"grid_help_chunks_owner\": %llu, \"solve_groups\": [%d, %d, %d, %d]}",
              (long long)h->n, (long long)h->nnzF, (long long)(h->nnzF + h->n), (long long)fo.nl,
              (long long)fo.nnz_low, fo.stats[3], fo.pool_used, fo.f_used, fo.scratch_used, fo.stats[0], fo.stats[1],
              fo.stats[2], fo.stats[5], fo.stats[6], fo.stats[4], fo.regrows, fo.max_lower_column, fo.blocks, fo.warps, h->prec, fo.samples, fo.fill_store, sys_index, fo.t_ingest, fo.t_elim,
              fo.t_compact, h->depth, h->max_row, fo.stats[8], fo.stats[9], fo.stats[10], fo.stats[11], fo.stats[12],
              fo.stats[13], fo.stats[14], fo.stats[15], fo.stats[16], fo.stats[17], fo.stats[18], fo.stats[19],
-             fo.stats[20], fo.stats[21], fo.stats[22], fo.stats[23], fo.stats[24], fo.stats[25], fo.stats[26]);
+             fo.stats[20], fo.stats[21], fo.stats[22], fo.stats[23], fo.stats[24], fo.stats[25], fo.stats[26], h->sng_f, h->sng_b,
+             h->snslot_f, h->snslot_b);
     std::string out = buf;
     if (fo.stats[24] > 0 && (fo.stats[32] | fo.stats[33] | fo.stats[34]) != 0) {
         // grid-help step profile (timing >= 2): per step, the owner's post /
@@ -1101,7 +1124,7 @@ parac_status parac_factor(int64_t n, const int64_t *colptr, const int32_t *rowin
         h->n = n; h->prec = O.o.g_precision; h->spin_limit = O.o.spin_limit; h->sptrsv = O.o.sptrsv;
         h->check_every = O.o.check_every; h->stream = st;
         h->trsv_blocks = O.o.trsv_blocks; h->poll_ns = O.o.poll_ns; h->pcg_graph = O.o.pcg_graph;
-        h->pcg_many = O.o.pcg_many; h->pcg_workers = O.o.pcg_workers;
+        h->pcg_many = O.o.pcg_many; h->pcg_workers = O.o.pcg_workers; h->host_tables = O.o.host_tables == PARAC_ON;
         DView<int64_t> cp; cp.set(colptr, (size_t)n + 1, st);
         int64_t nnz = 0;
         if (n > 0) {
@@ -1471,7 +1494,27 @@ void ensure_block_cache(parac_factor_s *G, const SolveArgs &A, int nrhs, cudaStr
 void ensure_block_groups(parac_factor_s *G, int warps, cudaStream_t st)
 {
     BlockCache &c = G->bcache;
-    if (c.g_warps != warps) {
+    if (c.g_warps != warps && !G->host_tables) {         // built on the device
+        const int64_t n = G->n;
+        DBuf tmp(row_groups_tmp_bytes(n), st);
+        int64_t ngf = 0, nsf = 0, ngb = 0, nsb = 0;
+        CK(row_groups_count(G->Srp.as<int64_t>(), n, false, warps, LONG_ROW_BLOCK, SPLIT_ROW_BLOCK, CHUNK_BLOCK, tmp.p,
+                            &ngf, &nsf, st));
+        c.gt_f = dalloc<int32_t>((size_t)(4 * ngf), st);
+        CK(row_groups_write(G->Srp.as<int64_t>(), n, false, warps, SPLIT_ROW_BLOCK, CHUNK_BLOCK, tmp.p,
+                            c.gt_f.as<int32_t>(), st));
+        CK(row_groups_count(G->Scp.as<int64_t>(), n, true, warps, LONG_ROW_BLOCK, SPLIT_ROW_BLOCK, CHUNK_BLOCK, tmp.p,
+                            &ngb, &nsb, st));
+        c.gt_b = dalloc<int32_t>((size_t)(4 * ngb), st);
+        CK(row_groups_write(G->Scp.as<int64_t>(), n, true, warps, SPLIT_ROW_BLOCK, CHUNK_BLOCK, tmp.p,
+                            c.gt_b.as<int32_t>(), st));
+        c.part_f = dalloc<double>((size_t)std::max<int64_t>(nsf, 1) * 32, st);
+        c.part_b = dalloc<double>((size_t)std::max<int64_t>(nsb, 1) * 32, st);
+        CK(cudaStreamSynchronize(st));
+        c.ng_f = (int32_t)ngf; c.ng_b = (int32_t)ngb;
+        c.nslot_f = (int32_t)nsf; c.nslot_b = (int32_t)nsb;
+        c.g_warps = warps;
+    } else if (c.g_warps != warps) {                     // the host builder
         const size_t n = (size_t)G->n;
         std::vector<int64_t> rp(n + 1), cp(n + 1);
         CK(cudaMemcpyAsync(rp.data(), G->Srp.p, 8 * (n + 1), cudaMemcpyDeviceToHost, st));

@@ -299,6 +299,79 @@ __global__ void k_dinv(int32_t n, const double *D, double *Dinv)
         Dinv[t] = D[t] > 0.0 ? 1.0 / D[t] : 0.0;
 }
 
+// ---------------------------------------------------------------- solve group tables on the device
+// The group table of row_groups (schedule.cpp) built by scans: walk position
+// kk takes row j = kk (or n - 1 - kk descending) of `ptr`.  A row longer than
+// long_row is "long"; a maximal run of short positions is cut into groups of
+// `warps` consecutive positions from the run's start; a long row emits one
+// shared group, or (above split_row) nch = ceil(len / chunk) chunk groups
+// followed by their combine, with nch partial slots.  Groups are emitted at
+// their first position, in walk order.
+__global__ void k_rg_mark(const int64_t *ptr, int64_t n, int desc, int long_row, int split_row, int chunk,
+                          int32_t *islong, int32_t *cntL, int32_t *slots)
+{
+    for (int64_t kk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; kk < n; kk += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = desc ? n - 1 - kk : kk;
+        const int64_t len = ptr[j + 1] - ptr[j];
+        const bool lng = len > long_row;
+        const int32_t nch = (int32_t)((len + chunk - 1) / chunk);
+        islong[kk] = lng ? 1 : 0;
+        cntL[kk] = lng ? (len > split_row ? nch + 1 : 1) : 0;
+        slots[kk] = lng && len > split_row ? nch : 0;
+    }
+}
+
+__global__ void k_rg_longpos(int64_t n, const int32_t *islong, const int64_t *lrank, int64_t *longpos)
+{
+    for (int64_t kk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; kk < n; kk += (int64_t)gridDim.x * blockDim.x)
+        if (islong[kk]) longpos[lrank[kk]] = kk;
+}
+
+// groups emitted at each position (cntL for long rows, 1 where a short group starts)
+__global__ void k_rg_count(int64_t n, int warps, const int32_t *islong, const int64_t *lrank, const int64_t *longpos,
+                           int32_t *cnt)
+{
+    for (int64_t kk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; kk < n; kk += (int64_t)gridDim.x * blockDim.x) {
+        if (islong[kk]) continue;
+        const int64_t r = lrank[kk];
+        const int64_t prev = r > 0 ? longpos[r - 1] : -1;
+        cnt[kk] = ((kk - prev - 1) % warps) == 0 ? 1 : 0;
+    }
+}
+
+__global__ void k_rg_write(const int64_t *ptr, int64_t n, int desc, int warps, int split_row, int chunk,
+                           const int32_t *islong, const int64_t *lrank, const int64_t *longpos, const int64_t *goff,
+                           const int64_t *soff, int32_t *g)
+{
+    for (int64_t kk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; kk < n; kk += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g0 = goff[kk];
+        if (!islong[kk]) {
+            if (goff[kk + 1] == g0) continue;                // no group starts here
+            const int64_t r = lrank[kk], nlong = lrank[n];
+            const int64_t next = r < nlong ? longpos[r] : n;
+            const int64_t rows = next - kk < warps ? next - kk : warps;
+            int32_t *e = g + 4 * g0;
+            e[0] = (int32_t)kk; e[1] = GK_ROWS; e[2] = (int32_t)rows; e[3] = 0;
+            continue;
+        }
+        const int64_t j = desc ? n - 1 - kk : kk;
+        const int64_t len = ptr[j + 1] - ptr[j];
+        if (len > split_row) {
+            const int32_t nch = (int32_t)((len + chunk - 1) / chunk);
+            const int32_t s0 = (int32_t)soff[kk];
+            for (int32_t c = 0; c < nch; ++c) {
+                int32_t *e = g + 4 * (g0 + c);
+                e[0] = (int32_t)kk; e[1] = GK_CHUNK; e[2] = c; e[3] = s0 + c;
+            }
+            int32_t *e = g + 4 * (g0 + nch);
+            e[0] = (int32_t)kk; e[1] = GK_COMBINE; e[2] = nch; e[3] = s0;
+        } else {
+            int32_t *e = g + 4 * g0;
+            e[0] = (int32_t)kk; e[1] = GK_SHARED; e[2] = 0; e[3] = 0;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_out_of_label_single(int32_t nl, int32_t n, int32_t *o, cudaStream_t st)
@@ -476,6 +549,59 @@ cudaError_t launch_dinv(int32_t n, const double *D, double *Dinv, cudaStream_t s
 {
     if (n == 0) return cudaSuccess;
     k_dinv<<<grid_for(n, 256), 256, 0, st>>>(n, D, Dinv); count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- solve group tables on the device
+size_t row_groups_tmp_bytes(int64_t n)
+{
+    const size_t n1 = (size_t)n + 1;
+    return 3 * 4 * n1 + 4 * 8 * n1 + scan_tmp_bytes(n + 1) + 1024;
+}
+
+// First pass: counts (ngroups, nslots), read back to the host (one small copy).
+cudaError_t row_groups_count(const int64_t *ptr, int64_t n, bool descending, int warps, int long_row, int split_row,
+                             int chunk, void *tmp, int64_t *ngroups, int64_t *nslots, cudaStream_t st)
+{
+    *ngroups = 0; *nslots = 0;
+    if (n <= 0) return cudaSuccess;
+    const size_t n1 = (size_t)n + 1;
+    unsigned char *t = (unsigned char *)tmp;
+    int32_t *islong = (int32_t *)t, *cnt = islong + n1, *slots = cnt + n1;
+    int64_t *lrank = (int64_t *)(((uintptr_t)(slots + n1) + 15) & ~(uintptr_t)15);
+    int64_t *longpos = lrank + n1, *goff = longpos + n1, *soff = goff + n1;
+    void *stmp = (void *)(((uintptr_t)(soff + n1) + 255) & ~(uintptr_t)255);
+    const int gr = grid_for(n, 256);
+    k_rg_mark<<<gr, 256, 0, st>>>(ptr, n, descending ? 1 : 0, long_row, split_row, chunk, islong, cnt, slots);
+    count_launches(1);
+    cudaError_t e = scan_i32_to_i64(islong, lrank, n, stmp, st);
+    if (e != cudaSuccess) return e;
+    k_rg_longpos<<<gr, 256, 0, st>>>(n, islong, lrank, longpos); count_launches(1);
+    k_rg_count<<<gr, 256, 0, st>>>(n, warps, islong, lrank, longpos, cnt); count_launches(1);
+    e = scan_i32_to_i64(cnt, goff, n, stmp, st);
+    if (e != cudaSuccess) return e;
+    e = scan_i32_to_i64(slots, soff, n, stmp, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(ngroups, goff + n, 8, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(nslots, soff + n, 8, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+// Second pass: the table (4 ints per group) from the first pass's scans in tmp.
+cudaError_t row_groups_write(const int64_t *ptr, int64_t n, bool descending, int warps, int split_row, int chunk,
+                             const void *tmp, int32_t *table, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const size_t n1 = (size_t)n + 1;
+    const unsigned char *t = (const unsigned char *)tmp;
+    const int32_t *islong = (const int32_t *)t, *slots = islong + 2 * n1;
+    const int64_t *lrank = (const int64_t *)(((uintptr_t)(slots + n1) + 15) & ~(uintptr_t)15);
+    const int64_t *longpos = lrank + n1, *goff = longpos + n1, *soff = goff + n1;
+    k_rg_write<<<grid_for(n, 256), 256, 0, st>>>(ptr, n, descending ? 1 : 0, warps, split_row, chunk, islong, lrank,
+                                                  longpos, goff, soff, table);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -156,6 +156,15 @@ struct SolveArgs {
 constexpr int LONG_ROW_SINGLE = 512, SPLIT_ROW_SINGLE = 32768, CHUNK_SINGLE = 8192;
 constexpr int LONG_ROW_BLOCK = 64, SPLIT_ROW_BLOCK = 1024, CHUNK_BLOCK = 512;
 constexpr int SOLVE_WARPS = 8;        // warps per block of the solves (default)
+// Group table of the one-row-per-warp solves (row_groups of schedule.cpp)
+// built on the device: row_groups_count runs the scans in tmp
+// (row_groups_tmp_bytes(n)) and returns the group and slot counts;
+// row_groups_write then fills table[4 * ngroups] from the same tmp.
+size_t row_groups_tmp_bytes(int64_t n);
+cudaError_t row_groups_count(const int64_t *ptr, int64_t n, bool descending, int warps, int long_row, int split_row,
+                             int chunk, void *tmp, int64_t *ngroups, int64_t *nslots, cudaStream_t st);
+cudaError_t row_groups_write(const int64_t *ptr, int64_t n, bool descending, int warps, int split_row, int chunk,
+                             const void *tmp, int32_t *table, cudaStream_t st);
 // thread-per-row solves: used for factors whose rows and columns all have at
 // most TPR_MAX_ROW entries; blocks of 256 threads
 constexpr int TPR_MAX_ROW = 2048, TPR_THREADS = 256;

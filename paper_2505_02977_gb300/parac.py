@@ -32,7 +32,8 @@ class parac_opts(C.Structure):
                 ("block_cap", C.c_int32), ("coop", C.c_int32), ("sample_sort", C.c_int32), ("idle_ns", C.c_int32),
                 ("trace_path", C.c_char_p), ("trsv_blocks", C.c_int32), ("poll_ns", C.c_int32),
                 ("pcg_graph", C.c_int32), ("pcg_many", C.c_int32), ("pcg_workers", C.c_int32),
-                ("order", C.c_int32), ("grid_help", C.c_int32), ("grid_help_min", C.c_int32)]
+                ("order", C.c_int32), ("grid_help", C.c_int32), ("grid_help_min", C.c_int32),
+                ("host_tables", C.c_int32)]
 
 DEFAULT, ON, OFF = 0, 1, 2
 ORDER_GIVEN, ORDER_NNZ = 0, 1

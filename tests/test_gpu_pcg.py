@@ -374,3 +374,37 @@ def test_pcg_many_batched_maxit(P):
         assert abs(_relres(A, xs[i], b) - rrs[i]) <= 1e-6 * rrs[i]
     for G in Gs:
         G.free()
+
+
+@pytest.mark.parametrize("n", [40000, 120000])
+def test_device_group_tables_match_host(P, n):
+    """The warp-per-row solves' group tables (factors with rows of more than
+    2,048 entries) built on the device equal the host builder's: the same
+    group and partial-slot counts, and preconditioner applies and block PCG
+    solves (which walk those tables, and the block solves' own ones) that
+    agree to rounding.  Not bit for bit: the hub row's CSR entries keep
+    their scatter order, so two factorisations sum it in different orders;
+    a wrong table (a group's start or row count) would show as a wrong
+    solve or a bounded-wait timeout.  The hub row is longer than the split
+    length, so chunk and combine groups are exercised."""
+    A, perm, b = _hub_system(n, 7)
+    r = np.ascontiguousarray(b, np.float64).reshape(-1)
+    Bm = W.gaussian_rhs(n, 4, 9, center=False)
+    out = []
+    for host in (P.ON, P.DEFAULT):
+        G = P.parac_factor(n, A.colptr, A.rowind, A.val, perm, 3,
+                           P.parac_opts_default(host_tables=host, sptrsv=P.SPTRSV_WARP))
+        st = G.stats()
+        z = P.parac_precond_apply(G, r)
+        X, it, rr, status = P.parac_pcg(G, n, A.colptr, A.rowind, A.val, Bm, tol=1e-8, maxit=200)
+        out.append((st["solve_groups"], st["max_row_F"], z, X, it))
+        G.free()
+    (g0, m0, z0, X0, it0), (g1, m1, z1, X1, it1) = out
+    assert m0 > 2048 and g0[0] > 0 and g0[1] > 0
+    assert g0 == g1
+    assert g0[2] > 0                           # the hub row (forward solve) is split: partial slots
+    assert np.linalg.norm(z0 - z1) <= 1e-12 * np.linalg.norm(z1)
+    assert np.all(np.abs(np.asarray(it0) - np.asarray(it1)) <= 1)
+    X0, X1 = np.asarray(X0), np.asarray(X1)
+    for j in range(X0.shape[1]):
+        assert np.linalg.norm(X0[:, j] - X1[:, j]) <= 1e-10 * np.linalg.norm(X1[:, j]), j
