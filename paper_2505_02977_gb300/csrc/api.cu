@@ -702,6 +702,19 @@ std::string stats_json(const parac_factor_s *h, const FactorOut &fo, int sys_ind
 // Group tables of the one-row-per-warp solves for a factor with rows longer
 // than 4 x LONG_ROW_SINGLE entries (a host pass over the relabelled factor's
 // row and column pointers).
+// CSR rows of more than 2,048 entries sorted by column as well (the shorter
+// ones are sorted by launch_sort_rows / launch_sort_long_rows), so that the
+// solve arrays are the same on every run.
+void sort_huge_rows(int64_t n, int64_t *rp, int32_t *cols, double *vals, cudaStream_t st)
+{
+    DBuf tmp(huge_rows_tmp_bytes(n), st);
+    int64_t nrows = 0, entries = 0;
+    CK(huge_rows_count((int32_t)n, rp, tmp.p, &nrows, &entries, st));
+    if (nrows == 0) return;
+    DBuf work(huge_rows_sort_bytes(nrows, entries), st);
+    CK(huge_rows_sort((int32_t)n, rp, cols, vals, tmp.p, nrows, entries, work.p, st));
+}
+
 void build_group_tables(parac_factor_s *h, cudaStream_t st)
 {
     const int64_t n = h->n;
@@ -806,6 +819,7 @@ void finish_handle(parac_factor_s *h, int64_t n, int64_t nnzF, const Opts &O)
                                 h->Srp.as<int64_t>(), cnt.as<int32_t>(), h->Scol.as<int32_t>(), h->Svalr.as<double>(), st));
     CK(launch_sort_rows((int32_t)n, h->Srp.as<int64_t>(), h->Scol.as<int32_t>(), h->Svalr.as<double>(), st));
     CK(launch_sort_long_rows((int32_t)n, h->Srp.as<int64_t>(), h->Scol.as<int32_t>(), h->Svalr.as<double>(), st));
+    sort_huge_rows(n, h->Srp.as<int64_t>(), h->Scol.as<int32_t>(), h->Svalr.as<double>(), st);
     // pivots and original indices by position
     DBuf Dpos = dalloc<double>(n1, st);
     CK(launch_gather_f64((int32_t)n, order.as<int32_t>(), h->D.as<double>(), Dpos.as<double>(), st));
@@ -917,6 +931,7 @@ void finish_batch(std::vector<std::unique_ptr<parac_factor_s>> &hs, FactorOut &f
                                 cnt.as<int32_t>(), Scol.as<int32_t>(), Svalr.as<double>(), st));
     CK(launch_sort_rows((int32_t)N, Srp.as<int64_t>(), Scol.as<int32_t>(), Svalr.as<double>(), st));
     CK(launch_sort_long_rows((int32_t)N, Srp.as<int64_t>(), Scol.as<int32_t>(), Svalr.as<double>(), st));
+    sort_huge_rows(N, Srp.as<int64_t>(), Scol.as<int32_t>(), Svalr.as<double>(), st);
     DBuf Dpos = dalloc<double>(n1, st), Sdinv = dalloc<double>(n1, st), Sperm = dalloc<int32_t>(n1, st);
     CK(launch_gather_f64((int32_t)N, order.as<int32_t>(), fo.D.as<double>(), Dpos.as<double>(), st));
     CK(launch_dinv((int32_t)N, Dpos.as<double>(), Sdinv.as<double>(), st));

@@ -372,6 +372,57 @@ __global__ void k_rg_write(const int64_t *ptr, int64_t n, int desc, int warps, i
     }
 }
 
+// ---------------------------------------------------------------- rows above SORT_LONG entries
+// Rows longer than the shared-memory row sort are sorted by column as one
+// segmented sort: their entries gathered into one buffer (segment = the
+// row's rank among them), stably sorted by column, then stably by segment,
+// and written back into their rows.
+__global__ void k_huge_flags(int32_t n, const int64_t *rp, int lim, int32_t *flag, int32_t *len)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = rp[r + 1] - rp[r];
+        flag[r] = l > lim ? 1 : 0;
+        len[r] = l > lim ? (int32_t)l : 0;
+    }
+}
+
+// one block per row (grid-stride over rows); seg_start[s] / seg_row[s]: the
+// segment's first buffer position and its row's first CSR position
+__global__ void k_huge_gather(int32_t n, const int64_t *rp, const int32_t *flag, const int64_t *hrank,
+                              const int64_t *hoff, const int32_t *cols, const double *vals, int32_t *key,
+                              int32_t *idx, int32_t *seg_of, int32_t *tcol, double *tval, int64_t *seg_start,
+                              int64_t *seg_row)
+{
+    for (int32_t r = blockIdx.x; r < n; r += gridDim.x) {
+        if (!flag[r]) continue;
+        const int64_t s = hrank[r], base = hoff[r], start = rp[r], len = rp[r + 1] - start;
+        if (threadIdx.x == 0) { seg_start[s] = base; seg_row[s] = start; }
+        for (int64_t t = threadIdx.x; t < len; t += blockDim.x) {
+            const int32_t c = cols[start + t];
+            key[base + t] = c; idx[base + t] = (int32_t)(base + t); seg_of[base + t] = (int32_t)s;
+            tcol[base + t] = c; tval[base + t] = vals[start + t];
+        }
+    }
+}
+
+__global__ void k_huge_segkeys(int64_t e, const int32_t *idx, const int32_t *seg_of, int32_t *key)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < e; t += (int64_t)gridDim.x * blockDim.x)
+        key[t] = seg_of[idx[t]];
+}
+
+__global__ void k_huge_scatter(int64_t e, const int32_t *idx, const int32_t *seg, const int64_t *seg_start,
+                               const int64_t *seg_row, const int32_t *tcol, const double *tval, int32_t *cols,
+                               double *vals)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < e; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = seg[t], src = idx[t];
+        const int64_t pos = seg_row[s] + (t - seg_start[s]);
+        cols[pos] = tcol[src];
+        vals[pos] = tval[src];
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_out_of_label_single(int32_t nl, int32_t n, int32_t *o, cudaStream_t st)
@@ -601,6 +652,68 @@ cudaError_t row_groups_write(const int64_t *ptr, int64_t n, bool descending, int
     const int64_t *longpos = lrank + n1, *goff = longpos + n1, *soff = goff + n1;
     k_rg_write<<<grid_for(n, 256), 256, 0, st>>>(ptr, n, descending ? 1 : 0, warps, split_row, chunk, islong, lrank,
                                                   longpos, goff, soff, table);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- rows above SORT_LONG entries
+size_t huge_rows_tmp_bytes(int64_t n)
+{
+    const size_t n1 = (size_t)n + 1;
+    return 2 * 4 * n1 + 2 * 8 * n1 + scan_tmp_bytes(n + 1) + 512;
+}
+
+cudaError_t huge_rows_count(int32_t n, const int64_t *rp, void *tmp, int64_t *nrows, int64_t *entries,
+                            cudaStream_t st)
+{
+    *nrows = 0; *entries = 0;
+    if (n <= 0) return cudaSuccess;
+    const size_t n1 = (size_t)n + 1;
+    int32_t *flag = (int32_t *)tmp, *len = flag + n1;
+    int64_t *hrank = (int64_t *)(((uintptr_t)(len + n1) + 15) & ~(uintptr_t)15), *hoff = hrank + n1;
+    void *stmp = (void *)(((uintptr_t)(hoff + n1) + 255) & ~(uintptr_t)255);
+    k_huge_flags<<<grid_for(n, 256), 256, 0, st>>>(n, rp, SORT_LONG, flag, len); count_launches(1);
+    cudaError_t e = scan_i32_to_i64(flag, hrank, n, stmp, st);
+    if (e != cudaSuccess) return e;
+    e = scan_i32_to_i64(len, hoff, n, stmp, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(nrows, hrank + n, 8, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(entries, hoff + n, 8, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+size_t huge_rows_sort_bytes(int64_t nrows, int64_t entries)
+{
+    const size_t e = (size_t)entries;
+    return 4 * 4 * e + 8 * e + 2 * 8 * (size_t)nrows + radix_tmp_bytes(entries) + 1024;
+}
+
+cudaError_t huge_rows_sort(int32_t n, const int64_t *rp, int32_t *cols, double *vals, const void *tmp, int64_t nrows,
+                           int64_t entries, void *work, cudaStream_t st)
+{
+    if (nrows <= 0 || entries <= 0) return cudaSuccess;
+    const size_t n1 = (size_t)n + 1, e = (size_t)entries;
+    const int32_t *flag = (const int32_t *)tmp, *len = flag + n1;
+    const int64_t *hrank = (const int64_t *)(((uintptr_t)(len + n1) + 15) & ~(uintptr_t)15), *hoff = hrank + n1;
+    unsigned char *w = (unsigned char *)work;
+    int32_t *key = (int32_t *)w, *idx = key + e, *seg_of = idx + e, *tcol = seg_of + e;
+    double *tval = (double *)(((uintptr_t)(tcol + e) + 15) & ~(uintptr_t)15);
+    int64_t *seg_start = (int64_t *)(tval + e), *seg_row = seg_start + nrows;
+    void *rtmp = (void *)(((uintptr_t)(seg_row + nrows) + 255) & ~(uintptr_t)255);
+    k_huge_gather<<<std::min(n, 4096), 256, 0, st>>>(n, rp, flag, hrank, hoff, cols, vals, key, idx, seg_of, tcol, tval,
+                                                     seg_start, seg_row);
+    count_launches(1);
+    int cbits = 1, sbits = 1;
+    while (cbits < 31 && ((int64_t)1 << cbits) < (int64_t)n) ++cbits;
+    while (sbits < 31 && ((int64_t)1 << sbits) < nrows) ++sbits;
+    cudaError_t er = stable_sort_pairs((int32_t)entries, key, idx, cbits, rtmp, st);   // by column
+    if (er != cudaSuccess) return er;
+    k_huge_segkeys<<<grid_for(entries, 256), 256, 0, st>>>(entries, idx, seg_of, key); count_launches(1);
+    er = stable_sort_pairs((int32_t)entries, key, idx, sbits, rtmp, st);                // then by row
+    if (er != cudaSuccess) return er;
+    k_huge_scatter<<<grid_for(entries, 256), 256, 0, st>>>(entries, idx, key, seg_start, seg_row, tcol, tval, cols, vals);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -1502,8 +1502,9 @@ __device__ void coop_weight_phase(View v, int d, unsigned char *bbuf, int cap, C
 // counts its chunk done; the owner acquires the done count before the next
 // step.  Data that other SMs wrote are read through L2 (ld.cg).
 enum : int32_t {
-    GH_GATHER = 1, GH_COUNT0, GH_COUNT1, GH_SCATTER0, GH_SCATTER1, GH_ROWB, GH_COMPACT, GH_WB, GH_TILES,
-    GH_CARRYMAX, GH_SAMPLE, GH_DECR
+    // numbered as in the step profile of the statistics (2 and 3 are unused)
+    GH_GATHER = 1, GH_SCATTER0 = 4, GH_SCATTER1, GH_ROWB, GH_COMPACT, GH_WB, GH_TILES, GH_CARRYMAX, GH_SAMPLE,
+    GH_DECR
 };
 static_assert(sizeof(GhTask) % 16 == 0, "task descriptors are copied in 16-byte units");
 
@@ -1622,9 +1623,10 @@ __device__ __forceinline__ void gh_src_entry(const ElimArgs &a, int32_t k, int n
     }
 }
 
-// Count (SCATTER = false) or scatter one chunk of entries into their buckets.
-template <int KEY, bool SCATTER>
-__device__ void gh_partition_chunk(const GhTask &t, int lo, int hi, unsigned char *slice)
+// Scatter one chunk of entries into their buckets (positions from the
+// bucket offsets and per-bucket cursors).
+template <int KEY>
+__device__ void gh_scatter_chunk(const GhTask &t, int lo, int hi, unsigned char *slice)
 {
     const int lane = (int)lane_id();
     const View v = make_view(t.vbase, t.cap);
@@ -1640,8 +1642,8 @@ __device__ void gh_partition_chunk(const GhTask &t, int lo, int hi, unsigned cha
         for (int q = 0; q < 8; ++q) {
             const int i = i0 + 32 * q + lane;
             r[q] = i < hi ? __ldcg(v.row + i) : 0;
-            w[q] = (KEY == 1 || SCATTER) && i < hi ? __ldcg(v.w + i) : 0.0;
-            m[q] = KEY == 1 && SCATTER && i < hi ? __ldcg(v.mult + i) : 0;
+            w[q] = i < hi ? __ldcg(v.w + i) : 0.0;
+            m[q] = KEY == 1 && i < hi ? __ldcg(v.mult + i) : 0;
         }
         unsigned grp[8];
         int base[8];
@@ -1655,12 +1657,9 @@ __device__ void gh_partition_chunk(const GhTask &t, int lo, int hi, unsigned cha
         for (int q = 0; q < 8; ++q) {                      // all of the batch's atomics in flight together
             const int leader = __ffs(grp[q]) - 1;
             base[q] = 0;
-            if (bk[q] >= 0 && lane == leader) {
-                if (!SCATTER) atomicAdd(t.cnt_b + bk[q], __popc(grp[q]));
-                else base[q] = atomicAdd(t.cur_b + bk[q], __popc(grp[q]));
-            }
+            if (bk[q] >= 0 && lane == leader) base[q] = atomicAdd(t.cur_b + bk[q], __popc(grp[q]));
         }
-        if (SCATTER) {
+        {
             int off[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) off[q] = bk[q] >= 0 ? __ldcg(t.gbo + bk[q]) : 0;
@@ -1726,8 +1725,8 @@ __device__ __noinline__ bool gh_do(const ElimArgs &a, const GhTask &t, int idx, 
         __syncwarp();
         return true;
     }
-    case GH_SCATTER0: gh_partition_chunk<0, true>(t, lo, hi, slice); return true;
-    case GH_SCATTER1: gh_partition_chunk<1, true>(t, lo, hi, slice); return true;
+    case GH_SCATTER0: gh_scatter_chunk<0>(t, lo, hi, slice); return true;
+    case GH_SCATTER1: gh_scatter_chunk<1>(t, lo, hi, slice); return true;
     case GH_ROWB: {
         const View sv = slice_view(slice);
         for (int b = lo; b < hi; ++b) {

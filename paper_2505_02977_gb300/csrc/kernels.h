@@ -97,6 +97,16 @@ cudaError_t launch_sort_long_rows(int32_t n, const int64_t *rp, int32_t *cols, d
 // radix_tmp_bytes(n) bytes.
 size_t radix_tmp_bytes(int64_t n);
 cudaError_t stable_sort_pairs(int32_t n, int32_t *keys, int32_t *vals, int key_bits, void *tmp, cudaStream_t st);
+// CSR rows of more than 2,048 entries sorted by column (a segmented sort:
+// by column, then stably by row).  huge_rows_count finds them with scans in
+// tmp (huge_rows_tmp_bytes(n)) and returns their number and total entries;
+// huge_rows_sort then sorts them with `work` of huge_rows_sort_bytes bytes.
+size_t huge_rows_tmp_bytes(int64_t n);
+cudaError_t huge_rows_count(int32_t n, const int64_t *rp, void *tmp, int64_t *nrows, int64_t *entries,
+                            cudaStream_t st);
+size_t huge_rows_sort_bytes(int64_t nrows, int64_t entries);
+cudaError_t huge_rows_sort(int32_t n, const int64_t *rp, int32_t *cols, double *vals, const void *tmp, int64_t nrows,
+                           int64_t entries, void *work, cudaStream_t st);
 cudaError_t launch_scatter_levels(int32_t nl, const int32_t *out_of_label, const int32_t *lvl, int32_t *lev_out,
                                   cudaStream_t st);
 cudaError_t launch_max_i32(const int32_t *a, int64_t n, int32_t *mx, cudaStream_t st);

@@ -382,11 +382,10 @@ def test_device_group_tables_match_host(P, n):
     2,048 entries) built on the device equal the host builder's: the same
     group and partial-slot counts, and preconditioner applies and block PCG
     solves (which walk those tables, and the block solves' own ones) that
-    agree to rounding.  Not bit for bit: the hub row's CSR entries keep
-    their scatter order, so two factorisations sum it in different orders;
-    a wrong table (a group's start or row count) would show as a wrong
-    solve or a bounded-wait timeout.  The hub row is longer than the split
-    length, so chunk and combine groups are exercised."""
+    agree bit for bit (every CSR row, the hub's included, is sorted by
+    column, so two handles of one factor sum in the same order).  The hub
+    row is longer than the split length, so chunk and combine groups are
+    exercised."""
     A, perm, b = _hub_system(n, 7)
     r = np.ascontiguousarray(b, np.float64).reshape(-1)
     Bm = W.gaussian_rhs(n, 4, 9, center=False)
@@ -403,8 +402,6 @@ def test_device_group_tables_match_host(P, n):
     assert m0 > 2048 and g0[0] > 0 and g0[1] > 0
     assert g0 == g1
     assert g0[2] > 0                           # the hub row (forward solve) is split: partial slots
-    assert np.linalg.norm(z0 - z1) <= 1e-12 * np.linalg.norm(z1)
-    assert np.all(np.abs(np.asarray(it0) - np.asarray(it1)) <= 1)
-    X0, X1 = np.asarray(X0), np.asarray(X1)
-    for j in range(X0.shape[1]):
-        assert np.linalg.norm(X0[:, j] - X1[:, j]) <= 1e-10 * np.linalg.norm(X1[:, j]), j
+    assert np.array_equal(z0.view(np.uint64), z1.view(np.uint64))
+    assert np.array_equal(np.asarray(it0), np.asarray(it1))
+    assert np.array_equal(np.asarray(X0).view(np.uint64), np.asarray(X1).view(np.uint64))
