@@ -292,3 +292,65 @@ def test_hybrid_table(lib, seed):
         for j in range(ns):
             for d in deps[s_][j]:
                 assert entry_of[off[s_] + d] < entry_of[off[s_] + j]
+
+
+def scan_row_groups(ptr, descending, warps, long_row, split_row, chunk):
+    """The device builder's construction of the same table (csrc/compact.cu,
+    row_groups_count / row_groups_write), step for step in numpy: long-row
+    flags, their exclusive ranks and compacted positions, groups emitted at
+    each position (a long row's own groups; one where a run of short rows
+    starts a group of `warps`), exclusive offsets of groups and slots, and
+    every group written at its offset."""
+    ptr = np.asarray(ptr, np.int64)
+    n = len(ptr) - 1
+    kk = np.arange(n)
+    j = n - 1 - kk if descending else kk
+    ln = ptr[j + 1] - ptr[j]
+    islong = ln > long_row
+    nch = (ln + chunk - 1) // chunk
+    split = islong & (ln > split_row)
+    slots = np.where(split, nch, 0)
+    lrank = np.concatenate([[0], np.cumsum(islong)])          # exclusive, lrank[n] = long rows
+    longpos = kk[islong]
+    prev = np.where(lrank[:n] > 0, longpos[np.maximum(lrank[:n] - 1, 0)] if len(longpos) else -1, -1)
+    start = (~islong) & (((kk - prev - 1) % warps) == 0)
+    cnt = np.where(islong, np.where(split, nch + 1, 1), start.astype(np.int64))
+    goff = np.concatenate([[0], np.cumsum(cnt)])
+    soff = np.concatenate([[0], np.cumsum(slots)])
+    g = np.zeros((int(goff[n]), 4), np.int32)
+    nlong = int(lrank[n])
+    for k in range(n):
+        g0 = int(goff[k])
+        if not islong[k]:
+            if not start[k]:
+                continue
+            nxt = int(longpos[lrank[k]]) if lrank[k] < nlong else n
+            g[g0] = (k, GK_ROWS, min(warps, nxt - k), 0)
+        elif split[k]:
+            for c in range(int(nch[k])):
+                g[g0 + c] = (k, GK_CHUNK, c, int(soff[k]) + c)
+            g[g0 + int(nch[k])] = (k, GK_COMBINE, int(nch[k]), int(soff[k]))
+        else:
+            g[g0] = (k, GK_SHARED, 0, 0)
+    return g, int(soff[n])
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_scan_construction_matches_row_groups(lib, seed):
+    """The scan-based construction used on the device gives row_groups'
+    table exactly: random row lengths with runs of long rows, long rows at
+    both ends, and rows above the split length."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 3000))
+    ln = rng.integers(0, 40, n)
+    hot = rng.random(n) < [0.0, 0.01, 0.05, 0.2, 0.5, 0.9][seed]
+    ln[hot] = rng.integers(41, 400, hot.sum())
+    if n > 2 and seed % 2:
+        ln[0] = 500; ln[-1] = 300
+    ptr = np.concatenate([[0], np.cumsum(ln)])
+    for desc in (False, True):
+        for warps in (1, 3, 8):
+            ref, ns_ref = row_groups(lib, ptr, desc, warps, 40, 120, 50)
+            got, ns = scan_row_groups(ptr, desc, warps, 40, 120, 50)
+            assert ns == ns_ref
+            assert np.array_equal(got, ref), (desc, warps)
