@@ -7,6 +7,6 @@ what each function computes and which passage of the ParAC paper it follows.
 """
 from .oracle import (  # noqa: F401
     build, lib, philox4x64_10, slot_uniform, suffix_scan, pick_bruteforce, pick_search,
-    eliminate_one, ingest, factor, factor_tracked, dp_update, precond_apply, pcg,
+    eliminate_one, eliminate_one_ac, ingest, factor, factor_tracked, dp_update, precond_apply, pcg,
     OracleError, KIND_AUTO, KIND_LAPLACIAN, KIND_SDDM,
 )

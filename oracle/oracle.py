@@ -60,6 +60,10 @@ def _declare(L):
                                  P(C.c_void_p)]
     L.orc_factor_run_k.argtypes = [C.c_int64, i64p, i32p, f64p, i32p, C.c_int, C.c_uint64, C.c_uint64, C.c_int,
                                    P(C.c_void_p)]
+    L.orc_factor_run_ac.argtypes = [C.c_int64, i64p, i32p, f64p, i32p, C.c_int, C.c_uint64, C.c_uint64, C.c_int,
+                                    P(C.c_void_p)]
+    L.orc_eliminate_one_ac.argtypes = [C.c_int64, i32p, f64p, C.c_uint64, C.c_uint64, C.c_uint64,
+                                       i64p, f64p, i64p, i32p, f64p, i32p, f64p, i32p, i32p, f64p, i64p]
     L.orc_factor_tracked.argtypes = [C.c_int64, i64p, i32p, f64p, i32p, C.c_int, C.c_uint64, C.c_uint64,
                                      C.c_uint64, C.c_int, P(C.c_void_p)]
     L.orc_factor_dims.argtypes = [C.c_void_p, i64p, i64p, i64p]
@@ -161,6 +165,29 @@ def eliminate_one(rows, w, seed, k, sys=0, samples=1, L=None):
                 pick=spick[:ns].copy())
 
 
+def eliminate_one_ac(rows, w, seed, k, sys=0, L=None):
+    """One AC(k) pivot on gathered entries (orc_eliminate_one_ac): merged rows
+    and F column as eliminate_one; one slot per entry in (weight bits, row)
+    order, c[p-1] the weight of slot p, lo = hi = -1 where its sample is a
+    self-loop."""
+    L = L or lib()
+    rows = _arr(rows, np.int32); w = _arr(w, np.float64)
+    g = len(rows); m = max(g, 1)
+    d = C.c_int64(); D = C.c_double(); ns = C.c_int64()
+    mrow = np.zeros(m, np.int32); mw = np.zeros(m); mmult = np.zeros(m, np.int32); fval = np.zeros(m)
+    slo = np.zeros(m, np.int32); shi = np.zeros(m, np.int32); sc = np.zeros(m); spick = np.zeros(m, np.int64)
+    rc = L.orc_eliminate_one_ac(g, _p(rows, C.c_int32), _p(w, C.c_double), seed, k, sys, C.byref(d), C.byref(D),
+                                C.byref(ns), _p(mrow, C.c_int32), _p(mw, C.c_double), _p(mmult, C.c_int32),
+                                _p(fval, C.c_double), _p(slo, C.c_int32), _p(shi, C.c_int32), _p(sc, C.c_double),
+                                _p(spick, C.c_int64))
+    if rc:
+        raise OracleError(rc)
+    dd, nn = d.value, ns.value
+    return dict(d=dd, D=D.value, rows=mrow[:dd].copy(), w=mw[:dd].copy(), mult=mmult[:dd].copy(),
+                fval=fval[:dd].copy(), lo=slo[:nn].copy(), hi=shi[:nn].copy(), c=sc[:nn].copy(),
+                pick=spick[:nn].copy())
+
+
 def ingest(colptr, rowind, val, ordering=None, kind=KIND_AUTO, L=None):
     L = L or lib()
     colptr = _arr(colptr, np.int64); rowind = _arr(rowind, np.int32); val = _arr(val, np.float64)
@@ -192,15 +219,22 @@ def _collect(L, h):
                 depth=int(st[4]), violations=int(st[5]))
 
 
-def factor(colptr, rowind, val, ordering=None, seed=0, sys=0, kind=KIND_AUTO, samples=1, L=None):
+def factor(colptr, rowind, val, ordering=None, seed=0, sys=0, kind=KIND_AUTO, samples=1, ac=0, L=None):
     """Sequential rchol factor L ~ F D F^T in label space (Alg. 1 + Alg. 2;
     samples > 1: per-slot multi-sampling MS(samples), every clique-tree slot
-    drawing that many edges -- not Sec. VI's AC(2))."""
+    drawing that many edges -- not Sec. VI's AC(2); ac = k >= 1: AC(k), the
+    input's entries split into k parallel entries and the elimination run on
+    the multigraph, one clique-tree slot per entry, see orc_eliminate_ac)."""
     L = L or lib()
     colptr = _arr(colptr, np.int64); rowind = _arr(rowind, np.int32); val = _arr(val, np.float64)
     ordp = None if ordering is None else _arr(ordering, np.int32)
     h = C.c_void_p()
-    if samples == 1:
+    if ac:
+        if samples != 1:
+            raise ValueError("AC(k) takes one sample per slot")
+        rc = L.orc_factor_run_ac(len(colptr) - 1, _p(colptr, C.c_int64), _p(rowind, C.c_int32),
+                                 _p(val, C.c_double), _p(ordp, C.c_int32), kind, seed, sys, ac, C.byref(h))
+    elif samples == 1:
         rc = L.orc_factor_run(len(colptr) - 1, _p(colptr, C.c_int64), _p(rowind, C.c_int32),
                               _p(val, C.c_double), _p(ordp, C.c_int32), kind, seed, sys, C.byref(h))
     else:

@@ -64,6 +64,15 @@
  *      of weight e_j; e_j < -1e-12 * l_jj is not diagonally dominant.
  *   R8 dependency counters start at the number of stored lower entries of each
  *      row (with multiplicity; equals Sec. III's d_0 for duplicate-free input).
+ *   R9 AC(k) (Sec. VI: two samples per original entry, after Gao, Kyng and
+ *      Spielman).  Each strict-lower entry of the ingested matrix, ground
+ *      edges included, is split into k parallel entries of weight RN(w / k);
+ *      the elimination then runs on the multigraph: every gathered entry is
+ *      a clique-tree slot of its own (R2-R5 over the g entries instead of the
+ *      d merged ones; D_k = S[0] of that scan), a sample pairing two entries
+ *      of one row is a self-loop and adds nothing, and the factor column and
+ *      the counters use the merged rows of R1.  Unlike MS(k) (orc_eliminate_k),
+ *      fill entries are not resampled k times: each slot draws once.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -199,6 +208,7 @@ typedef struct {
     int32_t *slo, *shi; /* sampled edges (min, max label)    [ksamp * g], sample q of slot p at q*(d-1) + p-1 */
     double  *sc;        /* sampled edge weights              [ksamp * g] */
     int64_t *spick;     /* 0-based weight-order index picked [ksamp * g] */
+    int64_t ns;         /* sampled slots written (entries with slo < 0 are self-loops, no edge) */
 } orc_step;
 
 /* Eliminate pivot k whose gathered entries are (rows[i], w[i]), i < g.
@@ -231,6 +241,7 @@ static int orc_eliminate_k(int64_t g, const int32_t *rows, const double *w, uint
         i = j + 1;
     }
     st->d = d;
+    st->ns = (int64_t)ksamp * (d > 0 ? d - 1 : 0);
     if (d == 0) { st->D = 0.0; free(e); free(s); free(S); free(M); return ORC_OK; }
 
     for (int64_t i = 0; i < d; ++i) { s[i].row = st->mrow[i]; s[i].w = st->mw[i]; s[i].bits = dbits(st->mw[i]); }
@@ -264,6 +275,67 @@ static int orc_eliminate_k(int64_t g, const int32_t *rows, const double *w, uint
         }
     }
     free(e); free(s); free(S); free(M);
+    return ORC_OK;
+}
+
+/* AC(k) of Sec. VI (after Gao, Kyng and Spielman): the input's own entries
+ * are split into k parallel entries of weight w/k before the elimination
+ * (orc_factor_run_ac), and the elimination runs on the multigraph.  At a
+ * pivot every gathered entry -- an original copy or a fill entry -- is its
+ * own clique-tree slot: the entries are sorted by (weight bits, row) without
+ * merging (R2 over entries; equal keys are identical entries, so their
+ * order does not matter), the canonical suffix scan runs over all g of them
+ * (R3), D_k = S[1], and slot p = 1..g-1 samples by R4/R5 among the later
+ * entries.  A sample that pairs two entries of the same row is a self-loop
+ * and adds nothing (its Laplacian term is zero): no fill, no counter
+ * increment.  The factor column and the counters use the merged rows (R1):
+ * F(u,k) = -(run sum of u's entries) / D_k, multiplicity m_u.  slo = shi =
+ * -1 marks a self-loop; sc holds every slot's weight c_p. */
+static int orc_eliminate_ac(int64_t g, const int32_t *rows, const double *w, uint64_t seed,
+                            uint64_t k, uint64_t sys, orc_step *st)
+{
+    orc_ent *e = malloc(sizeof(orc_ent) * (size_t)(g > 0 ? g : 1));
+    double *S = malloc(sizeof(double) * (size_t)(g > 0 ? g : 1));
+    double *M = malloc(sizeof(double) * (size_t)(g > 0 ? g : 1));
+    double *ws = malloc(sizeof(double) * (size_t)(g > 0 ? g : 1));
+    if (!e || !S || !M || !ws) { free(e); free(S); free(M); free(ws); return ORC_ENOMEM; }
+
+    for (int64_t i = 0; i < g; ++i) { e[i].row = rows[i]; e[i].w = w[i]; e[i].bits = dbits(w[i]); }
+    qsort(e, (size_t)g, sizeof(orc_ent), cmp_row_bits);            /* R1: merged rows for F and the counters */
+    int64_t d = 0;
+    for (int64_t i = 0; i < g;) {
+        int64_t j = i;
+        double sum = e[i].w;
+        while (j + 1 < g && e[j + 1].row == e[i].row) { ++j; sum = sum + e[j].w; }
+        st->mrow[d] = e[i].row; st->mw[d] = sum; st->mmult[d] = (int32_t)(j - i + 1);
+        ++d;
+        i = j + 1;
+    }
+    st->d = d;
+    st->ns = g > 0 ? g - 1 : 0;
+    if (d == 0) { st->D = 0.0; free(e); free(S); free(M); free(ws); return ORC_OK; }
+
+    qsort(e, (size_t)g, sizeof(orc_ent), cmp_bits_row);            /* R2 over the entries */
+    for (int64_t i = 0; i < g; ++i) ws[i] = e[i].w;
+    orc_suffix_scan(g, ws, S);                                     /* R3 over the entries */
+    const double D = S[0];
+    st->D = D;
+    for (int64_t i = 0; i < d; ++i) st->fval[i] = -st->mw[i] / D;
+
+    M[g - 1] = S[g - 1];
+    for (int64_t j = g - 2; j >= 0; --j) M[j] = S[j] > M[j + 1] ? S[j] : M[j + 1];
+    for (int64_t p = 1; p <= g - 1; ++p) {                         /* R4, R5 per entry slot */
+        double v = orc_slot_uniform_s(seed, k, (uint64_t)p, sys, 0);
+        double R = S[p] * v;
+        int64_t j = orc_pick_search(g, M, p, R);
+        int32_t u = e[p - 1].row, x = e[j].row;
+        double c = (S[p] * e[p - 1].w) / D;
+        st->sc[p - 1] = c;
+        st->spick[p - 1] = j;
+        if (u == x) { st->slo[p - 1] = -1; st->shi[p - 1] = -1; }
+        else { st->slo[p - 1] = u < x ? u : x; st->shi[p - 1] = u < x ? x : u; }
+    }
+    free(e); free(S); free(M); free(ws);
     return ORC_OK;
 }
 
@@ -415,6 +487,7 @@ typedef struct {
     int64_t *level;         /* dependency-DAG level per label */
     int64_t max_gather, nfill, nnz_all;
     int ksamp;              /* samples per clique-tree slot (MS(ksamp)); 1 = Alg. 2 */
+    int ac;                 /* nonzero: AC(k) multigraph elimination (orc_eliminate_ac) */
 } orc_state;
 
 static void state_free(orc_state *S)
@@ -463,7 +536,8 @@ static int state_eliminate(orc_state *S, int64_t k, uint64_t seed, uint64_t sys,
     for (int64_t q = 0; q < S->fill[k].cnt; ++q) { rows[t] = S->fill[k].row[q]; w[t] = S->fill[k].w[q]; ++t; }
     free(S->fill[k].row); free(S->fill[k].w); memset(&S->fill[k], 0, sizeof(orc_fillcol));
 
-    int rc = orc_eliminate_k(g, rows, w, seed, (uint64_t)k, sys, ks, &st);
+    int rc = S->ac ? orc_eliminate_ac(g, rows, w, seed, (uint64_t)k, sys, &st)
+                   : orc_eliminate_k(g, rows, w, seed, (uint64_t)k, sys, ks, &st);
     free(rows); free(w);
     if (rc) return rc;
     S->D[k] = st.D;
@@ -477,8 +551,9 @@ static int state_eliminate(orc_state *S, int64_t k, uint64_t seed, uint64_t sys,
     int64_t lk = S->level[k] + 1;
     for (int64_t i = 0; i < st.d; ++i)
         if (S->level[st.mrow[i]] < lk) S->level[st.mrow[i]] = lk;
-    const int64_t nsamp = st.d > 0 ? (int64_t)ks * (st.d - 1) : 0;
+    const int64_t nsamp = st.ns;
     for (int64_t p = 0; p < nsamp; ++p) {
+        if (st.slo[p] < 0) continue;                      /* AC(k): a self-loop adds nothing */
         rc = fill_push(&S->fill[st.slo[p]], st.shi[p], st.sc[p]);
         if (rc) return rc;
         S->nfill++;
@@ -546,6 +621,43 @@ int orc_factor_run_k(int64_t n, const int64_t *colptr, const int32_t *rowind, co
     S.ksamp = ksamp;
     int rc = orc_ingest(n, colptr, rowind, val, ordering, kind, &S.L);
     if (rc) return rc;
+    rc = state_init(&S);
+    for (int64_t k = 0; !rc && k < S.L.n; ++k) rc = state_eliminate(&S, k, seed, sys, NULL);
+    if (!rc) rc = state_to_factor(&S, out);
+    state_free(&S);
+    return rc;
+}
+
+/* AC(k): every strict-lower entry of the ingested matrix (ground edges
+ * included) split into k parallel entries of weight RN(w / k), then the
+ * multigraph elimination of orc_eliminate_ac. */
+int orc_factor_run_ac(int64_t n, const int64_t *colptr, const int32_t *rowind, const double *val,
+                      const int32_t *ordering, int kind, uint64_t seed, uint64_t sys, int ksplit, orc_factor **out)
+{
+    *out = NULL;
+    if (ksplit < 1) return ORC_EINVAL;
+    orc_state S;
+    memset(&S, 0, sizeof S);
+    S.ksamp = 1;
+    S.ac = 1;
+    int rc = orc_ingest(n, colptr, rowind, val, ordering, kind, &S.L);
+    if (rc) return rc;
+    {
+        const int64_t nl = S.L.n, m = S.L.colptr[nl];
+        int64_t *cp = malloc(sizeof(int64_t) * (size_t)(nl + 1));
+        int32_t *row = malloc(sizeof(int32_t) * (size_t)(m * ksplit > 0 ? m * ksplit : 1));
+        double *w = malloc(sizeof(double) * (size_t)(m * ksplit > 0 ? m * ksplit : 1));
+        if (!cp || !row || !w) { free(cp); free(row); free(w); low_free(&S.L); return ORC_ENOMEM; }
+        cp[0] = 0;
+        for (int64_t c = 0; c < nl; ++c) {
+            int64_t t = cp[c];
+            for (int64_t q = S.L.colptr[c]; q < S.L.colptr[c + 1]; ++q)
+                for (int r = 0; r < ksplit; ++r) { row[t] = S.L.row[q]; w[t] = S.L.w[q] / (double)ksplit; ++t; }
+            cp[c + 1] = t;
+        }
+        free(S.L.colptr); free(S.L.row); free(S.L.w);
+        S.L.colptr = cp; S.L.row = row; S.L.w = w;
+    }
     rc = state_init(&S);
     for (int64_t k = 0; !rc && k < S.L.n; ++k) rc = state_eliminate(&S, k, seed, sys, NULL);
     if (!rc) rc = state_to_factor(&S, out);
@@ -709,7 +821,7 @@ int orc_eliminate_one(int64_t g, const int32_t *rows, const double *w, uint64_t 
                       int32_t *mmult, double *fval, int32_t *slo, int32_t *shi, double *sc,
                       int64_t *spick)
 {
-    orc_step st = { 0, 0.0, mrow, mw, mmult, fval, slo, shi, sc, spick };
+    orc_step st = { 0, 0.0, mrow, mw, mmult, fval, slo, shi, sc, spick, 0 };
     int rc = orc_eliminate(g, rows, w, seed, k, sys, &st);
     *d_out = st.d; *D_out = st.D;
     return rc;
@@ -722,9 +834,21 @@ int orc_eliminate_one_k(int64_t g, const int32_t *rows, const double *w, uint64_
                         int32_t *mmult, double *fval, int32_t *slo, int32_t *shi, double *sc, int64_t *spick)
 {
     if (ksamp < 1) return ORC_EINVAL;
-    orc_step st = { 0, 0.0, mrow, mw, mmult, fval, slo, shi, sc, spick };
+    orc_step st = { 0, 0.0, mrow, mw, mmult, fval, slo, shi, sc, spick, 0 };
     int rc = orc_eliminate_k(g, rows, w, seed, k, sys, ksamp, &st);
     *d_out = st.d; *D_out = st.D;
+    return rc;
+}
+
+/* One AC(k) pivot (orc_eliminate_ac) on gathered entries; the slot arrays
+ * need room for g entries; *ns_out receives the slot count (g - 1). */
+int orc_eliminate_one_ac(int64_t g, const int32_t *rows, const double *w, uint64_t seed, uint64_t k,
+                         uint64_t sys, int64_t *d_out, double *D_out, int64_t *ns_out, int32_t *mrow, double *mw,
+                         int32_t *mmult, double *fval, int32_t *slo, int32_t *shi, double *sc, int64_t *spick)
+{
+    orc_step st = { 0, 0.0, mrow, mw, mmult, fval, slo, shi, sc, spick, 0 };
+    int rc = orc_eliminate_ac(g, rows, w, seed, k, sys, &st);
+    *d_out = st.d; *D_out = st.D; *ns_out = st.ns;
     return rc;
 }
 

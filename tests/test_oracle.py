@@ -571,7 +571,7 @@ def test_ac2_counter_word_and_weights():
             assert two["c"][m + p - 1] == two["c"][p - 1]
 
 
-def test_ac2_unbiased_by_enumeration():
+def test_ms2_unbiased_by_enumeration():
     """MS(2): summed over all outcomes of both samples of every slot, the
     expected update equals the exact Schur complement update, as for Alg. 2."""
     rng = np.random.default_rng(19)
@@ -597,7 +597,7 @@ def test_ac2_unbiased_by_enumeration():
         assert np.allclose(E, Cex, rtol=0, atol=1e-14 * max(1.0, np.abs(Cex).max()))
 
 
-def test_ac2_factor_counts_mean_and_variance():
+def test_ms2_factor_counts_mean_and_variance():
     """MS(2) appends twice the fill edges of Alg. 2; paths stay exact; the mean
     of F D F^T over seeds matches L within 4 standard errors, with a smaller
     variance than Alg. 2's (the reason for more samples)."""
@@ -628,3 +628,126 @@ def test_ac2_factor_counts_mean_and_variance():
         assert np.all(np.abs(mean - Ad) <= 4 * se + 1e-10 * np.abs(Ad).max())
         stats[ks] = var.sum()
     assert stats[2] < stats[1]
+
+
+# ----------------------------------------------------------------- AC(k): Sec. VI's multigraph variant
+def _ac_expected_update(rows_e, w_e, out):
+    """E[sampled clique] of one AC(k) pivot over every outcome: slots are the
+    entries in (weight, row) order, slot p picks later entry j with
+    probability w_j / S[p] and adds c_p (b_u - b_x)(b_u - b_x)^T, which is
+    zero for a self-loop (u = x)."""
+    order = np.lexsort((rows_e, w_e))
+    ws = w_e[order]; rs = rows_e[order]
+    g = len(ws)
+    idx = {r: i for i, r in enumerate(out["rows"])}
+    d = len(out["rows"])
+    S = np.cumsum(ws[::-1])[::-1]
+    E = np.zeros((d, d))
+    for p in range(1, g):
+        c = out["c"][p - 1]
+        a = idx[rs[p - 1]]
+        for j in range(p, g):
+            b = idx[rs[j]]
+            if a == b:
+                continue
+            prob = ws[j] / S[p]
+            E[a, a] += prob * c; E[b, b] += prob * c; E[a, b] -= prob * c; E[b, a] -= prob * c
+    return E
+
+
+def test_acsplit_unbiased_by_enumeration():
+    """AC(k), one pivot on a multiset with repeated rows (split copies of equal
+    weight, fill entries of other weights): summed over every outcome of
+    every slot the update is the exact Schur complement of the merged star,
+    diag(w_u) - w w^T / D (Sec. II-B, with the self-loop terms zero); the
+    pivot is the total weight, F(u,k) = -w_u / D, self-loops are exactly the
+    slots whose pick shares their row, and every slot carries c_p = S[p] w_p / D."""
+    rng = np.random.default_rng(31)
+    for trial in range(300):
+        nr = int(rng.integers(1, 5))
+        base = np.arange(200, 200 + nr, dtype=np.int32)
+        mult = rng.integers(1, 4, nr)
+        rows_e = np.repeat(base, mult)
+        w_e = np.concatenate([np.full(m, rng.lognormal(0, 1)) if rng.random() < 0.5 else rng.lognormal(0, 1, m)
+                              for m in mult])
+        perm = rng.permutation(len(rows_e))
+        rows_e, w_e = rows_e[perm], w_e[perm]
+        out = oracle.eliminate_one_ac(rows_e, w_e, seed=trial, k=4)
+        g = len(rows_e)
+        assert out["d"] == nr and len(out["c"]) == g - 1
+        wm = np.array([w_e[rows_e == r].sum() for r in out["rows"]])
+        assert np.allclose(out["w"], wm, rtol=1e-15, atol=0)
+        assert np.array_equal(out["mult"], [int((rows_e == r).sum()) for r in out["rows"]])
+        D = out["D"]
+        assert abs(D - w_e.sum()) <= 1e-14 * w_e.sum()
+        assert np.allclose(out["fval"], -out["w"] / D, rtol=1e-15, atol=0)
+        order = np.lexsort((rows_e, w_e))
+        ws, rs = w_e[order], rows_e[order]
+        S = np.cumsum(ws[::-1])[::-1]
+        for p in range(1, g):
+            assert abs(out["c"][p - 1] - S[p] * ws[p - 1] / D) <= 1e-14 * abs(out["c"][p - 1]) + 1e-300
+            j = out["pick"][p - 1]
+            assert p <= j < g
+            loop = rs[j] == rs[p - 1]
+            assert (out["lo"][p - 1] == -1) == loop and (out["hi"][p - 1] == -1) == loop
+            if not loop:
+                assert (out["lo"][p - 1], out["hi"][p - 1]) == (min(rs[j], rs[p - 1]), max(rs[j], rs[p - 1]))
+        E = _ac_expected_update(rows_e, w_e, out)
+        Cex = np.diag(out["w"]) - np.outer(out["w"], out["w"]) / D
+        assert np.allclose(E, Cex, rtol=0, atol=1e-13 * max(1.0, np.abs(Cex).max()))
+
+
+@pytest.mark.parametrize("n", [2, 5, 40])
+def test_acsplit_one_copy_on_paths_is_alg2(n):
+    """With one copy per entry and no repeated row in any gathered list (a
+    path: eliminating a vertex links its two neighbours, which were not
+    adjacent), AC(1) takes exactly Alg. 2's steps: the same factor, bit for
+    bit, under any ordering."""
+    rng = np.random.default_rng(n)
+    a, b = W.path_edges(n)
+    A = _mat(n, a, b, rng.uniform(0.5, 2.0, len(a)))
+    for s in range(5):
+        perm = W.random_ordering(n, s)
+        F1 = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=s)
+        Fa = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=s, ac=1)
+        assert np.array_equal(F1["colptr"], Fa["colptr"]) and np.array_equal(F1["row"], Fa["row"])
+        assert np.array_equal(F1["val"].view(np.uint64), Fa["val"].view(np.uint64))
+        assert np.array_equal(np.asarray(F1["D"]).view(np.uint64), np.asarray(Fa["D"]).view(np.uint64))
+
+
+def test_acsplit_factor_mean_matches_L():
+    """AC(2) on a dense 6-vertex graph: every sampled factor has the zero row
+    sums of a Laplacian, and over 20,000 seeds the mean of F D F^T is L
+    within 4 standard errors (the factorization is unbiased, Sec. II-B)."""
+    rng = np.random.default_rng(41)
+    n = 6
+    ia, ib = np.triu_indices(n, 1)
+    A = _mat(n, ia, ib, rng.uniform(0.2, 3, len(ia)))
+    perm = W.random_ordering(n, 5)
+    L = oracle.lib()
+    nseeds = 20_000
+    acc = np.zeros((n, n)); acc2 = np.zeros((n, n))
+    for s in range(nseeds):
+        G = reconstruct(oracle.factor(A.colptr, A.rowind, A.val, perm, seed=s, ac=2, L=L), perm)
+        assert np.abs(G.sum(axis=1)).max() <= 1e-12 * np.abs(G).max()
+        acc += G; acc2 += G * G
+    mean = acc / nseeds
+    se = np.sqrt(np.maximum(acc2 / nseeds - mean ** 2, 0) / nseeds)
+    Ad = A.dense()
+    assert np.all(np.abs(mean - Ad) <= 4 * se + 1e-10 * np.abs(Ad).max())
+
+
+def test_acsplit_denser_than_alg2_far_below_ms2():
+    """On the 64x64 grid AC(2) keeps more of the factor than Alg. 2 (more
+    slots per pivot) while its fill stays within a small multiple of Alg.
+    2's; MS(2), whose fill entries are resampled at every later pivot,
+    grows far more.  Grounded SDDM input splits its ground edges too."""
+    A, perm, seed, _ = W.config("grid2d-64")
+    F1 = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed)
+    Fa = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed, ac=2)
+    Fm = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=seed, samples=2)
+    assert len(Fa["row"]) > len(F1["row"]) and Fa["fill"] > F1["fill"]
+    assert Fa["fill"] < 4 * F1["fill"] < Fm["fill"]
+    B, pb, sb, _ = W.config("poisson-contrast-16")
+    Fb = oracle.factor(B.colptr, B.rowind, B.val, pb, seed=sb, ac=2)
+    assert Fb["n"] == B.n and np.all(np.asarray(Fb["D"]) > 0)
