@@ -67,3 +67,32 @@ def test_pcg_many_binding_checks_lengths():
     from paper_2505_02977_gb300 import parac
     with pytest.raises(ValueError):
         parac.parac_pcg_many([object(), object()], [None])
+
+
+def test_opts_layout_matches_header(tmp_path):
+    """The binding's parac_opts has the header's size and every field at the
+    header's offset (a C program built against include/parac.h prints them),
+    and parac_opts_default fills the documented defaults through it."""
+    import shutil
+    import subprocess
+    from paper_2505_02977_gb300 import parac
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    fields = [f[0] for f in parac.parac_opts._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "parac.h"\nint main(void) {\n'
+                   '    printf("size %zu\\n", sizeof(parac_opts));\n'
+                   + "".join(f'    printf("{f} %zu\\n", offsetof(parac_opts, {f}));\n' for f in fields)
+                   + "    return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    assert int(got["size"]) == ctypes.sizeof(parac.parac_opts)
+    for f in fields:
+        assert int(got[f]) == getattr(parac.parac_opts, f).offset, f
+    o = parac.parac_opts_default()
+    assert o.g_precision == 64 and o.max_pool_regrow == 2 and o.spin_limit == 1 << 24 and o.samples == 1
+    assert o.grid_help == parac.DEFAULT and o.grid_help_min == 0 and o.host_tables == parac.DEFAULT
+    assert o.order == parac.ORDER_GIVEN and o.trace_path is None
