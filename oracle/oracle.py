@@ -66,6 +66,8 @@ def _declare(L):
                                        i64p, f64p, i64p, i32p, f64p, i32p, f64p, i32p, i32p, f64p, i64p]
     L.orc_factor_tracked.argtypes = [C.c_int64, i64p, i32p, f64p, i32p, C.c_int, C.c_uint64, C.c_uint64,
                                      C.c_uint64, C.c_int, P(C.c_void_p)]
+    L.orc_factor_tracked_ac.argtypes = [C.c_int64, i64p, i32p, f64p, i32p, C.c_int, C.c_uint64, C.c_uint64,
+                                        C.c_uint64, C.c_int, C.c_int, P(C.c_void_p)]
     L.orc_factor_dims.argtypes = [C.c_void_p, i64p, i64p, i64p]
     L.orc_factor_copy.argtypes = [C.c_void_p, i64p, i32p, f64p, f64p]
     L.orc_factor_free.argtypes = [C.c_void_p]
@@ -246,15 +248,16 @@ def factor(colptr, rowind, val, ordering=None, seed=0, sys=0, kind=KIND_AUTO, sa
 
 
 def factor_tracked(colptr, rowind, val, ordering=None, seed=0, sys=0, kind=KIND_AUTO, sched_seed=1,
-                   check=True, L=None):
-    """Counter-scheduled factor (Sec. III) with a random pick among ready vertices."""
+                   check=True, ac=0, L=None):
+    """Counter-scheduled factor (Sec. III) with a random pick among ready
+    vertices (ac = k >= 1: the AC(k) multigraph elimination, see factor)."""
     L = L or lib()
     colptr = _arr(colptr, np.int64); rowind = _arr(rowind, np.int32); val = _arr(val, np.float64)
     ordp = None if ordering is None else _arr(ordering, np.int32)
     h = C.c_void_p()
-    rc = L.orc_factor_tracked(len(colptr) - 1, _p(colptr, C.c_int64), _p(rowind, C.c_int32),
-                              _p(val, C.c_double), _p(ordp, C.c_int32), kind, seed, sys, sched_seed,
-                              1 if check else 0, C.byref(h))
+    rc = L.orc_factor_tracked_ac(len(colptr) - 1, _p(colptr, C.c_int64), _p(rowind, C.c_int32),
+                                 _p(val, C.c_double), _p(ordp, C.c_int32), kind, seed, sys, sched_seed,
+                                 1 if check else 0, ac, C.byref(h))
     if rc:
         raise OracleError(rc)
     return _collect(L, h)

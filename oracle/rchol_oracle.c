@@ -628,6 +628,27 @@ int orc_factor_run_k(int64_t n, const int64_t *colptr, const int32_t *rowind, co
     return rc;
 }
 
+/* Every strict-lower entry of L split into k parallel entries of weight
+ * RN(w / k), in place of the entry (AC(k), reading R9). */
+static int low_split(orc_low *L, int k)
+{
+    const int64_t nl = L->n, m = L->colptr[nl];
+    int64_t *cp = malloc(sizeof(int64_t) * (size_t)(nl + 1));
+    int32_t *row = malloc(sizeof(int32_t) * (size_t)(m * k > 0 ? m * k : 1));
+    double *w = malloc(sizeof(double) * (size_t)(m * k > 0 ? m * k : 1));
+    if (!cp || !row || !w) { free(cp); free(row); free(w); return ORC_ENOMEM; }
+    cp[0] = 0;
+    for (int64_t c = 0; c < nl; ++c) {
+        int64_t t = cp[c];
+        for (int64_t q = L->colptr[c]; q < L->colptr[c + 1]; ++q)
+            for (int r = 0; r < k; ++r) { row[t] = L->row[q]; w[t] = L->w[q] / (double)k; ++t; }
+        cp[c + 1] = t;
+    }
+    free(L->colptr); free(L->row); free(L->w);
+    L->colptr = cp; L->row = row; L->w = w;
+    return ORC_OK;
+}
+
 /* AC(k): every strict-lower entry of the ingested matrix (ground edges
  * included) split into k parallel entries of weight RN(w / k), then the
  * multigraph elimination of orc_eliminate_ac. */
@@ -642,22 +663,8 @@ int orc_factor_run_ac(int64_t n, const int64_t *colptr, const int32_t *rowind, c
     S.ac = 1;
     int rc = orc_ingest(n, colptr, rowind, val, ordering, kind, &S.L);
     if (rc) return rc;
-    {
-        const int64_t nl = S.L.n, m = S.L.colptr[nl];
-        int64_t *cp = malloc(sizeof(int64_t) * (size_t)(nl + 1));
-        int32_t *row = malloc(sizeof(int32_t) * (size_t)(m * ksplit > 0 ? m * ksplit : 1));
-        double *w = malloc(sizeof(double) * (size_t)(m * ksplit > 0 ? m * ksplit : 1));
-        if (!cp || !row || !w) { free(cp); free(row); free(w); low_free(&S.L); return ORC_ENOMEM; }
-        cp[0] = 0;
-        for (int64_t c = 0; c < nl; ++c) {
-            int64_t t = cp[c];
-            for (int64_t q = S.L.colptr[c]; q < S.L.colptr[c + 1]; ++q)
-                for (int r = 0; r < ksplit; ++r) { row[t] = S.L.row[q]; w[t] = S.L.w[q] / (double)ksplit; ++t; }
-            cp[c + 1] = t;
-        }
-        free(S.L.colptr); free(S.L.row); free(S.L.w);
-        S.L.colptr = cp; S.L.row = row; S.L.w = w;
-    }
+    rc = low_split(&S.L, ksplit);
+    if (rc) { low_free(&S.L); return rc; }
     rc = state_init(&S);
     for (int64_t k = 0; !rc && k < S.L.n; ++k) rc = state_eliminate(&S, k, seed, sys, NULL);
     if (!rc) rc = state_to_factor(&S, out);
@@ -676,7 +683,8 @@ int orc_factor_run(int64_t n, const int64_t *colptr, const int32_t *rowind, cons
 /* ------------------------------------------------------------------------ */
 
 /* One pivot's counter update, in the paper's order: for every sampled edge
- * (a,b), dp[max(a,b)] += 1; then for every merged neighbour u with
+ * (a,b), dp[max(a,b)] += 1 (a < 0 marks an AC(k) self-loop: no edge); then
+ * for every merged neighbour u with
  * multiplicity m, r = dp[u]; dp[u] -= m; u is enqueued when r == m (a
  * positive-to-zero transition).  If deletes_first is nonzero the two phases
  * are swapped and a vertex is enqueued whenever its counter reads zero
@@ -688,7 +696,7 @@ int64_t orc_dp_update(int32_t *dp, int64_t nsamp, const int32_t *sa, const int32
 {
     int64_t ne = 0;
     if (!deletes_first) {
-        for (int64_t s = 0; s < nsamp; ++s) dp[sa[s] > sb[s] ? sa[s] : sb[s]] += 1;
+        for (int64_t s = 0; s < nsamp; ++s) if (sa[s] >= 0) dp[sa[s] > sb[s] ? sa[s] : sb[s]] += 1;
         for (int64_t i = 0; i < nnbr; ++i) {
             int32_t r = dp[nbr[i]];
             dp[nbr[i]] = r - mult[i];
@@ -699,7 +707,7 @@ int64_t orc_dp_update(int32_t *dp, int64_t nsamp, const int32_t *sa, const int32
             dp[nbr[i]] -= mult[i];
             if (dp[nbr[i]] == 0) enq[ne++] = nbr[i];
         }
-        for (int64_t s = 0; s < nsamp; ++s) dp[sa[s] > sb[s] ? sa[s] : sb[s]] += 1;
+        for (int64_t s = 0; s < nsamp; ++s) if (sa[s] >= 0) dp[sa[s] > sb[s] ? sa[s] : sb[s]] += 1;
     }
     return ne;
 }
@@ -718,16 +726,22 @@ static uint64_t splitmix64(uint64_t *s)
     return z ^ (z >> 31);
 }
 
-int orc_factor_tracked(int64_t n, const int64_t *colptr, const int32_t *rowind, const double *val,
-                       const int32_t *ordering, int kind, uint64_t seed, uint64_t sys,
-                       uint64_t sched_seed, int check, orc_factor **out)
+int orc_factor_tracked_ac(int64_t n, const int64_t *colptr, const int32_t *rowind, const double *val,
+                          const int32_t *ordering, int kind, uint64_t seed, uint64_t sys,
+                          uint64_t sched_seed, int check, int ksplit, orc_factor **out)
 {
     *out = NULL;
+    if (ksplit < 0) return ORC_EINVAL;
     orc_state S;
     memset(&S, 0, sizeof S);
     S.ksamp = 1;
+    S.ac = ksplit > 0;
     int rc = orc_ingest(n, colptr, rowind, val, ordering, kind, &S.L);
     if (rc) return rc;
+    if (ksplit > 0) {
+        rc = low_split(&S.L, ksplit);
+        if (rc) { low_free(&S.L); return rc; }
+    }
     rc = state_init(&S);
     int64_t nl = S.L.n;
     size_t nn = (size_t)(nl > 0 ? nl : 1);
@@ -753,7 +767,7 @@ int orc_factor_tracked(int64_t n, const int64_t *colptr, const int32_t *rowind, 
         if (rc) break;
         done[k] = 1;
         eliminated++;
-        int64_t ne = orc_dp_update(dp, st.d > 0 ? st.d - 1 : 0, st.slo, st.shi, st.d, st.mrow, st.mmult, enq, 0);
+        int64_t ne = orc_dp_update(dp, st.ns, st.slo, st.shi, st.d, st.mrow, st.mmult, enq, 0);
         for (int64_t i = 0; i < ne; ++i) ready[nready++] = enq[i];
         step_free(&st);
         if (check) {
@@ -786,6 +800,13 @@ int orc_factor_tracked(int64_t n, const int64_t *colptr, const int32_t *rowind, 
     free(dp); free(ready); free(done); free(recount); free(enq);
     state_free(&S);
     return rc;
+}
+
+int orc_factor_tracked(int64_t n, const int64_t *colptr, const int32_t *rowind, const double *val,
+                       const int32_t *ordering, int kind, uint64_t seed, uint64_t sys,
+                       uint64_t sched_seed, int check, orc_factor **out)
+{
+    return orc_factor_tracked_ac(n, colptr, rowind, val, ordering, kind, seed, sys, sched_seed, check, 0, out);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -751,3 +751,23 @@ def test_acsplit_denser_than_alg2_far_below_ms2():
     B, pb, sb, _ = W.config("poisson-contrast-16")
     Fb = oracle.factor(B.colptr, B.rowind, B.val, pb, seed=sb, ac=2)
     assert Fb["n"] == B.n and np.all(np.asarray(Fb["D"]) > 0)
+
+
+@pytest.mark.parametrize("s", range(3))
+def test_acsplit_counter_schedule_invariants_and_bit_identity(s):
+    """AC(2) under the dependency counters of Sec. III: the counters start at
+    the split copies (two per input entry), self-loop samples add no edge and
+    no increment, and after every pivot they equal a recount of the entries
+    still waiting; ready vertices are pairwise non-adjacent; and whatever
+    ready vertex is taken next, the factor is the label-order one, bit for
+    bit (entries of equal key are identical, so the sorts are canonical)."""
+    rng = np.random.default_rng(500 + s)
+    n = int(rng.integers(40, 160))
+    a, b = W.sparse_random_edges(n, 3 * n, s)
+    A = _mat(n, a, b, rng.lognormal(0, 1, len(a)))
+    perm = W.random_ordering(n, s)
+    ref = oracle.factor(A.colptr, A.rowind, A.val, perm, seed=70 + s, ac=2)
+    for sched in (1, 2, 3):
+        T = oracle.factor_tracked(A.colptr, A.rowind, A.val, perm, seed=70 + s, sched_seed=sched, check=True, ac=2)
+        assert T["violations"] == 0
+        assert same_factor(T, ref)
